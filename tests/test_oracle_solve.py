@@ -1,0 +1,297 @@
+"""Pins of the oracle's per-Gaussian Newton solves (Eq. local_newton and the
+position / scaling / rotation / opacity / colour solves of Sec. 4.2)."""
+import math
+
+import numpy as np
+import scipy.linalg
+from scipy.spatial.transform import Rotation
+
+from oracle import oracle as O
+from paper_2501_13975_b300 import synth
+from tests.oracle_scenes import NOTHRESH, micro_camera, micro_scene
+
+
+def _pack(H):
+    D = H.shape[0]
+    return np.array([H[a, b] for a in range(D) for b in range(a, D)])
+
+
+def _spd(rng, D, cond=10.0):
+    Q, _ = np.linalg.qr(rng.standard_normal((D, D)))
+    ev = np.geomspace(1.0, cond, D)
+    return Q @ np.diag(ev) @ Q.T
+
+
+def test_damped_cholesky_matches_numpy():
+    """Colour blocks go through the plain damped solve: (H + mu0 m I) x = -g with
+    m = mean |diag H|, against numpy.linalg.solve."""
+    rng = np.random.default_rng(0)
+    sc = synth.tiny_scene(n=4, sh_degree=3)
+    S, n = 16, 4
+    g = rng.standard_normal((3, S, n))
+    H = np.zeros((3, S * (S + 1) // 2, n))
+    Hf = {}
+    for ch in range(3):
+        for k in range(n):
+            A = _spd(rng, S, 1e3)
+            Hf[ch, k] = A
+            H[ch, :, k] = _pack(A)
+    r = O.solve(O.COLOR, sc, synth.ring_cameras()[0], g, H, dict(damping_mu0=1e-4))
+    for ch in range(3):
+        for k in range(n):
+            A = Hf[ch, k]
+            m = np.abs(np.diag(A)).mean()
+            x = np.linalg.solve(A + 1e-4 * m * np.eye(S), -g[ch, :, k])
+            assert np.allclose(r["step"][ch, :, k], x, rtol=1e-10, atol=1e-12)
+            assert r["status"][ch, k] == 0
+
+
+def test_damping_ladder_on_indefinite_block():
+    """An indefinite block is shifted by mu0 10^i m I for the smallest i that
+    makes it positive definite (Cholesky succeeds), textbook eigenvalue check."""
+    rng = np.random.default_rng(1)
+    sc = synth.tiny_scene(n=6, sh_degree=1)
+    S, n = 4, 6
+    g = rng.standard_normal((3, S, n))
+    H = np.zeros((3, 10, n))
+    mats = {}
+    for k in range(n):
+        Q, _ = np.linalg.qr(rng.standard_normal((S, S)))
+        ev = np.array([-10.0 ** (-k), 0.5, 1.0, 2.0])
+        A = Q @ np.diag(ev) @ Q.T
+        mats[k] = A
+        for ch in range(3):
+            H[ch, :, k] = _pack(A)
+    r = O.solve(O.COLOR, sc, synth.ring_cameras()[0], g, H, dict(damping_mu0=1e-4))
+    for k in range(n):
+        A = mats[k]
+        m = np.abs(np.diag(A)).mean()
+        want = None
+        for i in range(7):
+            mu = 1e-4 * 10 ** i
+            if np.linalg.eigvalsh(A + mu * m * np.eye(S)).min() > 0:
+                want = mu
+                break
+        assert want is not None
+        assert math.isclose(r["info"][0, 0, k], want, rel_tol=1e-12)
+        x = np.linalg.solve(A + want * m * np.eye(S), -g[0, :, k])
+        assert np.allclose(r["step"][0, :, k], x, rtol=1e-9)
+
+
+def test_no_contribution_gives_zero_step():
+    sc = synth.tiny_scene(n=3)
+    cam = synth.ring_cameras()[0]
+    for grp in O.GROUPS:
+        gs, hs = O.block_shapes(grp, 3, 1)
+        r = O.solve(grp, sc, cam, np.zeros(gs), np.zeros(hs))
+        assert np.all(r["step"] == 0) and np.all(r["status"] == 2)
+
+
+def test_position_step_is_plane_minimiser():
+    """Delta p lies in the plane perpendicular to r (primary view) and minimises
+    g.d + 1/2 d^T H d over that plane (basis-independent: scipy null space)."""
+    rng = np.random.default_rng(2)
+    n = 8
+    sc = micro_scene(n, 3)
+    cam = micro_camera(eye=(0.3, 0.4, -0.5))
+    g = rng.standard_normal((3, n))
+    H = np.zeros((6, n))
+    mats = []
+    for k in range(n):
+        A = _spd(rng, 3, 20.0)
+        mats.append(A)
+        H[:, k] = _pack(A)
+    r = O.solve(O.POS, sc, cam, g, H, dict(damping_mu0=0.0))
+    o = cam.center()
+    for k in range(n):
+        rr = sc.mean[:, k].astype(np.float64) - o
+        rr /= np.linalg.norm(rr)
+        d = r["step"][:, k]
+        assert abs(d @ rr) < 1e-12 * np.linalg.norm(d)
+        N = scipy.linalg.null_space(rr[None, :])
+        v = np.linalg.solve(N.T @ mats[k] @ N, -N.T @ g[:, k])
+        assert np.allclose(d, N @ v, rtol=1e-10)
+
+
+def _eig_jacobian(sc, k, cam, eps=1e-6):
+    """d lambda / d s of the projected (no low-pass) covariance, by FD of numpy's
+    eigvalsh of the oracle's Sigma2D."""
+    base = O.scene_handle(sc)
+    J = np.zeros((2, 3))
+    for j in range(3):
+        vals = []
+        for sgn in (1, -1):
+            h = O._SceneHandle(base)
+            h.scale[j, k] += sgn * eps
+            s2 = O.project(h, cam, dict(lowpass=0.0))["sigma2d"][:, k]
+            vals.append(np.linalg.eigvalsh(np.array([[s2[0], s2[1]], [s2[1], s2[2]]])))
+        J[:, j] = (vals[0] - vals[1]) / (2 * eps)
+    return J
+
+
+def test_scale_step_is_newton_on_eigen_subspace():
+    """Delta s = B (B^T H B)^{-1} (-B^T g) for any orthonormal basis B of the row
+    space of d lambda / d s (the eigenvalue Jacobian of the projected
+    covariance, here by FD), i.e. the reduced solve is basis independent."""
+    rng = np.random.default_rng(4)
+    n = 6
+    sc = micro_scene(n, 5)
+    cam = micro_camera()
+    g = 0.01 * rng.standard_normal((3, n))     # small steps: s stays positive
+    H = np.zeros((6, n))
+    mats = []
+    for k in range(n):
+        A = _spd(rng, 3, 5.0)
+        mats.append(A)
+        H[:, k] = _pack(A)
+    r = O.solve(O.SCALE, O.scene_handle(sc), cam, g, H, dict(damping_mu0=0.0, scale_trust=1e30))
+    for k in range(n):
+        Jl = _eig_jacobian(sc, k, cam)
+        B = scipy.linalg.orth(Jl.T)
+        assert B.shape[1] == 2
+        want = B @ np.linalg.solve(B.T @ mats[k] @ B, -B.T @ g[:, k])
+        assert np.allclose(r["step"][:, k], want, rtol=2e-6, atol=1e-9)
+
+
+def test_scale_trust_bound():
+    """The scale update stays within [s / kappa, kappa s] per axis."""
+    rng = np.random.default_rng(14)
+    n = 20
+    sc = micro_scene(n, 15)
+    cam = micro_camera()
+    g = 50.0 * rng.standard_normal((3, n))
+    H = np.zeros((6, n))
+    for k in range(n):
+        H[:, k] = _pack(_spd(rng, 3, 5.0))
+    r = O.solve(O.SCALE, sc, cam, g, H, dict(damping_mu0=0.0, scale_trust=2.0))
+    s = sc.scale.astype(np.float64)
+    ns = s + r["step"]
+    assert np.all(ns >= s / 2 - 1e-15) and np.all(ns <= 2 * s + 1e-15)
+    assert np.any(np.isclose(ns, 2 * s)) and np.any(np.isclose(ns, s / 2))
+
+
+def test_rotation_apply_is_rotation_about_view_axis():
+    """q <- dq(theta) (x) q rotates the ellipsoid about the primary view direction
+    by theta, keeping |q| = 1."""
+    sc = micro_scene(5, 6)
+    cam = micro_camera(eye=(0.2, -0.1, 0.3))
+    theta = np.array([[0.3, -0.7, 1.1, 0.0, 2.5]])
+    h = O.apply(O.ROT, sc, cam, theta)
+    o = cam.center()
+    for k in range(5):
+        a = sc.mean[:, k].astype(np.float64) - o
+        a /= np.linalg.norm(a)
+        w, x, y, z = sc.quat[:, k].astype(np.float64)
+        want = (Rotation.from_rotvec(theta[0, k] * a) * Rotation.from_quat([x, y, z, w])).as_matrix()
+        w2, x2, y2, z2 = h.quat[:, k]
+        got = Rotation.from_quat([x2, y2, z2, w2]).as_matrix()
+        assert np.allclose(got, want, atol=1e-12)
+        assert abs(np.linalg.norm(h.quat[:, k]) - 1) < 1e-14
+
+
+def _isolated(group, sh_degree=0):
+    cam = micro_camera(W=64, H=64, f=60.0)
+    sc = micro_scene(1, 7, sh_degree)
+    sc.mean[:, 0] = [0.05, -0.03, 4.0]
+    tgt = micro_scene(1, 8, sh_degree)
+    tgt.mean[:, 0] = [0.05, -0.03, 4.0]
+    tgt.scale = sc.scale.copy()
+    tgt.quat = sc.quat.copy()
+    cfg = dict(NOTHRESH, lambda_ssim=0.0, barrier_alpha=0.0, damping_mu0=0.0)
+    target = O.render(tgt, cam, cfg)["image"]
+    return cam, sc, target, cfg
+
+
+def _grad(group, h, cam, target, cfg):
+    img = O.render(h, cam, cfg)["image"]
+    L = O.loss(img, target, cfg)
+    return O.accum(group, h, cam, cam, L["e"], L["h"], cfg)["g"], L["loss"]
+
+
+def test_opacity_one_step_exact():
+    """Pixel colour is linear in sigma (d2c/dsigma2 = 0): with the L2 loss, no
+    barrier and no damping one Newton step reaches the stationary point."""
+    cam, sc, target, cfg = _isolated(O.OPACITY)
+    sc.opacity[0] = np.float32(0.5)
+    h = O.scene_handle(sc)
+    g0, L0 = _grad(O.OPACITY, h, cam, target, cfg)
+    img = O.render(h, cam, cfg)["image"]
+    L = O.loss(img, target, cfg)
+    b = O.accum(O.OPACITY, h, cam, cam, L["e"], L["h"], cfg)
+    st = O.solve(O.OPACITY, h, cam, b["g"], b["H"], cfg)
+    h2 = O.apply(O.OPACITY, h, cam, st["step"], cfg)
+    g1, L1 = _grad(O.OPACITY, h2, cam, target, cfg)
+    assert abs(g1[0, 0]) < 1e-10 * abs(g0[0, 0]) and L1 < L0
+    assert 0 < h2.opacity[0] < 1
+
+
+def test_color_one_step_exact():
+    """Pixel colour is linear in the SH coefficients: one Newton step on the L2
+    loss reaches the stationary point per channel."""
+    cam, sc, target, cfg = _isolated(O.COLOR)
+    h = O.scene_handle(sc)
+    img = O.render(h, cam, cfg)["image"]
+    L = O.loss(img, target, cfg)
+    b = O.accum(O.COLOR, h, cam, cam, L["e"], L["h"], cfg)
+    st = O.solve(O.COLOR, h, cam, b["g"], b["H"], cfg)
+    h2 = O.apply(O.COLOR, h, cam, st["step"], cfg)
+    g1, L1 = _grad(O.COLOR, h2, cam, target, cfg)
+    assert np.abs(g1).max() < 1e-10 * np.abs(b["g"]).max()
+    assert L1 < L["loss"]
+
+
+def test_opacity_fraction_to_boundary():
+    """A step that would leave (0, 1) is cut to a fraction tau of the distance to
+    the boundary (barrier / interior-point reading)."""
+    sc = synth.tiny_scene(n=2)
+    sc.opacity[:] = [0.3, 0.9]
+    cam = synth.ring_cameras()[0]
+    g = np.array([[-10.0, 10.0]])
+    H = np.array([[1.0, 1.0]])
+    r = O.solve(O.OPACITY, sc, cam, g, H, dict(barrier_alpha=0.0, damping_mu0=0.0))
+    s = sc.opacity.astype(np.float64)
+    assert math.isclose(s[0] + r["step"][0, 0], s[0] + 0.99 * (1 - s[0]), rel_tol=1e-12)
+    assert math.isclose(s[1] + r["step"][0, 1], s[1] - 0.99 * s[1], rel_tol=1e-12)
+
+
+def test_barrier_terms():
+    """Barrier B = -a (ln s + ln(1 - s)): its derivative enters the gradient and
+    its second derivative the curvature of the scalar solve."""
+    sc = synth.tiny_scene(n=1)
+    s = float(sc.opacity[0])
+    a = 0.05
+    cam = synth.ring_cameras()[0]
+    g, Hh = np.array([[0.2]]), np.array([[3.0]])
+    r = O.solve(O.OPACITY, sc, cam, g, Hh, dict(barrier_alpha=a, damping_mu0=0.0))
+    Bp = a * (-1 / s + 1 / (1 - s))
+    Bpp = a * (1 / s ** 2 + 1 / (1 - s) ** 2)
+    # FD of the barrier itself
+    B = lambda x: -a * (math.log(x) + math.log(1 - x))
+    e = 1e-5
+    assert math.isclose(Bp, (B(s + e) - B(s - e)) / (2 * e), rel_tol=1e-8)
+    assert math.isclose(Bpp, (B(s + e) - 2 * B(s) + B(s - e)) / e ** 2, rel_tol=1e-5)
+    assert math.isclose(r["step"][0, 0], -(0.2 + Bp) / (3.0 + Bpp), rel_tol=1e-12)
+
+
+def test_sweep_reduces_loss_tiny():
+    """Behaviour (not a parity pin): a few sweeps on a small tiny-scene variant
+    reduce the total L2+SSIM loss over the training views (default damping
+    mu0 = 1 and scale trust 2; mu0 = 1e-4 diverges on this scene)."""
+    sc = synth.tiny_scene(n=300)
+    gt = synth.perturbed(sc, seed=2, sd=0.05)
+    cams = synth.ring_cameras(4, 64)
+    cfg = dict(knn_k=3)
+    targets = np.stack([O.render(gt, c, cfg)["image"] for c in cams])
+    sphere = O.bounding_sphere(sc)
+    nb, _ = O.knn(np.stack([c.center() for c in cams]), sphere, 3)
+
+    def total(h):
+        return sum(O.loss(O.render(h, c, cfg)["image"], targets[i], cfg, derivs=False)["loss"]
+                   for i, c in enumerate(cams))
+
+    h = O.scene_handle(sc)
+    L0 = total(h)
+    for t in range(4):
+        h, losses, nfail = O.sweep(h, cams, targets, nb, t, cfg)
+    L1 = total(h)
+    assert L1 < 0.5 * L0, (L0, L1)
