@@ -1,0 +1,238 @@
+/*
+ * gs2 — B300-native hot path of near-second-order (local Newton) 3D Gaussian
+ * Splatting training, arXiv 2501.13975 ("3DGS^2").  C ABI of libgs2.so.
+ *
+ * Conventions for every call
+ *  - Device pointers are CUDA device addresses owned by the caller; the
+ *    library never frees them.  Host pointers are marked "host".
+ *  - Every call that takes a cudaStream_t is asynchronous on that stream.
+ *    Argument and shape errors are reported synchronously as a gs2_status;
+ *    faults found on the device (pair-capacity overflow, non-finite input)
+ *    are recorded in a device status word read by gs2_check().
+ *  - No C++ exception crosses this ABI.  A gs2_ctx is not thread-safe: use
+ *    one context per host thread / stream.
+ *  - Layouts are planar structure-of-arrays in FP32 ("[3][n]" means three
+ *    contiguous rows of n floats).  Images are planar [3][H][W].
+ *  - Pixel (m, n) of an image has its centre at pixel coordinates (m, n).
+ *
+ * The method (section / equation of the paper):
+ *  Sec. 3 Eq. 3dgs         front-to-back alpha compositing of depth-sorted,
+ *                          projected Gaussians (gs2_project, gs2_raster_fwd)
+ *  Sec. 4.2 loss eqs.      per-pixel first and diagonal second derivatives of
+ *                          L = L2 + lambda L_SSIM (gs2_loss_derivs)
+ *  Eq. local_hessian_gradient  per-Gaussian, per-attribute-group gradient and
+ *                          Hessian blocks by the chain rule (gs2_accum_newton_blocks)
+ *  Eq. local_newton, Sec. 4.2 solves  damped local Newton steps: position in
+ *                          the plane perpendicular to the view ray, scaling in
+ *                          the projected-eigenvalue subspace, rotation about the
+ *                          view ray, opacity with a log barrier, colour per
+ *                          channel (gs2_solve_step, gs2_apply_step)
+ *  Sec. 4.1, 4.3 Eq. tildel  camera KNN on the bounding sphere; secondary
+ *                          targets (downsampled) added to the primary's blocks
+ *                          (gs2_camera_knn, gs2_sweep)
+ */
+#ifndef GS2_H
+#define GS2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gs2_stream; /* same type as cudaStream_t */
+typedef struct gs2_ctx gs2_ctx;
+
+typedef enum {
+    GS2_OK = 0,
+    GS2_ERR_ARG = 1,         /* null pointer, bad enum, bad config value */
+    GS2_ERR_SHAPE = 2,       /* size beyond what the context was created for */
+    GS2_ERR_CUDA = 3,        /* a CUDA runtime call failed (see gs2_last_error) */
+    GS2_ERR_OOM = 4,         /* scratch allocation failed in gs2_create */
+    GS2_ERR_NONFINITE = 5,   /* device status: non-finite value met */
+    GS2_ERR_TIMEOUT = 6,     /* device status: a bounded device wait gave up */
+    GS2_ERR_UNSUPPORTED = 7, /* e.g. SH degree > 3 */
+    GS2_ERR_CAPACITY = 8     /* device status: more tile/Gaussian pairs than max_pairs */
+} gs2_status;
+
+/* Attribute groups, solved in this order within a sweep (Sec. 4.2). */
+typedef enum { GS2_POS = 0, GS2_ROT = 1, GS2_SCALE = 2, GS2_OPACITY = 3, GS2_COLOR = 4 } gs2_group;
+
+/* Scene: caller-owned device buffers, FP32, planar SoA.
+ *   mean    [3][n]   world positions p
+ *   quat    [4][n]   unit quaternions (w, x, y, z)
+ *   scale   [3][n]   linear axis scales s (> 0)
+ *   opacity [n]      sigma in (0, 1)
+ *   sh      [3][S][n] SH coefficients per channel, S = (sh_degree + 1)^2 */
+typedef struct {
+    int32_t n;
+    int32_t sh_degree;
+    float *mean;
+    float *quat;
+    float *scale;
+    float *opacity;
+    float *sh;
+} gs2_scene;
+
+/* Pinhole camera looking along +z of its frame (x right, y down).
+ * viewmat: host, row-major 3x4 [R | t], world -> camera.
+ * pi = (fx tx/tz + cx, fy ty/tz + cy) in pixels for t = R p + t. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[12];
+} gs2_camera;
+
+/* Configuration.  Every constant the paper leaves unstated is a field; the
+ * defaults (gs2_config_default) are the readings documented in the design doc. */
+typedef struct {
+    float lambda_ssim;      /* weight of the SSIM loss (0.2) */
+    float alpha_min;        /* skip terms with alpha < alpha_min (1/255) */
+    float alpha_max;        /* alpha = min(sigma G, alpha_max) (0.99) */
+    float t_min;            /* stop before T falls below t_min (1e-4) */
+    float lowpass;          /* screen-space low-pass added to Sigma2D (0.3) */
+    float near_z;           /* cull centres with camera depth < near_z (0.2) */
+    float barrier_alpha;    /* opacity log-barrier weight (1e-6) */
+    float frac_to_boundary; /* opacity fraction-to-boundary tau (0.99) */
+    float damping_mu0;      /* first damping factor mu0 (1.0) */
+    int32_t damping_tries;  /* extra x10 damping attempts (6) */
+    float scale_min;        /* floor of any scale (1e-7) */
+    float scale_trust;      /* scale update bounded to [s/k, k s] (2.0) */
+    float ssim_c1, ssim_c2; /* 0.01^2, 0.03^2 */
+    float ssim_sigma;       /* Gaussian window sigma (1.5) */
+    int32_t ssim_radius;    /* window radius (5: 11x11); only 5 is supported */
+    int32_t knn_k;          /* secondary targets per primary (3) */
+    int32_t downsample;     /* secondary-target downsampling factor (2) */
+    int32_t precision;      /* 0: FP32 path; 1: mixed (FP64 solve of ill-conditioned blocks) */
+} gs2_config;
+
+void gs2_config_default(gs2_config *cfg);
+
+/* Context: owns only scratch (sorting buffers, tile ranges, per-view
+ * image-space accumulators, per-pixel loss derivatives, sweep buffers).
+ * max_pairs: capacity of the (tile, Gaussian) pair list per view (0 picks
+ * 16 * max_gaussians).  Returns GS2_ERR_OOM if scratch cannot be allocated.
+ * Creates scratch on the current CUDA device. */
+gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t max_gaussians, int32_t max_width,
+                      int32_t max_height, int32_t max_sh_degree, int64_t max_pairs);
+gs2_status gs2_destroy(gs2_ctx *ctx);
+const char *gs2_last_error(const gs2_ctx *ctx);
+gs2_status gs2_set_config(gs2_ctx *ctx, const gs2_config *cfg);
+
+/* Synchronises the stream, returns and clears the device status word
+ * (GS2_OK, GS2_ERR_CAPACITY, GS2_ERR_NONFINITE, GS2_ERR_TIMEOUT). */
+gs2_status gs2_check(gs2_ctx *ctx, gs2_stream stream);
+
+/* Sizes of caller-owned buffers, in bytes. */
+size_t gs2_proj_bytes(int64_t n);
+size_t gs2_raster_state_bytes(int32_t width, int32_t height);
+/* Blocks of one group for n Gaussians; colour keeps one factored slot per view
+ * (n_views = 1 + knn_k in a sweep). */
+size_t gs2_blocks_bytes(gs2_group group, int64_t n, int32_t sh_degree, int32_t n_views);
+size_t gs2_step_bytes(gs2_group group, int64_t n, int32_t sh_degree);
+
+/* Projection of every Gaussian into one view (Sec. 3; App. A.1-A.3):
+ * centre pi, EWA covariance Sigma2D = J Wr R S S^T R^T Wr^T J^T + lowpass I
+ * with J the perspective Jacobian, its inverse (conic), view-dependent SH
+ * colour c~ (App. A.2), depth key and screen-tile rectangle of the support
+ * { sigma G >= alpha_min }.  proj: device, gs2_proj_bytes(n) bytes, opaque. */
+gs2_status gs2_project(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cam, void *proj,
+                       gs2_stream stream);
+
+/* Tile binning, per-tile depth sort (key = FP32 camera depth, ties by index)
+ * and front-to-back compositing, Eq. 3dgs:
+ *   c = sum_k alpha_k c~_k prod_{j<k} (1 - alpha_j),  alpha = min(sigma G, alpha_max),
+ * terms with alpha < alpha_min skipped, stop before T < t_min, black background.
+ * image: device [3][H][W] out.  raster_state: device, gs2_raster_state_bytes,
+ * out (final transmittance and per-pixel list length).  The sorted tile lists
+ * stay in ctx until the next gs2_raster_fwd on this ctx. */
+gs2_status gs2_raster_fwd(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cam, const void *proj,
+                          float *image, void *raster_state, gs2_stream stream);
+
+/* Per-pixel loss derivatives (Sec. 4.2 loss equations):
+ *   e = dL/dc and h = d2L/dc_q^2 (pixel-diagonal) of L = L2 + lambda L_S,
+ *   L2 = 1/(3|I|) sum 1/2 (c - c^t)^2, L_S = 1/(3|I|) sum (1 - SSIM), SSIM per
+ *   channel with an 11x11 Gaussian window, zero-padded.
+ * image, target: device [3][H][W]; e, h: device [3][H][W] out;
+ * loss_out: device double[2] (L2, L_S) accumulated (+=), may be NULL. */
+gs2_status gs2_loss_derivs(gs2_ctx *ctx, const float *image, const float *target, int32_t width,
+                           int32_t height, float *e, float *h, double *loss_out, gs2_stream stream);
+
+/* Gradient and Hessian blocks of one group from one view (Eq.
+ * local_hessian_gradient, full Newton: g = sum e dc/dy,
+ * H = sum (dc/dy)^T diag(h) dc/dy + e . d2c/dy2), added into blocks.
+ * Must follow gs2_raster_fwd of the same view on this ctx (uses its tile
+ * lists).  primary: the primary view, which fixes the rotation axis.
+ * image: device [3][H][W], this view's gs2_raster_fwd output; target: device
+ * [3][H][W] of this view; the per-pixel derivatives are formed internally
+ * (as gs2_loss_derivs).  loss_out as gs2_loss_derivs.
+ * blocks (device, gs2_blocks_bytes), layout:
+ *   POS, SCALE: g [3][n], H [6][n] (upper triangle 00 01 02 11 12 22)
+ *   ROT, OPACITY: g [1][n], H [1][n]
+ *   COLOR: slot v (= view_slot) of n_views: [a_ch (3), s_ch (3), b (S)][n] with
+ *          a_ch = sum_p w e_ch, s_ch = sum_p w^2 h_ch, b = B Phi(r_v); the
+ *          channel block is H_ch = sum_v s_ch b b^T, g_ch = sum_v a_ch b.
+ *          The slot is overwritten, other groups accumulate (+=). */
+gs2_status gs2_accum_newton_blocks(gs2_ctx *ctx, gs2_group group, const gs2_scene *scene,
+                                   const gs2_camera *view, const gs2_camera *primary, const void *proj,
+                                   const void *raster_state, const float *image, const float *target,
+                                   int32_t view_slot, void *blocks, double *loss_out, gs2_stream stream);
+
+/* Damped local Newton step per Gaussian (Eq. local_newton), H + mu m I with
+ * m = mean |diag H| and mu = mu0 10^i until Cholesky succeeds; reduced
+ * bases from the primary view: position in span(U), U perpendicular to the
+ * view ray; scaling in the row space of d lambda / d s (projected
+ * eigenvalues); rotation angle about the view ray; opacity with barrier and
+ * fraction-to-boundary; colour per channel.
+ * step: device, gs2_step_bytes.  n_failed: device int, incremented by the
+ * number of blocks whose damping ladder failed (their step is 0). */
+gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *blocks, int32_t n_views,
+                          const gs2_scene *scene, const gs2_camera *primary, void *step, int32_t *n_failed,
+                          gs2_stream stream);
+
+/* Update in place (Sec. 4.2): p += dp; q <- dq(theta) (x) q with dq the
+ * rotation by theta about the primary view ray, renormalised;
+ * s <- max(s + ds, scale_min); sigma += dsigma; c += dc. */
+gs2_status gs2_apply_step(gs2_ctx *ctx, gs2_group group, const void *step, gs2_scene *scene,
+                          const gs2_camera *primary, gs2_stream stream);
+
+/* f x f box downsampling of a [3][H][W] image (secondary targets, Sec. 4.3)
+ * to [3][H/f][W/f]; the matching camera (host) keeps pixel centres aligned. */
+gs2_status gs2_downsample(gs2_ctx *ctx, const float *in, int32_t width, int32_t height, int32_t f, float *out,
+                          gs2_stream stream);
+void gs2_camera_downsample(const gs2_camera *in, int32_t f, gs2_camera *out);
+
+/* Data preparation (Sec. 4.1): bounding sphere of the means (centre of their
+ * bounding box, radius = largest distance to a mean): sphere_out device
+ * float[4].  Camera KNN (host): centres [ncam][3], sphere [4], out [ncam][k]
+ * by great-circle distance of the radially projected centres, ties by index. */
+gs2_status gs2_bounding_sphere(gs2_ctx *ctx, const gs2_scene *scene, float *sphere_out, gs2_stream stream);
+gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const float *sphere, int32_t k, int32_t *out);
+
+/* One sweep for primary image t (Sec. 4.2 group order, Sec. 4.3 Eq. tildel):
+ * for each group in order, render the primary (full resolution) and its k
+ * secondaries (downsampled), accumulate, solve, apply.  Uses only ctx
+ * scratch.  cams: host [ncam]; targets: host array of ncam device pointers to
+ * full-resolution [3][H][W] images; knn: host [ncam][knn_k].
+ * losses_out: device double[5][2], (L2, L_S) of the primary view seen by each
+ * group (+=), may be NULL.  n_failed: device int (+=), may be NULL. */
+gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                     const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
+                     int32_t *n_failed, gs2_stream stream);
+
+/* Introspection for tests: copies the current tile ranges (device uint32
+ * [ntiles][2]) and sorted Gaussian ids (device uint32, up to capacity) and
+ * returns the pair count (host) after synchronising the stream. */
+gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32_t *ids_out, int64_t capacity,
+                           int64_t *n_pairs_out, gs2_stream stream);
+/* Depth keys (FP32 bit patterns) written by the last gs2_project into proj. */
+gs2_status gs2_debug_keys(const void *proj, int64_t n, uint32_t *keys_out, gs2_stream stream);
+/* Unpacks proj into planar FP32 [12][n]: pix_x pix_y conic_xx conic_xy conic_yy
+ * sigma col0 col1 col2 depth tiles_touched(as float) 0. */
+gs2_status gs2_debug_proj(const void *proj, int64_t n, float *out, gs2_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1023,7 +1023,9 @@ static void quat_R_plain(const double q0[4], double R[3][3]) {
  * Q = Tt^T (Tt Tt^T)^{-1} (3x2), g_l = Q^T g_s, H_l = Q^T H_s Q,
  * dl = -H_l^{-1} g_l, ds = Q dl (the Newton step restricted to row(Tt)).
  * Returns 0 ok, 3 if not in front of the primary camera or Tt is rank
- * deficient.  gap_out = relative eigenvalue gap (ambiguity indicator). */
+ * deficient.  gap_out = min(relative eigenvalue gap, det(Tt Tt^T) /
+ * (|t1|^2 |t2|^2)): how close the reduction is to degenerate (a diagnostic
+ * for tolerances; it does not change the step). */
 static int scale_basis(const orc_camera *cam, const orc_config *cfg, const double p[3], const double q[4],
                        const double s[3], double Q[3][2], double *gap_out) {
     const double *V = cam->viewmat;
@@ -1073,7 +1075,9 @@ static int scale_basis(const orc_camera *cam, const orc_config *cfg, const doubl
         G11 += Tt[1][j] * Tt[1][j];
     }
     double det = G00 * G11 - G01 * G01;
-    if (!(det > 1e-300) || !(det > 1e-14 * G00 * G11)) return 3;
+    if (gap_out && G00 * G11 > 0 && det / (G00 * G11) < *gap_out) *gap_out = det / (G00 * G11);
+    /* rank test: rows of Tt closer than ~0.06 degrees count as parallel */
+    if (!(det > 1e-300) || !(det > 1e-6 * G00 * G11)) return 3;
     double I00 = G11 / det, I01 = -G01 / det, I11 = G00 / det;
     for (int j = 0; j < 3; ++j) {
         Q[j][0] = Tt[0][j] * I00 + Tt[1][j] * I01;

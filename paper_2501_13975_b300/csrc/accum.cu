@@ -1,0 +1,582 @@
+// gs2_accum_newton_blocks (Eq. local_hessian_gradient, full Newton).
+//
+// Pass 1 (k_accum, one 16x16 CTA per tile, one thread per pixel): walk the
+// tile's depth-sorted list back to front (the order that yields the colour
+// behind each Gaussian, C_back, and its transmittance T_k = T_after/(1-alpha)).
+// For pixel c = C_front + T_k (alpha_k c~_k + (1 - alpha_k) C_back):
+//   dc/dalpha = T_k (c~ - C_back) =: a,  dc/dc~ = alpha T_k =: w,
+//   d2c/dalpha2 = 0, d2c/dalpha dc~ = T_k,
+// and alpha = sigma G(z), z = (pi_x, pi_y, Sxx, Sxy, Syy).  Each pixel forms
+// the group's image-space payload (position 41 floats: g_z, H_zz, cross
+// terms, colour sums; scale/rotation 9; opacity 2; colour 6), the warp sums
+// it with shuffles and lane 0 adds it with atomics into a per-view,
+// per-Gaussian buffer zbuf[P][n] (L2-resident at the working-set sizes).
+//
+// Pass 2 (k_epi_*, one thread per Gaussian): chain rule from z to the group's
+// parameters with the per-view constant Jacobians (dz/dp, d2z/dp2, dc~/dp,
+// d2c~/dp2, dSigma/ds, dSigma/dtheta), added into the group's blocks; the
+// zbuf entries are cleared for the next view.
+#include "common.cuh"
+#include "sh.cuh"
+
+template <int G> struct Payload;
+template <> struct Payload<GS2_POS> { static constexpr int P = 41; };
+template <> struct Payload<GS2_ROT> { static constexpr int P = 9; };
+template <> struct Payload<GS2_SCALE> { static constexpr int P = 9; };
+template <> struct Payload<GS2_OPACITY> { static constexpr int P = 2; };
+template <> struct Payload<GS2_COLOR> { static constexpr int P = 6; };
+
+// packed upper-triangle index of a 5x5 / 3x3 symmetric matrix
+__host__ __device__ constexpr int ut5(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i); }
+__host__ __device__ constexpr int ut3(int i, int j) { return i * 3 - i * (i - 1) / 2 + (j - i); }
+
+// Derivatives of G = exp(-1/2 d^T A d), d = x - pi, A = Sigma^{-1}, w.r.t.
+// pi (2) and the covariance parameters (Sxx, Sxy, Syy) (Sxy counted once, the
+// matrix entries (0,1) and (1,0) both move):
+//   u = A d; dG/dpi = G u; d2G/dpi2 = G (u u^T - A);
+//   q_t = -u^T E_t u, dG/dS_t = -G q_t / 2;
+//   d2G/dS_t dS_f = G (q_t q_f / 4 - v_t^T A v_f), v_t = E_t u;
+//   d2G/dpi dS_t = G (-u q_t / 2 - A v_t).
+template <bool WITH_PI>
+__device__ __forceinline__ void falloff_derivs(float G, float ca, float cb, float cc, float dx, float dy, float gz[5],
+                                               float gzz[15]) {
+    const float ux = ca * dx + cb * dy, uy = cb * dx + cc * dy;
+    const float q[3] = {-ux * ux, -2.f * ux * uy, -uy * uy};
+    const float v[3][2] = {{ux, 0.f}, {uy, ux}, {0.f, uy}};
+    float Av[3][2];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        Av[t][0] = ca * v[t][0] + cb * v[t][1];
+        Av[t][1] = cb * v[t][0] + cc * v[t][1];
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) gz[2 + t] = -0.5f * G * q[t];
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int f = t; f < 3; ++f)
+            gzz[ut5(2 + t, 2 + f)] = G * (0.25f * q[t] * q[f] - (v[t][0] * Av[f][0] + v[t][1] * Av[f][1]));
+    if (WITH_PI) {
+        gz[0] = G * ux;
+        gz[1] = G * uy;
+        gzz[ut5(0, 0)] = G * (ux * ux - ca);
+        gzz[ut5(0, 1)] = G * (ux * uy - cb);
+        gzz[ut5(1, 1)] = G * (uy * uy - cc);
+        const float u[2] = {ux, uy};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) gzz[ut5(a, 2 + t)] = G * (-0.5f * u[a] * q[t] - Av[t][a]);
+    }
+}
+
+template <int GROUP>
+__global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict__ ranges,
+                                                        const uint32_t *__restrict__ ids, ProjView pv, RasterView rv,
+                                                        const float *__restrict__ E, const float *__restrict__ Hh,
+                                                        int W, int H, int tiles_x, float amin, float amax,
+                                                        float *__restrict__ zbuf, int n) {
+    constexpr int P = Payload<GROUP>::P;
+    __shared__ uint32_t sId[GS2_TILE_PIX];
+    __shared__ float4 sA[GS2_TILE_PIX], sB[GS2_TILE_PIX], sC[GS2_TILE_PIX];
+    __shared__ uint32_t sMax;
+    const int t = threadIdx.x, lane = t & 31;
+    const int tile = blockIdx.y * tiles_x + blockIdx.x;
+    const int px = blockIdx.x * GS2_TILE + (t % GS2_TILE), py = blockIdx.y * GS2_TILE + (t / GS2_TILE);
+    const bool inside = px < W && py < H;
+    const size_t PI = (size_t)W * H, pp = (size_t)py * W + px;
+    uint32_t last = 0u;
+    float T = 1.f, e[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
+    if (inside) {
+        last = rv.last[pp];
+        T = rv.tfinal[pp];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e[c] = E[c * PI + pp];
+            h[c] = Hh[c * PI + pp];
+        }
+    }
+    if (t == 0) sMax = 0u;
+    __syncthreads();
+    atomicMax(&sMax, last);
+    __syncthreads();
+    const int maxlast = (int)sMax;
+    const uint2 r = ranges[tile];
+    const float fx = (float)px, fy = (float)py;
+    float cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+    for (int bend = maxlast; bend > 0; bend -= GS2_TILE_PIX) {
+        const int bbeg = max(0, bend - GS2_TILE_PIX);
+        __syncthreads();
+        const int j = bbeg + t;
+        if (j < bend) {
+            const uint32_t k = ids[r.x + j];
+            sId[t] = k;
+            sA[t] = pv.recA[k];
+            sB[t] = pv.recB[k];
+            sC[t] = pv.col[k];
+        }
+        __syncthreads();
+        for (int jj = bend - 1; jj >= bbeg; --jj) {
+            const int s = jj - bbeg;
+            const float4 A = sA[s], B = sB[s];
+            bool act = inside && (uint32_t)jj < last;
+            float G = 0.f, alpha = 0.f, dx = 0.f, dy = 0.f;
+            bool clamped = false;
+            if (act) {
+                dx = __fsub_rn(fx, A.x);
+                dy = __fsub_rn(fy, A.y);
+                G = gs2_gauss(A.z, A.w, B.x, dx, dy);
+                const float araw = __fmul_rn(B.y, G);
+                clamped = araw > amax;
+                alpha = fminf(araw, amax);
+                if (alpha < amin) act = false;
+            }
+            if (!__any_sync(0xFFFFFFFFu, act)) continue;
+            float pl[P];
+#pragma unroll
+            for (int i = 0; i < P; ++i) pl[i] = 0.f;
+            if (act) {
+                const float4 C = sC[s];
+                const float Tk = __fdiv_rn(T, __fsub_rn(1.f, alpha));
+                const float w = alpha * Tk;
+                const float a0 = Tk * (C.x - cb0), a1 = Tk * (C.y - cb1), a2 = Tk * (C.z - cb2);
+                const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
+                const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
+                if (GROUP == GS2_OPACITY) {
+                    if (!clamped) {
+                        pl[0] = Ea * G;
+                        pl[1] = Ah * G * G;
+                    }
+                } else if (GROUP == GS2_COLOR) {
+                    pl[0] = w * e[0];
+                    pl[1] = w * e[1];
+                    pl[2] = w * e[2];
+                    pl[3] = w * w * h[0];
+                    pl[4] = w * w * h[1];
+                    pl[5] = w * w * h[2];
+                } else if (GROUP == GS2_ROT || GROUP == GS2_SCALE) {
+                    if (!clamped) {
+                        float gz[5], gzz[15];
+                        falloff_derivs<false>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
+                        const float sg = B.y;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) pl[i] = Ea * sg * gz[2 + i];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int jx = i; jx < 3; ++jx)
+                                pl[3 + ut3(i, jx)] =
+                                    Ah * sg * sg * gz[2 + i] * gz[2 + jx] + Ea * sg * gzz[ut5(2 + i, 2 + jx)];
+                    }
+                } else {  // position
+                    const float ee[3] = {e[0], e[1], e[2]}, hh[3] = {h[0], h[1], h[2]};
+                    const float aa[3] = {a0, a1, a2};
+                    if (!clamped) {
+                        float gz[5], gzz[15];
+                        falloff_derivs<true>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
+                        const float sg = B.y;
+                        float az[5];
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) az[i] = sg * gz[i];
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) pl[i] = Ea * az[i];
+#pragma unroll
+                        for (int i = 0; i < 5; ++i)
+#pragma unroll
+                            for (int jx = i; jx < 5; ++jx)
+                                pl[5 + ut5(i, jx)] = Ah * az[i] * az[jx] + Ea * sg * gzz[ut5(i, jx)];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float xc = hh[c] * aa[c] * w + ee[c] * Tk;
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) pl[20 + c * 5 + i] = xc * az[i];
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        pl[35 + c] = w * ee[c];
+                        pl[38 + c] = w * w * hh[c];
+                    }
+                }
+                cb0 = alpha * C.x + (1.f - alpha) * cb0;
+                cb1 = alpha * C.y + (1.f - alpha) * cb1;
+                cb2 = alpha * C.z + (1.f - alpha) * cb2;
+                T = Tk;
+            }
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                float v = pl[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                pl[i] = v;
+            }
+            if (lane == 0) {
+                const uint32_t k = sId[s];
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    if (pl[i] != 0.f) atomicAdd(&zbuf[(size_t)i * n + k], pl[i]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ epilogues
+struct GaussGeo {
+    float p[3], s[3], R[3][3];
+};
+
+__device__ __forceinline__ void load_geo(const DevScene &sc, int k, GaussGeo &g) {
+    const int n = sc.n;
+    for (int i = 0; i < 3; ++i) {
+        g.p[i] = sc.mean[i * n + k];
+        g.s[i] = sc.scale[i * n + k];
+    }
+    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
+    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+    g.R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); g.R[0][1] = 2.f * (qx * qy - qw * qz); g.R[0][2] = 2.f * (qx * qz + qw * qy);
+    g.R[1][0] = 2.f * (qx * qy + qw * qz); g.R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); g.R[1][2] = 2.f * (qy * qz - qw * qx);
+    g.R[2][0] = 2.f * (qx * qz - qw * qy); g.R[2][1] = 2.f * (qy * qz + qw * qx); g.R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+}
+
+// camera-space centre and the 2x3 T = J Wr
+__device__ __forceinline__ void cam_T(const DevCam &cam, const float p[3], float t[3], float T[2][3]) {
+    const float *V = cam.V;
+    for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * p[0] + V[i * 4 + 1] * p[1] + V[i * 4 + 2] * p[2] + V[i * 4 + 3];
+    const float iz = 1.f / t[2];
+    const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz * iz, j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz * iz;
+    for (int j = 0; j < 3; ++j) {
+        T[0][j] = j00 * V[j] + j02 * V[8 + j];
+        T[1][j] = j11 * V[4 + j] + j12 * V[8 + j];
+    }
+}
+
+// S2 = T S3 T^T as the parameter vector (xx, xy, yy)
+__device__ __forceinline__ void push_cov(const float T[2][3], const float S3[3][3], float out[3]) {
+    float TS[2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 3; ++j) TS[a][j] = T[a][0] * S3[0][j] + T[a][1] * S3[1][j] + T[a][2] * S3[2][j];
+    out[0] = TS[0][0] * T[0][0] + TS[0][1] * T[0][1] + TS[0][2] * T[0][2];
+    out[1] = TS[0][0] * T[1][0] + TS[0][1] * T[1][1] + TS[0][2] * T[1][2];
+    out[2] = TS[1][0] * T[1][0] + TS[1][1] * T[1][1] + TS[1][2] * T[1][2];
+}
+
+__global__ void k_epi_opacity(const ProjView pv, float *zbuf, int n, float *blocks) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || pv.touched[k] == 0u) return;
+    blocks[k] += zbuf[k];
+    blocks[n + k] += zbuf[n + k];
+    zbuf[k] = 0.f;
+    zbuf[n + k] = 0.f;
+}
+
+__global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, float *zbuf, float *slot) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    const bool vis = pv.touched[k] != 0u;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        slot[(size_t)i * n + k] = vis ? zbuf[(size_t)i * n + k] : 0.f;
+        if (vis) zbuf[(size_t)i * n + k] = 0.f;
+    }
+    float rx = sc.mean[k] - cam.o[0], ry = sc.mean[n + k] - cam.o[1], rz = sc.mean[2 * n + k] - cam.o[2];
+    const float rn = rsqrtf(rx * rx + ry * ry + rz * rz);
+    float phi[GS2_MAX_SH];
+    sh_phi(sc.S, rx * rn, ry * rn, rz * rn, phi);
+    for (int i = 0; i < sc.S; ++i) slot[(size_t)(6 + i) * n + k] = sh_norm(i) * phi[i];
+}
+
+__global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, float *zbuf, float *blocks) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n || pv.touched[k] == 0u) return;
+    float z[9];
+    for (int i = 0; i < 9; ++i) {
+        z[i] = zbuf[(size_t)i * n + k];
+        zbuf[(size_t)i * n + k] = 0.f;
+    }
+    GaussGeo g;
+    load_geo(sc, k, g);
+    float t[3], T[2][3];
+    cam_T(cam, g.p, t, T);
+    float dS[3][3], d2S[3][3];  // [param j][(xx,xy,yy)]
+    for (int j = 0; j < 3; ++j) {
+        const float m0 = T[0][0] * g.R[0][j] + T[0][1] * g.R[1][j] + T[0][2] * g.R[2][j];
+        const float m1 = T[1][0] * g.R[0][j] + T[1][1] * g.R[1][j] + T[1][2] * g.R[2][j];
+        d2S[j][0] = 2.f * m0 * m0; d2S[j][1] = 2.f * m0 * m1; d2S[j][2] = 2.f * m1 * m1;
+        for (int a = 0; a < 3; ++a) dS[j][a] = g.s[j] * d2S[j][a];
+    }
+    float Hz[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) Hz[a][b] = Hz[b][a] = z[3 + ut3(a, b)];
+    for (int j = 0; j < 3; ++j) {
+        float gj = 0.f;
+        for (int a = 0; a < 3; ++a) gj += z[a] * dS[j][a];
+        blocks[(size_t)j * n + k] += gj;
+    }
+    for (int j = 0; j < 3; ++j)
+        for (int l = j; l < 3; ++l) {
+            float hv = 0.f;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) hv += dS[j][a] * Hz[a][b] * dS[l][b];
+            if (j == l)
+                for (int a = 0; a < 3; ++a) hv += z[a] * d2S[j][a];
+            blocks[(size_t)(3 + ut3(j, l)) * n + k] += hv;
+        }
+}
+
+__global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjView pv, float *zbuf, float *blocks) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n || pv.touched[k] == 0u) return;
+    float z[9];
+    for (int i = 0; i < 9; ++i) {
+        z[i] = zbuf[(size_t)i * n + k];
+        zbuf[(size_t)i * n + k] = 0.f;
+    }
+    GaussGeo g;
+    load_geo(sc, k, g);
+    float t[3], T[2][3];
+    cam_T(cam, g.p, t, T);
+    // Sigma3 = R diag(s^2) R^T; K = [a]x with a the primary view direction
+    float S3[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.f;
+            for (int l = 0; l < 3; ++l) acc += g.R[i][l] * g.s[l] * g.s[l] * g.R[j][l];
+            S3[i][j] = acc;
+        }
+    float a[3] = {g.p[0] - primary.o[0], g.p[1] - primary.o[1], g.p[2] - primary.o[2]};
+    const float an = rsqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    for (int i = 0; i < 3; ++i) a[i] *= an;
+    const float K[3][3] = {{0.f, -a[2], a[1]}, {a[2], 0.f, -a[0]}, {-a[1], a[0], 0.f}};
+    float KS[3][3], SK[3][3], KSK[3][3], K2S[3][3], SK2[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float ks = 0.f, sk = 0.f;
+            for (int l = 0; l < 3; ++l) {
+                ks += K[i][l] * S3[l][j];
+                sk += S3[i][l] * K[l][j];
+            }
+            KS[i][j] = ks;
+            SK[i][j] = sk;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float ksk = 0.f, k2s = 0.f, sk2 = 0.f;
+            for (int l = 0; l < 3; ++l) {
+                ksk += KS[i][l] * K[l][j];
+                k2s += K[i][l] * KS[l][j];
+                sk2 += SK[i][l] * K[l][j];
+            }
+            KSK[i][j] = ksk;
+            K2S[i][j] = k2s;
+            SK2[i][j] = sk2;
+        }
+    float D1[3][3], D2[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            D1[i][j] = KS[i][j] - SK[i][j];
+            D2[i][j] = K2S[i][j] - 2.f * KSK[i][j] + SK2[i][j];
+        }
+    float d1[3], d2[3];
+    push_cov(T, D1, d1);
+    push_cov(T, D2, d2);
+    float gth = 0.f, hth = 0.f;
+    for (int aa = 0; aa < 3; ++aa) {
+        gth += z[aa] * d1[aa];
+        hth += z[aa] * d2[aa];
+        for (int b = 0; b < 3; ++b) {
+            const float hz = z[3 + (aa <= b ? ut3(aa, b) : ut3(b, aa))];
+            hth += d1[aa] * hz * d1[b];
+        }
+    }
+    blocks[k] += gth;
+    blocks[n + k] += hth;
+}
+
+__global__ void k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, float *zbuf, float *blocks) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n || pv.touched[k] == 0u) return;
+    float z[GS2_ZPOS];
+    for (int i = 0; i < GS2_ZPOS; ++i) {
+        z[i] = zbuf[(size_t)i * n + k];
+        zbuf[(size_t)i * n + k] = 0.f;
+    }
+    GaussGeo g;
+    load_geo(sc, k, g);
+    const float *V = cam.V;
+    float t[3];
+    for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * g.p[0] + V[i * 4 + 1] * g.p[1] + V[i * 4 + 2] * g.p[2] + V[i * 4 + 3];
+    const float iz = 1.f / t[2], iz2 = iz * iz, iz3 = iz2 * iz, iz4 = iz2 * iz2;
+    const float fx = cam.fx, fy = cam.fy;
+    // camera-space covariance Vc = (Wr R diag(s)) (Wr R diag(s))^T
+    float M3[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            M3[i][j] = (V[i * 4] * g.R[0][j] + V[i * 4 + 1] * g.R[1][j] + V[i * 4 + 2] * g.R[2][j]) * g.s[j];
+    float Vc[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Vc[i][j] = M3[i][0] * M3[j][0] + M3[i][1] * M3[j][1] + M3[i][2] * M3[j][2];
+    // J rows and their derivatives w.r.t. t
+    float J[2][3] = {{fx * iz, 0.f, -fx * t[0] * iz2}, {0.f, fy * iz, -fy * t[1] * iz2}};
+    float dJ[2][3][3];   // [row][k][col]
+    float d2J[2][3][3][3];
+    for (int a = 0; a < 2; ++a)
+        for (int kk = 0; kk < 3; ++kk)
+            for (int c = 0; c < 3; ++c) {
+                dJ[a][kk][c] = 0.f;
+                for (int l = 0; l < 3; ++l) d2J[a][kk][l][c] = 0.f;
+            }
+    dJ[0][0][2] = -fx * iz2;
+    dJ[0][2][0] = -fx * iz2;
+    dJ[0][2][2] = 2.f * fx * t[0] * iz3;
+    dJ[1][1][2] = -fy * iz2;
+    dJ[1][2][1] = -fy * iz2;
+    dJ[1][2][2] = 2.f * fy * t[1] * iz3;
+    d2J[0][0][2][2] = d2J[0][2][0][2] = 2.f * fx * iz3;
+    d2J[0][2][2][0] = 2.f * fx * iz3;
+    d2J[0][2][2][2] = -6.f * fx * t[0] * iz4;
+    d2J[1][1][2][2] = d2J[1][2][1][2] = 2.f * fy * iz3;
+    d2J[1][2][2][1] = 2.f * fy * iz3;
+    d2J[1][2][2][2] = -6.f * fy * t[1] * iz4;
+    // z derivatives w.r.t. t: dz[5][3], d2z[5][3][3]
+    float dz[5][3], d2z[5][3][3];
+    for (int i = 0; i < 5; ++i)
+        for (int a = 0; a < 3; ++a) {
+            dz[i][a] = 0.f;
+            for (int b = 0; b < 3; ++b) d2z[i][a][b] = 0.f;
+        }
+    dz[0][0] = fx * iz; dz[0][2] = -fx * t[0] * iz2;
+    dz[1][1] = fy * iz; dz[1][2] = -fy * t[1] * iz2;
+    d2z[0][0][2] = d2z[0][2][0] = -fx * iz2; d2z[0][2][2] = 2.f * fx * t[0] * iz3;
+    d2z[1][1][2] = d2z[1][2][1] = -fy * iz2; d2z[1][2][2] = 2.f * fy * t[1] * iz3;
+    const int ea[3] = {0, 0, 1}, eb[3] = {0, 1, 1};
+    // helper: x^T Vc y
+    auto vq = [&](const float *x, const float *y) {
+        float acc = 0.f;
+        for (int i = 0; i < 3; ++i) acc += x[i] * (Vc[i][0] * y[0] + Vc[i][1] * y[1] + Vc[i][2] * y[2]);
+        return acc;
+    };
+    for (int e = 0; e < 3; ++e) {
+        const int a = ea[e], b = eb[e];
+        for (int kk = 0; kk < 3; ++kk) {
+            dz[2 + e][kk] = vq(dJ[a][kk], J[b]) + vq(J[a], dJ[b][kk]);
+            for (int l = 0; l < 3; ++l)
+                d2z[2 + e][kk][l] = vq(d2J[a][kk][l], J[b]) + vq(dJ[a][kk], dJ[b][l]) + vq(dJ[a][l], dJ[b][kk]) +
+                                    vq(J[a], d2J[b][kk][l]);
+        }
+    }
+    // to world: Jzp = dz Wr; d2z_p = Wr^T d2z Wr
+    float Jzp[5][3];
+    for (int i = 0; i < 5; ++i)
+        for (int c = 0; c < 3; ++c) Jzp[i][c] = dz[i][0] * V[c] + dz[i][1] * V[4 + c] + dz[i][2] * V[8 + c];
+    float Hp[3][3], gp[3];
+    // g = Jzp^T gz ; H = Jzp^T Hzz Jzp + sum_i gz_i d2z_i
+    float Hzz[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = i; j < 5; ++j) Hzz[i][j] = Hzz[j][i] = z[5 + ut5(i, j)];
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.f;
+        for (int i = 0; i < 5; ++i) acc += Jzp[i][c] * z[i];
+        gp[c] = acc;
+    }
+    float Gt[3][3];  // sum_i gz_i d2z_i (camera frame)
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            float acc = 0.f;
+            for (int i = 0; i < 5; ++i) acc += z[i] * d2z[i][a][b];
+            Gt[a][b] = acc;
+        }
+    for (int c = 0; c < 3; ++c)
+        for (int d = c; d < 3; ++d) {
+            float acc = 0.f;
+            for (int i = 0; i < 5; ++i) {
+                float row = 0.f;
+                for (int j = 0; j < 5; ++j) row += Hzz[i][j] * Jzp[j][d];
+                acc += Jzp[i][c] * row;
+            }
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) acc += V[a * 4 + c] * Gt[a][b] * V[b * 4 + d];
+            Hp[c][d] = acc;
+        }
+    // colour path: c~(p) through r(p)
+    float r[3] = {g.p[0] - cam.o[0], g.p[1] - cam.o[1], g.p[2] - cam.o[2]};
+    const float rho = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), irho = 1.f / rho;
+    for (int i = 0; i < 3; ++i) r[i] *= irho;
+    float Pm[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Pm[a][b] = ((a == b ? 1.f : 0.f) - r[a] * r[b]) * irho;
+    const int S = sc.S;
+    for (int ch = 0; ch < 3; ++ch) {
+        const float WE = z[35 + ch], SS = z[38 + ch];
+        float wco[GS2_MAX_SH];
+        for (int i = 0; i < S; ++i) wco[i] = sh_norm(i) * sc.sh[(size_t)(ch * S + i) * n + k];
+        float f, gr[3], hs[6];
+        sh_poly_derivs(S, wco, r[0], r[1], r[2], f, gr, hs);
+        const float Hr[3][3] = {{hs[0], hs[1], hs[2]}, {hs[1], hs[3], hs[4]}, {hs[2], hs[4], hs[5]}};
+        float gc[3];
+        for (int a = 0; a < 3; ++a) gc[a] = Pm[a][0] * gr[0] + Pm[a][1] * gr[1] + Pm[a][2] * gr[2];
+        // second derivative of c~ w.r.t. p
+        float HPm[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) HPm[a][b] = Hr[a][0] * Pm[0][b] + Hr[a][1] * Pm[1][b] + Hr[a][2] * Pm[2][b];
+        float y[3];  // Jzp^T X_ch
+        for (int c = 0; c < 3; ++c) {
+            float acc = 0.f;
+            for (int i = 0; i < 5; ++i) acc += Jzp[i][c] * z[20 + ch * 5 + i];
+            y[c] = acc;
+        }
+        for (int a = 0; a < 3; ++a) {
+            gp[a] += WE * gc[a];
+            for (int b = a; b < 3; ++b) {
+                float h2 = Pm[a][0] * HPm[0][b] + Pm[a][1] * HPm[1][b] + Pm[a][2] * HPm[2][b];
+                for (int m = 0; m < 3; ++m) {
+                    const float d2r = (3.f * r[m] * r[a] * r[b] - (m == a ? r[b] : 0.f) - (m == b ? r[a] : 0.f) -
+                                       (a == b ? r[m] : 0.f)) * irho * irho;
+                    h2 += gr[m] * d2r;
+                }
+                Hp[a][b] += y[a] * gc[b] + gc[a] * y[b] + SS * gc[a] * gc[b] + WE * h2;
+            }
+        }
+    }
+    for (int c = 0; c < 3; ++c) blocks[(size_t)c * n + k] += gp[c];
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) blocks[(size_t)(3 + ut3(a, b)) * n + k] += Hp[a][b];
+}
+
+cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
+                         ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
+                         cudaStream_t st) {
+    const int n = sc.n;
+    dim3 grid(ctx->tiles_x, ctx->tiles_y);
+    const uint32_t *ids = ctx->vals[ctx->sorted];
+#define ACC(G)                                                                                                    \
+    k_accum<G><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h,   \
+                                              ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, ctx->zbuf, n)
+    switch (group) {
+    case GS2_POS: ACC(GS2_POS); break;
+    case GS2_ROT: ACC(GS2_ROT); break;
+    case GS2_SCALE: ACC(GS2_SCALE); break;
+    case GS2_OPACITY: ACC(GS2_OPACITY); break;
+    default: ACC(GS2_COLOR); break;
+    }
+#undef ACC
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n == 0) return e;
+    const int eg = (n + 255) / 256;
+    float *b = (float *)blocks;
+    switch (group) {
+    case GS2_POS: k_epi_pos<<<eg, 128 * 2, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
+    case GS2_ROT: k_epi_rot<<<eg, 256, 0, st>>>(sc, view, primary, pv, ctx->zbuf, b); break;
+    case GS2_SCALE: k_epi_scale<<<eg, 256, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
+    case GS2_OPACITY: k_epi_opacity<<<eg, 256, 0, st>>>(pv, ctx->zbuf, n, b); break;
+    default: {
+        float *slot = b + (size_t)view_slot * (6 + sc.S) * n;
+        k_epi_color<<<eg, 256, 0, st>>>(sc, view, pv, ctx->zbuf, slot);
+    }
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,177 @@
+// Internal declarations shared by the gs2 CUDA translation units.
+// Not part of the public ABI (include/gs2.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "../../include/gs2.h"
+
+#define GS2_TILE 16                  // screen tile edge in pixels
+#define GS2_TILE_PIX (GS2_TILE * GS2_TILE)
+#define GS2_ZPOS 41                  // image-space payload of the position group
+#define GS2_MAX_SH 16
+
+// device status bits
+#define GS2_ST_CAPACITY 1u
+#define GS2_ST_NONFINITE 2u
+#define GS2_ST_TIMEOUT 4u
+
+static inline int sh_count(int deg) { return (deg + 1) * (deg + 1); }
+static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// --------------------------------------------------------------------------
+// Layout of the caller-owned projection buffer (opaque to callers).
+struct ProjView {
+    float4 *recA;      // (pi_x, pi_y, conic_xx, conic_xy)
+    float4 *recB;      // (conic_yy, sigma, depth, 0)
+    float4 *col;       // (c~_r, c~_g, c~_b, 0)
+    uint2 *rect;       // tile rectangle: x = tx0 | ty0 << 16, y = tx1 | ty1 << 16 (exclusive ends)
+    uint32_t *touched; // number of tiles in rect (0 = not rendered)
+    uint32_t *key;     // FP32 bit pattern of the camera depth (positive)
+    uint32_t *offs;    // exclusive prefix sum of touched
+};
+
+static inline size_t proj_bytes_impl(int64_t n) {
+    size_t b = 0;
+    b += align256(16 * (size_t)n) * 3;
+    b += align256(8 * (size_t)n);
+    b += align256(4 * (size_t)n) * 3;
+    return b;
+}
+
+static inline ProjView proj_view(void *base, int64_t n) {
+    char *p = (char *)base;
+    ProjView v;
+    v.recA = (float4 *)p; p += align256(16 * (size_t)n);
+    v.recB = (float4 *)p; p += align256(16 * (size_t)n);
+    v.col = (float4 *)p; p += align256(16 * (size_t)n);
+    v.rect = (uint2 *)p; p += align256(8 * (size_t)n);
+    v.touched = (uint32_t *)p; p += align256(4 * (size_t)n);
+    v.key = (uint32_t *)p; p += align256(4 * (size_t)n);
+    v.offs = (uint32_t *)p;
+    return v;
+}
+
+struct RasterView {
+    float *tfinal;   // [H*W] final transmittance
+    uint32_t *last;  // [H*W] number of tile-list entries consumed (last contributor + 1)
+};
+
+static inline size_t raster_state_bytes_impl(int w, int h) {
+    return align256(4 * (size_t)w * h) * 2;
+}
+
+static inline RasterView raster_view(void *base, int w, int h) {
+    RasterView r;
+    r.tfinal = (float *)base;
+    r.last = (uint32_t *)((char *)base + align256(4 * (size_t)w * h));
+    return r;
+}
+
+// camera as passed to kernels (by value)
+struct DevCam {
+    int w, h;
+    float fx, fy, cx, cy;
+    float V[12];     // row-major [R | t]
+    float o[3];      // camera centre
+};
+
+static inline DevCam make_devcam(const gs2_camera *c) {
+    DevCam d;
+    d.w = c->width;
+    d.h = c->height;
+    d.fx = c->fx; d.fy = c->fy; d.cx = c->cx; d.cy = c->cy;
+    for (int i = 0; i < 12; ++i) d.V[i] = c->viewmat[i];
+    for (int i = 0; i < 3; ++i) {
+        double s = 0;
+        for (int j = 0; j < 3; ++j) s -= (double)c->viewmat[j * 4 + i] * (double)c->viewmat[j * 4 + 3];
+        d.o[i] = (float)s;
+    }
+    return d;
+}
+
+struct DevScene {
+    int n, S;
+    const float *mean, *quat, *scale, *opacity, *sh;
+};
+
+static inline DevScene make_devscene(const gs2_scene *s) {
+    DevScene d;
+    d.n = s->n;
+    d.S = sh_count(s->sh_degree);
+    d.mean = s->mean; d.quat = s->quat; d.scale = s->scale; d.opacity = s->opacity; d.sh = s->sh;
+    return d;
+}
+
+// --------------------------------------------------------------------------
+struct gs2_ctx {
+    gs2_config cfg;
+    int64_t max_n;
+    int max_w, max_h, max_sh;
+    int64_t max_pairs;
+    int nb_sort;                 // blocks of the radix sort grid
+    // sorting
+    unsigned long long *keys[2];
+    uint32_t *vals[2];
+    uint32_t *ghist;             // [256][nb_sort]
+    uint32_t *bsum;              // scan block sums
+    uint32_t *d_count;           // [0] = clamped pair count, [1] = raw count
+    uint2 *ranges;               // [max tiles]
+    int sorted;                  // which of keys/vals holds the sorted pairs
+    int tiles_x, tiles_y;        // of the last gs2_raster_fwd
+    // accumulation
+    float *zbuf;                 // [GS2_ZPOS][max_n], zero between uses
+    float *pix_e, *pix_h;        // [3][max_w*max_h]
+    // sweep scratch
+    void *sw_proj;
+    void *sw_rstate;
+    float *sw_image;
+    float *sw_tgt;               // downsampled secondary targets
+    void *sw_blocks;
+    void *sw_step;
+    size_t sw_blocks_bytes, sw_step_bytes;
+    uint32_t *d_status;
+    std::string err;
+};
+
+// --------------------------------------------------------------------------
+// launchers implemented in the .cu files (return a CUDA error code)
+cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
+                           int tiles_y, cudaStream_t st);
+cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st);
+cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
+                          RasterView rv, cudaStream_t st);
+cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,
+                        float *hh, double *loss_out, cudaStream_t st);
+cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
+                         ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
+                         cudaStream_t st);
+cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
+                         const gs2_config &cfg, void *step, int32_t *n_failed, cudaStream_t st);
+cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
+                         const gs2_config &cfg, cudaStream_t st);
+cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);
+cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t st);
+
+// --------------------------------------------------------------------------
+// Device helpers shared by the rasteriser and the accumulation: both must take
+// the same alpha decisions bit for bit, so the Gaussian falloff is evaluated
+// with explicitly rounded operations (no compiler contraction choices).
+#ifdef __CUDACC__
+__device__ __forceinline__ float gs2_quadform(float ca, float cb, float cc, float dx, float dy) {
+    // q = ca dx^2 + 2 cb dx dy + cc dy^2
+    float q = __fmul_rn(__fmul_rn(ca, dx), dx);
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, cb), dx), dy));
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(cc, dy), dy));
+    return q;
+}
+
+// Gaussian falloff G = exp(-q/2) at pixel offset (dx, dy)
+__device__ __forceinline__ float gs2_gauss(float ca, float cb, float cc, float dx, float dy) {
+    return expf(__fmul_rn(-0.5f, gs2_quadform(ca, cb, cc, dx, dy)));
+}
+#endif

@@ -1,0 +1,490 @@
+// C-ABI entry points of libgs2.so: argument checking, scratch ownership and
+// launch sequencing.  Every compute step runs in the kernels of this library.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+#define RET_CUDA(ctx, expr)                                                                       \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            if (ctx) (ctx)->err = std::string(#expr) + ": " + cudaGetErrorString(e_);             \
+            return GS2_ERR_CUDA;                                                                  \
+        }                                                                                         \
+    } while (0)
+
+#define REQUIRE(ctx, cond, code, msg)                                                             \
+    do {                                                                                          \
+        if (!(cond)) {                                                                            \
+            if (ctx) (ctx)->err = (msg);                                                          \
+            return (code);                                                                        \
+        }                                                                                         \
+    } while (0)
+
+static const int SORT_BLOCKS = 148 * 4;
+
+extern "C" void gs2_config_default(gs2_config *c) {
+    if (!c) return;
+    c->lambda_ssim = 0.2f;
+    c->alpha_min = 1.f / 255.f;
+    c->alpha_max = 0.99f;
+    c->t_min = 1e-4f;
+    c->lowpass = 0.3f;
+    c->near_z = 0.2f;
+    c->barrier_alpha = 1e-6f;
+    c->frac_to_boundary = 0.99f;
+    c->damping_mu0 = 1.0f;
+    c->damping_tries = 6;
+    c->scale_min = 1e-7f;
+    c->scale_trust = 2.0f;
+    c->ssim_c1 = 1e-4f;
+    c->ssim_c2 = 9e-4f;
+    c->ssim_sigma = 1.5f;
+    c->ssim_radius = 5;
+    c->knn_k = 3;
+    c->downsample = 2;
+    c->precision = 0;
+}
+
+static bool cfg_ok(const gs2_config *c, std::string &err) {
+    if (!(c->alpha_min > 0.f && c->alpha_min < 1.f)) { err = "alpha_min must be in (0,1)"; return false; }
+    if (!(c->alpha_max >= c->alpha_min && c->alpha_max <= 1.f)) { err = "alpha_max must be in [alpha_min,1]"; return false; }
+    if (!(c->t_min >= 0.f && c->t_min < 1.f)) { err = "t_min must be in [0,1)"; return false; }
+    if (!(c->lowpass >= 0.f) || !(c->near_z > 0.f)) { err = "lowpass >= 0 and near_z > 0 required"; return false; }
+    if (c->ssim_radius != 5) { err = "only an 11x11 SSIM window (ssim_radius 5) is supported"; return false; }
+    if (c->knn_k < 0 || c->knn_k > 16) { err = "knn_k must be in [0,16]"; return false; }
+    if (c->downsample < 1 || c->downsample > 8) { err = "downsample must be in [1,8]"; return false; }
+    if (c->damping_tries < 0 || c->damping_tries > 30 || !(c->damping_mu0 >= 0.f)) { err = "bad damping"; return false; }
+    if (!(c->scale_trust > 1.f) || !(c->scale_min > 0.f)) { err = "scale_trust > 1 and scale_min > 0 required"; return false; }
+    if (!(c->frac_to_boundary > 0.f && c->frac_to_boundary < 1.f)) { err = "frac_to_boundary in (0,1)"; return false; }
+    return true;
+}
+
+static size_t blocks_bytes_impl(int group, int64_t n, int sh_degree, int n_views) {
+    const int S = sh_count(sh_degree);
+    switch (group) {
+    case GS2_POS:
+    case GS2_SCALE: return sizeof(float) * 9 * (size_t)n;
+    case GS2_ROT:
+    case GS2_OPACITY: return sizeof(float) * 2 * (size_t)n;
+    default: return sizeof(float) * (size_t)(6 + S) * n * (size_t)n_views;
+    }
+}
+
+static size_t step_bytes_impl(int group, int64_t n, int sh_degree) {
+    switch (group) {
+    case GS2_POS:
+    case GS2_SCALE: return sizeof(float) * 3 * (size_t)n;
+    case GS2_ROT:
+    case GS2_OPACITY: return sizeof(float) * (size_t)n;
+    default: return sizeof(float) * 3 * (size_t)sh_count(sh_degree) * n;
+    }
+}
+
+extern "C" size_t gs2_proj_bytes(int64_t n) { return proj_bytes_impl(n < 1 ? 1 : n); }
+extern "C" size_t gs2_raster_state_bytes(int32_t w, int32_t h) { return raster_state_bytes_impl(w, h); }
+extern "C" size_t gs2_blocks_bytes(gs2_group g, int64_t n, int32_t sh, int32_t nv) {
+    return blocks_bytes_impl(g, n, sh, nv < 1 ? 1 : nv);
+}
+extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return step_bytes_impl(g, n, sh); }
+
+static void free_ctx(gs2_ctx *c) {
+    void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
+                    c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
+                    c->sw_step, c->d_status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t max_n, int32_t max_w, int32_t max_h,
+                                 int32_t max_sh, int64_t max_pairs) {
+    if (!out) return GS2_ERR_ARG;
+    *out = nullptr;
+    if (max_n < 1 || max_w < 1 || max_h < 1 || max_sh < 0) return GS2_ERR_ARG;
+    if (max_sh > 3) return GS2_ERR_UNSUPPORTED;
+    if (max_n > (int64_t)0x7FFFFFFF || (int64_t)max_w * max_h > (int64_t)1 << 28) return GS2_ERR_SHAPE;
+    gs2_ctx *c = new (std::nothrow) gs2_ctx();
+    if (!c) return GS2_ERR_OOM;
+    if (cfg) c->cfg = *cfg;
+    else gs2_config_default(&c->cfg);
+    if (!cfg_ok(&c->cfg, c->err)) {
+        delete c;
+        return GS2_ERR_ARG;
+    }
+    if (max_pairs <= 0) max_pairs = 16 * max_n;
+    if (max_pairs > (int64_t)0xF0000000ll) max_pairs = (int64_t)0xF0000000ll;
+    c->max_n = max_n;
+    c->max_w = max_w;
+    c->max_h = max_h;
+    c->max_sh = max_sh;
+    c->max_pairs = max_pairs;
+    c->nb_sort = SORT_BLOCKS;
+    const size_t P = (size_t)max_w * max_h;
+    const int tiles = ((max_w + GS2_TILE - 1) / GS2_TILE) * ((max_h + GS2_TILE - 1) / GS2_TILE);
+    const int K = c->cfg.knn_k, f = c->cfg.downsample;
+    const int S = sh_count(max_sh);
+    bool ok = true;
+    auto A = [&](void **p, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+            ok = false;
+            *p = nullptr;
+        }
+    };
+    for (int i = 0; i < 2; ++i) {
+        A((void **)&c->keys[i], sizeof(unsigned long long) * (size_t)max_pairs);
+        A((void **)&c->vals[i], sizeof(uint32_t) * (size_t)max_pairs);
+    }
+    A((void **)&c->ghist, sizeof(uint32_t) * 256 * (size_t)SORT_BLOCKS);
+    A((void **)&c->bsum, sizeof(unsigned long long) * 1024);
+    A((void **)&c->d_count, sizeof(uint32_t) * 4);
+    A((void **)&c->ranges, sizeof(uint2) * (size_t)tiles);
+    A((void **)&c->zbuf, sizeof(float) * GS2_ZPOS * (size_t)max_n);
+    A((void **)&c->pix_e, sizeof(float) * 3 * P);
+    A((void **)&c->pix_h, sizeof(float) * 3 * P);
+    A(&c->sw_proj, proj_bytes_impl(max_n));
+    A(&c->sw_rstate, raster_state_bytes_impl(max_w, max_h));
+    A((void **)&c->sw_image, sizeof(float) * 3 * P);
+    A((void **)&c->sw_tgt, sizeof(float) * 3 * (size_t)(max_w / f) * (max_h / f) * (size_t)std::max(K, 1));
+    size_t bmax = 0;
+    for (int g = 0; g < 5; ++g) bmax = std::max(bmax, blocks_bytes_impl(g, max_n, max_sh, 1 + K));
+    c->sw_blocks_bytes = bmax;
+    A(&c->sw_blocks, bmax);
+    c->sw_step_bytes = sizeof(float) * 3 * (size_t)S * max_n;
+    A(&c->sw_step, c->sw_step_bytes);
+    A((void **)&c->d_status, sizeof(uint32_t) * 4);
+    if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(float) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
+    if (!ok) {
+        free_ctx(c);
+        delete c;
+        cudaGetLastError();
+        return GS2_ERR_OOM;
+    }
+    *out = c;
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_destroy(gs2_ctx *ctx) {
+    if (!ctx) return GS2_ERR_ARG;
+    free_ctx(ctx);
+    delete ctx;
+    return GS2_OK;
+}
+
+extern "C" const char *gs2_last_error(const gs2_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" gs2_status gs2_set_config(gs2_ctx *ctx, const gs2_config *cfg) {
+    if (!ctx || !cfg) return GS2_ERR_ARG;
+    std::string err;
+    REQUIRE(ctx, cfg_ok(cfg, err), GS2_ERR_ARG, err);
+    REQUIRE(ctx, cfg->knn_k <= ctx->cfg.knn_k || cfg->knn_k == 0, GS2_ERR_SHAPE,
+            "knn_k larger than at gs2_create (sweep scratch sized for it)");
+    REQUIRE(ctx, cfg->downsample >= ctx->cfg.downsample, GS2_ERR_SHAPE,
+            "downsample smaller than at gs2_create (sweep scratch sized for it)");
+    const int K0 = ctx->cfg.knn_k, f0 = ctx->cfg.downsample;
+    ctx->cfg = *cfg;
+    ctx->cfg.knn_k = cfg->knn_k;
+    (void)K0;
+    (void)f0;
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_check(gs2_ctx *ctx, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    RET_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t st = 0;
+    RET_CUDA(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    RET_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
+    if (st & GS2_ST_CAPACITY) {
+        ctx->err = "more (tile, Gaussian) pairs than max_pairs";
+        return GS2_ERR_CAPACITY;
+    }
+    if (st & GS2_ST_NONFINITE) return GS2_ERR_NONFINITE;
+    if (st & GS2_ST_TIMEOUT) return GS2_ERR_TIMEOUT;
+    return GS2_OK;
+}
+
+static gs2_status check_scene(gs2_ctx *ctx, const gs2_scene *s) {
+    REQUIRE(ctx, s != nullptr, GS2_ERR_ARG, "scene is null");
+    REQUIRE(ctx, s->n >= 0 && s->n <= ctx->max_n, GS2_ERR_SHAPE, "scene larger than max_gaussians");
+    REQUIRE(ctx, s->sh_degree >= 0 && s->sh_degree <= ctx->max_sh, GS2_ERR_SHAPE, "sh_degree above max_sh_degree");
+    REQUIRE(ctx, s->n == 0 || (s->mean && s->quat && s->scale && s->opacity && s->sh), GS2_ERR_ARG,
+            "scene has a null buffer");
+    return GS2_OK;
+}
+
+static gs2_status check_cam(gs2_ctx *ctx, const gs2_camera *c) {
+    REQUIRE(ctx, c != nullptr, GS2_ERR_ARG, "camera is null");
+    REQUIRE(ctx, c->width >= 1 && c->height >= 1, GS2_ERR_ARG, "camera has no pixels");
+    REQUIRE(ctx, c->width <= ctx->max_w && c->height <= ctx->max_h, GS2_ERR_SHAPE, "camera larger than max size");
+    REQUIRE(ctx, c->fx > 0.f && c->fy > 0.f, GS2_ERR_ARG, "focal lengths must be positive");
+    return GS2_OK;
+}
+
+#define TRY(x)                        \
+    do {                              \
+        gs2_status s_ = (x);          \
+        if (s_ != GS2_OK) return s_;  \
+    } while (0)
+
+static gs2_status do_project(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cam, void *proj,
+                             cudaStream_t st) {
+    const DevScene sc = make_devscene(scene);
+    const DevCam dc = make_devcam(cam);
+    const int tx = (cam->width + GS2_TILE - 1) / GS2_TILE, ty = (cam->height + GS2_TILE - 1) / GS2_TILE;
+    RET_CUDA(ctx, launch_project(sc, dc, ctx->cfg, proj_view(proj, scene->n), tx, ty, st));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_project(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cam, void *proj,
+                                  gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    TRY(check_scene(ctx, scene));
+    TRY(check_cam(ctx, cam));
+    REQUIRE(ctx, proj != nullptr, GS2_ERR_ARG, "proj is null");
+    return do_project(ctx, scene, cam, proj, (cudaStream_t)stream);
+}
+
+static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const void *proj, float *image,
+                            void *rstate, cudaStream_t st) {
+    ctx->tiles_x = (cam->width + GS2_TILE - 1) / GS2_TILE;
+    ctx->tiles_y = (cam->height + GS2_TILE - 1) / GS2_TILE;
+    ProjView pv = proj_view(const_cast<void *>(proj), n);
+    RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st));
+    RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image,
+                                raster_view(rstate, cam->width, cam->height), st));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_raster_fwd(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cam, const void *proj,
+                                     float *image, void *raster_state, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    TRY(check_scene(ctx, scene));
+    TRY(check_cam(ctx, cam));
+    REQUIRE(ctx, proj && image && raster_state, GS2_ERR_ARG, "null buffer");
+    return do_raster(ctx, scene->n, cam, proj, image, raster_state, (cudaStream_t)stream);
+}
+
+extern "C" gs2_status gs2_loss_derivs(gs2_ctx *ctx, const float *image, const float *target, int32_t w, int32_t h,
+                                      float *e, float *hh, double *loss_out, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    REQUIRE(ctx, image && target && e && hh, GS2_ERR_ARG, "null buffer");
+    REQUIRE(ctx, w >= 1 && h >= 1, GS2_ERR_ARG, "empty image");
+    RET_CUDA(ctx, launch_loss(image, target, w, h, ctx->cfg, e, hh, loss_out, (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+static gs2_status do_accum(gs2_ctx *ctx, int group, const gs2_scene *scene, const gs2_camera *view,
+                           const gs2_camera *primary, const void *proj, const void *rstate, const float *image,
+                           const float *target, int slot, void *blocks, double *loss_out, cudaStream_t st) {
+    RET_CUDA(ctx, launch_loss(image, target, view->width, view->height, ctx->cfg, ctx->pix_e, ctx->pix_h, loss_out,
+                              st));
+    RET_CUDA(ctx, launch_accum(ctx, group, make_devscene(scene), make_devcam(view), make_devcam(primary),
+                               proj_view(const_cast<void *>(proj), scene->n),
+                               raster_view(const_cast<void *>(rstate), view->width, view->height), ctx->cfg, slot,
+                               blocks, st));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_accum_newton_blocks(gs2_ctx *ctx, gs2_group group, const gs2_scene *scene,
+                                              const gs2_camera *view, const gs2_camera *primary, const void *proj,
+                                              const void *raster_state, const float *image, const float *target,
+                                              int32_t view_slot, void *blocks, double *loss_out,
+                                              gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    REQUIRE(ctx, group >= GS2_POS && group <= GS2_COLOR, GS2_ERR_ARG, "bad group");
+    TRY(check_scene(ctx, scene));
+    TRY(check_cam(ctx, view));
+    TRY(check_cam(ctx, primary));
+    REQUIRE(ctx, proj && raster_state && image && target && blocks, GS2_ERR_ARG, "null buffer");
+    REQUIRE(ctx, view_slot >= 0, GS2_ERR_ARG, "negative view_slot");
+    REQUIRE(ctx, ctx->tiles_x == (view->width + GS2_TILE - 1) / GS2_TILE &&
+                     ctx->tiles_y == (view->height + GS2_TILE - 1) / GS2_TILE,
+            GS2_ERR_ARG, "the last gs2_raster_fwd on this context was for a different image size");
+    return do_accum(ctx, group, scene, view, primary, proj, raster_state, image, target, view_slot, blocks, loss_out,
+                    (cudaStream_t)stream);
+}
+
+extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *blocks, int32_t n_views,
+                                     const gs2_scene *scene, const gs2_camera *primary, void *step, int32_t *n_failed,
+                                     gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    REQUIRE(ctx, group >= GS2_POS && group <= GS2_COLOR, GS2_ERR_ARG, "bad group");
+    TRY(check_scene(ctx, scene));
+    TRY(check_cam(ctx, primary));
+    REQUIRE(ctx, blocks && step, GS2_ERR_ARG, "null buffer");
+    REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
+    RET_CUDA(ctx, launch_solve(group, blocks, n_views, make_devscene(scene), make_devcam(primary), ctx->cfg, step,
+                               n_failed, (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_apply_step(gs2_ctx *ctx, gs2_group group, const void *step, gs2_scene *scene,
+                                     const gs2_camera *primary, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    REQUIRE(ctx, group >= GS2_POS && group <= GS2_COLOR, GS2_ERR_ARG, "bad group");
+    TRY(check_scene(ctx, scene));
+    TRY(check_cam(ctx, primary));
+    REQUIRE(ctx, step != nullptr, GS2_ERR_ARG, "step is null");
+    RET_CUDA(ctx, launch_apply(group, step, make_devscene(scene), make_devcam(primary), ctx->cfg,
+                               (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" void gs2_camera_downsample(const gs2_camera *in, int32_t f, gs2_camera *out) {
+    if (!in || !out || f < 1) return;
+    *out = *in;
+    out->width = in->width / f;
+    out->height = in->height / f;
+    out->fx = in->fx / (float)f;
+    out->fy = in->fy / (float)f;
+    out->cx = (in->cx + 0.5f) / (float)f - 0.5f;
+    out->cy = (in->cy + 0.5f) / (float)f - 0.5f;
+}
+
+extern "C" gs2_status gs2_downsample(gs2_ctx *ctx, const float *in, int32_t w, int32_t h, int32_t f, float *out,
+                                     gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    REQUIRE(ctx, in && out && f >= 1 && w >= f && h >= f, GS2_ERR_ARG, "bad downsample arguments");
+    RET_CUDA(ctx, launch_downsample(in, w, h, f, out, (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_bounding_sphere(gs2_ctx *ctx, const gs2_scene *scene, float *sphere_out,
+                                          gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    TRY(check_scene(ctx, scene));
+    REQUIRE(ctx, sphere_out != nullptr && scene->n > 0, GS2_ERR_ARG, "empty scene or null output");
+    RET_CUDA(ctx, launch_bounding_sphere(make_devscene(scene), sphere_out, (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const float *sphere, int32_t k,
+                                     int32_t *out) {
+    if (!centres || !sphere || !out || ncam < 1 || k < 0) return GS2_ERR_ARG;
+    std::vector<double> u(3 * (size_t)ncam);
+    for (int i = 0; i < ncam; ++i) {
+        double nn = 0;
+        for (int a = 0; a < 3; ++a) {
+            u[i * 3 + a] = (double)centres[i * 3 + a] - (double)sphere[a];
+            nn += u[i * 3 + a] * u[i * 3 + a];
+        }
+        nn = sqrt(nn);
+        if (!(nn > 0)) return GS2_ERR_ARG;
+        for (int a = 0; a < 3; ++a) u[i * 3 + a] /= nn;
+    }
+    std::vector<std::pair<double, int>> d;
+    for (int i = 0; i < ncam; ++i) {
+        d.clear();
+        for (int j = 0; j < ncam; ++j) {
+            if (j == i) continue;
+            double c = u[i * 3] * u[j * 3] + u[i * 3 + 1] * u[j * 3 + 1] + u[i * 3 + 2] * u[j * 3 + 2];
+            c = std::min(1.0, std::max(-1.0, c));
+            d.emplace_back((double)sphere[3] * acos(c), j);
+        }
+        std::sort(d.begin(), d.end());
+        for (int q = 0; q < k; ++q) out[i * k + q] = q < (int)d.size() ? d[q].second : -1;
+    }
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                                const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
+                                int32_t *n_failed, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    TRY(check_scene(ctx, scene));
+    REQUIRE(ctx, cams && targets && ncam >= 1 && t >= 0 && t < ncam, GS2_ERR_ARG, "bad cameras or primary index");
+    const int K = ctx->cfg.knn_k, f = ctx->cfg.downsample;
+    REQUIRE(ctx, K == 0 || knn != nullptr, GS2_ERR_ARG, "knn table is null");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nv = 1 + K;
+    int vid[17];
+    gs2_camera vcam[17];
+    const float *vtgt[17];
+    vid[0] = t;
+    vcam[0] = cams[t];
+    vtgt[0] = targets[t];
+    TRY(check_cam(ctx, &cams[t]));
+    REQUIRE(ctx, targets[t] != nullptr, GS2_ERR_ARG, "null target");
+    const size_t slot = 3 * (size_t)(ctx->max_w / f) * (ctx->max_h / f);
+    for (int i = 1; i < nv; ++i) {
+        const int v = knn[t * K + (i - 1)];
+        vid[i] = v;
+        if (v < 0) continue;
+        REQUIRE(ctx, v < ncam && targets[v] != nullptr, GS2_ERR_ARG, "bad knn entry or null target");
+        TRY(check_cam(ctx, &cams[v]));
+        gs2_camera_downsample(&cams[v], f, &vcam[i]);
+        REQUIRE(ctx, vcam[i].width >= 1 && vcam[i].height >= 1, GS2_ERR_ARG, "secondary too small to downsample");
+        float *dst = ctx->sw_tgt + (size_t)(i - 1) * slot;
+        if (f > 1) {
+            RET_CUDA(ctx, launch_downsample(targets[v], cams[v].width, cams[v].height, f, dst, st));
+            vtgt[i] = dst;
+        } else {
+            vtgt[i] = targets[v];
+        }
+    }
+    const gs2_camera *primary = &cams[t];
+    for (int group = 0; group < 5; ++group) {
+        RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, blocks_bytes_impl(group, scene->n, scene->sh_degree, nv), st));
+        for (int i = 0; i < nv; ++i) {
+            if (vid[i] < 0) continue;
+            TRY(do_project(ctx, scene, &vcam[i], ctx->sw_proj, st));
+            TRY(do_raster(ctx, scene->n, &vcam[i], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st));
+            TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image, vtgt[i],
+                         i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, st));
+        }
+        RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
+                                   ctx->sw_step, n_failed, st));
+        RET_CUDA(ctx, launch_apply(group, ctx->sw_step, make_devscene(scene), make_devcam(primary), ctx->cfg, st));
+    }
+    return GS2_OK;
+}
+
+// ------------------------------------------------------------------ introspection
+__global__ void k_unpack_proj(ProjView pv, int n, float *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float4 a = pv.recA[k], b = pv.recB[k], c = pv.col[k];
+    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, c.x, c.y, c.z, b.z, (float)pv.touched[k], 0.f};
+    for (int i = 0; i < 12; ++i) out[(size_t)i * n + k] = v[i];
+}
+
+extern "C" gs2_status gs2_debug_proj(const void *proj, int64_t n, float *out, gs2_stream stream) {
+    if (!proj || !out || n < 0) return GS2_ERR_ARG;
+    if (n == 0) return GS2_OK;
+    k_unpack_proj<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(proj_view(const_cast<void *>(proj), n),
+                                                                            (int)n, out);
+    return cudaGetLastError() == cudaSuccess ? GS2_OK : GS2_ERR_CUDA;
+}
+
+extern "C" gs2_status gs2_debug_keys(const void *proj, int64_t n, uint32_t *keys_out, gs2_stream stream) {
+    if (!proj || !keys_out || n < 0) return GS2_ERR_ARG;
+    ProjView pv = proj_view(const_cast<void *>(proj), n);
+    return cudaMemcpyAsync(keys_out, pv.key, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream) == cudaSuccess
+               ? GS2_OK
+               : GS2_ERR_CUDA;
+}
+
+extern "C" gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32_t *ids_out, int64_t capacity,
+                                      int64_t *n_pairs_out, gs2_stream stream) {
+    if (!ctx || !ranges_out || !ids_out || !n_pairs_out) return GS2_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t cnt[2];
+    RET_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    RET_CUDA(ctx, cudaStreamSynchronize(st));
+    *n_pairs_out = cnt[0];
+    const size_t ntiles = (size_t)ctx->tiles_x * ctx->tiles_y;
+    RET_CUDA(ctx, cudaMemcpyAsync(ranges_out, ctx->ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
+    const size_t m = std::min<size_t>(cnt[0], (size_t)std::max<int64_t>(capacity, 0));
+    if (m) RET_CUDA(ctx, cudaMemcpyAsync(ids_out, ctx->vals[ctx->sorted], sizeof(uint32_t) * m,
+                                         cudaMemcpyDeviceToDevice, st));
+    return GS2_OK;
+}

@@ -1,0 +1,215 @@
+// gs2_loss_derivs: per-pixel e = dL/dc and h = d2L/dc_q^2 (pixel diagonal) of
+// L = L2 + lambda L_SSIM (Sec. 4.2 loss equations), fused in one pass.
+//
+// For window centre p and pixel q (weight w_pq of the 11x11 Gaussian window):
+//   dSSIM_p/dc_q   = w_pq (A_p + B_p c^t_q + C_p c_q)
+//   d2SSIM_p/dc_q2 = w_pq^2 (K0_p + Kc_p c_q + Kt_p c^t_q + Kct_p c_q c^t_q + Kcc_p c_q^2) + w_pq C_p
+// (exact differentiation of f0 f1 / (f2 f3) with the window moments; the
+// coefficients depend only on p), so the sums over all windows containing q
+// are separable 11-tap correlations of eight coefficient maps with w or w^2.
+//
+// One CTA owns a 32x16 output tile and keeps everything in shared memory:
+// inputs with a 10-pixel halo (52x36), horizontal moment sums, the
+// coefficient maps on the 42x26 window-centre region and their horizontal
+// correlations.  HBM traffic per pixel: read c, c^t (24 B), write e, h (24 B).
+#include "common.cuh"
+
+#define LT_W 32
+#define LT_H 16
+#define LRAD 5
+#define LWIN 11
+#define IN_W (LT_W + 4 * LRAD)
+#define IN_H (LT_H + 4 * LRAD)
+#define MO_W (LT_W + 2 * LRAD)
+#define MO_H (LT_H + 2 * LRAD)
+#define SM_IN (IN_W * IN_H)
+#define SM_H1 (5 * IN_H * MO_W)
+#define SM_K (8 * MO_H * MO_W)
+#define SSIM_SMEM_FLOATS (2 * SM_IN + SM_H1 + SM_K)
+
+struct SsimConst {
+    float g[LWIN];
+    float g2[LWIN];
+    float c1, c2, lam, scale;
+};
+
+__device__ __forceinline__ void block_add_double(double v, double *dst, double *sred) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sred[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sred[i];
+        atomicAdd(dst, s);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, const float *__restrict__ tgt, int W,
+                                              int H, SsimConst K, float *__restrict__ eo, float *__restrict__ ho,
+                                              double *loss) {
+    extern __shared__ float sm[];
+    float *sX = sm, *sY = sm + SM_IN, *sH = sm + 2 * SM_IN, *sK = sm + 2 * SM_IN + SM_H1;
+    float *sHC = sH;  // reused after the moments are formed
+    __shared__ double sred[8];
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * LT_W, y0 = blockIdx.y * LT_H;
+    const size_t P = (size_t)W * H;
+    double l2acc = 0.0, lsacc = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const float *X = img + c * P, *Y = tgt + c * P;
+        for (int i = t; i < SM_IN; i += 256) {
+            const int r = i / IN_W, q = i % IN_W;
+            const int gx = x0 - 2 * LRAD + q, gy = y0 - 2 * LRAD + r;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            sX[i] = in ? X[(size_t)gy * W + gx] : 0.f;
+            sY[i] = in ? Y[(size_t)gy * W + gx] : 0.f;
+        }
+        __syncthreads();
+        // horizontal window sums of x, y, xx, yy, xy
+        for (int i = t; i < IN_H * MO_W; i += 256) {
+            const int r = i / MO_W, j = i % MO_W;
+            float a = 0.f, b = 0.f, cxx = 0.f, cyy = 0.f, cxy = 0.f;
+#pragma unroll
+            for (int d = 0; d < LWIN; ++d) {
+                const float xv = sX[r * IN_W + j + d], yv = sY[r * IN_W + j + d], w = K.g[d];
+                a = fmaf(w, xv, a);
+                b = fmaf(w, yv, b);
+                cxx = fmaf(w * xv, xv, cxx);
+                cyy = fmaf(w * yv, yv, cyy);
+                cxy = fmaf(w * xv, yv, cxy);
+            }
+            sH[0 * IN_H * MO_W + i] = a;
+            sH[1 * IN_H * MO_W + i] = b;
+            sH[2 * IN_H * MO_W + i] = cxx;
+            sH[3 * IN_H * MO_W + i] = cyy;
+            sH[4 * IN_H * MO_W + i] = cxy;
+        }
+        __syncthreads();
+        // vertical sums -> moments -> per-centre coefficients
+        for (int i = t; i < MO_H * MO_W; i += 256) {
+            const int r = i / MO_W, j = i % MO_W;
+            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int d = 0; d < LWIN; ++d) {
+                const float w = K.g[d];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) m[q] = fmaf(w, sH[q * IN_H * MO_W + (r + d) * MO_W + j], m[q]);
+            }
+            const int gx = x0 - LRAD + j, gy = y0 - LRAD + r;
+            float co[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const float mu = m[0], mt = m[1];
+                const float var = m[2] - mu * mu, vart = m[3] - mt * mt, cov = m[4] - mu * mt;
+                const float f0 = 2.f * mu * mt + K.c1, f1 = 2.f * cov + K.c2;
+                const float f2 = mu * mu + mt * mt + K.c1, f3 = var + vart + K.c2;
+                const float D = f2 * f3, N = f0 * f1;
+                const float iD = 1.f / D, iD2 = iD * iD, iD3 = iD2 * iD;
+                const float d10 = f1 - f0, d32 = f3 - f2;
+                co[0] = 2.f * mt * d10 * iD - 2.f * N * mu * d32 * iD2;                       // A
+                co[1] = 2.f * f0 * iD;                                                        // B
+                co[2] = -2.f * N * f2 * iD2;                                                  // C
+                co[3] = -8.f * mt * mt * iD - 8.f * mt * mu * d10 * d32 * iD2                 // K0
+                        - N * (2.f * f3 - 2.f * f2 - 8.f * mu * mu) * iD2 + 8.f * N * mu * mu * d32 * d32 * iD3;
+                co[4] = -8.f * mt * d10 * f2 * iD2 - 8.f * N * mu * iD2 + 16.f * N * mu * d32 * f2 * iD3;  // Kc
+                co[5] = 8.f * mt * iD - 8.f * f0 * mu * d32 * iD2;                            // Kt
+                co[6] = -8.f * f0 * f2 * iD2;                                                 // Kct
+                co[7] = 8.f * N * f2 * f2 * iD3;                                              // Kcc
+                if (j >= LRAD && j < LRAD + LT_W && r >= LRAD && r < LRAD + LT_H) lsacc += 1.0 - (double)(N * iD);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sK[q * MO_H * MO_W + i] = co[q];
+        }
+        __syncthreads();
+        // horizontal correlation of the coefficient maps (w for A, B, C; w^2 for the rest)
+        for (int i = t; i < 8 * MO_H * LT_W; i += 256) {
+            const int q = i / (MO_H * LT_W), rem = i % (MO_H * LT_W);
+            const int r = rem / LT_W, j = rem % LT_W;
+            const float *wt = (q < 3) ? K.g : K.g2;
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < LWIN; ++d) acc = fmaf(wt[d], sK[q * MO_H * MO_W + r * MO_W + j + d], acc);
+            sHC[i] = acc;
+        }
+        __syncthreads();
+        for (int i = t; i < LT_H * LT_W; i += 256) {
+            const int r = i / LT_W, j = i % LT_W;
+            const int gx = x0 + j, gy = y0 + r;
+            if (gx >= W || gy >= H) continue;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float *wt = (q < 3) ? K.g : K.g2;
+                float acc = 0.f;
+#pragma unroll
+                for (int d = 0; d < LWIN; ++d) acc = fmaf(wt[d], sHC[q * MO_H * LT_W + (r + d) * LT_W + j], acc);
+                v[q] = acc;
+            }
+            const float x = sX[(r + 2 * LRAD) * IN_W + j + 2 * LRAD], y = sY[(r + 2 * LRAD) * IN_W + j + 2 * LRAD];
+            const float dS = v[0] + y * v[1] + x * v[2];
+            const float d2S = v[3] + x * v[4] + y * v[5] + x * y * v[6] + x * x * v[7] + v[2];
+            const size_t p = (size_t)c * P + (size_t)gy * W + gx;
+            eo[p] = K.scale * (x - y) - K.lam * K.scale * dS;
+            ho[p] = K.scale - K.lam * K.scale * d2S;
+            l2acc += 0.5 * (double)(x - y) * (double)(x - y);
+        }
+        __syncthreads();
+    }
+    if (loss) {
+        block_add_double(l2acc * (double)K.scale, &loss[0], sred);
+        block_add_double(lsacc * (double)K.scale, &loss[1], sred);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_l2(const float *__restrict__ img, const float *__restrict__ tgt, size_t P3,
+                                            float scale, float *__restrict__ eo, float *__restrict__ ho,
+                                            double *loss) {
+    __shared__ double sred[8];
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P3; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = img[i] - tgt[i];
+        eo[i] = scale * d;
+        ho[i] = scale;
+        acc += 0.5 * (double)d * (double)d;
+    }
+    if (loss) block_add_double(acc * (double)scale, &loss[0], sred);
+}
+
+cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,
+                        float *hh, double *loss_out, cudaStream_t st) {
+    const size_t P = (size_t)w * h;
+    if (P == 0) return cudaSuccess;
+    const float scale = (float)(1.0 / (3.0 * (double)P));
+    if (cfg.lambda_ssim == 0.f) {
+        const size_t P3 = 3 * P;
+        int grid = (int)std::min<size_t>((P3 + 255) / 256, 148 * 16);
+        k_l2<<<grid, 256, 0, st>>>(image, target, P3, scale, e, hh, loss_out);
+        return cudaGetLastError();
+    }
+    SsimConst K;
+    double g[LWIN], s = 0.0;
+    for (int i = 0; i < LWIN; ++i) {
+        const double x = i - LRAD;
+        g[i] = exp(-x * x / (2.0 * (double)cfg.ssim_sigma * (double)cfg.ssim_sigma));
+        s += g[i];
+    }
+    for (int i = 0; i < LWIN; ++i) {
+        K.g[i] = (float)(g[i] / s);
+        K.g2[i] = (float)((g[i] / s) * (g[i] / s));
+    }
+    K.c1 = cfg.ssim_c1;
+    K.c2 = cfg.ssim_c2;
+    K.lam = cfg.lambda_ssim;
+    K.scale = scale;
+    const int smem = SSIM_SMEM_FLOATS * (int)sizeof(float);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e0 = cudaFuncSetAttribute(k_ssim, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e0 != cudaSuccess) return e0;
+        attr_set = true;
+    }
+    dim3 grid((w + LT_W - 1) / LT_W, (h + LT_H - 1) / LT_H);
+    k_ssim<<<grid, 256, smem, st>>>(image, target, w, h, K, e, hh, loss_out);
+    return cudaGetLastError();
+}

@@ -1,0 +1,125 @@
+// gs2_project: one thread per Gaussian (Sec. 3; App. A.1-A.3).
+//
+// Per Gaussian: camera-space centre t = Wr p + w, pixel centre
+// pi = (fx tx/tz + cx, fy ty/tz + cy), EWA covariance
+// Sigma2D = J Wr R diag(s^2) R^T Wr^T J^T + lowpass I with J the perspective
+// Jacobian at t, its inverse (conic), SH colour c~ = sum_i c_i B_i Phi_i(r)
+// with r the unit camera->centre direction, the tile rectangle of the support
+// { sigma G >= alpha_min } and the depth key.
+//
+// Memory: reads 13 + 3S floats per Gaussian from planar SoA rows (coalesced
+// 4-byte loads across the warp), writes 3 float4 records + rect + counts.
+// HBM-bound; FP64 is used only for the depth key (4 DFMA-equivalent ops).
+#include "common.cuh"
+#include "sh.cuh"
+
+__global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float lowpass, float near_z,
+                                                 float alpha_min, ProjView pv, int tiles_x, int tiles_y) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= sc.n) return;
+    const int n = sc.n;
+    const float px = sc.mean[k], py = sc.mean[n + k], pz = sc.mean[2 * n + k];
+    const float sigma = sc.opacity[k];
+    // depth key: FP64, fixed summation order, rounded to FP32 (products of
+    // FP32 values are exact in FP64, so the key is reproducible bit for bit)
+    double d = (double)cam.V[8] * (double)px;
+    d = d + (double)cam.V[9] * (double)py;
+    d = d + (double)cam.V[10] * (double)pz;
+    d = d + (double)cam.V[11];
+    const float tz = (float)d;
+    pv.key[k] = __float_as_uint(tz);
+    const bool vis = (d >= (double)near_z) && (sigma >= alpha_min);
+    if (!vis) {
+        pv.touched[k] = 0u;
+        pv.rect[k] = make_uint2(0u, 0u);
+        pv.recA[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pv.recB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float *V = cam.V;
+    const float tx = fmaf(V[0], px, fmaf(V[1], py, fmaf(V[2], pz, V[3])));
+    const float ty = fmaf(V[4], px, fmaf(V[5], py, fmaf(V[6], pz, V[7])));
+
+    // rotation from the normalised quaternion
+    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
+    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+    float R[3][3];
+    R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
+    R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
+    R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+    const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
+
+    // T = J Wr (2x3)
+    const float itz = 1.f / tz;
+    const float j00 = cam.fx * itz, j02 = -cam.fx * tx * itz * itz;
+    const float j11 = cam.fy * itz, j12 = -cam.fy * ty * itz * itz;
+    float T0[3], T1[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T0[j] = j00 * V[j] + j02 * V[8 + j];
+        T1[j] = j11 * V[4 + j] + j12 * V[8 + j];
+    }
+    // Sigma2D = sum_j s_j^2 m_j m_j^T, m_j = T R e_j
+    const float ss[3] = {s0 * s0, s1 * s1, s2 * s2};
+    float sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float m0 = T0[0] * R[0][j] + T0[1] * R[1][j] + T0[2] * R[2][j];
+        const float m1 = T1[0] * R[0][j] + T1[1] * R[1][j] + T1[2] * R[2][j];
+        sxx = fmaf(ss[j] * m0, m0, sxx);
+        sxy = fmaf(ss[j] * m0, m1, sxy);
+        syy = fmaf(ss[j] * m1, m1, syy);
+    }
+    sxx += lowpass;
+    syy += lowpass;
+    const float det = sxx * syy - sxy * sxy;
+    const float idet = 1.f / det;
+    const float ca = syy * idet, cb = -sxy * idet, cc = sxx * idet;
+    const float pix_x = fmaf(cam.fx * tx, itz, cam.cx);
+    const float pix_y = fmaf(cam.fy * ty, itz, cam.cy);
+
+    // tile rectangle of the support ellipse (half extents sqrt(2 ln(sigma/alpha_min) Sigma_ii)),
+    // widened slightly so FP32 rounding can only add tiles, never drop one
+    const float l = 2.f * logf(sigma / alpha_min);
+    const float rx = sqrtf(fmaxf(l * sxx, 0.f)) * 1.0005f + 0.02f;
+    const float ry = sqrtf(fmaxf(l * syy, 0.f)) * 1.0005f + 0.02f;
+    const float fx0 = fmaxf(ceilf(pix_x - rx), 0.f), fx1 = fminf(floorf(pix_x + rx), (float)(cam.w - 1));
+    const float fy0 = fmaxf(ceilf(pix_y - ry), 0.f), fy1 = fminf(floorf(pix_y + ry), (float)(cam.h - 1));
+    uint32_t touched = 0u;
+    uint2 rect = make_uint2(0u, 0u);
+    if (fx0 <= fx1 && fy0 <= fy1) {
+        const uint32_t tx0 = (uint32_t)fx0 / GS2_TILE, tx1 = (uint32_t)fx1 / GS2_TILE + 1u;
+        const uint32_t ty0 = (uint32_t)fy0 / GS2_TILE, ty1 = (uint32_t)fy1 / GS2_TILE + 1u;
+        touched = (tx1 - tx0) * (ty1 - ty0);
+        rect = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
+    }
+    pv.touched[k] = touched;
+    pv.rect[k] = rect;
+
+    // view-dependent colour
+    float rxv = px - cam.o[0], ryv = py - cam.o[1], rzv = pz - cam.o[2];
+    const float rn = rsqrtf(rxv * rxv + ryv * ryv + rzv * rzv);
+    rxv *= rn; ryv *= rn; rzv *= rn;
+    float phi[GS2_MAX_SH];
+    sh_phi(sc.S, rxv, ryv, rzv, phi);
+    float col[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.f;
+        for (int i = 0; i < sc.S; ++i) acc = fmaf(sh_norm(i) * phi[i], sc.sh[(size_t)(c * sc.S + i) * n + k], acc);
+        col[c] = acc;
+    }
+    pv.recA[k] = make_float4(pix_x, pix_y, ca, cb);
+    pv.recB[k] = make_float4(cc, sigma, tz, 0.f);
+    pv.col[k] = make_float4(col[0], col[1], col[2], 0.f);
+}
+
+cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
+                           int tiles_y, cudaStream_t st) {
+    if (sc.n == 0) return cudaSuccess;
+    k_project<<<(sc.n + 255) / 256, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x,
+                                                   tiles_y);
+    return cudaGetLastError();
+}

@@ -1,0 +1,73 @@
+// gs2_raster_fwd compositing (Eq. 3dgs): one 16x16 CTA per screen tile, one
+// thread per pixel, the tile's depth-sorted Gaussian list staged through
+// shared memory in batches of 256 records (one record gather per thread per
+// batch; the per-pixel inner loop reads shared memory only).
+//   alpha = min(sigma G, alpha_max); skip alpha < alpha_min; stop before
+//   T (1 - alpha) < t_min; c += alpha T c~; black background.
+// Writes the planar image, the final transmittance and the list position
+// after the last contributor (consumed by the accumulation pass).
+#include "common.cuh"
+
+__global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ ids, ProjView pv, int W, int H,
+                                                         int tiles_x, float amin, float amax, float tmin,
+                                                         float *__restrict__ image, RasterView rv) {
+    __shared__ float4 sA[GS2_TILE_PIX], sB[GS2_TILE_PIX], sC[GS2_TILE_PIX];
+    const int t = threadIdx.x;
+    const int tile = blockIdx.y * tiles_x + blockIdx.x;
+    const int px = blockIdx.x * GS2_TILE + (t % GS2_TILE), py = blockIdx.y * GS2_TILE + (t / GS2_TILE);
+    const bool inside = px < W && py < H;
+    bool done = !inside;
+    const uint2 r = ranges[tile];
+    const int n = (int)(r.y - r.x);
+    const float fx = (float)px, fy = (float)py;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    uint32_t lastc = 0u;
+    for (int b0 = 0; b0 < n; b0 += GS2_TILE_PIX) {
+        if (__syncthreads_count(done) == GS2_TILE_PIX) break;
+        const int j = b0 + t;
+        if (j < n) {
+            const uint32_t k = ids[r.x + j];
+            sA[t] = pv.recA[k];
+            sB[t] = pv.recB[k];
+            sC[t] = pv.col[k];
+        }
+        __syncthreads();
+        const int m = min(GS2_TILE_PIX, n - b0);
+        for (int i = 0; i < m && !done; ++i) {
+            const float4 A = sA[i];
+            const float4 B = sB[i];
+            const float G = gs2_gauss(A.z, A.w, B.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
+            const float alpha = fminf(__fmul_rn(B.y, G), amax);
+            if (alpha < amin) continue;
+            const float tt = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            if (tt < tmin) {
+                done = true;
+                break;
+            }
+            const float4 C = sC[i];
+            const float wgt = alpha * T;
+            c0 = fmaf(wgt, C.x, c0);
+            c1 = fmaf(wgt, C.y, c1);
+            c2 = fmaf(wgt, C.z, c2);
+            T = tt;
+            lastc = (uint32_t)(b0 + i + 1);
+        }
+    }
+    if (inside) {
+        const size_t P = (size_t)W * H, p = (size_t)py * W + px;
+        image[p] = c0;
+        image[P + p] = c1;
+        image[2 * P + p] = c2;
+        rv.tfinal[p] = T;
+        rv.last[p] = lastc;
+    }
+}
+
+cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
+                          RasterView rv, cudaStream_t st) {
+    dim3 grid(ctx->tiles_x, ctx->tiles_y);
+    k_raster<<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->vals[ctx->sorted], pv, cam.w, cam.h, ctx->tiles_x,
+                                            cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv);
+    return cudaGetLastError();
+}

@@ -1,0 +1,325 @@
+// gs2_solve_step / gs2_apply_step: per-Gaussian damped local Newton steps
+// (Eq. local_newton) and the group updates (Sec. 4.2).
+//
+// Damping (the paper fixes step size 1 and is silent on indefinite blocks):
+// H + mu m I with m = mean |diag H|, mu = mu0 10^i, i = 0..tries, until the
+// Cholesky factorisation has positive pivots; otherwise the step is 0 and the
+// failure is counted.  A block with all-zero gradient and Hessian (no
+// contributing pixel) gets a zero step.
+//   position: 2x2 solve in U = [u_x, u_y] perpendicular to the primary view ray
+//   rotation: scalar angle about the primary view ray
+//   scaling:  2x2 solve in the row space of d lambda / d s (eigenvalues of the
+//             primary view's projected covariance), update kept in [s/k, k s]
+//   opacity:  scalar with the log barrier, fraction-to-boundary inside (0, 1)
+//   colour:   S x S per channel from the factored per-view slots
+// One thread per Gaussian (per Gaussian and channel for colour); blocks of
+// size <= 3 live in registers, the 16x16 colour factor in local memory.
+#include "common.cuh"
+
+template <int NMAX>
+__device__ int damped_solve(int N, const float *H, const float *g, float mu0, int tries, float *x) {
+    float m = 0.f, gz = 0.f;
+    for (int i = 0; i < N; ++i) {
+        m += fabsf(H[i * N + i]);
+        gz += fabsf(g[i]);
+        x[i] = 0.f;
+    }
+    for (int i = 0; i < N * N; ++i) gz += fabsf(H[i]);
+    if (gz == 0.f) return 2;
+    m /= (float)N;
+    float mu = mu0;
+    float L[NMAX * NMAX];
+    for (int att = 0; att <= tries; ++att, mu *= 10.f) {
+        bool ok = true;
+        for (int j = 0; j < N && ok; ++j) {
+            float d = H[j * N + j] + mu * m;
+            for (int k = 0; k < j; ++k) d -= L[j * N + k] * L[j * N + k];
+            if (!(d > 0.f)) {
+                ok = false;
+                break;
+            }
+            const float ljj = sqrtf(d);
+            L[j * N + j] = ljj;
+            const float il = 1.f / ljj;
+            for (int i = j + 1; i < N; ++i) {
+                float s = H[i * N + j];
+                for (int k = 0; k < j; ++k) s -= L[i * N + k] * L[j * N + k];
+                L[i * N + j] = s * il;
+            }
+        }
+        if (!ok) continue;
+        float y[NMAX];
+        for (int i = 0; i < N; ++i) {
+            float s = -g[i];
+            for (int k = 0; k < i; ++k) s -= L[i * N + k] * y[k];
+            y[i] = s / L[i * N + i];
+        }
+        for (int i = N - 1; i >= 0; --i) {
+            float s = y[i];
+            for (int k = i + 1; k < N; ++k) s -= L[k * N + i] * x[k];
+            x[i] = s / L[i * N + i];
+        }
+        return 0;
+    }
+    for (int i = 0; i < N; ++i) x[i] = 0.f;
+    return 1;
+}
+
+__device__ __forceinline__ void unit_dir(const DevCam &cam, const float p[3], float r[3]) {
+    r[0] = p[0] - cam.o[0];
+    r[1] = p[1] - cam.o[1];
+    r[2] = p[2] - cam.o[2];
+    const float in = rsqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    r[0] *= in; r[1] *= in; r[2] *= in;
+}
+
+__global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries, float *step,
+                            int32_t *nfail) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    float p[3] = {sc.mean[k], sc.mean[n + k], sc.mean[2 * n + k]};
+    float r[3];
+    unit_dir(pr, p, r);
+    float e[3] = {0.f, 1.f, 0.f};
+    if (fabsf(r[1]) > 0.999f) { e[0] = 1.f; e[1] = 0.f; }
+    const float d = r[0] * e[0] + r[1] * e[1] + r[2] * e[2];
+    float uy[3] = {e[0] - d * r[0], e[1] - d * r[1], e[2] - d * r[2]};
+    const float un = rsqrtf(uy[0] * uy[0] + uy[1] * uy[1] + uy[2] * uy[2]);
+    uy[0] *= un; uy[1] *= un; uy[2] *= un;
+    const float ux[3] = {r[1] * uy[2] - r[2] * uy[1], r[2] * uy[0] - r[0] * uy[2], r[0] * uy[1] - r[1] * uy[0]};
+    const float g[3] = {B[k], B[n + k], B[2 * n + k]};
+    const float h00 = B[3 * n + k], h01 = B[4 * n + k], h02 = B[5 * n + k], h11 = B[6 * n + k], h12 = B[7 * n + k],
+                h22 = B[8 * n + k];
+    const float Hm[3][3] = {{h00, h01, h02}, {h01, h11, h12}, {h02, h12, h22}};
+    const float *U[2] = {ux, uy};
+    float gv[2], Hv[4];
+    for (int a = 0; a < 2; ++a) {
+        gv[a] = U[a][0] * g[0] + U[a][1] * g[1] + U[a][2] * g[2];
+        for (int b = 0; b < 2; ++b) {
+            float acc = 0.f;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += U[a][i] * Hm[i][j] * U[b][j];
+            Hv[a * 2 + b] = acc;
+        }
+    }
+    float dv[2];
+    const int st = damped_solve<2>(2, Hv, gv, mu0, tries, dv);
+    if (st == 1 && nfail) atomicAdd(nfail, 1);
+    for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = ux[i] * dv[0] + uy[i] * dv[1];
+}
+
+__global__ void k_solve_scalar(int n, const float *__restrict__ B, float mu0, int tries, float *step, int32_t *nfail) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float g = B[k], h = B[n + k];
+    float x;
+    const int st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+    if (st == 1 && nfail) atomicAdd(nfail, 1);
+    step[k] = x;
+}
+
+__global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float mu0, int tries, float barrier,
+                                float tau, float *step, int32_t *nfail) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    const float sg = sc.opacity[k];
+    float g = B[k], h = B[n + k], x = 0.f;
+    int st = 2;
+    if (!(g == 0.f && h == 0.f)) {
+        g += barrier * (-1.f / sg + 1.f / (1.f - sg));
+        h += barrier * (1.f / (sg * sg) + 1.f / ((1.f - sg) * (1.f - sg)));
+        st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+    }
+    if (st == 1 && nfail) atomicAdd(nfail, 1);
+    // fraction-to-boundary on the increment itself: x in [-tau sigma, tau (1 - sigma)]
+    const float xc = fminf(fmaxf(x, -tau * sg), tau * (1.f - sg));
+    step[k] = (st == 0) ? xc : 0.f;
+}
+
+__global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries,
+                              float near_z, float trust, float *step, int32_t *nfail) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    const float g[3] = {B[k], B[n + k], B[2 * n + k]};
+    float Hs[6];
+    bool zero = g[0] == 0.f && g[1] == 0.f && g[2] == 0.f;
+    for (int i = 0; i < 6; ++i) {
+        Hs[i] = B[(size_t)(3 + i) * n + k];
+        zero = zero && Hs[i] == 0.f;
+    }
+    for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = 0.f;
+    if (zero) return;
+    const float p[3] = {sc.mean[k], sc.mean[n + k], sc.mean[2 * n + k]};
+    const float s[3] = {sc.scale[k], sc.scale[n + k], sc.scale[2 * n + k]};
+    const float *V = pr.V;
+    double dz = (double)V[8] * (double)p[0];
+    dz = dz + (double)V[9] * (double)p[1];
+    dz = dz + (double)V[10] * (double)p[2];
+    dz = dz + (double)V[11];
+    if (!(dz >= (double)near_z)) return;
+    float t[3];
+    for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * p[0] + V[i * 4 + 1] * p[1] + V[i * 4 + 2] * p[2] + V[i * 4 + 3];
+    const float J[2][3] = {{pr.fx / t[2], 0.f, -pr.fx * t[0] / (t[2] * t[2])},
+                           {0.f, pr.fy / t[2], -pr.fy * t[1] / (t[2] * t[2])}};
+    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
+    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+    float M[2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) {
+            float acc = 0.f;
+            for (int i = 0; i < 3; ++i) {
+                const float wr = V[i * 4] * R[0][b] + V[i * 4 + 1] * R[1][b] + V[i * 4 + 2] * R[2][b];
+                acc += J[a][i] * wr;
+            }
+            M[a][b] = acc;
+        }
+    float A00 = 0.f, A01 = 0.f, A11 = 0.f;
+    for (int j = 0; j < 3; ++j) {
+        const float s2 = s[j] * s[j];
+        A00 += M[0][j] * M[0][j] * s2;
+        A01 += M[0][j] * M[1][j] * s2;
+        A11 += M[1][j] * M[1][j] * s2;
+    }
+    const float phi = 0.5f * atan2f(2.f * A01, A00 - A11);
+    const float c = cosf(phi), sn = sinf(phi);
+    float Tt[2][3];
+    for (int j = 0; j < 3; ++j) {
+        const float a = c * M[0][j] + sn * M[1][j];
+        const float b = -sn * M[0][j] + c * M[1][j];
+        Tt[0][j] = 2.f * a * a * s[j];
+        Tt[1][j] = 2.f * b * b * s[j];
+    }
+    float G00 = 0.f, G01 = 0.f, G11 = 0.f;
+    for (int j = 0; j < 3; ++j) {
+        G00 += Tt[0][j] * Tt[0][j];
+        G01 += Tt[0][j] * Tt[1][j];
+        G11 += Tt[1][j] * Tt[1][j];
+    }
+    const float det = G00 * G11 - G01 * G01;
+    if (!(det > 1e-30f) || !(det > 1e-6f * G00 * G11)) return;
+    const float I00 = G11 / det, I01 = -G01 / det, I11 = G00 / det;
+    float Q[3][2];
+    for (int j = 0; j < 3; ++j) {
+        Q[j][0] = Tt[0][j] * I00 + Tt[1][j] * I01;
+        Q[j][1] = Tt[0][j] * I01 + Tt[1][j] * I11;
+    }
+    const float Hm[3][3] = {{Hs[0], Hs[1], Hs[2]}, {Hs[1], Hs[3], Hs[4]}, {Hs[2], Hs[4], Hs[5]}};
+    float gl[2], Hl[4];
+    for (int a = 0; a < 2; ++a) {
+        gl[a] = Q[0][a] * g[0] + Q[1][a] * g[1] + Q[2][a] * g[2];
+        for (int b = 0; b < 2; ++b) {
+            float acc = 0.f;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += Q[i][a] * Hm[i][j] * Q[j][b];
+            Hl[a * 2 + b] = acc;
+        }
+    }
+    float dl[2];
+    const int st = damped_solve<2>(2, Hl, gl, mu0, tries, dl);
+    if (st == 1 && nfail) atomicAdd(nfail, 1);
+    for (int i = 0; i < 3; ++i) {
+        const float ds = Q[i][0] * dl[0] + Q[i][1] * dl[1];
+        // s + ds stays in [s / trust, s trust], clamped on the increment
+        step[(size_t)i * n + k] = fminf(fmaxf(ds, s[i] / trust - s[i]), s[i] * trust - s[i]);
+    }
+}
+
+__global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_views, float mu0, int tries,
+                              float *step, int32_t *nfail) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n, S = sc.S;
+    if (idx >= 3 * n) return;
+    const int ch = idx / n, k = idx % n;
+    float H[GS2_MAX_SH * GS2_MAX_SH], g[GS2_MAX_SH], x[GS2_MAX_SH];
+    for (int i = 0; i < S * S; ++i) H[i] = 0.f;
+    for (int i = 0; i < S; ++i) g[i] = 0.f;
+    const size_t slot = (size_t)(6 + S) * n;
+    for (int v = 0; v < n_views; ++v) {
+        const float *Bv = B + v * slot;
+        const float a = Bv[(size_t)ch * n + k], s = Bv[(size_t)(3 + ch) * n + k];
+        if (a == 0.f && s == 0.f) continue;
+        float b[GS2_MAX_SH];
+        for (int i = 0; i < S; ++i) b[i] = Bv[(size_t)(6 + i) * n + k];
+        for (int i = 0; i < S; ++i) {
+            g[i] += a * b[i];
+            for (int j = 0; j < S; ++j) H[i * S + j] += s * b[i] * b[j];
+        }
+    }
+    const int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x);
+    if (st == 1 && nfail) atomicAdd(nfail, 1);
+    for (int i = 0; i < S; ++i) step[(size_t)(ch * S + i) * n + k] = x[i];
+}
+
+cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
+                         const gs2_config &cfg, void *step, int32_t *n_failed, cudaStream_t st) {
+    const int n = sc.n;
+    if (n == 0) return cudaSuccess;
+    const float *B = (const float *)blocks;
+    float *s = (float *)step;
+    const int g = (n + 255) / 256;
+    switch (group) {
+    case GS2_POS: k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, s, n_failed); break;
+    case GS2_ROT: k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, s, n_failed); break;
+    case GS2_SCALE:
+        k_solve_scale<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.near_z,
+                                         cfg.scale_trust, s, n_failed);
+        break;
+    case GS2_OPACITY:
+        k_solve_opacity<<<g, 256, 0, st>>>(sc, B, cfg.damping_mu0, cfg.damping_tries, cfg.barrier_alpha,
+                                           cfg.frac_to_boundary, s, n_failed);
+        break;
+    default:
+        k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries, s,
+                                                          n_failed);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ apply
+__global__ void k_apply(int group, DevScene sc, DevCam pr, const float *__restrict__ step, float scale_min) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    float *mean = const_cast<float *>(sc.mean), *quat = const_cast<float *>(sc.quat);
+    float *scale = const_cast<float *>(sc.scale), *op = const_cast<float *>(sc.opacity);
+    float *sh = const_cast<float *>(sc.sh);
+    if (group == GS2_POS) {
+        for (int i = 0; i < 3; ++i) mean[(size_t)i * n + k] += step[(size_t)i * n + k];
+    } else if (group == GS2_ROT) {
+        const float p[3] = {mean[k], mean[n + k], mean[2 * n + k]};
+        float a[3];
+        unit_dir(pr, p, a);
+        const float th = step[k];
+        const float cw = cosf(0.5f * th), sw = sinf(0.5f * th);
+        const float q0 = quat[k], q1 = quat[n + k], q2 = quat[2 * n + k], q3 = quat[3 * n + k];
+        const float adv = a[0] * q1 + a[1] * q2 + a[2] * q3;
+        const float axv[3] = {a[1] * q3 - a[2] * q2, a[2] * q1 - a[0] * q3, a[0] * q2 - a[1] * q1};
+        float qn[4];
+        qn[0] = cw * q0 - sw * adv;
+        qn[1] = cw * q1 + sw * (q0 * a[0] + axv[0]);
+        qn[2] = cw * q2 + sw * (q0 * a[1] + axv[1]);
+        qn[3] = cw * q3 + sw * (q0 * a[2] + axv[2]);
+        const float in = rsqrtf(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        for (int i = 0; i < 4; ++i) quat[(size_t)i * n + k] = qn[i] * in;
+    } else if (group == GS2_SCALE) {
+        for (int i = 0; i < 3; ++i) scale[(size_t)i * n + k] = fmaxf(scale[(size_t)i * n + k] + step[(size_t)i * n + k], scale_min);
+    } else if (group == GS2_OPACITY) {
+        op[k] += step[k];
+    } else {
+        for (int i = 0; i < 3 * sc.S; ++i) sh[(size_t)i * n + k] += step[(size_t)i * n + k];
+    }
+}
+
+cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
+                         const gs2_config &cfg, cudaStream_t st) {
+    if (sc.n == 0) return cudaSuccess;
+    k_apply<<<(sc.n + 255) / 256, 256, 0, st>>>(group, sc, primary, (const float *)step, cfg.scale_min);
+    return cudaGetLastError();
+}

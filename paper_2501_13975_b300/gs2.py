@@ -1,0 +1,341 @@
+"""ctypes binding of libgs2.so (include/gs2.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; PyTorch only
+provides device memory and the stream. Importing this module raises if the
+compiled library is missing (build it with ``python -m
+paper_2501_13975_b300.build``); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgs2.so")
+
+POS, ROT, SCALE, OPACITY, COLOR = 0, 1, 2, 3, 4
+GROUPS = (POS, ROT, SCALE, OPACITY, COLOR)
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_CUDA", 4: "ERR_OOM", 5: "ERR_NONFINITE",
+          6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED", 8: "ERR_CAPACITY"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libgs2.so not found at {LIB_PATH}; build it with `python -m paper_2501_13975_b300.build`")
+
+_lib = C.CDLL(LIB_PATH)
+
+_vp = C.c_void_p
+
+
+class Scene_(C.Structure):
+    _fields_ = [("n", C.c_int32), ("sh_degree", C.c_int32), ("mean", _vp), ("quat", _vp), ("scale", _vp),
+                ("opacity", _vp), ("sh", _vp)]
+
+
+class Camera_(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("viewmat", C.c_float * 12)]
+
+
+class Config_(C.Structure):
+    _fields_ = [("lambda_ssim", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("t_min", C.c_float), ("lowpass", C.c_float), ("near_z", C.c_float),
+                ("barrier_alpha", C.c_float), ("frac_to_boundary", C.c_float), ("damping_mu0", C.c_float),
+                ("damping_tries", C.c_int32), ("scale_min", C.c_float), ("scale_trust", C.c_float),
+                ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
+                ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+_sigs = {
+    "gs2_config_default": (None, [C.POINTER(Config_)]),
+    "gs2_create": (C.c_int, [C.POINTER(_vp), C.POINTER(Config_), C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                             C.c_int64]),
+    "gs2_destroy": (C.c_int, [_vp]),
+    "gs2_last_error": (C.c_char_p, [_vp]),
+    "gs2_set_config": (C.c_int, [_vp, C.POINTER(Config_)]),
+    "gs2_check": (C.c_int, [_vp, _vp]),
+    "gs2_proj_bytes": (C.c_size_t, [C.c_int64]),
+    "gs2_raster_state_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "gs2_blocks_bytes": (C.c_size_t, [C.c_int, C.c_int64, C.c_int32, C.c_int32]),
+    "gs2_step_bytes": (C.c_size_t, [C.c_int, C.c_int64, C.c_int32]),
+    "gs2_project": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), _vp, _vp]),
+    "gs2_raster_fwd": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), _vp, _vp, _vp, _vp]),
+    "gs2_loss_derivs": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
+    "gs2_accum_newton_blocks": (C.c_int, [_vp, C.c_int, C.POINTER(Scene_), C.POINTER(Camera_), C.POINTER(Camera_),
+                                          _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp, _vp]),
+    "gs2_solve_step": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), C.POINTER(Camera_), _vp, _vp,
+                                 _vp]),
+    "gs2_apply_step": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(Scene_), C.POINTER(Camera_), _vp]),
+    "gs2_downsample": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp]),
+    "gs2_camera_downsample": (None, [C.POINTER(Camera_), C.c_int32, C.POINTER(Camera_)]),
+    "gs2_bounding_sphere": (C.c_int, [_vp, C.POINTER(Scene_), _vp, _vp]),
+    "gs2_camera_knn": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32, _vp]),
+    "gs2_sweep": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
+                            C.c_int32, _vp, _vp, _vp]),
+    "gs2_debug_tiles": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
+    "gs2_debug_keys": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+    "gs2_debug_proj": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+class GS2Error(RuntimeError):
+    pass
+
+
+def default_config(**kw) -> dict:
+    c = Config_()
+    _lib.gs2_config_default(C.byref(c))
+    d = {k: getattr(c, k) for k, _ in Config_._fields_}
+    for k, v in kw.items():
+        if k not in d:
+            raise KeyError(k)
+        d[k] = v
+    return d
+
+
+def _config_struct(cfg: dict | None) -> Config_:
+    d = default_config(**(cfg or {}))
+    c = Config_()
+    for k, _ in Config_._fields_:
+        setattr(c, k, d[k])
+    return c
+
+
+def camera_struct(cam) -> Camera_:
+    c = Camera_()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    vm = np.asarray(cam.viewmat, np.float32).reshape(-1)
+    for i in range(12):
+        c.viewmat[i] = float(vm[i])
+    return c
+
+
+def camera_downsample(cam, f: int) -> Camera_:
+    out = Camera_()
+    _lib.gs2_camera_downsample(C.byref(camera_struct(cam)), int(f), C.byref(out))
+    return out
+
+
+@dataclasses.dataclass
+class DeviceScene:
+    """Scene parameters as CUDA tensors in the library's planar layout."""
+    mean: torch.Tensor      # (3, n)
+    quat: torch.Tensor      # (4, n)
+    scale: torch.Tensor     # (3, n)
+    opacity: torch.Tensor   # (n,)
+    sh: torch.Tensor        # (3, S, n)
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[1])
+
+    @staticmethod
+    def from_host(scene, device="cuda") -> "DeviceScene":
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device)
+        return DeviceScene(t(scene.mean), t(scene.quat), t(scene.scale), t(scene.opacity), t(scene.sh),
+                           int(scene.sh_degree))
+
+    def to_host(self):
+        from . import synth
+        return synth.Scene(self.mean.cpu().numpy(), self.quat.cpu().numpy(), self.scale.cpu().numpy(),
+                           self.opacity.cpu().numpy(), self.sh.cpu().numpy(), self.sh_degree)
+
+    def clone(self) -> "DeviceScene":
+        return DeviceScene(self.mean.clone(), self.quat.clone(), self.scale.clone(), self.opacity.clone(),
+                           self.sh.clone(), self.sh_degree)
+
+    def struct(self) -> Scene_:
+        for t in (self.mean, self.quat, self.scale, self.opacity, self.sh):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        return Scene_(self.n, self.sh_degree, self.mean.data_ptr(), self.quat.data_ptr(), self.scale.data_ptr(),
+                      self.opacity.data_ptr(), self.sh.data_ptr())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def sh_count(degree: int) -> int:
+    return (degree + 1) ** 2
+
+
+class Context:
+    """Owns a gs2_ctx (library scratch) on the current CUDA device."""
+
+    def __init__(self, max_gaussians: int, max_width: int, max_height: int, max_sh_degree: int = 3,
+                 max_pairs: int = 0, config: dict | None = None):
+        self.config = default_config(**(config or {}))
+        self._cfg = _config_struct(self.config)
+        h = _vp()
+        st = _lib.gs2_create(C.byref(h), C.byref(self._cfg), int(max_gaussians), int(max_width), int(max_height),
+                             int(max_sh_degree), int(max_pairs))
+        if st != 0:
+            raise GS2Error(f"gs2_create failed: {STATUS.get(st, st)}")
+        self.h = h
+        self.max_sh_degree = max_sh_degree
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.gs2_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ok(self, st, what):
+        if st != 0:
+            msg = _lib.gs2_last_error(self.h).decode() if self.h else ""
+            raise GS2Error(f"{what}: {STATUS.get(st, st)} {msg}")
+
+    def set_config(self, **kw):
+        self.config = default_config(**{**self.config, **kw})
+        self._cfg = _config_struct(self.config)
+        self._ok(_lib.gs2_set_config(self.h, C.byref(self._cfg)), "gs2_set_config")
+
+    def check(self, stream=None):
+        st = _lib.gs2_check(self.h, _stream(stream))
+        self._ok(st, "device status")
+
+    # ---------------------------------------------------------------- buffers
+    @staticmethod
+    def empty_bytes(nbytes: int, device="cuda"):
+        return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+    def proj_buffer(self, n):
+        return self.empty_bytes(_lib.gs2_proj_bytes(int(n)))
+
+    def raster_state_buffer(self, w, h):
+        return self.empty_bytes(_lib.gs2_raster_state_bytes(int(w), int(h)))
+
+    def blocks_buffer(self, group, n, sh_degree, n_views):
+        nb = _lib.gs2_blocks_bytes(int(group), int(n), int(sh_degree), int(n_views))
+        return torch.zeros(nb // 4, dtype=torch.float32, device="cuda")
+
+    def step_buffer(self, group, n, sh_degree):
+        nb = _lib.gs2_step_bytes(int(group), int(n), int(sh_degree))
+        return torch.zeros(max(nb // 4, 1), dtype=torch.float32, device="cuda")
+
+    # ---------------------------------------------------------------- calls
+    def project(self, scene: DeviceScene, cam, proj=None, stream=None):
+        proj = self.proj_buffer(scene.n) if proj is None else proj
+        s = scene.struct()
+        self._ok(_lib.gs2_project(self.h, C.byref(s), C.byref(camera_struct(cam)), _ptr(proj), _stream(stream)),
+                 "gs2_project")
+        return proj
+
+    def raster_fwd(self, scene: DeviceScene, cam, proj, image=None, rstate=None, stream=None):
+        W, H = int(cam.width), int(cam.height)
+        image = torch.empty((3, H, W), dtype=torch.float32, device="cuda") if image is None else image
+        rstate = self.raster_state_buffer(W, H) if rstate is None else rstate
+        s = scene.struct()
+        self._ok(_lib.gs2_raster_fwd(self.h, C.byref(s), C.byref(camera_struct(cam)), _ptr(proj), _ptr(image),
+                                     _ptr(rstate), _stream(stream)), "gs2_raster_fwd")
+        return image, rstate
+
+    def raster_state(self, rstate, w, h):
+        """(tfinal (H,W) float32, last (H,W) int32) views of a raster-state buffer."""
+        P = w * h
+        a = ((4 * P + 255) // 256) * 256
+        tf = rstate[: 4 * P].view(torch.float32).view(h, w)
+        last = rstate[a: a + 4 * P].view(torch.int32).view(h, w)
+        return tf, last
+
+    def loss_derivs(self, image, target, loss=None, stream=None):
+        _, H, W = image.shape
+        e = torch.empty_like(image)
+        h = torch.empty_like(image)
+        self._ok(_lib.gs2_loss_derivs(self.h, _ptr(image), _ptr(target), W, H, _ptr(e), _ptr(h), _ptr(loss),
+                                      _stream(stream)), "gs2_loss_derivs")
+        return e, h
+
+    def accum(self, group, scene: DeviceScene, view, primary, proj, rstate, image, target, view_slot, blocks,
+              loss=None, stream=None):
+        s = scene.struct()
+        self._ok(_lib.gs2_accum_newton_blocks(self.h, int(group), C.byref(s), C.byref(camera_struct(view)),
+                                              C.byref(camera_struct(primary)), _ptr(proj), _ptr(rstate),
+                                              _ptr(image), _ptr(target), int(view_slot), _ptr(blocks), _ptr(loss),
+                                              _stream(stream)), "gs2_accum_newton_blocks")
+
+    def solve(self, group, blocks, n_views, scene: DeviceScene, primary, step=None, n_failed=None, stream=None):
+        step = self.step_buffer(group, scene.n, scene.sh_degree) if step is None else step
+        s = scene.struct()
+        self._ok(_lib.gs2_solve_step(self.h, int(group), _ptr(blocks), int(n_views), C.byref(s),
+                                     C.byref(camera_struct(primary)), _ptr(step), _ptr(n_failed), _stream(stream)),
+                 "gs2_solve_step")
+        return step
+
+    def apply(self, group, step, scene: DeviceScene, primary, stream=None):
+        s = scene.struct()
+        self._ok(_lib.gs2_apply_step(self.h, int(group), _ptr(step), C.byref(s), C.byref(camera_struct(primary)),
+                                     _stream(stream)), "gs2_apply_step")
+
+    def downsample(self, img, f, stream=None):
+        _, H, W = img.shape
+        out = torch.empty((3, H // f, W // f), dtype=torch.float32, device="cuda")
+        self._ok(_lib.gs2_downsample(self.h, _ptr(img), W, H, int(f), _ptr(out), _stream(stream)), "gs2_downsample")
+        return out
+
+    def bounding_sphere(self, scene: DeviceScene, stream=None):
+        out = torch.empty(4, dtype=torch.float32, device="cuda")
+        s = scene.struct()
+        self._ok(_lib.gs2_bounding_sphere(self.h, C.byref(s), _ptr(out), _stream(stream)), "gs2_bounding_sphere")
+        return out
+
+    def sweep(self, scene: DeviceScene, cams, targets, knn, t, losses=None, n_failed=None, stream=None):
+        arr = (Camera_ * len(cams))(*[camera_struct(c) for c in cams])
+        tp = (_vp * len(targets))(*[_ptr(x) for x in targets])
+        kt = np.ascontiguousarray(knn, np.int32)
+        s = scene.struct()
+        self._ok(_lib.gs2_sweep(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
+                                _ptr(losses), _ptr(n_failed), _stream(stream)), "gs2_sweep")
+
+    def debug_tiles(self, w, h, capacity, stream=None):
+        tx, ty = (w + 15) // 16, (h + 15) // 16
+        ranges = torch.zeros((tx * ty, 2), dtype=torch.int32, device="cuda")
+        ids = torch.zeros(max(capacity, 1), dtype=torch.int32, device="cuda")
+        m = C.c_int64(0)
+        self._ok(_lib.gs2_debug_tiles(self.h, _ptr(ranges), _ptr(ids), int(capacity), C.byref(m), _stream(stream)),
+                 "gs2_debug_tiles")
+        return ranges, ids[: min(m.value, capacity)], m.value
+
+    @staticmethod
+    def debug_proj(proj, n, stream=None):
+        out = torch.empty((12, n), dtype=torch.float32, device="cuda")
+        keys = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert _lib.gs2_debug_proj(_ptr(proj), int(n), _ptr(out), _stream(stream)) == 0
+        assert _lib.gs2_debug_keys(_ptr(proj), int(n), _ptr(keys), _stream(stream)) == 0
+        return out, keys
+
+
+def camera_knn(centres: np.ndarray, sphere: np.ndarray, k: int) -> np.ndarray:
+    c = np.ascontiguousarray(centres, np.float32)
+    s = np.ascontiguousarray(sphere, np.float32)
+    out = np.zeros((c.shape[0], k), np.int32)
+    st = _lib.gs2_camera_knn(c.ctypes.data_as(_vp), c.shape[0], s.ctypes.data_as(_vp), int(k),
+                             out.ctypes.data_as(_vp))
+    if st != 0:
+        raise GS2Error(f"gs2_camera_knn: {STATUS.get(st, st)}")
+    return out
