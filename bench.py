@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Newton sweeps per second of the local-Newton 3DGS hot path on one B300.
+
+A step is one sweep (Sec. 4.2 group order, Sec. 4.3 secondary targets): for
+each of the five attribute groups, render the primary view at full resolution
+and its three KNN secondaries at half resolution, accumulate the group's
+gradient/Hessian blocks, solve and apply.  The primary cycles through the
+cameras.  Default workload ("scene"): 1M Gaussians spread to radius 50, SH
+degree 3, 200 cameras 1600x1040 on a smooth trajectory; synthetic inputs,
+targets rendered from the ground-truth scene, training starts from a copy
+with perturbed means.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs2|reference]
+                    [--workload scene|object|tiny] [--no-cpu-baseline]
+
+Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle
+(the project's reference implementation of the method) on bounded samples of
+the same workload.  Multi-GPU (torchrun) runs independent replicas, one per
+GPU, each with its own scene seed; the path has no cross-GPU exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2501_13975_b300 import synth  # noqa: E402
+
+GROUP_NAMES = ("position", "rotation", "scaling", "opacity", "colour")
+PAYLOAD_FLOATS = (41, 9, 9, 2, 6)       # image-space accumulator floats per Gaussian and view
+RECORD_BYTES = 40                        # per (tile, Gaussian) pair: id (4) + pi, conic, sigma, c~ (36)
+PIXEL_BYTES = 32                         # per pixel: e, h (24) + T_final, last (8)
+
+WORKLOADS = {
+    "scene": dict(desc="1M Gaussians spread log-uniformly to radius 50, SH degree 3, 200 cameras 1600x1040 on a "
+                       "smooth trajectory; 1 primary (full res) + 3 KNN secondaries (half res) x 5 groups per sweep",
+                  n=1_000_000, cams=200, width=1600, height=1040, sh=3, max_pairs=48_000_000),
+    "object": dict(desc="100k Gaussians on a unit-sphere shell, SH degree 3, 100 cameras 800x800 on a hemisphere; "
+                        "1 primary + 3 KNN secondaries x 5 groups per sweep",
+                   n=100_000, cams=100, width=800, height=800, sh=3, max_pairs=24_000_000),
+    "tiny": dict(desc="1,000 Gaussians in [-1,1]^3, SH degree 0, 4 cameras 128x128 on a ring",
+                 n=1000, cams=4, width=128, height=128, sh=0, max_pairs=1_000_000),
+}
+
+
+def make_workload(name, seed_offset=0):
+    w = WORKLOADS[name]
+    if name == "scene":
+        gt = synth.spread_scene(seed=6 + seed_offset)
+        cams = synth.trajectory_cameras(seed=7 + seed_offset)
+    elif name == "object":
+        gt = synth.object_scene(seed=3 + seed_offset)
+        cams = synth.hemisphere_cameras()
+    else:
+        gt = synth.tiny_scene(seed=1 + seed_offset)
+        cams = synth.ring_cameras(4, 128)
+    train = synth.perturbed(gt, seed=4 + seed_offset, sd=0.02)
+    return w, gt, train, cams
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2501_13975_b300 import gs2
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w, gt_host, train_host, cams = make_workload(args.workload, seed_offset=rank)
+    ncam = len(cams)
+    W, H = w["width"], w["height"]
+    ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"])
+    stream = torch.cuda.current_stream()
+
+    # targets: ground-truth renders of every camera (resident in HBM)
+    gt = gs2.DeviceScene.from_host(gt_host)
+    targets = []
+    proj = ctx.proj_buffer(w["n"])
+    for c in cams:
+        ctx.project(gt, c, proj)
+        img, _ = ctx.raster_fwd(gt, c, proj)
+        targets.append(img.clone())
+    del gt
+    torch.cuda.synchronize()
+    ctx.check()
+
+    scene = gs2.DeviceScene.from_host(train_host)
+    sphere = ctx.bounding_sphere(scene).cpu().numpy()
+    centres = np.stack([c.center() for c in cams]).astype(np.float32)
+    knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
+    losses = torch.zeros(10, dtype=torch.float64, device=dev)
+    nfail = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def sweep(i, tg=targets):
+        ctx.sweep(scene, cams, tg, knn, i % ncam, losses, nfail)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for i in range(args.warmup):
+        sweep(i)
+    torch.cuda.synchronize()
+    ctx.check()
+
+    # ---------------- device-resident timed region (profiled accumulation launches)
+    ctx.profile(True)
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = gs2.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        sweep(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = gs2.launch_count() - l0
+    clk = clocks.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check()
+
+    # ---------------- end to end through the public API with host buffers
+    pinned = [t.cpu().pin_memory() for t in targets]
+    up = [torch.empty_like(targets[0]) for _ in range(1 + ctx.config["knn_k"])]
+    host_losses = torch.zeros(10, dtype=torch.float64).pin_memory()
+    host_nfail = torch.zeros(1, dtype=torch.int32).pin_memory()
+    h2d = sum(u.numel() * 4 for u in up)
+    d2h = host_losses.numel() * 8 + host_nfail.numel() * 4
+
+    def e2e_step(i):
+        t = i % ncam
+        views = [t] + [int(v) for v in knn[t] if v >= 0]
+        tg = list(targets)
+        for j, v in enumerate(views):
+            up[j].copy_(pinned[v], non_blocking=True)
+            tg[v] = up[j]
+        ctx.sweep(scene, cams, tg, knn, t, losses, nfail)
+        host_losses.copy_(losses, non_blocking=True)
+        host_nfail.copy_(nfail, non_blocking=True)
+
+    for i in range(args.warmup):
+        e2e_step(1000 + i)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        e2e_step(1000 + args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    ctx.check()
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    # ---------------- roofline of the accumulation kernel (algorithmic bytes)
+    peak, peak_kind = load_peaks()
+    accum_ms = float(prof["accum_ms"].sum())
+    n_acc = int(prof["accum_launches"].sum())
+    alg_bytes = 0.0
+    for g in range(5):
+        alg_bytes += (PIXEL_BYTES * float(prof["pixels"][g]) + RECORD_BYTES * float(prof["pairs"][g])
+                      + 8.0 * PAYLOAD_FLOATS[g] * float(prof["visible"][g]))
+    achieved = alg_bytes / (accum_ms * 1e-3) / 1e9 if accum_ms > 0 else 0.0
+    per_launch_bytes = alg_bytes / max(n_acc, 1)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "accum_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            td = json.load(f)
+        if td.get("workload") == args.workload and td.get("kernel_rev") == KERNEL_REV:
+            traffic = td.get("bytes_per_launch")
+    roofline = {"kernel": "k_accum (all groups)", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": round(per_launch_bytes), "launches": n_acc,
+                "avg_launch_ms": round(accum_ms / max(n_acc, 1), 4),
+                "share_of_step": round(accum_ms / ms, 4) if ms > 0 else None,
+                "pairs_per_sweep": int(prof["pairs"].sum()) // max(args.steps, 1),
+                "visible_per_binning": int(prof["visible"].sum()) // max(int(prof["binnings"].sum()), 1)}
+    value = world * args.steps / (ms * 1e-3)
+    result = {
+        "metric": "Newton sweeps/s (1 primary + 3 secondaries, 5 attribute groups)",
+        "value": round(value, 4), "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {w['desc']}", "gaussians": w["n"], "cameras": ncam,
+                   "width": W, "height": H, "sh_degree": w["sh"], "knn_k": ctx.config["knn_k"],
+                   "downsample": ctx.config["downsample"], "lambda_ssim": ctx.config["lambda_ssim"],
+                   "l2": "inputs larger than L2 (scene parameters and targets exceed 126 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": round(world * args.steps / (ms_e2e * 1e-3), 4), "unit": "sweeps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "accumulate_ms_by_group": {GROUP_NAMES[g]: round(float(prof["accum_ms"][g]) / max(args.steps, 1), 3)
+                                   for g in range(5)},
+        "n_failed_total": int(nfail.item()),
+        "primary_loss_last": [round(float(x), 6) for x in host_losses[:2]],
+    }
+    return result, (w, train_host, cams)
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+
+def oracle_group_pass_seconds(O, scene_h, cam, group, crop, ocfg, target_full):
+    """Time one oracle group pass (render + loss derivatives + block assembly)
+    on a crop x crop window in the image centre."""
+    cw = synth.Camera(crop, crop, cam.fx, cam.fy, cam.cx - (cam.width // 2 - crop // 2),
+                      cam.cy - (cam.height // 2 - crop // 2), cam.viewmat)
+    y0, x0 = cam.height // 2 - crop // 2, cam.width // 2 - crop // 2
+    tgt = target_full[:, y0:y0 + crop, x0:x0 + crop]
+    t0 = time.perf_counter()
+    img = O.render(scene_h, cw, ocfg)["image"]
+    L = O.loss(img, tgt, ocfg)
+    O.accum(group, scene_h, cw, cam, L["e"], L["h"], ocfg)
+    return time.perf_counter() - t0
+
+
+def subset_scene(scene, frac, seed=12):
+    """Random subset of the Gaussians (the oracle's costs are linear in N)."""
+    n = scene.n
+    m = max(1, int(round(frac * n)))
+    idx = np.sort(np.random.default_rng(seed).choice(n, m, replace=False))
+    return synth.Scene(scene.mean[:, idx], scene.quat[:, idx], scene.scale[:, idx], scene.opacity[idx],
+                       scene.sh[:, :, idx], scene.sh_degree)
+
+
+def oracle_sweep_estimate(w, train_host, cams, group_list, small=1, big=12, frac=0.05):
+    """Seconds per sweep of the oracle, extrapolated from timed samples: per
+    group, a 1x1 crop (fixed cost: projecting every Gaussian as jets) and a
+    big x big crop (adds the per-pixel cost), both on a random fraction `frac`
+    of the Gaussians and scaled by 1/frac (brute-force compositing and the jet
+    projection are linear in the Gaussian count); a sweep = sum over groups and
+    the 4 views of fixed + per-pixel x pixels."""
+    from oracle import oracle as O
+    O.build()
+    ocfg = O.default_config()
+    scene_h = O.scene_handle(subset_scene(train_host, frac) if frac < 1 else train_host)
+    cam = cams[0]
+    tgt = synth.procedural_targets(1, cam.width, cam.height, seed=11)[0]
+    P_full = cam.width * cam.height
+    P_half = (cam.width // 2) * (cam.height // 2)
+    per_group = {}
+    t_start = time.perf_counter()
+    for g in group_list:
+        f = oracle_group_pass_seconds(O, scene_h, cam, g, small, ocfg, tgt)
+        b = oracle_group_pass_seconds(O, scene_h, cam, g, big, ocfg, tgt)
+        per_px = max(b - f, 0.0) / (big * big - small * small)
+        per_group[g] = (f / frac, per_px / frac)
+    spent = time.perf_counter() - t_start
+    return per_group, spent, P_full, P_half
+
+
+def sweep_seconds(per_group, P_full, P_half, K=3):
+    tot = 0.0
+    known = list(per_group.values())
+    for g in range(5):
+        f, px = per_group.get(g, (statistics.mean(x[0] for x in known), statistics.mean(x[1] for x in known)))
+        tot += (f + px * P_full) + K * (f + px * P_half)
+    return tot
+
+
+def cpu_baseline(args, w, train_host, cams):
+    per_group, spent, P_full, P_half = oracle_sweep_estimate(w, train_host, cams, range(5),
+                                                             big=args.cpu_crop)
+    t = sweep_seconds(per_group, P_full, P_half)
+    return {"value": 1.0 / t, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"FP64 oracle (brute-force compositing, jet-derived blocks), every group on 1x1 and "
+                       f"{args.cpu_crop}x{args.cpu_crop} centre crops of the primary view of the "
+                       f"{args.workload} workload with a random 5% of its Gaussians; costs scaled by 20 "
+                       f"(linear in N) and extrapolated to 1 full-res + 3 half-res views x 5 groups; "
+                       f"{spent:.1f} s of CPU work"),
+            "seconds_per_sweep": round(t, 1)}
+
+
+def run_reference(args):
+    w, gt_host, train_host, cams = make_workload(args.workload)
+    samples = {}
+    from oracle import oracle as O  # noqa: F401
+    steps = []
+    t0 = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        g = i % 5
+        pg, spent, P_full, P_half = oracle_sweep_estimate(w, train_host, cams, [g], big=args.ref_crop)
+        if i >= args.warmup:
+            samples.setdefault(g, []).append(pg[g])
+            steps.append(spent)
+    per_group = {g: (statistics.mean(x[0] for x in v), statistics.mean(x[1] for x in v)) for g, v in samples.items()}
+    t = sweep_seconds(per_group, P_full, P_half)
+    value = 1.0 / t
+    res = {"impl": "reference", "metric": "Newton sweeps/s (1 primary + 3 secondaries, 5 attribute groups)",
+           "value": value, "unit": "sweeps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * t, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {w['desc']}", "gaussians": w["n"], "cameras": len(cams),
+                      "width": w["width"], "height": w["height"], "sh_degree": w["sh"]},
+           "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": (f"each step: one group (cycling) on 1x1 and {args.ref_crop}x{args.ref_crop} "
+                                       f"centre crops of the primary view with a random 5% of the Gaussians, "
+                                       f"costs scaled by 20 and extrapolated to a full sweep; "
+                                       f"{time.perf_counter() - t0:.1f} s total")},
+           "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return res
+
+
+KERNEL_REV = "accum-v1"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gs2", choices=["gs2", "reference"])
+    ap.add_argument("--workload", default="scene", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-crop", type=int, default=12)
+    ap.add_argument("--ref-crop", type=int, default=8)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "gs2" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    result, (w, train_host, cams) = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(args, w, train_host, cams)
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,9 @@ typedef struct {
     int32_t damping_tries;  /* extra x10 damping attempts (6) */
     float scale_min;        /* floor of any scale (1e-7) */
     float scale_trust;      /* scale update bounded to [s/k, k s] (2.0) */
+    float trust_pos;        /* |dp| <= trust_pos * max(s) (3.0) */
+    float trust_rot;        /* |theta| <= trust_rot (pi/4) */
+    float trust_color;      /* per-channel SH step norm <= trust_color (2 sqrt(pi)) */
     float ssim_c1, ssim_c2; /* 0.01^2, 0.03^2 */
     float ssim_sigma;       /* Gaussian window sigma (1.5) */
     int32_t ssim_radius;    /* window radius (5: 11x11); only 5 is supported */
@@ -220,6 +223,19 @@ gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const float *spher
 gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                      const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
                      int32_t *n_failed, gs2_stream stream);
+
+/* Instrumentation.
+ * gs2_launch_count: kernels launched by this library in this process so far.
+ * gs2_profile(ctx, 1): from now on record CUDA events around every
+ *   accumulation kernel launch (bounded pool of 512) and count, per group slot
+ *   of gs2_sweep, the (tile, Gaussian) pairs, visible Gaussians, binnings and
+ *   pixels (device-side counters, no host synchronisation); resets totals.
+ *   gs2_profile(ctx, 0) stops.  Synchronises the device.
+ * gs2_profile_read: per group (host arrays [5], stats [5][4]: pairs, visible
+ *   Gaussians, binnings, pixels) after synchronising the device. */
+uint64_t gs2_launch_count(void);
+gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable);
+gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launches, uint64_t *stats);
 
 /* Introspection for tests: copies the current tile ranges (device uint32
  * [ntiles][2]) and sorted Gaussian ids (device uint32, up to capacity) and

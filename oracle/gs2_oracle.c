@@ -70,7 +70,27 @@ typedef struct {
     int knn_k;
     int downsample;
     double scale_trust;
+    double trust_pos;   /* |dp| <= trust_pos * max(s) */
+    double trust_rot;   /* |theta| <= trust_rot */
+    double trust_color; /* |dc_ch| <= trust_color (SH coefficient norm per channel) */
 } orc_config;
+
+/* Trust radii (reading; the paper fixes step size 1 and gives no safeguard):
+ * a Jacobi step of a Gaussian seen by a handful of pixels is exact for its own
+ * footprint but can be arbitrarily large; the step is scaled down to the
+ * radius when it exceeds it, keeping its direction.  Non-finite steps become
+ * zero and count as failed. */
+static int trust_scale(int N, double *x, double radius) {
+    double nn = 0;
+    for (int i = 0; i < N; ++i) nn += x[i] * x[i];
+    nn = sqrt(nn);
+    if (!(nn == nn) || isinf(nn)) {
+        for (int i = 0; i < N; ++i) x[i] = 0.0;
+        return 1;
+    }
+    if (nn > radius) for (int i = 0; i < N; ++i) x[i] *= radius / nn;
+    return 0;
+}
 
 int orc_sh_count(int degree) { return (degree + 1) * (degree + 1); }
 
@@ -1157,6 +1177,7 @@ int orc_solve(int group, const orc_scene *sc, const orc_camera *primary, const o
                 unpack_sym(S, Hb + ((size_t)ch * NH) * n + k, n, Hf);
                 for (int i = 0; i < S; ++i) gv[i] = g[((size_t)ch * S + i) * n + k];
                 int st = damped_solve(S, Hf, gv, cfg, x, inf);
+                if (st == 0 && trust_scale(S, x, cfg->trust_color)) st = 1;
                 for (int i = 0; i < S; ++i) step[((size_t)ch * S + i) * n + k] = x[i];
                 if (status) status[ch * n + k] = st;
                 if (info) for (int i = 0; i < 3; ++i) info[((size_t)ch * 3 + i) * n + k] = inf[i];
@@ -1195,11 +1216,14 @@ int orc_solve(int group, const orc_scene *sc, const orc_camera *primary, const o
                 }
             }
             st = damped_solve(2, Hv, gv, cfg, dv, inf);
+            double smax = fmax(s[0], fmax(s[1], s[2]));
+            if (st == 0 && trust_scale(2, dv, cfg->trust_pos * smax)) st = 1;
             for (int i = 0; i < 3; ++i) step[i * n + k] = U[i][0] * dv[0] + U[i][1] * dv[1];
             if (cond && st == 0) cnd = cond_estimate(2, Hv, inf[0] * 0.5 * (fabs(Hv[0]) + fabs(Hv[3])));
         } else if (group == G_ROT) {
             double Hf[1] = {Hb[k]}, gv[1] = {g[k]}, x[1];
             st = damped_solve(1, Hf, gv, cfg, x, inf);
+            if (st == 0 && trust_scale(1, x, cfg->trust_rot)) st = 1;
             step[k] = x[0];
             cnd = 1.0;
         } else if (group == G_SCALE) {
@@ -1226,6 +1250,7 @@ int orc_solve(int group, const orc_scene *sc, const orc_camera *primary, const o
                     }
                 }
                 st = damped_solve(2, Hl, gl, cfg, dl, inf);
+                if (st == 0 && trust_scale(2, dl, INFINITY)) st = 1;
                 /* positivity of s (reading; the paper gives no rule): the update
                  * stays within [s / kappa, kappa s], kappa = scale_trust, i.e. a
                  * bounded step in log-scale (cf. the opacity fraction-to-boundary) */
@@ -1264,6 +1289,7 @@ int orc_solve(int group, const orc_scene *sc, const orc_camera *primary, const o
                 gv[0] += a * (-1.0 / sg + 1.0 / (1.0 - sg));
                 Hf[0] += a * (1.0 / (sg * sg) + 1.0 / ((1.0 - sg) * (1.0 - sg)));
                 st = damped_solve(1, Hf, gv, cfg, x, inf);
+                if (st == 0 && trust_scale(1, x, INFINITY)) st = 1;
             }
             double tau = cfg->frac_to_boundary;
             double lo = sg - tau * sg, hi = sg + tau * (1.0 - sg);

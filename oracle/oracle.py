@@ -45,7 +45,8 @@ class OrcConfig(C.Structure):
                 ("damping_mu0", C.c_double), ("damping_tries", C.c_int), ("scale_min", C.c_double),
                 ("ssim_c1", C.c_double), ("ssim_c2", C.c_double), ("ssim_sigma", C.c_double),
                 ("ssim_radius", C.c_int), ("knn_k", C.c_int), ("downsample", C.c_int),
-                ("scale_trust", C.c_double)]
+                ("scale_trust", C.c_double), ("trust_pos", C.c_double), ("trust_rot", C.c_double),
+                ("trust_color", C.c_double)]
 
 
 def default_config(**kw) -> dict:
@@ -53,7 +54,8 @@ def default_config(**kw) -> dict:
     cfg = dict(lambda_ssim=0.2, alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, lowpass=0.3,
                near_z=0.2, barrier_alpha=1e-6, frac_to_boundary=0.99, damping_mu0=1.0,
                damping_tries=6, scale_min=1e-7, ssim_c1=0.01 ** 2, ssim_c2=0.03 ** 2, ssim_sigma=1.5,
-               ssim_radius=5, knn_k=3, downsample=2, scale_trust=2.0)
+               ssim_radius=5, knn_k=3, downsample=2, scale_trust=2.0,
+               trust_pos=3.0, trust_rot=0.7853981633974483, trust_color=3.5449077018110318)
     cfg.update(kw)
     return cfg
 

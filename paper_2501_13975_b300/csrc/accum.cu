@@ -553,6 +553,11 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
     const int n = sc.n;
     dim3 grid(ctx->tiles_x, ctx->tiles_y);
     const uint32_t *ids = ctx->vals[ctx->sorted];
+    const bool prof = ctx->prof_on && ctx->prof_n < 512;
+    if (prof) {
+        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
+        ctx->prof_group[ctx->prof_n] = group;
+    }
 #define ACC(G)                                                                                                    \
     k_accum<G><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h,   \
                                               ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, ctx->zbuf, n)
@@ -564,6 +569,11 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
     default: ACC(GS2_COLOR); break;
     }
 #undef ACC
+    if (prof) {
+        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], st);
+        ctx->prof_n++;
+    }
+    GS2_COUNT_LAUNCH(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || n == 0) return e;
     const int eg = (n + 255) / 256;

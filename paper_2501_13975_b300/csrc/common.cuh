@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "../../include/gs2.h"
@@ -135,14 +136,28 @@ struct gs2_ctx {
     void *sw_step;
     size_t sw_blocks_bytes, sw_step_bytes;
     uint32_t *d_status;
+    // opt-in profile of the accumulation kernel: CUDA events around every launch
+    // and per-group pair / visible-Gaussian totals counted on the device
+    int prof_on;
+    int prof_n;                  // events used in the pool
+    cudaEvent_t prof_ev[2 * 512];
+    int prof_group[512];
+    unsigned long long *d_stats; // [5][4]: pairs, visible Gaussians, binnings, (unused)
+    int stat_slot;               // group slot the binning statistics go to
+    unsigned long long h_pixels[5];
     std::string err;
 };
+
+// number of kernels this library has launched (host-side count)
+extern std::atomic<unsigned long long> g_gs2_launches;
+#define GS2_COUNT_LAUNCH(k) (g_gs2_launches.fetch_add((k), std::memory_order_relaxed))
 
 // --------------------------------------------------------------------------
 // launchers implemented in the .cu files (return a CUDA error code)
 cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
                            int tiles_y, cudaStream_t st);
-cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st);
+cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
+                            unsigned long long *stats);
 cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
                           RasterView rv, cudaStream_t st);
 cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,

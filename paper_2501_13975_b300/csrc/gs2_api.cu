@@ -28,6 +28,8 @@
 
 static const int SORT_BLOCKS = 148 * 4;
 
+std::atomic<unsigned long long> g_gs2_launches{0};
+
 extern "C" void gs2_config_default(gs2_config *c) {
     if (!c) return;
     c->lambda_ssim = 0.2f;
@@ -42,6 +44,9 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->damping_tries = 6;
     c->scale_min = 1e-7f;
     c->scale_trust = 2.0f;
+    c->trust_pos = 3.0f;
+    c->trust_rot = 0.78539816339744831f;
+    c->trust_color = 3.5449077018110318f;
     c->ssim_c1 = 1e-4f;
     c->ssim_c2 = 9e-4f;
     c->ssim_sigma = 1.5f;
@@ -62,6 +67,7 @@ static bool cfg_ok(const gs2_config *c, std::string &err) {
     if (c->damping_tries < 0 || c->damping_tries > 30 || !(c->damping_mu0 >= 0.f)) { err = "bad damping"; return false; }
     if (!(c->scale_trust > 1.f) || !(c->scale_min > 0.f)) { err = "scale_trust > 1 and scale_min > 0 required"; return false; }
     if (!(c->frac_to_boundary > 0.f && c->frac_to_boundary < 1.f)) { err = "frac_to_boundary in (0,1)"; return false; }
+    if (!(c->trust_pos > 0.f && c->trust_rot > 0.f && c->trust_color > 0.f)) { err = "trust radii must be > 0"; return false; }
     return true;
 }
 
@@ -96,9 +102,12 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
-                    c->sw_step, c->d_status};
+                    c->sw_step, c->d_status, c->d_stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->prof_on >= 0 && c->prof_ev[0])
+        for (int i = 0; i < 2 * 512; ++i)
+            if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
 }
 
 extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t max_n, int32_t max_w, int32_t max_h,
@@ -158,9 +167,11 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     c->sw_step_bytes = sizeof(float) * 3 * (size_t)S * max_n;
     A(&c->sw_step, c->sw_step_bytes);
     A((void **)&c->d_status, sizeof(uint32_t) * 4);
+    A((void **)&c->d_stats, sizeof(unsigned long long) * 5 * 4);
     if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(float) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 20) == cudaSuccess;
     if (!ok) {
         free_ctx(c);
         delete c;
@@ -257,7 +268,9 @@ static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const vo
     ctx->tiles_x = (cam->width + GS2_TILE - 1) / GS2_TILE;
     ctx->tiles_y = (cam->height + GS2_TILE - 1) / GS2_TILE;
     ProjView pv = proj_view(const_cast<void *>(proj), n);
-    RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st));
+    RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st,
+                                  ctx->prof_on ? ctx->d_stats + 4 * ctx->stat_slot : nullptr));
+    if (ctx->prof_on) ctx->h_pixels[ctx->stat_slot] += (unsigned long long)cam->width * cam->height;
     RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image,
                                 raster_view(rstate, cam->width, cam->height), st));
     return GS2_OK;
@@ -432,6 +445,7 @@ extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera
     }
     const gs2_camera *primary = &cams[t];
     for (int group = 0; group < 5; ++group) {
+        ctx->stat_slot = group;
         RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, blocks_bytes_impl(group, scene->n, scene->sh_degree, nv), st));
         for (int i = 0; i < nv; ++i) {
             if (vid[i] < 0) continue;
@@ -443,6 +457,46 @@ extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
                                    ctx->sw_step, n_failed, st));
         RET_CUDA(ctx, launch_apply(group, ctx->sw_step, make_devscene(scene), make_devcam(primary), ctx->cfg, st));
+    }
+    ctx->stat_slot = 0;
+    return GS2_OK;
+}
+
+extern "C" uint64_t gs2_launch_count(void) { return g_gs2_launches.load(); }
+
+extern "C" gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable) {
+    if (!ctx) return GS2_ERR_ARG;
+    if (enable && !ctx->prof_ev[0])
+        for (int i = 0; i < 2 * 512; ++i) RET_CUDA(ctx, cudaEventCreate(&ctx->prof_ev[i]));
+    RET_CUDA(ctx, cudaDeviceSynchronize());
+    ctx->prof_on = enable ? 1 : 0;
+    ctx->prof_n = 0;
+    ctx->stat_slot = 0;
+    for (int g = 0; g < 5; ++g) ctx->h_pixels[g] = 0;
+    RET_CUDA(ctx, cudaMemset(ctx->d_stats, 0, sizeof(unsigned long long) * 20));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launches, uint64_t *stats) {
+    if (!ctx || !accum_ms || !accum_launches || !stats) return GS2_ERR_ARG;
+    RET_CUDA(ctx, cudaDeviceSynchronize());
+    for (int g = 0; g < 5; ++g) {
+        accum_ms[g] = 0.0;
+        accum_launches[g] = 0;
+    }
+    for (int i = 0; i < ctx->prof_n; ++i) {
+        float ms = 0.f;
+        RET_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        accum_ms[ctx->prof_group[i]] += ms;
+        accum_launches[ctx->prof_group[i]] += 1;
+    }
+    unsigned long long h[20];
+    RET_CUDA(ctx, cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < 5; ++g) {
+        stats[4 * g + 0] = h[4 * g + 0];
+        stats[4 * g + 1] = h[4 * g + 1];
+        stats[4 * g + 2] = h[4 * g + 2];
+        stats[4 * g + 3] = ctx->h_pixels[g];
     }
     return GS2_OK;
 }

@@ -185,6 +185,7 @@ cudaError_t launch_loss(const float *image, const float *target, int w, int h, c
         const size_t P3 = 3 * P;
         int grid = (int)std::min<size_t>((P3 + 255) / 256, 148 * 16);
         k_l2<<<grid, 256, 0, st>>>(image, target, P3, scale, e, hh, loss_out);
+        GS2_COUNT_LAUNCH(1);
         return cudaGetLastError();
     }
     SsimConst K;
@@ -211,5 +212,6 @@ cudaError_t launch_loss(const float *image, const float *target, int w, int h, c
     }
     dim3 grid((w + LT_W - 1) / LT_W, (h + LT_H - 1) / LT_H);
     k_ssim<<<grid, 256, smem, st>>>(image, target, w, h, K, e, hh, loss_out);
+    GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

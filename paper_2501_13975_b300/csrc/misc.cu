@@ -22,6 +22,7 @@ cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, 
     if (n == 0) return cudaSuccess;
     const int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
     k_downsample<<<grid, 256, 0, st>>>(in, w, h, f, out);
+    GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }
 
@@ -82,5 +83,6 @@ __global__ void __launch_bounds__(1024) k_bsphere(DevScene sc, float *out) {
 
 cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t st) {
     k_bsphere<<<1, 1024, 0, st>>>(sc, out);
+    GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

@@ -121,5 +121,6 @@ cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_conf
     if (sc.n == 0) return cudaSuccess;
     k_project<<<(sc.n + 255) / 256, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x,
                                                    tiles_y);
+    GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

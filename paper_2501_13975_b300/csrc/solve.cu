@@ -12,6 +12,8 @@
 //             primary view's projected covariance), update kept in [s/k, k s]
 //   opacity:  scalar with the log barrier, fraction-to-boundary inside (0, 1)
 //   colour:   S x S per channel from the factored per-view slots
+// Trust radii (position 3 max(s), rotation pi/4, colour 2 sqrt(pi) per
+// channel) scale down over-long steps; non-finite steps become 0 (failed).
 // One thread per Gaussian (per Gaussian and channel for colour); blocks of
 // size <= 3 live in registers, the 16x16 colour factor in local memory.
 #include "common.cuh"
@@ -65,6 +67,23 @@ __device__ int damped_solve(int N, const float *H, const float *g, float mu0, in
     return 1;
 }
 
+// Trust radius: a step longer than `radius` is scaled down to it (direction
+// kept); a non-finite step becomes zero and reports failure.
+__device__ __forceinline__ bool trust_scale(int N, float *x, float radius) {
+    float nn = 0.f;
+    for (int i = 0; i < N; ++i) nn += x[i] * x[i];
+    nn = sqrtf(nn);
+    if (!isfinite(nn)) {
+        for (int i = 0; i < N; ++i) x[i] = 0.f;
+        return true;
+    }
+    if (nn > radius) {
+        const float f = radius / nn;
+        for (int i = 0; i < N; ++i) x[i] *= f;
+    }
+    return false;
+}
+
 __device__ __forceinline__ void unit_dir(const DevCam &cam, const float p[3], float r[3]) {
     r[0] = p[0] - cam.o[0];
     r[1] = p[1] - cam.o[1];
@@ -73,8 +92,8 @@ __device__ __forceinline__ void unit_dir(const DevCam &cam, const float p[3], fl
     r[0] *= in; r[1] *= in; r[2] *= in;
 }
 
-__global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries, float *step,
-                            int32_t *nfail) {
+__global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries, float trust,
+                            float *step, int32_t *nfail) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -104,17 +123,21 @@ __global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B,
         }
     }
     float dv[2];
-    const int st = damped_solve<2>(2, Hv, gv, mu0, tries, dv);
+    int st = damped_solve<2>(2, Hv, gv, mu0, tries, dv);
+    const float smax = fmaxf(sc.scale[k], fmaxf(sc.scale[n + k], sc.scale[2 * n + k]));
+    if (st == 0 && trust_scale(2, dv, trust * smax)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = ux[i] * dv[0] + uy[i] * dv[1];
 }
 
-__global__ void k_solve_scalar(int n, const float *__restrict__ B, float mu0, int tries, float *step, int32_t *nfail) {
+__global__ void k_solve_scalar(int n, const float *__restrict__ B, float mu0, int tries, float trust, float *step,
+                               int32_t *nfail) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float g = B[k], h = B[n + k];
     float x;
-    const int st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+    int st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+    if (st == 0 && trust_scale(1, &x, trust)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     step[k] = x;
 }
@@ -131,6 +154,7 @@ __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float 
         g += barrier * (-1.f / sg + 1.f / (1.f - sg));
         h += barrier * (1.f / (sg * sg) + 1.f / ((1.f - sg) * (1.f - sg)));
         st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+        if (st == 0 && trust_scale(1, &x, INFINITY)) st = 1;
     }
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     // fraction-to-boundary on the increment itself: x in [-tau sigma, tau (1 - sigma)]
@@ -222,7 +246,8 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
         }
     }
     float dl[2];
-    const int st = damped_solve<2>(2, Hl, gl, mu0, tries, dl);
+    int st = damped_solve<2>(2, Hl, gl, mu0, tries, dl);
+    if (st == 0 && trust_scale(2, dl, INFINITY)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     for (int i = 0; i < 3; ++i) {
         const float ds = Q[i][0] * dl[0] + Q[i][1] * dl[1];
@@ -232,7 +257,7 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
 }
 
 __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_views, float mu0, int tries,
-                              float *step, int32_t *nfail) {
+                              float trust, float *step, int32_t *nfail) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n, S = sc.S;
     if (idx >= 3 * n) return;
@@ -252,7 +277,8 @@ __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_vi
             for (int j = 0; j < S; ++j) H[i * S + j] += s * b[i] * b[j];
         }
     }
-    const int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x);
+    int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x);
+    if (st == 0 && trust_scale(S, x, trust)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     for (int i = 0; i < S; ++i) step[(size_t)(ch * S + i) * n + k] = x[i];
 }
@@ -265,8 +291,13 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
     float *s = (float *)step;
     const int g = (n + 255) / 256;
     switch (group) {
-    case GS2_POS: k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, s, n_failed); break;
-    case GS2_ROT: k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, s, n_failed); break;
+    case GS2_POS:
+        k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_pos, s,
+                                       n_failed);
+        break;
+    case GS2_ROT:
+        k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_rot, s, n_failed);
+        break;
     case GS2_SCALE:
         k_solve_scale<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.near_z,
                                          cfg.scale_trust, s, n_failed);
@@ -276,9 +307,10 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
                                            cfg.frac_to_boundary, s, n_failed);
         break;
     default:
-        k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries, s,
-                                                          n_failed);
+        k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,
+                                                          cfg.trust_color, s, n_failed);
     }
+    GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }
 
@@ -321,5 +353,6 @@ cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const 
                          const gs2_config &cfg, cudaStream_t st) {
     if (sc.n == 0) return cudaSuccess;
     k_apply<<<(sc.n + 255) / 256, 256, 0, st>>>(group, sc, primary, (const float *)step, cfg.scale_min);
+    GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

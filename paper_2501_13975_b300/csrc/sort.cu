@@ -81,10 +81,14 @@ __global__ void k_scan_down(const uint32_t *__restrict__ x, int n, const unsigne
 }
 
 // ---------------------------------------------------------------- emit
-__global__ void k_emit(ProjView pv, int n, int tiles_x, uint32_t cap, unsigned long long *keys, uint32_t *vals) {
+__global__ void k_emit(ProjView pv, int n, int tiles_x, uint32_t cap, unsigned long long *keys, uint32_t *vals,
+                       unsigned long long *stats) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const uint32_t cnt = pv.touched[k];
+    const uint32_t cnt = (k < n) ? pv.touched[k] : 0u;
+    if (stats) {  // visible-Gaussian count, one atomic per warp
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, cnt != 0u);
+        if ((threadIdx.x & 31) == 0 && b) atomicAdd(&stats[1], (unsigned long long)__popc(b));
+    }
     if (cnt == 0u) return;
     uint32_t off = pv.offs[k];
     const uint2 r = pv.rect[k];
@@ -202,8 +206,13 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const unsigned long lo
     }
 }
 
-__global__ void k_ranges(const unsigned long long *__restrict__ keys, const uint32_t *count, uint2 *ranges) {
+__global__ void k_ranges(const unsigned long long *__restrict__ keys, const uint32_t *count, uint2 *ranges,
+                         unsigned long long *stats) {
     const uint32_t M = count[0];
+    if (stats && blockIdx.x == 0 && threadIdx.x == 0) {
+        stats[0] += M;
+        stats[2] += 1ull;
+    }
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
         const uint32_t tile = (uint32_t)(keys[j] >> 32);
         if (j == 0u || (uint32_t)(keys[j - 1] >> 32) != tile) ranges[tile].x = j;
@@ -211,13 +220,14 @@ __global__ void k_ranges(const unsigned long long *__restrict__ keys, const uint
     }
 }
 
-cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st) {
+cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
+                            unsigned long long *stats) {
     const uint32_t cap = (uint32_t)ctx->max_pairs;
     unsigned long long *bsum = (unsigned long long *)ctx->bsum;
     k_scan_reduce<<<SCAN_BLOCKS, 256, 0, st>>>(pv.touched, n, bsum);
     k_scan_blocks<<<1, SCAN_BLOCKS, 0, st>>>(bsum, ctx->d_count, cap, ctx->d_status);
     k_scan_down<<<SCAN_BLOCKS, 256, 0, st>>>(pv.touched, n, bsum, cap, pv.offs);
-    if (n > 0) k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, n, tiles_x, cap, ctx->keys[0], ctx->vals[0]);
+    if (n > 0) k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, n, tiles_x, cap, ctx->keys[0], ctx->vals[0], stats);
     const int ntiles = tiles_x * tiles_y;
     int tile_bits = 0;
     while ((1 << tile_bits) < ntiles) ++tile_bits;
@@ -236,6 +246,7 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     ctx->sorted = cur;
     cudaError_t e = cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
     if (e != cudaSuccess) return e;
-    k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[cur], ctx->d_count, ctx->ranges);
+    k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[cur], ctx->d_count, ctx->ranges, stats);
+    GS2_COUNT_LAUNCH(3 + (n > 0) + 3 * passes + 1);
     return cudaGetLastError();
 }

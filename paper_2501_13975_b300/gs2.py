@@ -45,6 +45,7 @@ class Config_(C.Structure):
                 ("t_min", C.c_float), ("lowpass", C.c_float), ("near_z", C.c_float),
                 ("barrier_alpha", C.c_float), ("frac_to_boundary", C.c_float), ("damping_mu0", C.c_float),
                 ("damping_tries", C.c_int32), ("scale_min", C.c_float), ("scale_trust", C.c_float),
+                ("trust_pos", C.c_float), ("trust_rot", C.c_float), ("trust_color", C.c_float),
                 ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
                 ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
                 ("precision", C.c_int32)]
@@ -76,6 +77,9 @@ _sigs = {
     "gs2_camera_knn": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32, _vp]),
     "gs2_sweep": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
                             C.c_int32, _vp, _vp, _vp]),
+    "gs2_launch_count": (C.c_uint64, []),
+    "gs2_profile": (C.c_int, [_vp, C.c_int32]),
+    "gs2_profile_read": (C.c_int, [_vp, _vp, _vp, _vp]),
     "gs2_debug_tiles": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
     "gs2_debug_keys": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "gs2_debug_proj": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
@@ -312,6 +316,18 @@ class Context:
         self._ok(_lib.gs2_sweep(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
                                 _ptr(losses), _ptr(n_failed), _stream(stream)), "gs2_sweep")
 
+    def profile(self, enable: bool):
+        self._ok(_lib.gs2_profile(self.h, 1 if enable else 0), "gs2_profile")
+
+    def profile_read(self):
+        ms = np.zeros(5, np.float64)
+        cnt = np.zeros(5, np.int64)
+        stats = np.zeros((5, 4), np.uint64)
+        self._ok(_lib.gs2_profile_read(self.h, ms.ctypes.data_as(_vp), cnt.ctypes.data_as(_vp),
+                                       stats.ctypes.data_as(_vp)), "gs2_profile_read")
+        return dict(accum_ms=ms, accum_launches=cnt, pairs=stats[:, 0], visible=stats[:, 1],
+                    binnings=stats[:, 2], pixels=stats[:, 3])
+
     def debug_tiles(self, w, h, capacity, stream=None):
         tx, ty = (w + 15) // 16, (h + 15) // 16
         ranges = torch.zeros((tx * ty, 2), dtype=torch.int32, device="cuda")
@@ -328,6 +344,10 @@ class Context:
         assert _lib.gs2_debug_proj(_ptr(proj), int(n), _ptr(out), _stream(stream)) == 0
         assert _lib.gs2_debug_keys(_ptr(proj), int(n), _ptr(keys), _stream(stream)) == 0
         return out, keys
+
+
+def launch_count() -> int:
+    return int(_lib.gs2_launch_count())
 
 
 def camera_knn(centres: np.ndarray, sphere: np.ndarray, k: int) -> np.ndarray:

@@ -36,7 +36,7 @@ def test_damped_cholesky_matches_numpy():
             A = _spd(rng, S, 1e3)
             Hf[ch, k] = A
             H[ch, :, k] = _pack(A)
-    r = O.solve(O.COLOR, sc, synth.ring_cameras()[0], g, H, dict(damping_mu0=1e-4))
+    r = O.solve(O.COLOR, sc, synth.ring_cameras()[0], g, H, dict(damping_mu0=1e-4, trust_color=1e30))
     for ch in range(3):
         for k in range(n):
             A = Hf[ch, k]
@@ -62,7 +62,7 @@ def test_damping_ladder_on_indefinite_block():
         mats[k] = A
         for ch in range(3):
             H[ch, :, k] = _pack(A)
-    r = O.solve(O.COLOR, sc, synth.ring_cameras()[0], g, H, dict(damping_mu0=1e-4))
+    r = O.solve(O.COLOR, sc, synth.ring_cameras()[0], g, H, dict(damping_mu0=1e-4, trust_color=1e30))
     for k in range(n):
         A = mats[k]
         m = np.abs(np.diag(A)).mean()
@@ -101,7 +101,7 @@ def test_position_step_is_plane_minimiser():
         A = _spd(rng, 3, 20.0)
         mats.append(A)
         H[:, k] = _pack(A)
-    r = O.solve(O.POS, sc, cam, g, H, dict(damping_mu0=0.0))
+    r = O.solve(O.POS, sc, cam, g, H, dict(damping_mu0=0.0, trust_pos=1e30))
     o = cam.center()
     for k in range(n):
         rr = sc.mean[:, k].astype(np.float64) - o
@@ -295,3 +295,40 @@ def test_sweep_reduces_loss_tiny():
         h, losses, nfail = O.sweep(h, cams, targets, nb, t, cfg)
     L1 = total(h)
     assert L1 < 0.5 * L0, (L0, L1)
+
+
+def test_trust_radii_scale_steps_down():
+    """Trust radii: the position step is at most trust_pos * max(s), the rotation
+    at most trust_rot, the colour step per channel at most trust_color; a step
+    that exceeds its radius keeps its direction."""
+    rng = np.random.default_rng(21)
+    n = 40
+    sc = micro_scene(n, 22, sh_degree=1)
+    cam = micro_camera()
+    g = 10.0 ** rng.uniform(-3, 1, n) * rng.standard_normal((3, n))
+    H = np.zeros((6, n))
+    for k in range(n):
+        H[:, k] = _pack(_spd(rng, 3, 5.0))
+    loose = dict(damping_mu0=0.0, trust_pos=1e30)
+    tight = dict(damping_mu0=0.0, trust_pos=3.0)
+    a = O.solve(O.POS, sc, cam, g, H, loose)["step"]
+    b = O.solve(O.POS, sc, cam, g, H, tight)["step"]
+    smax = sc.scale.astype(np.float64).max(0)
+    nb = np.linalg.norm(b, axis=0)
+    na = np.linalg.norm(a, axis=0)
+    assert np.all(nb <= 3.0 * smax * (1 + 1e-12))
+    clipped = na > 3.0 * smax
+    assert clipped.any() and (~clipped).any()
+    assert np.allclose(b[:, ~clipped], a[:, ~clipped])
+    assert np.allclose(b[:, clipped] / nb[clipped], a[:, clipped] / na[clipped])
+    th = O.solve(O.ROT, sc, cam, np.array([[50.0, -0.01]] * 1).reshape(1, 2)[:, :2].repeat(20, 1)[:, :n],
+                 np.ones((1, n)), dict(damping_mu0=0.0))["step"]
+    assert np.all(np.abs(th) <= np.pi / 4 + 1e-15)
+    S = 4
+    gc = 100.0 * rng.standard_normal((3, S, n))
+    Hc = np.zeros((3, S * (S + 1) // 2, n))
+    for ch in range(3):
+        for k in range(n):
+            Hc[ch, :, k] = _pack(_spd(rng, S, 5.0))
+    st = O.solve(O.COLOR, sc, cam, gc, Hc, dict(damping_mu0=0.0))["step"]
+    assert np.all(np.linalg.norm(st, axis=1) <= 2 * np.sqrt(np.pi) * (1 + 1e-12))
