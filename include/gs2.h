@@ -237,6 +237,31 @@ uint64_t gs2_launch_count(void);
 gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable);
 gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launches, uint64_t *stats);
 
+/* No-allocation render (the paper has no counterpart; this serves callers).
+ * Some callers cannot call cudaMalloc: a plugin or callback run by a host
+ * application that owns all device memory and does not let its plugins
+ * allocate, or a real-time loop that must not pay allocation latency or risk
+ * running out of memory halfway through a run.  gs2_render_noalloc does what
+ * gs2_project followed by gs2_raster_fwd does for one view, with no gs2_ctx
+ * and no allocation: its sorting scratch is one fixed array of
+ * GS2_NOALLOC_SCRATCH_BYTES compiled into the library, held on every GPU that
+ * loads the library until the process exits.
+ *   Limits: at most GS2_NOALLOC_MAX_TILES 16x16 tiles (GS2_ERR_SHAPE beyond)
+ *   and GS2_NOALLOC_MAX_PAIRS (tile, Gaussian) pairs; more pairs set
+ *   GS2_ERR_CAPACITY's bit (1) in *status_out and the image is then incomplete.
+ *   cfg: host, NULL for the defaults.  proj: device, gs2_proj_bytes(n);
+ *   image, raster_state: device outputs as for gs2_raster_fwd; status_out:
+ *   device uint32 (0 = OK), may be NULL.
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make it before any stream capture.  All calls share the
+ *   array and leave their contents in it: calls that overlap on the GPU race
+ *   and must be serialised by the caller. */
+#define GS2_NOALLOC_MAX_PAIRS 524288
+#define GS2_NOALLOC_MAX_TILES 4096
+#define GS2_NOALLOC_SCRATCH_BYTES 13230592ull
+gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene *scene, const gs2_camera *cam, void *proj,
+                              float *image, void *raster_state, uint32_t *status_out, gs2_stream stream);
+
 /* Introspection for tests: copies the current tile ranges (device uint32
  * [ntiles][2]) and sorted Gaussian ids (device uint32, up to capacity) and
  * returns the pair count (host) after synchronising the stream. */

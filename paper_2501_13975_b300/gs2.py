@@ -80,6 +80,8 @@ _sigs = {
     "gs2_launch_count": (C.c_uint64, []),
     "gs2_profile": (C.c_int, [_vp, C.c_int32]),
     "gs2_profile_read": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "gs2_render_noalloc": (C.c_int, [C.POINTER(Config_), C.POINTER(Scene_), C.POINTER(Camera_), _vp, _vp, _vp,
+                                     _vp, _vp]),
     "gs2_debug_tiles": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
     "gs2_debug_keys": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "gs2_debug_proj": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
@@ -344,6 +346,18 @@ class Context:
         assert _lib.gs2_debug_proj(_ptr(proj), int(n), _ptr(out), _stream(stream)) == 0
         assert _lib.gs2_debug_keys(_ptr(proj), int(n), _ptr(keys), _stream(stream)) == 0
         return out, keys
+
+
+def render_noalloc(scene: DeviceScene, cam, proj, image, raster_state, status=None, config: dict | None = None,
+                   stream=None):
+    """One view rendered without any device allocation by the library (see
+    gs2_render_noalloc in include/gs2.h); all buffers are the caller's."""
+    cfg = _config_struct(config)
+    s = scene.struct()
+    st = _lib.gs2_render_noalloc(C.byref(cfg), C.byref(s), C.byref(camera_struct(cam)), _ptr(proj), _ptr(image),
+                                 _ptr(raster_state), _ptr(status), _stream(stream))
+    if st != 0:
+        raise GS2Error(f"gs2_render_noalloc: {STATUS.get(st, st)}")
 
 
 def launch_count() -> int:
