@@ -293,7 +293,8 @@ def oracle_group_pass_seconds(O, scene_h, cam, group, crop, ocfg, target_full):
     """Time one oracle group pass (render + loss derivatives + block assembly)
     on a crop x crop window in the image centre."""
     cw = synth.Camera(crop, crop, cam.fx, cam.fy, cam.cx - (cam.width // 2 - crop // 2),
-                      cam.cy - (cam.height // 2 - crop // 2), cam.viewmat)
+                      cam.cy - (cam.height // 2 - crop // 2), cam.viewmat,
+                      1.3 * 0.5 * cam.width / cam.fx, 1.3 * 0.5 * cam.height / cam.fy)
     y0, x0 = cam.height // 2 - crop // 2, cam.width // 2 - crop // 2
     tgt = target_full[:, y0:y0 + crop, x0:x0 + crop]
     t0 = time.perf_counter()

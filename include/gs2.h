@@ -77,11 +77,15 @@ typedef struct {
 
 /* Pinhole camera looking along +z of its frame (x right, y down).
  * viewmat: host, row-major 3x4 [R | t], world -> camera.
- * pi = (fx tx/tz + cx, fy ty/tz + cy) in pixels for t = R p + t. */
+ * pi = (fx tx/tz + cx, fy ty/tz + cy) in pixels for t = R p + t.
+ * clip_x, clip_y: limits of tx/tz, ty/tz inside the projection Jacobian of the
+ *   EWA covariance (the standard 3DGS frustum clamp); 0 selects
+ *   1.3 * (width/2) / fx and 1.3 * (height/2) / fy of this camera. */
 typedef struct {
     int32_t width, height;
     float fx, fy, cx, cy;
     float viewmat[12];
+    float clip_x, clip_y;
 } gs2_camera;
 
 /* Configuration.  Every constant the paper leaves unstated is a field; the
@@ -258,7 +262,7 @@ gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launc
  *   and must be serialised by the caller. */
 #define GS2_NOALLOC_MAX_PAIRS 524288
 #define GS2_NOALLOC_MAX_TILES 4096
-#define GS2_NOALLOC_SCRATCH_BYTES 13230592ull
+#define GS2_NOALLOC_SCRATCH_BYTES 13231616ull
 gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene *scene, const gs2_camera *cam, void *proj,
                               float *image, void *raster_state, uint32_t *status_out, gs2_stream stream);
 

@@ -55,7 +55,19 @@ typedef struct {
     int width, height;
     double fx, fy, cx, cy;
     double viewmat[12]; /* row-major [R | t], world -> camera; camera looks along +z */
+    double clip_x, clip_y; /* frustum clamp of tx/tz, ty/tz in J; 0: 1.3 (W/2)/fx, 1.3 (H/2)/fy */
 } orc_camera;
+
+/* Frustum clamp limits of the projection Jacobian (reading: the standard 3DGS
+ * rasteriser the paper builds on clamps tx/tz, ty/tz to 1.3x the half field of
+ * view inside J; without it, Gaussians close to the camera plane and far off
+ * axis become screen-space needles no FP32 rasteriser can evaluate). */
+static double clip_lim(const orc_camera *c, int axis) {
+    double v = axis == 0 ? c->clip_x : c->clip_y;
+    if (v > 0) return v;
+    return axis == 0 ? (double)(float)(1.3f * (0.5f * (float)c->width) / (float)c->fx)
+                     : (double)(float)(1.3f * (0.5f * (float)c->height) / (float)c->fy);
+}
 
 typedef struct {
     double lambda_ssim;
@@ -318,7 +330,8 @@ static void quat_to_R(const jet q[4], jet R[3][3]) {
  *    pixel (m, n) has its centre at integer coordinates (m, n);
  *  - EWA: Sigma2D = J Wr R S S^T R^T Wr^T J^T + lowpass*I with J the
  *    perspective Jacobian at t (the paper's "orthographic" is read as the
- *    Jacobian of the projection P), no frustum clamp;
+ *    Jacobian of the projection P), with tx/tz, ty/tz clamped to the frustum
+ *    limits inside J (the standard 3DGS clamp; clip_lim);
  *  - a Gaussian with t_z < near_z is culled;
  *  - c~ = sum_i B_i Phi_i(r) c_i with r the unit camera->centre direction, no
  *    offset and no clamp (c~ is linear in c, as the colour solve states).
@@ -348,15 +361,22 @@ static void project_one(const orc_camera *cam, const orc_config *cfg, int S, gpa
     jscale(&tmp, &tmp, cam->fy);
     jaddc(&out->pix[1], &tmp, cam->cy);
 
-    /* J (2x3) */
-    jet J[2][3];
+    /* J (2x3) with tau = t_xy / t_z clamped to the frustum limits (a clamped
+     * tau is a constant) */
+    jet J[2][3], tau[2];
+    for (int a = 0; a < 2; ++a) {
+        double L = clip_lim(cam, a);
+        jmul(&tau[a], &t[a], &itz);
+        if (tau[a].v > L) jconst(&tau[a], L);
+        else if (tau[a].v < -L) jconst(&tau[a], -L);
+    }
     jscale(&J[0][0], &itz, cam->fx);
     jconst(&J[0][1], 0.0);
-    jmul(&tmp, &t[0], &itz2);
+    jmul(&tmp, &tau[0], &itz);
     jscale(&J[0][2], &tmp, -cam->fx);
     jconst(&J[1][0], 0.0);
     jscale(&J[1][1], &itz, cam->fy);
-    jmul(&tmp, &t[1], &itz2);
+    jmul(&tmp, &tau[1], &itz);
     jscale(&J[1][2], &tmp, -cam->fy);
 
     /* M = J Wr R diag(s)  (2x3); Sigma2D = M M^T + lowpass I */
@@ -1053,8 +1073,10 @@ static int scale_basis(const orc_camera *cam, const orc_config *cfg, const doubl
     for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * p[0] + V[i * 4 + 1] * p[1] + V[i * 4 + 2] * p[2] + V[i * 4 + 3];
     double tz = depth_fp64(cam, p[0], p[1], p[2]);
     if (!(tz >= cfg->near_z)) return 3;
-    double J[2][3] = {{cam->fx / t[2], 0, -cam->fx * t[0] / (t[2] * t[2])},
-                      {0, cam->fy / t[2], -cam->fy * t[1] / (t[2] * t[2])}};
+    double tx = t[0] / t[2], ty = t[1] / t[2], Lx = clip_lim(cam, 0), Ly = clip_lim(cam, 1);
+    tx = tx > Lx ? Lx : (tx < -Lx ? -Lx : tx);
+    ty = ty > Ly ? Ly : (ty < -Ly ? -Ly : ty);
+    double J[2][3] = {{cam->fx / t[2], 0, -cam->fx * tx / t[2]}, {0, cam->fy / t[2], -cam->fy * ty / t[2]}};
     double R[3][3];
     quat_R_plain(q, R);
     double M[2][3];

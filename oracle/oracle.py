@@ -35,7 +35,8 @@ class OrcScene(C.Structure):
 
 class OrcCamera(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("fx", C.c_double), ("fy", C.c_double),
-                ("cx", C.c_double), ("cy", C.c_double), ("viewmat", C.c_double * 12)]
+                ("cx", C.c_double), ("cy", C.c_double), ("viewmat", C.c_double * 12),
+                ("clip_x", C.c_double), ("clip_y", C.c_double)]
 
 
 class OrcConfig(C.Structure):
@@ -116,6 +117,8 @@ def cam_struct(cam) -> OrcCamera:
     vm = np.asarray(cam.viewmat, np.float64).reshape(-1)
     for i in range(12):
         c.viewmat[i] = vm[i]
+    c.clip_x = float(getattr(cam, "clip_x", 0.0))
+    c.clip_y = float(getattr(cam, "clip_y", 0.0))
     return c
 
 
@@ -254,6 +257,7 @@ class _Cam:
         self.width, self.height = c.width, c.height
         self.fx, self.fy, self.cx, self.cy = c.fx, c.fy, c.cx, c.cy
         self.viewmat = np.array(list(c.viewmat)).reshape(3, 4)
+        self.clip_x, self.clip_y = c.clip_x, c.clip_y
 
 
 def downsample_camera(cam, f):

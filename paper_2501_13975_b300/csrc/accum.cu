@@ -70,6 +70,54 @@ __device__ __forceinline__ void falloff_derivs(float G, float ca, float cb, floa
     }
 }
 
+// Warp sum of a P-float payload followed by atomic adds into zbuf[i][k].
+// Reduce-scatter transpose: the payload is padded to PP = 2^m floats; at each
+// butterfly step a lane keeps half of its current values (chosen by its lane
+// bit) and adds the partner's matching half, so after the five steps lane L
+// holds fully reduced entries at distinct indices (PP/32 of them when PP >= 32,
+// or one entry shared by 32/PP lanes).  P (5 - 1/32) shuffles become about PP,
+// and the atomics are issued by many lanes at once instead of lane 0 alone.
+template <int P> struct Pad { static constexpr int PP = P <= 2 ? 2 : P <= 4 ? 4 : P <= 8 ? 8 : P <= 16 ? 16 : P <= 32 ? 32 : 64; };
+
+template <int P>
+__device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], int lane, float *__restrict__ zbuf,
+                                                        int n, uint32_t k) {
+    constexpr int PP = Pad<P>::PP;
+    float v[PP];
+#pragma unroll
+    for (int i = 0; i < PP; ++i) v[i] = (i < P) ? pl[i] : 0.f;
+    int off = 0;           // index of v[0] in the payload
+    int len = PP;          // values this lane still holds
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = (lane & o) != 0;
+        if (len > 1) {
+            const int h = len >> 1;
+#pragma unroll
+            for (int i = 0; i < PP / 2; ++i) {
+                if (i < h) {
+                    const float send = up ? v[i] : v[i + h];
+                    const float keep = up ? v[i + h] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+                }
+            }
+            if (up) off += h;
+            len = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], o);
+        }
+    }
+    // lanes that share an entry (PP < 32): only the one with the low lane bits clear writes
+    constexpr int share = (PP >= 32) ? 1 : 32 / PP;
+    if ((lane & (share - 1)) == 0) {
+#pragma unroll
+        for (int j = 0; j < (PP >= 32 ? PP / 32 : 1); ++j) {
+            const int idx = off + j;
+            if (idx < P && v[j] != 0.f) atomicAdd(&zbuf[(size_t)idx * n + k], v[j]);
+        }
+    }
+}
+
 template <int GROUP>
 __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict__ ranges,
                                                         const uint32_t *__restrict__ ids, ProjView pv, RasterView rv,
@@ -203,19 +251,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
                 cb2 = alpha * C.z + (1.f - alpha) * cb2;
                 T = Tk;
             }
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-                float v = pl[i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                pl[i] = v;
-            }
-            if (lane == 0) {
-                const uint32_t k = sId[s];
-#pragma unroll
-                for (int i = 0; i < P; ++i)
-                    if (pl[i] != 0.f) atomicAdd(&zbuf[(size_t)i * n + k], pl[i]);
-            }
+            warp_reduce_scatter_add<P>(pl, lane, zbuf, n, sId[s]);
         }
     }
 }
@@ -244,7 +280,8 @@ __device__ __forceinline__ void cam_T(const DevCam &cam, const float p[3], float
     const float *V = cam.V;
     for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * p[0] + V[i * 4 + 1] * p[1] + V[i * 4 + 2] * p[2] + V[i * 4 + 3];
     const float iz = 1.f / t[2];
-    const float j00 = cam.fx * iz, j02 = -cam.fx * t[0] * iz * iz, j11 = cam.fy * iz, j12 = -cam.fy * t[1] * iz * iz;
+    const float taux = fminf(fmaxf(t[0] * iz, -cam.Lx), cam.Lx), tauy = fminf(fmaxf(t[1] * iz, -cam.Ly), cam.Ly);
+    const float j00 = cam.fx * iz, j02 = -cam.fx * taux * iz, j11 = cam.fy * iz, j12 = -cam.fy * tauy * iz;
     for (int j = 0; j < 3; ++j) {
         T[0][j] = j00 * V[j] + j02 * V[8 + j];
         T[1][j] = j11 * V[4 + j] + j12 * V[8 + j];
@@ -264,8 +301,9 @@ __device__ __forceinline__ void push_cov(const float T[2][3], const float S3[3][
 __global__ void k_epi_opacity(const ProjView pv, float *zbuf, int n, float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || pv.touched[k] == 0u) return;
-    blocks[k] += zbuf[k];
-    blocks[n + k] += zbuf[n + k];
+    const float z0 = zbuf[k], z1 = zbuf[n + k];
+    blocks[k] += z0;
+    blocks[n + k] += z1;
     zbuf[k] = 0.f;
     zbuf[n + k] = 0.f;
 }
@@ -275,11 +313,14 @@ __global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, float *z
     const int n = sc.n;
     if (k >= n) return;
     const bool vis = pv.touched[k] != 0u;
+    float zz[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        slot[(size_t)i * n + k] = vis ? zbuf[(size_t)i * n + k] : 0.f;
-        if (vis) zbuf[(size_t)i * n + k] = 0.f;
-    }
+    for (int i = 0; i < 6; ++i) zz[i] = vis ? zbuf[(size_t)i * n + k] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) slot[(size_t)i * n + k] = zz[i];
+    if (vis)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) zbuf[(size_t)i * n + k] = 0.f;
     float rx = sc.mean[k] - cam.o[0], ry = sc.mean[n + k] - cam.o[1], rz = sc.mean[2 * n + k] - cam.o[2];
     const float rn = rsqrtf(rx * rx + ry * ry + rz * rz);
     float phi[GS2_MAX_SH];
@@ -292,10 +333,10 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, float *z
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
     float z[9];
-    for (int i = 0; i < 9; ++i) {
-        z[i] = zbuf[(size_t)i * n + k];
-        zbuf[(size_t)i * n + k] = 0.f;
-    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) z[i] = zbuf[(size_t)i * n + k];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
     GaussGeo g;
     load_geo(sc, k, g);
     float t[3], T[2][3];
@@ -331,10 +372,10 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
     float z[9];
-    for (int i = 0; i < 9; ++i) {
-        z[i] = zbuf[(size_t)i * n + k];
-        zbuf[(size_t)i * n + k] = 0.f;
-    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) z[i] = zbuf[(size_t)i * n + k];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
     GaussGeo g;
     load_geo(sc, k, g);
     float t[3], T[2][3];
@@ -396,154 +437,225 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
     blocks[n + k] += hth;
 }
 
-__global__ void k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, float *zbuf, float *blocks) {
+// Position epilogue.  With u = 1/t_z and a, b in {x, y}:
+//   pi_a = f_a t_a u + c_a,
+//   Sigma_ab = f_a f_b u^2 Q_ab(tau) (+ low-pass), tau_a = clamp(t_a u),
+// V the camera-space 3D covariance (J V J^T written out); derivatives by the
+// chain rule through the intermediates (u, tau_x, tau_y).
+__global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, float *zbuf,
+                                                 float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
     float z[GS2_ZPOS];
-    for (int i = 0; i < GS2_ZPOS; ++i) {
-        z[i] = zbuf[(size_t)i * n + k];
-        zbuf[(size_t)i * n + k] = 0.f;
-    }
+    // all loads first, then the clears (interleaving them serialises the loads)
+#pragma unroll
+    for (int i = 0; i < GS2_ZPOS; ++i) z[i] = zbuf[(size_t)i * n + k];
+#pragma unroll
+    for (int i = 0; i < GS2_ZPOS; ++i) zbuf[(size_t)i * n + k] = 0.f;
     GaussGeo g;
     load_geo(sc, k, g);
     const float *V = cam.V;
     float t[3];
+#pragma unroll
     for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * g.p[0] + V[i * 4 + 1] * g.p[1] + V[i * 4 + 2] * g.p[2] + V[i * 4 + 3];
-    const float iz = 1.f / t[2], iz2 = iz * iz, iz3 = iz2 * iz, iz4 = iz2 * iz2;
-    const float fx = cam.fx, fy = cam.fy;
+    const float u = 1.f / t[2], u2 = u * u, u3 = u2 * u, u4 = u2 * u2;
     // camera-space covariance Vc = (Wr R diag(s)) (Wr R diag(s))^T
     float M3[3][3];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
         for (int j = 0; j < 3; ++j)
             M3[i][j] = (V[i * 4] * g.R[0][j] + V[i * 4 + 1] * g.R[1][j] + V[i * 4 + 2] * g.R[2][j]) * g.s[j];
     float Vc[3][3];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
         for (int j = 0; j < 3; ++j) Vc[i][j] = M3[i][0] * M3[j][0] + M3[i][1] * M3[j][1] + M3[i][2] * M3[j][2];
-    // J rows and their derivatives w.r.t. t
-    float J[2][3] = {{fx * iz, 0.f, -fx * t[0] * iz2}, {0.f, fy * iz, -fy * t[1] * iz2}};
-    float dJ[2][3][3];   // [row][k][col]
-    float d2J[2][3][3][3];
-    for (int a = 0; a < 2; ++a)
-        for (int kk = 0; kk < 3; ++kk)
-            for (int c = 0; c < 3; ++c) {
-                dJ[a][kk][c] = 0.f;
-                for (int l = 0; l < 3; ++l) d2J[a][kk][l][c] = 0.f;
-            }
-    dJ[0][0][2] = -fx * iz2;
-    dJ[0][2][0] = -fx * iz2;
-    dJ[0][2][2] = 2.f * fx * t[0] * iz3;
-    dJ[1][1][2] = -fy * iz2;
-    dJ[1][2][1] = -fy * iz2;
-    dJ[1][2][2] = 2.f * fy * t[1] * iz3;
-    d2J[0][0][2][2] = d2J[0][2][0][2] = 2.f * fx * iz3;
-    d2J[0][2][2][0] = 2.f * fx * iz3;
-    d2J[0][2][2][2] = -6.f * fx * t[0] * iz4;
-    d2J[1][1][2][2] = d2J[1][2][1][2] = 2.f * fy * iz3;
-    d2J[1][2][2][1] = 2.f * fy * iz3;
-    d2J[1][2][2][2] = -6.f * fy * t[1] * iz4;
-    // z derivatives w.r.t. t: dz[5][3], d2z[5][3][3]
-    float dz[5][3], d2z[5][3][3];
-    for (int i = 0; i < 5; ++i)
-        for (int a = 0; a < 3; ++a) {
-            dz[i][a] = 0.f;
-            for (int b = 0; b < 3; ++b) d2z[i][a][b] = 0.f;
-        }
-    dz[0][0] = fx * iz; dz[0][2] = -fx * t[0] * iz2;
-    dz[1][1] = fy * iz; dz[1][2] = -fy * t[1] * iz2;
-    d2z[0][0][2] = d2z[0][2][0] = -fx * iz2; d2z[0][2][2] = 2.f * fx * t[0] * iz3;
-    d2z[1][1][2] = d2z[1][2][1] = -fy * iz2; d2z[1][2][2] = 2.f * fy * t[1] * iz3;
-    const int ea[3] = {0, 0, 1}, eb[3] = {0, 1, 1};
-    // helper: x^T Vc y
-    auto vq = [&](const float *x, const float *y) {
-        float acc = 0.f;
-        for (int i = 0; i < 3; ++i) acc += x[i] * (Vc[i][0] * y[0] + Vc[i][1] * y[1] + Vc[i][2] * y[2]);
-        return acc;
-    };
-    for (int e = 0; e < 3; ++e) {
-        const int a = ea[e], b = eb[e];
-        for (int kk = 0; kk < 3; ++kk) {
-            dz[2 + e][kk] = vq(dJ[a][kk], J[b]) + vq(J[a], dJ[b][kk]);
-            for (int l = 0; l < 3; ++l)
-                d2z[2 + e][kk][l] = vq(d2J[a][kk][l], J[b]) + vq(dJ[a][kk], dJ[b][l]) + vq(dJ[a][l], dJ[b][kk]) +
-                                    vq(J[a], d2J[b][kk][l]);
-        }
+    const float f[2] = {cam.fx, cam.fy};
+    // dz[i][k]: derivative of z_i w.r.t. t_k; Gt = sum_i z_i d2z_i/dt2 (symmetric 3x3)
+    float dz[5][3];
+    float Gt[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Gt[a][b] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {      // pi_a
+        dz[a][0] = (a == 0) ? f[0] * u : 0.f;
+        dz[a][1] = (a == 1) ? f[1] * u : 0.f;
+        dz[a][2] = -f[a] * t[a] * u2;
+        Gt[a][2] += -f[a] * u2 * z[a];
+        Gt[2][a] += -f[a] * u2 * z[a];
+        Gt[2][2] += 2.f * f[a] * t[a] * u3 * z[a];
     }
-    // to world: Jzp = dz Wr; d2z_p = Wr^T d2z Wr
+    // Sigma_ab = f_a f_b u^2 Q_ab(tau), Q_ab = V_ab - tau_a V_zb - tau_b V_za + tau_a tau_b V_zz,
+    // tau_a = t_a u clamped to the frustum limit (constant where clamped).
+    // Intermediates y = (u, tau_x, tau_y): Jacobian Jy[m][k] = dy_m/dt_k, Hessians Hy[m].
+    const float Lc[2] = {cam.Lx, cam.Ly};
+    float tau[2];
+    bool cl[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float tr = t[a] * u;
+        cl[a] = fabsf(tr) > Lc[a];
+        tau[a] = fminf(fmaxf(tr, -Lc[a]), Lc[a]);
+    }
+    float Jy[3][3], Hy[3][3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Jy[m][a] = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) Hy[m][a][b] = 0.f;
+        }
+    Jy[0][2] = -u2;
+    Hy[0][2][2] = 2.f * u3;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+        if (!cl[a]) {
+            Jy[1 + a][a] = u;
+            Jy[1 + a][2] = -t[a] * u2;
+            Hy[1 + a][a][2] = -u2;
+            Hy[1 + a][2][a] = -u2;
+            Hy[1 + a][2][2] = 2.f * t[a] * u3;
+        }
+    const int EA[3] = {0, 0, 1}, EB[3] = {0, 1, 1};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {      // Sigma_ab
+        const int a = EA[e], b = EB[e];
+        const float ff = f[a] * f[b];
+        const float Vab = Vc[a][b], Vzb = Vc[2][b], Vza = Vc[2][a], Vzz = Vc[2][2];
+        const float Q = Vab - tau[a] * Vzb - tau[b] * Vza + tau[a] * tau[b] * Vzz;
+        float dQ[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float dac = (a == c) ? 1.f : 0.f, dbc = (b == c) ? 1.f : 0.f;
+            dQ[c] = -dac * Vzb - dbc * Vza + (dac * tau[b] + dbc * tau[a]) * Vzz;
+        }
+        float Fy[3], Fyy[3][3];
+        Fy[0] = 2.f * ff * u * Q;
+        Fy[1] = ff * u2 * dQ[0];
+        Fy[2] = ff * u2 * dQ[1];
+        Fyy[0][0] = 2.f * ff * Q;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            Fyy[0][1 + c] = Fyy[1 + c][0] = 2.f * ff * u * dQ[c];
+#pragma unroll
+            for (int d = 0; d < 2; ++d)
+                Fyy[1 + c][1 + d] =
+                    ff * u2 * (((a == c) && (b == d) ? 1.f : 0.f) + ((b == c) && (a == d) ? 1.f : 0.f)) * Vzz;
+        }
+        const float ze = z[2 + e];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) dz[2 + e][kk] = Fy[0] * Jy[0][kk] + Fy[1] * Jy[1][kk] + Fy[2] * Jy[2][kk];
+        float FJ[3][3];   // Fyy Jy
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) FJ[m][kk] = Fyy[m][0] * Jy[0][kk] + Fyy[m][1] * Jy[1][kk] + Fyy[m][2] * Jy[2][kk];
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) {
+                const float sec = Jy[0][k1] * FJ[0][k2] + Jy[1][k1] * FJ[1][k2] + Jy[2][k1] * FJ[2][k2] +
+                                  Fy[0] * Hy[0][k1][k2] + Fy[1] * Hy[1][k1][k2] + Fy[2] * Hy[2][k1][k2];
+                Gt[k1][k2] += ze * sec;
+            }
+    }
+    // to world coordinates: Jzp = dz Wr, sum_i z_i d2z_i/dp2 = Wr^T Gt Wr
     float Jzp[5][3];
+#pragma unroll
     for (int i = 0; i < 5; ++i)
+#pragma unroll
         for (int c = 0; c < 3; ++c) Jzp[i][c] = dz[i][0] * V[c] + dz[i][1] * V[4 + c] + dz[i][2] * V[8 + c];
-    float Hp[3][3], gp[3];
-    // g = Jzp^T gz ; H = Jzp^T Hzz Jzp + sum_i gz_i d2z_i
-    float Hzz[5][5];
-    for (int i = 0; i < 5; ++i)
-        for (int j = i; j < 5; ++j) Hzz[i][j] = Hzz[j][i] = z[5 + ut5(i, j)];
+    float gp[3], Hp[3][3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         float acc = 0.f;
+#pragma unroll
         for (int i = 0; i < 5; ++i) acc += Jzp[i][c] * z[i];
         gp[c] = acc;
     }
-    float Gt[3][3];  // sum_i gz_i d2z_i (camera frame)
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
+    float HJ[5][3];   // Hzz Jzp
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
             float acc = 0.f;
-            for (int i = 0; i < 5; ++i) acc += z[i] * d2z[i][a][b];
-            Gt[a][b] = acc;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) acc += z[5 + (i <= j ? ut5(i, j) : ut5(j, i))] * Jzp[j][c];
+            HJ[i][c] = acc;
         }
+    float GW[3][3];   // Gt Wr
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) GW[a][d] = Gt[a][0] * V[d] + Gt[a][1] * V[4 + d] + Gt[a][2] * V[8 + d];
+#pragma unroll
     for (int c = 0; c < 3; ++c)
+#pragma unroll
         for (int d = c; d < 3; ++d) {
             float acc = 0.f;
-            for (int i = 0; i < 5; ++i) {
-                float row = 0.f;
-                for (int j = 0; j < 5; ++j) row += Hzz[i][j] * Jzp[j][d];
-                acc += Jzp[i][c] * row;
-            }
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) acc += V[a * 4 + c] * Gt[a][b] * V[b * 4 + d];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) acc += Jzp[i][c] * HJ[i][d];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc += V[a * 4 + c] * GW[a][d];
             Hp[c][d] = acc;
         }
     // colour path: c~(p) through r(p)
     float r[3] = {g.p[0] - cam.o[0], g.p[1] - cam.o[1], g.p[2] - cam.o[2]};
     const float rho = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), irho = 1.f / rho;
+#pragma unroll
     for (int i = 0; i < 3; ++i) r[i] *= irho;
     float Pm[3][3];
+#pragma unroll
     for (int a = 0; a < 3; ++a)
+#pragma unroll
         for (int b = 0; b < 3; ++b) Pm[a][b] = ((a == b ? 1.f : 0.f) - r[a] * r[b]) * irho;
     const int S = sc.S;
+#pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         const float WE = z[35 + ch], SS = z[38 + ch];
         float wco[GS2_MAX_SH];
         for (int i = 0; i < S; ++i) wco[i] = sh_norm(i) * sc.sh[(size_t)(ch * S + i) * n + k];
-        float f, gr[3], hs[6];
-        sh_poly_derivs(S, wco, r[0], r[1], r[2], f, gr, hs);
+        float fv, gr[3], hs[6];
+        sh_poly_derivs(S, wco, r[0], r[1], r[2], fv, gr, hs);
         const float Hr[3][3] = {{hs[0], hs[1], hs[2]}, {hs[1], hs[3], hs[4]}, {hs[2], hs[4], hs[5]}};
-        float gc[3];
+        float gc[3], y[3];
+#pragma unroll
         for (int a = 0; a < 3; ++a) gc[a] = Pm[a][0] * gr[0] + Pm[a][1] * gr[1] + Pm[a][2] * gr[2];
-        // second derivative of c~ w.r.t. p
-        float HPm[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) HPm[a][b] = Hr[a][0] * Pm[0][b] + Hr[a][1] * Pm[1][b] + Hr[a][2] * Pm[2][b];
-        float y[3];  // Jzp^T X_ch
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             float acc = 0.f;
+#pragma unroll
             for (int i = 0; i < 5; ++i) acc += Jzp[i][c] * z[20 + ch * 5 + i];
             y[c] = acc;
         }
+        float HPm[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) HPm[a][b] = Hr[a][0] * Pm[0][b] + Hr[a][1] * Pm[1][b] + Hr[a][2] * Pm[2][b];
+        const float gdr = gr[0] * r[0] + gr[1] * r[1] + gr[2] * r[2];
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             gp[a] += WE * gc[a];
+#pragma unroll
             for (int b = a; b < 3; ++b) {
                 float h2 = Pm[a][0] * HPm[0][b] + Pm[a][1] * HPm[1][b] + Pm[a][2] * HPm[2][b];
-                for (int m = 0; m < 3; ++m) {
-                    const float d2r = (3.f * r[m] * r[a] * r[b] - (m == a ? r[b] : 0.f) - (m == b ? r[a] : 0.f) -
-                                       (a == b ? r[m] : 0.f)) * irho * irho;
-                    h2 += gr[m] * d2r;
-                }
+                // sum_m gr_m d2r_m/dp_a dp_b = (3 (gr.r) r_a r_b - gr_a r_b - gr_b r_a - d_ab (gr.r)) / rho^2
+                h2 += (3.f * gdr * r[a] * r[b] - gr[a] * r[b] - gr[b] * r[a] - (a == b ? gdr : 0.f)) * irho * irho;
                 Hp[a][b] += y[a] * gc[b] + gc[a] * y[b] + SS * gc[a] * gc[b] + WE * h2;
             }
         }
     }
+#pragma unroll
     for (int c = 0; c < 3; ++c) blocks[(size_t)c * n + k] += gp[c];
+#pragma unroll
     for (int a = 0; a < 3; ++a)
+#pragma unroll
         for (int b = a; b < 3; ++b) blocks[(size_t)(3 + ut3(a, b)) * n + k] += Hp[a][b];
 }
 
@@ -579,7 +691,7 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
     const int eg = (n + 255) / 256;
     float *b = (float *)blocks;
     switch (group) {
-    case GS2_POS: k_epi_pos<<<eg, 128 * 2, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
+    case GS2_POS: k_epi_pos<<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
     case GS2_ROT: k_epi_rot<<<eg, 256, 0, st>>>(sc, view, primary, pv, ctx->zbuf, b); break;
     case GS2_SCALE: k_epi_scale<<<eg, 256, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
     case GS2_OPACITY: k_epi_opacity<<<eg, 256, 0, st>>>(pv, ctx->zbuf, n, b); break;

@@ -79,6 +79,7 @@ struct DevCam {
     float fx, fy, cx, cy;
     float V[12];     // row-major [R | t]
     float o[3];      // camera centre
+    float Lx, Ly;    // frustum clamp of tx/tz, ty/tz in the projection Jacobian
 };
 
 static inline DevCam make_devcam(const gs2_camera *c) {
@@ -87,6 +88,8 @@ static inline DevCam make_devcam(const gs2_camera *c) {
     d.h = c->height;
     d.fx = c->fx; d.fy = c->fy; d.cx = c->cx; d.cy = c->cy;
     for (int i = 0; i < 12; ++i) d.V[i] = c->viewmat[i];
+    d.Lx = c->clip_x > 0.f ? c->clip_x : 1.3f * (0.5f * (float)c->width) / c->fx;
+    d.Ly = c->clip_y > 0.f ? c->clip_y : 1.3f * (0.5f * (float)c->height) / c->fy;
     for (int i = 0; i < 3; ++i) {
         double s = 0;
         for (int j = 0; j < 3; ++j) s -= (double)c->viewmat[j * 4 + i] * (double)c->viewmat[j * 4 + 3];

@@ -149,7 +149,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         A((void **)&c->keys[i], sizeof(unsigned long long) * (size_t)max_pairs);
         A((void **)&c->vals[i], sizeof(uint32_t) * (size_t)max_pairs);
     }
-    A((void **)&c->ghist, sizeof(uint32_t) * 256 * (size_t)SORT_BLOCKS);
+    A((void **)&c->ghist, sizeof(uint32_t) * (256 * (size_t)SORT_BLOCKS + 256));  // + digit totals
     A((void **)&c->bsum, sizeof(unsigned long long) * 1024);
     A((void **)&c->d_count, sizeof(uint32_t) * 4);
     A((void **)&c->ranges, sizeof(uint2) * (size_t)tiles);

@@ -24,7 +24,7 @@
 // carve-up of the scratch array (byte offsets, each 256-aligned)
 #define NA_KEYS_BYTES (8ull * GS2_NOALLOC_MAX_PAIRS)
 #define NA_VALS_BYTES (4ull * GS2_NOALLOC_MAX_PAIRS)
-#define NA_GHIST_BYTES (4ull * 256 * NA_SORT_BLOCKS)
+#define NA_GHIST_BYTES (4ull * (256 * NA_SORT_BLOCKS + 256))
 #define NA_BSUM_BYTES (8ull * 1024)
 #define NA_RANGES_BYTES (8ull * GS2_NOALLOC_MAX_TILES)
 #define NA_OFF_KEYS0 0ull

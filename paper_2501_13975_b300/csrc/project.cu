@@ -3,7 +3,8 @@
 // Per Gaussian: camera-space centre t = Wr p + w, pixel centre
 // pi = (fx tx/tz + cx, fy ty/tz + cy), EWA covariance
 // Sigma2D = J Wr R diag(s^2) R^T Wr^T J^T + lowpass I with J the perspective
-// Jacobian at t, its inverse (conic), SH colour c~ = sum_i c_i B_i Phi_i(r)
+// Jacobian at t (tx/tz, ty/tz clamped to 1.3x the half field of view, the
+// standard 3DGS frustum clamp), its inverse (conic), SH colour c~ = sum_i c_i B_i Phi_i(r)
 // with r the unit camera->centre direction, the tile rectangle of the support
 // { sigma G >= alpha_min } and the depth key.
 //
@@ -51,10 +52,11 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
     R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
     const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
 
-    // T = J Wr (2x3)
+    // T = J Wr (2x3); J uses tx/tz, ty/tz clamped to the camera's frustum limits
     const float itz = 1.f / tz;
-    const float j00 = cam.fx * itz, j02 = -cam.fx * tx * itz * itz;
-    const float j11 = cam.fy * itz, j12 = -cam.fy * ty * itz * itz;
+    const float taux = fminf(fmaxf(tx * itz, -cam.Lx), cam.Lx), tauy = fminf(fmaxf(ty * itz, -cam.Ly), cam.Ly);
+    const float j00 = cam.fx * itz, j02 = -cam.fx * taux * itz;
+    const float j11 = cam.fy * itz, j12 = -cam.fy * tauy * itz;
     float T0[3], T1[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -63,18 +65,31 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
     }
     // Sigma2D = sum_j s_j^2 m_j m_j^T, m_j = T R e_j
     const float ss[3] = {s0 * s0, s1 * s1, s2 * s2};
+    float m0[3], m1[3];
     float sxx = 0.f, sxy = 0.f, syy = 0.f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float m0 = T0[0] * R[0][j] + T0[1] * R[1][j] + T0[2] * R[2][j];
-        const float m1 = T1[0] * R[0][j] + T1[1] * R[1][j] + T1[2] * R[2][j];
-        sxx = fmaf(ss[j] * m0, m0, sxx);
-        sxy = fmaf(ss[j] * m0, m1, sxy);
-        syy = fmaf(ss[j] * m1, m1, syy);
+        m0[j] = T0[0] * R[0][j] + T0[1] * R[1][j] + T0[2] * R[2][j];
+        m1[j] = T1[0] * R[0][j] + T1[1] * R[1][j] + T1[2] * R[2][j];
+        sxx = fmaf(ss[j] * m0[j], m0[j], sxx);
+        sxy = fmaf(ss[j] * m0[j], m1[j], sxy);
+        syy = fmaf(ss[j] * m1[j], m1[j], syy);
     }
+    // det(A + l I) = det A + l tr A + l^2 with det A by Cauchy-Binet,
+    // sum_{i<j} s_i^2 s_j^2 (m_i x m_j)^2: a sum of non-negative terms, so no
+    // cancellation for thin, elongated screen-space ellipses (where
+    // sxx syy - sxy^2 loses all FP32 digits)
+    float detA = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) {
+            const float cr = m0[i] * m1[j] - m1[i] * m0[j];
+            detA = fmaf(ss[i] * ss[j] * cr, cr, detA);
+        }
+    const float det = detA + lowpass * (sxx + syy) + lowpass * lowpass;
     sxx += lowpass;
     syy += lowpass;
-    const float det = sxx * syy - sxy * sxy;
     const float idet = 1.f / det;
     const float ca = syy * idet, cb = -sxy * idet, cc = sxx * idet;
     const float pix_x = fmaf(cam.fx * tx, itz, cam.cx);

@@ -186,8 +186,9 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
     if (!(dz >= (double)near_z)) return;
     float t[3];
     for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * p[0] + V[i * 4 + 1] * p[1] + V[i * 4 + 2] * p[2] + V[i * 4 + 3];
-    const float J[2][3] = {{pr.fx / t[2], 0.f, -pr.fx * t[0] / (t[2] * t[2])},
-                           {0.f, pr.fy / t[2], -pr.fy * t[1] / (t[2] * t[2])}};
+    const float iz = 1.f / t[2];
+    const float taux = fminf(fmaxf(t[0] * iz, -pr.Lx), pr.Lx), tauy = fminf(fmaxf(t[1] * iz, -pr.Ly), pr.Ly);
+    const float J[2][3] = {{pr.fx * iz, 0.f, -pr.fx * taux * iz}, {0.f, pr.fy * iz, -pr.fy * tauy * iz}};
     float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
     const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     qw *= qn; qx *= qn; qy *= qn; qz *= qn;

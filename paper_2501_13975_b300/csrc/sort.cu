@@ -81,27 +81,50 @@ __global__ void k_scan_down(const uint32_t *__restrict__ x, int n, const unsigne
 }
 
 // ---------------------------------------------------------------- emit
-__global__ void k_emit(ProjView pv, int n, int tiles_x, uint32_t cap, unsigned long long *keys, uint32_t *vals,
-                       unsigned long long *stats) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// One CTA per 256 consecutive Gaussians: their pairs occupy one contiguous
+// output range, which the CTA writes with all threads striding (coalesced,
+// balanced even when one Gaussian covers thousands of tiles); a pair finds
+// its Gaussian by binary search over the CTA's offsets in shared memory.
+__global__ void __launch_bounds__(256) k_emit(ProjView pv, int n, int tiles_x, uint32_t cap,
+                                              unsigned long long *keys, uint32_t *vals, unsigned long long *stats) {
+    __shared__ uint32_t s_off[257];
+    __shared__ uint2 s_rect[256];
+    __shared__ uint32_t s_key[256];
+    const int t = threadIdx.x;
+    const int k = blockIdx.x * 256 + t;
     const uint32_t cnt = (k < n) ? pv.touched[k] : 0u;
     if (stats) {  // visible-Gaussian count, one atomic per warp
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, cnt != 0u);
-        if ((threadIdx.x & 31) == 0 && b) atomicAdd(&stats[1], (unsigned long long)__popc(b));
+        if ((t & 31) == 0 && b) atomicAdd(&stats[1], (unsigned long long)__popc(b));
     }
-    if (cnt == 0u) return;
-    uint32_t off = pv.offs[k];
-    const uint2 r = pv.rect[k];
-    const uint32_t tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu, ty1 = r.y >> 16;
-    const unsigned long long dk = pv.key[k];
-    for (uint32_t ty = ty0; ty < ty1; ++ty)
-        for (uint32_t tx = tx0; tx < tx1; ++tx) {
-            if (off >= cap) return;
-            const unsigned long long tile = (unsigned long long)(ty * (uint32_t)tiles_x + tx);
-            keys[off] = (tile << 32) | dk;
-            vals[off] = (uint32_t)k;
-            ++off;
+    const uint32_t off = (k < n) ? pv.offs[k] : 0u;
+    s_off[t] = (k < n) ? off : 0xFFFFFFFFu;
+    s_rect[t] = (k < n) ? pv.rect[k] : make_uint2(0u, 0u);
+    s_key[t] = (k < n) ? pv.key[k] : 0u;
+    const int last = min(n - 1, blockIdx.x * 256 + 255) - blockIdx.x * 256;
+    __shared__ uint32_t s_beg, s_end;
+    if (t == last) {
+        s_end = min(off + cnt, cap);  // offsets are already clamped to cap
+    }
+    if (t == 0) s_beg = off;
+    if (t == 0) s_off[256] = 0xFFFFFFFFu;
+    __syncthreads();
+    const uint32_t beg = s_beg, end = s_end;
+    for (uint32_t j = beg + t; j < end; j += 256) {
+        // largest i with s_off[i] <= j
+        int lo = 0, hi = last;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= j) lo = mid;
+            else hi = mid - 1;
         }
+        const uint2 r = s_rect[lo];
+        const uint32_t tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
+        const uint32_t wdt = tx1 - tx0, rel = j - s_off[lo];
+        const uint32_t ty = ty0 + rel / wdt, tx = tx0 + rel % wdt;
+        keys[j] = ((unsigned long long)(ty * (uint32_t)tiles_x + tx) << 32) | (unsigned long long)s_key[lo];
+        vals[j] = (uint32_t)(blockIdx.x * 256 + lo);
+    }
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -125,41 +148,63 @@ __global__ void __launch_bounds__(SORT_THREADS) k_hist(const unsigned long long 
     ghist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of the (digit-major) histogram table, one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_hist_scan(uint32_t *ghist, int total) {
-    __shared__ uint32_t s[1024];
-    const int t = threadIdx.x;
-    const int per = (total + 1023) / 1024;
-    const int beg = min(t * per, total), end = min(beg + per, total);
-    uint32_t acc = 0;
-    for (int i = beg; i < end; ++i) acc += ghist[i];
-    s[t] = acc;
+// Per-digit scan of the block histograms: CTA d turns row d of ghist (one count
+// per sort block, coalesced) into exclusive prefixes and writes the digit's
+// total; each scatter block adds the exclusive scan of the 256 digit totals.
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *swarp, uint32_t &total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) swarp[w] = x;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = (t >= off) ? s[t - off] : 0u;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t z = lane < nw ? swarp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < nw) swarp[lane] = z;
     }
-    uint32_t run = s[t] - acc;
-    for (int i = beg; i < end; ++i) {
-        const uint32_t v = ghist[i];
-        ghist[i] = run;
-        run += v;
-    }
+    __syncthreads();
+    total = swarp[(blockDim.x >> 5) - 1];
+    const uint32_t before = (w > 0) ? swarp[w - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *ghist, int nb, uint32_t *dtot) {
+    __shared__ uint32_t swarp[32];
+    const int d = blockIdx.x, t = threadIdx.x;
+    const uint32_t v = (t < nb) ? ghist[d * nb + t] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan_1024(v, swarp, tot);
+    if (t < nb) ghist[d * nb + t] = ex;
+    if (t == 0) dtot[d] = tot;
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const unsigned long long *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
                                                           unsigned long long *__restrict__ kout,
                                                           uint32_t *__restrict__ vout, const uint32_t *count,
-                                                          int shift, const uint32_t *ghist, int nb) {
+                                                          int shift, const uint32_t *ghist, int nb,
+                                                          const uint32_t *dtot) {
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[SORT_THREADS / 32][256];
+    __shared__ uint32_t swarp[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t beg, end;
     chunk_of(count[0], nb, blockIdx.x, beg, end);
-    s_off[t] = ghist[t * nb + blockIdx.x];
+    {
+        uint32_t tot;
+        const uint32_t base = block_excl_scan_1024(dtot[t], swarp, tot);
+        s_off[t] = base + ghist[t * nb + blockIdx.x];
+    }
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (uint32_t base = beg; base < end; base += SORT_TILE) {
 #pragma unroll
@@ -234,13 +279,14 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     const int bits = 32 + tile_bits;
     const int passes = (bits + 7) / 8;
     const int nb = ctx->nb_sort;
+    uint32_t *dtot = ctx->ghist + 256 * nb;   // 256 digit totals after the histogram table
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         k_hist<<<nb, SORT_THREADS, 0, st>>>(ctx->keys[cur], ctx->d_count, shift, ctx->ghist, nb);
-        k_hist_scan<<<1, 1024, 0, st>>>(ctx->ghist, 256 * nb);
+        k_digit_scan<<<256, 1024, 0, st>>>(ctx->ghist, nb, dtot);
         k_scatter<<<nb, SORT_THREADS, 0, st>>>(ctx->keys[cur], ctx->vals[cur], ctx->keys[cur ^ 1],
-                                               ctx->vals[cur ^ 1], ctx->d_count, shift, ctx->ghist, nb);
+                                               ctx->vals[cur ^ 1], ctx->d_count, shift, ctx->ghist, nb, dtot);
         cur ^= 1;
     }
     ctx->sorted = cur;

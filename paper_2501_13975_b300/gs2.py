@@ -37,7 +37,8 @@ class Scene_(C.Structure):
 
 class Camera_(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
-                ("cx", C.c_float), ("cy", C.c_float), ("viewmat", C.c_float * 12)]
+                ("cx", C.c_float), ("cy", C.c_float), ("viewmat", C.c_float * 12),
+                ("clip_x", C.c_float), ("clip_y", C.c_float)]
 
 
 class Config_(C.Structure):
@@ -124,6 +125,8 @@ def camera_struct(cam) -> Camera_:
     vm = np.asarray(cam.viewmat, np.float32).reshape(-1)
     for i in range(12):
         c.viewmat[i] = float(vm[i])
+    c.clip_x = float(getattr(cam, "clip_x", 0.0))
+    c.clip_y = float(getattr(cam, "clip_y", 0.0))
     return c
 
 

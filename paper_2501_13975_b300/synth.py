@@ -52,6 +52,8 @@ class Camera:
     cx: float
     cy: float
     viewmat: np.ndarray   # (3, 4) float32 row-major [R | t], world -> camera, +z forward, y down
+    clip_x: float = 0.0   # frustum clamp limits (0: derived from this image's size)
+    clip_y: float = 0.0
 
     def center(self) -> np.ndarray:
         R = self.viewmat[:, :3].astype(np.float64)

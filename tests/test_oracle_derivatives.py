@@ -162,3 +162,25 @@ def test_ssim_identical_images():
     L = O.loss(img, img, dict(lambda_ssim=0.2))
     assert abs(L["lssim"]) < 1e-12 and abs(L["l2"]) == 0.0
     assert np.abs(L["e"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("group", [O.POS, O.SCALE, O.ROT])
+def test_blocks_fd_through_frustum_clamp(group):
+    """A Gaussian whose centre lies beyond the frustum clamp (tx/tz = 1.05 >
+    1.3 * 24/40): its covariance uses the clamped ratio, and the jet-derived
+    gradient and Hessian still match FD of the loss."""
+    sc = micro_scene(2, 41)
+    sc.mean[:, 1] = [4.2, 0.1, 4.0]
+    sc.scale[:, 1] = [1.2, 0.9, 1.5]
+    sc.opacity[1] = 0.7
+    cfg = dict(NOTHRESH, lambda_ssim=0.0)
+    cam = micro_camera()
+    h = O.scene_handle(sc)
+    target = O.render(micro_scene(2, 42), cam, cfg)["image"]
+    img = O.render(h, cam, cfg)["image"]
+    L = O.loss(img, target, cfg)
+    blk = O.accum(group, h, cam, cam, L["e"], L["h"], cfg)
+    D = O.group_dims(group, 1)
+    gfd, Hfd = _fd_blocks(group, h, 1, cam, cam, target, cfg, EPS[group])
+    assert np.abs(blk["g"][:, 1] - gfd).max() <= 2e-5 * np.abs(gfd).max()
+    assert np.abs(_unpack(blk["H"][:, 1], D) - Hfd).max() <= 2e-4 * np.abs(Hfd).max()
