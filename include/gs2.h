@@ -262,7 +262,7 @@ gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launc
  *   and must be serialised by the caller. */
 #define GS2_NOALLOC_MAX_PAIRS 524288
 #define GS2_NOALLOC_MAX_TILES 4096
-#define GS2_NOALLOC_SCRATCH_BYTES 13231616ull
+#define GS2_NOALLOC_SCRATCH_BYTES 9037312ull
 gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene *scene, const gs2_camera *cam, void *proj,
                               float *image, void *raster_state, uint32_t *status_out, gs2_stream stream);
 

@@ -33,14 +33,17 @@ struct ProjView {
     uint2 *rect;       // tile rectangle: x = tx0 | ty0 << 16, y = tx1 | ty1 << 16 (exclusive ends)
     uint32_t *touched; // number of tiles in rect (0 = not rendered)
     uint32_t *key;     // FP32 bit pattern of the camera depth (positive)
-    uint32_t *offs;    // exclusive prefix sum of touched
+    uint32_t *offs;    // exclusive prefix sum of touched, in depth-rank order
+    uint32_t *dk[2];   // depth-sort keys (ping-pong)
+    uint32_t *dv[2];   // depth-sort values: Gaussian ids, finally in depth-rank order
+    uint32_t *tsort;   // touched in depth-rank order
 };
 
 static inline size_t proj_bytes_impl(int64_t n) {
     size_t b = 0;
     b += align256(16 * (size_t)n) * 3;
     b += align256(8 * (size_t)n);
-    b += align256(4 * (size_t)n) * 3;
+    b += align256(4 * (size_t)n) * 8;
     return b;
 }
 
@@ -53,7 +56,12 @@ static inline ProjView proj_view(void *base, int64_t n) {
     v.rect = (uint2 *)p; p += align256(8 * (size_t)n);
     v.touched = (uint32_t *)p; p += align256(4 * (size_t)n);
     v.key = (uint32_t *)p; p += align256(4 * (size_t)n);
-    v.offs = (uint32_t *)p;
+    v.offs = (uint32_t *)p; p += align256(4 * (size_t)n);
+    for (int i = 0; i < 2; ++i) {
+        v.dk[i] = (uint32_t *)p; p += align256(4 * (size_t)n);
+        v.dv[i] = (uint32_t *)p; p += align256(4 * (size_t)n);
+    }
+    v.tsort = (uint32_t *)p;
     return v;
 }
 
@@ -119,11 +127,11 @@ struct gs2_ctx {
     int64_t max_pairs;
     int nb_sort;                 // blocks of the radix sort grid
     // sorting
-    unsigned long long *keys[2];
-    uint32_t *vals[2];
+    uint32_t *keys[2];           // pair keys: tile id
+    uint32_t *vals[2];           // pair values: Gaussian id
     uint32_t *ghist;             // [256][nb_sort]
     uint32_t *bsum;              // scan block sums
-    uint32_t *d_count;           // [0] = clamped pair count, [1] = raw count
+    uint32_t *d_count;           // [0] clamped pair count, [1] raw count, [2] Gaussian count (depth sort)
     uint2 *ranges;               // [max tiles]
     int sorted;                  // which of keys/vals holds the sorted pairs
     int tiles_x, tiles_y;        // of the last gs2_raster_fwd

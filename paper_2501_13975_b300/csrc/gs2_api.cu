@@ -146,7 +146,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         }
     };
     for (int i = 0; i < 2; ++i) {
-        A((void **)&c->keys[i], sizeof(unsigned long long) * (size_t)max_pairs);
+        A((void **)&c->keys[i], sizeof(uint32_t) * (size_t)max_pairs);
         A((void **)&c->vals[i], sizeof(uint32_t) * (size_t)max_pairs);
     }
     A((void **)&c->ghist, sizeof(uint32_t) * (256 * (size_t)SORT_BLOCKS + 256));  // + digit totals

@@ -6,7 +6,7 @@
 // allocate, or a real-time loop that must not pay allocation latency or risk
 // an out-of-memory failure halfway through a run.  This entry point needs no
 // gs2_ctx: its sorting scratch lives in one fixed-size array compiled into the
-// library (GS2_NOALLOC_SCRATCH_BYTES, about 13 MB), which every GPU that loads
+// library (GS2_NOALLOC_SCRATCH_BYTES, about 9 MB), which every GPU that loads
 // the library holds until the process exits.  The caller still passes the
 // projection buffer, the image and the raster state.
 //
@@ -22,7 +22,7 @@
 #define NA_SORT_BLOCKS (148 * 4)
 
 // carve-up of the scratch array (byte offsets, each 256-aligned)
-#define NA_KEYS_BYTES (8ull * GS2_NOALLOC_MAX_PAIRS)
+#define NA_KEYS_BYTES (4ull * GS2_NOALLOC_MAX_PAIRS)
 #define NA_VALS_BYTES (4ull * GS2_NOALLOC_MAX_PAIRS)
 #define NA_GHIST_BYTES (4ull * (256 * NA_SORT_BLOCKS + 256))
 #define NA_BSUM_BYTES (8ull * 1024)
@@ -86,8 +86,8 @@ extern "C" gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene 
     v.cfg = c;
     v.max_pairs = GS2_NOALLOC_MAX_PAIRS;
     v.nb_sort = NA_SORT_BLOCKS;
-    v.keys[0] = (unsigned long long *)(base + NA_OFF_KEYS0);
-    v.keys[1] = (unsigned long long *)(base + NA_OFF_KEYS1);
+    v.keys[0] = (uint32_t *)(base + NA_OFF_KEYS0);
+    v.keys[1] = (uint32_t *)(base + NA_OFF_KEYS1);
     v.vals[0] = (uint32_t *)(base + NA_OFF_VALS0);
     v.vals[1] = (uint32_t *)(base + NA_OFF_VALS1);
     v.ghist = (uint32_t *)(base + NA_OFF_GHIST);

@@ -284,6 +284,180 @@ __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_vi
     for (int i = 0; i < S; ++i) step[(size_t)(ch * S + i) * n + k] = x[i];
 }
 
+// Colour solve in the range of the view basis (exact algebra, no dense block):
+// H_ch = sum_v s_v b_v b_v^T = B S B^T with B = [b_1 .. b_V] (S x V, V <= 4).
+// With B = Q R (modified Gram-Schmidt, re-orthogonalised; Q has r <= V
+// orthonormal columns), H + d I = Q (d I_r + R S R^T) Q^T + d (I - Q Q^T), so
+// the damped block is positive definite iff d I_r + K (K = R S R^T) is, and
+// d > 0 when r < S; g = B a = Q R a lies in range(Q), hence
+// x = -Q (d I_r + K)^{-1} R a.  m = mean |diag H| as for the dense block.
+// Q and R are shared by the three channels.  One thread per Gaussian.
+template <int S>
+__global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float *__restrict__ B, int n_views,
+                                                        float mu0, int tries, float trust, float *step,
+                                                        int32_t *nfail) {
+    constexpr int VMAX = 4;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    const size_t slot = (size_t)(6 + S) * n;
+    float q[VMAX][S], a[VMAX][3], s[VMAX][3];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+        const bool on = v < n_views;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[v][c] = on ? B[v * slot + (size_t)c * n + k] : 0.f;
+            s[v][c] = on ? B[v * slot + (size_t)(3 + c) * n + k] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i) q[v][i] = on ? B[v * slot + (size_t)(6 + i) * n + k] : 0.f;
+    }
+    // m per channel from diag H = sum_v s_v b_v^2
+    float m[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            float d = 0.f;
+#pragma unroll
+            for (int v = 0; v < VMAX; ++v) d += s[v][c] * q[v][i] * q[v][i];
+            acc += fabsf(d);
+        }
+        m[c] = acc / (float)S;
+    }
+    // modified Gram-Schmidt with one re-orthogonalisation: B = Q R
+    float R[VMAX][VMAX];
+    bool keep[VMAX];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+#pragma unroll
+        for (int u = 0; u < VMAX; ++u) R[u][v] = 0.f;
+        float b2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < S; ++i) b2 += q[v][i] * q[v][i];
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+            for (int u = 0; u < VMAX; ++u) {
+                if (u >= v || !keep[u]) continue;
+                float d = 0.f;
+#pragma unroll
+                for (int i = 0; i < S; ++i) d += q[u][i] * q[v][i];
+                R[u][v] += d;
+#pragma unroll
+                for (int i = 0; i < S; ++i) q[v][i] -= d * q[u][i];
+            }
+        float nn = 0.f;
+#pragma unroll
+        for (int i = 0; i < S; ++i) nn += q[v][i] * q[v][i];
+        nn = sqrtf(nn);
+        keep[v] = (v < n_views) && nn > 1e-5f * sqrtf(b2) && nn > 0.f;
+        R[v][v] = keep[v] ? nn : 0.f;
+        const float inv = keep[v] ? 1.f / nn : 0.f;
+#pragma unroll
+        for (int i = 0; i < S; ++i) q[v][i] *= inv;
+    }
+    int r = 0;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) r += keep[v] ? 1 : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float out[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) out[i] = 0.f;
+        bool zero = true;
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v) zero = zero && a[v][c] == 0.f && s[v][c] == 0.f;
+        int st = 2;
+        if (!zero) {
+            // K = R S R^T and R a over the kept rows
+            float K[VMAX][VMAX], ra[VMAX];
+#pragma unroll
+            for (int u = 0; u < VMAX; ++u) {
+                float acc = 0.f;
+#pragma unroll
+                for (int v = 0; v < VMAX; ++v) acc += R[u][v] * a[v][c];
+                ra[u] = acc;
+#pragma unroll
+                for (int w = 0; w < VMAX; ++w) {
+                    float kk = 0.f;
+#pragma unroll
+                    for (int v = 0; v < VMAX; ++v) kk += R[u][v] * s[v][c] * R[w][v];
+                    K[u][w] = kk;
+                }
+            }
+            st = 1;
+            float mu = mu0;
+            for (int att = 0; att <= tries && st == 1; ++att, mu *= 10.f) {
+                const float dl = mu * m[c];
+                if (r < S && !(dl > 0.f)) continue;
+                // Cholesky of d I + K on the kept indices
+                float L[VMAX][VMAX];
+                bool ok = true;
+#pragma unroll
+                for (int j = 0; j < VMAX; ++j) {
+                    if (!keep[j] || !ok) continue;
+                    float d = dl + K[j][j];
+#pragma unroll
+                    for (int t = 0; t < VMAX; ++t)
+                        if (t < j && keep[t]) d -= L[j][t] * L[j][t];
+                    if (!(d > 0.f)) {
+                        ok = false;
+                        continue;
+                    }
+                    L[j][j] = sqrtf(d);
+#pragma unroll
+                    for (int i = 0; i < VMAX; ++i) {
+                        if (i <= j || !keep[i]) continue;
+                        float sm = K[i][j];
+#pragma unroll
+                        for (int t = 0; t < VMAX; ++t)
+                            if (t < j && keep[t]) sm -= L[i][t] * L[j][t];
+                        L[i][j] = sm / L[j][j];
+                    }
+                }
+                if (!ok) continue;
+                float y[VMAX], z[VMAX];
+#pragma unroll
+                for (int i = 0; i < VMAX; ++i) {
+                    if (!keep[i]) { y[i] = 0.f; continue; }
+                    float sm = -ra[i];
+#pragma unroll
+                    for (int t = 0; t < VMAX; ++t)
+                        if (t < i && keep[t]) sm -= L[i][t] * y[t];
+                    y[i] = sm / L[i][i];
+                }
+#pragma unroll
+                for (int i = VMAX - 1; i >= 0; --i) {
+                    if (!keep[i]) { z[i] = 0.f; continue; }
+                    float sm = y[i];
+#pragma unroll
+                    for (int t = 0; t < VMAX; ++t)
+                        if (t > i && keep[t]) sm -= L[t][i] * z[t];
+                    z[i] = sm / L[i][i];
+                }
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int u = 0; u < VMAX; ++u) acc += q[u][i] * z[u];
+                    out[i] = acc;
+                }
+                st = 0;
+            }
+            if (st == 0 && trust_scale(S, out, trust)) st = 1;
+            if (st != 0)
+#pragma unroll
+                for (int i = 0; i < S; ++i) out[i] = 0.f;
+        }
+        if (st == 1 && nfail) atomicAdd(nfail, 1);
+#pragma unroll
+        for (int i = 0; i < S; ++i) step[(size_t)(c * S + i) * n + k] = out[i];
+    }
+}
+
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, void *step, int32_t *n_failed, cudaStream_t st) {
     const int n = sc.n;
@@ -308,8 +482,21 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
                                            cfg.frac_to_boundary, s, n_failed);
         break;
     default:
-        k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,
-                                                          cfg.trust_color, s, n_failed);
+        if (n_views <= 4) {
+            const int gq = (n + 127) / 128;
+#define QR(SS) k_solve_color_qr<SS><<<gq, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries, \
+                                                        cfg.trust_color, s, n_failed)
+            switch (sc.S) {
+            case 1: QR(1); break;
+            case 4: QR(4); break;
+            case 9: QR(9); break;
+            default: QR(16); break;
+            }
+#undef QR
+        } else {
+            k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,
+                                                              cfg.trust_color, s, n_failed);
+        }
     }
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();

@@ -1,18 +1,20 @@
 // Tile binning and per-tile depth sort (Sec. 3: "sorted based on the current
 // camera depth"; the standard tile-splatting pipeline the paper builds on).
 //
-//  1. scan     exclusive prefix sum of tiles-touched per Gaussian (3 kernels,
-//              fixed grid); total pair count M kept on the device, clamped to
-//              the context capacity (overflow sets a status bit).
-//  2. emit     pair j of Gaussian k: key = (tile << 32) | depth bits, value = k,
-//              written in Gaussian order, so equal keys keep index order.
-//  3. sort     stable LSD radix sort over the significant key bits, 8-bit
-//              digits; each pass = block histograms, one scan over
-//              (digit, block), stable scatter.  The grid is fixed (NB blocks,
-//              each owning a contiguous chunk of ceil(M / NB) pairs) so that
-//              no host synchronisation is needed to size it.
-//  4. ranges   [start, end) of every tile in the sorted list.
-// Result: total order (tile, depth key, Gaussian index), bit-exact.
+//  1. depth   stable LSD radix sort of the Gaussians by FP32 depth bits (4
+//             passes over n; Gaussians that touch no tile get the largest key
+//             and sort last) -> rank order (key, index);
+//  2. scan    exclusive prefix sum of tiles-touched in rank order (3 kernels,
+//             fixed grid); total pair count M on the device, clamped to the
+//             context capacity (overflow sets a status bit);
+//  3. emit    pairs (tile id, Gaussian id) in rank order, one CTA per 256 ranks;
+//  4. tiles   stable LSD radix sort of the pairs by tile id (ceil(tile bits/8)
+//             passes, 2 at 1600x1040) -- stability keeps rank order per tile;
+//  5. ranges  [start, end) of every tile in the sorted list.
+// Result: total order (tile, depth key, Gaussian index), bit-exact.  Each
+// radix pass = block histograms over a fixed grid of NB CTAs (each owning a
+// contiguous chunk), a per-digit scan, and a stable scatter; element counts
+// live on the device, so no host synchronisation sizes anything.
 #include "common.cuh"
 
 #define SCAN_BLOCKS 1024
@@ -80,54 +82,70 @@ __global__ void k_scan_down(const uint32_t *__restrict__ x, int n, const unsigne
     }
 }
 
+// ---------------------------------------------------------------- depth keys
+// key = FP32 depth bits for a Gaussian that touches a tile, all ones otherwise
+// (positive FP32 bit patterns order like the values); value = index.  Thread 0
+// also publishes the element count n for the radix passes.
+__global__ void k_depth_keys(ProjView pv, int n, uint32_t *count_slot) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) *count_slot = (uint32_t)n;
+    if (k >= n) return;
+    pv.dk[0][k] = pv.touched[k] ? pv.key[k] : 0xFFFFFFFFu;
+    pv.dv[0][k] = (uint32_t)k;
+}
+
+// tiles-touched in rank order
+__global__ void k_gather_touched(ProjView pv, const uint32_t *__restrict__ order, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    pv.tsort[r] = pv.touched[order[r]];
+}
+
 // ---------------------------------------------------------------- emit
-// One CTA per 256 consecutive Gaussians: their pairs occupy one contiguous
-// output range, which the CTA writes with all threads striding (coalesced,
-// balanced even when one Gaussian covers thousands of tiles); a pair finds
-// its Gaussian by binary search over the CTA's offsets in shared memory.
-__global__ void __launch_bounds__(256) k_emit(ProjView pv, int n, int tiles_x, uint32_t cap,
-                                              unsigned long long *keys, uint32_t *vals, unsigned long long *stats) {
-    __shared__ uint32_t s_off[257];
+// One CTA per 256 consecutive ranks: their pairs occupy one contiguous output
+// range, which the CTA writes with all threads striding (coalesced, balanced
+// even when one Gaussian covers thousands of tiles); a pair finds its rank by
+// binary search over the CTA's offsets in shared memory.
+__global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__restrict__ order, int n, int tiles_x,
+                                              uint32_t cap, uint32_t *keys, uint32_t *vals,
+                                              unsigned long long *stats) {
+    __shared__ uint32_t s_off[256];
     __shared__ uint2 s_rect[256];
-    __shared__ uint32_t s_key[256];
+    __shared__ uint32_t s_id[256];
+    __shared__ uint32_t s_beg, s_end;
     const int t = threadIdx.x;
-    const int k = blockIdx.x * 256 + t;
-    const uint32_t cnt = (k < n) ? pv.touched[k] : 0u;
+    const int r = blockIdx.x * 256 + t;
+    const uint32_t id = (r < n) ? order[r] : 0u;
+    const uint32_t cnt = (r < n) ? pv.tsort[r] : 0u;
     if (stats) {  // visible-Gaussian count, one atomic per warp
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, cnt != 0u);
         if ((t & 31) == 0 && b) atomicAdd(&stats[1], (unsigned long long)__popc(b));
     }
-    const uint32_t off = (k < n) ? pv.offs[k] : 0u;
-    s_off[t] = (k < n) ? off : 0xFFFFFFFFu;
-    s_rect[t] = (k < n) ? pv.rect[k] : make_uint2(0u, 0u);
-    s_key[t] = (k < n) ? pv.key[k] : 0u;
+    const uint32_t off = (r < n) ? pv.offs[r] : 0u;
+    s_off[t] = (r < n) ? off : 0xFFFFFFFFu;
+    s_rect[t] = (r < n) ? pv.rect[id] : make_uint2(0u, 0u);
+    s_id[t] = id;
     const int last = min(n - 1, blockIdx.x * 256 + 255) - blockIdx.x * 256;
-    __shared__ uint32_t s_beg, s_end;
-    if (t == last) {
-        s_end = min(off + cnt, cap);  // offsets are already clamped to cap
-    }
+    if (t == last) s_end = min(off + cnt, cap);   // offsets are already clamped to cap
     if (t == 0) s_beg = off;
-    if (t == 0) s_off[256] = 0xFFFFFFFFu;
     __syncthreads();
     const uint32_t beg = s_beg, end = s_end;
     for (uint32_t j = beg + t; j < end; j += 256) {
-        // largest i with s_off[i] <= j
-        int lo = 0, hi = last;
+        int lo = 0, hi = last;   // largest i with s_off[i] <= j
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_off[mid] <= j) lo = mid;
             else hi = mid - 1;
         }
-        const uint2 r = s_rect[lo];
-        const uint32_t tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
+        const uint2 rc = s_rect[lo];
+        const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
         const uint32_t wdt = tx1 - tx0, rel = j - s_off[lo];
-        const uint32_t ty = ty0 + rel / wdt, tx = tx0 + rel % wdt;
-        keys[j] = ((unsigned long long)(ty * (uint32_t)tiles_x + tx) << 32) | (unsigned long long)s_key[lo];
-        vals[j] = (uint32_t)(blockIdx.x * 256 + lo);
+        keys[j] = (ty0 + rel / wdt) * (uint32_t)tiles_x + tx0 + rel % wdt;
+        vals[j] = s_id[lo];
     }
 }
 
-// ---------------------------------------------------------------- radix sort
+// ---------------------------------------------------------------- radix sort (32-bit keys, 32-bit values)
 __device__ __forceinline__ void chunk_of(uint32_t M, int nb, int b, uint32_t &beg, uint32_t &end) {
     const unsigned long long chunk = ((unsigned long long)M + nb - 1) / nb;
     const unsigned long long bb = min((unsigned long long)b * chunk, (unsigned long long)M);
@@ -135,15 +153,14 @@ __device__ __forceinline__ void chunk_of(uint32_t M, int nb, int b, uint32_t &be
     end = (uint32_t)min(bb + chunk, (unsigned long long)M);
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_hist(const unsigned long long *__restrict__ keys,
-                                                       const uint32_t *count, int shift, uint32_t *ghist, int nb) {
+__global__ void __launch_bounds__(SORT_THREADS) k_hist(const uint32_t *__restrict__ keys, const uint32_t *count,
+                                                       int shift, uint32_t *ghist, int nb) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0u;
     __syncthreads();
     uint32_t beg, end;
-    chunk_of(count[0], nb, blockIdx.x, beg, end);
-    for (uint32_t i = beg + threadIdx.x; i < end; i += SORT_THREADS)
-        atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    chunk_of(*count, nb, blockIdx.x, beg, end);
+    for (uint32_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
     __syncthreads();
     ghist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
@@ -151,7 +168,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_hist(const unsigned long long 
 // Per-digit scan of the block histograms: CTA d turns row d of ghist (one count
 // per sort block, coalesced) into exclusive prefixes and writes the digit's
 // total; each scatter block adds the exclusive scan of the 256 digit totals.
-__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *swarp, uint32_t &total) {
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *swarp, uint32_t &total) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -183,26 +200,25 @@ __global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *ghist, int nb, ui
     const int d = blockIdx.x, t = threadIdx.x;
     const uint32_t v = (t < nb) ? ghist[d * nb + t] : 0u;
     uint32_t tot;
-    const uint32_t ex = block_excl_scan_1024(v, swarp, tot);
+    const uint32_t ex = block_excl_scan(v, swarp, tot);
     if (t < nb) ghist[d * nb + t] = ex;
     if (t == 0) dtot[d] = tot;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_scatter(const unsigned long long *__restrict__ kin,
+__global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
-                                                          unsigned long long *__restrict__ kout,
-                                                          uint32_t *__restrict__ vout, const uint32_t *count,
-                                                          int shift, const uint32_t *ghist, int nb,
-                                                          const uint32_t *dtot) {
+                                                          uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                          const uint32_t *count, int shift,
+                                                          const uint32_t *ghist, int nb, const uint32_t *dtot) {
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[SORT_THREADS / 32][256];
     __shared__ uint32_t swarp[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t beg, end;
-    chunk_of(count[0], nb, blockIdx.x, beg, end);
+    chunk_of(*count, nb, blockIdx.x, beg, end);
     {
         uint32_t tot;
-        const uint32_t base = block_excl_scan_1024(dtot[t], swarp, tot);
+        const uint32_t base = block_excl_scan(dtot[t], swarp, tot);
         s_off[t] = base + ghist[t * nb + blockIdx.x];
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -210,15 +226,14 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const unsigned long lo
 #pragma unroll
         for (int i = 0; i < SORT_THREADS / 32; ++i) s_wc[i][t] = 0u;
         __syncthreads();
-        unsigned long long key[SORT_ROWS];
-        uint32_t val[SORT_ROWS], dig[SORT_ROWS], pos[SORT_ROWS];
+        uint32_t key[SORT_ROWS], val[SORT_ROWS], dig[SORT_ROWS], pos[SORT_ROWS];
 #pragma unroll
         for (int r = 0; r < SORT_ROWS; ++r) {
             const uint32_t idx = base + (uint32_t)(w * (32 * SORT_ROWS) + r * 32 + lane);
             const bool valid = idx < end;
-            key[r] = valid ? kin[idx] : 0ull;
+            key[r] = valid ? kin[idx] : 0u;
             val[r] = valid ? vin[idx] : 0u;
-            dig[r] = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+            dig[r] = valid ? ((key[r] >> shift) & 255u) : 256u;
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[r]);
             const uint32_t rank = __popc(peers & lt_mask);
             uint32_t cnt = 0u;
@@ -251,7 +266,26 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const unsigned long lo
     }
 }
 
-__global__ void k_ranges(const unsigned long long *__restrict__ keys, const uint32_t *count, uint2 *ranges,
+// `bits` significant key bits, ping-pong between (k[0], v[0]) and (k[1], v[1]);
+// returns the index of the buffer holding the result
+static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int bits, uint32_t *ghist, int nb,
+                      cudaStream_t st, int *launches) {
+    uint32_t *dtot = ghist + 256 * nb;
+    int cur = 0;
+    const int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_hist<<<nb, SORT_THREADS, 0, st>>>(k[cur], count, shift, ghist, nb);
+        k_digit_scan<<<256, 1024, 0, st>>>(ghist, nb, dtot);
+        k_scatter<<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist, nb,
+                                               dtot);
+        cur ^= 1;
+    }
+    *launches += 3 * passes;
+    return cur;
+}
+
+__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *count, uint2 *ranges,
                          unsigned long long *stats) {
     const uint32_t M = count[0];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -259,40 +293,42 @@ __global__ void k_ranges(const unsigned long long *__restrict__ keys, const uint
         stats[2] += 1ull;
     }
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        const uint32_t tile = (uint32_t)(keys[j] >> 32);
-        if (j == 0u || (uint32_t)(keys[j - 1] >> 32) != tile) ranges[tile].x = j;
-        if (j == M - 1u || (uint32_t)(keys[j + 1] >> 32) != tile) ranges[tile].y = j + 1u;
+        const uint32_t tile = keys[j];
+        if (j == 0u || keys[j - 1] != tile) ranges[tile].x = j;
+        if (j == M - 1u || keys[j + 1] != tile) ranges[tile].y = j + 1u;
     }
 }
 
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
                             unsigned long long *stats) {
     const uint32_t cap = (uint32_t)ctx->max_pairs;
-    unsigned long long *bsum = (unsigned long long *)ctx->bsum;
-    k_scan_reduce<<<SCAN_BLOCKS, 256, 0, st>>>(pv.touched, n, bsum);
-    k_scan_blocks<<<1, SCAN_BLOCKS, 0, st>>>(bsum, ctx->d_count, cap, ctx->d_status);
-    k_scan_down<<<SCAN_BLOCKS, 256, 0, st>>>(pv.touched, n, bsum, cap, pv.offs);
-    if (n > 0) k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, n, tiles_x, cap, ctx->keys[0], ctx->vals[0], stats);
-    const int ntiles = tiles_x * tiles_y;
-    int tile_bits = 0;
-    while ((1 << tile_bits) < ntiles) ++tile_bits;
-    const int bits = 32 + tile_bits;
-    const int passes = (bits + 7) / 8;
     const int nb = ctx->nb_sort;
-    uint32_t *dtot = ctx->ghist + 256 * nb;   // 256 digit totals after the histogram table
-    int cur = 0;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_hist<<<nb, SORT_THREADS, 0, st>>>(ctx->keys[cur], ctx->d_count, shift, ctx->ghist, nb);
-        k_digit_scan<<<256, 1024, 0, st>>>(ctx->ghist, nb, dtot);
-        k_scatter<<<nb, SORT_THREADS, 0, st>>>(ctx->keys[cur], ctx->vals[cur], ctx->keys[cur ^ 1],
-                                               ctx->vals[cur ^ 1], ctx->d_count, shift, ctx->ghist, nb, dtot);
-        cur ^= 1;
-    }
-    ctx->sorted = cur;
+    int launches = 0;
+    const int ntiles = tiles_x * tiles_y;
     cudaError_t e = cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
     if (e != cudaSuccess) return e;
-    k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[cur], ctx->d_count, ctx->ranges, stats);
-    GS2_COUNT_LAUNCH(3 + (n > 0) + 3 * passes + 1);
+    if (n == 0) {
+        ctx->sorted = 0;
+        return cudaMemsetAsync(ctx->d_count, 0, sizeof(uint32_t) * 2, st);
+    }
+    // 1. depth order of the Gaussians
+    k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(pv, n, ctx->d_count + 2);
+    const int dcur = radix_sort(pv.dk, pv.dv, ctx->d_count + 2, 32, ctx->ghist, nb, st, &launches);
+    const uint32_t *order = pv.dv[dcur];
+    // 2. tiles-touched in rank order, exclusive scan -> pair offsets and the pair count
+    k_gather_touched<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n);
+    unsigned long long *bsum = (unsigned long long *)ctx->bsum;
+    k_scan_reduce<<<SCAN_BLOCKS, 256, 0, st>>>(pv.tsort, n, bsum);
+    k_scan_blocks<<<1, SCAN_BLOCKS, 0, st>>>(bsum, ctx->d_count, cap, ctx->d_status);
+    k_scan_down<<<SCAN_BLOCKS, 256, 0, st>>>(pv.tsort, n, bsum, cap, pv.offs);
+    // 3. pairs in rank order
+    k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n, tiles_x, cap, ctx->keys[0], ctx->vals[0], stats);
+    // 4. stable sort by tile id
+    int tile_bits = 1;
+    while ((1 << tile_bits) < ntiles) ++tile_bits;
+    ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, tile_bits, ctx->ghist, nb, st, &launches);
+    // 5. tile ranges
+    k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, stats);
+    GS2_COUNT_LAUNCH(launches + 8);
     return cudaGetLastError();
 }
