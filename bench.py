@@ -141,7 +141,7 @@ def run_gpu(args, rank, world, local_rank):
     w, gt_host, train_host, cams = make_workload(args.workload, seed_offset=rank)
     ncam = len(cams)
     W, H = w["width"], w["height"]
-    ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"])
+    ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=args.precision))
     stream = torch.cuda.current_stream()
 
     # targets: ground-truth renders of every camera (resident in HBM)
@@ -268,10 +268,11 @@ def run_gpu(args, rank, world, local_rank):
         "metric": "Newton sweeps/s (1 primary + 3 secondaries, 5 attribute groups)",
         "value": round(value, 4), "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {w['desc']}", "gaussians": w["n"], "cameras": ncam,
                    "width": W, "height": H, "sh_degree": w["sh"], "knn_k": ctx.config["knn_k"],
                    "downsample": ctx.config["downsample"], "lambda_ssim": ctx.config["lambda_ssim"],
+                   "precision": "fp32" if args.precision == 0 else "mixed (FP64 accumulation, FP64 re-solve if cond > 1e6)",
                    "l2": "inputs larger than L2 (scene parameters and targets exceed 126 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": round(world * args.steps / (ms_e2e * 1e-3), 4), "unit": "sweeps/s",
@@ -404,6 +405,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=12)
     ap.add_argument("--ref-crop", type=int, default=8)
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gs2" else args.warmup
 

@@ -79,8 +79,8 @@ __device__ __forceinline__ void falloff_derivs(float G, float ca, float cb, floa
 // and the atomics are issued by many lanes at once instead of lane 0 alone.
 template <int P> struct Pad { static constexpr int PP = P <= 2 ? 2 : P <= 4 ? 4 : P <= 8 ? 8 : P <= 16 ? 16 : P <= 32 ? 32 : 64; };
 
-template <int P>
-__device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], int lane, float *__restrict__ zbuf,
+template <int P, typename ACC>
+__device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], int lane, ACC *__restrict__ zbuf,
                                                         int n, uint32_t k) {
     constexpr int PP = Pad<P>::PP;
     float v[PP];
@@ -113,17 +113,17 @@ __device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], in
 #pragma unroll
         for (int j = 0; j < (PP >= 32 ? PP / 32 : 1); ++j) {
             const int idx = off + j;
-            if (idx < P && v[j] != 0.f) atomicAdd(&zbuf[(size_t)idx * n + k], v[j]);
+            if (idx < P && v[j] != 0.f) atomicAdd(&zbuf[(size_t)idx * n + k], (ACC)v[j]);
         }
     }
 }
 
-template <int GROUP>
+template <int GROUP, typename ACC>
 __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict__ ranges,
                                                         const uint32_t *__restrict__ ids, ProjView pv, RasterView rv,
                                                         const float *__restrict__ E, const float *__restrict__ Hh,
                                                         int W, int H, int tiles_x, float amin, float amax,
-                                                        float *__restrict__ zbuf, int n) {
+                                                        ACC *__restrict__ zbuf, int n) {
     constexpr int P = Payload<GROUP>::P;
     __shared__ uint32_t sId[GS2_TILE_PIX];
     __shared__ float4 sA[GS2_TILE_PIX], sB[GS2_TILE_PIX], sC[GS2_TILE_PIX];
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
                 cb2 = alpha * C.z + (1.f - alpha) * cb2;
                 T = Tk;
             }
-            warp_reduce_scatter_add<P>(pl, lane, zbuf, n, sId[s]);
+            warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[s]);
         }
     }
 }
@@ -298,24 +298,26 @@ __device__ __forceinline__ void push_cov(const float T[2][3], const float S3[3][
     out[2] = TS[1][0] * T[1][0] + TS[1][1] * T[1][1] + TS[1][2] * T[1][2];
 }
 
-__global__ void k_epi_opacity(const ProjView pv, float *zbuf, int n, float *blocks) {
+template <typename ACC>
+__global__ void k_epi_opacity(const ProjView pv, ACC *zbuf, int n, float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || pv.touched[k] == 0u) return;
-    const float z0 = zbuf[k], z1 = zbuf[n + k];
+    const float z0 = (float)zbuf[k], z1 = (float)zbuf[n + k];
     blocks[k] += z0;
     blocks[n + k] += z1;
     zbuf[k] = 0.f;
     zbuf[n + k] = 0.f;
 }
 
-__global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, float *zbuf, float *slot) {
+template <typename ACC>
+__global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf, float *slot) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
     const bool vis = pv.touched[k] != 0u;
     float zz[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) zz[i] = vis ? zbuf[(size_t)i * n + k] : 0.f;
+    for (int i = 0; i < 6; ++i) zz[i] = vis ? (float)zbuf[(size_t)i * n + k] : 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) slot[(size_t)i * n + k] = zz[i];
     if (vis)
@@ -328,13 +330,14 @@ __global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, float *z
     for (int i = 0; i < sc.S; ++i) slot[(size_t)(6 + i) * n + k] = sh_norm(i) * phi[i];
 }
 
-__global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, float *zbuf, float *blocks) {
+template <typename ACC>
+__global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf, float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
     float z[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) z[i] = zbuf[(size_t)i * n + k];
+    for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
 #pragma unroll
     for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
     GaussGeo g;
@@ -367,13 +370,14 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, float *z
         }
 }
 
-__global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjView pv, float *zbuf, float *blocks) {
+template <typename ACC>
+__global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjView pv, ACC *zbuf, float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
     float z[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) z[i] = zbuf[(size_t)i * n + k];
+    for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
 #pragma unroll
     for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
     GaussGeo g;
@@ -442,7 +446,8 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
 //   Sigma_ab = f_a f_b u^2 Q_ab(tau) (+ low-pass), tau_a = clamp(t_a u),
 // V the camera-space 3D covariance (J V J^T written out); derivatives by the
 // chain rule through the intermediates (u, tau_x, tau_y).
-__global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, float *zbuf,
+template <typename ACC>
+__global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf,
                                                  float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const 
     float z[GS2_ZPOS];
     // all loads first, then the clears (interleaving them serialises the loads)
 #pragma unroll
-    for (int i = 0; i < GS2_ZPOS; ++i) z[i] = zbuf[(size_t)i * n + k];
+    for (int i = 0; i < GS2_ZPOS; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
 #pragma unroll
     for (int i = 0; i < GS2_ZPOS; ++i) zbuf[(size_t)i * n + k] = 0.f;
     GaussGeo g;
@@ -659,6 +664,43 @@ __global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const 
         for (int b = a; b < 3; ++b) blocks[(size_t)(3 + ut3(a, b)) * n + k] += Hp[a][b];
 }
 
+template <typename ACC>
+static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
+                           ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks, dim3 grid,
+                           const uint32_t *ids, bool prof, cudaStream_t st) {
+    const int n = sc.n;
+    ACC *zb = (ACC *)ctx->zbuf;
+#define ACC_LAUNCH(G)                                                                                             \
+    k_accum<G, ACC><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
+                                                   view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n)
+    switch (group) {
+    case GS2_POS: ACC_LAUNCH(GS2_POS); break;
+    case GS2_ROT: ACC_LAUNCH(GS2_ROT); break;
+    case GS2_SCALE: ACC_LAUNCH(GS2_SCALE); break;
+    case GS2_OPACITY: ACC_LAUNCH(GS2_OPACITY); break;
+    default: ACC_LAUNCH(GS2_COLOR); break;
+    }
+#undef ACC_LAUNCH
+    if (prof) {
+        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], st);
+        ctx->prof_n++;
+    }
+    GS2_COUNT_LAUNCH(2);
+    if (n == 0) return;
+    const int eg = (n + 255) / 256;
+    float *b = (float *)blocks;
+    switch (group) {
+    case GS2_POS: k_epi_pos<ACC><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+    case GS2_ROT: k_epi_rot<ACC><<<eg, 256, 0, st>>>(sc, view, primary, pv, zb, b); break;
+    case GS2_SCALE: k_epi_scale<ACC><<<eg, 256, 0, st>>>(sc, view, pv, zb, b); break;
+    case GS2_OPACITY: k_epi_opacity<ACC><<<eg, 256, 0, st>>>(pv, zb, n, b); break;
+    default: {
+        float *slot = b + (size_t)view_slot * (6 + sc.S) * n;
+        k_epi_color<ACC><<<eg, 256, 0, st>>>(sc, view, pv, zb, slot);
+    }
+    }
+}
+
 cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st) {
@@ -670,35 +712,9 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
         ctx->prof_group[ctx->prof_n] = group;
     }
-#define ACC(G)                                                                                                    \
-    k_accum<G><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h,   \
-                                              ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, ctx->zbuf, n)
-    switch (group) {
-    case GS2_POS: ACC(GS2_POS); break;
-    case GS2_ROT: ACC(GS2_ROT); break;
-    case GS2_SCALE: ACC(GS2_SCALE); break;
-    case GS2_OPACITY: ACC(GS2_OPACITY); break;
-    default: ACC(GS2_COLOR); break;
-    }
-#undef ACC
-    if (prof) {
-        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], st);
-        ctx->prof_n++;
-    }
-    GS2_COUNT_LAUNCH(2);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || n == 0) return e;
-    const int eg = (n + 255) / 256;
-    float *b = (float *)blocks;
-    switch (group) {
-    case GS2_POS: k_epi_pos<<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
-    case GS2_ROT: k_epi_rot<<<eg, 256, 0, st>>>(sc, view, primary, pv, ctx->zbuf, b); break;
-    case GS2_SCALE: k_epi_scale<<<eg, 256, 0, st>>>(sc, view, pv, ctx->zbuf, b); break;
-    case GS2_OPACITY: k_epi_opacity<<<eg, 256, 0, st>>>(pv, ctx->zbuf, n, b); break;
-    default: {
-        float *slot = b + (size_t)view_slot * (6 + sc.S) * n;
-        k_epi_color<<<eg, 256, 0, st>>>(sc, view, pv, ctx->zbuf, slot);
-    }
-    }
+    if (cfg.precision == 0)
+        launch_accum_t<float>(ctx, group, sc, view, primary, pv, rv, cfg, view_slot, blocks, grid, ids, prof, st);
+    else
+        launch_accum_t<double>(ctx, group, sc, view, primary, pv, rv, cfg, view_slot, blocks, grid, ids, prof, st);
     return cudaGetLastError();
 }

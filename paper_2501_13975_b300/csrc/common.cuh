@@ -147,6 +147,7 @@ struct gs2_ctx {
     void *sw_step;
     size_t sw_blocks_bytes, sw_step_bytes;
     uint32_t *d_status;
+    uint8_t *flags;              // [max_n] per-Gaussian flags (FP64 re-solve of the colour block)
     // opt-in profile of the accumulation kernel: CUDA events around every launch
     // and per-group pair / visible-Gaussian totals counted on the device
     int prof_on;
@@ -177,7 +178,7 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st);
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
-                         const gs2_config &cfg, void *step, int32_t *n_failed, cudaStream_t st);
+                         const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st);
 cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);

@@ -102,7 +102,7 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
-                    c->sw_step, c->d_status, c->d_stats};
+                    c->sw_step, c->d_status, c->d_stats, c->flags};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
@@ -153,7 +153,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A((void **)&c->bsum, sizeof(unsigned long long) * 1024);
     A((void **)&c->d_count, sizeof(uint32_t) * 4);
     A((void **)&c->ranges, sizeof(uint2) * (size_t)tiles);
-    A((void **)&c->zbuf, sizeof(float) * GS2_ZPOS * (size_t)max_n);
+    A((void **)&c->zbuf, sizeof(double) * GS2_ZPOS * (size_t)max_n);   // FP64 with precision = 1
     A((void **)&c->pix_e, sizeof(float) * 3 * P);
     A((void **)&c->pix_h, sizeof(float) * 3 * P);
     A(&c->sw_proj, proj_bytes_impl(max_n));
@@ -168,7 +168,8 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A(&c->sw_step, c->sw_step_bytes);
     A((void **)&c->d_status, sizeof(uint32_t) * 4);
     A((void **)&c->d_stats, sizeof(unsigned long long) * 5 * 4);
-    if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(float) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
+    A((void **)&c->flags, (size_t)max_n);
+    if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(double) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 20) == cudaSuccess;
@@ -335,7 +336,7 @@ extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *
     REQUIRE(ctx, blocks && step, GS2_ERR_ARG, "null buffer");
     REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
     RET_CUDA(ctx, launch_solve(group, blocks, n_views, make_devscene(scene), make_devcam(primary), ctx->cfg, step,
-                               n_failed, (cudaStream_t)stream));
+                               n_failed, ctx->flags, (cudaStream_t)stream));
     return GS2_OK;
 }
 
@@ -455,7 +456,7 @@ extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera
                          i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, st));
         }
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
-                                   ctx->sw_step, n_failed, st));
+                                   ctx->sw_step, n_failed, ctx->flags, st));
         RET_CUDA(ctx, launch_apply(group, ctx->sw_step, make_devscene(scene), make_devcam(primary), ctx->cfg, st));
     }
     ctx->stat_slot = 0;

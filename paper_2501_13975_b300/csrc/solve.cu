@@ -18,53 +18,76 @@
 // size <= 3 live in registers, the 16x16 colour factor in local memory.
 #include "common.cuh"
 
-template <int NMAX>
-__device__ int damped_solve(int N, const float *H, const float *g, float mu0, int tries, float *x) {
-    float m = 0.f, gz = 0.f;
+template <int NMAX, typename T>
+__device__ int damped_solve_t(int N, const float *H, const float *g, float mu0, int tries, T *x, float *kappa) {
+    T m = 0, gz = 0;
     for (int i = 0; i < N; ++i) {
-        m += fabsf(H[i * N + i]);
-        gz += fabsf(g[i]);
-        x[i] = 0.f;
+        m += fabs((T)H[i * N + i]);
+        gz += fabs((T)g[i]);
+        x[i] = 0;
     }
-    for (int i = 0; i < N * N; ++i) gz += fabsf(H[i]);
-    if (gz == 0.f) return 2;
-    m /= (float)N;
-    float mu = mu0;
-    float L[NMAX * NMAX];
-    for (int att = 0; att <= tries; ++att, mu *= 10.f) {
+    for (int i = 0; i < N * N; ++i) gz += fabs((T)H[i]);
+    if (kappa) *kappa = 1.f;
+    if (gz == 0) return 2;
+    m /= (T)N;
+    T mu = (T)mu0;
+    T L[NMAX * NMAX];
+    for (int att = 0; att <= tries; ++att, mu *= 10) {
         bool ok = true;
         for (int j = 0; j < N && ok; ++j) {
-            float d = H[j * N + j] + mu * m;
+            T d = (T)H[j * N + j] + mu * m;
             for (int k = 0; k < j; ++k) d -= L[j * N + k] * L[j * N + k];
-            if (!(d > 0.f)) {
+            if (!(d > 0)) {
                 ok = false;
                 break;
             }
-            const float ljj = sqrtf(d);
+            const T ljj = sqrt(d);
             L[j * N + j] = ljj;
-            const float il = 1.f / ljj;
+            const T il = 1 / ljj;
             for (int i = j + 1; i < N; ++i) {
-                float s = H[i * N + j];
-                for (int k = 0; k < j; ++k) s -= L[i * N + k] * L[j * N + k];
-                L[i * N + j] = s * il;
+                T sm = (T)H[i * N + j];
+                for (int k = 0; k < j; ++k) sm -= L[i * N + k] * L[j * N + k];
+                L[i * N + j] = sm * il;
             }
         }
         if (!ok) continue;
-        float y[NMAX];
+        T y[NMAX];
         for (int i = 0; i < N; ++i) {
-            float s = -g[i];
-            for (int k = 0; k < i; ++k) s -= L[i * N + k] * y[k];
-            y[i] = s / L[i * N + i];
+            T sm = -(T)g[i];
+            for (int k = 0; k < i; ++k) sm -= L[i * N + k] * y[k];
+            y[i] = sm / L[i * N + i];
         }
         for (int i = N - 1; i >= 0; --i) {
-            float s = y[i];
-            for (int k = i + 1; k < N; ++k) s -= L[k * N + i] * x[k];
-            x[i] = s / L[i * N + i];
+            T sm = y[i];
+            for (int k = i + 1; k < N; ++k) sm -= L[k * N + i] * x[k];
+            x[i] = sm / L[i * N + i];
+        }
+        if (kappa) {   // condition estimate from the factor: (max L_ii / min L_ii)^2
+            T lo = L[0], hi = L[0];
+            for (int i = 1; i < N; ++i) {
+                lo = fmin(lo, L[i * N + i]);
+                hi = fmax(hi, L[i * N + i]);
+            }
+            *kappa = (float)((hi / lo) * (hi / lo));
         }
         return 0;
     }
-    for (int i = 0; i < N; ++i) x[i] = 0.f;
+    for (int i = 0; i < N; ++i) x[i] = 0;
     return 1;
+}
+
+// FP32 damped solve; with mixed precision (precision = 1) a block whose
+// condition estimate exceeds 1e6 is solved again in FP64.
+template <int NMAX>
+__device__ int damped_solve(int N, const float *H, const float *g, float mu0, int tries, float *x, int precision) {
+    float kappa = 1.f;
+    int st = damped_solve_t<NMAX, float>(N, H, g, mu0, tries, x, &kappa);
+    if (precision != 0 && st != 2 && (st == 1 || kappa > 1e6f)) {
+        double xd[NMAX];
+        st = damped_solve_t<NMAX, double>(N, H, g, mu0, tries, xd, nullptr);
+        for (int i = 0; i < N; ++i) x[i] = (float)xd[i];
+    }
+    return st;
 }
 
 // Trust radius: a step longer than `radius` is scaled down to it (direction
@@ -93,7 +116,7 @@ __device__ __forceinline__ void unit_dir(const DevCam &cam, const float p[3], fl
 }
 
 __global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries, float trust,
-                            float *step, int32_t *nfail) {
+                            float *step, int32_t *nfail, int prec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -123,7 +146,7 @@ __global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B,
         }
     }
     float dv[2];
-    int st = damped_solve<2>(2, Hv, gv, mu0, tries, dv);
+    int st = damped_solve<2>(2, Hv, gv, mu0, tries, dv, prec);
     const float smax = fmaxf(sc.scale[k], fmaxf(sc.scale[n + k], sc.scale[2 * n + k]));
     if (st == 0 && trust_scale(2, dv, trust * smax)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
@@ -131,19 +154,19 @@ __global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B,
 }
 
 __global__ void k_solve_scalar(int n, const float *__restrict__ B, float mu0, int tries, float trust, float *step,
-                               int32_t *nfail) {
+                               int32_t *nfail, int prec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float g = B[k], h = B[n + k];
     float x;
-    int st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+    int st = damped_solve<1>(1, &h, &g, mu0, tries, &x, prec);
     if (st == 0 && trust_scale(1, &x, trust)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     step[k] = x;
 }
 
 __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float mu0, int tries, float barrier,
-                                float tau, float *step, int32_t *nfail) {
+                                float tau, float *step, int32_t *nfail, int prec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -153,7 +176,7 @@ __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float 
     if (!(g == 0.f && h == 0.f)) {
         g += barrier * (-1.f / sg + 1.f / (1.f - sg));
         h += barrier * (1.f / (sg * sg) + 1.f / ((1.f - sg) * (1.f - sg)));
-        st = damped_solve<1>(1, &h, &g, mu0, tries, &x);
+        st = damped_solve<1>(1, &h, &g, mu0, tries, &x, prec);
         if (st == 0 && trust_scale(1, &x, INFINITY)) st = 1;
     }
     if (st == 1 && nfail) atomicAdd(nfail, 1);
@@ -163,7 +186,7 @@ __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float 
 }
 
 __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries,
-                              float near_z, float trust, float *step, int32_t *nfail) {
+                              float near_z, float trust, float *step, int32_t *nfail, int prec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -247,7 +270,7 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
         }
     }
     float dl[2];
-    int st = damped_solve<2>(2, Hl, gl, mu0, tries, dl);
+    int st = damped_solve<2>(2, Hl, gl, mu0, tries, dl, prec);
     if (st == 0 && trust_scale(2, dl, INFINITY)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     for (int i = 0; i < 3; ++i) {
@@ -258,7 +281,7 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
 }
 
 __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_views, float mu0, int tries,
-                              float trust, float *step, int32_t *nfail) {
+                              float trust, float *step, int32_t *nfail, int prec) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n, S = sc.S;
     if (idx >= 3 * n) return;
@@ -278,7 +301,7 @@ __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_vi
             for (int j = 0; j < S; ++j) H[i * S + j] += s * b[i] * b[j];
         }
     }
-    int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x);
+    int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x, prec);
     if (st == 0 && trust_scale(S, x, trust)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     for (int i = 0; i < S; ++i) step[(size_t)(ch * S + i) * n + k] = x[i];
@@ -292,49 +315,41 @@ __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_vi
 // d > 0 when r < S; g = B a = Q R a lies in range(Q), hence
 // x = -Q (d I_r + K)^{-1} R a.  m = mean |diag H| as for the dense block.
 // Q and R are shared by the three channels.  One thread per Gaussian.
-template <int S>
-__global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float *__restrict__ B, int n_views,
-                                                        float mu0, int tries, float trust, float *step,
-                                                        int32_t *nfail) {
-    constexpr int VMAX = 4;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = sc.n;
-    if (k >= n) return;
-    const size_t slot = (size_t)(6 + S) * n;
-    float q[VMAX][S], a[VMAX][3], s[VMAX][3];
+#define QR_VMAX 4
+
+template <int S, typename T>
+__device__ void qr_color_solve(const float (&a)[QR_VMAX][3], const float (&s)[QR_VMAX][3], const float (&b)[QR_VMAX][S],
+                               int n_views, float mu0, int tries, float trust, unsigned chan_mask, float (&out)[3][S],
+                               int (&status)[3], float (&kappa)[3]) {
+    constexpr int VMAX = QR_VMAX;
+    T q[VMAX][S];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v) {
-        const bool on = v < n_views;
+    for (int v = 0; v < VMAX; ++v)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            a[v][c] = on ? B[v * slot + (size_t)c * n + k] : 0.f;
-            s[v][c] = on ? B[v * slot + (size_t)(3 + c) * n + k] : 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < S; ++i) q[v][i] = on ? B[v * slot + (size_t)(6 + i) * n + k] : 0.f;
-    }
+        for (int i = 0; i < S; ++i) q[v][i] = (T)b[v][i];
     // m per channel from diag H = sum_v s_v b_v^2
-    float m[3];
+    T m[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float acc = 0.f;
+        T acc = 0;
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            float d = 0.f;
+            T d = 0;
 #pragma unroll
-            for (int v = 0; v < VMAX; ++v) d += s[v][c] * q[v][i] * q[v][i];
-            acc += fabsf(d);
+            for (int v = 0; v < VMAX; ++v) d += (T)s[v][c] * q[v][i] * q[v][i];
+            acc += fabs(d);
         }
-        m[c] = acc / (float)S;
+        m[c] = acc / (T)S;
     }
     // modified Gram-Schmidt with one re-orthogonalisation: B = Q R
-    float R[VMAX][VMAX];
+    T R[VMAX][VMAX];
     bool keep[VMAX];
 #pragma unroll
     for (int v = 0; v < VMAX; ++v) {
+        keep[v] = false;
 #pragma unroll
-        for (int u = 0; u < VMAX; ++u) R[u][v] = 0.f;
-        float b2 = 0.f;
+        for (int u = 0; u < VMAX; ++u) R[u][v] = 0;
+        T b2 = 0;
 #pragma unroll
         for (int i = 0; i < S; ++i) b2 += q[v][i] * q[v][i];
 #pragma unroll
@@ -342,20 +357,20 @@ __global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float
 #pragma unroll
             for (int u = 0; u < VMAX; ++u) {
                 if (u >= v || !keep[u]) continue;
-                float d = 0.f;
+                T d = 0;
 #pragma unroll
                 for (int i = 0; i < S; ++i) d += q[u][i] * q[v][i];
                 R[u][v] += d;
 #pragma unroll
                 for (int i = 0; i < S; ++i) q[v][i] -= d * q[u][i];
             }
-        float nn = 0.f;
+        T nn = 0;
 #pragma unroll
         for (int i = 0; i < S; ++i) nn += q[v][i] * q[v][i];
-        nn = sqrtf(nn);
-        keep[v] = (v < n_views) && nn > 1e-5f * sqrtf(b2) && nn > 0.f;
-        R[v][v] = keep[v] ? nn : 0.f;
-        const float inv = keep[v] ? 1.f / nn : 0.f;
+        nn = sqrt(nn);
+        keep[v] = (v < n_views) && nn > (T)1e-5 * sqrt(b2) && nn > 0;
+        R[v][v] = keep[v] ? nn : (T)0;
+        const T inv = keep[v] ? (T)1 / nn : (T)0;
 #pragma unroll
         for (int i = 0; i < S; ++i) q[v][i] *= inv;
     }
@@ -364,54 +379,54 @@ __global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float
     for (int v = 0; v < VMAX; ++v) r += keep[v] ? 1 : 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float out[S];
+        if (!(chan_mask & (1u << c))) continue;
+        T x[S];
 #pragma unroll
-        for (int i = 0; i < S; ++i) out[i] = 0.f;
+        for (int i = 0; i < S; ++i) x[i] = 0;
+        kappa[c] = 1.f;
         bool zero = true;
 #pragma unroll
         for (int v = 0; v < VMAX; ++v) zero = zero && a[v][c] == 0.f && s[v][c] == 0.f;
         int st = 2;
         if (!zero) {
-            // K = R S R^T and R a over the kept rows
-            float K[VMAX][VMAX], ra[VMAX];
+            T K[VMAX][VMAX], ra[VMAX];   // K = R S R^T, R a
 #pragma unroll
             for (int u = 0; u < VMAX; ++u) {
-                float acc = 0.f;
+                T acc = 0;
 #pragma unroll
-                for (int v = 0; v < VMAX; ++v) acc += R[u][v] * a[v][c];
+                for (int v = 0; v < VMAX; ++v) acc += R[u][v] * (T)a[v][c];
                 ra[u] = acc;
 #pragma unroll
                 for (int w = 0; w < VMAX; ++w) {
-                    float kk = 0.f;
+                    T kk = 0;
 #pragma unroll
-                    for (int v = 0; v < VMAX; ++v) kk += R[u][v] * s[v][c] * R[w][v];
+                    for (int v = 0; v < VMAX; ++v) kk += R[u][v] * (T)s[v][c] * R[w][v];
                     K[u][w] = kk;
                 }
             }
             st = 1;
-            float mu = mu0;
-            for (int att = 0; att <= tries && st == 1; ++att, mu *= 10.f) {
-                const float dl = mu * m[c];
-                if (r < S && !(dl > 0.f)) continue;
-                // Cholesky of d I + K on the kept indices
-                float L[VMAX][VMAX];
+            T mu = (T)mu0;
+            for (int att = 0; att <= tries && st == 1; ++att, mu *= 10) {
+                const T dl = mu * m[c];
+                if (r < S && !(dl > 0)) continue;
+                T L[VMAX][VMAX];
                 bool ok = true;
 #pragma unroll
                 for (int j = 0; j < VMAX; ++j) {
                     if (!keep[j] || !ok) continue;
-                    float d = dl + K[j][j];
+                    T d = dl + K[j][j];
 #pragma unroll
                     for (int t = 0; t < VMAX; ++t)
                         if (t < j && keep[t]) d -= L[j][t] * L[j][t];
-                    if (!(d > 0.f)) {
+                    if (!(d > 0)) {
                         ok = false;
                         continue;
                     }
-                    L[j][j] = sqrtf(d);
+                    L[j][j] = sqrt(d);
 #pragma unroll
                     for (int i = 0; i < VMAX; ++i) {
                         if (i <= j || !keep[i]) continue;
-                        float sm = K[i][j];
+                        T sm = K[i][j];
 #pragma unroll
                         for (int t = 0; t < VMAX; ++t)
                             if (t < j && keep[t]) sm -= L[i][t] * L[j][t];
@@ -419,11 +434,13 @@ __global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float
                     }
                 }
                 if (!ok) continue;
-                float y[VMAX], z[VMAX];
+                T y[VMAX], z[VMAX], lo = (T)1e30, hi = 0;
 #pragma unroll
                 for (int i = 0; i < VMAX; ++i) {
-                    if (!keep[i]) { y[i] = 0.f; continue; }
-                    float sm = -ra[i];
+                    if (!keep[i]) { y[i] = 0; continue; }
+                    lo = fmin(lo, L[i][i]);
+                    hi = fmax(hi, L[i][i]);
+                    T sm = -ra[i];
 #pragma unroll
                     for (int t = 0; t < VMAX; ++t)
                         if (t < i && keep[t]) sm -= L[i][t] * y[t];
@@ -431,35 +448,118 @@ __global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float
                 }
 #pragma unroll
                 for (int i = VMAX - 1; i >= 0; --i) {
-                    if (!keep[i]) { z[i] = 0.f; continue; }
-                    float sm = y[i];
+                    if (!keep[i]) { z[i] = 0; continue; }
+                    T sm = y[i];
 #pragma unroll
                     for (int t = 0; t < VMAX; ++t)
                         if (t > i && keep[t]) sm -= L[t][i] * z[t];
                     z[i] = sm / L[i][i];
                 }
+                if (r < S) lo = fmin(lo, sqrt(dl));   // the complement contributes d
+                kappa[c] = (hi > 0 && lo > 0) ? (float)((hi / lo) * (hi / lo)) : 1e30f;
 #pragma unroll
                 for (int i = 0; i < S; ++i) {
-                    float acc = 0.f;
+                    T acc = 0;
 #pragma unroll
                     for (int u = 0; u < VMAX; ++u) acc += q[u][i] * z[u];
-                    out[i] = acc;
+                    x[i] = acc;
                 }
                 st = 0;
             }
-            if (st == 0 && trust_scale(S, out, trust)) st = 1;
-            if (st != 0)
-#pragma unroll
-                for (int i = 0; i < S; ++i) out[i] = 0.f;
         }
-        if (st == 1 && nfail) atomicAdd(nfail, 1);
 #pragma unroll
-        for (int i = 0; i < S; ++i) step[(size_t)(c * S + i) * n + k] = out[i];
+        for (int i = 0; i < S; ++i) out[c][i] = (float)x[i];
+        if (st == 0 && trust_scale(S, out[c], trust)) st = 1;
+        if (st != 0)
+#pragma unroll
+            for (int i = 0; i < S; ++i) out[c][i] = 0.f;
+        status[c] = st;
+    }
+}
+
+// Colour solve in the range of the view basis (exact algebra, no dense block):
+// H_ch = sum_v s_v b_v b_v^T = B S B^T with B = [b_1 .. b_V] (S x V, V <= 4).
+// With B = Q R (modified Gram-Schmidt, re-orthogonalised; Q has r <= V
+// orthonormal columns), H + d I = Q (d I_r + R S R^T) Q^T + d (I - Q Q^T), so
+// the damped block is positive definite iff d I_r + K (K = R S R^T) is, and
+// d > 0 when r < S; g = B a = Q R a lies in range(Q), hence
+// x = -Q (d I_r + K)^{-1} R a.  m = mean |diag H| as for the dense block.
+// Q and R are shared by the three channels.  One thread per Gaussian.  With
+// mixed precision, a channel whose condition estimate exceeds 1e6 (or whose
+// damping ladder failed) is solved again in FP64.
+template <int S>
+__device__ __forceinline__ void load_color_slots(const float *__restrict__ B, int n, int k, int n_views,
+                                                 float (&a)[QR_VMAX][3], float (&s)[QR_VMAX][3],
+                                                 float (&b)[QR_VMAX][S]) {
+    const size_t slot = (size_t)(6 + S) * n;
+#pragma unroll
+    for (int v = 0; v < QR_VMAX; ++v) {
+        const bool on = v < n_views;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[v][c] = on ? B[v * slot + (size_t)c * n + k] : 0.f;
+            s[v][c] = on ? B[v * slot + (size_t)(3 + c) * n + k] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i) b[v][i] = on ? B[v * slot + (size_t)(6 + i) * n + k] : 0.f;
+    }
+}
+
+// FP32 pass: one thread per Gaussian.  With mixed precision it leaves in
+// flags[k] the channels whose condition estimate exceeds 1e6 or whose ladder
+// failed; k_solve_color_qr64 solves those again in FP64.
+template <int S>
+__global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float *__restrict__ B, int n_views,
+                                                        float mu0, int tries, float trust, float *step,
+                                                        int32_t *nfail, int prec, uint8_t *flags) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    float a[QR_VMAX][3], s[QR_VMAX][3], b[QR_VMAX][S];
+    load_color_slots<S>(B, n, k, n_views, a, s, b);
+    float out[3][S], kappa[3];
+    int status[3];
+    qr_color_solve<S, float>(a, s, b, n_views, mu0, tries, trust, 7u, out, status, kappa);
+    unsigned redo = 0u;
+    if (prec != 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (status[c] == 1 || (status[c] == 0 && kappa[c] > 1e6f)) redo |= 1u << c;
+        flags[k] = (uint8_t)redo;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (status[c] == 1 && !(redo & (1u << c)) && nfail) atomicAdd(nfail, 1);
+#pragma unroll
+        for (int i = 0; i < S; ++i) step[(size_t)(c * S + i) * n + k] = out[c][i];
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(64) k_solve_color_qr64(DevScene sc, const float *__restrict__ B, int n_views,
+                                                         float mu0, int tries, float trust, float *step,
+                                                         int32_t *nfail, const uint8_t *__restrict__ flags) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n;
+    if (k >= n) return;
+    const unsigned redo = flags[k];
+    if (!redo) return;
+    float a[QR_VMAX][3], s[QR_VMAX][3], b[QR_VMAX][S];
+    load_color_slots<S>(B, n, k, n_views, a, s, b);
+    float out[3][S], kappa[3];
+    int status[3];
+    qr_color_solve<S, double>(a, s, b, n_views, mu0, tries, trust, redo, out, status, kappa);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (!(redo & (1u << c))) continue;
+        if (status[c] == 1 && nfail) atomicAdd(nfail, 1);
+#pragma unroll
+        for (int i = 0; i < S; ++i) step[(size_t)(c * S + i) * n + k] = out[c][i];
     }
 }
 
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
-                         const gs2_config &cfg, void *step, int32_t *n_failed, cudaStream_t st) {
+                         const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st) {
     const int n = sc.n;
     if (n == 0) return cudaSuccess;
     const float *B = (const float *)blocks;
@@ -468,24 +568,33 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
     switch (group) {
     case GS2_POS:
         k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_pos, s,
-                                       n_failed);
+                                       n_failed, cfg.precision);
         break;
     case GS2_ROT:
-        k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_rot, s, n_failed);
+        k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_rot, s, n_failed,
+                                          cfg.precision);
         break;
     case GS2_SCALE:
         k_solve_scale<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.near_z,
-                                         cfg.scale_trust, s, n_failed);
+                                         cfg.scale_trust, s, n_failed, cfg.precision);
         break;
     case GS2_OPACITY:
         k_solve_opacity<<<g, 256, 0, st>>>(sc, B, cfg.damping_mu0, cfg.damping_tries, cfg.barrier_alpha,
-                                           cfg.frac_to_boundary, s, n_failed);
+                                           cfg.frac_to_boundary, s, n_failed, cfg.precision);
         break;
     default:
         if (n_views <= 4) {
             const int gq = (n + 127) / 128;
-#define QR(SS) k_solve_color_qr<SS><<<gq, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries, \
-                                                        cfg.trust_color, s, n_failed)
+            const int prec = (cfg.precision != 0 && flags) ? 1 : 0;
+#define QR(SS)                                                                                                    \
+    do {                                                                                                          \
+        k_solve_color_qr<SS><<<gq, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,              \
+                                                 cfg.trust_color, s, n_failed, prec, flags);                      \
+        if (prec)                                                                                                 \
+            k_solve_color_qr64<SS><<<(n + 63) / 64, 64, 0, st>>>(sc, B, n_views, cfg.damping_mu0,                 \
+                                                                 cfg.damping_tries, cfg.trust_color, s, n_failed, \
+                                                                 flags);                                          \
+    } while (0)
             switch (sc.S) {
             case 1: QR(1); break;
             case 4: QR(4); break;
@@ -495,7 +604,7 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
 #undef QR
         } else {
             k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,
-                                                              cfg.trust_color, s, n_failed);
+                                                              cfg.trust_color, s, n_failed, cfg.precision);
         }
     }
     GS2_COUNT_LAUNCH(1);
