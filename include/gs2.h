@@ -228,6 +228,73 @@ gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
                      const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
                      int32_t *n_failed, gs2_stream stream);
 
+/* Learned step scale (an extension; the paper's local Newton step has step
+ * size 1, Sec. 4.2).  A 8-64-64-1 MLP (ReLU; BF16 weights, FP32 accumulation)
+ * maps 8 features of a Gaussian's plain damped step d to alpha = 2 sigmoid(y)
+ * in (0, 2); the step becomes alpha d, limited by the same trust radii and
+ * bounds as d.  The plain step stays wherever the features are unusable
+ * (|d| = 0, g . d >= 0, a non-finite value) or alpha is not finite.
+ *
+ * Records: float [GS2_REC_ROWS][n] per group and sweep: rows 0-7 the
+ * features, row 8 phi0 = g . d, row 9 the label alpha* in [0, 2] (the minimum
+ * of the quadratic line model through phi0 and phi1 = g_after . d, with
+ * g_after the group's gradient after all of its Gaussians stepped; 2 where
+ * that model is not convex) or -1 for an unusable record.  Features:
+ *   f0 log10 clamp(d^T H d / (-g.d), 1e-6, 1e6)   f1 cos(-g, d)
+ *   f2 log10 max(|d|/u, 1e-12), u = max(s) for position and scaling, else 1
+ *   f3 sigma   f4 log10 max(max(s), 1e-12)
+ *   f5 1 if a trust radius or bound is within 1e-3 of limiting d, else 0
+ *   f6 log10 clamp(|g| / (mean|diag H| |d|), 1e-6, 1e6)   f7 group / 4
+ * Parameters (GS2_MLP_NPARAM words): W1 [64][8], b1 [64], W2 [64][64],
+ * b2 [64], W3 [64], b3. */
+#define GS2_MLP_NFEAT 8
+#define GS2_MLP_HIDDEN 64
+#define GS2_MLP_NPARAM 4801
+#define GS2_MLP_GRID 148
+#define GS2_REC_ROWS 10
+
+/* Install (device, GS2_MLP_NPARAM BF16 words, read at every solve; the caller
+ * keeps it alive) or remove (NULL) the step-scale network: gs2_solve_step and
+ * gs2_sweep then scale each step after the plain solve. */
+gs2_status gs2_set_step_model(gs2_ctx *ctx, const uint16_t *w_bf16);
+
+/* Records of the plain step: features and phi0 of step (from blocks, as
+ * passed to gs2_solve_step), label row set to 0 (pending) or -1 (unusable).
+ * records: device float [GS2_REC_ROWS][scene->n] out. */
+gs2_status gs2_step_records(gs2_ctx *ctx, gs2_group group, const void *blocks, int32_t n_views,
+                            const gs2_scene *scene, const void *step, float *records, gs2_stream stream);
+/* Labels: blocks_after are the group's blocks accumulated over the same views
+ * after the step was applied; fills row 9 of the pending records. */
+gs2_status gs2_step_labels(gs2_ctx *ctx, gs2_group group, const void *blocks_after, int32_t n_views,
+                           const gs2_scene *scene, const void *step, float *records, gs2_stream stream);
+/* gs2_sweep of the plain method (an installed step model is not used) that
+ * also logs every group's records: after a group's step is applied its views
+ * are accumulated again for the labels.  records: device float
+ * [5][GS2_REC_ROWS][n] out.  The scene ends as after gs2_sweep. */
+gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                            const float *const *targets, const int32_t *knn, int32_t t, float *records,
+                            double *losses_out, int32_t *n_failed, gs2_stream stream);
+
+/* Network training and evaluation on record buffers made of chunks
+ * [GS2_REC_ROWS][chunk_n] (row j of record i at
+ * records[(i / chunk_n) GS2_REC_ROWS chunk_n + j chunk_n + i % chunk_n]);
+ * record r of a batch is idx[r] (device int64, NULL: r).
+ * gs2_mlp_forward: out[r] = alpha(features of record r), device float [nrec].
+ * gs2_mlp_grad: loss 1/2 sum (alpha - alpha*)^2 over the usable records
+ *   (label >= 0); partial: device float [GS2_MLP_GRID][GS2_MLP_NPARAM] out,
+ *   per-CTA gradient sums w.r.t. the BF16 weights' values; stats: device
+ *   double [GS2_MLP_GRID][2] out, per-CTA (loss, usable count).
+ * gs2_mlp_adam: one Adam step of the FP32 master weights with the mean
+ *   gradient (sum of partial rows / usable count; no change if the count is
+ *   0), then w_bf16 = round-to-nearest-even BF16 of master.  m, v: device
+ *   float [GS2_MLP_NPARAM] moments; step >= 1 is the Adam step number. */
+gs2_status gs2_mlp_forward(const uint16_t *w_bf16, const float *records, int64_t chunk_n, const int64_t *idx,
+                           int64_t nrec, float *out, gs2_stream stream);
+gs2_status gs2_mlp_grad(const uint16_t *w_bf16, const float *records, int64_t chunk_n, const int64_t *idx,
+                        int64_t nrec, float *partial, double *stats, gs2_stream stream);
+gs2_status gs2_mlp_adam(float *master, uint16_t *w_bf16, const float *partial, const double *stats, float *m,
+                        float *v, int32_t step, float lr, float beta1, float beta2, float eps, gs2_stream stream);
+
 /* Instrumentation.
  * gs2_launch_count: kernels launched by this library in this process so far.
  * gs2_profile(ctx, 1): from now on record CUDA events around every

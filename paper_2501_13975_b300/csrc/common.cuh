@@ -148,6 +148,7 @@ struct gs2_ctx {
     size_t sw_blocks_bytes, sw_step_bytes;
     uint32_t *d_status;
     uint8_t *flags;              // [max_n] per-Gaussian flags (FP64 re-solve of the colour block)
+    const void *mlp_w;           // installed step-scale network (BF16, caller-owned) or NULL
     // opt-in profile of the accumulation kernel: CUDA events around every launch
     // and per-group pair / visible-Gaussian totals counted on the device
     int prof_on;
@@ -182,6 +183,12 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
 cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);
+cudaError_t launch_step_records(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
+                                const gs2_config &cfg, float *rec, cudaStream_t st);
+cudaError_t launch_step_labels(int group, const void *blocks_after, int n_views, const DevScene &sc,
+                               const void *step, float *rec, cudaStream_t st);
+cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, const DevScene &sc, void *step,
+                                 const gs2_config &cfg, const void *w, cudaStream_t st);
 cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t st);
 
 // --------------------------------------------------------------------------

@@ -337,6 +337,41 @@ extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *
     REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
     RET_CUDA(ctx, launch_solve(group, blocks, n_views, make_devscene(scene), make_devcam(primary), ctx->cfg, step,
                                n_failed, ctx->flags, (cudaStream_t)stream));
+    RET_CUDA(ctx, launch_learned_scale(group, blocks, n_views, make_devscene(scene), step, ctx->cfg, ctx->mlp_w,
+                                       (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_set_step_model(gs2_ctx *ctx, const uint16_t *w_bf16) {
+    if (!ctx) return GS2_ERR_ARG;
+    ctx->mlp_w = w_bf16;
+    return GS2_OK;
+}
+
+static gs2_status check_records_args(gs2_ctx *ctx, int group, const void *blocks, int n_views,
+                                     const gs2_scene *scene, const void *step, const float *records) {
+    REQUIRE(ctx, group >= GS2_POS && group <= GS2_COLOR, GS2_ERR_ARG, "bad group");
+    TRY(check_scene(ctx, scene));
+    REQUIRE(ctx, blocks && step && records, GS2_ERR_ARG, "null buffer");
+    REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_step_records(gs2_ctx *ctx, gs2_group group, const void *blocks, int32_t n_views,
+                                       const gs2_scene *scene, const void *step, float *records, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    TRY(check_records_args(ctx, group, blocks, n_views, scene, step, records));
+    RET_CUDA(ctx, launch_step_records(group, blocks, n_views, make_devscene(scene), step, ctx->cfg, records,
+                                      (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_step_labels(gs2_ctx *ctx, gs2_group group, const void *blocks_after, int32_t n_views,
+                                      const gs2_scene *scene, const void *step, float *records, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    TRY(check_records_args(ctx, group, blocks_after, n_views, scene, step, records));
+    RET_CUDA(ctx, launch_step_labels(group, blocks_after, n_views, make_devscene(scene), step, records,
+                                     (cudaStream_t)stream));
     return GS2_OK;
 }
 
@@ -409,15 +444,16 @@ extern "C" gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const f
     return GS2_OK;
 }
 
-extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
-                                const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
-                                int32_t *n_failed, gs2_stream stream) {
-    if (!ctx) return GS2_ERR_ARG;
+// one sweep; with records != NULL the plain method's records of every group
+// are logged (the step model is then not applied)
+static gs2_status sweep_impl(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                             const float *const *targets, const int32_t *knn, int32_t t, float *records,
+                             double *losses_out, int32_t *n_failed, cudaStream_t stream) {
     TRY(check_scene(ctx, scene));
     REQUIRE(ctx, cams && targets && ncam >= 1 && t >= 0 && t < ncam, GS2_ERR_ARG, "bad cameras or primary index");
     const int K = ctx->cfg.knn_k, f = ctx->cfg.downsample;
     REQUIRE(ctx, K == 0 || knn != nullptr, GS2_ERR_ARG, "knn table is null");
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t st = stream;
     const int nv = 1 + K;
     int vid[17];
     gs2_camera vcam[17];
@@ -455,12 +491,47 @@ extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera
             TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image, vtgt[i],
                          i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, st));
         }
+        const size_t bbytes = blocks_bytes_impl(group, scene->n, scene->sh_degree, nv);
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
                                    ctx->sw_step, n_failed, ctx->flags, st));
+        float *rec = records ? records + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;
+        if (rec)
+            RET_CUDA(ctx, launch_step_records(group, ctx->sw_blocks, nv, make_devscene(scene), ctx->sw_step, ctx->cfg,
+                                              rec, st));
+        else
+            RET_CUDA(ctx, launch_learned_scale(group, ctx->sw_blocks, nv, make_devscene(scene), ctx->sw_step,
+                                               ctx->cfg, ctx->mlp_w, st));
         RET_CUDA(ctx, launch_apply(group, ctx->sw_step, make_devscene(scene), make_devcam(primary), ctx->cfg, st));
+        if (rec) {
+            // the same views again at the new parameters: g_after for the labels
+            RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, bbytes, st));
+            for (int i = 0; i < nv; ++i) {
+                if (vid[i] < 0) continue;
+                TRY(do_project(ctx, scene, &vcam[i], ctx->sw_proj, st));
+                TRY(do_raster(ctx, scene->n, &vcam[i], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st));
+                TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image,
+                             vtgt[i], i, ctx->sw_blocks, nullptr, st));
+            }
+            RET_CUDA(ctx, launch_step_labels(group, ctx->sw_blocks, nv, make_devscene(scene), ctx->sw_step, rec, st));
+        }
     }
     ctx->stat_slot = 0;
     return GS2_OK;
+}
+
+extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                                const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
+                                int32_t *n_failed, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    return sweep_impl(ctx, scene, cams, ncam, targets, knn, t, nullptr, losses_out, n_failed, (cudaStream_t)stream);
+}
+
+extern "C" gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                                       const float *const *targets, const int32_t *knn, int32_t t, float *records,
+                                       double *losses_out, int32_t *n_failed, gs2_stream stream) {
+    if (!ctx) return GS2_ERR_ARG;
+    REQUIRE(ctx, records != nullptr, GS2_ERR_ARG, "records is null");
+    return sweep_impl(ctx, scene, cams, ncam, targets, knn, t, records, losses_out, n_failed, (cudaStream_t)stream);
 }
 
 extern "C" uint64_t gs2_launch_count(void) { return g_gs2_launches.load(); }

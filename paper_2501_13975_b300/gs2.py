@@ -78,6 +78,15 @@ _sigs = {
     "gs2_camera_knn": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32, _vp]),
     "gs2_sweep": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
                             C.c_int32, _vp, _vp, _vp]),
+    "gs2_sweep_logged": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
+                                   C.c_int32, _vp, _vp, _vp, _vp]),
+    "gs2_set_step_model": (C.c_int, [_vp, _vp]),
+    "gs2_step_records": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), _vp, _vp, _vp]),
+    "gs2_step_labels": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), _vp, _vp, _vp]),
+    "gs2_mlp_forward": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp]),
+    "gs2_mlp_grad": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, _vp]),
+    "gs2_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.c_float, C.c_float,
+                               C.c_float, _vp]),
     "gs2_launch_count": (C.c_uint64, []),
     "gs2_profile": (C.c_int, [_vp, C.c_int32]),
     "gs2_profile_read": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -93,6 +102,9 @@ for _name, (_res, _args) in _sigs.items():
     _f.argtypes = _args
 
 EXPORTED = tuple(_sigs)
+
+# learned step scale (include/gs2.h)
+MLP_NFEAT, MLP_HIDDEN, MLP_NPARAM, MLP_GRID, REC_ROWS = 8, 64, 4801, 148, 10
 
 
 class GS2Error(RuntimeError):
@@ -321,6 +333,40 @@ class Context:
         self._ok(_lib.gs2_sweep(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
                                 _ptr(losses), _ptr(n_failed), _stream(stream)), "gs2_sweep")
 
+    def sweep_logged(self, scene: DeviceScene, cams, targets, knn, t, records=None, losses=None, n_failed=None,
+                     stream=None):
+        """Plain sweep that logs the records of every group: float [5][REC_ROWS][n]."""
+        if records is None:
+            records = torch.empty((5, REC_ROWS, scene.n), dtype=torch.float32, device="cuda")
+        arr = (Camera_ * len(cams))(*[camera_struct(c) for c in cams])
+        tp = (_vp * len(targets))(*[_ptr(x) for x in targets])
+        kt = np.ascontiguousarray(knn, np.int32)
+        s = scene.struct()
+        self._ok(_lib.gs2_sweep_logged(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
+                                       _ptr(records), _ptr(losses), _ptr(n_failed), _stream(stream)),
+                 "gs2_sweep_logged")
+        return records
+
+    def set_step_model(self, w_bf16):
+        """Install (a device int16/uint16 tensor of MLP_NPARAM BF16 words, kept
+        alive by this context) or remove (None) the step-scale network."""
+        self._step_model = w_bf16
+        self._ok(_lib.gs2_set_step_model(self.h, _ptr(w_bf16)), "gs2_set_step_model")
+
+    def step_records(self, group, blocks, n_views, scene: DeviceScene, step, records=None, stream=None):
+        if records is None:
+            records = torch.empty((REC_ROWS, scene.n), dtype=torch.float32, device="cuda")
+        s = scene.struct()
+        self._ok(_lib.gs2_step_records(self.h, int(group), _ptr(blocks), int(n_views), C.byref(s), _ptr(step),
+                                       _ptr(records), _stream(stream)), "gs2_step_records")
+        return records
+
+    def step_labels(self, group, blocks_after, n_views, scene: DeviceScene, step, records, stream=None):
+        s = scene.struct()
+        self._ok(_lib.gs2_step_labels(self.h, int(group), _ptr(blocks_after), int(n_views), C.byref(s), _ptr(step),
+                                      _ptr(records), _stream(stream)), "gs2_step_labels")
+        return records
+
     def profile(self, enable: bool):
         self._ok(_lib.gs2_profile(self.h, 1 if enable else 0), "gs2_profile")
 
@@ -361,6 +407,32 @@ def render_noalloc(scene: DeviceScene, cam, proj, image, raster_state, status=No
                                  _ptr(raster_state), _ptr(status), _stream(stream))
     if st != 0:
         raise GS2Error(f"gs2_render_noalloc: {STATUS.get(st, st)}")
+
+
+def _mlp_call(st, what):
+    if st != 0:
+        raise GS2Error(f"{what}: {STATUS.get(st, st)}")
+
+
+def mlp_forward(w_bf16, records, chunk_n, nrec, idx=None, out=None, stream=None):
+    """alpha of records (chunks [REC_ROWS][chunk_n]); out: device float [nrec]."""
+    if out is None:
+        out = torch.empty(max(int(nrec), 1), dtype=torch.float32, device="cuda")
+    _mlp_call(_lib.gs2_mlp_forward(_ptr(w_bf16), _ptr(records), int(chunk_n), _ptr(idx), int(nrec), _ptr(out),
+                                   _stream(stream)), "gs2_mlp_forward")
+    return out[: int(nrec)]
+
+
+def mlp_grad(w_bf16, records, chunk_n, nrec, partial, stats, idx=None, stream=None):
+    """Per-CTA gradient sums [MLP_GRID][MLP_NPARAM] and (loss, count) [MLP_GRID][2]."""
+    _mlp_call(_lib.gs2_mlp_grad(_ptr(w_bf16), _ptr(records), int(chunk_n), _ptr(idx), int(nrec), _ptr(partial),
+                                _ptr(stats), _stream(stream)), "gs2_mlp_grad")
+
+
+def mlp_adam(master, w_bf16, partial, stats, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _mlp_call(_lib.gs2_mlp_adam(_ptr(master), _ptr(w_bf16), _ptr(partial), _ptr(stats), _ptr(m), _ptr(v),
+                                int(step), float(lr), float(beta1), float(beta2), float(eps), _stream(stream)),
+              "gs2_mlp_adam")
 
 
 def launch_count() -> int:

@@ -223,3 +223,20 @@ def procedural_targets(count: int, width: int, height: int, seed: int = 11) -> n
                 acc += np.float32(0.12) * np.cos(kx * xx + ky * yy + ph).astype(np.float32)
             out[i, c] = np.clip(acc, 0.0, 1.0)
     return out
+
+
+def mlp_init(seed: int = 20, nfeat: int = 8, hidden: int = 64, out_scale: float = 0.1):
+    """Initial parameters of the 8-64-64-1 step-scale network, packed as
+    W1 [64][8], b1 [64], W2 [64][64], b2 [64], W3 [64], b3: W1, W2 normal with
+    variance 2 / fan-in, W3 the same times out_scale, biases 0 (the output
+    then starts near y = 0, alpha = 1: the plain step).  Values are truncated
+    to BF16-representable FP32 numbers, so the FP32 master copy and the BF16
+    copy hold the same values.  Returns (master float32 [P], bits uint16 [P])."""
+    rng = _rng(seed)
+    w1 = rng.normal(0.0, math.sqrt(2.0 / nfeat), hidden * nfeat)
+    w2 = rng.normal(0.0, math.sqrt(2.0 / hidden), hidden * hidden)
+    w3 = rng.normal(0.0, out_scale * math.sqrt(2.0 / hidden), hidden)
+    p = np.concatenate([w1, np.zeros(hidden), w2, np.zeros(hidden), w3, np.zeros(1)]).astype(np.float32)
+    bits = (p.view(np.uint32) >> np.uint32(16)).astype(np.uint16)
+    master = (bits.astype(np.uint32) << np.uint32(16)).view(np.float32)
+    return master, bits
