@@ -10,15 +10,23 @@ Definitions (g, H: a Gaussian's group block; d: its plain damped step):
   record  f0 = log10 clamp(d^T H d / (-g.d), 1e-6, 1e6)
           f1 = cos(-g, d)
           f2 = log10 max(|d| / u, 1e-12), u = max(s) for position/scaling, else 1
-          f3 = sigma, f4 = log10 max(max(s), 1e-12)
+          f3 = sigma
+          f4 = clamp(g_p.d / g.d, -4, 4): the share of the predicted decrease
+               that the primary view's own gradient g_p gives (1 without g_p)
           f5 = 1 if a trust radius or bound is within 1e-3 of limiting d
           f6 = log10 clamp(|g| / (mean|diag H| |d|), 1e-6, 1e6)
           f7 = group / 4
           phi0 = g.d; usable iff |d| > 0, phi0 < 0 and all features finite
-  label   phi1 = g_after.d with g_after the group's gradient once every
-          Gaussian of the group took its step; the quadratic through phi0 and
-          phi1 along d has its minimum at alpha* = phi0 / (phi0 - phi1) (2 when
-          phi1 <= phi0, the model then being concave), clipped to [0, 2]
+  label   of a loss L_lab along d: phi0 = grad L_lab . d before the step,
+          phi1 = grad L_lab . d once every Gaussian of the group took its
+          step; alpha* = 0 if phi0 >= 0 (d does not descend L_lab: the step
+          is rejected), else the minimum of the quadratic through phi0 and
+          phi1, phi0 / (phi0 - phi1) (2 when phi1 <= phi0, the model then
+          being concave), clipped to [0, 2].  With L_lab the local loss (the
+          views the step was solved from) phi0 is the record's own g.d; the
+          logged sweep takes L_lab = the loss summed over every training view
+          at full resolution, whose increase is what the paper calls
+          overshoot (Sec. overshoot).
   network y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, alpha = 2 sigmoid(y)
   loss    1/2 sum over usable records (alpha - alpha*)^2
   Adam    m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
@@ -164,10 +172,11 @@ def _as_vectors(group, g, H, d, S):
     return (np.asarray(g, np.float64).reshape(3 * S, n).T, Hf, np.asarray(d, np.float64).reshape(3 * S, n).T)
 
 
-def step_records(group, g, H, d, scene, cfg):
+def step_records(group, g, H, d, scene, cfg, g_primary=None):
     """Records [REC_ROWS][n] (label row 0 = pending, -1 = unusable) of the
     plain step d (oracle layouts: g, H, d as O.accum / O.solve give them) at
-    the scene's current parameters."""
+    the scene's current parameters; g_primary: the primary view's own
+    gradient (same layout as g), None for f4 = 1."""
     cfg = O.default_config(**(cfg or {}))
     sc = O.scene_handle(scene)
     n, S = sc.n, O.sh_count(sc.sh_degree)
@@ -201,7 +210,11 @@ def step_records(group, g, H, d, scene, cfg):
         f[1] = np.where(gn * dn > 0, -gd / np.where(gn * dn > 0, gn * dn, 1.0), 0.0)
         f[2] = np.log10(np.maximum(dn / u, 1e-12))
         f[3] = sigma
-        f[4] = np.log10(np.maximum(smax, 1e-12))
+        if g_primary is None:
+            f[4] = 1.0
+        else:
+            gpd = np.sum(np.asarray(g_primary, np.float64).reshape(-1, n) * dv.T, axis=0)
+            f[4] = np.where(gd < 0, np.clip(gpd / np.where(gd < 0, gd, -1.0), -4.0, 4.0), 0.0)
         f[5] = clipped.astype(np.float64)
         den = hd * dn
         f[6] = np.log10(np.clip(np.where(den > 0, gn / np.where(den > 0, den, 1.0), 1e6), 1e-6, 1e6))
@@ -214,29 +227,39 @@ def step_records(group, g, H, d, scene, cfg):
     return rec
 
 
-def step_labels(group, g_after, d, rec, S=1):
-    """Fills the label row of pending records from the after-step gradient."""
+def step_labels(group, g_after, d, rec, S=1, phi0=None):
+    """Fills the label row of pending records: phi1 = g_after . d and phi0 =
+    the record's row 8, or the given phi0 (then also written to row 8)."""
     n = rec.shape[1]
     gv = np.asarray(g_after, np.float64).reshape(-1, n)
     dv = np.asarray(d, np.float64).reshape(-1, n)
-    phi0 = rec[NF]
+    out = rec.copy()
+    if phi0 is not None:
+        out[NF] = phi0
+    phi0 = out[NF]
     phi1 = np.sum(gv * dv, axis=0)
     den = phi0 - phi1
     with np.errstate(divide="ignore", invalid="ignore"):
         a = np.where(den < 0, phi0 / np.where(den < 0, den, -1.0), 2.0)
-    out = rec.copy()
+    a = np.where(phi0 >= 0, 0.0, a)
     pend = rec[NF + 1] >= 0
     out[NF + 1] = np.where(pend, np.where(np.isfinite(a), np.clip(a, 0.0, 2.0), -1.0), rec[NF + 1])
     return out
 
 
-def learned_step(group, g, H, d, scene, cfg, p):
+def phi(group, g, d):
+    """g . d per Gaussian (any layout of g and d with n last)."""
+    n = np.asarray(d).shape[-1]
+    return np.sum(np.asarray(g, np.float64).reshape(-1, n) * np.asarray(d, np.float64).reshape(-1, n), axis=0)
+
+
+def learned_step(group, g, H, d, scene, cfg, p, g_primary=None):
     """alpha d (alpha from the network on the step's record) inside the plain
     step's trust radii and bounds; d where the record is unusable."""
     cfg = O.default_config(**(cfg or {}))
     sc = O.scene_handle(scene)
     n, S = sc.n, O.sh_count(sc.sh_degree)
-    rec = step_records(group, g, H, d, scene, cfg)
+    rec = step_records(group, g, H, d, scene, cfg, g_primary)
     ok = rec[NF + 1] >= 0
     a, _ = mlp_forward(p, np.where(ok[:, None], rec[:NF].T, 0.0))
     ok &= np.isfinite(a)
@@ -291,19 +314,24 @@ def _blocks(group, scene, views, primary, cfg):
 
 def sweep_logged(scene, cams, targets, knn_table, t, cfg):
     """The oracle's sweep (same order as O.sweep) logging every group's
-    records and labels.  Returns (scene handle, records [5][REC_ROWS][n])."""
+    records; labels from the loss over every training view at full
+    resolution.  Returns (scene handle, records [5][REC_ROWS][n])."""
     cfg = O.default_config(**(cfg or {}))
     cur = O.scene_handle(scene)
     views = _views(cams, targets, knn_table, t, cfg)
+    every = [(c, np.asarray(targets[v], np.float64)) for v, c in enumerate(cams)]
     primary = cams[t]
     S = O.sh_count(cur.sh_degree)
     recs = []
     for group in O.GROUPS:
         ob = _blocks(group, cur, views, primary, cfg)
+        gp = _blocks(group, cur, views[:1], primary, cfg)["g"]
         st = O.solve(group, cur, primary, ob["g"], ob["H"], cfg)
-        rec = step_records(group, ob["g"], ob["H"], st["step"], cur, cfg)
-        nxt = O.apply(group, cur, primary, st["step"], cfg)
-        oa = _blocks(group, nxt, views, primary, cfg)
-        recs.append(step_labels(group, oa["g"], st["step"], rec, S))
+        d = st["step"]
+        rec = step_records(group, ob["g"], ob["H"], d, cur, cfg, gp)
+        phi0 = phi(group, _blocks(group, cur, every, primary, cfg)["g"], d)
+        nxt = O.apply(group, cur, primary, d, cfg)
+        g_after = _blocks(group, nxt, every, primary, cfg)["g"]
+        recs.append(step_labels(group, g_after, d, rec, S, phi0=phi0))
         cur = nxt
     return cur, np.stack(recs)

@@ -227,7 +227,8 @@ def test_phi0_phi1_are_directional_derivatives(group):
     ob = Lr._blocks(group, cur, views, cams[0], cfg)
     st = O.solve(group, cur, cams[0], ob["g"], ob["H"], cfg)
     d = st["step"]
-    rec = Lr.step_records(group, ob["g"], ob["H"], d, cur, cfg)
+    gp = Lr._blocks(group, cur, views[:1], cams[0], cfg)["g"]
+    rec = Lr.step_records(group, ob["g"], ob["H"], d, cur, cfg, gp)
     S = O.sh_count(sc.sh_degree)
     checked = 0
     for k in range(sc.n):
@@ -243,6 +244,10 @@ def test_phi0_phi1_are_directional_derivatives(group):
         phi0_fd = (L(h) - L(-h)) / (2 * h)
         phi1_fd = (L(1 + h) - L(1 - h)) / (2 * h)
         assert rec[Lr.NF, k] == pytest.approx(phi0_fd, rel=1e-4, abs=1e-12)
+        # f4: the primary view's share of that derivative
+        Lp = lambda a: _group_loss(O.apply(group, cur, cams[0], a * dk, cfg), views[:1], cfg)  # noqa: E731
+        share = ((Lp(h) - Lp(-h)) / (2 * h)) / phi0_fd
+        assert rec[4, k] == pytest.approx(min(max(share, -4.0), 4.0), rel=1e-3, abs=1e-6)
         # Gaussian k stepped alone: its after-step gradient along d
         oa = Lr._blocks(group, O.apply(group, cur, cams[0], dk, cfg), views, cams[0], cfg)
         phi1 = float(np.sum(np.asarray(oa["g"])[..., k] * d[..., k]))
@@ -253,6 +258,49 @@ def test_phi0_phi1_are_directional_derivatives(group):
         assert lab == pytest.approx(expect, rel=5e-3, abs=1e-6)
         checked += 1
     assert checked >= 2
+
+
+@pytest.mark.parametrize("group", [O.POS, O.ROT, O.OPACITY, O.COLOR])
+def test_global_phi_sums_are_derivatives_of_the_total_loss(group):
+    """Every Gaussian steps together: the sums over Gaussians of phi0 and
+    phi1 taken over all training views are the derivatives of the total loss
+    along the whole step at 0 and 1 (chain rule; central differences).  The
+    alpha_min skip is made negligible (1e-9): with every Gaussian moving, a
+    pixel crossing it would put a jump inside the difference quotient."""
+    sc = synth.tiny_scene(n=40, seed=18, sh_degree=1)
+    gt = synth.perturbed(sc, seed=19, sd=0.05)
+    cams = synth.ring_cameras(6, 32)
+    cfg = O.default_config(alpha_min=1e-9)
+    targets = [O.render(gt, c, cfg)["image"] for c in cams]
+    every = [(c, targets[v]) for v, c in enumerate(cams)]
+    knn = np.array([[1, 5, 2]] + [[0, 0, 0]] * 5, np.int32)
+    views = Lr._views(cams, targets, knn, 0, cfg)
+    cur = O.scene_handle(sc)
+    ob = Lr._blocks(group, cur, views, cams[0], cfg)
+    d = O.solve(group, cur, cams[0], ob["g"], ob["H"], cfg)["step"]
+    phi0 = Lr.phi(group, Lr._blocks(group, cur, every, cams[0], cfg)["g"], d)
+    phi1 = Lr.phi(group, Lr._blocks(group, O.apply(group, cur, cams[0], d, cfg), every, cams[0], cfg)["g"], d)
+    h = 1e-5
+
+    def L(a):
+        return _group_loss(O.apply(group, cur, cams[0], a * d, cfg), every, cfg)
+
+    assert phi0.sum() == pytest.approx((L(h) - L(-h)) / (2 * h), rel=2e-4)
+    assert phi1.sum() == pytest.approx((L(1 + h) - L(1 - h)) / (2 * h), rel=2e-4)
+
+
+def test_rejected_step_has_label_zero():
+    """A usable record whose step does not descend the label loss (phi0 >= 0)
+    gets label 0; a descending one the line-model minimum."""
+    rec = np.zeros((Lr.REC_ROWS, 3))
+    rec[Lr.NF] = -1.0
+    rec[Lr.NF + 1] = [0.0, 0.0, -1.0]
+    d = np.ones((1, 3))
+    out = Lr.step_labels(O.OPACITY, np.array([[0.5, 0.5, 0.5]]), d, rec, phi0=np.array([0.2, -1.0, -1.0]))
+    assert out[Lr.NF + 1, 0] == 0.0
+    assert out[Lr.NF + 1, 1] == pytest.approx(1.0 / 1.5)
+    assert out[Lr.NF + 1, 2] == -1.0
+    assert np.array_equal(out[Lr.NF], [0.2, -1.0, -1.0])
 
 
 def test_learned_step_bounds_and_fallback():
