@@ -288,6 +288,140 @@ def run_gpu(args, rank, world, local_rank):
     return result, (w, train_host, cams)
 
 
+# ----------------------------------------------------------------------------- time to PSNR
+
+def time_to_psnr(args):
+    """Time to PSNR on the object workload.  The plain FP32 path runs 30
+    sweeps (primaries in a seeded permutation, seed 5); the learned step scale
+    with the mixed-precision policy then runs from the same start until its
+    PSNR over all training views reaches the plain path's PSNR after 30
+    sweeps (at most --ttp-max sweeps).  Two starts: the workload's own (means
+    perturbed, everything else exact) and the initialised state a training
+    run starts from (grey colour, opacity 0.1, jittered scales).  Times are the
+    sweeps' device time (CUDA events); PSNR is taken between sweeps, outside
+    the timed work.  The network is trained first on records the plain method
+    logs on tiny scenes and on smaller shell scenes (other seeds); their
+    collection and training times are reported beside it."""
+    import torch
+    from paper_2501_13975_b300 import gs2, learned
+
+    torch.cuda.set_device(0)
+    w, gt_host, spec_host, cams = make_workload("object")
+    init_host = synth.initialised(spec_host, seed=9)
+    ncam = len(cams)
+    W, H = w["width"], w["height"]
+    order = np.random.Generator(np.random.PCG64(5)).permutation(ncam)
+
+    # ---- network: records of the plain method, then Adam
+    t0 = time.perf_counter()
+    tiny = learned.collect_records(range(100, 100 + args.ttp_runs), kind="tiny")
+    shell = learned.collect_records(range(1000, 1000 + args.ttp_shell), kind="shell", sweeps=4)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    parts = [r.split(0.1) for r in (tiny, shell)]
+    train_sets = [p[0] for p in parts]
+    held = [p[1] for p in parts]
+    model = learned.StepModel(seed=20)
+    t0 = time.perf_counter()
+    model.fit(train_sets, epochs=args.ttp_epochs, batch=16384)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    held_stats = {}
+    for name, hs in zip(("tiny", "shell"), held):
+        pl, cnt = learned.plain_loss(hs)
+        nl, _ = model.loss(hs)
+        held_stats[name] = {"records": cnt, "loss_plain": round(pl, 5), "loss_network": round(nl, 5)}
+
+    def run(start_host, precision, use_model, max_sweeps, target_psnr=None):
+        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision))
+        gt = gs2.DeviceScene.from_host(gt_host)
+        proj = ctx.proj_buffer(w["n"])
+        targets = []
+        for c in cams:
+            ctx.project(gt, c, proj)
+            img, _ = ctx.raster_fwd(gt, c, proj)
+            targets.append(img.clone())
+        del gt
+        scene = gs2.DeviceScene.from_host(start_host)
+        sphere = ctx.bounding_sphere(scene).cpu().numpy()
+        centres = np.stack([c.center() for c in cams]).astype(np.float32)
+        knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
+        if use_model:
+            ctx.set_step_model(model.w)
+        evl = torch.zeros((ncam, 2), dtype=torch.float64, device="cuda")
+
+        def psnr():
+            evl.zero_()
+            for v, c in enumerate(cams):
+                ctx.project(scene, c, proj)
+                img, _ = ctx.raster_fwd(scene, c, proj)
+                ctx.loss_derivs(img, targets[v], loss=evl[v])
+            mse = 2.0 * evl[:, 0].cpu().numpy()          # L2 = 1/(3|I|) sum 1/2 (c - c^t)^2
+            return float(np.mean(10.0 * np.log10(1.0 / np.maximum(mse, 1e-30))))
+
+        curve = [psnr()]
+        ms_total = 0.0
+        ms_curve = [0.0]
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        reached = None
+        for i in range(max_sweeps):
+            ev0.record()
+            ctx.sweep(scene, cams, targets, knn, int(order[i % ncam]))
+            ev1.record()
+            torch.cuda.synchronize()
+            ms_total += ev0.elapsed_time(ev1)
+            ms_curve.append(ms_total)
+            curve.append(psnr())
+            if target_psnr is not None and reached is None and curve[-1] >= target_psnr:
+                reached = i + 1
+                if i + 1 >= 30:
+                    break
+        ctx.check()
+        return dict(psnr=curve, ms=ms_curve, reached=reached, sweeps=len(curve) - 1)
+
+    def summary(r):
+        k = r["reached"] if r["reached"] is not None else r["sweeps"]
+        return {"sweeps_to_target": r["reached"], "seconds_to_target": round(r["ms"][k] * 1e-3, 5)
+                if r["reached"] is not None else None,
+                "psnr_at_30": round(r["psnr"][min(30, r["sweeps"])], 4), "best_psnr": round(max(r["psnr"]), 4),
+                "ms_per_sweep": round(r["ms"][-1] / max(r["sweeps"], 1), 3)}
+
+    starts = {}
+    for sname, host in (("workload", spec_host), ("initialised", init_host)):
+        plain = run(host, 0, False, 30)
+        target = plain["psnr"][30]
+        runs = {"plain_fp32": plain}
+        for name, prec, use in (("learned_mixed", 1, True), ("learned_fp32", 0, True), ("plain_mixed", 1, False)):
+            runs[name] = run(host, prec, use, max(args.ttp_max, 30), target)
+        lm = runs["learned_mixed"]
+        t_plain = plain["ms"][30] * 1e-3
+        t_lm = lm["ms"][lm["reached"]] * 1e-3 if lm["reached"] is not None else None
+        starts[sname] = {
+            "initial_psnr_db": round(plain["psnr"][0], 4), "target_psnr_db": round(target, 4),
+            "plain_fp32_seconds_30": round(t_plain, 5),
+            "plain_diverges": bool(target < plain["psnr"][0]),
+            "learned_mixed_seconds": None if t_lm is None else round(t_lm, 5),
+            "speedup_vs_plain": None if not t_lm else round(t_plain / t_lm, 3),
+            "runs": {k: summary(r) for k, r in runs.items()},
+            "psnr_curves": {k: [round(x, 3) for x in r["psnr"]] for k, r in runs.items()},
+        }
+    head = starts["workload"]
+    result = {
+        "metric": "time to PSNR vs plain FP32 path (object workload)",
+        "value": head["learned_mixed_seconds"], "unit": "s", "higher_is_better": False,
+        "starts": starts,
+        "network": {"tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell, "records": tiny.n + shell.n,
+                    "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
+                    "heldout": held_stats},
+        "config": {"workload": "object: " + w["desc"], "primaries": "seeded permutation (seed 5)",
+                   "psnr": "mean over all cameras of 10 log10(1 / MSE), images not clamped"},
+        "dtype": "f32 (plain) / f32+f64 (mixed), network bf16 weights f32 accumulation",
+        "data": "synthetic",
+    }
+    return result
+
+
 # ----------------------------------------------------------------------------- oracle (CPU) arm
 
 def oracle_group_pass_seconds(O, scene_h, cam, group, crop, ocfg, target_full):
@@ -406,12 +540,23 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=12)
     ap.add_argument("--ref-crop", type=int, default=8)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
+                                                       "vs plain FP32), one JSON line")
+    ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")
+    ap.add_argument("--ttp-shell", type=int, default=24, help="shell-scene record runs (4 sweeps each)")
+    ap.add_argument("--ttp-epochs", type=int, default=3)
+    ap.add_argument("--ttp-max", type=int, default=60)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gs2" else args.warmup
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.ttp:
+        if rank == 0:
+            print(json.dumps(time_to_psnr(args)), flush=True)
+        return
 
     if args.impl == "reference":
         if rank == 0:

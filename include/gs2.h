@@ -89,7 +89,7 @@ typedef struct {
 } gs2_camera;
 
 /* Configuration.  Every constant the paper leaves unstated is a field; the
- * defaults (gs2_config_default) are the readings documented in the design doc. */
+ * defaults (gs2_config_default) are this library's readings of them. */
 typedef struct {
     float lambda_ssim;      /* weight of the SSIM loss (0.2) */
     float alpha_min;        /* skip terms with alpha < alpha_min (1/255) */
@@ -236,15 +236,24 @@ gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
  * (|d| = 0, g . d >= 0, a non-finite value) or alpha is not finite.
  *
  * Records: float [GS2_REC_ROWS][n] per group and sweep: rows 0-7 the
- * features, row 8 phi0 = g . d, row 9 the label alpha* in [0, 2] (the minimum
- * of the quadratic line model through phi0 and phi1 = g_after . d, with
- * g_after the group's gradient after all of its Gaussians stepped; 2 where
- * that model is not convex) or -1 for an unusable record.  Features:
+ * features, row 8 phi0, row 9 the label alpha* in [0, 2] or -1 for an
+ * unusable record.  The label looks along d at a loss L_lab: phi0 = grad
+ * L_lab . d before the step, phi1 = grad L_lab . d after all Gaussians of the
+ * group stepped; alpha* = 0 if phi0 >= 0 (d does not descend L_lab: a
+ * rejected step), else the minimum of the quadratic line model
+ * phi0 / (phi0 - phi1) (2 where that model is not convex), clipped to
+ * [0, 2].  gs2_step_records/gs2_step_labels use the loss of the blocks passed
+ * (phi0 = g . d); gs2_sweep_logged uses the loss summed over every training
+ * view at full resolution, whose increase is the overshoot of Sec. 4.3.
+ * Features (g, H the group's block, g_p the primary view's own gradient):
  *   f0 log10 clamp(d^T H d / (-g.d), 1e-6, 1e6)   f1 cos(-g, d)
  *   f2 log10 max(|d|/u, 1e-12), u = max(s) for position and scaling, else 1
- *   f3 sigma   f4 log10 max(max(s), 1e-12)
+ *   f3 sigma   f4 clamp(g_p.d / g.d, -4, 4) (0 if g.d >= 0)
  *   f5 1 if a trust radius or bound is within 1e-3 of limiting d, else 0
  *   f6 log10 clamp(|g| / (mean|diag H| |d|), 1e-6, 1e6)   f7 group / 4
+ * g_p: gs2_accum_newton_blocks keeps the gradient rows of blocks as they are
+ * right after a view_slot 0 accumulation in the context (colour: slot 0 of
+ * its blocks); accumulate the primary view in slot 0, first.
  * Parameters (GS2_MLP_NPARAM words): W1 [64][8], b1 [64], W2 [64][64],
  * b2 [64], W3 [64], b3. */
 #define GS2_MLP_NFEAT 8
@@ -268,8 +277,9 @@ gs2_status gs2_step_records(gs2_ctx *ctx, gs2_group group, const void *blocks, i
 gs2_status gs2_step_labels(gs2_ctx *ctx, gs2_group group, const void *blocks_after, int32_t n_views,
                            const gs2_scene *scene, const void *step, float *records, gs2_stream stream);
 /* gs2_sweep of the plain method (an installed step model is not used) that
- * also logs every group's records: after a group's step is applied its views
- * are accumulated again for the labels.  records: device float
+ * also logs every group's records, labelled by the loss over all ncam views
+ * at full resolution (every view is accumulated before and after the step;
+ * all cameras must fit the context).  records: device float
  * [5][GS2_REC_ROWS][n] out.  The scene ends as after gs2_sweep. */
 gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                             const float *const *targets, const int32_t *knn, int32_t t, float *records,

@@ -149,6 +149,8 @@ struct gs2_ctx {
     uint32_t *d_status;
     uint8_t *flags;              // [max_n] per-Gaussian flags (FP64 re-solve of the colour block)
     const void *mlp_w;           // installed step-scale network (BF16, caller-owned) or NULL
+    float *g_prim;               // [3][max_n] gradient rows right after the view-slot-0 accumulation
+    float *lg_phi;               // [max_n] phi1 accumulator of the logged sweep
     // opt-in profile of the accumulation kernel: CUDA events around every launch
     // and per-group pair / visible-Gaussian totals counted on the device
     int prof_on;
@@ -184,11 +186,13 @@ cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const 
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);
 cudaError_t launch_step_records(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
-                                const gs2_config &cfg, float *rec, cudaStream_t st);
+                                const float *gp, const gs2_config &cfg, float *rec, cudaStream_t st);
 cudaError_t launch_step_labels(int group, const void *blocks_after, int n_views, const DevScene &sc,
-                               const void *step, float *rec, cudaStream_t st);
+                               const void *step, const float *phi1, float *rec, cudaStream_t st);
+cudaError_t launch_phi_add(int group, const void *blocks_one_view, const DevScene &sc, const void *step, float *out,
+                           cudaStream_t st);
 cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, const DevScene &sc, void *step,
-                                 const gs2_config &cfg, const void *w, cudaStream_t st);
+                                 const float *gp, const gs2_config &cfg, const void *w, cudaStream_t st);
 cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t st);
 
 // --------------------------------------------------------------------------

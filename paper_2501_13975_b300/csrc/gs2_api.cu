@@ -102,7 +102,7 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
-                    c->sw_step, c->d_status, c->d_stats, c->flags};
+                    c->sw_step, c->d_status, c->d_stats, c->flags, c->g_prim, c->lg_phi};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
@@ -169,6 +169,8 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A((void **)&c->d_status, sizeof(uint32_t) * 4);
     A((void **)&c->d_stats, sizeof(unsigned long long) * 5 * 4);
     A((void **)&c->flags, (size_t)max_n);
+    A((void **)&c->g_prim, sizeof(float) * 3 * (size_t)max_n);
+    A((void **)&c->lg_phi, sizeof(float) * (size_t)max_n);
     if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(double) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
@@ -295,15 +297,24 @@ extern "C" gs2_status gs2_loss_derivs(gs2_ctx *ctx, const float *image, const fl
     return GS2_OK;
 }
 
+// keep_primary: after a view-slot-0 accumulation, copy the gradient rows into
+// ctx->g_prim (the primary view's own gradient, a step-model feature; colour
+// keeps it in slot 0 of its blocks)
 static gs2_status do_accum(gs2_ctx *ctx, int group, const gs2_scene *scene, const gs2_camera *view,
                            const gs2_camera *primary, const void *proj, const void *rstate, const float *image,
-                           const float *target, int slot, void *blocks, double *loss_out, cudaStream_t st) {
+                           const float *target, int slot, void *blocks, double *loss_out, cudaStream_t st,
+                           bool keep_primary = true) {
     RET_CUDA(ctx, launch_loss(image, target, view->width, view->height, ctx->cfg, ctx->pix_e, ctx->pix_h, loss_out,
                               st));
     RET_CUDA(ctx, launch_accum(ctx, group, make_devscene(scene), make_devcam(view), make_devcam(primary),
                                proj_view(const_cast<void *>(proj), scene->n),
                                raster_view(const_cast<void *>(rstate), view->width, view->height), ctx->cfg, slot,
                                blocks, st));
+    if (keep_primary && slot == 0 && group != GS2_COLOR && scene->n > 0) {
+        const size_t D = (group == GS2_POS || group == GS2_SCALE) ? 3 : 1;
+        RET_CUDA(ctx, cudaMemcpyAsync(ctx->g_prim, blocks, sizeof(float) * D * scene->n, cudaMemcpyDeviceToDevice,
+                                      st));
+    }
     return GS2_OK;
 }
 
@@ -337,8 +348,8 @@ extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *
     REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
     RET_CUDA(ctx, launch_solve(group, blocks, n_views, make_devscene(scene), make_devcam(primary), ctx->cfg, step,
                                n_failed, ctx->flags, (cudaStream_t)stream));
-    RET_CUDA(ctx, launch_learned_scale(group, blocks, n_views, make_devscene(scene), step, ctx->cfg, ctx->mlp_w,
-                                       (cudaStream_t)stream));
+    RET_CUDA(ctx, launch_learned_scale(group, blocks, n_views, make_devscene(scene), step, ctx->g_prim, ctx->cfg,
+                                       ctx->mlp_w, (cudaStream_t)stream));
     return GS2_OK;
 }
 
@@ -361,8 +372,8 @@ extern "C" gs2_status gs2_step_records(gs2_ctx *ctx, gs2_group group, const void
                                        const gs2_scene *scene, const void *step, float *records, gs2_stream stream) {
     if (!ctx) return GS2_ERR_ARG;
     TRY(check_records_args(ctx, group, blocks, n_views, scene, step, records));
-    RET_CUDA(ctx, launch_step_records(group, blocks, n_views, make_devscene(scene), step, ctx->cfg, records,
-                                      (cudaStream_t)stream));
+    RET_CUDA(ctx, launch_step_records(group, blocks, n_views, make_devscene(scene), step, ctx->g_prim, ctx->cfg,
+                                      records, (cudaStream_t)stream));
     return GS2_OK;
 }
 
@@ -370,7 +381,7 @@ extern "C" gs2_status gs2_step_labels(gs2_ctx *ctx, gs2_group group, const void 
                                       const gs2_scene *scene, const void *step, float *records, gs2_stream stream) {
     if (!ctx) return GS2_ERR_ARG;
     TRY(check_records_args(ctx, group, blocks_after, n_views, scene, step, records));
-    RET_CUDA(ctx, launch_step_labels(group, blocks_after, n_views, make_devscene(scene), step, records,
+    RET_CUDA(ctx, launch_step_labels(group, blocks_after, n_views, make_devscene(scene), step, nullptr, records,
                                      (cudaStream_t)stream));
     return GS2_OK;
 }
@@ -480,6 +491,12 @@ static gs2_status sweep_impl(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *c
             vtgt[i] = targets[v];
         }
     }
+    if (records) {
+        for (int v = 0; v < ncam; ++v) {
+            TRY(check_cam(ctx, &cams[v]));
+            REQUIRE(ctx, targets[v] != nullptr, GS2_ERR_ARG, "null target");
+        }
+    }
     const gs2_camera *primary = &cams[t];
     for (int group = 0; group < 5; ++group) {
         ctx->stat_slot = group;
@@ -491,29 +508,36 @@ static gs2_status sweep_impl(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *c
             TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image, vtgt[i],
                          i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, st));
         }
-        const size_t bbytes = blocks_bytes_impl(group, scene->n, scene->sh_degree, nv);
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
                                    ctx->sw_step, n_failed, ctx->flags, st));
         float *rec = records ? records + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;
-        if (rec)
-            RET_CUDA(ctx, launch_step_records(group, ctx->sw_blocks, nv, make_devscene(scene), ctx->sw_step, ctx->cfg,
-                                              rec, st));
-        else
-            RET_CUDA(ctx, launch_learned_scale(group, ctx->sw_blocks, nv, make_devscene(scene), ctx->sw_step,
-                                               ctx->cfg, ctx->mlp_w, st));
-        RET_CUDA(ctx, launch_apply(group, ctx->sw_step, make_devscene(scene), make_devcam(primary), ctx->cfg, st));
-        if (rec) {
-            // the same views again at the new parameters: g_after for the labels
-            RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, bbytes, st));
-            for (int i = 0; i < nv; ++i) {
-                if (vid[i] < 0) continue;
-                TRY(do_project(ctx, scene, &vcam[i], ctx->sw_proj, st));
-                TRY(do_raster(ctx, scene->n, &vcam[i], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st));
-                TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image,
-                             vtgt[i], i, ctx->sw_blocks, nullptr, st));
-            }
-            RET_CUDA(ctx, launch_step_labels(group, ctx->sw_blocks, nv, make_devscene(scene), ctx->sw_step, rec, st));
+        const DevScene dsc = make_devscene(scene);
+        if (!rec) {
+            RET_CUDA(ctx, launch_learned_scale(group, ctx->sw_blocks, nv, dsc, ctx->sw_step, ctx->g_prim, ctx->cfg,
+                                               ctx->mlp_w, st));
+            RET_CUDA(ctx, launch_apply(group, ctx->sw_step, dsc, make_devcam(primary), ctx->cfg, st));
+            continue;
         }
+        // logged: records of the plain step, then the label loss (every view,
+        // full resolution) along the step before and after it is applied
+        RET_CUDA(ctx, launch_step_records(group, ctx->sw_blocks, nv, dsc, ctx->sw_step, ctx->g_prim, ctx->cfg, rec,
+                                          st));
+        const size_t b1 = blocks_bytes_impl(group, scene->n, scene->sh_degree, 1);
+        for (int pass = 0; pass < 2; ++pass) {
+            float *phi = pass == 0 ? rec + (size_t)GS2_MLP_NFEAT * scene->n : ctx->lg_phi;
+            RET_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(float) * scene->n, st));
+            for (int v = 0; v < ncam; ++v) {
+                RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, b1, st));
+                TRY(do_project(ctx, scene, &cams[v], ctx->sw_proj, st));
+                TRY(do_raster(ctx, scene->n, &cams[v], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st));
+                TRY(do_accum(ctx, group, scene, &cams[v], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image,
+                             targets[v], 0, ctx->sw_blocks, nullptr, st, false));
+                RET_CUDA(ctx, launch_phi_add(group, ctx->sw_blocks, dsc, ctx->sw_step, phi, st));
+            }
+            if (pass == 0)
+                RET_CUDA(ctx, launch_apply(group, ctx->sw_step, dsc, make_devcam(primary), ctx->cfg, st));
+        }
+        RET_CUDA(ctx, launch_step_labels(group, nullptr, 1, dsc, ctx->sw_step, ctx->lg_phi, rec, st));
     }
     ctx->stat_slot = 0;
     return GS2_OK;

@@ -6,21 +6,25 @@
 //
 // Records logged from the plain method (one per Gaussian and group), float
 // [GS2_REC_ROWS][n]:
-//   rows 0-7  features (below), row 8 phi0 = g . d,
+//   rows 0-7  features (below), row 8 phi0,
 //   row 9     label alpha* in [0, 2], or -1 where the record is unusable.
-// alpha* comes from the derivative of the loss along d before the step (phi0)
-// and after every Gaussian of the group took its step (phi1 = g_after . d, so
-// the coupling of the simultaneous updates is included): the quadratic line
-// model has its minimum at alpha* = phi0 / (phi0 - phi1), 2 where that model
-// is not convex, clipped to [0, 2].  The step "was accepted" (the model's loss
-// decreased) exactly when alpha* > 1/2.
+// The label looks at a loss L_lab along d: phi0 = grad L_lab . d before the
+// step, phi1 = grad L_lab . d after every Gaussian of the group took its step
+// (so the coupling of the simultaneous updates is included).  alpha* = 0 when
+// phi0 >= 0 (d does not descend L_lab: a rejected step), else the minimum of
+// the quadratic line model, phi0 / (phi0 - phi1), 2 where that model is not
+// convex, clipped to [0, 2].  The logged sweep takes L_lab = the loss summed
+// over every training view at full resolution: an increase of that loss is
+// the overshoot of Sec. 4.3.  The step "was accepted" (L_lab decreased under
+// the line model) exactly when alpha* > 1/2.
 //
 // Features, from g, H (the group's block), d and the Gaussian's parameters:
 //   f0 log10 clamp(d^T H d / (-g . d), 1e-6, 1e6)   (1 for the undamped step)
 //   f1 cos(-g, d)
 //   f2 log10 max(|d| / u, 1e-12), u = max(s) for position and scaling, else 1
 //   f3 sigma
-//   f4 log10 max(max(s), 1e-12)
+//   f4 clamp(g_p . d / g . d, -4, 4), g_p the primary view's own gradient: the
+//      primary's share of the step's predicted decrease (0 if g . d >= 0)
 //   f5 1 if a trust radius or bound limits the step (within 1e-3), else 0
 //   f6 log10 clamp(|g| / (mean|diag H| |d|), 1e-6, 1e6)
 //   f7 group / 4
@@ -51,6 +55,7 @@ static_assert(RROWS == NF + 2, "record rows: features, phi0, label");
 // ---------------------------------------------------------------- features
 struct StepStats {
     float gd, q, gg, dd, hd;   // g.d, d^T H d, |g|^2, |d|^2, mean |diag H|
+    float gpd;                 // g_p . d (primary view's own gradient)
     bool clipped;
 };
 
@@ -61,8 +66,11 @@ __device__ __forceinline__ float smax_of(const DevScene &sc, int k) {
 
 __device__ __forceinline__ bool near_or_past(float v, float lim) { return v >= (1.f - 1e-3f) * lim; }
 
+// gp: the primary view's gradient rows [D][n] (position, rotation, scaling,
+// opacity; colour takes it from view slot 0 of B)
 __device__ StepStats step_stats(int group, const float *__restrict__ B, int n_views, const DevScene &sc, int k,
-                                const float *__restrict__ step, const gs2_config &cfg, float smax) {
+                                const float *__restrict__ step, const float *__restrict__ gp, const gs2_config &cfg,
+                                float smax) {
     const int n = sc.n, S = sc.S;
     StepStats r{};
     if (group == GS2_POS || group == GS2_SCALE) {
@@ -74,6 +82,7 @@ __device__ StepStats step_stats(int group, const float *__restrict__ B, int n_vi
         const float h00 = B[(size_t)3 * n + k], h01 = B[(size_t)4 * n + k], h02 = B[(size_t)5 * n + k];
         const float h11 = B[(size_t)6 * n + k], h12 = B[(size_t)7 * n + k], h22 = B[(size_t)8 * n + k];
         r.gd = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
+        r.gpd = gp[k] * d[0] + gp[(size_t)n + k] * d[1] + gp[(size_t)2 * n + k] * d[2];
         r.q = h00 * d[0] * d[0] + h11 * d[1] * d[1] + h22 * d[2] * d[2] +
               2.f * (h01 * d[0] * d[1] + h02 * d[0] * d[2] + h12 * d[1] * d[2]);
         r.gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
@@ -92,6 +101,7 @@ __device__ StepStats step_stats(int group, const float *__restrict__ B, int n_vi
     if (group == GS2_ROT || group == GS2_OPACITY) {
         const float g = B[k], h = B[n + k], d = step[k];
         r.gd = g * d;
+        r.gpd = gp[k] * d;
         r.q = h * d * d;
         r.gg = g * g;
         r.dd = d * d;
@@ -128,6 +138,7 @@ __device__ StepStats step_stats(int group, const float *__restrict__ B, int n_vi
             }
             r.gd += a * t;
             r.q += s * t * t;
+            if (v == 0) r.gpd += a * t;
         }
         for (int i = 0; i < S; ++i) {
             r.gg += gc[i] * gc[i];
@@ -151,7 +162,7 @@ __device__ bool step_features(int group, const StepStats &st, float sigma, float
     f[1] = (gn * dn > 0.f) ? mgd / (gn * dn) : 0.f;
     f[2] = log10f(fmaxf(dn / u, 1e-12f));
     f[3] = sigma;
-    f[4] = log10f(fmaxf(smax, 1e-12f));
+    f[4] = (st.gd < 0.f) ? fminf(fmaxf(st.gpd / st.gd, -4.f), 4.f) : 0.f;
     f[5] = st.clipped ? 1.f : 0.f;
     f[6] = clamp_log10(st.hd * dn > 0.f ? gn / (st.hd * dn) : 1e6f, 1e-6f, 1e6f);
     f[7] = 0.25f * (float)group;
@@ -162,13 +173,14 @@ __device__ bool step_features(int group, const StepStats &st, float sigma, float
 }
 
 __global__ void __launch_bounds__(128) k_step_records(int group, const float *__restrict__ B, int n_views,
-                                                      DevScene sc, const float *__restrict__ step, gs2_config cfg,
+                                                      DevScene sc, const float *__restrict__ step,
+                                                      const float *__restrict__ gp, gs2_config cfg,
                                                       float *__restrict__ rec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
     const float smax = smax_of(sc, k);
-    const StepStats st = step_stats(group, B, n_views, sc, k, step, cfg, smax);
+    const StepStats st = step_stats(group, B, n_views, sc, k, step, gp, cfg, smax);
     float f[NF];
     const bool ok = step_features(group, st, sc.opacity[k], smax, f);
 #pragma unroll
@@ -199,19 +211,30 @@ __device__ float block_dot_step(int group, const float *__restrict__ B, int n_vi
     return r;
 }
 
+// phi1 from a block accumulated after the step (Bafter, n_views slots) or, if
+// phi1 is not NULL, as given; phi0 from row 8
 __global__ void __launch_bounds__(128) k_step_labels(int group, const float *__restrict__ Bafter, int n_views,
                                                      DevScene sc, const float *__restrict__ step,
-                                                     float *__restrict__ rec) {
+                                                     const float *__restrict__ phi1v, float *__restrict__ rec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
     float *lab = rec + (size_t)(NF + 1) * n + k;
     if (*lab < 0.f) return;
     const float phi0 = rec[(size_t)NF * n + k];
-    const float phi1 = block_dot_step(group, Bafter, n_views, n, sc.S, k, step);
-    const float den = phi0 - phi1;                    // phi0 < 0 for a usable record
-    const float a = (den < 0.f) ? phi0 / den : 2.f;
+    const float phi1 = phi1v ? phi1v[k] : block_dot_step(group, Bafter, n_views, n, sc.S, k, step);
+    const float den = phi0 - phi1;
+    float a = (den < 0.f) ? phi0 / den : 2.f;
+    if (!(phi0 < 0.f)) a = 0.f;                       // not a descent direction of the label loss
     *lab = isfinite(a) ? fminf(fmaxf(a, 0.f), 2.f) : -1.f;
+}
+
+// out[k] += g . d of a one-view block
+__global__ void __launch_bounds__(128) k_phi_add(int group, const float *__restrict__ B, DevScene sc,
+                                                 const float *__restrict__ step, float *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= sc.n) return;
+    out[k] += block_dot_step(group, B, 1, sc.n, sc.S, k, step);
 }
 
 // ---------------------------------------------------------------- inference
@@ -252,7 +275,8 @@ __device__ __forceinline__ void load_weights(float *sw, const __nv_bfloat16 *__r
 // step <- alpha d inside the plain step's trust radii and bounds; the plain
 // step stays where the record is unusable or alpha is not finite
 __global__ void __launch_bounds__(128) k_learned_scale(int group, const float *__restrict__ B, int n_views,
-                                                       DevScene sc, float *__restrict__ step, gs2_config cfg,
+                                                       DevScene sc, float *__restrict__ step,
+                                                       const float *__restrict__ gp, gs2_config cfg,
                                                        const __nv_bfloat16 *__restrict__ w) {
     __shared__ __align__(16) float sw[NPARAM + 3];
     load_weights(sw, w);
@@ -261,7 +285,7 @@ __global__ void __launch_bounds__(128) k_learned_scale(int group, const float *_
     const int n = sc.n, S = sc.S;
     if (k >= n) return;
     const float smax = smax_of(sc, k);
-    const StepStats st = step_stats(group, B, n_views, sc, k, step, cfg, smax);
+    const StepStats st = step_stats(group, B, n_views, sc, k, step, gp, cfg, smax);
     float f[NF];
     if (!step_features(group, st, sc.opacity[k], smax, f)) return;
     const float a = scale_of(mlp_eval(sw, f));
@@ -296,28 +320,37 @@ __global__ void __launch_bounds__(128) k_learned_scale(int group, const float *_
 }
 
 cudaError_t launch_step_records(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
-                                const gs2_config &cfg, float *rec, cudaStream_t st) {
+                                const float *gp, const gs2_config &cfg, float *rec, cudaStream_t st) {
     if (sc.n == 0) return cudaSuccess;
     k_step_records<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks, n_views, sc,
-                                                      (const float *)step, cfg, rec);
+                                                      (const float *)step, gp, cfg, rec);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_labels(int group, const void *blocks_after, int n_views, const DevScene &sc,
-                               const void *step, float *rec, cudaStream_t st) {
+                               const void *step, const float *phi1, float *rec, cudaStream_t st) {
     if (sc.n == 0) return cudaSuccess;
     k_step_labels<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks_after, n_views, sc,
-                                                     (const float *)step, rec);
+                                                     (const float *)step, phi1, rec);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_add(int group, const void *blocks_one_view, const DevScene &sc, const void *step, float *out,
+                           cudaStream_t st) {
+    if (sc.n == 0) return cudaSuccess;
+    k_phi_add<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks_one_view, sc, (const float *)step,
+                                                 out);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, const DevScene &sc, void *step,
-                                 const gs2_config &cfg, const void *w, cudaStream_t st) {
+                                 const float *gp, const gs2_config &cfg, const void *w, cudaStream_t st) {
     if (sc.n == 0 || !w) return cudaSuccess;
     k_learned_scale<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks, n_views, sc, (float *)step,
-                                                       cfg, (const __nv_bfloat16 *)w);
+                                                       gp, cfg, (const __nv_bfloat16 *)w);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

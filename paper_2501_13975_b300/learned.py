@@ -40,31 +40,55 @@ class RecordSet:
                 RecordSet(chunks[k:].reshape(-1), self.chunk_n))
 
 
-def collect_records(seeds, n: int = 1000, size: int = 128, sd: float = 0.02, ctx=None,
-                    stream=None) -> RecordSet:
-    """One logged sweep per seed on a tiny scene (n Gaussians in [-1,1]^3,
-    SH degree 0, 4 ring cameras size x size; targets rendered from a copy
-    whose means moved by N(0, sd^2)); primary view seed mod 4."""
+def collect_records(seeds, kind: str = "tiny", sweeps: int = 1, n: int | None = None, size: int | None = None,
+                    ncam: int | None = None, sd: float = 0.02, ctx=None, stream=None) -> RecordSet:
+    """Records of the plain method, `sweeps` logged sweeps per seed.
+
+    kind "tiny": n (1000) Gaussians in [-1,1]^3, SH degree 0, 4 ring cameras
+      size x size (128); training starts from the scene, targets come from a
+      copy whose means moved by N(0, sd^2).
+    kind "shell": n (20k) Gaussians on a unit-sphere shell, SH degree 3, ncam
+      (32) hemisphere cameras size x size (256); targets from the scene,
+      training starts from a copy with means moved by N(0, sd^2), every second
+      seed in the initialised state (grey colour, opacity 0.1, jittered
+      scales).
+    Primaries: a seeded permutation of the cameras per seed."""
     seeds = list(seeds)
-    cams = synth.ring_cameras(4, size)
+    if kind == "tiny":
+        n, size, ncam, sh = n or 1000, size or 128, 4, 0
+    elif kind == "shell":
+        n, size, ncam, sh = n or 20_000, size or 256, ncam or 32, 3
+    else:
+        raise ValueError(kind)
+    cams = synth.ring_cameras(4, size) if kind == "tiny" else synth.hemisphere_cameras(ncam, size)
     own = ctx is None
     if own:
-        ctx = gs2.Context(n, size, size, 0)
-    out = torch.empty((len(seeds), 5, gs2.REC_ROWS, n), dtype=torch.float32, device="cuda")
+        ctx = gs2.Context(n, size, size, sh, 64 * n)
+    out = torch.empty((len(seeds), sweeps, 5, gs2.REC_ROWS, n), dtype=torch.float32, device="cuda")
     centres = np.stack([c.center() for c in cams]).astype(np.float32)
+    proj = ctx.proj_buffer(n)
     for i, s in enumerate(seeds):
-        sc = synth.tiny_scene(seed=int(s), n=n)
-        gt = synth.perturbed(sc, seed=int(s) + 100_000, sd=sd)
+        s = int(s)
+        if kind == "tiny":
+            start = synth.tiny_scene(seed=s, n=n)
+            gt = synth.perturbed(start, seed=s + 100_000, sd=sd)
+        else:
+            gt = synth.object_scene(seed=s, n=n)
+            start = synth.perturbed(gt, seed=s + 100_000, sd=sd)
+            if i % 2 == 1:
+                start = synth.initialised(start, seed=s + 200_000)
         dg = gs2.DeviceScene.from_host(gt)
         targets = []
         for c in cams:
-            proj = ctx.project(dg, c, stream=stream)
+            ctx.project(dg, c, proj, stream=stream)
             img, _ = ctx.raster_fwd(dg, c, proj, stream=stream)
             targets.append(img)
-        ds = gs2.DeviceScene.from_host(sc)
+        ds = gs2.DeviceScene.from_host(start)
         sphere = ctx.bounding_sphere(ds, stream=stream).cpu().numpy()
         knn = gs2.camera_knn(centres, sphere, 3)
-        ctx.sweep_logged(ds, cams, targets, knn, int(s) % 4, records=out[i], stream=stream)
+        order = np.random.Generator(np.random.PCG64(s)).permutation(ncam)
+        for j in range(sweeps):
+            ctx.sweep_logged(ds, cams, targets, knn, int(order[j % ncam]), records=out[i, j], stream=stream)
     if own:
         torch.cuda.synchronize()
         ctx.check()
@@ -85,31 +109,41 @@ class StepModel:
         self.partial = torch.empty((gs2.MLP_GRID, gs2.MLP_NPARAM), dtype=torch.float32, device="cuda")
         self.stats = torch.empty((gs2.MLP_GRID, 2), dtype=torch.float64, device="cuda")
 
-    def loss(self, recs: RecordSet, idx: torch.Tensor | None = None, nrec: int | None = None):
-        """Mean of 1/2 (alpha - alpha*)^2 over the usable records, and their count."""
-        nrec = recs.n if nrec is None else nrec
-        gs2.mlp_grad(self.w, recs.data, recs.chunk_n, nrec, self.partial, self.stats, idx=idx)
-        s = self.stats.sum(0).cpu().numpy()
-        return float(s[0] / max(s[1], 1.0)), int(s[1])
+    def loss(self, recs, idx: torch.Tensor | None = None, nrec: int | None = None):
+        """Mean of 1/2 (alpha - alpha*)^2 over the usable records (of one
+        RecordSet or a list of them), and their count."""
+        sets = [recs] if isinstance(recs, RecordSet) else list(recs)
+        tot = np.zeros(2)
+        for r in sets:
+            m = r.n if nrec is None else nrec
+            gs2.mlp_grad(self.w, r.data, r.chunk_n, m, self.partial, self.stats, idx=idx)
+            tot += self.stats.sum(0).cpu().numpy()
+        return float(tot[0] / max(tot[1], 1.0)), int(tot[1])
 
     def step(self, recs: RecordSet, idx: torch.Tensor, nrec: int, lr: float):
         gs2.mlp_grad(self.w, recs.data, recs.chunk_n, nrec, self.partial, self.stats, idx=idx)
         self.t += 1
         gs2.mlp_adam(self.master, self.w, self.partial, self.stats, self.m, self.v, self.t, lr)
 
-    def fit(self, recs: RecordSet, epochs: int = 3, batch: int = 16384, lr: float = 2e-3, seed: int = 21,
+    def fit(self, recs, epochs: int = 3, batch: int = 16384, lr: float = 2e-3, seed: int = 21,
             lr_final: float = 2e-4):
-        """Adam over shuffled mini-batches (seeded permutation per epoch),
-        learning rate decayed geometrically from lr to lr_final."""
+        """Adam over shuffled mini-batches of one RecordSet or a list of them
+        (each batch from one set; per epoch a seeded permutation of every
+        set's records and a seeded order of all batches), learning rate
+        decayed geometrically from lr to lr_final."""
+        sets = [recs] if isinstance(recs, RecordSet) else list(recs)
         rng = np.random.Generator(np.random.PCG64(seed))
-        steps = epochs * max(1, math.ceil(recs.n / batch))
+        nb = [max(1, math.ceil(r.n / batch)) for r in sets]
+        steps = epochs * sum(nb)
         k = 0
         for _ in range(epochs):
-            perm = torch.tensor(rng.permutation(recs.n), dtype=torch.int64, device="cuda")
-            for b0 in range(0, recs.n, batch):
-                nb = min(batch, recs.n - b0)
-                r = lr * (lr_final / lr) ** (k / max(steps - 1, 1))
-                self.step(recs, perm[b0:b0 + nb], nb, r)
+            perms = [torch.tensor(rng.permutation(r.n), dtype=torch.int64, device="cuda") for r in sets]
+            plan = np.concatenate([np.stack([np.full(m, i), np.arange(m)], 1) for i, m in enumerate(nb)])
+            for i, b in plan[rng.permutation(len(plan))]:
+                r = sets[i]
+                b0 = int(b) * batch
+                m = min(batch, r.n - b0)
+                self.step(r, perms[i][b0:b0 + m], m, lr * (lr_final / lr) ** (k / max(steps - 1, 1)))
                 k += 1
         return self
 

@@ -140,6 +140,20 @@ def perturbed(scene: Scene, seed: int = 2, sd: float = 0.02) -> Scene:
     return s
 
 
+def initialised(scene: Scene, seed: int = 9, opacity: float = 0.1, scale_sd: float = 0.3) -> Scene:
+    """Copy in the state a 3DGS training run starts from: grey DC colour
+    (rendered 0.5), higher SH bands 0, every opacity `opacity`, scales
+    multiplied by exp(N(0, scale_sd^2)); means and rotations kept."""
+    rng = _rng(seed)
+    s = scene.copy()
+    sh = np.zeros_like(s.sh)
+    sh[:, 0, :] = 0.5 * DC_RANGE
+    s.sh = sh.astype(np.float32)
+    s.opacity = np.full_like(s.opacity, opacity)
+    s.scale = (s.scale * np.exp(rng.normal(0.0, scale_sd, s.scale.shape))).astype(np.float32)
+    return s
+
+
 # ----------------------------------------------------------------------------- object
 
 def object_scene(seed: int = 3, n: int = 100_000, sh_degree: int = 3) -> Scene:

@@ -100,6 +100,7 @@ def _blocks_and_steps(gs2, group, model_bits=None, seed=40):
     nv = 4
     blocks = ctx.blocks_buffer(group, sc.n, sh, nv)
     ob = None
+    gp = None
     amb = None
     for slot in range(4):
         cam = primary if slot == 0 else O.downsample_camera(cams[slot], 2)
@@ -112,6 +113,8 @@ def _blocks_and_steps(gs2, group, model_bits=None, seed=40):
         r = O.render(sc, cam, ocfg)
         L = O.loss(r["image"], tgt, ocfg)
         ob = O.accum(group, sc, cam, primary, L["e"], L["h"], ocfg, out=ob)
+        if slot == 0:
+            gp = np.array(ob["g"], copy=True)
         a, _ = ambiguous_gaussians(O, sc, cam, ocfg, r["margin"], thresh=2e-5, dilate=10)
         amb = a if amb is None else (amb | a)
     plain = ctx.solve(group, blocks, nv, ds, primary)
@@ -127,7 +130,7 @@ def _blocks_and_steps(gs2, group, model_bits=None, seed=40):
     os_ = O.solve(group, sc, primary, ob["g"], ob["H"], ocfg)
     st_ok = (os_["status"] == 0).all(0) if group == O.COLOR else (os_["status"] == 0)
     keep = ~amb & (ob["npix"] > 0) & st_ok
-    return dict(sc=sc, ocfg=ocfg, ob=ob, os=os_, keep=keep, plain=plain.cpu().numpy(), rec=rec.cpu().numpy(),
+    return dict(sc=sc, ocfg=ocfg, ob=ob, gp=gp, os=os_, keep=keep, plain=plain.cpu().numpy(), rec=rec.cpu().numpy(),
                 learned=None if learned is None else learned.cpu().numpy(), n=sc.n, S=(sh + 1) ** 2)
 
 
@@ -135,7 +138,7 @@ def _blocks_and_steps(gs2, group, model_bits=None, seed=40):
 def test_step_records_match_oracle(group):
     from paper_2501_13975_b300 import gs2
     c = _blocks_and_steps(gs2, group)
-    orec = Lr.step_records(group, c["ob"]["g"], c["ob"]["H"], c["os"]["step"], c["sc"], c["ocfg"])
+    orec = Lr.step_records(group, c["ob"]["g"], c["ob"]["H"], c["os"]["step"], c["sc"], c["ocfg"], c["gp"])
     grec = c["rec"]
     both = c["keep"] & (orec[Lr.NF + 1] >= 0) & (grec[Lr.NF + 1] >= 0)
     # usability agrees wherever the oracle's g.d is clearly negative
@@ -144,8 +147,11 @@ def test_step_records_match_oracle(group):
     clear = c["keep"] & (orec[Lr.NF] < -1e-3 * gn * dn)
     assert np.array_equal(grec[Lr.NF + 1][clear] >= 0, orec[Lr.NF + 1][clear] >= 0)
     assert both.sum() >= 50, both.sum()
-    for j, tol in ((0, 2e-3), (1, 2e-3), (2, 2e-3), (3, 1e-6), (4, 1e-6), (6, 2e-3)):
-        d = np.abs(grec[j][both] - orec[j][both])
+    # f4 divides by g.d: compared where the step clearly descends
+    firm = both & (orec[Lr.NF] < -0.05 * gn * dn)
+    for j, tol in ((0, 2e-3), (1, 2e-3), (2, 2e-3), (3, 1e-6), (4, 2e-3), (6, 2e-3)):
+        m = firm if j == 4 else both
+        d = np.abs(grec[j][m] - orec[j][m])
         assert np.quantile(d, 0.99) <= tol and d.max() <= 50 * tol, (j, d.max(), np.quantile(d, 0.99))
     assert np.all(grec[7] == np.float32(group / 4.0))
     # the clip flag: equal except within 1e-4 of the threshold
@@ -156,6 +162,9 @@ def test_step_records_match_oracle(group):
 
 
 def test_logged_sweep_matches_plain_sweep_and_oracle():
+    """The logged sweep ends where gs2_sweep ends; its records (features from
+    the solve's blocks, labels from the loss over all 4 views) match the
+    oracle's logged sweep."""
     from paper_2501_13975_b300 import gs2
     sc = synth.tiny_scene(n=300, seed=41)
     gt = synth.perturbed(sc, seed=42, sd=0.05)
@@ -203,7 +212,7 @@ def test_learned_scale_inside_solve_matches_oracle(group):
     _, bits = synth.mlp_init(43, out_scale=2.0)
     c = _blocks_and_steps(gs2, group, model_bits=bits)
     p = Lr.bf16_to_f64(bits)
-    ref = Lr.learned_step(group, c["ob"]["g"], c["ob"]["H"], c["os"]["step"], c["sc"], c["ocfg"], p)
+    ref = Lr.learned_step(group, c["ob"]["g"], c["ob"]["H"], c["os"]["step"], c["sc"], c["ocfg"], p, c["gp"])
     n = c["n"]
     got = c["learned"][: ref.size].reshape(ref.shape)
     ref2 = ref.reshape(-1, n)
