@@ -139,6 +139,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w, gt_host, train_host, cams = make_workload(args.workload, seed_offset=rank)
+    if args.cams:
+        cams = cams[: args.cams]
     ncam = len(cams)
     W, H = w["width"], w["height"]
     ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=args.precision))
@@ -540,6 +542,7 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=12)
     ap.add_argument("--ref-crop", type=int, default=8)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (profiling captures)")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")

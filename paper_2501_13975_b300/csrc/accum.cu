@@ -77,16 +77,18 @@ __device__ __forceinline__ void falloff_derivs(float G, float ca, float cb, floa
 // holds fully reduced entries at distinct indices (PP/32 of them when PP >= 32,
 // or one entry shared by 32/PP lanes).  P (5 - 1/32) shuffles become about PP,
 // and the atomics are issued by many lanes at once instead of lane 0 alone.
+// A payload longer than 32 is reduced in two parts, the first 32 entries and
+// the rest (41 = 32 + 9 -> 32 + 16 padded slots instead of 64).
 template <int P> struct Pad { static constexpr int PP = P <= 2 ? 2 : P <= 4 ? 4 : P <= 8 ? 8 : P <= 16 ? 16 : P <= 32 ? 32 : 64; };
 
-template <int P, typename ACC>
-__device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], int lane, ACC *__restrict__ zbuf,
-                                                        int n, uint32_t k) {
-    constexpr int PP = Pad<P>::PP;
+template <int Q, int OFF, int P, typename ACC>
+__device__ __forceinline__ void reduce_scatter_part(const float (&pl)[P], int lane, ACC *__restrict__ zbuf, int n,
+                                                    uint32_t k) {
+    constexpr int PP = Pad<Q>::PP;
     float v[PP];
 #pragma unroll
-    for (int i = 0; i < PP; ++i) v[i] = (i < P) ? pl[i] : 0.f;
-    int off = 0;           // index of v[0] in the payload
+    for (int i = 0; i < PP; ++i) v[i] = (i < Q) ? pl[OFF + i] : 0.f;
+    int off = 0;           // index of v[0] in this part
     int len = PP;          // values this lane still holds
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -113,8 +115,19 @@ __device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], in
 #pragma unroll
         for (int j = 0; j < (PP >= 32 ? PP / 32 : 1); ++j) {
             const int idx = off + j;
-            if (idx < P && v[j] != 0.f) atomicAdd(&zbuf[(size_t)idx * n + k], (ACC)v[j]);
+            if (idx < Q && v[j] != 0.f) atomicAdd(&zbuf[(size_t)(OFF + idx) * n + k], (ACC)v[j]);
         }
+    }
+}
+
+template <int P, typename ACC>
+__device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], int lane, ACC *__restrict__ zbuf,
+                                                        int n, uint32_t k) {
+    if constexpr (P > 32) {
+        reduce_scatter_part<32, 0, P, ACC>(pl, lane, zbuf, n, k);
+        reduce_scatter_part<P - 32, 32, P, ACC>(pl, lane, zbuf, n, k);
+    } else {
+        reduce_scatter_part<P, 0, P, ACC>(pl, lane, zbuf, n, k);
     }
 }
 
@@ -125,8 +138,9 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
                                                         int W, int H, int tiles_x, float amin, float amax,
                                                         ACC *__restrict__ zbuf, int n) {
     constexpr int P = Payload<GROUP>::P;
-    __shared__ uint32_t sId[GS2_TILE_PIX];
-    __shared__ float4 sA[GS2_TILE_PIX], sB[GS2_TILE_PIX], sC[GS2_TILE_PIX];
+    // two staging buffers: batch b + 1 is copied in while batch b is walked
+    __shared__ uint32_t sId[2][GS2_TILE_PIX];
+    __shared__ float4 sA[2][GS2_TILE_PIX], sB[2][GS2_TILE_PIX], sC[2][GS2_TILE_PIX];
     __shared__ uint32_t sMax;
     const int t = threadIdx.x, lane = t & 31;
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
@@ -152,21 +166,38 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
     const uint2 r = ranges[tile];
     const float fx = (float)px, fy = (float)py;
     float cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
-    for (int bend = maxlast; bend > 0; bend -= GS2_TILE_PIX) {
-        const int bbeg = max(0, bend - GS2_TILE_PIX);
-        __syncthreads();
-        const int j = bbeg + t;
-        if (j < bend) {
-            const uint32_t k = ids[r.x + j];
-            sId[t] = k;
-            sA[t] = pv.recA[k];
-            sB[t] = pv.recB[k];
-            sC[t] = pv.col[k];
+    // batches back to front: batch b covers [max(0, maxlast - 256 (b + 1)), maxlast - 256 b)
+    const int nbat = (maxlast + GS2_TILE_PIX - 1) / GS2_TILE_PIX;
+    auto list_index = [&](int b) { return maxlast - GS2_TILE_PIX * (b + 1) + t; };   // this thread's entry
+    auto issue = [&](int b, uint32_t k) {
+        const int buf = b & 1;
+        if (list_index(b) >= 0) {
+            sId[buf][t] = k;
+            cp_async16(&sA[buf][t], &pv.recA[k]);
+            cp_async16(&sB[buf][t], &pv.recB[k]);
+            cp_async16(&sC[buf][t], &pv.col[k]);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    uint32_t knext = 0u;
+    if (nbat > 0) {
+        if (list_index(0) >= 0) knext = ids[r.x + list_index(0)];
+        issue(0, knext);
+        if (nbat > 1 && list_index(1) >= 0) knext = ids[r.x + list_index(1)];
+    }
+    for (int b = 0; b < nbat; ++b) {
+        cp_async_wait_all();
+        __syncthreads();   // batch b visible to all; everyone is done with batch b - 1's buffer
+        if (b + 1 < nbat) {
+            issue(b + 1, knext);
+            if (b + 2 < nbat && list_index(b + 2) >= 0) knext = ids[r.x + list_index(b + 2)];
+        }
+        const int buf = b & 1;
+        const int bend = maxlast - GS2_TILE_PIX * b, bbeg = max(0, bend - GS2_TILE_PIX);
+        const int base = bend - GS2_TILE_PIX;   // list index of slot 0 of this batch (may be negative)
         for (int jj = bend - 1; jj >= bbeg; --jj) {
-            const int s = jj - bbeg;
-            const float4 A = sA[s], B = sB[s];
+            const int s = jj - base;
+            const float4 A = sA[buf][s], B = sB[buf][s];
             bool act = inside && (uint32_t)jj < last;
             float G = 0.f, alpha = 0.f, dx = 0.f, dy = 0.f;
             bool clamped = false;
@@ -184,7 +215,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
 #pragma unroll
             for (int i = 0; i < P; ++i) pl[i] = 0.f;
             if (act) {
-                const float4 C = sC[s];
+                const float4 C = sC[buf][s];
                 const float Tk = __fdiv_rn(T, __fsub_rn(1.f, alpha));
                 const float w = alpha * Tk;
                 const float a0 = Tk * (C.x - cb0), a1 = Tk * (C.y - cb1), a2 = Tk * (C.z - cb2);
@@ -251,7 +282,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
                 cb2 = alpha * C.z + (1.f - alpha) * cb2;
                 T = Tk;
             }
-            warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[s]);
+            warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
         }
     }
 }

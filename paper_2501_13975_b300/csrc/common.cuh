@@ -208,6 +208,14 @@ __device__ __forceinline__ float gs2_quadform(float ca, float cb, float cc, floa
     return q;
 }
 
+// asynchronous 16-byte global -> shared copies (the batch staging pipeline)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Gaussian falloff G = exp(-q/2) at pixel offset (dx, dy)
 __device__ __forceinline__ float gs2_gauss(float ca, float cb, float cc, float dx, float dy) {
     return expf(__fmul_rn(-0.5f, gs2_quadform(ca, cb, cc, dx, dy)));

@@ -67,92 +67,153 @@ __global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, con
             sY[i] = in ? Y[(size_t)gy * W + gx] : 0.f;
         }
         __syncthreads();
-        // horizontal window sums of x, y, xx, yy, xy
-        for (int i = t; i < IN_H * MO_W; i += 256) {
-            const int r = i / MO_W, j = i % MO_W;
-            float a = 0.f, b = 0.f, cxx = 0.f, cyy = 0.f, cxy = 0.f;
+        // horizontal window sums of x, y, xx, yy, xy: a thread slides one
+        // window along HR consecutive outputs of a row (inputs read once)
+        constexpr int HR = 6, HSEG = MO_W / HR;   // 42 = 7 x 6
+        for (int i = t; i < IN_H * HSEG; i += 256) {
+            const int r = i / HSEG, j0 = (i % HSEG) * HR;
+            const float *xr = sX + r * IN_W + j0, *yr = sY + r * IN_W + j0;
+            float xv[HR + LWIN - 1], yv[HR + LWIN - 1];
 #pragma unroll
-            for (int d = 0; d < LWIN; ++d) {
-                const float xv = sX[r * IN_W + j + d], yv = sY[r * IN_W + j + d], w = K.g[d];
-                a = fmaf(w, xv, a);
-                b = fmaf(w, yv, b);
-                cxx = fmaf(w * xv, xv, cxx);
-                cyy = fmaf(w * yv, yv, cyy);
-                cxy = fmaf(w * xv, yv, cxy);
-            }
-            sH[0 * IN_H * MO_W + i] = a;
-            sH[1 * IN_H * MO_W + i] = b;
-            sH[2 * IN_H * MO_W + i] = cxx;
-            sH[3 * IN_H * MO_W + i] = cyy;
-            sH[4 * IN_H * MO_W + i] = cxy;
-        }
-        __syncthreads();
-        // vertical sums -> moments -> per-centre coefficients
-        for (int i = t; i < MO_H * MO_W; i += 256) {
-            const int r = i / MO_W, j = i % MO_W;
-            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int d = 0; d < LWIN; ++d) {
-                const float w = K.g[d];
-#pragma unroll
-                for (int q = 0; q < 5; ++q) m[q] = fmaf(w, sH[q * IN_H * MO_W + (r + d) * MO_W + j], m[q]);
-            }
-            const int gx = x0 - LRAD + j, gy = y0 - LRAD + r;
-            float co[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const float mu = m[0], mt = m[1];
-                const float var = m[2] - mu * mu, vart = m[3] - mt * mt, cov = m[4] - mu * mt;
-                const float f0 = 2.f * mu * mt + K.c1, f1 = 2.f * cov + K.c2;
-                const float f2 = mu * mu + mt * mt + K.c1, f3 = var + vart + K.c2;
-                const float D = f2 * f3, N = f0 * f1;
-                const float iD = 1.f / D, iD2 = iD * iD, iD3 = iD2 * iD;
-                const float d10 = f1 - f0, d32 = f3 - f2;
-                co[0] = 2.f * mt * d10 * iD - 2.f * N * mu * d32 * iD2;                       // A
-                co[1] = 2.f * f0 * iD;                                                        // B
-                co[2] = -2.f * N * f2 * iD2;                                                  // C
-                co[3] = -8.f * mt * mt * iD - 8.f * mt * mu * d10 * d32 * iD2                 // K0
-                        - N * (2.f * f3 - 2.f * f2 - 8.f * mu * mu) * iD2 + 8.f * N * mu * mu * d32 * d32 * iD3;
-                co[4] = -8.f * mt * d10 * f2 * iD2 - 8.f * N * mu * iD2 + 16.f * N * mu * d32 * f2 * iD3;  // Kc
-                co[5] = 8.f * mt * iD - 8.f * f0 * mu * d32 * iD2;                            // Kt
-                co[6] = -8.f * f0 * f2 * iD2;                                                 // Kct
-                co[7] = 8.f * N * f2 * f2 * iD3;                                              // Kcc
-                if (j >= LRAD && j < LRAD + LT_W && r >= LRAD && r < LRAD + LT_H) lsacc += 1.0 - (double)(N * iD);
+            for (int d = 0; d < HR + LWIN - 1; ++d) {
+                xv[d] = xr[d];
+                yv[d] = yr[d];
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) sK[q * MO_H * MO_W + i] = co[q];
+            for (int o = 0; o < HR; ++o) {
+                float a = 0.f, b = 0.f, cxx = 0.f, cyy = 0.f, cxy = 0.f;
+#pragma unroll
+                for (int d = 0; d < LWIN; ++d) {
+                    const float x = xv[o + d], y = yv[o + d], w = K.g[d];
+                    a = fmaf(w, x, a);
+                    b = fmaf(w, y, b);
+                    cxx = fmaf(w * x, x, cxx);
+                    cyy = fmaf(w * y, y, cyy);
+                    cxy = fmaf(w * x, y, cxy);
+                }
+                const int q = r * MO_W + j0 + o;
+                sH[0 * IN_H * MO_W + q] = a;
+                sH[1 * IN_H * MO_W + q] = b;
+                sH[2 * IN_H * MO_W + q] = cxx;
+                sH[3 * IN_H * MO_W + q] = cyy;
+                sH[4 * IN_H * MO_W + q] = cxy;
+            }
         }
         __syncthreads();
-        // horizontal correlation of the coefficient maps (w for A, B, C; w^2 for the rest)
-        for (int i = t; i < 8 * MO_H * LT_W; i += 256) {
-            const int q = i / (MO_H * LT_W), rem = i % (MO_H * LT_W);
-            const int r = rem / LT_W, j = rem % LT_W;
-            const float *wt = (q < 3) ? K.g : K.g2;
-            float acc = 0.f;
+        // vertical sums -> moments -> per-centre coefficients: a thread slides
+        // down VR consecutive window centres of a column
+        constexpr int VR = 4, VSEG = (MO_H + VR - 1) / VR;   // 26 rows in 7 runs
+        for (int i = t; i < MO_W * VSEG; i += 256) {
+            const int j = i % MO_W, r0 = (i / MO_W) * VR;
+            const int nr = min(VR, MO_H - r0);
+            float m[VR][5];
 #pragma unroll
-            for (int d = 0; d < LWIN; ++d) acc = fmaf(wt[d], sK[q * MO_H * MO_W + r * MO_W + j + d], acc);
-            sHC[i] = acc;
+            for (int o = 0; o < VR; ++o)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) m[o][q] = 0.f;
+#pragma unroll
+            for (int d = 0; d < VR + LWIN - 1; ++d) {
+                if (r0 + d >= IN_H) break;
+                float hv[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) hv[q] = sH[q * IN_H * MO_W + (r0 + d) * MO_W + j];
+#pragma unroll
+                for (int o = 0; o < VR; ++o) {
+                    const int tap = d - o;
+                    if (tap >= 0 && tap < LWIN) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) m[o][q] = fmaf(K.g[tap], hv[q], m[o][q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < VR; ++o) {
+                if (o >= nr) break;
+                const int r = r0 + o;
+                const int gx = x0 - LRAD + j, gy = y0 - LRAD + r;
+                float co[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                    const float mu = m[o][0], mt = m[o][1];
+                    const float var = m[o][2] - mu * mu, vart = m[o][3] - mt * mt, cov = m[o][4] - mu * mt;
+                    const float f0 = 2.f * mu * mt + K.c1, f1 = 2.f * cov + K.c2;
+                    const float f2 = mu * mu + mt * mt + K.c1, f3 = var + vart + K.c2;
+                    const float D = f2 * f3, N = f0 * f1;
+                    const float iD = 1.f / D, iD2 = iD * iD, iD3 = iD2 * iD;
+                    const float d10 = f1 - f0, d32 = f3 - f2;
+                    co[0] = 2.f * mt * d10 * iD - 2.f * N * mu * d32 * iD2;                       // A
+                    co[1] = 2.f * f0 * iD;                                                        // B
+                    co[2] = -2.f * N * f2 * iD2;                                                  // C
+                    co[3] = -8.f * mt * mt * iD - 8.f * mt * mu * d10 * d32 * iD2                 // K0
+                            - N * (2.f * f3 - 2.f * f2 - 8.f * mu * mu) * iD2 + 8.f * N * mu * mu * d32 * d32 * iD3;
+                    co[4] = -8.f * mt * d10 * f2 * iD2 - 8.f * N * mu * iD2 + 16.f * N * mu * d32 * f2 * iD3;  // Kc
+                    co[5] = 8.f * mt * iD - 8.f * f0 * mu * d32 * iD2;                            // Kt
+                    co[6] = -8.f * f0 * f2 * iD2;                                                 // Kct
+                    co[7] = 8.f * N * f2 * f2 * iD3;                                              // Kcc
+                    if (j >= LRAD && j < LRAD + LT_W && r >= LRAD && r < LRAD + LT_H) lsacc += 1.0 - (double)(N * iD);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sK[q * MO_H * MO_W + r * MO_W + j] = co[q];
+            }
         }
         __syncthreads();
-        for (int i = t; i < LT_H * LT_W; i += 256) {
-            const int r = i / LT_W, j = i % LT_W;
-            const int gx = x0 + j, gy = y0 + r;
-            if (gx >= W || gy >= H) continue;
-            float v[8];
+        // horizontal correlation of the coefficient maps (w for A, B, C; w^2
+        // for the rest), CR consecutive outputs of a row per thread
+        constexpr int CR = 8, CSEG = LT_W / CR;   // 32 = 4 x 8
+        for (int i = t; i < 8 * MO_H * CSEG; i += 256) {
+            const int q = i / (MO_H * CSEG), rem = i % (MO_H * CSEG);
+            const int r = rem / CSEG, j0 = (rem % CSEG) * CR;
+            const float *src = sK + q * MO_H * MO_W + r * MO_W + j0;
+            float v[CR + LWIN - 1];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float *wt = (q < 3) ? K.g : K.g2;
+            for (int d = 0; d < CR + LWIN - 1; ++d) v[d] = src[d];
+            float wt[LWIN];
+#pragma unroll
+            for (int d = 0; d < LWIN; ++d) wt[d] = (q < 3) ? K.g[d] : K.g2[d];
+#pragma unroll
+            for (int o = 0; o < CR; ++o) {
                 float acc = 0.f;
 #pragma unroll
-                for (int d = 0; d < LWIN; ++d) acc = fmaf(wt[d], sHC[q * MO_H * LT_W + (r + d) * LT_W + j], acc);
-                v[q] = acc;
+                for (int d = 0; d < LWIN; ++d) acc = fmaf(wt[d], v[o + d], acc);
+                sHC[q * MO_H * LT_W + r * LT_W + j0 + o] = acc;
             }
+        }
+        __syncthreads();
+        // vertical correlation and the per-pixel derivatives: a thread slides
+        // down OR output rows of a column
+        constexpr int OR = 2, OSEG = LT_H / OR;   // 16 = 8 x 2
+        for (int i = t; i < LT_W * OSEG; i += 256) {
+            const int j = i % LT_W, r0 = (i / LT_W) * OR;
+            float v[OR][8];
+#pragma unroll
+            for (int o = 0; o < OR; ++o)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[o][q] = 0.f;
+#pragma unroll
+            for (int d = 0; d < OR + LWIN - 1; ++d) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float hv = sHC[q * MO_H * LT_W + (r0 + d) * LT_W + j];
+#pragma unroll
+                    for (int o = 0; o < OR; ++o) {
+                        const int tap = d - o;
+                        if (tap >= 0 && tap < LWIN) v[o][q] = fmaf(q < 3 ? K.g[tap] : K.g2[tap], hv, v[o][q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < OR; ++o) {
+            const int r = r0 + o;
+            const int gx = x0 + j, gy = y0 + r;
+            if (gx >= W || gy >= H) continue;
             const float x = sX[(r + 2 * LRAD) * IN_W + j + 2 * LRAD], y = sY[(r + 2 * LRAD) * IN_W + j + 2 * LRAD];
-            const float dS = v[0] + y * v[1] + x * v[2];
-            const float d2S = v[3] + x * v[4] + y * v[5] + x * y * v[6] + x * x * v[7] + v[2];
+            const float *vo = v[o];
+            const float dS = vo[0] + y * vo[1] + x * vo[2];
+            const float d2S = vo[3] + x * vo[4] + y * vo[5] + x * y * vo[6] + x * x * vo[7] + vo[2];
             const size_t p = (size_t)c * P + (size_t)gy * W + gx;
             eo[p] = K.scale * (x - y) - K.lam * K.scale * dS;
             ho[p] = K.scale - K.lam * K.scale * d2S;
             l2acc += 0.5 * (double)(x - y) * (double)(x - y);
+            }
         }
         __syncthreads();
     }

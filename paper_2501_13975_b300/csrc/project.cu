@@ -11,9 +11,14 @@
 // Memory: reads 13 + 3S floats per Gaussian from planar SoA rows (coalesced
 // 4-byte loads across the warp), writes 3 float4 records + rect + counts.
 // HBM-bound; FP64 is used only for the depth key (4 DFMA-equivalent ops).
+// The kernel is instantiated per SH count S, so every parameter load of a
+// visible Gaussian (4 + 3 + 3S rows) is unrolled and issued before the
+// arithmetic: a warp keeps all of them in flight at once instead of meeting
+// the memory latency once per loop iteration.
 #include "common.cuh"
 #include "sh.cuh"
 
+template <int S>
 __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float lowpass, float near_z,
                                                  float alpha_min, ProjView pv, int tiles_x, int tiles_y) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,19 +43,23 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
         pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
+    // every remaining parameter load first (independent, all in flight together)
+    float shc[3 * S];
+#pragma unroll
+    for (int i = 0; i < 3 * S; ++i) shc[i] = __ldcs(sc.sh + (size_t)i * n + k);
+    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
+    const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
     const float *V = cam.V;
     const float tx = fmaf(V[0], px, fmaf(V[1], py, fmaf(V[2], pz, V[3])));
     const float ty = fmaf(V[4], px, fmaf(V[5], py, fmaf(V[6], pz, V[7])));
 
     // rotation from the normalised quaternion
-    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
     const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     qw *= qn; qx *= qn; qy *= qn; qz *= qn;
     float R[3][3];
     R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
     R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
     R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
-    const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
 
     // T = J Wr (2x3); J uses tx/tz, ty/tz clamped to the camera's frustum limits
     const float itz = 1.f / tz;
@@ -118,24 +127,31 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
     const float rn = rsqrtf(rxv * rxv + ryv * ryv + rzv * rzv);
     rxv *= rn; ryv *= rn; rzv *= rn;
     float phi[GS2_MAX_SH];
-    sh_phi(sc.S, rxv, ryv, rzv, phi);
+    sh_phi(S, rxv, ryv, rzv, phi);
     float col[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float acc = 0.f;
-        for (int i = 0; i < sc.S; ++i) acc = fmaf(sh_norm(i) * phi[i], sc.sh[(size_t)(c * sc.S + i) * n + k], acc);
+#pragma unroll
+        for (int i = 0; i < S; ++i) acc = fmaf(sh_norm(i) * phi[i], shc[c * S + i], acc);
         col[c] = acc;
     }
+    // recB.w, col.w: the support's half extents in pixels
     pv.recA[k] = make_float4(pix_x, pix_y, ca, cb);
-    pv.recB[k] = make_float4(cc, sigma, tz, 0.f);
-    pv.col[k] = make_float4(col[0], col[1], col[2], 0.f);
+    pv.recB[k] = make_float4(cc, sigma, tz, rx);
+    pv.col[k] = make_float4(col[0], col[1], col[2], ry);
 }
 
 cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
                            int tiles_y, cudaStream_t st) {
     if (sc.n == 0) return cudaSuccess;
-    k_project<<<(sc.n + 255) / 256, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x,
-                                                   tiles_y);
+    const unsigned grid = (sc.n + 255) / 256;
+    switch (sc.S) {
+    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
+    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
+    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
+    default: k_project<16><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
+    }
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

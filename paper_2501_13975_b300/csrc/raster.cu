@@ -1,7 +1,8 @@
 // gs2_raster_fwd compositing (Eq. 3dgs): one 16x16 CTA per screen tile, one
 // thread per pixel, the tile's depth-sorted Gaussian list staged through
 // shared memory in batches of 256 records (one record gather per thread per
-// batch; the per-pixel inner loop reads shared memory only).
+// batch, copied asynchronously into the second buffer while the first is
+// walked; the per-pixel inner loop reads shared memory only).
 //   alpha = min(sigma G, alpha_max); skip alpha < alpha_min; stop before
 //   T (1 - alpha) < t_min; c += alpha T c~; black background.
 // Writes the planar image, the final transmittance and the list position
@@ -12,7 +13,8 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
                                                          const uint32_t *__restrict__ ids, ProjView pv, int W, int H,
                                                          int tiles_x, float amin, float amax, float tmin,
                                                          float *__restrict__ image, RasterView rv) {
-    __shared__ float4 sA[GS2_TILE_PIX], sB[GS2_TILE_PIX], sC[GS2_TILE_PIX];
+    // two staging buffers: batch b + 1 is copied in (cp.async) while batch b is walked
+    __shared__ float4 sA[2][GS2_TILE_PIX], sB[2][GS2_TILE_PIX], sC[2][GS2_TILE_PIX];
     const int t = threadIdx.x;
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
     const int px = blockIdx.x * GS2_TILE + (t % GS2_TILE), py = blockIdx.y * GS2_TILE + (t / GS2_TILE);
@@ -23,20 +25,35 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
     const float fx = (float)px, fy = (float)py;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
     uint32_t lastc = 0u;
-    for (int b0 = 0; b0 < n; b0 += GS2_TILE_PIX) {
-        if (__syncthreads_count(done) == GS2_TILE_PIX) break;
-        const int j = b0 + t;
-        if (j < n) {
-            const uint32_t k = ids[r.x + j];
-            sA[t] = pv.recA[k];
-            sB[t] = pv.recB[k];
-            sC[t] = pv.col[k];
+    const int nbat = (n + GS2_TILE_PIX - 1) / GS2_TILE_PIX;
+    auto issue = [&](int b, uint32_t k) {
+        const int buf = b & 1;
+        if (b * GS2_TILE_PIX + t < n) {
+            cp_async16(&sA[buf][t], &pv.recA[k]);
+            cp_async16(&sB[buf][t], &pv.recB[k]);
+            cp_async16(&sC[buf][t], &pv.col[k]);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    uint32_t knext = 0u;
+    if (nbat > 0) {
+        if (t < n) knext = ids[r.x + t];
+        issue(0, knext);
+        if (GS2_TILE_PIX + t < n) knext = ids[r.x + GS2_TILE_PIX + t];
+    }
+    for (int b = 0; b < nbat; ++b) {
+        cp_async_wait_all();
+        if (__syncthreads_count(done) == GS2_TILE_PIX) break;   // also: batch b visible, b - 1's buffer free
+        if (b + 1 < nbat) {
+            issue(b + 1, knext);
+            const int j2 = (b + 2) * GS2_TILE_PIX + t;
+            if (j2 < n) knext = ids[r.x + j2];
+        }
+        const int buf = b & 1, b0 = b * GS2_TILE_PIX;
         const int m = min(GS2_TILE_PIX, n - b0);
         for (int i = 0; i < m && !done; ++i) {
-            const float4 A = sA[i];
-            const float4 B = sB[i];
+            const float4 A = sA[buf][i];
+            const float4 B = sB[buf][i];
             const float G = gs2_gauss(A.z, A.w, B.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
             const float alpha = fminf(__fmul_rn(B.y, G), amax);
             if (alpha < amin) continue;
@@ -45,7 +62,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
                 done = true;
                 break;
             }
-            const float4 C = sC[i];
+            const float4 C = sC[buf][i];
             const float wgt = alpha * T;
             c0 = fmaf(wgt, C.x, c0);
             c1 = fmaf(wgt, C.y, c1);
