@@ -290,6 +290,108 @@ def run_gpu(args, rank, world, local_rank):
     return result, (w, train_host, cams)
 
 
+# ----------------------------------------------------------------------------- batched scenes
+
+def run_batched(args):
+    """Batched form: 16 independent scenes (Gaussian counts log-uniform in
+    [20k, 500k], 16-128 views, 512x512 to 1024x768, SH degree 3, shells and
+    spread scenes alternating; seed 8) swept together, one sweep per scene per
+    batched sweep (primary = sweep index mod views).  Per scene the kernel
+    tuning is chosen by gs2_autotune first.  Timed per batched sweep with CUDA
+    events: the scenes one after another on one stream, the scenes forked
+    onto their own streams, and the same captured as one CUDA graph; scenes/s
+    = scenes x sweeps / time."""
+    import ctypes as C
+
+    import torch
+    from paper_2501_13975_b300 import gs2
+
+    torch.cuda.set_device(0)
+    work = synth.batched_workload(seed=8)
+    sizes = [dict(max_gaussians=w["n"], max_width=w["width"], max_height=w["height"], max_sh_degree=3,
+                  max_pairs=96 * w["n"]) for w in work]
+    batch = gs2.Batch(sizes)
+    stream = torch.cuda.current_stream()
+    starts, scenes, targets, knns = [], [], [], []
+    for w in work:
+        tmp = gs2.Context(w["n"], w["width"], w["height"], 3, 96 * w["n"])
+        gt = gs2.DeviceScene.from_host(w["gt"])
+        proj = tmp.proj_buffer(w["n"])
+        tg = []
+        for c in w["cams"]:
+            tmp.project(gt, c, proj)
+            img, _ = tmp.raster_fwd(gt, c, proj)
+            tg.append(img.clone())
+        ds = gs2.DeviceScene.from_host(w["train"])
+        sphere = tmp.bounding_sphere(ds).cpu().numpy()
+        centres = np.stack([c.center() for c in w["cams"]]).astype(np.float32)
+        knns.append(gs2.camera_knn(centres, sphere, 3))
+        targets.append(tg)
+        scenes.append(ds)
+        starts.append(ds.clone())
+        tmp.close()
+    torch.cuda.synchronize()
+    tuning = []
+    t0 = time.perf_counter()
+    if not args.no_autotune:
+        for i, w in enumerate(work):
+            tuning.append(batch.autotune(i, scenes[i], w["cams"], targets[i], knns[i], 0, reps=2))
+    t_tune = time.perf_counter() - t0
+    prep = batch.prepare(scenes, [w["cams"] for w in work], targets, knns)
+    views = [w["views"] for w in work]
+
+    def restore():
+        for ds, st0 in zip(scenes, starts):
+            for name in ("mean", "quat", "scale", "opacity", "sh"):
+                getattr(ds, name).copy_(getattr(st0, name))
+
+    def timed(mode, steps, warmup):
+        restore()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(warmup + steps):
+            t = [i % v for v in views]
+            if i >= warmup:
+                ev[i - warmup][0].record(stream)
+            if mode == "sequential":
+                for s in range(len(work)):
+                    gs2._lib.gs2_sweep(batch.ctx_handle(s), C.byref(prep["scenes"][s]), prep["cams"][s],
+                                       len(work[s]["cams"]), prep["tgts"][s], prep["knn"][s], t[s], None, None,
+                                       gs2._stream(None))
+            else:
+                batch.sweep(prep, t, use_graph=(mode == "graph"))
+            if i >= warmup:
+                ev[i - warmup][1].record(stream)
+        torch.cuda.synchronize()
+        batch.check()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        return {"scenes_per_s": round(len(work) * steps / (ms.sum() * 1e-3), 3),
+                "ms_per_batched_sweep": {"p50": round(float(np.percentile(ms, 50)), 3),
+                                         "p99": round(float(np.percentile(ms, 99)), 3),
+                                         "mean": round(float(ms.mean()), 3)}}
+
+    res = {}
+    l0 = gs2.launch_count()
+    for mode in ("sequential", "streams", "graph"):
+        res[mode] = timed(mode, args.steps, args.warmup)
+    launches = gs2.launch_count() - l0
+    head = res["graph"]
+    return {
+        "metric": "scenes/s (batched sweeps, 16 independent scenes)", "value": head["scenes_per_s"],
+        "unit": "scenes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["ms_per_batched_sweep"]["mean"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched: 16 scenes, N log-uniform [20k, 500k], 16-128 views, 512x512..1024x768, "
+                               "SH3, shells and spread scenes alternating (seed 8)",
+                   "gaussians_total": int(sum(w["n"] for w in work)),
+                   "scenes": [{k: w[k] for k in ("kind", "n", "views", "width", "height")} for w in work],
+                   "sweep_restart": "every mode starts from the training start"},
+        "modes": res,
+        "graph": batch.stats(),
+        "autotune": {"seconds": round(t_tune, 2), "choices": tuning},
+        "gpu_launches": int(launches),
+    }
+
+
 # ----------------------------------------------------------------------------- time to PSNR
 
 def time_to_psnr(args):
@@ -537,12 +639,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs2", choices=["gs2", "reference"])
-    ap.add_argument("--workload", default="scene", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="scene", choices=list(WORKLOADS) + ["batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=12)
     ap.add_argument("--ref-crop", type=int, default=8)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (profiling captures)")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default tuning")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")
@@ -559,6 +662,10 @@ def main():
     if args.ttp:
         if rank == 0:
             print(json.dumps(time_to_psnr(args)), flush=True)
+        return
+    if args.workload == "batched" and args.impl == "gs2":
+        if rank == 0:
+            print(json.dumps(run_batched(args)), flush=True)
         return
 
     if args.impl == "reference":

@@ -305,6 +305,55 @@ gs2_status gs2_mlp_grad(const uint16_t *w_bf16, const float *records, int64_t ch
 gs2_status gs2_mlp_adam(float *master, uint16_t *w_bf16, const float *partial, const double *stats, float *m,
                         float *v, int32_t step, float lr, float beta1, float beta2, float eps, gs2_stream stream);
 
+/* Kernel tuning of a context (no effect on results: the sort is stable and
+ * exact for every setting).
+ *   sort_blocks: CTAs of every radix-sort pass (1..1024; default 592)
+ *   sort_rows:   keys per thread per scatter round (2, 4 or 8; default 4)
+ * gs2_autotune times `reps` sweeps with primary t for every candidate
+ * (sort_blocks 296, 592, 888 x sort_rows 2, 4, 8) on a scratch copy of the
+ * scene (the caller's scene is not changed), keeps the fastest in ctx and
+ * returns it and its ms per sweep (host outputs, may be NULL).  It allocates
+ * the copy, synchronises the stream and must not run under stream capture. */
+typedef struct {
+    int32_t sort_blocks;
+    int32_t sort_rows;
+} gs2_tuning;
+gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out);
+gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *tuning);
+gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                        const float *const *targets, const int32_t *knn, int32_t t, int32_t reps, gs2_tuning *best,
+                        float *best_ms, gs2_stream stream);
+
+/* Batched sweeps over independent scenes (an extension: the paper trains one
+ * scene at a time).  A batch owns one context and one stream per scene
+ * (created with cfg and the scene's maxima).  gs2_batch_sweep runs one
+ * gs2_sweep per scene (scene i: scenes[i], cams[i][ncam[i]], targets[i][],
+ * knn[i][], primary t[i]; host arrays of n_scenes entries), all forked from
+ * `stream` onto the scenes' streams and joined back, so the scenes' kernels
+ * share the GPU.  losses_out: device double [n_scenes][10] (+=) or NULL;
+ * n_failed: device int [n_scenes] (+=) or NULL.  use_graph = 1 captures the
+ * fork/join as one CUDA graph (on a stream of the batch, so `stream` may be
+ * the legacy default stream) and launches it on `stream`; the instantiated
+ * graph is kept and updated in place on later calls (re-instantiated if the
+ * update is refused).  A context's first use must not be under capture: create the
+ * batch before capturing anything.  gs2_batch_ctx gives scene i's context
+ * (for tuning or checks); gs2_batch_stats the graph instantiation and update
+ * counts. */
+typedef struct gs2_batch gs2_batch;
+typedef struct {
+    int64_t max_gaussians;
+    int32_t max_width, max_height, max_sh_degree;
+    int64_t max_pairs;
+} gs2_batch_scene;
+gs2_status gs2_batch_create(gs2_batch **out, const gs2_config *cfg, int32_t n_scenes, const gs2_batch_scene *desc);
+gs2_status gs2_batch_destroy(gs2_batch *batch);
+gs2_ctx *gs2_batch_ctx(gs2_batch *batch, int32_t i);
+const char *gs2_batch_last_error(const gs2_batch *batch);
+gs2_status gs2_batch_stats(const gs2_batch *batch, int32_t *instantiations, int32_t *updates);
+gs2_status gs2_batch_sweep(gs2_batch *batch, gs2_scene *scenes, const gs2_camera *const *cams, const int32_t *ncam,
+                           const float *const *const *targets, const int32_t *const *knn, const int32_t *t,
+                           double *losses_out, int32_t *n_failed, int32_t use_graph, gs2_stream stream);
+
 /* Instrumentation.
  * gs2_launch_count: kernels launched by this library in this process so far.
  * gs2_profile(ctx, 1): from now on record CUDA events around every

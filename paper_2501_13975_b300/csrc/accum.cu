@@ -477,7 +477,7 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
 //   Sigma_ab = f_a f_b u^2 Q_ab(tau) (+ low-pass), tau_a = clamp(t_a u),
 // V the camera-space 3D covariance (J V J^T written out); derivatives by the
 // chain rule through the intermediates (u, tau_x, tau_y).
-template <typename ACC>
+template <typename ACC, int S>
 __global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf,
                                                  float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const 
     float t[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * g.p[0] + V[i * 4 + 1] * g.p[1] + V[i * 4 + 2] * g.p[2] + V[i * 4 + 3];
-    const float u = 1.f / t[2], u2 = u * u, u3 = u2 * u, u4 = u2 * u2;
+    const float u = 1.f / t[2], u2 = u * u, u3 = u2 * u;
     // camera-space covariance Vc = (Wr R diag(s)) (Wr R diag(s))^T
     float M3[3][3];
 #pragma unroll
@@ -650,12 +650,12 @@ __global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const 
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) Pm[a][b] = ((a == b ? 1.f : 0.f) - r[a] * r[b]) * irho;
-    const int S = sc.S;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         const float WE = z[35 + ch], SS = z[38 + ch];
-        float wco[GS2_MAX_SH];
-        for (int i = 0; i < S; ++i) wco[i] = sh_norm(i) * sc.sh[(size_t)(ch * S + i) * n + k];
+        float wco[S];   // unrolled: the S loads of a channel are in flight together
+#pragma unroll
+        for (int i = 0; i < S; ++i) wco[i] = sh_norm(i) * __ldcs(sc.sh + (size_t)(ch * S + i) * n + k);
         float fv, gr[3], hs[6];
         sh_poly_derivs(S, wco, r[0], r[1], r[2], fv, gr, hs);
         const float Hr[3][3] = {{hs[0], hs[1], hs[2]}, {hs[1], hs[3], hs[4]}, {hs[2], hs[4], hs[5]}};
@@ -721,7 +721,14 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     const int eg = (n + 255) / 256;
     float *b = (float *)blocks;
     switch (group) {
-    case GS2_POS: k_epi_pos<ACC><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+    case GS2_POS:
+        switch (sc.S) {
+        case 1: k_epi_pos<ACC, 1><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+        case 4: k_epi_pos<ACC, 4><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+        case 9: k_epi_pos<ACC, 9><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+        default: k_epi_pos<ACC, 16><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+        }
+        break;
     case GS2_ROT: k_epi_rot<ACC><<<eg, 256, 0, st>>>(sc, view, primary, pv, zb, b); break;
     case GS2_SCALE: k_epi_scale<ACC><<<eg, 256, 0, st>>>(sc, view, pv, zb, b); break;
     case GS2_OPACITY: k_epi_opacity<ACC><<<eg, 256, 0, st>>>(pv, zb, n, b); break;
@@ -735,7 +742,6 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
 cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st) {
-    const int n = sc.n;
     dim3 grid(ctx->tiles_x, ctx->tiles_y);
     const uint32_t *ids = ctx->vals[ctx->sorted];
     const bool prof = ctx->prof_on && ctx->prof_n < 512;

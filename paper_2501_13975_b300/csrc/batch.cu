@@ -1,0 +1,268 @@
+// Batched sweeps over many independent scenes, kernel tuning and its autotuner
+// (an extension for throughput over many scenes; the paper trains one scene).
+//
+// gs2_batch owns one context and one stream per scene.  A batched sweep forks
+// every scene's sweep (Sec. 4.2 groups with the Sec. 4.3 secondaries) onto its
+// stream from the caller's stream and joins them back, so scenes of uneven
+// size fill the 148 SMs together: small scenes' kernels run beside a large
+// scene's instead of after it.  With use_graph the fork/join is captured as
+// one CUDA graph (one parallel branch per scene) and launched with a single
+// cudaGraphLaunch; later calls re-capture (the primaries change from sweep to
+// sweep, and with them the kernels' camera arguments) and update the
+// instantiated graph in place with cudaGraphExecUpdate, which succeeds while
+// the graph's shape (kernel sequence) is unchanged.
+//
+// Tuning: the radix sort's grid (CTAs) and keys per thread per scatter round.
+// The autotuner times whole sweeps on a scratch copy of the scene for every
+// candidate and keeps the fastest in the context.
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+#define RETC(expr)                                  \
+    do {                                            \
+        if ((expr) != cudaSuccess) return GS2_ERR_CUDA; \
+    } while (0)
+
+// batch variant: records the failing call in the batch
+#define RETB(b, expr)                                                                  \
+    do {                                                                               \
+        const cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess) {                                                       \
+            (b)->err = std::string(#expr) + ": " + cudaGetErrorString(e_);             \
+            return GS2_ERR_CUDA;                                                       \
+        }                                                                              \
+    } while (0)
+
+extern "C" gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out) {
+    if (!ctx || !out) return GS2_ERR_ARG;
+    out->sort_blocks = ctx->nb_sort;
+    out->sort_rows = ctx->sort_rows;
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *t) {
+    if (!ctx || !t) return GS2_ERR_ARG;
+    if (t->sort_blocks < 1 || t->sort_blocks > GS2_SORT_BLOCKS_MAX) return GS2_ERR_ARG;
+    if (t->sort_rows != 2 && t->sort_rows != 4 && t->sort_rows != 8) return GS2_ERR_ARG;
+    ctx->nb_sort = t->sort_blocks;
+    ctx->sort_rows = t->sort_rows;
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                                   const float *const *targets, const int32_t *knn, int32_t t, int32_t reps,
+                                   gs2_tuning *best_out, float *best_ms_out, gs2_stream stream) {
+    if (!ctx || !scene || !cams || !targets || reps < 1 || ncam < 1 || t < 0 || t >= ncam) return GS2_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = scene->n, S = sh_count(scene->sh_degree);
+    // scratch copy of the scene: the timed sweeps must not move the caller's
+    const size_t floats = (size_t)n * (3 + 4 + 3 + 1 + 3 * (size_t)S);
+    float *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(float) * (floats > 0 ? floats : 1)) != cudaSuccess) return GS2_ERR_OOM;
+    gs2_scene cp = *scene;
+    cp.mean = buf;
+    cp.quat = cp.mean + 3 * (size_t)n;
+    cp.scale = cp.quat + 4 * (size_t)n;
+    cp.opacity = cp.scale + 3 * (size_t)n;
+    cp.sh = cp.opacity + (size_t)n;
+    auto reset = [&]() {
+        return cudaMemcpyAsync(cp.mean, scene->mean, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+               cudaMemcpyAsync(cp.quat, scene->quat, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+               cudaMemcpyAsync(cp.scale, scene->scale, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+               cudaMemcpyAsync(cp.opacity, scene->opacity, sizeof(float) * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+               cudaMemcpyAsync(cp.sh, scene->sh, sizeof(float) * 3 * S * (size_t)n, cudaMemcpyDeviceToDevice, st) ==
+                   cudaSuccess;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gs2_status rc = GS2_OK;
+    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows};
+    gs2_tuning best = keep;
+    float best_ms = 1e30f;
+    const int blocks[3] = {148 * 2, 148 * 4, 148 * 6};
+    const int rows[3] = {2, 4, 8};
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = GS2_ERR_CUDA;
+    for (int bi = 0; bi < 3 && rc == GS2_OK; ++bi)
+        for (int ri = 0; ri < 3 && rc == GS2_OK; ++ri) {
+            ctx->nb_sort = blocks[bi];
+            ctx->sort_rows = rows[ri];
+            if (!reset()) { rc = GS2_ERR_CUDA; break; }
+            // one untimed sweep (first-touch effects), then the timed ones
+            rc = sweep_run(ctx, &cp, cams, ncam, targets, knn, t, nullptr, nullptr, nullptr, st);
+            if (rc != GS2_OK) break;
+            if (!reset() || cudaEventRecord(e0, st) != cudaSuccess) { rc = GS2_ERR_CUDA; break; }
+            for (int r = 0; r < reps && rc == GS2_OK; ++r)
+                rc = sweep_run(ctx, &cp, cams, ncam, targets, knn, t, nullptr, nullptr, nullptr, st);
+            if (rc != GS2_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = GS2_ERR_CUDA; break; }
+            ms /= (float)reps;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = {blocks[bi], rows[ri]};
+            }
+        }
+    cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc != GS2_OK) {
+        ctx->nb_sort = keep.sort_blocks;
+        ctx->sort_rows = keep.sort_rows;
+        return rc;
+    }
+    ctx->nb_sort = best.sort_blocks;
+    ctx->sort_rows = best.sort_rows;
+    if (best_out) *best_out = best;
+    if (best_ms_out) *best_ms_out = best_ms;
+    return GS2_OK;
+}
+
+// ------------------------------------------------------------------ batch
+struct gs2_batch {
+    std::vector<gs2_ctx *> ctx;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, ready = nullptr;
+    cudaStream_t cap = nullptr;   // capture origin (the caller's stream may be the legacy default stream)
+    cudaGraphExec_t exec = nullptr;
+    int graph_updates = 0, graph_instantiations = 0;
+    std::string err;
+};
+
+static void batch_free(gs2_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ready) cudaEventDestroy(b->ready);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (gs2_ctx *c : b->ctx)
+        if (c) gs2_destroy(c);
+}
+
+extern "C" gs2_status gs2_batch_create(gs2_batch **out, const gs2_config *cfg, int32_t n_scenes,
+                                       const gs2_batch_scene *desc) {
+    if (!out || n_scenes < 1 || !desc) return GS2_ERR_ARG;
+    *out = nullptr;
+    gs2_batch *b = new (std::nothrow) gs2_batch();
+    if (!b) return GS2_ERR_OOM;
+    b->ctx.assign(n_scenes, nullptr);
+    b->streams.assign(n_scenes, nullptr);
+    b->join.assign(n_scenes, nullptr);
+    gs2_status rc = GS2_OK;
+    for (int i = 0; i < n_scenes && rc == GS2_OK; ++i) {
+        rc = gs2_create(&b->ctx[i], cfg, desc[i].max_gaussians, desc[i].max_width, desc[i].max_height,
+                        desc[i].max_sh_degree, desc[i].max_pairs);
+        if (rc == GS2_OK && (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+                             cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess))
+            rc = GS2_ERR_CUDA;
+    }
+    if (rc == GS2_OK && (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess))
+        rc = GS2_ERR_CUDA;
+    if (rc != GS2_OK) {
+        batch_free(b);
+        delete b;
+        cudaGetLastError();
+        return rc;
+    }
+    *out = b;
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_batch_destroy(gs2_batch *b) {
+    if (!b) return GS2_ERR_ARG;
+    batch_free(b);
+    delete b;
+    return GS2_OK;
+}
+
+extern "C" gs2_ctx *gs2_batch_ctx(gs2_batch *b, int32_t i) {
+    if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+    return b->ctx[i];
+}
+
+extern "C" const char *gs2_batch_last_error(const gs2_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" gs2_status gs2_batch_stats(const gs2_batch *b, int32_t *instantiations, int32_t *updates) {
+    if (!b) return GS2_ERR_ARG;
+    if (instantiations) *instantiations = b->graph_instantiations;
+    if (updates) *updates = b->graph_updates;
+    return GS2_OK;
+}
+
+// fork, every scene's sweep on its stream, join
+static gs2_status batch_enqueue(gs2_batch *b, gs2_scene *scenes, const gs2_camera *const *cams,
+                                const int32_t *ncam, const float *const *const *targets,
+                                const int32_t *const *knn, const int32_t *t, double *losses, int32_t *n_failed,
+                                cudaStream_t st) {
+    const int ns = (int)b->ctx.size();
+    RETB(b, cudaEventRecord(b->fork, st));
+    for (int i = 0; i < ns; ++i) {
+        RETB(b, cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        const gs2_status rc = sweep_run(b->ctx[i], &scenes[i], cams[i], ncam[i], targets[i], knn[i], t[i], nullptr,
+                                        losses ? losses + 10 * (size_t)i : nullptr, n_failed ? n_failed + i : nullptr,
+                                        b->streams[i]);
+        if (rc != GS2_OK) {
+            b->err = "scene " + std::to_string(i) + ": " + b->ctx[i]->err;
+            return rc;
+        }
+        RETB(b, cudaEventRecord(b->join[i], b->streams[i]));
+        RETB(b, cudaStreamWaitEvent(st, b->join[i], 0));
+    }
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_batch_sweep(gs2_batch *b, gs2_scene *scenes, const gs2_camera *const *cams,
+                                      const int32_t *ncam, const float *const *const *targets,
+                                      const int32_t *const *knn, const int32_t *t, double *losses_out,
+                                      int32_t *n_failed, int32_t use_graph, gs2_stream stream) {
+    if (!b || !scenes || !cams || !ncam || !targets || !knn || !t) return GS2_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_graph) return batch_enqueue(b, scenes, cams, ncam, targets, knn, t, losses_out, n_failed, st);
+    // capture on the batch's own stream; the graph is launched on the caller's
+    RETB(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    const gs2_status rc = batch_enqueue(b, scenes, cams, ncam, targets, knn, t, losses_out, n_failed, b->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);   // always ends the capture
+    if (rc != GS2_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc;
+    }
+    if (ec != cudaSuccess || !g) {
+        b->err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec);
+        return GS2_ERR_CUDA;
+    }
+    bool ready = false;
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b->exec, g, &info) == cudaSuccess) {
+            ready = true;
+            ++b->graph_updates;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (!ready) {
+        const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(g);
+            b->exec = nullptr;
+            b->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+            return GS2_ERR_CUDA;
+        }
+        ++b->graph_instantiations;
+    }
+    cudaGraphDestroy(g);
+    RETB(b, cudaGraphLaunch(b->exec, st));
+    return GS2_OK;
+}

@@ -12,6 +12,7 @@
 #include "../../include/gs2.h"
 
 #define GS2_TILE 16                  // screen tile edge in pixels
+#define GS2_SORT_BLOCKS_MAX 1024     // the per-digit scan runs one 1024-thread CTA per digit
 #define GS2_TILE_PIX (GS2_TILE * GS2_TILE)
 #define GS2_ZPOS 41                  // image-space payload of the position group
 #define GS2_MAX_SH 16
@@ -125,7 +126,8 @@ struct gs2_ctx {
     int64_t max_n;
     int max_w, max_h, max_sh;
     int64_t max_pairs;
-    int nb_sort;                 // blocks of the radix sort grid
+    int nb_sort;                 // blocks of the radix sort grid (tuning, <= GS2_SORT_BLOCKS_MAX)
+    int sort_rows;               // keys per thread per scatter round (tuning: 2, 4, 8)
     // sorting
     uint32_t *keys[2];           // pair keys: tile id
     uint32_t *vals[2];           // pair values: Gaussian id
@@ -185,6 +187,11 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
 cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);
+cudaError_t prepare_loss_kernels();
+// one sweep on ctx (gs2_sweep / gs2_sweep_logged; records may be NULL)
+gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                     const float *const *targets, const int32_t *knn, int32_t t, float *records, double *losses_out,
+                     int32_t *n_failed, cudaStream_t stream);
 cudaError_t launch_step_records(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
                                 const float *gp, const gs2_config &cfg, float *rec, cudaStream_t st);
 cudaError_t launch_step_labels(int group, const void *blocks_after, int n_views, const DevScene &sc,

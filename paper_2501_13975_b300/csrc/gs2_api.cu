@@ -125,6 +125,11 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         delete c;
         return GS2_ERR_ARG;
     }
+    if (prepare_loss_kernels() != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return GS2_ERR_CUDA;
+    }
     if (max_pairs <= 0) max_pairs = 16 * max_n;
     if (max_pairs > (int64_t)0xF0000000ll) max_pairs = (int64_t)0xF0000000ll;
     c->max_n = max_n;
@@ -133,6 +138,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     c->max_sh = max_sh;
     c->max_pairs = max_pairs;
     c->nb_sort = SORT_BLOCKS;
+    c->sort_rows = 4;
     const size_t P = (size_t)max_w * max_h;
     const int tiles = ((max_w + GS2_TILE - 1) / GS2_TILE) * ((max_h + GS2_TILE - 1) / GS2_TILE);
     const int K = c->cfg.knn_k, f = c->cfg.downsample;
@@ -149,7 +155,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         A((void **)&c->keys[i], sizeof(uint32_t) * (size_t)max_pairs);
         A((void **)&c->vals[i], sizeof(uint32_t) * (size_t)max_pairs);
     }
-    A((void **)&c->ghist, sizeof(uint32_t) * (256 * (size_t)SORT_BLOCKS + 256));  // + digit totals
+    A((void **)&c->ghist, sizeof(uint32_t) * (256 * (size_t)GS2_SORT_BLOCKS_MAX + 256));  // + digit totals
     A((void **)&c->bsum, sizeof(unsigned long long) * 1024);
     A((void **)&c->d_count, sizeof(uint32_t) * 4);
     A((void **)&c->ranges, sizeof(uint2) * (size_t)tiles);
@@ -457,7 +463,7 @@ extern "C" gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const f
 
 // one sweep; with records != NULL the plain method's records of every group
 // are logged (the step model is then not applied)
-static gs2_status sweep_impl(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                              const float *const *targets, const int32_t *knn, int32_t t, float *records,
                              double *losses_out, int32_t *n_failed, cudaStream_t stream) {
     TRY(check_scene(ctx, scene));
@@ -547,7 +553,7 @@ extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera
                                 const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
                                 int32_t *n_failed, gs2_stream stream) {
     if (!ctx) return GS2_ERR_ARG;
-    return sweep_impl(ctx, scene, cams, ncam, targets, knn, t, nullptr, losses_out, n_failed, (cudaStream_t)stream);
+    return sweep_run(ctx, scene, cams, ncam, targets, knn, t, nullptr, losses_out, n_failed, (cudaStream_t)stream);
 }
 
 extern "C" gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
@@ -555,7 +561,7 @@ extern "C" gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2
                                        double *losses_out, int32_t *n_failed, gs2_stream stream) {
     if (!ctx) return GS2_ERR_ARG;
     REQUIRE(ctx, records != nullptr, GS2_ERR_ARG, "records is null");
-    return sweep_impl(ctx, scene, cams, ncam, targets, knn, t, records, losses_out, n_failed, (cudaStream_t)stream);
+    return sweep_run(ctx, scene, cams, ncam, targets, knn, t, records, losses_out, n_failed, (cudaStream_t)stream);
 }
 
 extern "C" uint64_t gs2_launch_count(void) { return g_gs2_launches.load(); }

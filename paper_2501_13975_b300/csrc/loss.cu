@@ -12,6 +12,8 @@
 // inputs with a 10-pixel halo (52x36), horizontal moment sums, the
 // coefficient maps on the 42x26 window-centre region and their horizontal
 // correlations.  HBM traffic per pixel: read c, c^t (24 B), write e, h (24 B).
+#include <mutex>
+
 #include "common.cuh"
 
 #define LT_W 32
@@ -237,6 +239,18 @@ __global__ void __launch_bounds__(256) k_l2(const float *__restrict__ img, const
     if (loss) block_add_double(acc * (double)scale, &loss[0], sred);
 }
 
+// The SSIM kernel's shared-memory opt-in, set once per process (gs2_create
+// calls this, so no first launch happens inside a stream capture).
+cudaError_t prepare_loss_kernels() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(k_ssim, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SSIM_SMEM_FLOATS * (int)sizeof(float));
+    });
+    return err;
+}
+
 cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,
                         float *hh, double *loss_out, cudaStream_t st) {
     const size_t P = (size_t)w * h;
@@ -265,12 +279,8 @@ cudaError_t launch_loss(const float *image, const float *target, int w, int h, c
     K.lam = cfg.lambda_ssim;
     K.scale = scale;
     const int smem = SSIM_SMEM_FLOATS * (int)sizeof(float);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e0 = cudaFuncSetAttribute(k_ssim, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e0 != cudaSuccess) return e0;
-        attr_set = true;
-    }
+    const cudaError_t e0 = prepare_loss_kernels();
+    if (e0 != cudaSuccess) return e0;
     dim3 grid((w + LT_W - 1) / LT_W, (h + LT_H - 1) / LT_H);
     k_ssim<<<grid, 256, smem, st>>>(image, target, w, h, K, e, hh, loss_out);
     GS2_COUNT_LAUNCH(1);

@@ -86,6 +86,7 @@ extern "C" gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene 
     v.cfg = c;
     v.max_pairs = GS2_NOALLOC_MAX_PAIRS;
     v.nb_sort = NA_SORT_BLOCKS;
+    v.sort_rows = 4;
     v.keys[0] = (uint32_t *)(base + NA_OFF_KEYS0);
     v.keys[1] = (uint32_t *)(base + NA_OFF_KEYS1);
     v.vals[0] = (uint32_t *)(base + NA_OFF_VALS0);

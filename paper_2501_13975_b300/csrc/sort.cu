@@ -19,8 +19,6 @@
 
 #define SCAN_BLOCKS 1024
 #define SORT_THREADS 256
-#define SORT_ROWS 4
-#define SORT_TILE (SORT_THREADS * SORT_ROWS)
 
 // ---------------------------------------------------------------- scan
 __global__ void k_scan_reduce(const uint32_t *__restrict__ x, int n, unsigned long long *bsum) {
@@ -205,6 +203,8 @@ __global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *ghist, int nb, ui
     if (t == 0) dtot[d] = tot;
 }
 
+// ROWS keys per thread per 256-thread round (a tuning parameter: 2, 4 or 8)
+template <int ROWS>
 __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
                                                           uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -222,14 +222,15 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         s_off[t] = base + ghist[t * nb + blockIdx.x];
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
+    constexpr int SORT_TILE = SORT_THREADS * ROWS;
     for (uint32_t base = beg; base < end; base += SORT_TILE) {
 #pragma unroll
         for (int i = 0; i < SORT_THREADS / 32; ++i) s_wc[i][t] = 0u;
         __syncthreads();
-        uint32_t key[SORT_ROWS], val[SORT_ROWS], dig[SORT_ROWS], pos[SORT_ROWS];
+        uint32_t key[ROWS], val[ROWS], dig[ROWS], pos[ROWS];
 #pragma unroll
-        for (int r = 0; r < SORT_ROWS; ++r) {
-            const uint32_t idx = base + (uint32_t)(w * (32 * SORT_ROWS) + r * 32 + lane);
+        for (int r = 0; r < ROWS; ++r) {
+            const uint32_t idx = base + (uint32_t)(w * (32 * ROWS) + r * 32 + lane);
             const bool valid = idx < end;
             key[r] = valid ? kin[idx] : 0u;
             val[r] = valid ? vin[idx] : 0u;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < SORT_ROWS; ++r) {
+        for (int r = 0; r < ROWS; ++r) {
             if (dig[r] < 256u) {
                 const uint32_t dst = s_off[dig[r]] + s_wc[w][dig[r]] + pos[r];
                 kout[dst] = key[r];
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
 // `bits` significant key bits, ping-pong between (k[0], v[0]) and (k[1], v[1]);
 // returns the index of the buffer holding the result
 static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int bits, uint32_t *ghist, int nb,
-                      cudaStream_t st, int *launches) {
+                      int rows, cudaStream_t st, int *launches) {
     uint32_t *dtot = ghist + 256 * nb;
     int cur = 0;
     const int passes = (bits + 7) / 8;
@@ -277,8 +278,15 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
         const int shift = 8 * p;
         k_hist<<<nb, SORT_THREADS, 0, st>>>(k[cur], count, shift, ghist, nb);
         k_digit_scan<<<256, 1024, 0, st>>>(ghist, nb, dtot);
-        k_scatter<<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist, nb,
-                                               dtot);
+        if (rows == 2)
+            k_scatter<2><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist,
+                                                      nb, dtot);
+        else if (rows == 8)
+            k_scatter<8><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist,
+                                                      nb, dtot);
+        else
+            k_scatter<4><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist,
+                                                      nb, dtot);
         cur ^= 1;
     }
     *launches += 3 * passes;
@@ -313,7 +321,7 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     }
     // 1. depth order of the Gaussians
     k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(pv, n, ctx->d_count + 2);
-    const int dcur = radix_sort(pv.dk, pv.dv, ctx->d_count + 2, 32, ctx->ghist, nb, st, &launches);
+    const int dcur = radix_sort(pv.dk, pv.dv, ctx->d_count + 2, 32, ctx->ghist, nb, ctx->sort_rows, st, &launches);
     const uint32_t *order = pv.dv[dcur];
     // 2. tiles-touched in rank order, exclusive scan -> pair offsets and the pair count
     k_gather_touched<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n);
@@ -326,7 +334,8 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     // 4. stable sort by tile id
     int tile_bits = 1;
     while ((1 << tile_bits) < ntiles) ++tile_bits;
-    ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, tile_bits, ctx->ghist, nb, st, &launches);
+    ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, tile_bits, ctx->ghist, nb, ctx->sort_rows, st,
+                             &launches);
     // 5. tile ranges
     k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, stats);
     GS2_COUNT_LAUNCH(launches + 8);

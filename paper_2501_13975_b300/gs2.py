@@ -52,6 +52,15 @@ class Config_(C.Structure):
                 ("precision", C.c_int32)]
 
 
+class Tuning_(C.Structure):
+    _fields_ = [("sort_blocks", C.c_int32), ("sort_rows", C.c_int32)]
+
+
+class BatchScene_(C.Structure):
+    _fields_ = [("max_gaussians", C.c_int64), ("max_width", C.c_int32), ("max_height", C.c_int32),
+                ("max_sh_degree", C.c_int32), ("max_pairs", C.c_int64)]
+
+
 _sigs = {
     "gs2_config_default": (None, [C.POINTER(Config_)]),
     "gs2_create": (C.c_int, [C.POINTER(_vp), C.POINTER(Config_), C.c_int64, C.c_int32, C.c_int32, C.c_int32,
@@ -87,6 +96,18 @@ _sigs = {
     "gs2_mlp_grad": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, _vp]),
     "gs2_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.c_float, C.c_float,
                                C.c_float, _vp]),
+    "gs2_get_tuning": (C.c_int, [_vp, C.POINTER(Tuning_)]),
+    "gs2_set_tuning": (C.c_int, [_vp, C.POINTER(Tuning_)]),
+    "gs2_autotune": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
+                               C.c_int32, C.c_int32, C.POINTER(Tuning_), C.POINTER(C.c_float), _vp]),
+    "gs2_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(Config_), C.c_int32, C.POINTER(BatchScene_)]),
+    "gs2_batch_destroy": (C.c_int, [_vp]),
+    "gs2_batch_ctx": (_vp, [_vp, C.c_int32]),
+    "gs2_batch_last_error": (C.c_char_p, [_vp]),
+    "gs2_batch_stats": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "gs2_batch_sweep": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(C.POINTER(Camera_)), C.POINTER(C.c_int32),
+                                  C.POINTER(C.POINTER(_vp)), C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int32),
+                                  _vp, _vp, C.c_int32, _vp]),
     "gs2_launch_count": (C.c_uint64, []),
     "gs2_profile": (C.c_int, [_vp, C.c_int32]),
     "gs2_profile_read": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -367,6 +388,27 @@ class Context:
                                       _ptr(records), _stream(stream)), "gs2_step_labels")
         return records
 
+    def tuning(self) -> dict:
+        t = Tuning_()
+        self._ok(_lib.gs2_get_tuning(self.h, C.byref(t)), "gs2_get_tuning")
+        return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows)
+
+    def set_tuning(self, sort_blocks: int, sort_rows: int):
+        t = Tuning_(int(sort_blocks), int(sort_rows))
+        self._ok(_lib.gs2_set_tuning(self.h, C.byref(t)), "gs2_set_tuning")
+
+    def autotune(self, scene: DeviceScene, cams, targets, knn, t, reps=2, stream=None):
+        """Times candidate tunings on a copy of the scene; keeps and returns the fastest."""
+        arr = (Camera_ * len(cams))(*[camera_struct(c) for c in cams])
+        tp = (_vp * len(targets))(*[_ptr(x) for x in targets])
+        kt = np.ascontiguousarray(knn, np.int32)
+        s = scene.struct()
+        best = Tuning_()
+        ms = C.c_float(0.0)
+        self._ok(_lib.gs2_autotune(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
+                                   int(reps), C.byref(best), C.byref(ms), _stream(stream)), "gs2_autotune")
+        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, ms=float(ms.value))
+
     def profile(self, enable: bool):
         self._ok(_lib.gs2_profile(self.h, 1 if enable else 0), "gs2_profile")
 
@@ -407,6 +449,94 @@ def render_noalloc(scene: DeviceScene, cam, proj, image, raster_state, status=No
                                  _ptr(raster_state), _ptr(status), _stream(stream))
     if st != 0:
         raise GS2Error(f"gs2_render_noalloc: {STATUS.get(st, st)}")
+
+
+class Batch:
+    """Many independent scenes swept together (include/gs2.h gs2_batch_*).
+
+    sizes: list of dicts with max_gaussians, max_width, max_height,
+    max_sh_degree, max_pairs (0 = default) per scene."""
+
+    def __init__(self, sizes, config: dict | None = None):
+        self.config = default_config(**(config or {}))
+        cfg = _config_struct(self.config)
+        desc = (BatchScene_ * len(sizes))(*[BatchScene_(int(d["max_gaussians"]), int(d["max_width"]),
+                                                        int(d["max_height"]), int(d.get("max_sh_degree", 3)),
+                                                        int(d.get("max_pairs", 0))) for d in sizes])
+        h = _vp()
+        st = _lib.gs2_batch_create(C.byref(h), C.byref(cfg), len(sizes), desc)
+        if st != 0:
+            raise GS2Error(f"gs2_batch_create: {STATUS.get(st, st)}")
+        self.h = h
+        self.n = len(sizes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.gs2_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ctx_handle(self, i: int):
+        return _lib.gs2_batch_ctx(self.h, int(i))
+
+    def stats(self):
+        a, b = C.c_int32(0), C.c_int32(0)
+        _lib.gs2_batch_stats(self.h, C.byref(a), C.byref(b))
+        return dict(instantiations=a.value, updates=b.value)
+
+    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int):
+        t = Tuning_(int(sort_blocks), int(sort_rows))
+        st = _lib.gs2_set_tuning(self.ctx_handle(i), C.byref(t))
+        if st != 0:
+            raise GS2Error(f"gs2_set_tuning: {STATUS.get(st, st)}")
+
+    def autotune(self, i: int, scene: DeviceScene, cams, targets, knn, t, reps=2, stream=None):
+        """gs2_autotune on scene i's context (a scratch copy of the scene is timed)."""
+        arr = (Camera_ * len(cams))(*[camera_struct(c) for c in cams])
+        tp = (_vp * len(targets))(*[_ptr(x) for x in targets])
+        kt = np.ascontiguousarray(knn, np.int32)
+        s = scene.struct()
+        best = Tuning_()
+        ms = C.c_float(0.0)
+        st = _lib.gs2_autotune(self.ctx_handle(i), C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
+                               int(reps), C.byref(best), C.byref(ms), _stream(stream))
+        if st != 0:
+            raise GS2Error(f"gs2_autotune: {STATUS.get(st, st)}")
+        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, ms=float(ms.value))
+
+    def prepare(self, scenes, cams, targets, knn):
+        """Marshals the per-scene host arrays once (cameras, target pointers,
+        KNN tables); the returned object is passed to sweep()."""
+        cam_arrs = [(Camera_ * len(c))(*[camera_struct(x) for x in c]) for c in cams]
+        tgt_arrs = [(_vp * len(tg))(*[_ptr(x) for x in tg]) for tg in targets]
+        knn_arrs = [np.ascontiguousarray(k, np.int32) for k in knn]
+        prep = dict(
+            scenes=(Scene_ * self.n)(*[s.struct() for s in scenes]),
+            cams=(C.POINTER(Camera_) * self.n)(*[C.cast(a, C.POINTER(Camera_)) for a in cam_arrs]),
+            ncam=(C.c_int32 * self.n)(*[len(c) for c in cams]),
+            tgts=(C.POINTER(_vp) * self.n)(*[C.cast(a, C.POINTER(_vp)) for a in tgt_arrs]),
+            knn=(C.POINTER(C.c_int32) * self.n)(*[k.ctypes.data_as(C.POINTER(C.c_int32)) for k in knn_arrs]),
+            keep=(cam_arrs, tgt_arrs, knn_arrs, scenes, targets))
+        return prep
+
+    def sweep(self, prep, t, losses=None, n_failed=None, use_graph=False, stream=None):
+        tt = (C.c_int32 * self.n)(*[int(x) for x in t])
+        st = _lib.gs2_batch_sweep(self.h, prep["scenes"], prep["cams"], prep["ncam"], prep["tgts"], prep["knn"], tt,
+                                  _ptr(losses), _ptr(n_failed), 1 if use_graph else 0, _stream(stream))
+        if st != 0:
+            raise GS2Error(f"gs2_batch_sweep: {STATUS.get(st, st)}: {_lib.gs2_batch_last_error(self.h).decode()}")
+
+    def check(self, stream=None):
+        torch.cuda.synchronize()
+        for i in range(self.n):
+            st = _lib.gs2_check(self.ctx_handle(i), _stream(stream))
+            if st != 0:
+                raise GS2Error(f"scene {i}: {STATUS.get(st, st)}")
 
 
 def _mlp_call(st, what):

@@ -171,7 +171,10 @@ def object_scene(seed: int = 3, n: int = 100_000, sh_degree: int = 3) -> Scene:
     return Scene(mean, quat, scale, opacity, sh, sh_degree)
 
 
-def hemisphere_cameras(count: int = 100, size: int = 800, radius: float = 4.0, fov: float = 60.0):
+def hemisphere_cameras(count: int = 100, size: int = 800, radius: float = 4.0, fov: float = 60.0,
+                       height: int | None = None):
+    """Fibonacci points on the upper hemisphere, looking at the origin; images
+    size x size (size x height when height is given, fov horizontal)."""
     golden = math.pi * (3.0 - math.sqrt(5.0))
     cams = []
     for i in range(count):
@@ -179,7 +182,7 @@ def hemisphere_cameras(count: int = 100, size: int = 800, radius: float = 4.0, f
         rr = math.sqrt(max(0.0, 1.0 - y * y))
         phi = golden * i
         eye = (radius * rr * math.cos(phi), radius * y, radius * rr * math.sin(phi))
-        cams.append(pinhole(size, size, fov, look_at(eye, (0.0, 0.0, 0.0))))
+        cams.append(pinhole(size, height or size, fov, look_at(eye, (0.0, 0.0, 0.0))))
     return cams
 
 
@@ -218,6 +221,38 @@ def trajectory_cameras(count: int = 200, width: int = 1600, height: int = 1040, 
         t = i / count
         cams.append(pinhole(width, height, fov, look_at(centre(t), 0.3 * centre(t + 0.05))))
     return cams
+
+
+BATCH_RESOLUTIONS = ((512, 512), (640, 480), (800, 600), (1024, 768))
+
+
+def batched_workload(seed: int = 8, count: int = 16, n_min: int = 20_000, n_max: int = 500_000,
+                     views_min: int = 16, views_max: int = 128):
+    """Independent scenes for the batched form: Gaussian counts log-uniform in
+    [n_min, n_max], view counts uniform in [views_min, views_max], resolution
+    uniform from BATCH_RESOLUTIONS, SH degree 3; even entries are shells
+    (object_scene, hemisphere cameras), odd ones spread scenes
+    (spread_scene, trajectory cameras).  Returns a list of dicts with the
+    ground-truth scene, the training start (means + N(0, 0.02^2)) and the
+    cameras."""
+    rng = _rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        views = int(rng.integers(views_min, views_max + 1))
+        w, h = BATCH_RESOLUTIONS[int(rng.integers(len(BATCH_RESOLUTIONS)))]
+        s = int(rng.integers(1 << 30))
+        if i % 2 == 0:
+            gt = object_scene(seed=s, n=n)
+            cams = hemisphere_cameras(views, w, height=h)
+            kind = "shell"
+        else:
+            gt = spread_scene(seed=s, n=n)
+            cams = trajectory_cameras(views, w, h, seed=s + 1)
+            kind = "spread"
+        out.append(dict(kind=kind, n=n, views=views, width=w, height=h, gt=gt,
+                        train=perturbed(gt, seed=s + 2, sd=0.02), cams=cams))
+    return out
 
 
 def procedural_targets(count: int, width: int, height: int, seed: int = 11) -> np.ndarray:
