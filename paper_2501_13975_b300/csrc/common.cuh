@@ -153,6 +153,7 @@ struct gs2_ctx {
     const void *mlp_w;           // installed step-scale network (BF16, caller-owned) or NULL
     float *g_prim;               // [3][max_n] gradient rows right after the view-slot-0 accumulation
     float *lg_phi;               // [max_n] phi1 accumulator of the logged sweep
+    uint32_t *order_cache;       // [1 + knn_k][max_n] depth orders of a sweep's views (reused while means are fixed)
     // opt-in profile of the accumulation kernel: CUDA events around every launch
     // and per-group pair / visible-Gaussian totals counted on the device
     int prof_on;
@@ -173,8 +174,11 @@ extern std::atomic<unsigned long long> g_gs2_launches;
 // launchers implemented in the .cu files (return a CUDA error code)
 cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
                            int tiles_y, cudaStream_t st);
+// order_in: a depth order of the same means and camera to reuse (skips the
+// depth sort); order_out: where to keep the computed one (both may be NULL)
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
-                            unsigned long long *stats);
+                            unsigned long long *stats, const uint32_t *order_in = nullptr,
+                            uint32_t *order_out = nullptr);
 cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
                           RasterView rv, cudaStream_t st);
 cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,

@@ -102,7 +102,8 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
-                    c->sw_step, c->d_status, c->d_stats, c->flags, c->g_prim, c->lg_phi};
+                    c->sw_step, c->d_status, c->d_stats, c->flags, c->g_prim, c->lg_phi,
+                    c->order_cache};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
@@ -177,6 +178,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A((void **)&c->flags, (size_t)max_n);
     A((void **)&c->g_prim, sizeof(float) * 3 * (size_t)max_n);
     A((void **)&c->lg_phi, sizeof(float) * (size_t)max_n);
+    A((void **)&c->order_cache, sizeof(uint32_t) * (size_t)(1 + K) * max_n);
     if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(double) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
@@ -273,12 +275,13 @@ extern "C" gs2_status gs2_project(gs2_ctx *ctx, const gs2_scene *scene, const gs
 }
 
 static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const void *proj, float *image,
-                            void *rstate, cudaStream_t st) {
+                            void *rstate, cudaStream_t st, const uint32_t *order_in = nullptr,
+                            uint32_t *order_out = nullptr) {
     ctx->tiles_x = (cam->width + GS2_TILE - 1) / GS2_TILE;
     ctx->tiles_y = (cam->height + GS2_TILE - 1) / GS2_TILE;
     ProjView pv = proj_view(const_cast<void *>(proj), n);
     RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st,
-                                  ctx->prof_on ? ctx->d_stats + 4 * ctx->stat_slot : nullptr));
+                                  ctx->prof_on ? ctx->d_stats + 4 * ctx->stat_slot : nullptr, order_in, order_out));
     if (ctx->prof_on) ctx->h_pixels[ctx->stat_slot] += (unsigned long long)cam->width * cam->height;
     RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image,
                                 raster_view(rstate, cam->width, cam->height), st));
@@ -509,8 +512,13 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, blocks_bytes_impl(group, scene->n, scene->sh_degree, nv), st));
         for (int i = 0; i < nv; ++i) {
             if (vid[i] < 0) continue;
+            // only the position group moves the means: the rotation pass sorts each
+            // view by depth and keeps the order, the scaling, opacity and colour
+            // passes reuse it (the same means and camera give the same order)
+            uint32_t *cache = ctx->order_cache + (size_t)i * ctx->max_n;
             TRY(do_project(ctx, scene, &vcam[i], ctx->sw_proj, st));
-            TRY(do_raster(ctx, scene->n, &vcam[i], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st));
+            TRY(do_raster(ctx, scene->n, &vcam[i], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st,
+                          group >= GS2_SCALE ? cache : nullptr, group == GS2_ROT ? cache : nullptr));
             TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image, vtgt[i],
                          i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, st));
         }

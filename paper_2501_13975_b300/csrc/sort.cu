@@ -81,14 +81,17 @@ __global__ void k_scan_down(const uint32_t *__restrict__ x, int n, const unsigne
 }
 
 // ---------------------------------------------------------------- depth keys
-// key = FP32 depth bits for a Gaussian that touches a tile, all ones otherwise
-// (positive FP32 bit patterns order like the values); value = index.  Thread 0
-// also publishes the element count n for the radix passes.
+// key = FP32 depth bits of every Gaussian (positive FP32 bit patterns order
+// like the values; depths behind the near plane sort after them and touch no
+// tile), value = index.  Sorting all Gaussians, not only those on screen,
+// makes the order depend on the means and the camera alone, so a sweep can
+// reuse it for every group that does not move the means.  Thread 0 also
+// publishes the element count n for the radix passes.
 __global__ void k_depth_keys(ProjView pv, int n, uint32_t *count_slot) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) *count_slot = (uint32_t)n;
     if (k >= n) return;
-    pv.dk[0][k] = pv.touched[k] ? pv.key[k] : 0xFFFFFFFFu;
+    pv.dk[0][k] = pv.key[k];
     pv.dv[0][k] = (uint32_t)k;
 }
 
@@ -308,7 +311,7 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *coun
 }
 
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
-                            unsigned long long *stats) {
+                            unsigned long long *stats, const uint32_t *order_in, uint32_t *order_out) {
     const uint32_t cap = (uint32_t)ctx->max_pairs;
     const int nb = ctx->nb_sort;
     int launches = 0;
@@ -319,10 +322,20 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
         ctx->sorted = 0;
         return cudaMemsetAsync(ctx->d_count, 0, sizeof(uint32_t) * 2, st);
     }
-    // 1. depth order of the Gaussians
-    k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(pv, n, ctx->d_count + 2);
-    const int dcur = radix_sort(pv.dk, pv.dv, ctx->d_count + 2, 32, ctx->ghist, nb, ctx->sort_rows, st, &launches);
-    const uint32_t *order = pv.dv[dcur];
+    // 1. depth order of the Gaussians (or the caller's copy of it for the same
+    //    means and camera)
+    const uint32_t *order = order_in;
+    if (!order) {
+        k_depth_keys<<<(n + 255) / 256, 256, 0, st>>>(pv, n, ctx->d_count + 2);
+        ++launches;
+        const int dcur =
+            radix_sort(pv.dk, pv.dv, ctx->d_count + 2, 32, ctx->ghist, nb, ctx->sort_rows, st, &launches);
+        order = pv.dv[dcur];
+        if (order_out) {
+            e = cudaMemcpyAsync(order_out, order, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
     // 2. tiles-touched in rank order, exclusive scan -> pair offsets and the pair count
     k_gather_touched<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n);
     unsigned long long *bsum = (unsigned long long *)ctx->bsum;
@@ -338,6 +351,6 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
                              &launches);
     // 5. tile ranges
     k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, stats);
-    GS2_COUNT_LAUNCH(launches + 8);
+    GS2_COUNT_LAUNCH(launches + 7);
     return cudaGetLastError();
 }
