@@ -39,6 +39,13 @@ if ROOT not in sys.path:
 from paper_2501_13975_b300 import synth  # noqa: E402
 
 GROUP_NAMES = ("position", "rotation", "scaling", "opacity", "colour")
+# FP32 operations of the accumulation per evaluated (pixel, Gaussian) pair:
+# 46 common (falloff and alpha 14, T_k 2, weight 1, colour-behind terms 6,
+# e.a 5, h.a^2 8, C_back update 10) + the group's payload + its P warp-sum adds:
+# position 232 + 41, rotation / scaling 124 + 9, opacity 3 + 2, colour 9 + 6
+EVAL_FLOPS = (319, 179, 179, 51, 61)
+# FP32 peak: 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 PAYLOAD_FLOATS = (41, 9, 9, 2, 6)       # image-space accumulator floats per Gaussian and view
 RECORD_BYTES = 40                        # per (tile, Gaussian) pair: id (4) + pi, conic, sigma, c~ (36)
 PIXEL_BYTES = 32                         # per pixel: e, h (24) + T_final, last (8)
@@ -240,7 +247,8 @@ def run_gpu(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms, ms_e2e = float(t[0]), float(t[1])
 
-    # ---------------- roofline of the accumulation kernel (algorithmic bytes)
+    # ---------------- roofline of the accumulation kernel: bound by its per-pair
+    # arithmetic (ALU), not HBM; the HBM figure with algorithmic bytes beside it
     peak, peak_kind = load_peaks()
     accum_ms = float(prof["accum_ms"].sum())
     n_acc = int(prof["accum_launches"].sum())
@@ -248,8 +256,9 @@ def run_gpu(args, rank, world, local_rank):
     for g in range(5):
         alg_bytes += (PIXEL_BYTES * float(prof["pixels"][g]) + RECORD_BYTES * float(prof["pairs"][g])
                       + 8.0 * PAYLOAD_FLOATS[g] * float(prof["visible"][g]))
-    achieved = alg_bytes / (accum_ms * 1e-3) / 1e9 if accum_ms > 0 else 0.0
-    per_launch_bytes = alg_bytes / max(n_acc, 1)
+    flops = sum(EVAL_FLOPS[g] * float(prof["evaluations"][g]) for g in range(5))
+    hbm_gbs = alg_bytes / (accum_ms * 1e-3) / 1e9 if accum_ms > 0 else 0.0
+    tflops = flops / (accum_ms * 1e-3) / 1e12 if accum_ms > 0 else 0.0
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "accum_traffic.json")
     if os.path.exists(tpath):
@@ -257,10 +266,16 @@ def run_gpu(args, rank, world, local_rank):
             td = json.load(f)
         if td.get("workload") == args.workload and td.get("kernel_rev") == KERNEL_REV:
             traffic = td.get("bytes_per_launch")
-    roofline = {"kernel": "k_accum (all groups)", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": round(per_launch_bytes), "launches": n_acc,
+    roofline = {"kernel": "k_accum (all groups)", "bound": "alu", "achieved": round(tflops, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4),
+                "traffic": traffic,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                "flops_per_launch": round(flops / max(n_acc, 1)),
+                "evaluations_per_sweep": int(prof["evaluations"].sum()) // max(args.steps, 1),
+                "hbm": {"achieved": round(hbm_gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(hbm_gbs / peak, 4), "peak_source": peak_kind,
+                        "algorithmic_bytes_per_launch": round(alg_bytes / max(n_acc, 1))},
+                "launches": n_acc,
                 "avg_launch_ms": round(accum_ms / max(n_acc, 1), 4),
                 "share_of_step": round(accum_ms / ms, 4) if ms > 0 else None,
                 "pairs_per_sweep": int(prof["pairs"].sum()) // max(args.steps, 1),
@@ -630,7 +645,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v1"
+KERNEL_REV = "accum-v2"
 
 
 def main():

@@ -361,8 +361,10 @@ gs2_status gs2_batch_sweep(gs2_batch *batch, gs2_scene *scenes, const gs2_camera
  *   of gs2_sweep, the (tile, Gaussian) pairs, visible Gaussians, binnings and
  *   pixels (device-side counters, no host synchronisation); resets totals.
  *   gs2_profile(ctx, 0) stops.  Synchronises the device.
- * gs2_profile_read: per group (host arrays [5], stats [5][4]: pairs, visible
- *   Gaussians, binnings, pixels) after synchronising the device. */
+ * gs2_profile_read: per group (host arrays [5], stats [5][5]: pairs, visible
+ *   Gaussians, binnings, pixels, accumulation evaluations = (pixel, Gaussian)
+ *   pairs with alpha >= alpha_min that the accumulation processed) after
+ *   synchronising the device. */
 uint64_t gs2_launch_count(void);
 gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable);
 gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launches, uint64_t *stats);

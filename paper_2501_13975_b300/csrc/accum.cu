@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
                                                         const uint32_t *__restrict__ ids, ProjView pv, RasterView rv,
                                                         const float *__restrict__ E, const float *__restrict__ Hh,
                                                         int W, int H, int tiles_x, float amin, float amax,
-                                                        ACC *__restrict__ zbuf, int n) {
+                                                        ACC *__restrict__ zbuf, int n,
+                                                        unsigned long long *__restrict__ active_stat) {
     constexpr int P = Payload<GROUP>::P;
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][GS2_TILE_PIX];
@@ -163,9 +164,12 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
     atomicMax(&sMax, last);
     __syncthreads();
     const int maxlast = (int)sMax;
+    // this warp's own end of list: its lanes have nothing to do beyond it
+    const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last);
     const uint2 r = ranges[tile];
     const float fx = (float)px, fy = (float)py;
     float cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+    uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
     // batches back to front: batch b covers [max(0, maxlast - 256 (b + 1)), maxlast - 256 b)
     const int nbat = (maxlast + GS2_TILE_PIX - 1) / GS2_TILE_PIX;
     auto list_index = [&](int b) { return maxlast - GS2_TILE_PIX * (b + 1) + t; };   // this thread's entry
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
         const int buf = b & 1;
         const int bend = maxlast - GS2_TILE_PIX * b, bbeg = max(0, bend - GS2_TILE_PIX);
         const int base = bend - GS2_TILE_PIX;   // list index of slot 0 of this batch (may be negative)
-        for (int jj = bend - 1; jj >= bbeg; --jj) {
+        for (int jj = min(bend, wlast) - 1; jj >= bbeg; --jj) {
             const int s = jj - base;
             const float4 A = sA[buf][s], B = sB[buf][s];
             bool act = inside && (uint32_t)jj < last;
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
                 if (alpha < amin) act = false;
             }
             if (!__any_sync(0xFFFFFFFFu, act)) continue;
+            nact += act ? 1u : 0u;
             float pl[P];
 #pragma unroll
             for (int i = 0; i < P; ++i) pl[i] = 0.f;
@@ -284,6 +289,12 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
             }
             warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
         }
+    }
+    if (active_stat) {
+        unsigned long long c = nact;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0 && c) atomicAdd(active_stat, c);
     }
 }
 
@@ -701,9 +712,10 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
                            const uint32_t *ids, bool prof, cudaStream_t st) {
     const int n = sc.n;
     ACC *zb = (ACC *)ctx->zbuf;
+    unsigned long long *act = ctx->prof_on ? ctx->d_stats + 4 * group + 3 : nullptr;
 #define ACC_LAUNCH(G)                                                                                             \
     k_accum<G, ACC><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
-                                                   view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n)
+                                                   view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n, act)
     switch (group) {
     case GS2_POS: ACC_LAUNCH(GS2_POS); break;
     case GS2_ROT: ACC_LAUNCH(GS2_ROT); break;

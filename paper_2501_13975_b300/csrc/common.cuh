@@ -160,7 +160,7 @@ struct gs2_ctx {
     int prof_n;                  // events used in the pool
     cudaEvent_t prof_ev[2 * 512];
     int prof_group[512];
-    unsigned long long *d_stats; // [5][4]: pairs, visible Gaussians, binnings, (unused)
+    unsigned long long *d_stats; // [5][4]: pairs, visible Gaussians, binnings, accumulation evaluations
     int stat_slot;               // group slot the binning statistics go to
     unsigned long long h_pixels[5];
     std::string err;

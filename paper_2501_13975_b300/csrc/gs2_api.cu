@@ -603,10 +603,11 @@ extern "C" gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *
     unsigned long long h[20];
     RET_CUDA(ctx, cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
     for (int g = 0; g < 5; ++g) {
-        stats[4 * g + 0] = h[4 * g + 0];
-        stats[4 * g + 1] = h[4 * g + 1];
-        stats[4 * g + 2] = h[4 * g + 2];
-        stats[4 * g + 3] = ctx->h_pixels[g];
+        stats[5 * g + 0] = h[4 * g + 0];
+        stats[5 * g + 1] = h[4 * g + 1];
+        stats[5 * g + 2] = h[4 * g + 2];
+        stats[5 * g + 3] = ctx->h_pixels[g];
+        stats[5 * g + 4] = h[4 * g + 3];
     }
     return GS2_OK;
 }

@@ -415,11 +415,11 @@ class Context:
     def profile_read(self):
         ms = np.zeros(5, np.float64)
         cnt = np.zeros(5, np.int64)
-        stats = np.zeros((5, 4), np.uint64)
+        stats = np.zeros((5, 5), np.uint64)
         self._ok(_lib.gs2_profile_read(self.h, ms.ctypes.data_as(_vp), cnt.ctypes.data_as(_vp),
                                        stats.ctypes.data_as(_vp)), "gs2_profile_read")
         return dict(accum_ms=ms, accum_launches=cnt, pairs=stats[:, 0], visible=stats[:, 1],
-                    binnings=stats[:, 2], pixels=stats[:, 3])
+                    binnings=stats[:, 2], pixels=stats[:, 3], evaluations=stats[:, 4])
 
     def debug_tiles(self, w, h, capacity, stream=None):
         tx, ty = (w + 15) // 16, (h + 15) // 16
