@@ -442,14 +442,17 @@ def time_to_psnr(args):
     held = [p[1] for p in parts]
     model = learned.StepModel(seed=20)
     t0 = time.perf_counter()
-    model.fit(train_sets, epochs=args.ttp_epochs, batch=16384)
+    model.fit(train_sets, epochs=args.ttp_epochs, batch=16384, objective=args.ttp_objective)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     held_stats = {}
     for name, hs in zip(("tiny", "shell"), held):
         pl, cnt = learned.plain_loss(hs)
         nl, _ = model.loss(hs)
-        held_stats[name] = {"records": cnt, "loss_plain": round(pl, 5), "loss_network": round(nl, 5)}
+        pll, _ = learned.plain_loss(hs, objective="line")
+        nll, _ = model.loss(hs, objective="line")
+        held_stats[name] = {"records": cnt, "label_loss_plain": round(pl, 5), "label_loss_network": round(nl, 5),
+                            "line_loss_plain": float(f"{pll:.5g}"), "line_loss_network": float(f"{nll:.5g}")}
 
     def run(start_host, precision, use_model, max_sweeps, target_psnr=None):
         ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision))
@@ -530,7 +533,8 @@ def time_to_psnr(args):
         "metric": "time to PSNR vs plain FP32 path (object workload)",
         "value": head["learned_mixed_seconds"], "unit": "s", "higher_is_better": False,
         "starts": starts,
-        "network": {"tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell, "records": tiny.n + shell.n,
+        "network": {"objective": args.ttp_objective, "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell,
+                    "records": tiny.n + shell.n,
                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
                     "heldout": held_stats},
         "config": {"workload": "object: " + w["desc"], "primaries": "seeded permutation (seed 5)",
@@ -667,6 +671,8 @@ def main():
     ap.add_argument("--ttp-shell", type=int, default=24, help="shell-scene record runs (4 sweeps each)")
     ap.add_argument("--ttp-epochs", type=int, default=3)
     ap.add_argument("--ttp-max", type=int, default=60)
+    ap.add_argument("--ttp-objective", default="line", choices=["line", "labels"],
+                    help="training loss of the step-scale network")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gs2" else args.warmup
 

@@ -237,7 +237,7 @@ gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
  *
  * Records: float [GS2_REC_ROWS][n] per group and sweep: rows 0-7 the
  * features, row 8 phi0, row 9 the label alpha* in [0, 2] or -1 for an
- * unusable record.  The label looks along d at a loss L_lab: phi0 = grad
+ * unusable record, row 10 phi1.  The label looks along d at a loss L_lab: phi0 = grad
  * L_lab . d before the step, phi1 = grad L_lab . d after all Gaussians of the
  * group stepped; alpha* = 0 if phi0 >= 0 (d does not descend L_lab: a
  * rejected step), else the minimum of the quadratic line model
@@ -260,7 +260,7 @@ gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
 #define GS2_MLP_HIDDEN 64
 #define GS2_MLP_NPARAM 4801
 #define GS2_MLP_GRID 148
-#define GS2_REC_ROWS 10
+#define GS2_REC_ROWS 11
 
 /* Install (device, GS2_MLP_NPARAM BF16 words, read at every solve; the caller
  * keeps it alive) or remove (NULL) the step-scale network: gs2_solve_step and
@@ -290,8 +290,11 @@ gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *ca
  * records[(i / chunk_n) GS2_REC_ROWS chunk_n + j chunk_n + i % chunk_n]);
  * record r of a batch is idx[r] (device int64, NULL: r).
  * gs2_mlp_forward: out[r] = alpha(features of record r), device float [nrec].
- * gs2_mlp_grad: loss 1/2 sum (alpha - alpha*)^2 over the usable records
- *   (label >= 0); partial: device float [GS2_MLP_GRID][GS2_MLP_NPARAM] out,
+ * gs2_mlp_grad: over the usable records (label >= 0) the loss
+ *   1/2 sum (alpha - alpha*)^2 (chunk_scale NULL), or, with chunk_scale
+ *   (device float, one per chunk), the line model's predicted change of the
+ *   label loss sum s_c (phi0 alpha + 1/2 (phi1 - phi0) alpha^2);
+ *   partial: device float [GS2_MLP_GRID][GS2_MLP_NPARAM] out,
  *   per-CTA gradient sums w.r.t. the BF16 weights' values; stats: device
  *   double [GS2_MLP_GRID][2] out, per-CTA (loss, usable count).
  * gs2_mlp_adam: one Adam step of the FP32 master weights with the mean
@@ -301,7 +304,11 @@ gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *ca
 gs2_status gs2_mlp_forward(const uint16_t *w_bf16, const float *records, int64_t chunk_n, const int64_t *idx,
                            int64_t nrec, float *out, gs2_stream stream);
 gs2_status gs2_mlp_grad(const uint16_t *w_bf16, const float *records, int64_t chunk_n, const int64_t *idx,
-                        int64_t nrec, float *partial, double *stats, gs2_stream stream);
+                        int64_t nrec, const float *chunk_scale, float *partial, double *stats, gs2_stream stream);
+/* Per-chunk scale of the line-model loss: out[c] = 1 / sum over the usable
+ * records of chunk c of |phi0| (0 if none); out: device float [n_chunks]. */
+gs2_status gs2_records_chunk_scale(const float *records, int64_t chunk_n, int64_t n_chunks, float *out,
+                                   gs2_stream stream);
 gs2_status gs2_mlp_adam(float *master, uint16_t *w_bf16, const float *partial, const double *stats, float *m,
                         float *v, int32_t step, float lr, float beta1, float beta2, float eps, gs2_stream stream);
 

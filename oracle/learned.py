@@ -27,8 +27,12 @@ Definitions (g, H: a Gaussian's group block; d: its plain damped step):
           logged sweep takes L_lab = the loss summed over every training view
           at full resolution, whose increase is what the paper calls
           overshoot (Sec. overshoot).
+  rows    0-7 features, 8 phi0, 9 label (-1 unusable, 0 pending), 10 phi1
   network y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, alpha = 2 sigmoid(y)
-  loss    1/2 sum over usable records (alpha - alpha*)^2
+  loss    over usable records: 1/2 sum (alpha - alpha*)^2 (labels), or the
+          line model's predicted change of the label loss,
+          sum s_c (phi0 alpha + 1/2 (phi1 - phi0) alpha^2) (line), with
+          s_c = 1 / sum |phi0| over the usable records of the record's chunk
   Adam    m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
           p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
 """
@@ -46,7 +50,7 @@ OFF_B2 = OFF_W2 + NH * NH
 OFF_W3 = OFF_B2 + NH
 OFF_B3 = OFF_W3 + NH
 NPARAM = OFF_B3 + 1
-REC_ROWS = NF + 2
+REC_ROWS = NF + 3
 
 
 # ---------------------------------------------------------------- parameters
@@ -87,22 +91,50 @@ def usable(X, Y):
     return (Y >= 0) & np.all(np.isfinite(X), axis=1)
 
 
-def mlp_loss(p, X, Y):
+def _per_record_loss(a, Y, m, line):
+    """Loss and dL/d alpha per record (zero where unusable)."""
+    if line is None:
+        e = (a - np.where(m, Y, 0.0)) * m
+        return 0.5 * e * e, e
+    p0, cv = line            # s phi0, s (phi1 - phi0)
+    p0 = np.where(m, p0, 0.0)
+    cv = np.where(m, cv, 0.0)
+    return (p0 * a + 0.5 * cv * a * a) * m, (p0 + cv * a) * m
+
+
+def line_terms(phi0, phi1, scale):
+    """(s phi0, s (phi1 - phi0)) per record for the line-model loss."""
+    phi0 = np.asarray(phi0, np.float64)
+    return scale * phi0, scale * (np.asarray(phi1, np.float64) - phi0)
+
+
+def chunk_scale(rec_chunks):
+    """s_c = 1 / sum |phi0| over the usable records of each chunk [..., REC_ROWS, n]."""
+    r = np.asarray(rec_chunks, np.float64).reshape(-1, REC_ROWS, np.asarray(rec_chunks).shape[-1])
+    ok = (r[:, NF + 1] >= 0) & np.isfinite(r[:, NF])
+    tot = np.sum(np.where(ok, np.abs(r[:, NF]), 0.0), axis=1)
+    return np.where(tot > 0, 1.0 / np.where(tot > 0, tot, 1.0), 0.0)
+
+
+def mlp_loss(p, X, Y, line=None):
     m = usable(X, Y)
+    if line is not None:
+        m = m & np.isfinite(line[0]) & np.isfinite(line[1])
     a, _ = mlp_forward(p, np.where(m[:, None], X, 0.0))
-    e = (a - np.where(m, Y, 0.0)) * m
-    return 0.5 * float(np.sum(e * e)), int(m.sum())
+    lr, _ = _per_record_loss(a, Y, m, line)
+    return float(np.sum(lr)), int(m.sum())
 
 
-def mlp_loss_grad(p, X, Y):
+def mlp_loss_grad(p, X, Y, line=None):
     """(loss sum, usable count, gradient of the loss sum w.r.t. p) by reverse-mode chain rule."""
     m = usable(X, Y)
+    if line is not None:
+        m = m & np.isfinite(line[0]) & np.isfinite(line[1])
     X = np.where(m[:, None], np.asarray(X, np.float64), 0.0)
-    Yu = np.where(m, np.asarray(Y, np.float64), 0.0)
     w = unpack(p)
     a, act = mlp_forward(p, X)
-    e = (a - Yu) * m
-    loss = 0.5 * float(np.sum(e * e))
+    lr, e = _per_record_loss(a, np.asarray(Y, np.float64), m, line)
+    loss = float(np.sum(lr))
     dy = e * a * (1.0 - 0.5 * a)                       # dL/dy; d alpha/dy = alpha (1 - alpha/2)
     gW3 = act["h2"].T @ dy
     gb3 = dy.sum()
@@ -244,6 +276,7 @@ def step_labels(group, g_after, d, rec, S=1, phi0=None):
     a = np.where(phi0 >= 0, 0.0, a)
     pend = rec[NF + 1] >= 0
     out[NF + 1] = np.where(pend, np.where(np.isfinite(a), np.clip(a, 0.0, 2.0), -1.0), rec[NF + 1])
+    out[NF + 2] = np.where(pend, phi1, 0.0)
     return out
 
 

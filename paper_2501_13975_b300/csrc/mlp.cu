@@ -7,7 +7,8 @@
 // Records logged from the plain method (one per Gaussian and group), float
 // [GS2_REC_ROWS][n]:
 //   rows 0-7  features (below), row 8 phi0,
-//   row 9     label alpha* in [0, 2], or -1 where the record is unusable.
+//   row 9     label alpha* in [0, 2], or -1 where the record is unusable,
+//   row 10    phi1.
 // The label looks at a loss L_lab along d: phi0 = grad L_lab . d before the
 // step, phi1 = grad L_lab . d after every Gaussian of the group took its step
 // (so the coupling of the simultaneous updates is included).  alpha* = 0 when
@@ -50,7 +51,7 @@
 #define RROWS GS2_REC_ROWS
 
 static_assert(NPARAM == GS2_MLP_NPARAM, "parameter count in gs2.h must match the layout");
-static_assert(RROWS == NF + 2, "record rows: features, phi0, label");
+static_assert(RROWS == NF + 3, "record rows: features, phi0, label, phi1");
 
 // ---------------------------------------------------------------- features
 struct StepStats {
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(128) k_step_records(int group, const float *__
     for (int i = 0; i < NF; ++i) rec[(size_t)i * n + k] = f[i];
     rec[(size_t)NF * n + k] = st.gd;
     rec[(size_t)(NF + 1) * n + k] = ok ? 0.f : -1.f;   // label pending (0) or unusable (-1)
+    rec[(size_t)(NF + 2) * n + k] = 0.f;
 }
 
 // g . d from a block (the after-step block for the labels)
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(128) k_step_labels(int group, const float *__r
     if (*lab < 0.f) return;
     const float phi0 = rec[(size_t)NF * n + k];
     const float phi1 = phi1v ? phi1v[k] : block_dot_step(group, Bafter, n_views, n, sc.S, k, step);
+    rec[(size_t)(NF + 2) * n + k] = phi1;
     const float den = phi0 - phi1;
     float a = (den < 0.f) ? phi0 / den : 2.f;
     if (!(phi0 < 0.f)) a = 0.f;                       // not a descent direction of the label loss
@@ -356,7 +359,11 @@ cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, con
 }
 
 // ---------------------------------------------------------------- training
-// Loss of a batch: 1/2 sum over usable records (alpha(x) - alpha*)^2.
+// Loss of a batch, over the usable records (label >= 0):
+//   labels:      1/2 sum (alpha(x) - alpha*)^2
+//   line model:  sum s_c (phi0 alpha + 1/2 (phi1 - phi0) alpha^2), the change of
+//                the label loss that the line model predicts for the step
+//                alpha d, with s_c a per-chunk scale (chunk_scale)
 // Record r of the batch is idx[r] (or r when idx is NULL) of a record buffer
 // made of chunks [RROWS][chunk_n]: row j of record i at
 // rec[(i / chunk_n) RROWS chunk_n + j chunk_n + i % chunk_n].
@@ -370,14 +377,21 @@ cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, con
 struct TileSmem {
     float x[TB][NF];
     float h1[TB][NH + 1], h2[TB][NH + 1], d2[TB][NH + 1], d1[TB][NH + 1];
-    float dy[TB], yl[TB], ml[TB];
+    float dy[TB], yl[TB], ml[TB], p0[TB], cv[TB];   // label, mask, s phi0, s (phi1 - phi0)
     double red[2][TB];
 };
 
+__device__ __forceinline__ const float *record_base(const float *__restrict__ rec, int64_t chunk_n,
+                                                   const int64_t *__restrict__ idx, int64_t r, int64_t *chunk) {
+    const int64_t i = idx ? idx[r] : r;
+    *chunk = i / chunk_n;
+    return rec + (i / chunk_n) * RROWS * chunk_n + (i % chunk_n);
+}
+
 __device__ __forceinline__ void load_record(const float *__restrict__ rec, int64_t chunk_n,
                                             const int64_t *__restrict__ idx, int64_t r, float x[NF], float *y) {
-    const int64_t i = idx ? idx[r] : r;
-    const float *base = rec + (i / chunk_n) * RROWS * chunk_n + (i % chunk_n);
+    int64_t c;
+    const float *base = record_base(rec, chunk_n, idx, r, &c);
 #pragma unroll
     for (int j = 0; j < NF; ++j) x[j] = base[j * chunk_n];
     *y = base[(NF + 1) * chunk_n];
@@ -385,7 +399,8 @@ __device__ __forceinline__ void load_record(const float *__restrict__ rec, int64
 
 __global__ void __launch_bounds__(GT) k_mlp_grad(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ rec,
                                                  int64_t chunk_n, const int64_t *__restrict__ idx, int64_t nrec,
-                                                 float *__restrict__ partial, double *__restrict__ stats) {
+                                                 const float *__restrict__ chunk_scale, float *__restrict__ partial,
+                                                 double *__restrict__ stats) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *sw = reinterpret_cast<float *>(smem_raw);
     TileSmem &sm = *reinterpret_cast<TileSmem *>(smem_raw + sizeof(float) * ((NPARAM + 3) & ~3));
@@ -400,18 +415,30 @@ __global__ void __launch_bounds__(GT) k_mlp_grad(const __nv_bfloat16 *__restrict
         __syncthreads();
         const int64_t r0 = tile * TB;
         if (t < TB) {
-            float x[NF], y = -1.f;
+            float x[NF], y = -1.f, p0 = 0.f, cv = 0.f;
             bool use = false;
             if (r0 + t < nrec) {
-                load_record(rec, chunk_n, idx, r0 + t, x, &y);
+                int64_t c;
+                const float *base = record_base(rec, chunk_n, idx, r0 + t, &c);
+#pragma unroll
+                for (int j = 0; j < NF; ++j) x[j] = base[j * chunk_n];
+                y = base[(NF + 1) * chunk_n];
                 use = y >= 0.f;
 #pragma unroll
                 for (int j = 0; j < NF; ++j) use = use && isfinite(x[j]);
+                if (chunk_scale) {
+                    const float sc = chunk_scale[c], f0 = base[NF * chunk_n], f1 = base[(NF + 2) * chunk_n];
+                    p0 = sc * f0;
+                    cv = sc * (f1 - f0);
+                    use = use && isfinite(p0) && isfinite(cv);
+                }
             }
 #pragma unroll
             for (int j = 0; j < NF; ++j) sm.x[t][j] = use ? x[j] : 0.f;
             sm.yl[t] = use ? y : 0.f;
             sm.ml[t] = use ? 1.f : 0.f;
+            sm.p0[t] = use ? p0 : 0.f;
+            sm.cv[t] = use ? cv : 0.f;
         }
         __syncthreads();
         for (int i = t; i < TB * NH; i += GT) {      // layer 1
@@ -434,10 +461,17 @@ __global__ void __launch_bounds__(GT) k_mlp_grad(const __nv_bfloat16 *__restrict
             float y = sw[OFF_B3];
             for (int c = 0; c < NH; ++c) y = fmaf(sw[OFF_W3 + c], sm.h2[t][c], y);
             const float a = scale_of(y);
-            const float e = (a - sm.yl[t]) * sm.ml[t];
-            lsum += 0.5 * (double)e * (double)e;
+            float dlda;                              // dL/d alpha
+            if (chunk_scale) {
+                lsum += (double)sm.ml[t] * ((double)sm.p0[t] * a + 0.5 * (double)sm.cv[t] * a * a);
+                dlda = (sm.p0[t] + sm.cv[t] * a) * sm.ml[t];
+            } else {
+                const float e = (a - sm.yl[t]) * sm.ml[t];
+                lsum += 0.5 * (double)e * (double)e;
+                dlda = e;
+            }
             cnt += (double)sm.ml[t];
-            sm.dy[t] = e * a * (1.f - 0.5f * a);     // d alpha / dy = alpha (1 - alpha / 2)
+            sm.dy[t] = dlda * a * (1.f - 0.5f * a);  // d alpha / dy = alpha (1 - alpha / 2)
         }
         __syncthreads();
         for (int i = t; i < TB * NH; i += GT) {      // through layer 3 and the second ReLU
@@ -554,8 +588,35 @@ extern "C" gs2_status gs2_mlp_forward(const uint16_t *w_bf16, const float *recor
     return cudaGetLastError() == cudaSuccess ? GS2_OK : GS2_ERR_CUDA;
 }
 
+// s_c = 1 / sum over the chunk's usable records of |phi0| (0 for none)
+__global__ void k_chunk_scale(const float *__restrict__ rec, int64_t chunk_n, float *__restrict__ out) {
+    __shared__ double red[256];
+    const float *base = rec + (int64_t)blockIdx.x * RROWS * chunk_n;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < chunk_n; i += blockDim.x) {
+        const float lab = base[(NF + 1) * chunk_n + i], p0 = base[NF * chunk_n + i];
+        if (lab >= 0.f && isfinite(p0)) acc += fabs((double)p0);
+    }
+    red[threadIdx.x] = acc;
+    for (int o = 128; o > 0; o >>= 1) {
+        __syncthreads();
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0] > 0.0 ? (float)(1.0 / red[0]) : 0.f;
+}
+
+extern "C" gs2_status gs2_records_chunk_scale(const float *records, int64_t chunk_n, int64_t n_chunks, float *out,
+                                              gs2_stream stream) {
+    if (!records || !out || chunk_n < 1 || n_chunks < 0) return GS2_ERR_ARG;
+    if (n_chunks == 0) return GS2_OK;
+    k_chunk_scale<<<(unsigned)n_chunks, 256, 0, (cudaStream_t)stream>>>(records, chunk_n, out);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError() == cudaSuccess ? GS2_OK : GS2_ERR_CUDA;
+}
+
 extern "C" gs2_status gs2_mlp_grad(const uint16_t *w_bf16, const float *records, int64_t chunk_n, const int64_t *idx,
-                                   int64_t nrec, float *partial, double *stats, gs2_stream stream) {
+                                   int64_t nrec, const float *chunk_scale, float *partial, double *stats,
+                                   gs2_stream stream) {
     if (!w_bf16 || !records || !partial || !stats || nrec < 0 || chunk_n < 1) return GS2_ERR_ARG;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -565,7 +626,7 @@ extern "C" gs2_status gs2_mlp_grad(const uint16_t *w_bf16, const float *records,
     });
     if (attr_err != cudaSuccess) return GS2_ERR_CUDA;
     k_mlp_grad<<<GS2_MLP_GRID, GT, smem, (cudaStream_t)stream>>>((const __nv_bfloat16 *)w_bf16, records, chunk_n,
-                                                                 idx, nrec, partial, stats);
+                                                                 idx, nrec, chunk_scale, partial, stats);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError() == cudaSuccess ? GS2_OK : GS2_ERR_CUDA;
 }

@@ -93,7 +93,8 @@ _sigs = {
     "gs2_step_records": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), _vp, _vp, _vp]),
     "gs2_step_labels": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), _vp, _vp, _vp]),
     "gs2_mlp_forward": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp]),
-    "gs2_mlp_grad": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, _vp]),
+    "gs2_mlp_grad": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
+    "gs2_records_chunk_scale": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, _vp]),
     "gs2_mlp_adam": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.c_float, C.c_float,
                                C.c_float, _vp]),
     "gs2_get_tuning": (C.c_int, [_vp, C.POINTER(Tuning_)]),
@@ -125,7 +126,7 @@ for _name, (_res, _args) in _sigs.items():
 EXPORTED = tuple(_sigs)
 
 # learned step scale (include/gs2.h)
-MLP_NFEAT, MLP_HIDDEN, MLP_NPARAM, MLP_GRID, REC_ROWS = 8, 64, 4801, 148, 10
+MLP_NFEAT, MLP_HIDDEN, MLP_NPARAM, MLP_GRID, REC_ROWS = 8, 64, 4801, 148, 11
 
 
 class GS2Error(RuntimeError):
@@ -553,10 +554,19 @@ def mlp_forward(w_bf16, records, chunk_n, nrec, idx=None, out=None, stream=None)
     return out[: int(nrec)]
 
 
-def mlp_grad(w_bf16, records, chunk_n, nrec, partial, stats, idx=None, stream=None):
-    """Per-CTA gradient sums [MLP_GRID][MLP_NPARAM] and (loss, count) [MLP_GRID][2]."""
-    _mlp_call(_lib.gs2_mlp_grad(_ptr(w_bf16), _ptr(records), int(chunk_n), _ptr(idx), int(nrec), _ptr(partial),
-                                _ptr(stats), _stream(stream)), "gs2_mlp_grad")
+def mlp_grad(w_bf16, records, chunk_n, nrec, partial, stats, idx=None, chunk_scale=None, stream=None):
+    """Per-CTA gradient sums [MLP_GRID][MLP_NPARAM] and (loss, count) [MLP_GRID][2];
+    with chunk_scale the line-model loss, else the label loss."""
+    _mlp_call(_lib.gs2_mlp_grad(_ptr(w_bf16), _ptr(records), int(chunk_n), _ptr(idx), int(nrec), _ptr(chunk_scale),
+                                _ptr(partial), _ptr(stats), _stream(stream)), "gs2_mlp_grad")
+
+
+def records_chunk_scale(records, chunk_n, n_chunks, out=None, stream=None):
+    if out is None:
+        out = torch.empty(max(int(n_chunks), 1), dtype=torch.float32, device="cuda")
+    _mlp_call(_lib.gs2_records_chunk_scale(_ptr(records), int(chunk_n), int(n_chunks), _ptr(out), _stream(stream)),
+              "gs2_records_chunk_scale")
+    return out[: int(n_chunks)]
 
 
 def mlp_adam(master, w_bf16, partial, stats, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

@@ -28,6 +28,13 @@ class RecordSet:
         self.data = data.contiguous()
         self.chunk_n = int(chunk_n)
         self.n = self.data.numel() // gs2.REC_ROWS
+        self._scale = None
+
+    def chunk_scale(self) -> torch.Tensor:
+        """Per-chunk scale of the line-model loss (computed once, on the device)."""
+        if self._scale is None:
+            self._scale = gs2.records_chunk_scale(self.data, self.chunk_n, self.n // self.chunk_n)
+        return self._scale
 
     def labels(self) -> torch.Tensor:
         return self.data.view(-1, gs2.REC_ROWS, self.chunk_n)[:, gs2.MLP_NFEAT + 1, :].reshape(-1)
@@ -109,24 +116,28 @@ class StepModel:
         self.partial = torch.empty((gs2.MLP_GRID, gs2.MLP_NPARAM), dtype=torch.float32, device="cuda")
         self.stats = torch.empty((gs2.MLP_GRID, 2), dtype=torch.float64, device="cuda")
 
-    def loss(self, recs, idx: torch.Tensor | None = None, nrec: int | None = None):
-        """Mean of 1/2 (alpha - alpha*)^2 over the usable records (of one
-        RecordSet or a list of them), and their count."""
+    def loss(self, recs, idx: torch.Tensor | None = None, nrec: int | None = None, objective: str = "labels"):
+        """Mean loss over the usable records (of one RecordSet or a list of
+        them), and their count.  objective "labels": 1/2 (alpha - alpha*)^2;
+        "line": the line model's predicted change of the label loss, scaled
+        per chunk (a descent of the plain step scores about -1 per chunk)."""
         sets = [recs] if isinstance(recs, RecordSet) else list(recs)
         tot = np.zeros(2)
         for r in sets:
             m = r.n if nrec is None else nrec
-            gs2.mlp_grad(self.w, r.data, r.chunk_n, m, self.partial, self.stats, idx=idx)
+            sc = r.chunk_scale() if objective == "line" else None
+            gs2.mlp_grad(self.w, r.data, r.chunk_n, m, self.partial, self.stats, idx=idx, chunk_scale=sc)
             tot += self.stats.sum(0).cpu().numpy()
         return float(tot[0] / max(tot[1], 1.0)), int(tot[1])
 
-    def step(self, recs: RecordSet, idx: torch.Tensor, nrec: int, lr: float):
-        gs2.mlp_grad(self.w, recs.data, recs.chunk_n, nrec, self.partial, self.stats, idx=idx)
+    def step(self, recs: RecordSet, idx: torch.Tensor, nrec: int, lr: float, objective: str = "labels"):
+        sc = recs.chunk_scale() if objective == "line" else None
+        gs2.mlp_grad(self.w, recs.data, recs.chunk_n, nrec, self.partial, self.stats, idx=idx, chunk_scale=sc)
         self.t += 1
         gs2.mlp_adam(self.master, self.w, self.partial, self.stats, self.m, self.v, self.t, lr)
 
     def fit(self, recs, epochs: int = 3, batch: int = 16384, lr: float = 2e-3, seed: int = 21,
-            lr_final: float = 2e-4):
+            lr_final: float = 2e-4, objective: str = "labels"):
         """Adam over shuffled mini-batches of one RecordSet or a list of them
         (each batch from one set; per epoch a seeded permutation of every
         set's records and a seeded order of all batches), learning rate
@@ -143,7 +154,7 @@ class StepModel:
                 r = sets[i]
                 b0 = int(b) * batch
                 m = min(batch, r.n - b0)
-                self.step(r, perms[i][b0:b0 + m], m, lr * (lr_final / lr) ** (k / max(steps - 1, 1)))
+                self.step(r, perms[i][b0:b0 + m], m, lr * (lr_final / lr) ** (k / max(steps - 1, 1)), objective)
                 k += 1
         return self
 
@@ -151,9 +162,9 @@ class StepModel:
         return gs2.mlp_forward(self.w, recs.data, recs.chunk_n, recs.n)
 
 
-def plain_loss(recs: RecordSet):
-    """Mean 1/2 (1 - alpha*)^2 over the usable records: the plain step's error
-    against the labels (the reference a trained network must beat), computed
-    by the same loss kernel with the all-zero network (y = 0, alpha = 1)."""
+def plain_loss(recs, objective: str = "labels"):
+    """The plain step's (alpha = 1) loss against the records: the reference a
+    trained network must beat; computed by the same loss kernel with the
+    all-zero network (y = 0, alpha = 1)."""
     zero = np.zeros(gs2.MLP_NPARAM, np.float32)
-    return StepModel(master=zero, bits=np.zeros(gs2.MLP_NPARAM, np.uint16)).loss(recs)
+    return StepModel(master=zero, bits=np.zeros(gs2.MLP_NPARAM, np.uint16)).loss(recs, objective=objective)

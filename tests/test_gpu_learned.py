@@ -19,7 +19,9 @@ def _random_records(seed, chunks=3, chunk_n=1000):
     rng = np.random.default_rng(seed)
     rec = np.zeros((chunks, Lr.REC_ROWS, chunk_n), np.float32)
     rec[:, :Lr.NF] = rng.normal(0.0, 1.0, (chunks, Lr.NF, chunk_n))
-    rec[:, Lr.NF] = -1.0
+    rec[:, Lr.NF] = -np.abs(rng.normal(1.0, 0.5, (chunks, chunk_n)))
+    rec[:, Lr.NF, ::23] *= -0.3                      # some rejected steps (phi0 > 0)
+    rec[:, Lr.NF + 2] = rec[:, Lr.NF] + rng.uniform(-0.5, 2.0, (chunks, chunk_n))
     rec[:, Lr.NF + 1] = rng.uniform(0.0, 2.0, (chunks, chunk_n))
     rec[:, Lr.NF + 1, ::17] = -1.0          # unusable labels
     rec[0, 3, 5::29] = np.nan               # unusable features
@@ -56,6 +58,37 @@ def test_mlp_forward_and_gradient_match_oracle():
     assert st[0] == pytest.approx(loss, rel=1e-5)
     err = np.abs(g - g_ref).max() / np.abs(g_ref).max()
     assert err <= 1e-4, err
+
+
+def test_line_objective_and_chunk_scale_match_oracle():
+    """The line-model loss (per-chunk scales from the device kernel) and its
+    gradient equal the oracle's."""
+    from paper_2501_13975_b300 import gs2
+    _, bits = synth.mlp_init(35, out_scale=1.0)
+    p = Lr.bf16_to_f64(bits)
+    rec = _random_records(36)
+    chunk_n = rec.shape[2]
+    recd = torch.tensor(rec, device="cuda").reshape(-1)
+    sc = gs2.records_chunk_scale(recd, chunk_n, rec.shape[0]).cpu().numpy()
+    sc_ref = Lr.chunk_scale(rec)
+    assert np.allclose(sc, sc_ref, rtol=1e-6)
+    perm = np.random.default_rng(37).permutation(rec.shape[0] * chunk_n)[:2000]
+    w = torch.tensor(bits.astype(np.int16), device="cuda")
+    idx = torch.tensor(perm, dtype=torch.int64, device="cuda")
+    partial = torch.empty((gs2.MLP_GRID, gs2.MLP_NPARAM), dtype=torch.float32, device="cuda")
+    stats = torch.empty((gs2.MLP_GRID, 2), dtype=torch.float64, device="cuda")
+    gs2.mlp_grad(w, recd, chunk_n, len(perm), partial, stats, idx=idx,
+                 chunk_scale=torch.tensor(sc, device="cuda"))
+    g = partial.double().sum(0).cpu().numpy()
+    st = stats.sum(0).cpu().numpy()
+    X, Y = _oracle_xy(rec, perm)
+    flat = np.moveaxis(rec.astype(np.float64), 1, 2).reshape(-1, Lr.REC_ROWS)[perm]
+    chunk = perm // chunk_n
+    line = Lr.line_terms(flat[:, Lr.NF], flat[:, Lr.NF + 2], sc_ref[chunk])
+    loss, cnt, g_ref = Lr.mlp_loss_grad(p, X, Y, line)
+    assert int(st[1]) == cnt
+    assert st[0] == pytest.approx(loss, rel=1e-4, abs=1e-9)
+    assert np.abs(g - g_ref).max() / np.abs(g_ref).max() <= 1e-4
 
 
 def test_adam_step_matches_oracle():
@@ -249,3 +282,10 @@ def test_trained_network_gains_over_plain_step():
     print(f"\nheld-out records {cnt}: plain {base:.4g}, initial {l0:.4g}, trained {l1:.4g}")
     assert cnt1 == cnt and cnt > 100_000
     assert l1 < 0.8 * base
+    # line-model objective: the predicted change of the loss over all views
+    # (about -1 per chunk for the plain step) falls further with the network
+    lbase, _ = learned.plain_loss(held, objective="line")
+    line_model = learned.StepModel(seed=20).fit(train, epochs=4, batch=8192, objective="line")
+    l2, _ = line_model.loss(held, objective="line")
+    print(f"line objective: plain {lbase:.4g}, trained {l2:.4g}")
+    assert l2 < lbase

@@ -351,3 +351,59 @@ def test_logged_sweep_equals_oracle_sweep():
     lab = rec[:, Lr.NF + 1]
     assert np.all((lab == -1.0) | ((lab >= 0.0) & (lab <= 2.0)))
     assert (lab >= 0).sum() >= 100
+
+
+def _line_batch(seed=20, m=24):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0.0, 1.0, (m, Lr.NF))
+    Y = rng.uniform(0.0, 2.0, m)
+    Y[2] = -1.0
+    phi0 = -np.abs(rng.normal(1.0, 0.5, m))
+    phi0[4] = 0.3                      # a rejected step (ascent of the label loss)
+    phi1 = phi0 + rng.uniform(-0.5, 2.0, m)
+    return X, Y, Lr.line_terms(phi0, phi1, 0.7)
+
+
+def test_line_objective_gradient_central_differences():
+    p = _params(seed=21)
+    X, Y, line = _line_batch()
+    loss, cnt, g = Lr.mlp_loss_grad(p, X, Y, line)
+    assert cnt == 23
+    assert loss == pytest.approx(Lr.mlp_loss(p, X, Y, line)[0], rel=1e-13)
+    h = 1e-6
+    idx = np.random.default_rng(22).choice(Lr.NPARAM, 400, replace=False)
+    for i in idx:
+        e = np.zeros(Lr.NPARAM)
+        e[i] = h
+        fd = (Lr.mlp_loss(p + e, X, Y, line)[0] - Lr.mlp_loss(p - e, X, Y, line)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i], abs=1e-7 * np.abs(g).max())
+
+
+def test_line_objective_closed_form_and_minimiser():
+    """W3 = 0: every alpha = 2 sigmoid(b3) and dL/db3 = sum (s phi0 + s (phi1 - phi0) alpha)
+    alpha (1 - alpha/2); a single convex descent record's loss is smallest at its label."""
+    p = _params(seed=23)
+    p[Lr.OFF_W3:Lr.OFF_B3] = 0.0
+    p[Lr.OFF_B3] = -0.3
+    X, Y, line = _line_batch(seed=24)
+    a0 = 2.0 / (1.0 + np.exp(0.3))
+    m = Lr.usable(X, Y)
+    _, _, g = Lr.mlp_loss_grad(p, X, Y, line)
+    assert g[Lr.OFF_B3] == pytest.approx(np.sum(((line[0] + line[1] * a0) * a0 * (1 - a0 / 2))[m]), rel=1e-12)
+    # minimiser of s (phi0 a + 1/2 (phi1 - phi0) a^2) = the label of step_labels
+    rec = np.zeros((Lr.REC_ROWS, 1))
+    rec[Lr.NF] = -0.8
+    lab = Lr.step_labels(O.POS, np.array([[0.4]]), np.array([[1.0]]), rec)   # phi1 = 0.4
+    a = np.linspace(0, 2, 200001)
+    q = -0.8 * a + 0.5 * (0.4 + 0.8) * a * a
+    assert lab[Lr.NF + 1, 0] == pytest.approx(a[np.argmin(q)], abs=1e-4)
+    assert lab[Lr.NF + 2, 0] == pytest.approx(0.4)
+
+
+def test_chunk_scale():
+    rec = np.zeros((2, Lr.REC_ROWS, 3))
+    rec[0, Lr.NF] = [-1.0, -3.0, 2.0]
+    rec[0, Lr.NF + 1] = [0.0, 1.0, -1.0]          # the third record is unusable
+    rec[1, Lr.NF + 1] = -1.0                       # no usable record
+    s = Lr.chunk_scale(rec)
+    assert s[0] == pytest.approx(0.25) and s[1] == 0.0
