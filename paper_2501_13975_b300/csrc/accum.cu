@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict_
     __shared__ uint32_t sMax;
     const int t = threadIdx.x, lane = t & 31;
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
-    const int px = blockIdx.x * GS2_TILE + (t % GS2_TILE), py = blockIdx.y * GS2_TILE + (t / GS2_TILE);
+    const int px = blockIdx.x * GS2_TILE + gs2_tile_px(t), py = blockIdx.y * GS2_TILE + gs2_tile_py(t);
     const bool inside = px < W && py < H;
     const size_t PI = (size_t)W * H, pp = (size_t)py * W + px;
     uint32_t last = 0u;

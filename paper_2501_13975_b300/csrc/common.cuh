@@ -219,6 +219,13 @@ __device__ __forceinline__ float gs2_quadform(float ca, float cb, float cc, floa
     return q;
 }
 
+// Pixel of thread t in its 16x16 tile: warp w covers the 8x4 block
+// (w % 2, w / 2) of the tile, lane l its pixel (l % 8, l / 8) -- compact
+// warp blocks keep more of a warp's lanes inside a small Gaussian footprint
+// than 16x2 rows do.
+__device__ __forceinline__ int gs2_tile_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
+__device__ __forceinline__ int gs2_tile_py(int t) { return (t >> 6) * 4 + ((t >> 3) & 3); }
+
 // asynchronous 16-byte global -> shared copies (the batch staging pipeline)
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
     __shared__ float4 sA[2][GS2_TILE_PIX], sB[2][GS2_TILE_PIX], sC[2][GS2_TILE_PIX];
     const int t = threadIdx.x;
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
-    const int px = blockIdx.x * GS2_TILE + (t % GS2_TILE), py = blockIdx.y * GS2_TILE + (t / GS2_TILE);
+    const int px = blockIdx.x * GS2_TILE + gs2_tile_px(t), py = blockIdx.y * GS2_TILE + gs2_tile_py(t);
     const bool inside = px < W && py < H;
     bool done = !inside;
     const uint2 r = ranges[tile];
