@@ -489,7 +489,7 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
 // V the camera-space 3D covariance (J V J^T written out); derivatives by the
 // chain rule through the intermediates (u, tau_x, tau_y).
 template <typename ACC, int S>
-__global__ void __launch_bounds__(128) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf,
+__global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf,
                                                  float *blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;

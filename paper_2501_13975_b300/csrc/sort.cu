@@ -303,6 +303,8 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
     return cur;
 }
 
+// [start, end) of every tile: each thread checks four consecutive sorted keys
+// (one 16-byte load when aligned) against their successors
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *count, uint2 *ranges,
                          unsigned long long *stats) {
     const uint32_t M = count[0];
@@ -310,10 +312,29 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *coun
         stats[0] += M;
         stats[2] += 1ull;
     }
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        const uint32_t tile = keys[j];
-        if (j == 0u || keys[j - 1] != tile) ranges[tile].x = j;
-        if (j == M - 1u || keys[j + 1] != tile) ranges[tile].y = j + 1u;
+    const uint32_t nq = (M + 3u) / 4u;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t j0 = 4u * q;
+        uint32_t k[5];
+        if (j0 + 4u <= M) {
+            const uint4 v = reinterpret_cast<const uint4 *>(keys)[q];
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+            for (int i = 0; i < 4; ++i) k[i] = (j0 + i < M) ? keys[j0 + i] : 0u;
+        }
+        k[4] = (j0 + 4u < M) ? keys[j0 + 4u] : 0u;
+        if (j0 == 0u) ranges[k[0]].x = 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t j = j0 + i;
+            if (j >= M) break;
+            if (j + 1u == M) {
+                ranges[k[i]].y = M;
+            } else if (k[i + 1] != k[i]) {
+                ranges[k[i]].y = j + 1u;
+                ranges[k[i + 1]].x = j + 1u;
+            }
+        }
     }
 }
 
