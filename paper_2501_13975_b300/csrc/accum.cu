@@ -341,12 +341,13 @@ __device__ __forceinline__ void push_cov(const float T[2][3], const float S3[3][
 }
 
 template <typename ACC>
-__global__ void k_epi_opacity(const ProjView pv, ACC *zbuf, int n, float *blocks) {
+__global__ void k_epi_opacity(const ProjView pv, ACC *__restrict__ zbuf, int n, float *__restrict__ blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || pv.touched[k] == 0u) return;
     const float z0 = (float)zbuf[k], z1 = (float)zbuf[n + k];
-    blocks[k] += z0;
-    blocks[n + k] += z1;
+    const float b0 = blocks[k], b1 = blocks[n + k];
+    blocks[k] = b0 + z0;
+    blocks[n + k] = b1 + z1;
     zbuf[k] = 0.f;
     zbuf[n + k] = 0.f;
 }
@@ -373,17 +374,22 @@ __global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, ACC *zbu
 }
 
 template <typename ACC>
-__global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf, float *blocks) {
+__global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__restrict__ zbuf,
+                            float *__restrict__ blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
-    float z[9];
+    // every load first (accumulators, the block entries updated, parameters):
+    // they are then in flight together instead of one memory latency each
+    float z[9], bk[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
+    for (int i = 0; i < 9; ++i) bk[i] = blocks[(size_t)i * n + k];
     GaussGeo g;
     load_geo(sc, k, g);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
     float t[3], T[2][3];
     cam_T(cam, g.p, t, T);
     float dS[3][3], d2S[3][3];  // [param j][(xx,xy,yy)]
@@ -396,34 +402,43 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *zbu
     float Hz[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = a; b < 3; ++b) Hz[a][b] = Hz[b][a] = z[3 + ut3(a, b)];
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
         float gj = 0.f;
+#pragma unroll
         for (int a = 0; a < 3; ++a) gj += z[a] * dS[j][a];
-        blocks[(size_t)j * n + k] += gj;
+        blocks[(size_t)j * n + k] = bk[j] + gj;
     }
+#pragma unroll
     for (int j = 0; j < 3; ++j)
+#pragma unroll
         for (int l = j; l < 3; ++l) {
             float hv = 0.f;
+#pragma unroll
             for (int a = 0; a < 3; ++a)
+#pragma unroll
                 for (int b = 0; b < 3; ++b) hv += dS[j][a] * Hz[a][b] * dS[l][b];
             if (j == l)
+#pragma unroll
                 for (int a = 0; a < 3; ++a) hv += z[a] * d2S[j][a];
-            blocks[(size_t)(3 + ut3(j, l)) * n + k] += hv;
+            blocks[(size_t)(3 + ut3(j, l)) * n + k] = bk[3 + ut3(j, l)] + hv;
         }
 }
 
 template <typename ACC>
-__global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjView pv, ACC *zbuf, float *blocks) {
+__global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjView pv, ACC *__restrict__ zbuf,
+                          float *__restrict__ blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
     float z[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
+    const float b0 = blocks[k], b1 = blocks[n + k];
     GaussGeo g;
     load_geo(sc, k, g);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
     float t[3], T[2][3];
     cam_T(cam, g.p, t, T);
     // Sigma3 = R diag(s^2) R^T; K = [a]x with a the primary view direction
@@ -479,8 +494,8 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
             hth += d1[aa] * hz * d1[b];
         }
     }
-    blocks[k] += gth;
-    blocks[n + k] += hth;
+    blocks[k] = b0 + gth;
+    blocks[n + k] = b1 + hth;
 }
 
 // Position epilogue.  With u = 1/t_z and a, b in {x, y}:
@@ -489,8 +504,8 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
 // V the camera-space 3D covariance (J V J^T written out); derivatives by the
 // chain rule through the intermediates (u, tau_x, tau_y).
 template <typename ACC, int S>
-__global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv, ACC *zbuf,
-                                                 float *blocks) {
+__global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv,
+                                                    ACC *__restrict__ zbuf, float *__restrict__ blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
