@@ -213,8 +213,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
                                                           uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                           const uint32_t *count, int shift,
                                                           const uint32_t *ghist, int nb, const uint32_t *dtot) {
+    constexpr int SORT_TILE = SORT_THREADS * ROWS;
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[SORT_THREADS / 32][256];
+    __shared__ uint32_t s_lb[256];                       // tile-local start of each digit
+    __shared__ uint32_t s_k[SORT_TILE], s_v[SORT_TILE];  // the tile, stably sorted by digit
     __shared__ uint32_t swarp[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t beg, end;
@@ -225,7 +228,6 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         s_off[t] = base + ghist[t * nb + blockIdx.x];
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
-    constexpr int SORT_TILE = SORT_THREADS * ROWS;
     for (uint32_t base = beg; base < end; base += SORT_TILE) {
 #pragma unroll
         for (int i = 0; i < SORT_THREADS / 32; ++i) s_wc[i][t] = 0u;
@@ -262,14 +264,25 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
             s_wc[i][t] = run;
             run += c;
         }
+        uint32_t tile_n;
+        s_lb[t] = block_excl_scan(run, swarp, tile_n);
         __syncthreads();
+        // local stable sort of the tile by digit in shared memory ...
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             if (dig[r] < 256u) {
-                const uint32_t dst = s_off[dig[r]] + s_wc[w][dig[r]] + pos[r];
-                kout[dst] = key[r];
-                vout[dst] = val[r];
+                const uint32_t li = s_lb[dig[r]] + s_wc[w][dig[r]] + pos[r];
+                s_k[li] = key[r];
+                s_v[li] = val[r];
             }
+        }
+        __syncthreads();
+        // ... then consecutive threads write consecutive positions of each digit's run
+        for (uint32_t i = t; i < tile_n; i += SORT_THREADS) {
+            const uint32_t kk = s_k[i], d = (kk >> shift) & 255u;
+            const uint32_t dst = s_off[d] + (i - s_lb[d]);
+            kout[dst] = kk;
+            vout[dst] = s_v[i];
         }
         __syncthreads();
         s_off[t] += run;
