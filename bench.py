@@ -171,6 +171,7 @@ def run_gpu(args, rank, world, local_rank):
     knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
     losses = torch.zeros(10, dtype=torch.float64, device=dev)
     nfail = torch.zeros(1, dtype=torch.int32, device=dev)
+    tuning = ctx.autotune(scene, cams, targets, knn, 0, reps=2) if not args.no_autotune else ctx.tuning()
 
     def sweep(i, tg=targets):
         ctx.sweep(scene, cams, tg, knn, i % ncam, losses, nfail)
@@ -296,6 +297,7 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline,
         "gpu_launches": int(launches),
+        "tuning": tuning,
         "clocks": clk,
         "accumulate_ms_by_group": {GROUP_NAMES[g]: round(float(prof["accum_ms"][g]) / max(args.steps, 1), 3)
                                    for g in range(5)},
@@ -664,7 +666,7 @@ def main():
     ap.add_argument("--ref-crop", type=int, default=8)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (profiling captures)")
-    ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default tuning")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")
