@@ -139,6 +139,18 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over the process group (the
+    slowest replica sets the job's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2501_13975_b300 import gs2
@@ -243,10 +255,7 @@ def run_gpu(args, rank, world, local_rank):
     ctx.check()
 
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+        ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
 
     # ---------------- roofline of the accumulation kernel: bound by its per-pair
     # arithmetic (ALU), not HBM; the HBM figure with algorithmic bytes beside it
@@ -651,7 +660,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v2"
+KERNEL_REV = "accum-v3"
 
 
 def main():

@@ -143,7 +143,9 @@ size_t gs2_step_bytes(gs2_group group, int64_t n, int32_t sh_degree);
  * centre pi, EWA covariance Sigma2D = J Wr R S S^T R^T Wr^T J^T + lowpass I
  * with J the perspective Jacobian, its inverse (conic), view-dependent SH
  * colour c~ (App. A.2), depth key and screen-tile rectangle of the support
- * { sigma G >= alpha_min }.  proj: device, gs2_proj_bytes(n) bytes, opaque. */
+ * { sigma G >= alpha_min }.  proj: device, gs2_proj_bytes(n) bytes, opaque.
+ * A Gaussian with a non-finite parameter is left off screen and the device
+ * status gets GS2_ERR_NONFINITE's bit (read by gs2_check). */
 gs2_status gs2_project(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *cam, void *proj,
                        gs2_stream stream);
 
@@ -162,7 +164,9 @@ gs2_status gs2_raster_fwd(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera
  *   L2 = 1/(3|I|) sum 1/2 (c - c^t)^2, L_S = 1/(3|I|) sum (1 - SSIM), SSIM per
  *   channel with an 11x11 Gaussian window, zero-padded.
  * image, target: device [3][H][W]; e, h: device [3][H][W] out;
- * loss_out: device double[2] (L2, L_S) accumulated (+=), may be NULL. */
+ * loss_out: device double[2] (L2, L_S) accumulated (+=), may be NULL.
+ * A non-finite pixel of image or target counts as 0 and sets the status bit
+ * of GS2_ERR_NONFINITE. */
 gs2_status gs2_loss_derivs(gs2_ctx *ctx, const float *image, const float *target, int32_t width,
                            int32_t height, float *e, float *h, double *loss_out, gs2_stream stream);
 

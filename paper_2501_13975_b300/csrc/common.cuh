@@ -173,7 +173,7 @@ extern std::atomic<unsigned long long> g_gs2_launches;
 // --------------------------------------------------------------------------
 // launchers implemented in the .cu files (return a CUDA error code)
 cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
-                           int tiles_y, cudaStream_t st);
+                           int tiles_y, cudaStream_t st, uint32_t *status);
 // order_in: a depth order of the same means and camera to reuse (skips the
 // depth sort); order_out: where to keep the computed one (both may be NULL)
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
@@ -182,7 +182,7 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
 cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
                           RasterView rv, cudaStream_t st);
 cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,
-                        float *hh, double *loss_out, cudaStream_t st);
+                        float *hh, double *loss_out, cudaStream_t st, uint32_t *status);
 cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st);

@@ -261,7 +261,7 @@ static gs2_status do_project(gs2_ctx *ctx, const gs2_scene *scene, const gs2_cam
     const DevScene sc = make_devscene(scene);
     const DevCam dc = make_devcam(cam);
     const int tx = (cam->width + GS2_TILE - 1) / GS2_TILE, ty = (cam->height + GS2_TILE - 1) / GS2_TILE;
-    RET_CUDA(ctx, launch_project(sc, dc, ctx->cfg, proj_view(proj, scene->n), tx, ty, st));
+    RET_CUDA(ctx, launch_project(sc, dc, ctx->cfg, proj_view(proj, scene->n), tx, ty, st, ctx->d_status));
     return GS2_OK;
 }
 
@@ -302,7 +302,7 @@ extern "C" gs2_status gs2_loss_derivs(gs2_ctx *ctx, const float *image, const fl
     if (!ctx) return GS2_ERR_ARG;
     REQUIRE(ctx, image && target && e && hh, GS2_ERR_ARG, "null buffer");
     REQUIRE(ctx, w >= 1 && h >= 1, GS2_ERR_ARG, "empty image");
-    RET_CUDA(ctx, launch_loss(image, target, w, h, ctx->cfg, e, hh, loss_out, (cudaStream_t)stream));
+    RET_CUDA(ctx, launch_loss(image, target, w, h, ctx->cfg, e, hh, loss_out, (cudaStream_t)stream, ctx->d_status));
     return GS2_OK;
 }
 
@@ -314,7 +314,7 @@ static gs2_status do_accum(gs2_ctx *ctx, int group, const gs2_scene *scene, cons
                            const float *target, int slot, void *blocks, double *loss_out, cudaStream_t st,
                            bool keep_primary = true) {
     RET_CUDA(ctx, launch_loss(image, target, view->width, view->height, ctx->cfg, ctx->pix_e, ctx->pix_h, loss_out,
-                              st));
+                              st, ctx->d_status));
     RET_CUDA(ctx, launch_accum(ctx, group, make_devscene(scene), make_devcam(view), make_devcam(primary),
                                proj_view(const_cast<void *>(proj), scene->n),
                                raster_view(const_cast<void *>(rstate), view->width, view->height), ctx->cfg, slot,

@@ -50,7 +50,7 @@ __device__ __forceinline__ void block_add_double(double v, double *dst, double *
 
 __global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, const float *__restrict__ tgt, int W,
                                               int H, SsimConst K, float *__restrict__ eo, float *__restrict__ ho,
-                                              double *loss) {
+                                              double *loss, uint32_t *__restrict__ status) {
     extern __shared__ float sm[];
     float *sX = sm, *sY = sm + SM_IN, *sH = sm + 2 * SM_IN, *sK = sm + 2 * SM_IN + SM_H1;
     float *sHC = sH;  // reused after the moments are formed
@@ -65,8 +65,15 @@ __global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, con
             const int r = i / IN_W, q = i % IN_W;
             const int gx = x0 - 2 * LRAD + q, gy = y0 - 2 * LRAD + r;
             const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            sX[i] = in ? X[(size_t)gy * W + gx] : 0.f;
-            sY[i] = in ? Y[(size_t)gy * W + gx] : 0.f;
+            float xv = in ? X[(size_t)gy * W + gx] : 0.f, yv = in ? Y[(size_t)gy * W + gx] : 0.f;
+            // a non-finite pixel counts as 0 and raises the status bit
+            if (!(isfinite(xv) && isfinite(yv))) {
+                if (status) atomicOr(status, GS2_ST_NONFINITE);
+                xv = isfinite(xv) ? xv : 0.f;
+                yv = isfinite(yv) ? yv : 0.f;
+            }
+            sX[i] = xv;
+            sY[i] = yv;
         }
         __syncthreads();
         // horizontal window sums of x, y, xx, yy, xy: a thread slides one
@@ -227,11 +234,15 @@ __global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, con
 
 __global__ void __launch_bounds__(256) k_l2(const float *__restrict__ img, const float *__restrict__ tgt, size_t P3,
                                             float scale, float *__restrict__ eo, float *__restrict__ ho,
-                                            double *loss) {
+                                            double *loss, uint32_t *__restrict__ status) {
     __shared__ double sred[8];
     double acc = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P3; i += (size_t)gridDim.x * blockDim.x) {
-        const float d = img[i] - tgt[i];
+        float d = img[i] - tgt[i];
+        if (!isfinite(d)) {   // a non-finite pixel counts as 0 and raises the status bit
+            if (status) atomicOr(status, GS2_ST_NONFINITE);
+            d = 0.f;
+        }
         eo[i] = scale * d;
         ho[i] = scale;
         acc += 0.5 * (double)d * (double)d;
@@ -252,14 +263,14 @@ cudaError_t prepare_loss_kernels() {
 }
 
 cudaError_t launch_loss(const float *image, const float *target, int w, int h, const gs2_config &cfg, float *e,
-                        float *hh, double *loss_out, cudaStream_t st) {
+                        float *hh, double *loss_out, cudaStream_t st, uint32_t *status) {
     const size_t P = (size_t)w * h;
     if (P == 0) return cudaSuccess;
     const float scale = (float)(1.0 / (3.0 * (double)P));
     if (cfg.lambda_ssim == 0.f) {
         const size_t P3 = 3 * P;
         int grid = (int)std::min<size_t>((P3 + 255) / 256, 148 * 16);
-        k_l2<<<grid, 256, 0, st>>>(image, target, P3, scale, e, hh, loss_out);
+        k_l2<<<grid, 256, 0, st>>>(image, target, P3, scale, e, hh, loss_out, status);
         GS2_COUNT_LAUNCH(1);
         return cudaGetLastError();
     }
@@ -282,7 +293,7 @@ cudaError_t launch_loss(const float *image, const float *target, int w, int h, c
     const cudaError_t e0 = prepare_loss_kernels();
     if (e0 != cudaSuccess) return e0;
     dim3 grid((w + LT_W - 1) / LT_W, (h + LT_H - 1) / LT_H);
-    k_ssim<<<grid, 256, smem, st>>>(image, target, w, h, K, e, hh, loss_out);
+    k_ssim<<<grid, 256, smem, st>>>(image, target, w, h, K, e, hh, loss_out, status);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

@@ -104,7 +104,7 @@ extern "C" gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene 
     const DevScene sc = make_devscene(scene);
     const DevCam dc = make_devcam(cam);
     ProjView pv = proj_view(proj, scene->n);
-    if (launch_project(sc, dc, c, pv, tiles_x, tiles_y, st) != cudaSuccess) return GS2_ERR_CUDA;
+    if (launch_project(sc, dc, c, pv, tiles_x, tiles_y, st, v.d_status) != cudaSuccess) return GS2_ERR_CUDA;
     if (launch_bin_sort(&v, pv, scene->n, tiles_x, tiles_y, st, nullptr) != cudaSuccess) return GS2_ERR_CUDA;
     if (launch_raster(&v, pv, dc, c, image, raster_view(raster_state, cam->width, cam->height), st) != cudaSuccess)
         return GS2_ERR_CUDA;

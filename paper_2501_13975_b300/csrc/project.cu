@@ -20,7 +20,8 @@
 
 template <int S>
 __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float lowpass, float near_z,
-                                                 float alpha_min, ProjView pv, int tiles_x, int tiles_y) {
+                                                 float alpha_min, ProjView pv, int tiles_x, int tiles_y,
+                                                 uint32_t *__restrict__ status) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= sc.n) return;
     const int n = sc.n;
@@ -34,7 +35,12 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
     d = d + (double)cam.V[11];
     const float tz = (float)d;
     pv.key[k] = __float_as_uint(tz);
-    const bool vis = (d >= (double)near_z) && (sigma >= alpha_min);
+    // a non-finite parameter makes the Gaussian invisible and raises the
+    // status bit; the rest of the view is unaffected (rotation and scales are
+    // checked below, once they are loaded for a Gaussian in front of the camera)
+    const bool finite = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(sigma);
+    if (!finite && status) atomicOr(status, GS2_ST_NONFINITE);
+    const bool vis = finite && (d >= (double)near_z) && (sigma >= alpha_min);
     if (!vis) {
         pv.touched[k] = 0u;
         pv.rect[k] = make_uint2(0u, 0u);
@@ -49,6 +55,16 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
     for (int i = 0; i < 3 * S; ++i) shc[i] = __ldcs(sc.sh + (size_t)i * n + k);
     float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
     const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
+    if (!(isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(s0) && isfinite(s1) &&
+          isfinite(s2))) {
+        if (status) atomicOr(status, GS2_ST_NONFINITE);
+        pv.touched[k] = 0u;
+        pv.rect[k] = make_uint2(0u, 0u);
+        pv.recA[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pv.recB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const float *V = cam.V;
     const float tx = fmaf(V[0], px, fmaf(V[1], py, fmaf(V[2], pz, V[3])));
     const float ty = fmaf(V[4], px, fmaf(V[5], py, fmaf(V[6], pz, V[7])));
@@ -143,14 +159,14 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
 }
 
 cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
-                           int tiles_y, cudaStream_t st) {
+                           int tiles_y, cudaStream_t st, uint32_t *status) {
     if (sc.n == 0) return cudaSuccess;
     const unsigned grid = (sc.n + 255) / 256;
     switch (sc.S) {
-    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
-    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
-    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
-    default: k_project<16><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y); break;
+    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
+    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
+    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
+    default: k_project<16><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
     }
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
