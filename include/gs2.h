@@ -346,10 +346,14 @@ gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const gs2_camera *
  * fork/join as one CUDA graph (on a stream of the batch, so `stream` may be
  * the legacy default stream) and launches it on `stream`; the instantiated
  * graph is kept and updated in place on later calls (re-instantiated if the
- * update is refused).  A context's first use must not be under capture: create the
+ * update is refused).  use_graph = 2 keeps one instantiated graph per scene
+ * and sweep inputs (a hash of the primary, its views' cameras and target
+ * pointers, the scene, output pointers, configuration, step model and
+ * tuning; up to 512 per scene): a sweep seen before is replayed without
+ * capture, a new one is captured once.  A context's first use must not be under capture: create the
  * batch before capturing anything.  gs2_batch_ctx gives scene i's context
- * (for tuning or checks); gs2_batch_stats the graph instantiation and update
- * counts. */
+ * (for tuning or checks); gs2_batch_stats the graph instantiation, update
+ * and replay counts. */
 typedef struct gs2_batch gs2_batch;
 typedef struct {
     int64_t max_gaussians;
@@ -360,7 +364,7 @@ gs2_status gs2_batch_create(gs2_batch **out, const gs2_config *cfg, int32_t n_sc
 gs2_status gs2_batch_destroy(gs2_batch *batch);
 gs2_ctx *gs2_batch_ctx(gs2_batch *batch, int32_t i);
 const char *gs2_batch_last_error(const gs2_batch *batch);
-gs2_status gs2_batch_stats(const gs2_batch *batch, int32_t *instantiations, int32_t *updates);
+gs2_status gs2_batch_stats(const gs2_batch *batch, int32_t *instantiations, int32_t *updates, int32_t *replays);
 gs2_status gs2_batch_sweep(gs2_batch *batch, gs2_scene *scenes, const gs2_camera *const *cams, const int32_t *ncam,
                            const float *const *const *targets, const int32_t *const *knn, const int32_t *t,
                            double *losses_out, int32_t *n_failed, int32_t use_graph, gs2_stream stream);

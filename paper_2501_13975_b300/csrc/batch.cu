@@ -5,17 +5,26 @@
 // every scene's sweep (Sec. 4.2 groups with the Sec. 4.3 secondaries) onto its
 // stream from the caller's stream and joins them back, so scenes of uneven
 // size fill the 148 SMs together: small scenes' kernels run beside a large
-// scene's instead of after it.  With use_graph the fork/join is captured as
-// one CUDA graph (one parallel branch per scene) and launched with a single
-// cudaGraphLaunch; later calls re-capture (the primaries change from sweep to
-// sweep, and with them the kernels' camera arguments) and update the
-// instantiated graph in place with cudaGraphExecUpdate, which succeeds while
-// the graph's shape (kernel sequence) is unchanged.
+// scene's instead of after it.
+//
+// use_graph = 1: the whole fork/join is captured as one CUDA graph (one
+// parallel branch per scene) and launched with a single cudaGraphLaunch;
+// later calls re-capture (the primaries change from sweep to sweep, and with
+// them the kernels' camera arguments) and update the instantiated graph in
+// place with cudaGraphExecUpdate (accepted while the kernel sequence is the
+// same).
+// use_graph = 2: one graph per scene and sweep inputs, kept: the inputs that
+// end up in kernel arguments (primary, the cameras of its views, target,
+// scene and output pointers, configuration, step model, tuning) are hashed;
+// a sweep whose key was seen before replays its instantiated graph without
+// any capture -- in training the primaries cycle through the cameras, so
+// every graph is captured once and replayed from then on.
 //
 // Tuning: the radix sort's grid (CTAs) and keys per thread per scatter round.
 // The autotuner times whole sweeps on a scratch copy of the scene for every
 // candidate and keeps the fastest in the context.
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -121,6 +130,8 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
 }
 
 // ------------------------------------------------------------------ batch
+#define GS2_GRAPH_CACHE_MAX 512   // per scene; beyond it the cache is emptied and refilled
+
 struct gs2_batch {
     std::vector<gs2_ctx *> ctx;
     std::vector<cudaStream_t> streams;
@@ -128,12 +139,24 @@ struct gs2_batch {
     cudaEvent_t fork = nullptr, ready = nullptr;
     cudaStream_t cap = nullptr;   // capture origin (the caller's stream may be the legacy default stream)
     cudaGraphExec_t exec = nullptr;
-    int graph_updates = 0, graph_instantiations = 0;
+    int graph_updates = 0, graph_instantiations = 0, graph_replays = 0;
+    std::vector<std::unordered_map<uint64_t, cudaGraphExec_t>> cache;   // per scene (use_graph = 2)
     std::string err;
 };
 
+// FNV-1a over raw bytes
+static inline void fnv(uint64_t &h, const void *p, size_t nbytes) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < nbytes; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+}
+
 static void batch_free(gs2_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto &m : b->cache)
+        for (auto &kv : m) cudaGraphExecDestroy(kv.second);
     for (cudaEvent_t e : b->join)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -154,6 +177,7 @@ extern "C" gs2_status gs2_batch_create(gs2_batch **out, const gs2_config *cfg, i
     b->ctx.assign(n_scenes, nullptr);
     b->streams.assign(n_scenes, nullptr);
     b->join.assign(n_scenes, nullptr);
+    b->cache.resize(n_scenes);
     gs2_status rc = GS2_OK;
     for (int i = 0; i < n_scenes && rc == GS2_OK; ++i) {
         rc = gs2_create(&b->ctx[i], cfg, desc[i].max_gaussians, desc[i].max_width, desc[i].max_height,
@@ -190,10 +214,93 @@ extern "C" gs2_ctx *gs2_batch_ctx(gs2_batch *b, int32_t i) {
 
 extern "C" const char *gs2_batch_last_error(const gs2_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
-extern "C" gs2_status gs2_batch_stats(const gs2_batch *b, int32_t *instantiations, int32_t *updates) {
+extern "C" gs2_status gs2_batch_stats(const gs2_batch *b, int32_t *instantiations, int32_t *updates,
+                                      int32_t *replays) {
     if (!b) return GS2_ERR_ARG;
     if (instantiations) *instantiations = b->graph_instantiations;
     if (updates) *updates = b->graph_updates;
+    if (replays) *replays = b->graph_replays;
+    return GS2_OK;
+}
+
+// key of everything a scene's sweep bakes into kernel arguments
+static uint64_t sweep_key(const gs2_ctx *c, const gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
+                          const float *const *targets, const int32_t *knn, int32_t t, const double *losses,
+                          const int32_t *n_failed) {
+    uint64_t h = 1469598103934665603ull;
+    fnv(h, scene, sizeof(*scene));
+    fnv(h, &t, sizeof(t));
+    fnv(h, &ncam, sizeof(ncam));
+    fnv(h, &cams[t], sizeof(gs2_camera));
+    fnv(h, &targets[t], sizeof(targets[t]));
+    const int K = c->cfg.knn_k;
+    for (int q = 0; q < K; ++q) {
+        const int v = knn[t * K + q];
+        fnv(h, &v, sizeof(v));
+        if (v >= 0 && v < ncam) {
+            fnv(h, &cams[v], sizeof(gs2_camera));
+            fnv(h, &targets[v], sizeof(targets[v]));
+        }
+    }
+    fnv(h, &losses, sizeof(losses));
+    fnv(h, &n_failed, sizeof(n_failed));
+    fnv(h, &c->cfg, sizeof(c->cfg));
+    fnv(h, &c->mlp_w, sizeof(c->mlp_w));
+    fnv(h, &c->nb_sort, sizeof(c->nb_sort));
+    fnv(h, &c->sort_rows, sizeof(c->sort_rows));
+    return h;
+}
+
+// use_graph = 2: per scene, replay the graph of this sweep's key or capture it
+static gs2_status batch_cached(gs2_batch *b, gs2_scene *scenes, const gs2_camera *const *cams, const int32_t *ncam,
+                               const float *const *const *targets, const int32_t *const *knn, const int32_t *t,
+                               double *losses, int32_t *n_failed, cudaStream_t st) {
+    const int ns = (int)b->ctx.size();
+    RETB(b, cudaEventRecord(b->fork, st));
+    for (int i = 0; i < ns; ++i) {
+        double *li = losses ? losses + 10 * (size_t)i : nullptr;
+        int32_t *fi = n_failed ? n_failed + i : nullptr;
+        const uint64_t key = sweep_key(b->ctx[i], &scenes[i], cams[i], ncam[i], targets[i], knn[i], t[i], li, fi);
+        auto &m = b->cache[i];
+        auto it = m.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (it != m.end()) {
+            exec = it->second;
+            ++b->graph_replays;
+        } else {
+            if ((int)m.size() >= GS2_GRAPH_CACHE_MAX) {
+                for (auto &kv : m) cudaGraphExecDestroy(kv.second);
+                m.clear();
+            }
+            RETB(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            const gs2_status rc = sweep_run(b->ctx[i], &scenes[i], cams[i], ncam[i], targets[i], knn[i], t[i], nullptr,
+                                            li, fi, b->cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+            if (rc != GS2_OK) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                b->err = "scene " + std::to_string(i) + ": " + b->ctx[i]->err;
+                return rc;
+            }
+            if (ec != cudaSuccess || !g) {
+                b->err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec);
+                return GS2_ERR_CUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                b->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+                return GS2_ERR_CUDA;
+            }
+            m.emplace(key, exec);
+            ++b->graph_instantiations;
+        }
+        RETB(b, cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        RETB(b, cudaGraphLaunch(exec, b->streams[i]));
+        RETB(b, cudaEventRecord(b->join[i], b->streams[i]));
+        RETB(b, cudaStreamWaitEvent(st, b->join[i], 0));
+    }
     return GS2_OK;
 }
 
@@ -226,6 +333,7 @@ extern "C" gs2_status gs2_batch_sweep(gs2_batch *b, gs2_scene *scenes, const gs2
     if (!b || !scenes || !cams || !ncam || !targets || !knn || !t) return GS2_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (!use_graph) return batch_enqueue(b, scenes, cams, ncam, targets, knn, t, losses_out, n_failed, st);
+    if (use_graph == 2) return batch_cached(b, scenes, cams, ncam, targets, knn, t, losses_out, n_failed, st);
     // capture on the batch's own stream; the graph is launched on the caller's
     RETB(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     const gs2_status rc = batch_enqueue(b, scenes, cams, ncam, targets, knn, t, losses_out, n_failed, b->cap);

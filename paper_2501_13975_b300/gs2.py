@@ -105,7 +105,7 @@ _sigs = {
     "gs2_batch_destroy": (C.c_int, [_vp]),
     "gs2_batch_ctx": (_vp, [_vp, C.c_int32]),
     "gs2_batch_last_error": (C.c_char_p, [_vp]),
-    "gs2_batch_stats": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "gs2_batch_stats": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "gs2_batch_sweep": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(C.POINTER(Camera_)), C.POINTER(C.c_int32),
                                   C.POINTER(C.POINTER(_vp)), C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int32),
                                   _vp, _vp, C.c_int32, _vp]),
@@ -486,9 +486,9 @@ class Batch:
         return _lib.gs2_batch_ctx(self.h, int(i))
 
     def stats(self):
-        a, b = C.c_int32(0), C.c_int32(0)
-        _lib.gs2_batch_stats(self.h, C.byref(a), C.byref(b))
-        return dict(instantiations=a.value, updates=b.value)
+        a, b, r = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        _lib.gs2_batch_stats(self.h, C.byref(a), C.byref(b), C.byref(r))
+        return dict(instantiations=a.value, updates=b.value, replays=r.value)
 
     def set_tuning(self, i: int, sort_blocks: int, sort_rows: int):
         t = Tuning_(int(sort_blocks), int(sort_rows))
@@ -526,9 +526,11 @@ class Batch:
         return prep
 
     def sweep(self, prep, t, losses=None, n_failed=None, use_graph=False, stream=None):
+        """use_graph: False (eager), True or 1 (one graph, re-captured and
+        updated per call), 2 (graphs kept per scene and sweep inputs)."""
         tt = (C.c_int32 * self.n)(*[int(x) for x in t])
         st = _lib.gs2_batch_sweep(self.h, prep["scenes"], prep["cams"], prep["ncam"], prep["tgts"], prep["knn"], tt,
-                                  _ptr(losses), _ptr(n_failed), 1 if use_graph else 0, _stream(stream))
+                                  _ptr(losses), _ptr(n_failed), int(use_graph), _stream(stream))
         if st != 0:
             raise GS2Error(f"gs2_batch_sweep: {STATUS.get(st, st)}: {_lib.gs2_batch_last_error(self.h).decode()}")
 

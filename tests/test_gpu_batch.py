@@ -80,7 +80,7 @@ def _close(a, b, before=None):
             (name, float(np.median(r)), float(np.quantile(r, 0.98)), float((r > 0.5).mean()))
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
 def test_batched_sweep_equals_per_scene_sweeps(use_graph):
     """Each batched sweep (a different primary per scene) against gs2_sweep
     of every scene alone, from the same snapshot of the scene: one sweep at a
@@ -88,7 +88,8 @@ def test_batched_sweep_equals_per_scene_sweeps(use_graph):
     sweeps of a diverging scene."""
     from paper_2501_13975_b300 import gs2
     work, sizes, targets, knns = _setup(gs2)
-    schedule = [[0, 1, 2], [3, 0, 4], [5, 2, 1]]
+    # the last sweep repeats the first's primaries: with kept graphs it replays
+    schedule = [[0, 1, 2], [3, 0, 4], [5, 2, 1], [0, 1, 2]]
     batch = gs2.Batch(sizes)
     refs = [gs2.Context(s["n"], s["w"], s["h"], 3, 64 * s["n"]) for s in work]
     scenes = [gs2.DeviceScene.from_host(s["train"]) for s in work]
@@ -110,10 +111,12 @@ def test_batched_sweep_equals_per_scene_sweeps(use_graph):
             _close(scenes[i], ref[i], snap[i])
     assert bool((losses[:, 0] > 0).all())
     st = batch.stats()
-    if use_graph:
+    if use_graph == 1:
         assert st["instantiations"] >= 1 and st["instantiations"] + st["updates"] == len(schedule)
+    elif use_graph == 2:
+        assert st == dict(instantiations=3 * len(work), updates=0, replays=len(work))
     else:
-        assert st == dict(instantiations=0, updates=0)
+        assert st == dict(instantiations=0, updates=0, replays=0)
 
 
 def test_autotune_keeps_scene_and_results():
