@@ -81,17 +81,21 @@ __device__ __forceinline__ void falloff_derivs(float G, float ca, float cb, floa
 // the rest (41 = 32 + 9 -> 32 + 16 padded slots instead of 64).
 template <int P> struct Pad { static constexpr int PP = P <= 2 ? 2 : P <= 4 ? 4 : P <= 8 ? 8 : P <= 16 ? 16 : P <= 32 ? 32 : 64; };
 
-template <int Q, int OFF, int P, typename ACC>
+// TOP: first butterfly offset; 16 reduces over the whole warp, 8 over each
+// half-warp separately (one step fewer, twice the atomics -- measured slower
+// for the position payload on the scene workload, so 16 is used)
+template <int Q, int OFF, int P, typename ACC, int TOP = 16>
 __device__ __forceinline__ void reduce_scatter_part(const float (&pl)[P], int lane, ACC *__restrict__ zbuf, int n,
                                                     uint32_t k) {
     constexpr int PP = Pad<Q>::PP;
+    constexpr int GROUP_LANES = 2 * TOP;   // lanes that end up sharing one reduction
     float v[PP];
 #pragma unroll
     for (int i = 0; i < PP; ++i) v[i] = (i < Q) ? pl[OFF + i] : 0.f;
     int off = 0;           // index of v[0] in this part
     int len = PP;          // values this lane still holds
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = TOP; o > 0; o >>= 1) {
         const bool up = (lane & o) != 0;
         if (len > 1) {
             const int h = len >> 1;
@@ -109,11 +113,11 @@ __device__ __forceinline__ void reduce_scatter_part(const float (&pl)[P], int la
             v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], o);
         }
     }
-    // lanes that share an entry (PP < 32): only the one with the low lane bits clear writes
-    constexpr int share = (PP >= 32) ? 1 : 32 / PP;
+    // lanes that share an entry (PP < GROUP_LANES): only the one with the low lane bits clear writes
+    constexpr int share = (PP >= GROUP_LANES) ? 1 : GROUP_LANES / PP;
     if ((lane & (share - 1)) == 0) {
 #pragma unroll
-        for (int j = 0; j < (PP >= 32 ? PP / 32 : 1); ++j) {
+        for (int j = 0; j < (PP >= GROUP_LANES ? PP / GROUP_LANES : 1); ++j) {
             const int idx = off + j;
             if (idx < Q && v[j] != 0.f) atomicAdd(&zbuf[(size_t)(OFF + idx) * n + k], (ACC)v[j]);
         }
