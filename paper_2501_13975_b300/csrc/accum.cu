@@ -349,9 +349,8 @@ __global__ void k_epi_opacity(const ProjView pv, ACC *__restrict__ zbuf, int n, 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || pv.touched[k] == 0u) return;
     const float z0 = (float)zbuf[k], z1 = (float)zbuf[n + k];
-    const float b0 = blocks[k], b1 = blocks[n + k];
-    blocks[k] = b0 + z0;
-    blocks[n + k] = b1 + z1;
+    atomicAdd(&blocks[k], z0);          // the views of a group may run concurrently
+    atomicAdd(&blocks[n + k], z1);
     zbuf[k] = 0.f;
     zbuf[n + k] = 0.f;
 }
@@ -385,11 +384,9 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__r
     if (k >= n || pv.touched[k] == 0u) return;
     // every load first (accumulators, the block entries updated, parameters):
     // they are then in flight together instead of one memory latency each
-    float z[9], bk[9];
+    float z[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) bk[i] = blocks[(size_t)i * n + k];
     GaussGeo g;
     load_geo(sc, k, g);
 #pragma unroll
@@ -411,7 +408,7 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__r
         float gj = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) gj += z[a] * dS[j][a];
-        blocks[(size_t)j * n + k] = bk[j] + gj;
+        atomicAdd(&blocks[(size_t)j * n + k], gj);
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -425,7 +422,7 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__r
             if (j == l)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) hv += z[a] * d2S[j][a];
-            blocks[(size_t)(3 + ut3(j, l)) * n + k] = bk[3 + ut3(j, l)] + hv;
+            atomicAdd(&blocks[(size_t)(3 + ut3(j, l)) * n + k], hv);
         }
 }
 
@@ -438,7 +435,6 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
     float z[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
-    const float b0 = blocks[k], b1 = blocks[n + k];
     GaussGeo g;
     load_geo(sc, k, g);
 #pragma unroll
@@ -498,8 +494,8 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
             hth += d1[aa] * hz * d1[b];
         }
     }
-    blocks[k] = b0 + gth;
-    blocks[n + k] = b1 + hth;
+    atomicAdd(&blocks[k], gth);
+    atomicAdd(&blocks[n + k], hth);
 }
 
 // Position epilogue.  With u = 1/t_z and a, b in {x, y}:
@@ -718,11 +714,11 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
         }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) blocks[(size_t)c * n + k] += gp[c];
+    for (int c = 0; c < 3; ++c) atomicAdd(&blocks[(size_t)c * n + k], gp[c]);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = a; b < 3; ++b) blocks[(size_t)(3 + ut3(a, b)) * n + k] += Hp[a][b];
+        for (int b = a; b < 3; ++b) atomicAdd(&blocks[(size_t)(3 + ut3(a, b)) * n + k], Hp[a][b]);
 }
 
 template <typename ACC>
@@ -731,7 +727,8 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
                            const uint32_t *ids, bool prof, cudaStream_t st) {
     const int n = sc.n;
     ACC *zb = (ACC *)ctx->zbuf;
-    unsigned long long *act = ctx->prof_on ? ctx->d_stats + 4 * group + 3 : nullptr;
+    gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
+    unsigned long long *act = pc->prof_on ? pc->d_stats + 4 * group + 3 : nullptr;
 #define ACC_LAUNCH(G)                                                                                             \
     k_accum<G, ACC><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
                                                    view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n, act)
@@ -744,8 +741,8 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     }
 #undef ACC_LAUNCH
     if (prof) {
-        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], st);
-        ctx->prof_n++;
+        cudaEventRecord(pc->prof_ev[2 * pc->prof_n + 1], st);
+        pc->prof_n++;
     }
     GS2_COUNT_LAUNCH(2);
     if (n == 0) return;
@@ -775,10 +772,11 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
                          cudaStream_t st) {
     dim3 grid(ctx->tiles_x, ctx->tiles_y);
     const uint32_t *ids = ctx->vals[ctx->sorted];
-    const bool prof = ctx->prof_on && ctx->prof_n < 512;
+    gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool (shared by a sweep's view lanes)
+    const bool prof = pc->prof_on && pc->prof_n < 512;
     if (prof) {
-        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
-        ctx->prof_group[ctx->prof_n] = group;
+        cudaEventRecord(pc->prof_ev[2 * pc->prof_n], st);
+        pc->prof_group[pc->prof_n] = group;
     }
     if (cfg.precision == 0)
         launch_accum_t<float>(ctx, group, sc, view, primary, pv, rv, cfg, view_slot, blocks, grid, ids, prof, st);

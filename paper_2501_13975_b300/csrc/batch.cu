@@ -48,6 +48,7 @@ extern "C" gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out) {
     if (!ctx || !out) return GS2_ERR_ARG;
     out->sort_blocks = ctx->nb_sort;
     out->sort_rows = ctx->sort_rows;
+    out->view_lanes = ctx->view_lanes;
     return GS2_OK;
 }
 
@@ -55,8 +56,10 @@ extern "C" gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *t) {
     if (!ctx || !t) return GS2_ERR_ARG;
     if (t->sort_blocks < 1 || t->sort_blocks > GS2_SORT_BLOCKS_MAX) return GS2_ERR_ARG;
     if (t->sort_rows != 2 && t->sort_rows != 4 && t->sort_rows != 8) return GS2_ERR_ARG;
+    if (t->view_lanes != 0 && t->view_lanes != 1) return GS2_ERR_ARG;
     ctx->nb_sort = t->sort_blocks;
     ctx->sort_rows = t->sort_rows;
+    ctx->view_lanes = t->view_lanes;
     return GS2_OK;
 }
 
@@ -86,7 +89,7 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gs2_status rc = GS2_OK;
-    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows};
+    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows, ctx->view_lanes};
     gs2_tuning best = keep;
     float best_ms = 1e30f;
     const int blocks[3] = {148 * 2, 148 * 4, 148 * 6};
@@ -110,7 +113,7 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
             ms /= (float)reps;
             if (ms < best_ms) {
                 best_ms = ms;
-                best = {blocks[bi], rows[ri]};
+                best = {blocks[bi], rows[ri], ctx->view_lanes};
             }
         }
     cudaStreamSynchronize(st);
@@ -248,6 +251,7 @@ static uint64_t sweep_key(const gs2_ctx *c, const gs2_scene *scene, const gs2_ca
     fnv(h, &c->mlp_w, sizeof(c->mlp_w));
     fnv(h, &c->nb_sort, sizeof(c->nb_sort));
     fnv(h, &c->sort_rows, sizeof(c->sort_rows));
+    fnv(h, &c->view_lanes, sizeof(c->view_lanes));
     return h;
 }
 

@@ -13,6 +13,7 @@
 
 #define GS2_TILE 16                  // screen tile edge in pixels
 #define GS2_SORT_BLOCKS_MAX 1024     // the per-digit scan runs one 1024-thread CTA per digit
+#define GS2_MAX_LANES 16             // concurrent views per group in a sweep (secondaries)
 #define GS2_TILE_PIX (GS2_TILE * GS2_TILE)
 #define GS2_ZPOS 41                  // image-space payload of the position group
 #define GS2_MAX_SH 16
@@ -128,6 +129,7 @@ struct gs2_ctx {
     int64_t max_pairs;
     int nb_sort;                 // blocks of the radix sort grid (tuning, <= GS2_SORT_BLOCKS_MAX)
     int sort_rows;               // keys per thread per scatter round (tuning: 2, 4, 8)
+    int view_lanes;              // run a sweep's views concurrently (tuning: 0, 1)
     // sorting
     uint32_t *keys[2];           // pair keys: tile id
     uint32_t *vals[2];           // pair values: Gaussian id
@@ -164,6 +166,15 @@ struct gs2_ctx {
     int stat_slot;               // group slot the binning statistics go to
     unsigned long long h_pixels[5];
     std::string err;
+    // view lanes: a sweep runs the views of a group concurrently, view slot
+    // i >= 1 on lane i - 1 (own sorting / render / accumulation scratch and
+    // stream, sharing the status word, the statistics and the depth-order
+    // cache); owner: the context whose profile pool and statistics a lane uses
+    gs2_ctx *owner;
+    int n_lanes;
+    gs2_ctx *lanes[GS2_MAX_LANES];
+    cudaStream_t lane_st[GS2_MAX_LANES];
+    cudaEvent_t lane_ev[GS2_MAX_LANES + 1];
 };
 
 // number of kernels this library has launched (host-side count)

@@ -99,7 +99,24 @@ extern "C" size_t gs2_blocks_bytes(gs2_group g, int64_t n, int32_t sh, int32_t n
 }
 extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return step_bytes_impl(g, n, sh); }
 
+// a view lane's own scratch (the rest is shared with its owner)
+static void free_lane(gs2_ctx *l) {
+    void *ptrs[] = {l->keys[0], l->keys[1], l->vals[0], l->vals[1], l->ghist, l->bsum, l->d_count, l->ranges,
+                    l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
 static void free_ctx(gs2_ctx *c) {
+    for (int i = 0; i < c->n_lanes; ++i) {
+        if (c->lanes[i]) {
+            free_lane(c->lanes[i]);
+            delete c->lanes[i];
+        }
+        if (c->lane_st[i]) cudaStreamDestroy(c->lane_st[i]);
+    }
+    for (int i = 0; i <= c->n_lanes && i <= GS2_MAX_LANES; ++i)
+        if (c->lane_ev[i]) cudaEventDestroy(c->lane_ev[i]);
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->flags, c->g_prim, c->lg_phi,
@@ -140,6 +157,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     c->max_pairs = max_pairs;
     c->nb_sort = SORT_BLOCKS;
     c->sort_rows = 4;
+    c->view_lanes = 1;
     const size_t P = (size_t)max_w * max_h;
     const int tiles = ((max_w + GS2_TILE - 1) / GS2_TILE) * ((max_h + GS2_TILE - 1) / GS2_TILE);
     const int K = c->cfg.knn_k, f = c->cfg.downsample;
@@ -183,6 +201,50 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 20) == cudaSuccess;
+    // view lanes for the secondaries of a sweep
+    c->owner = nullptr;
+    c->n_lanes = 0;
+    const int nl = std::min(K, GS2_MAX_LANES);
+    for (int i = 0; i < nl && ok; ++i) {
+        gs2_ctx *l = new (std::nothrow) gs2_ctx();
+        if (!l) {
+            ok = false;
+            break;
+        }
+        c->lanes[i] = l;
+        c->n_lanes = i + 1;
+        l->cfg = c->cfg;
+        l->max_n = max_n;
+        l->max_w = max_w;
+        l->max_h = max_h;
+        l->max_sh = max_sh;
+        l->max_pairs = max_pairs;
+        l->nb_sort = c->nb_sort;
+        l->sort_rows = c->sort_rows;
+        for (int j = 0; j < 2; ++j) {
+            A((void **)&l->keys[j], sizeof(uint32_t) * (size_t)max_pairs);
+            A((void **)&l->vals[j], sizeof(uint32_t) * (size_t)max_pairs);
+        }
+        A((void **)&l->ghist, sizeof(uint32_t) * (256 * (size_t)GS2_SORT_BLOCKS_MAX + 256));
+        A((void **)&l->bsum, sizeof(unsigned long long) * 1024);
+        A((void **)&l->d_count, sizeof(uint32_t) * 4);
+        A((void **)&l->ranges, sizeof(uint2) * (size_t)tiles);
+        A((void **)&l->zbuf, sizeof(double) * GS2_ZPOS * (size_t)max_n);
+        A((void **)&l->pix_e, sizeof(float) * 3 * P);
+        A((void **)&l->pix_h, sizeof(float) * 3 * P);
+        A(&l->sw_proj, proj_bytes_impl(max_n));
+        A(&l->sw_rstate, raster_state_bytes_impl(max_w, max_h));
+        A((void **)&l->sw_image, sizeof(float) * 3 * P);
+        if (ok) ok = cudaMemset(l->zbuf, 0, sizeof(double) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
+        if (ok) ok = cudaMemset(l->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
+        l->d_status = c->d_status;
+        l->d_stats = c->d_stats;
+        l->order_cache = c->order_cache;
+        l->owner = c;
+        if (ok) ok = cudaStreamCreateWithFlags(&c->lane_st[i], cudaStreamNonBlocking) == cudaSuccess;
+    }
+    for (int i = 0; i <= nl && ok; ++i)
+        ok = cudaEventCreateWithFlags(&c->lane_ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         free_ctx(c);
         delete c;
@@ -280,9 +342,10 @@ static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const vo
     ctx->tiles_x = (cam->width + GS2_TILE - 1) / GS2_TILE;
     ctx->tiles_y = (cam->height + GS2_TILE - 1) / GS2_TILE;
     ProjView pv = proj_view(const_cast<void *>(proj), n);
+    gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // statistics (shared by a sweep's view lanes)
     RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st,
-                                  ctx->prof_on ? ctx->d_stats + 4 * ctx->stat_slot : nullptr, order_in, order_out));
-    if (ctx->prof_on) ctx->h_pixels[ctx->stat_slot] += (unsigned long long)cam->width * cam->height;
+                                  pc->prof_on ? pc->d_stats + 4 * pc->stat_slot : nullptr, order_in, order_out));
+    if (pc->prof_on) pc->h_pixels[pc->stat_slot] += (unsigned long long)cam->width * cam->height;
     RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image,
                                 raster_view(rstate, cam->width, cam->height), st));
     return GS2_OK;
@@ -507,20 +570,51 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         }
     }
     const gs2_camera *primary = &cams[t];
+    // the views of a group run concurrently: slot 0 on the caller's stream,
+    // slot i >= 1 on view lane i - 1 (forked and joined with events); their
+    // epilogues add into the shared blocks atomically (the logged sweep keeps
+    // one stream: its label passes reuse slot 0's scratch)
+    const bool lanes = ctx->view_lanes && !records && nv > 1 && ctx->n_lanes >= nv - 1;
+    if (lanes) {
+        for (int i = 0; i < nv - 1; ++i) {
+            gs2_ctx *l = ctx->lanes[i];
+            l->cfg = ctx->cfg;
+            l->nb_sort = ctx->nb_sort;
+            l->sort_rows = ctx->sort_rows;
+        }
+    }
     for (int group = 0; group < 5; ++group) {
         ctx->stat_slot = group;
         RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, blocks_bytes_impl(group, scene->n, scene->sh_degree, nv), st));
+        if (lanes) {
+            RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[0], st));
+            for (int i = 1; i < nv; ++i) RET_CUDA(ctx, cudaStreamWaitEvent(ctx->lane_st[i - 1], ctx->lane_ev[0], 0));
+        }
         for (int i = 0; i < nv; ++i) {
             if (vid[i] < 0) continue;
+            gs2_ctx *vc = (lanes && i > 0) ? ctx->lanes[i - 1] : ctx;
+            cudaStream_t vs = (lanes && i > 0) ? ctx->lane_st[i - 1] : st;
             // only the position group moves the means: the rotation pass sorts each
             // view by depth and keeps the order, the scaling, opacity and colour
             // passes reuse it (the same means and camera give the same order)
             uint32_t *cache = ctx->order_cache + (size_t)i * ctx->max_n;
-            TRY(do_project(ctx, scene, &vcam[i], ctx->sw_proj, st));
-            TRY(do_raster(ctx, scene->n, &vcam[i], ctx->sw_proj, ctx->sw_image, ctx->sw_rstate, st,
-                          group >= GS2_SCALE ? cache : nullptr, group == GS2_ROT ? cache : nullptr));
-            TRY(do_accum(ctx, group, scene, &vcam[i], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image, vtgt[i],
-                         i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, st));
+            gs2_status rc = do_project(vc, scene, &vcam[i], vc->sw_proj, vs);
+            if (rc == GS2_OK)
+                rc = do_raster(vc, scene->n, &vcam[i], vc->sw_proj, vc->sw_image, vc->sw_rstate, vs,
+                               group >= GS2_SCALE ? cache : nullptr, group == GS2_ROT ? cache : nullptr);
+            if (rc == GS2_OK)
+                rc = do_accum(vc, group, scene, &vcam[i], primary, vc->sw_proj, vc->sw_rstate, vc->sw_image, vtgt[i],
+                              i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, vs);
+            if (rc != GS2_OK) {
+                if (vc != ctx) ctx->err = vc->err;
+                return rc;
+            }
+        }
+        if (lanes) {
+            for (int i = 1; i < nv; ++i) {
+                RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[i], ctx->lane_st[i - 1]));
+                RET_CUDA(ctx, cudaStreamWaitEvent(st, ctx->lane_ev[i], 0));
+            }
         }
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
                                    ctx->sw_step, n_failed, ctx->flags, st));

@@ -321,9 +321,9 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *count, uint2 *ranges,
                          unsigned long long *stats) {
     const uint32_t M = count[0];
-    if (stats && blockIdx.x == 0 && threadIdx.x == 0) {
-        stats[0] += M;
-        stats[2] += 1ull;
+    if (stats && blockIdx.x == 0 && threadIdx.x == 0) {   // atomic: concurrent views share the counters
+        atomicAdd(&stats[0], (unsigned long long)M);
+        atomicAdd(&stats[2], 1ull);
     }
     const uint32_t nq = (M + 3u) / 4u;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {

@@ -53,7 +53,7 @@ class Config_(C.Structure):
 
 
 class Tuning_(C.Structure):
-    _fields_ = [("sort_blocks", C.c_int32), ("sort_rows", C.c_int32)]
+    _fields_ = [("sort_blocks", C.c_int32), ("sort_rows", C.c_int32), ("view_lanes", C.c_int32)]
 
 
 class BatchScene_(C.Structure):
@@ -392,10 +392,13 @@ class Context:
     def tuning(self) -> dict:
         t = Tuning_()
         self._ok(_lib.gs2_get_tuning(self.h, C.byref(t)), "gs2_get_tuning")
-        return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows)
+        return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows, view_lanes=t.view_lanes)
 
-    def set_tuning(self, sort_blocks: int, sort_rows: int):
-        t = Tuning_(int(sort_blocks), int(sort_rows))
+    def set_tuning(self, sort_blocks: int | None = None, sort_rows: int | None = None, view_lanes: int | None = None):
+        cur = self.tuning()
+        t = Tuning_(int(cur["sort_blocks"] if sort_blocks is None else sort_blocks),
+                    int(cur["sort_rows"] if sort_rows is None else sort_rows),
+                    int(cur["view_lanes"] if view_lanes is None else view_lanes))
         self._ok(_lib.gs2_set_tuning(self.h, C.byref(t)), "gs2_set_tuning")
 
     def autotune(self, scene: DeviceScene, cams, targets, knn, t, reps=2, stream=None):
@@ -408,7 +411,8 @@ class Context:
         ms = C.c_float(0.0)
         self._ok(_lib.gs2_autotune(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
                                    int(reps), C.byref(best), C.byref(ms), _stream(stream)), "gs2_autotune")
-        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, ms=float(ms.value))
+        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, view_lanes=best.view_lanes,
+                    ms=float(ms.value))
 
     def profile(self, enable: bool):
         self._ok(_lib.gs2_profile(self.h, 1 if enable else 0), "gs2_profile")
@@ -490,8 +494,8 @@ class Batch:
         _lib.gs2_batch_stats(self.h, C.byref(a), C.byref(b), C.byref(r))
         return dict(instantiations=a.value, updates=b.value, replays=r.value)
 
-    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int):
-        t = Tuning_(int(sort_blocks), int(sort_rows))
+    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int, view_lanes: int = 1):
+        t = Tuning_(int(sort_blocks), int(sort_rows), int(view_lanes))
         st = _lib.gs2_set_tuning(self.ctx_handle(i), C.byref(t))
         if st != 0:
             raise GS2Error(f"gs2_set_tuning: {STATUS.get(st, st)}")
@@ -508,7 +512,8 @@ class Batch:
                                int(reps), C.byref(best), C.byref(ms), _stream(stream))
         if st != 0:
             raise GS2Error(f"gs2_autotune: {STATUS.get(st, st)}")
-        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, ms=float(ms.value))
+        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, view_lanes=best.view_lanes,
+                    ms=float(ms.value))
 
     def prepare(self, scenes, cams, targets, knn):
         """Marshals the per-scene host arrays once (cameras, target pointers,

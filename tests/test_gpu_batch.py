@@ -131,7 +131,7 @@ def test_autotune_keeps_scene_and_results():
     for name in NAMES:
         assert torch.equal(getattr(ds, name), getattr(before, name)), name
     assert best["sort_blocks"] in (296, 592, 888) and best["sort_rows"] in (2, 4, 8) and best["ms"] > 0
-    assert ctx.tuning() == dict(sort_blocks=best["sort_blocks"], sort_rows=best["sort_rows"])
+    assert ctx.tuning() == dict(sort_blocks=best["sort_blocks"], sort_rows=best["sort_rows"], view_lanes=1)
     ctx.sweep(ds, s["cams"], targets[2], knns[2], 1)
     ref = gs2.DeviceScene.from_host(s["train"])
     ctx2 = gs2.Context(s["n"], s["w"], s["h"], 3, 64 * s["n"])
@@ -165,3 +165,24 @@ def test_tuning_rejects_bad_values():
     for b, r in ((0, 4), (2000, 4), (592, 3)):
         with pytest.raises(gs2.GS2Error):
             ctx.set_tuning(b, r)
+    with pytest.raises(gs2.GS2Error):
+        ctx.set_tuning(view_lanes=2)
+
+
+def test_concurrent_views_equal_serial_views():
+    """A sweep with the views of each group on their own streams equals the
+    same sweep with the views one after another (same snapshot, one sweep)."""
+    from paper_2501_13975_b300 import gs2
+    work, sizes, targets, knns = _setup(gs2)
+    for i, s in enumerate(work):
+        a = gs2.DeviceScene.from_host(s["train"])
+        b = gs2.DeviceScene.from_host(s["train"])
+        before = a.clone()
+        ctx = gs2.Context(s["n"], s["w"], s["h"], 3, 64 * s["n"])
+        assert ctx.tuning()["view_lanes"] == 1
+        ctx.sweep(a, s["cams"], targets[i], knns[i], 1)
+        ctx.set_tuning(view_lanes=0)
+        ctx.sweep(b, s["cams"], targets[i], knns[i], 1)
+        torch.cuda.synchronize()
+        ctx.check()
+        _close(a, b, before)
