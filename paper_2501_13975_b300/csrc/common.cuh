@@ -222,14 +222,6 @@ cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t 
 // the same alpha decisions bit for bit, so the Gaussian falloff is evaluated
 // with explicitly rounded operations (no compiler contraction choices).
 #ifdef __CUDACC__
-__device__ __forceinline__ float gs2_quadform(float ca, float cb, float cc, float dx, float dy) {
-    // q = ca dx^2 + 2 cb dx dy + cc dy^2
-    float q = __fmul_rn(__fmul_rn(ca, dx), dx);
-    q = __fadd_rn(q, __fmul_rn(__fmul_rn(__fmul_rn(2.0f, cb), dx), dy));
-    q = __fadd_rn(q, __fmul_rn(__fmul_rn(cc, dy), dy));
-    return q;
-}
-
 // Pixel of thread t in its 16x16 tile: warp w covers the 8x4 block
 // (w % 2, w / 2) of the tile, lane l its pixel (l % 8, l / 8) -- compact
 // warp blocks keep more of a warp's lanes inside a small Gaussian footprint
@@ -245,11 +237,21 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Gaussian falloff G = exp(-q/2) at pixel offset (dx, dy), with the hardware
-// exponential intrinsic (relative error ~1e-6, far inside the image and
-// derivative tolerances); the compositing and the accumulation both call this
-// function, so their alpha decisions stay identical bit for bit
+// Gaussian falloff G = exp(-q/2) at pixel offset (dx, dy), where
+// q = ca dx^2 + 2 cb dx dy + cc dy^2 (the conic's quadratic form).  q is formed
+// by explicitly rounded multiplies and fused multiply-adds in a fixed order
+// (no contraction choice is left to the compiler), and exp(-q/2) is taken as
+// 2^(-q / (2 ln 2)) with the hardware base-2 exponential (relative error
+// ~2^-22, flushed to 0 below the normal range: far inside the image and
+// derivative tolerances).  The compositing and the accumulation both call
+// this function, so their alpha decisions stay identical bit for bit.
 __device__ __forceinline__ float gs2_gauss(float ca, float cb, float cc, float dx, float dy) {
-    return __expf(__fmul_rn(-0.5f, gs2_quadform(ca, cb, cc, dx, dy)));
+    float a = __fmaf_rn(ca, dx, __fmul_rn(cb, dy));   // ca dx + cb dy
+    a = __fmaf_rn(cb, dy, a);                         // ca dx + 2 cb dy
+    const float q = __fmaf_rn(dx, a, __fmul_rn(__fmul_rn(cc, dy), dy));
+    const float x = __fmul_rn(q, -0.72134752044448170368f);   // -1 / (2 ln 2)
+    float g;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(x));
+    return g;
 }
 #endif

@@ -11,7 +11,11 @@
 // One CTA owns a 32x16 output tile and keeps everything in shared memory:
 // inputs with a 10-pixel halo (52x36), horizontal moment sums, the
 // coefficient maps on the 42x26 window-centre region and their horizontal
-// correlations.  HBM traffic per pixel: read c, c^t (24 B), write e, h (24 B).
+// correlations.  Each buffer reuses the space of one that is dead by then
+// (inputs and coefficient maps share one region, moment sums and correlated
+// maps the other): 65 KB, so three CTAs fit on an SM.  HBM traffic per
+// pixel: read c, c^t (24 B), write e, h (24 B); the final pass re-reads its
+// pixel's c, c^t from L2.
 #include <mutex>
 
 #include "common.cuh"
@@ -27,7 +31,8 @@
 #define SM_IN (IN_W * IN_H)
 #define SM_H1 (5 * IN_H * MO_W)
 #define SM_K (8 * MO_H * MO_W)
-#define SSIM_SMEM_FLOATS (2 * SM_IN + SM_H1 + SM_K)
+#define SM_R2 (2 * SM_IN > SM_K ? 2 * SM_IN : SM_K)
+#define SSIM_SMEM_FLOATS (SM_H1 + SM_R2)
 
 struct SsimConst {
     float g[LWIN];
@@ -48,12 +53,14 @@ __device__ __forceinline__ void block_add_double(double v, double *dst, double *
     }
 }
 
-__global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, const float *__restrict__ tgt, int W,
+__global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, const float *__restrict__ tgt, int W,
                                               int H, SsimConst K, float *__restrict__ eo, float *__restrict__ ho,
                                               double *loss, uint32_t *__restrict__ status) {
     extern __shared__ float sm[];
-    float *sX = sm, *sY = sm + SM_IN, *sH = sm + 2 * SM_IN, *sK = sm + 2 * SM_IN + SM_H1;
-    float *sHC = sH;  // reused after the moments are formed
+    // region 1: moment sums, then (once they are consumed) the correlated maps;
+    // region 2: the inputs, then (once the moments are formed) the coefficient maps
+    float *sH = sm, *sHC = sm;
+    float *sX = sm + SM_H1, *sY = sm + SM_H1 + SM_IN, *sK = sm + SM_H1;
     __shared__ double sred[8];
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * LT_W, y0 = blockIdx.y * LT_H;
@@ -214,11 +221,13 @@ __global__ void __launch_bounds__(256) k_ssim(const float *__restrict__ img, con
             const int r = r0 + o;
             const int gx = x0 + j, gy = y0 + r;
             if (gx >= W || gy >= H) continue;
-            const float x = sX[(r + 2 * LRAD) * IN_W + j + 2 * LRAD], y = sY[(r + 2 * LRAD) * IN_W + j + 2 * LRAD];
+            const size_t p = (size_t)c * P + (size_t)gy * W + gx;
+            float x = __ldg(img + p), y = __ldg(tgt + p);   // sanitised as in the staging pass
+            x = isfinite(x) ? x : 0.f;
+            y = isfinite(y) ? y : 0.f;
             const float *vo = v[o];
             const float dS = vo[0] + y * vo[1] + x * vo[2];
             const float d2S = vo[3] + x * vo[4] + y * vo[5] + x * y * vo[6] + x * x * vo[7] + vo[2];
-            const size_t p = (size_t)c * P + (size_t)gy * W + gx;
             eo[p] = K.scale * (x - y) - K.lam * K.scale * dS;
             ho[p] = K.scale - K.lam * K.scale * d2S;
             l2acc += 0.5 * (double)(x - y) * (double)(x - y);
