@@ -183,6 +183,15 @@ extern std::atomic<unsigned long long> g_gs2_launches;
 
 // --------------------------------------------------------------------------
 // launchers implemented in the .cu files (return a CUDA error code)
+// up to GS2_PROJ_VIEWS views of one scene projected by one launch
+#define GS2_PROJ_VIEWS 4
+struct ProjViews {
+    int nv;
+    DevCam cam[GS2_PROJ_VIEWS];
+    ProjView pv[GS2_PROJ_VIEWS];
+};
+cudaError_t launch_project_views(const DevScene &sc, const ProjViews &views, const gs2_config &cfg, cudaStream_t st,
+                                 uint32_t *status);
 cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
                            int tiles_y, cudaStream_t st, uint32_t *status);
 // order_in: a depth order of the same means and camera to reuse (skips the

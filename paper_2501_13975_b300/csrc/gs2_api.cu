@@ -587,6 +587,21 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         ctx->stat_slot = group;
         RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, blocks_bytes_impl(group, scene->n, scene->sh_degree, nv), st));
         if (lanes) {
+            // every view has its own projection buffer here: project them
+            // together (the parameters are read once per group, not per view)
+            ProjViews pvs;
+            pvs.nv = 0;
+            for (int i = 0; i < nv; ++i) {
+                if (vid[i] < 0) continue;
+                gs2_ctx *vc = i > 0 ? ctx->lanes[i - 1] : ctx;
+                pvs.cam[pvs.nv] = make_devcam(&vcam[i]);
+                pvs.pv[pvs.nv] = proj_view(vc->sw_proj, scene->n);
+                if (++pvs.nv == GS2_PROJ_VIEWS) {
+                    RET_CUDA(ctx, launch_project_views(make_devscene(scene), pvs, ctx->cfg, st, ctx->d_status));
+                    pvs.nv = 0;
+                }
+            }
+            RET_CUDA(ctx, launch_project_views(make_devscene(scene), pvs, ctx->cfg, st, ctx->d_status));
             RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[0], st));
             for (int i = 1; i < nv; ++i) RET_CUDA(ctx, cudaStreamWaitEvent(ctx->lane_st[i - 1], ctx->lane_ev[0], 0));
         }
@@ -598,7 +613,7 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             // view by depth and keeps the order, the scaling, opacity and colour
             // passes reuse it (the same means and camera give the same order)
             uint32_t *cache = ctx->order_cache + (size_t)i * ctx->max_n;
-            gs2_status rc = do_project(vc, scene, &vcam[i], vc->sw_proj, vs);
+            gs2_status rc = lanes ? GS2_OK : do_project(vc, scene, &vcam[i], vc->sw_proj, vs);
             if (rc == GS2_OK)
                 rc = do_raster(vc, scene->n, &vcam[i], vc->sw_proj, vc->sw_image, vc->sw_rstate, vs,
                                group >= GS2_SCALE ? cache : nullptr, group == GS2_ROT ? cache : nullptr);

@@ -9,74 +9,46 @@
 // { sigma G >= alpha_min } and the depth key.
 //
 // Memory: reads 13 + 3S floats per Gaussian from planar SoA rows (coalesced
-// 4-byte loads across the warp), writes 3 float4 records + rect + counts.
-// HBM-bound; FP64 is used only for the depth key (4 DFMA-equivalent ops).
-// The kernel is instantiated per SH count S, so every parameter load of a
-// visible Gaussian (4 + 3 + 3S rows) is unrolled and issued before the
-// arithmetic: a warp keeps all of them in flight at once instead of meeting
-// the memory latency once per loop iteration.
+// 4-byte loads across the warp), writes 3 float4 records + rect + counts per
+// view.  HBM-bound; FP64 is used only for the depth key (4 DFMA-equivalent
+// ops).  One launch projects up to GS2_PROJ_VIEWS views of the same scene
+// (the views of a sweep group): the parameters are read once and the
+// rotation is formed once, so four views cost 244 + 4 x 64 bytes per
+// Gaussian instead of 4 x (244 + 64).  The kernel is instantiated per SH
+// count S, so every parameter load of a visible Gaussian (4 + 3 + 3S rows) is
+// unrolled and issued before the arithmetic: a warp keeps all of them in
+// flight at once instead of meeting the memory latency once per loop
+// iteration.
 #include "common.cuh"
 #include "sh.cuh"
 
-template <int S>
-__global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float lowpass, float near_z,
-                                                 float alpha_min, ProjView pv, int tiles_x, int tiles_y,
-                                                 uint32_t *__restrict__ status) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= sc.n) return;
-    const int n = sc.n;
-    const float px = sc.mean[k], py = sc.mean[n + k], pz = sc.mean[2 * n + k];
-    const float sigma = sc.opacity[k];
-    // depth key: FP64, fixed summation order, rounded to FP32 (products of
-    // FP32 values are exact in FP64, so the key is reproducible bit for bit)
+__device__ __forceinline__ void write_invisible(const ProjView &pv, int k) {
+    pv.touched[k] = 0u;
+    pv.rect[k] = make_uint2(0u, 0u);
+    pv.recA[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    pv.recB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// depth along the view axis: FP64, fixed summation order (products of FP32
+// values are exact in FP64, so the key, rounded to FP32, is reproducible bit
+// for bit)
+__device__ __forceinline__ double view_depth(const DevCam &cam, float px, float py, float pz) {
     double d = (double)cam.V[8] * (double)px;
     d = d + (double)cam.V[9] * (double)py;
     d = d + (double)cam.V[10] * (double)pz;
-    d = d + (double)cam.V[11];
-    const float tz = (float)d;
-    pv.key[k] = __float_as_uint(tz);
-    // a non-finite parameter makes the Gaussian invisible and raises the
-    // status bit; the rest of the view is unaffected (rotation and scales are
-    // checked below, once they are loaded for a Gaussian in front of the camera)
-    const bool finite = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(sigma);
-    if (!finite && status) atomicOr(status, GS2_ST_NONFINITE);
-    const bool vis = finite && (d >= (double)near_z) && (sigma >= alpha_min);
-    if (!vis) {
-        pv.touched[k] = 0u;
-        pv.rect[k] = make_uint2(0u, 0u);
-        pv.recA[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        pv.recB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    // every remaining parameter load first (independent, all in flight together)
-    float shc[3 * S];
-#pragma unroll
-    for (int i = 0; i < 3 * S; ++i) shc[i] = __ldcs(sc.sh + (size_t)i * n + k);
-    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
-    const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
-    if (!(isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(s0) && isfinite(s1) &&
-          isfinite(s2))) {
-        if (status) atomicOr(status, GS2_ST_NONFINITE);
-        pv.touched[k] = 0u;
-        pv.rect[k] = make_uint2(0u, 0u);
-        pv.recA[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        pv.recB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
+    return d + (double)cam.V[11];
+}
+
+// One visible Gaussian in one view: EWA covariance, conic, tile rectangle,
+// view-dependent colour; writes its records.
+template <int S>
+__device__ __forceinline__ void project_one(const DevCam &cam, const ProjView &pv, int k, float px, float py, float pz,
+                                            float tz, float sigma, const float (&R)[3][3], const float (&ss)[3],
+                                            const float (&shc)[3 * S], float lowpass, float alpha_min) {
     const float *V = cam.V;
     const float tx = fmaf(V[0], px, fmaf(V[1], py, fmaf(V[2], pz, V[3])));
     const float ty = fmaf(V[4], px, fmaf(V[5], py, fmaf(V[6], pz, V[7])));
-
-    // rotation from the normalised quaternion
-    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-    float R[3][3];
-    R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
-    R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
-    R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
-
     // T = J Wr (2x3); J uses tx/tz, ty/tz clamped to the camera's frustum limits
     const float itz = 1.f / tz;
     const float taux = fminf(fmaxf(tx * itz, -cam.Lx), cam.Lx), tauy = fminf(fmaxf(ty * itz, -cam.Ly), cam.Ly);
@@ -89,7 +61,6 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
         T1[j] = j11 * V[4 + j] + j12 * V[8 + j];
     }
     // Sigma2D = sum_j s_j^2 m_j m_j^T, m_j = T R e_j
-    const float ss[3] = {s0 * s0, s1 * s1, s2 * s2};
     float m0[3], m1[3];
     float sxx = 0.f, sxy = 0.f, syy = 0.f;
 #pragma unroll
@@ -158,16 +129,91 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, DevCam cam, float 
     pv.col[k] = make_float4(col[0], col[1], col[2], ry);
 }
 
-cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
-                           int tiles_y, cudaStream_t st, uint32_t *status) {
-    if (sc.n == 0) return cudaSuccess;
+template <int S>
+__global__ void __launch_bounds__(256) k_project(DevScene sc, ProjViews views, float lowpass, float near_z,
+                                                 float alpha_min, uint32_t *__restrict__ status) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= sc.n) return;
+    const int n = sc.n, nv = views.nv;
+    const float px = sc.mean[k], py = sc.mean[n + k], pz = sc.mean[2 * n + k];
+    const float sigma = sc.opacity[k];
+    // a non-finite parameter makes the Gaussian invisible and raises the
+    // status bit; the rest of the view is unaffected (rotation and scales are
+    // checked below, once they are loaded for a Gaussian in front of a camera)
+    const bool finite = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(sigma);
+    if (!finite && status) atomicOr(status, GS2_ST_NONFINITE);
+    float tz[GS2_PROJ_VIEWS];
+    bool vis[GS2_PROJ_VIEWS], any = false;
+#pragma unroll
+    for (int v = 0; v < GS2_PROJ_VIEWS; ++v) {
+        vis[v] = false;
+        if (v < nv) {
+            const double d = view_depth(views.cam[v], px, py, pz);
+            tz[v] = (float)d;
+            views.pv[v].key[k] = __float_as_uint(tz[v]);
+            vis[v] = finite && (d >= (double)near_z) && (sigma >= alpha_min);
+            any = any || vis[v];
+        }
+    }
+    if (!any) {
+#pragma unroll
+        for (int v = 0; v < GS2_PROJ_VIEWS; ++v)
+            if (v < nv) write_invisible(views.pv[v], k);
+        return;
+    }
+    // every remaining parameter load first (independent, all in flight together)
+    float shc[3 * S];
+#pragma unroll
+    for (int i = 0; i < 3 * S; ++i) shc[i] = __ldcs(sc.sh + (size_t)i * n + k);
+    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
+    const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
+    if (!(isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(s0) && isfinite(s1) &&
+          isfinite(s2))) {
+        if (status) atomicOr(status, GS2_ST_NONFINITE);
+#pragma unroll
+        for (int v = 0; v < GS2_PROJ_VIEWS; ++v)
+            if (v < nv) write_invisible(views.pv[v], k);
+        return;
+    }
+    // rotation from the normalised quaternion (shared by the views)
+    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+    float R[3][3];
+    R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
+    R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
+    R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+    const float ss[3] = {s0 * s0, s1 * s1, s2 * s2};
+#pragma unroll
+    for (int v = 0; v < GS2_PROJ_VIEWS; ++v) {
+        if (v >= nv) break;
+        if (vis[v])
+            project_one<S>(views.cam[v], views.pv[v], k, px, py, pz, tz[v], sigma, R, ss, shc, lowpass, alpha_min);
+        else
+            write_invisible(views.pv[v], k);
+    }
+}
+
+cudaError_t launch_project_views(const DevScene &sc, const ProjViews &views, const gs2_config &cfg, cudaStream_t st,
+                                 uint32_t *status) {
+    if (sc.n == 0 || views.nv == 0) return cudaSuccess;
     const unsigned grid = (sc.n + 255) / 256;
     switch (sc.S) {
-    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
-    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
-    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
-    default: k_project<16><<<grid, 256, 0, st>>>(sc, cam, cfg.lowpass, cfg.near_z, cfg.alpha_min, pv, tiles_x, tiles_y, status); break;
+    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
+    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
+    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
+    default: k_project<16><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
     }
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_config &cfg, ProjView pv, int tiles_x,
+                           int tiles_y, cudaStream_t st, uint32_t *status) {
+    (void)tiles_x;
+    (void)tiles_y;
+    ProjViews views;
+    views.nv = 1;
+    views.cam[0] = cam;
+    views.pv[0] = pv;
+    return launch_project_views(sc, views, cfg, st, status);
 }

@@ -228,17 +228,32 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         s_off[t] = base + ghist[t * nb + blockIdx.x];
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
+    // the next tile's keys and values are loaded while this one is ranked and written
+    uint32_t nkey[ROWS], nval[ROWS];
+    auto load_tile = [&](uint32_t b0) {
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const uint32_t idx = b0 + (uint32_t)(w * (32 * ROWS) + r * 32 + lane);
+            nkey[r] = idx < end ? kin[idx] : 0u;
+            nval[r] = idx < end ? vin[idx] : 0u;
+        }
+    };
+    load_tile(beg);
     for (uint32_t base = beg; base < end; base += SORT_TILE) {
+        uint32_t key[ROWS], val[ROWS], dig[ROWS], pos[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            key[r] = nkey[r];
+            val[r] = nval[r];
+        }
+        if (base + SORT_TILE < end) load_tile(base + SORT_TILE);
 #pragma unroll
         for (int i = 0; i < SORT_THREADS / 32; ++i) s_wc[i][t] = 0u;
         __syncthreads();
-        uint32_t key[ROWS], val[ROWS], dig[ROWS], pos[ROWS];
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             const uint32_t idx = base + (uint32_t)(w * (32 * ROWS) + r * 32 + lane);
             const bool valid = idx < end;
-            key[r] = valid ? kin[idx] : 0u;
-            val[r] = valid ? vin[idx] : 0u;
             dig[r] = valid ? ((key[r] >> shift) & 255u) : 256u;
             // lanes with the same 9-bit digit value, from one ballot per bit
             uint32_t peers = 0xFFFFFFFFu;
