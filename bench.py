@@ -687,7 +687,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v4"
+KERNEL_REV = "accum-v5"
 
 
 def main():
