@@ -687,7 +687,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v5"
+KERNEL_REV = "accum-v6"
 
 
 def main():

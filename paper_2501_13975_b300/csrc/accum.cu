@@ -1,6 +1,6 @@
 // gs2_accum_newton_blocks (Eq. local_hessian_gradient, full Newton).
 //
-// Pass 1 (k_accum, one 16x16 CTA per tile, one thread per pixel): walk the
+// Pass 1 (k_accum, one 16x16 CTA per tile, one thread per two pixels): walk the
 // tile's depth-sorted list back to front (the order that yields the colour
 // behind each Gaussian, C_back, and its transmittance T_k = T_after/(1-alpha)).
 // For pixel c = C_front + T_k (alpha_k c~_k + (1 - alpha_k) C_back):
@@ -135,162 +135,217 @@ __device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], in
     }
 }
 
+// Pixels of thread t (GS2_ACC_THREADS = 128 per 16x16 tile): warp w covers
+// the 8x8 block ((w & 1) 8, (w >> 1) 8), lane l the pixels (l % 8, l / 8) and
+// (l % 8, l / 8 + 4) of it.  A Gaussian that reaches one 8x4 half of such a
+// block nearly always reaches the other, so one warp reduction serves both
+// pixels of a lane (the reduction, not the payload, is most of the cost).
+#define GS2_ACC_THREADS 128
+__device__ __forceinline__ int acc_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
+__device__ __forceinline__ int acc_py(int t) { return (t >> 6) * 8 + ((t >> 3) & 3); }
+
+// back-to-front state of one pixel
+struct PixState {
+    float T, cb0, cb1, cb2;
+    float e[3], h[3];
+    uint32_t last;
+    bool inside;
+};
+
+// One active (pixel, Gaussian) pair: adds the group's payload into pl and
+// steps the pixel's state past the Gaussian.
+template <int GROUP, int P>
+__device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, const float4 &B, const float4 &C,
+                                              float G, float alpha, float dx, float dy, bool clamped,
+                                              float (&pl)[P]) {
+    const float Tk = __fdiv_rn(ps.T, __fsub_rn(1.f, alpha));
+    const float w = alpha * Tk;
+    const float a0 = Tk * (C.x - ps.cb0), a1 = Tk * (C.y - ps.cb1), a2 = Tk * (C.z - ps.cb2);
+    const float *e = ps.e, *h = ps.h;
+    const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
+    const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
+    if (GROUP == GS2_OPACITY) {
+        if (!clamped) {
+            pl[0] += Ea * G;
+            pl[1] += Ah * G * G;
+        }
+    } else if (GROUP == GS2_COLOR) {
+        pl[0] += w * e[0];
+        pl[1] += w * e[1];
+        pl[2] += w * e[2];
+        pl[3] += w * w * h[0];
+        pl[4] += w * w * h[1];
+        pl[5] += w * w * h[2];
+    } else if (GROUP == GS2_ROT || GROUP == GS2_SCALE) {
+        if (!clamped) {
+            float gz[5], gzz[15];
+            falloff_derivs<false>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
+            const float sg = B.y;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pl[i] += Ea * sg * gz[2 + i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int jx = i; jx < 3; ++jx)
+                    pl[3 + ut3(i, jx)] += Ah * sg * sg * gz[2 + i] * gz[2 + jx] + Ea * sg * gzz[ut5(2 + i, 2 + jx)];
+        }
+    } else {  // position
+        const float aa[3] = {a0, a1, a2};
+        if (!clamped) {
+            float gz[5], gzz[15];
+            falloff_derivs<true>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
+            const float sg = B.y;
+            float az[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) az[i] = sg * gz[i];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) pl[i] += Ea * az[i];
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int jx = i; jx < 5; ++jx) pl[5 + ut5(i, jx)] += Ah * az[i] * az[jx] + Ea * sg * gzz[ut5(i, jx)];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float xc = h[c] * aa[c] * w + e[c] * Tk;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) pl[20 + c * 5 + i] += xc * az[i];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pl[35 + c] += w * e[c];
+            pl[38 + c] += w * w * h[c];
+        }
+    }
+    ps.cb0 = alpha * C.x + (1.f - alpha) * ps.cb0;
+    ps.cb1 = alpha * C.y + (1.f - alpha) * ps.cb1;
+    ps.cb2 = alpha * C.z + (1.f - alpha) * ps.cb2;
+    ps.T = Tk;
+}
+
 template <int GROUP, typename ACC>
-__global__ void __launch_bounds__(GS2_TILE_PIX) k_accum(const uint2 *__restrict__ ranges,
-                                                        const uint32_t *__restrict__ ids, ProjView pv, RasterView rv,
-                                                        const float *__restrict__ E, const float *__restrict__ Hh,
-                                                        int W, int H, int tiles_x, float amin, float amax,
-                                                        ACC *__restrict__ zbuf, int n,
-                                                        unsigned long long *__restrict__ active_stat) {
+__global__ void __launch_bounds__(GS2_ACC_THREADS) k_accum(const uint2 *__restrict__ ranges,
+                                                           const uint32_t *__restrict__ ids, ProjView pv,
+                                                           RasterView rv, const float *__restrict__ E,
+                                                           const float *__restrict__ Hh, int W, int H, int tiles_x,
+                                                           float amin, float amax, ACC *__restrict__ zbuf, int n,
+                                                           unsigned long long *__restrict__ active_stat) {
     constexpr int P = Payload<GROUP>::P;
+    constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
+    constexpr int PER = NB / GS2_ACC_THREADS;        // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
-    __shared__ uint32_t sId[2][GS2_TILE_PIX];
-    __shared__ float4 sA[2][GS2_TILE_PIX], sB[2][GS2_TILE_PIX], sC[2][GS2_TILE_PIX];
+    __shared__ uint32_t sId[2][NB];
+    __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
     const int t = threadIdx.x, lane = t & 31;
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
-    const int px = blockIdx.x * GS2_TILE + gs2_tile_px(t), py = blockIdx.y * GS2_TILE + gs2_tile_py(t);
-    const bool inside = px < W && py < H;
-    const size_t PI = (size_t)W * H, pp = (size_t)py * W + px;
-    uint32_t last = 0u;
-    float T = 1.f, e[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
-    if (inside) {
-        last = rv.last[pp];
-        T = rv.tfinal[pp];
+    const int px = blockIdx.x * GS2_TILE + acc_px(t), py = blockIdx.y * GS2_TILE + acc_py(t);
+    const size_t PI = (size_t)W * H;
+    PixState ps[2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            e[c] = E[c * PI + pp];
-            h[c] = Hh[c * PI + pp];
+    for (int q = 0; q < 2; ++q) {
+        const int y = py + 4 * q;
+        PixState &s = ps[q];
+        s.inside = px < W && y < H;
+        s.last = 0u;
+        s.T = 1.f;
+        s.cb0 = s.cb1 = s.cb2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s.e[c] = s.h[c] = 0.f;
+        if (s.inside) {
+            const size_t pp = (size_t)y * W + px;
+            s.last = rv.last[pp];
+            s.T = rv.tfinal[pp];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                s.e[c] = E[c * PI + pp];
+                s.h[c] = Hh[c * PI + pp];
+            }
         }
     }
+    const uint32_t last2 = max(ps[0].last, ps[1].last);
     if (t == 0) sMax = 0u;
     __syncthreads();
-    atomicMax(&sMax, last);
+    atomicMax(&sMax, last2);
     __syncthreads();
     const int maxlast = (int)sMax;
     // this warp's own end of list: its lanes have nothing to do beyond it
-    const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last);
+    const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last2);
     const uint2 r = ranges[tile];
-    const float fx = (float)px, fy = (float)py;
-    float cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+    const float fx = (float)px, fy0 = (float)py, fy1 = (float)(py + 4);
     uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
-    // batches back to front: batch b covers [max(0, maxlast - 256 (b + 1)), maxlast - 256 b)
-    const int nbat = (maxlast + GS2_TILE_PIX - 1) / GS2_TILE_PIX;
-    auto list_index = [&](int b) { return maxlast - GS2_TILE_PIX * (b + 1) + t; };   // this thread's entry
-    auto issue = [&](int b, uint32_t k) {
+    // batches back to front: batch b covers [max(0, maxlast - NB (b + 1)), maxlast - NB b)
+    const int nbat = (maxlast + NB - 1) / NB;
+    auto list_index = [&](int b, int i) { return maxlast - NB * (b + 1) + t + i * GS2_ACC_THREADS; };
+    uint32_t knext[PER];
+    auto fetch = [&](int b) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int li = list_index(b, i);
+            knext[i] = li >= 0 ? ids[r.x + li] : 0u;
+        }
+    };
+    auto issue = [&](int b) {
         const int buf = b & 1;
-        if (list_index(b) >= 0) {
-            sId[buf][t] = k;
-            cp_async16(&sA[buf][t], &pv.recA[k]);
-            cp_async16(&sB[buf][t], &pv.recB[k]);
-            cp_async16(&sC[buf][t], &pv.col[k]);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int j = t + i * GS2_ACC_THREADS;
+            if (list_index(b, i) >= 0) {
+                const uint32_t k = knext[i];
+                sId[buf][j] = k;
+                cp_async16(&sA[buf][j], &pv.recA[k]);
+                cp_async16(&sB[buf][j], &pv.recB[k]);
+                cp_async16(&sC[buf][j], &pv.col[k]);
+            }
         }
         cp_async_commit();
     };
-    uint32_t knext = 0u;
     if (nbat > 0) {
-        if (list_index(0) >= 0) knext = ids[r.x + list_index(0)];
-        issue(0, knext);
-        if (nbat > 1 && list_index(1) >= 0) knext = ids[r.x + list_index(1)];
+        fetch(0);
+        issue(0);
+        if (nbat > 1) fetch(1);
     }
     for (int b = 0; b < nbat; ++b) {
         cp_async_wait_all();
         __syncthreads();   // batch b visible to all; everyone is done with batch b - 1's buffer
         if (b + 1 < nbat) {
-            issue(b + 1, knext);
-            if (b + 2 < nbat && list_index(b + 2) >= 0) knext = ids[r.x + list_index(b + 2)];
+            issue(b + 1);
+            if (b + 2 < nbat) fetch(b + 2);
         }
         const int buf = b & 1;
-        const int bend = maxlast - GS2_TILE_PIX * b, bbeg = max(0, bend - GS2_TILE_PIX);
-        const int base = bend - GS2_TILE_PIX;   // list index of slot 0 of this batch (may be negative)
+        const int bend = maxlast - NB * b, bbeg = max(0, bend - NB);
+        const int base = bend - NB;   // list index of slot 0 of this batch (may be negative)
         for (int jj = min(bend, wlast) - 1; jj >= bbeg; --jj) {
             const int s = jj - base;
             const float4 A = sA[buf][s], B = sB[buf][s];
-            bool act = inside && (uint32_t)jj < last;
-            float G = 0.f, alpha = 0.f, dx = 0.f, dy = 0.f;
-            bool clamped = false;
-            if (act) {
-                dx = __fsub_rn(fx, A.x);
-                dy = __fsub_rn(fy, A.y);
-                G = gs2_gauss(A.z, A.w, B.x, dx, dy);
-                const float araw = __fmul_rn(B.y, G);
-                clamped = araw > amax;
-                alpha = fminf(araw, amax);
-                if (alpha < amin) act = false;
+            const float dx = __fsub_rn(fx, A.x);
+            bool act[2], clamped[2];
+            float G[2], alpha[2], dy[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                act[q] = ps[q].inside && (uint32_t)jj < ps[q].last;
+                G[q] = 0.f;
+                alpha[q] = 0.f;
+                dy[q] = 0.f;
+                clamped[q] = false;
+                if (act[q]) {
+                    dy[q] = __fsub_rn(q ? fy1 : fy0, A.y);
+                    G[q] = gs2_gauss(A.z, A.w, B.x, dx, dy[q]);
+                    const float araw = __fmul_rn(B.y, G[q]);
+                    clamped[q] = araw > amax;
+                    alpha[q] = fminf(araw, amax);
+                    if (alpha[q] < amin) act[q] = false;
+                }
             }
-            if (!__any_sync(0xFFFFFFFFu, act)) continue;
-            nact += act ? 1u : 0u;
+            if (!__any_sync(0xFFFFFFFFu, act[0] || act[1])) continue;
+            nact += (act[0] ? 1u : 0u) + (act[1] ? 1u : 0u);
             float pl[P];
 #pragma unroll
             for (int i = 0; i < P; ++i) pl[i] = 0.f;
-            if (act) {
-                const float4 C = sC[buf][s];
-                const float Tk = __fdiv_rn(T, __fsub_rn(1.f, alpha));
-                const float w = alpha * Tk;
-                const float a0 = Tk * (C.x - cb0), a1 = Tk * (C.y - cb1), a2 = Tk * (C.z - cb2);
-                const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
-                const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
-                if (GROUP == GS2_OPACITY) {
-                    if (!clamped) {
-                        pl[0] = Ea * G;
-                        pl[1] = Ah * G * G;
-                    }
-                } else if (GROUP == GS2_COLOR) {
-                    pl[0] = w * e[0];
-                    pl[1] = w * e[1];
-                    pl[2] = w * e[2];
-                    pl[3] = w * w * h[0];
-                    pl[4] = w * w * h[1];
-                    pl[5] = w * w * h[2];
-                } else if (GROUP == GS2_ROT || GROUP == GS2_SCALE) {
-                    if (!clamped) {
-                        float gz[5], gzz[15];
-                        falloff_derivs<false>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
-                        const float sg = B.y;
+            const float4 C = sC[buf][s];
 #pragma unroll
-                        for (int i = 0; i < 3; ++i) pl[i] = Ea * sg * gz[2 + i];
-#pragma unroll
-                        for (int i = 0; i < 3; ++i)
-#pragma unroll
-                            for (int jx = i; jx < 3; ++jx)
-                                pl[3 + ut3(i, jx)] =
-                                    Ah * sg * sg * gz[2 + i] * gz[2 + jx] + Ea * sg * gzz[ut5(2 + i, 2 + jx)];
-                    }
-                } else {  // position
-                    const float ee[3] = {e[0], e[1], e[2]}, hh[3] = {h[0], h[1], h[2]};
-                    const float aa[3] = {a0, a1, a2};
-                    if (!clamped) {
-                        float gz[5], gzz[15];
-                        falloff_derivs<true>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
-                        const float sg = B.y;
-                        float az[5];
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) az[i] = sg * gz[i];
-#pragma unroll
-                        for (int i = 0; i < 5; ++i) pl[i] = Ea * az[i];
-#pragma unroll
-                        for (int i = 0; i < 5; ++i)
-#pragma unroll
-                            for (int jx = i; jx < 5; ++jx)
-                                pl[5 + ut5(i, jx)] = Ah * az[i] * az[jx] + Ea * sg * gzz[ut5(i, jx)];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float xc = hh[c] * aa[c] * w + ee[c] * Tk;
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) pl[20 + c * 5 + i] = xc * az[i];
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        pl[35 + c] = w * ee[c];
-                        pl[38 + c] = w * w * hh[c];
-                    }
-                }
-                cb0 = alpha * C.x + (1.f - alpha) * cb0;
-                cb1 = alpha * C.y + (1.f - alpha) * cb1;
-                cb2 = alpha * C.z + (1.f - alpha) * cb2;
-                T = Tk;
-            }
+            for (int q = 0; q < 2; ++q)
+                if (act[q]) pixel_payload<GROUP, P>(ps[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], pl);
             warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
         }
     }
@@ -730,7 +785,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
     unsigned long long *act = pc->prof_on ? pc->d_stats + 4 * group + 3 : nullptr;
 #define ACC_LAUNCH(G)                                                                                             \
-    k_accum<G, ACC><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
+    k_accum<G, ACC><<<grid, GS2_ACC_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
                                                    view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n, act)
     switch (group) {
     case GS2_POS: ACC_LAUNCH(GS2_POS); break;
