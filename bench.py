@@ -236,34 +236,36 @@ def run_gpu(args, rank, world, local_rank):
     ctx.set_tuning(view_lanes=lanes_on)
     ctx.check()
 
-    # ---------------- end to end through the public API with host buffers
-    pinned = [t.cpu().pin_memory() for t in targets]
-    up = [torch.empty_like(targets[0]) for _ in range(1 + ctx.config["knn_k"])]
+    # ---------------- end to end through the public API with host buffers: the
+    # targets live in pinned host memory (HostTargets); each sweep's views are
+    # uploaded on a copy stream, the next sweep's while the current one runs.
+    # Every timed step's upload happens inside the timed region: none is
+    # prefetched before it starts or after it ends.
+    ht = gs2.HostTargets([t.cpu() for t in targets], knn)
     host_losses = torch.zeros(10, dtype=torch.float64).pin_memory()
     host_nfail = torch.zeros(1, dtype=torch.int32).pin_memory()
-    h2d = sum(u.numel() * 4 for u in up)
+    h2d = ht.bytes_for(0)
     d2h = host_losses.numel() * 8 + host_nfail.numel() * 4
 
-    def e2e_step(i):
+    def e2e_step(i, prefetch_next):
         t = i % ncam
-        views = [t] + [int(v) for v in knn[t] if v >= 0]
-        tg = list(targets)
-        for j, v in enumerate(views):
-            up[j].copy_(pinned[v], non_blocking=True)
-            tg[v] = up[j]
+        tg = ht.targets(t)
         ctx.sweep(scene, cams, tg, knn, t, losses, nfail)
+        ht.release(t)
+        if prefetch_next:
+            ht.prefetch((i + 1) % ncam)
         host_losses.copy_(losses, non_blocking=True)
         host_nfail.copy_(nfail, non_blocking=True)
 
     for i in range(args.warmup):
-        e2e_step(1000 + i)
+        e2e_step(1000 + i, i + 1 < args.warmup)
     torch.cuda.synchronize()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        e2e_step(1000 + args.warmup + i)
+        e2e_step(1000 + args.warmup + i, i + 1 < args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()

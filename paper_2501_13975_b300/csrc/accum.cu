@@ -135,15 +135,6 @@ __device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], in
     }
 }
 
-// Pixels of thread t (GS2_ACC_THREADS = 128 per 16x16 tile): warp w covers
-// the 8x8 block ((w & 1) 8, (w >> 1) 8), lane l the pixels (l % 8, l / 8) and
-// (l % 8, l / 8 + 4) of it.  A Gaussian that reaches one 8x4 half of such a
-// block nearly always reaches the other, so one warp reduction serves both
-// pixels of a lane (the reduction, not the payload, is most of the cost).
-#define GS2_ACC_THREADS 128
-__device__ __forceinline__ int acc_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
-__device__ __forceinline__ int acc_py(int t) { return (t >> 6) * 8 + ((t >> 3) & 3); }
-
 // back-to-front state of one pixel
 struct PixState {
     float T, cb0, cb1, cb2;
@@ -224,7 +215,7 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
 }
 
 template <int GROUP, typename ACC>
-__global__ void __launch_bounds__(GS2_ACC_THREADS) k_accum(const uint2 *__restrict__ ranges,
+__global__ void __launch_bounds__(GS2_PAIR_THREADS) k_accum(const uint2 *__restrict__ ranges,
                                                            const uint32_t *__restrict__ ids, ProjView pv,
                                                            RasterView rv, const float *__restrict__ E,
                                                            const float *__restrict__ Hh, int W, int H, int tiles_x,
@@ -232,14 +223,14 @@ __global__ void __launch_bounds__(GS2_ACC_THREADS) k_accum(const uint2 *__restri
                                                            unsigned long long *__restrict__ active_stat) {
     constexpr int P = Payload<GROUP>::P;
     constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
-    constexpr int PER = NB / GS2_ACC_THREADS;        // entries each thread stages
+    constexpr int PER = NB / GS2_PAIR_THREADS;        // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
     const int t = threadIdx.x, lane = t & 31;
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
-    const int px = blockIdx.x * GS2_TILE + acc_px(t), py = blockIdx.y * GS2_TILE + acc_py(t);
+    const int px = blockIdx.x * GS2_TILE + gs2_pair_px(t), py = blockIdx.y * GS2_TILE + gs2_pair_py(t);
     const size_t PI = (size_t)W * H;
     PixState ps[2];
 #pragma unroll
@@ -276,7 +267,7 @@ __global__ void __launch_bounds__(GS2_ACC_THREADS) k_accum(const uint2 *__restri
     uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
     // batches back to front: batch b covers [max(0, maxlast - NB (b + 1)), maxlast - NB b)
     const int nbat = (maxlast + NB - 1) / NB;
-    auto list_index = [&](int b, int i) { return maxlast - NB * (b + 1) + t + i * GS2_ACC_THREADS; };
+    auto list_index = [&](int b, int i) { return maxlast - NB * (b + 1) + t + i * GS2_PAIR_THREADS; };
     uint32_t knext[PER];
     auto fetch = [&](int b) {
 #pragma unroll
@@ -289,7 +280,7 @@ __global__ void __launch_bounds__(GS2_ACC_THREADS) k_accum(const uint2 *__restri
         const int buf = b & 1;
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            const int j = t + i * GS2_ACC_THREADS;
+            const int j = t + i * GS2_PAIR_THREADS;
             if (list_index(b, i) >= 0) {
                 const uint32_t k = knext[i];
                 sId[buf][j] = k;
@@ -785,7 +776,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
     unsigned long long *act = pc->prof_on ? pc->d_stats + 4 * group + 3 : nullptr;
 #define ACC_LAUNCH(G)                                                                                             \
-    k_accum<G, ACC><<<grid, GS2_ACC_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
+    k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
                                                    view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n, act)
     switch (group) {
     case GS2_POS: ACC_LAUNCH(GS2_POS); break;

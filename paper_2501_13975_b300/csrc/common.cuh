@@ -231,12 +231,23 @@ cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t 
 // the same alpha decisions bit for bit, so the Gaussian falloff is evaluated
 // with explicitly rounded operations (no compiler contraction choices).
 #ifdef __CUDACC__
-// Pixel of thread t in its 16x16 tile: warp w covers the 8x4 block
-// (w % 2, w / 2) of the tile, lane l its pixel (l % 8, l / 8) -- compact
-// warp blocks keep more of a warp's lanes inside a small Gaussian footprint
-// than 16x2 rows do.
+// Pixel of thread t in its 16x16 tile (compositing, 256 threads): warp w
+// covers the 8x4 block (w % 2, w / 2) of the tile, lane l its pixel
+// (l % 8, l / 8) -- compact warp blocks keep more of a warp's lanes inside a
+// small Gaussian footprint than 16x2 rows do.
 __device__ __forceinline__ int gs2_tile_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
 __device__ __forceinline__ int gs2_tile_py(int t) { return (t >> 6) * 4 + ((t >> 3) & 3); }
+
+// Two pixels per thread (accumulation, GS2_PAIR_THREADS = 128 per tile):
+// warp w covers the 8x8 block ((w & 1) 8, (w >> 1) 8), lane l the pixels
+// (l % 8, l / 8) and (l % 8, l / 8 + 4) of it.  One warp reduction serves
+// both pixels of a lane (a Gaussian that reaches one 8x4 half of such a
+// block nearly always reaches the other).  The compositing keeps one pixel
+// per thread: there a lane would run on until both of its pixels saturate
+// (measured slower).
+#define GS2_PAIR_THREADS 128
+__device__ __forceinline__ int gs2_pair_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
+__device__ __forceinline__ int gs2_pair_py(int t) { return (t >> 6) * 8 + ((t >> 3) & 3); }
 
 // asynchronous 16-byte global -> shared copies (the batch staging pipeline)
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {

@@ -547,6 +547,85 @@ class Batch:
                 raise GS2Error(f"scene {i}: {STATUS.get(st, st)}")
 
 
+class HostTargets:
+    """Sweep targets kept in pinned host memory and uploaded per sweep.
+
+    Only the images a sweep reads (its primary and KNN views) are copied, on
+    a copy stream, into one of two device buffer sets: the upload of the next
+    sweep's views (`prefetch`) runs while the current sweep computes.  A
+    buffer set is written again only after the sweep that read it has
+    finished on its compute stream (`release`).  Plumbing only: the copies
+    are plain host-to-device transfers.
+
+        ht = HostTargets(images, knn)
+        for i, t in enumerate(primaries):
+            tg = ht.targets(t)                 # device tensors for t's views
+            ctx.sweep(scene, cams, tg, knn, t)
+            ht.release(t)
+            if i + 1 < len(primaries):
+                ht.prefetch(primaries[i + 1])
+    """
+
+    def __init__(self, images, knn):
+        self.host = [im if im.is_pinned() else im.contiguous().pin_memory() for im in images]
+        self.knn = np.asarray(knn, np.int32).reshape(len(self.host), -1)
+        self.copy = torch.cuda.Stream()
+        self.sets = [[], []]
+        self.ready = [torch.cuda.Event(), torch.cuda.Event()]
+        self.free = [torch.cuda.Event(), torch.cuda.Event()]
+        self.used = [False, False]
+        self.next_set = 0
+        self.pending = {}
+
+    def views(self, t: int):
+        return [int(t)] + [int(v) for v in self.knn[t] if v >= 0]
+
+    def bytes_for(self, t: int) -> int:
+        return sum(self.host[v].numel() * self.host[v].element_size() for v in self.views(t))
+
+    def prefetch(self, t: int):
+        """Enqueue the upload of sweep t's views on the copy stream."""
+        t = int(t)
+        if t in self.pending:
+            return
+        s = self.next_set
+        self.next_set ^= 1
+        views = self.views(t)
+        bufs = self.sets[s]
+        while len(bufs) < len(views):
+            bufs.append(None)
+        with torch.cuda.stream(self.copy):
+            if self.used[s]:
+                self.copy.wait_event(self.free[s])
+            for j, v in enumerate(views):
+                src = self.host[v]
+                if bufs[j] is None or bufs[j].shape != src.shape or bufs[j].dtype != src.dtype:
+                    bufs[j] = torch.empty(src.shape, dtype=src.dtype, device="cuda")
+                bufs[j].copy_(src, non_blocking=True)
+            self.ready[s].record(self.copy)
+        self.pending[t] = s
+
+    def targets(self, t: int, stream=None):
+        """Target list for sweep t: device tensors at its views, None
+        elsewhere (a sweep reads no other entry); `stream` (default: the
+        current one) waits for the upload."""
+        t = int(t)
+        self.prefetch(t)
+        s = self.pending[t]
+        (stream or torch.cuda.current_stream()).wait_event(self.ready[s])
+        tg = [None] * len(self.host)
+        for j, v in enumerate(self.views(t)):
+            tg[v] = self.sets[s][j]
+        return tg
+
+    def release(self, t: int, stream=None):
+        """Mark sweep t's buffer set free once the work enqueued so far on
+        `stream` (its sweep) has run."""
+        s = self.pending.pop(int(t))
+        self.free[s].record(stream or torch.cuda.current_stream())
+        self.used[s] = True
+
+
 def _mlp_call(st, what):
     if st != 0:
         raise GS2Error(f"{what}: {STATUS.get(st, st)}")
