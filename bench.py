@@ -310,6 +310,29 @@ def run_gpu(args, rank, world, local_rank):
                                f"({ms_serial / args.steps:.2f} ms/sweep; the timed sweeps run them concurrently)",
                 "pairs_per_sweep": int(prof["pairs"].sum()) // max(args.steps, 1),
                 "visible_per_binning": int(prof["visible"].sum()) // max(int(prof["binnings"].sum()), 1)}
+    # ---------------- the other stages, reported separately (same serial pass):
+    # algorithmic bytes per sweep against the measured HBM peak
+    binn = prof["binnings"].astype(np.float64)
+    pairs = float(prof["pairs"].sum())
+    pixels = float(prof["pixels"].sum())
+    depth_sorts = float(binn[0] + binn[1])   # the position and rotation passes sort by depth
+    stage_bytes = {
+        # emit 8 B, two tile radix passes (4 B histogram read + 8 B read + 8 B written), ranges 4 B per
+        # pair; four depth radix passes of 20 B per Gaussian; tiles-touched gather and offsets 12 B
+        "binning": pairs * (8 + 2 * 20 + 4) + depth_sorts * w["n"] * 4 * 20 + float(binn.sum()) * w["n"] * 12,
+        # per pixel 12 B image + 8 B state written; per listed pair 4 B id + 48 B staged record
+        "compositing": pixels * 20 + pairs * 52,
+        # per pixel c, target read (24 B), e, h written (24 B)
+        "loss": pixels * 48,
+    }
+    stages = {}
+    for k, b in stage_bytes.items():
+        t_ms = float(prof["stage_ms"][k])
+        gbs = b / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+        stages[k] = {"ms_per_sweep": round(t_ms / max(args.steps, 1), 3), "launch_groups": prof["stage_count"][k],
+                     "algorithmic_bytes_per_sweep": round(b / max(args.steps, 1)),
+                     "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+                     "share_of_step": round(t_ms / ms_serial, 4) if ms_serial > 0 else None}
     value = world * args.steps / (ms * 1e-3)
     result = {
         "metric": "Newton sweeps/s (1 primary + 3 secondaries, 5 attribute groups)",
@@ -325,6 +348,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": round(world * args.steps / (ms_e2e * 1e-3), 4), "unit": "sweeps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline,
+        "stages": stages,
         "gpu_launches": int(launches),
         "tuning": tuning,
         "clocks": clk,

@@ -376,17 +376,25 @@ gs2_status gs2_batch_sweep(gs2_batch *batch, gs2_scene *scenes, const gs2_camera
 /* Instrumentation.
  * gs2_launch_count: kernels launched by this library in this process so far.
  * gs2_profile(ctx, 1): from now on record CUDA events around every
- *   accumulation kernel launch (bounded pool of 512) and count, per group slot
- *   of gs2_sweep, the (tile, Gaussian) pairs, visible Gaussians, binnings and
- *   pixels (device-side counters, no host synchronisation); resets totals.
- *   gs2_profile(ctx, 0) stops.  Synchronises the device.
+ *   accumulation kernel launch and around every binning (depth and tile
+ *   sort), compositing and loss-derivative stage (one bounded pool of 2048
+ *   event pairs), and count, per group slot of gs2_sweep, the (tile,
+ *   Gaussian) pairs, visible Gaussians, binnings and pixels (device-side
+ *   counters, no host synchronisation); resets totals.  gs2_profile(ctx, 0)
+ *   stops.  Synchronises the device.  Event durations of views that run
+ *   concurrently overlap: time with tuning.view_lanes = 0 for per-stage
+ *   figures.
  * gs2_profile_read: per group (host arrays [5], stats [5][5]: pairs, visible
  *   Gaussians, binnings, pixels, accumulation evaluations = (pixel, Gaussian)
  *   pairs with alpha >= alpha_min that the accumulation processed) after
- *   synchronising the device. */
+ *   synchronising the device.
+ * gs2_profile_read_stages: host arrays [3] (binning, compositing, loss
+ *   derivatives): summed event milliseconds and the number of timed stages,
+ *   after synchronising the device. */
 uint64_t gs2_launch_count(void);
 gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable);
 gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launches, uint64_t *stats);
+gs2_status gs2_profile_read_stages(gs2_ctx *ctx, double *ms_out, int64_t *count_out);
 
 /* No-allocation render (the paper has no counterpart; this serves callers).
  * Some callers cannot call cudaMalloc: a plugin or callback run by a host

@@ -819,7 +819,7 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
     dim3 grid(ctx->tiles_x, ctx->tiles_y);
     const uint32_t *ids = ctx->vals[ctx->sorted];
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool (shared by a sweep's view lanes)
-    const bool prof = pc->prof_on && pc->prof_n < 512;
+    const bool prof = pc->prof_on && pc->prof_n < GS2_PROF_POOL;
     if (prof) {
         cudaEventRecord(pc->prof_ev[2 * pc->prof_n], st);
         pc->prof_group[pc->prof_n] = group;

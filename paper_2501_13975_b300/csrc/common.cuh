@@ -13,6 +13,11 @@
 
 #define GS2_TILE 16                  // screen tile edge in pixels
 #define GS2_SORT_BLOCKS_MAX 1024     // the per-digit scan runs one 1024-thread CTA per digit
+// profiling pool (event pairs) and the stage tags beside the accumulation groups
+#define GS2_PROF_POOL 2048
+#define GS2_PROF_BIN 5
+#define GS2_PROF_RASTER 6
+#define GS2_PROF_LOSS 7
 #define GS2_MAX_LANES 16             // concurrent views per group in a sweep (secondaries)
 #define GS2_TILE_PIX (GS2_TILE * GS2_TILE)
 #define GS2_ZPOS 41                  // image-space payload of the position group
@@ -159,9 +164,9 @@ struct gs2_ctx {
     // opt-in profile of the accumulation kernel: CUDA events around every launch
     // and per-group pair / visible-Gaussian totals counted on the device
     int prof_on;
-    int prof_n;                  // events used in the pool
-    cudaEvent_t prof_ev[2 * 512];
-    int prof_group[512];
+    int prof_n;                  // event pairs used in the pool
+    cudaEvent_t prof_ev[2 * GS2_PROF_POOL];
+    int prof_group[GS2_PROF_POOL];   // 0..4: accumulation of that group; GS2_PROF_BIN/RASTER/LOSS: stages
     unsigned long long *d_stats; // [5][4]: pairs, visible Gaussians, binnings, accumulation evaluations
     int stat_slot;               // group slot the binning statistics go to
     unsigned long long h_pixels[5];
@@ -212,6 +217,10 @@ cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const 
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);
 cudaError_t prepare_loss_kernels();
+// profiling: an event pair around a stage's launches on stream st (no-ops
+// unless profiling is on and the pool has room); returns the pair index or -1
+int prof_begin(gs2_ctx *ctx, int tag, cudaStream_t st);
+void prof_end(gs2_ctx *ctx, int idx, cudaStream_t st);
 // one sweep on ctx (gs2_sweep / gs2_sweep_logged; records may be NULL)
 gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                      const float *const *targets, const int32_t *knn, int32_t t, float *records, double *losses_out,

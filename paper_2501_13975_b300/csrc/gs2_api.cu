@@ -124,7 +124,7 @@ static void free_ctx(gs2_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
-        for (int i = 0; i < 2 * 512; ++i)
+        for (int i = 0; i < 2 * GS2_PROF_POOL; ++i)
             if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
 }
 
@@ -343,11 +343,15 @@ static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const vo
     ctx->tiles_y = (cam->height + GS2_TILE - 1) / GS2_TILE;
     ProjView pv = proj_view(const_cast<void *>(proj), n);
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // statistics (shared by a sweep's view lanes)
+    int pe = prof_begin(ctx, GS2_PROF_BIN, st);
     RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st,
                                   pc->prof_on ? pc->d_stats + 4 * pc->stat_slot : nullptr, order_in, order_out));
+    prof_end(ctx, pe, st);
     if (pc->prof_on) pc->h_pixels[pc->stat_slot] += (unsigned long long)cam->width * cam->height;
+    pe = prof_begin(ctx, GS2_PROF_RASTER, st);
     RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image,
                                 raster_view(rstate, cam->width, cam->height), st));
+    prof_end(ctx, pe, st);
     return GS2_OK;
 }
 
@@ -376,8 +380,10 @@ static gs2_status do_accum(gs2_ctx *ctx, int group, const gs2_scene *scene, cons
                            const gs2_camera *primary, const void *proj, const void *rstate, const float *image,
                            const float *target, int slot, void *blocks, double *loss_out, cudaStream_t st,
                            bool keep_primary = true) {
+    const int pe = prof_begin(ctx, GS2_PROF_LOSS, st);
     RET_CUDA(ctx, launch_loss(image, target, view->width, view->height, ctx->cfg, ctx->pix_e, ctx->pix_h, loss_out,
                               st, ctx->d_status));
+    prof_end(ctx, pe, st);
     RET_CUDA(ctx, launch_accum(ctx, group, make_devscene(scene), make_devcam(view), make_devcam(primary),
                                proj_view(const_cast<void *>(proj), scene->n),
                                raster_view(const_cast<void *>(rstate), view->width, view->height), ctx->cfg, slot,
@@ -686,7 +692,7 @@ extern "C" uint64_t gs2_launch_count(void) { return g_gs2_launches.load(); }
 extern "C" gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable) {
     if (!ctx) return GS2_ERR_ARG;
     if (enable && !ctx->prof_ev[0])
-        for (int i = 0; i < 2 * 512; ++i) RET_CUDA(ctx, cudaEventCreate(&ctx->prof_ev[i]));
+        for (int i = 0; i < 2 * GS2_PROF_POOL; ++i) RET_CUDA(ctx, cudaEventCreate(&ctx->prof_ev[i]));
     RET_CUDA(ctx, cudaDeviceSynchronize());
     ctx->prof_on = enable ? 1 : 0;
     ctx->prof_n = 0;
@@ -704,6 +710,7 @@ extern "C" gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *
         accum_launches[g] = 0;
     }
     for (int i = 0; i < ctx->prof_n; ++i) {
+        if (ctx->prof_group[i] >= 5) continue;   // a stage, not an accumulation
         float ms = 0.f;
         RET_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
         accum_ms[ctx->prof_group[i]] += ms;
@@ -719,6 +726,39 @@ extern "C" gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *
         stats[5 * g + 4] = h[4 * g + 3];
     }
     return GS2_OK;
+}
+
+extern "C" gs2_status gs2_profile_read_stages(gs2_ctx *ctx, double *ms_out, int64_t *count_out) {
+    if (!ctx || !ms_out || !count_out) return GS2_ERR_ARG;
+    RET_CUDA(ctx, cudaDeviceSynchronize());
+    for (int k = 0; k < 3; ++k) {
+        ms_out[k] = 0.0;
+        count_out[k] = 0;
+    }
+    for (int i = 0; i < ctx->prof_n; ++i) {
+        const int k = ctx->prof_group[i] - GS2_PROF_BIN;
+        if (k < 0 || k > 2) continue;
+        float ms = 0.f;
+        RET_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        ms_out[k] += ms;
+        count_out[k] += 1;
+    }
+    return GS2_OK;
+}
+
+int prof_begin(gs2_ctx *ctx, int tag, cudaStream_t st) {
+    gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;
+    if (!pc->prof_on || pc->prof_n >= GS2_PROF_POOL) return -1;
+    const int i = pc->prof_n++;
+    pc->prof_group[i] = tag;
+    cudaEventRecord(pc->prof_ev[2 * i], st);
+    return i;
+}
+
+void prof_end(gs2_ctx *ctx, int idx, cudaStream_t st) {
+    if (idx < 0) return;
+    gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;
+    cudaEventRecord(pc->prof_ev[2 * idx + 1], st);
 }
 
 // ------------------------------------------------------------------ introspection

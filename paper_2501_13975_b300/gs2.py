@@ -112,6 +112,7 @@ _sigs = {
     "gs2_launch_count": (C.c_uint64, []),
     "gs2_profile": (C.c_int, [_vp, C.c_int32]),
     "gs2_profile_read": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "gs2_profile_read_stages": (C.c_int, [_vp, _vp, _vp]),
     "gs2_render_noalloc": (C.c_int, [C.POINTER(Config_), C.POINTER(Scene_), C.POINTER(Camera_), _vp, _vp, _vp,
                                      _vp, _vp]),
     "gs2_debug_tiles": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
@@ -423,8 +424,14 @@ class Context:
         stats = np.zeros((5, 5), np.uint64)
         self._ok(_lib.gs2_profile_read(self.h, ms.ctypes.data_as(_vp), cnt.ctypes.data_as(_vp),
                                        stats.ctypes.data_as(_vp)), "gs2_profile_read")
+        sms = np.zeros(3, np.float64)
+        scnt = np.zeros(3, np.int64)
+        self._ok(_lib.gs2_profile_read_stages(self.h, sms.ctypes.data_as(_vp), scnt.ctypes.data_as(_vp)),
+                 "gs2_profile_read_stages")
         return dict(accum_ms=ms, accum_launches=cnt, pairs=stats[:, 0], visible=stats[:, 1],
-                    binnings=stats[:, 2], pixels=stats[:, 3], evaluations=stats[:, 4])
+                    binnings=stats[:, 2], pixels=stats[:, 3], evaluations=stats[:, 4],
+                    stage_ms=dict(binning=sms[0], compositing=sms[1], loss=sms[2]),
+                    stage_count=dict(binning=int(scnt[0]), compositing=int(scnt[1]), loss=int(scnt[2])))
 
     def debug_tiles(self, w, h, capacity, stream=None):
         tx, ty = (w + 15) // 16, (h + 15) // 16
