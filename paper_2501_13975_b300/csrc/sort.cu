@@ -9,7 +9,8 @@
 //             context capacity (overflow sets a status bit);
 //  3. emit    pairs (tile id, Gaussian id) in rank order, one CTA per 256 ranks;
 //  4. tiles   stable LSD radix sort of the pairs by tile id (ceil(tile bits/8)
-//             passes, 2 at 1600x1040) -- stability keeps rank order per tile;
+//             passes of equal width, 2 of 7 and 6 bits at 1600x1040) --
+//             stability keeps rank order per tile;
 //  5. ranges  [start, end) of every tile in the sorted list.
 // Result: total order (tile, depth key, Gaussian index), bit-exact.  Each
 // radix pass = block histograms over a fixed grid of NB CTAs (each owning a
@@ -155,13 +156,13 @@ __device__ __forceinline__ void chunk_of(uint32_t M, int nb, int b, uint32_t &be
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) k_hist(const uint32_t *__restrict__ keys, const uint32_t *count,
-                                                       int shift, uint32_t *ghist, int nb) {
+                                                       int shift, uint32_t mask, uint32_t *ghist, int nb) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0u;
     __syncthreads();
     uint32_t beg, end;
     chunk_of(*count, nb, blockIdx.x, beg, end);
-    for (uint32_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    for (uint32_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
     __syncthreads();
     ghist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
@@ -211,7 +212,7 @@ template <int ROWS>
 __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
                                                           uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                          const uint32_t *count, int shift,
+                                                          const uint32_t *count, int shift, uint32_t mask,
                                                           const uint32_t *ghist, int nb, const uint32_t *dtot) {
     constexpr int SORT_TILE = SORT_THREADS * ROWS;
     __shared__ uint32_t s_off[256];
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         for (int r = 0; r < ROWS; ++r) {
             const uint32_t idx = base + (uint32_t)(w * (32 * ROWS) + r * 32 + lane);
             const bool valid = idx < end;
-            dig[r] = valid ? ((key[r] >> shift) & 255u) : 256u;
+            dig[r] = valid ? ((key[r] >> shift) & mask) : 256u;
             // lanes with the same 9-bit digit value, from one ballot per bit
             uint32_t peers = 0xFFFFFFFFu;
 #pragma unroll
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         __syncthreads();
         // ... then consecutive threads write consecutive positions of each digit's run
         for (uint32_t i = t; i < tile_n; i += SORT_THREADS) {
-            const uint32_t kk = s_k[i], d = (kk >> shift) & 255u;
+            const uint32_t kk = s_k[i], d = (kk >> shift) & mask;
             const uint32_t dst = s_off[d] + (i - s_lb[d]);
             kout[dst] = kk;
             vout[dst] = s_v[i];
@@ -306,25 +307,30 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
 }
 
 // `bits` significant key bits, ping-pong between (k[0], v[0]) and (k[1], v[1]);
-// returns the index of the buffer holding the result
+// returns the index of the buffer holding the result.  The passes split the
+// bits evenly (13 tile bits: 7 + 6, not 8 + 5): a digit of fewer values
+// leaves longer runs of equal digits in each radix tile, so the scatter's
+// stores cover fewer memory segments.
 static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int bits, uint32_t *ghist, int nb,
                       int rows, cudaStream_t st, int *launches) {
     uint32_t *dtot = ghist + 256 * nb;
     int cur = 0;
     const int passes = (bits + 7) / 8;
+    const int width = (bits + passes - 1) / passes;
+    const uint32_t mask = (1u << width) - 1u;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_hist<<<nb, SORT_THREADS, 0, st>>>(k[cur], count, shift, ghist, nb);
+        const int shift = width * p;
+        k_hist<<<nb, SORT_THREADS, 0, st>>>(k[cur], count, shift, mask, ghist, nb);
         k_digit_scan<<<256, 1024, 0, st>>>(ghist, nb, dtot);
         if (rows == 2)
-            k_scatter<2><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist,
-                                                      nb, dtot);
+            k_scatter<2><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
+                                                      ghist, nb, dtot);
         else if (rows == 8)
-            k_scatter<8><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist,
-                                                      nb, dtot);
+            k_scatter<8><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
+                                                      ghist, nb, dtot);
         else
-            k_scatter<4><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, ghist,
-                                                      nb, dtot);
+            k_scatter<4><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
+                                                      ghist, nb, dtot);
         cur ^= 1;
     }
     *launches += 3 * passes;
