@@ -566,6 +566,40 @@ def time_to_psnr(args):
         ctx.check()
         return dict(psnr=curve, ms=ms_curve, reached=reached, sweeps=len(curve) - 1)
 
+    def first_sweep_ms(precision, use_model, reps=5):
+        """Median device time of the first sweep from the workload's start,
+        each repetition from a fresh copy of it: the cost of the network's
+        inference and of the precision policy on one scene state (the runs
+        above move through different states, so their per-sweep times also
+        reflect how far each has diverged)."""
+        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision))
+        gt = gs2.DeviceScene.from_host(gt_host)
+        proj = ctx.proj_buffer(w["n"])
+        targets = []
+        for c in cams:
+            ctx.project(gt, c, proj)
+            img, _ = ctx.raster_fwd(gt, c, proj)
+            targets.append(img.clone())
+        del gt
+        centres = np.stack([c.center() for c in cams]).astype(np.float32)
+        sphere = ctx.bounding_sphere(gs2.DeviceScene.from_host(spec_host)).cpu().numpy()
+        knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
+        if use_model:
+            ctx.set_step_model(model.w)
+        times = []
+        for _ in range(reps + 1):
+            scene = gs2.DeviceScene.from_host(spec_host)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.sweep(scene, cams, targets, knn, int(order[0]))
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ctx.check()
+        return round(float(np.median(times[1:])), 3)
+
     def summary(r):
         k = r["reached"] if r["reached"] is not None else r["sweeps"]
         return {"sweeps_to_target": r["reached"], "seconds_to_target": round(r["ms"][k] * 1e-3, 5)
@@ -593,10 +627,14 @@ def time_to_psnr(args):
             "psnr_curves": {k: [round(x, 3) for x in r["psnr"]] for k, r in runs.items()},
         }
     head = starts["workload"]
+    first = {name: first_sweep_ms(prec, use) for name, prec, use in
+             (("plain_fp32", 0, False), ("learned_fp32", 0, True), ("plain_mixed", 1, False),
+              ("learned_mixed", 1, True))}
     result = {
         "metric": "time to PSNR vs plain FP32 path (object workload)",
         "value": head["learned_mixed_seconds"], "unit": "s", "higher_is_better": False,
         "starts": starts,
+        "first_sweep_ms": first,
         "network": {"objective": args.ttp_objective, "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell,
                     "records": tiny.n + shell.n,
                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
