@@ -212,6 +212,15 @@ def test_blocks_parity_primary(gs2, group, lam):
     _check_blocks(r)
 
 
+@pytest.mark.parametrize("group", [0, 3, 4])
+def test_blocks_parity_ragged_tiles(gs2, group):
+    """90x90 view: the last tile row and column are ragged (10 of 16), so
+    some accumulation threads have their first pixel inside and their second
+    (four rows below) outside, and some have both outside."""
+    r = _blocks_case(gs2, group, sh=(1 if group == O.COLOR else 0), lam=0.2, n=700, size=90)
+    _check_blocks(r)
+
+
 @pytest.mark.parametrize("group", [0, 1, 2, 4])
 def test_blocks_parity_secondary_sh3(gs2, group):
     """Downsampled secondary view, primary-view axes, SH degree 3 colour path."""

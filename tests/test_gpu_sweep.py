@@ -59,6 +59,35 @@ def test_native_sweep_equals_call_sequence():
     assert torch.allclose(la, lb, rtol=1e-5, atol=0)
 
 
+@pytest.mark.parametrize("lanes", [0, 1])
+def test_profile_counts_every_stage(lanes):
+    """With profiling on, one sweep (4 views x 5 groups) times 20 binnings,
+    20 compositings, 20 loss passes and 20 accumulations, and its counters
+    match the views' pixels and the tile lists' pairs."""
+    from paper_2501_13975_b300 import gs2
+    sc, gt, cams = _scene_setup()
+    ctx = gs2.Context(sc.n, 64, 64, 0)
+    ocfg = oracle_cfg(ctx.config)
+    targets = [torch.tensor(O.render(gt, c, ocfg)["image"].astype(np.float32), device="cuda") for c in cams]
+    centres = np.stack([c.center() for c in cams]).astype(np.float32)
+    sphere = ctx.bounding_sphere(gs2.DeviceScene.from_host(sc)).cpu().numpy()
+    knn = gs2.camera_knn(centres, sphere, 3)
+    ctx.set_tuning(view_lanes=lanes)
+    a = gs2.DeviceScene.from_host(sc)
+    ctx.profile(True)
+    ctx.sweep(a, cams, targets, knn, 0)
+    p = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check()
+    assert p["stage_count"] == dict(binning=20, compositing=20, loss=20)
+    assert all(p["stage_ms"][k] > 0 for k in ("binning", "compositing", "loss"))
+    assert list(p["accum_launches"]) == [4, 4, 4, 4, 4]
+    assert np.all(p["accum_ms"] > 0)
+    assert list(p["binnings"]) == [4, 4, 4, 4, 4]
+    assert list(p["pixels"]) == [64 * 64 + 3 * 32 * 32] * 5
+    assert np.all(p["pairs"] > 0) and np.all(p["evaluations"] > 0)
+
+
 def test_sweep_parity_with_oracle():
     """One full sweep on the GPU vs the oracle's sweep (FP64 state throughout):
     the primary loss seen by each group agrees to 1e-3 and the parameters move
