@@ -185,18 +185,38 @@ def run_gpu(args, rank, world, local_rank):
     nfail = torch.zeros(1, dtype=torch.int32, device=dev)
     tuning = ctx.autotune(scene, cams, targets, knn, 0, reps=2) if not args.no_autotune else ctx.tuning()
 
-    def sweep(i, tg=targets):
-        ctx.sweep(scene, cams, tg, knn, i % ncam, losses, nfail)
+    # the timed sweeps: through a one-scene gs2_batch captured as a CUDA graph
+    # per sweep (re-captured and updated in place: no priming, any primary
+    # order), or eagerly through the context (--graph 0)
+    batch = prep = None
+    if args.graph:
+        batch = gs2.Batch([dict(max_gaussians=w["n"], max_width=W, max_height=H, max_sh_degree=w["sh"],
+                                max_pairs=w["max_pairs"])], dict(precision=args.precision))
+        batch.set_tuning(0, tuning["sort_blocks"], tuning["sort_rows"], tuning["view_lanes"])
+        prep = batch.prepare([scene], [cams], [targets], [knn])
+
+    def sweep(i, tg=None):
+        if batch is not None:
+            if tg is not None:
+                batch.set_targets(prep, 0, tg)
+            batch.sweep(prep, [i % ncam], losses, nfail, use_graph=args.graph)
+        else:
+            ctx.sweep(scene, cams, targets if tg is None else tg, knn, i % ncam, losses, nfail)
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
+    def check():
+        ctx.check()
+        if batch is not None:
+            batch.check()
+
     for i in range(args.warmup):
         sweep(i)
     torch.cuda.synchronize()
-    ctx.check()
+    check()
 
     # ---------------- device-resident timed region (the views of each group concurrent)
     clocks = ClockSampler(local_rank)
@@ -215,7 +235,7 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    ctx.check()
+    check()
 
     # ---------------- roofline pass (untimed): the same sweeps with the views one
     # after another, so that each accumulation launch's CUDA-event duration is
@@ -227,7 +247,7 @@ def run_gpu(args, rank, world, local_rank):
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     for i in range(args.steps):
-        sweep(args.warmup + args.steps + i)
+        ctx.sweep(scene, cams, targets, knn, (args.warmup + args.steps + i) % ncam, losses, nfail)
     p1.record(stream)
     torch.cuda.synchronize()
     ms_serial = p0.elapsed_time(p1)
@@ -249,8 +269,7 @@ def run_gpu(args, rank, world, local_rank):
 
     def e2e_step(i, prefetch_next):
         t = i % ncam
-        tg = ht.targets(t)
-        ctx.sweep(scene, cams, tg, knn, t, losses, nfail)
+        sweep(i, ht.targets(t))
         ht.release(t)
         if prefetch_next:
             ht.prefetch((i + 1) % ncam)
@@ -270,7 +289,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ms_e2e = e0.elapsed_time(e1)
-    ctx.check()
+    check()
 
     if world > 1:
         ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
@@ -351,6 +370,7 @@ def run_gpu(args, rank, world, local_rank):
         "stages": stages,
         "gpu_launches": int(launches),
         "tuning": tuning,
+        "launch": "one CUDA graph per sweep (captured, updated in place)" if args.graph else "eager",
         "clocks": clk,
         "accumulate_ms_by_group": {GROUP_NAMES[g]: round(float(prof["accum_ms"][g]) / max(args.steps, 1), 3)
                                    for g in range(5)},
@@ -767,6 +787,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (profiling captures)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning")
+    ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
+                    help="1: time sweeps as a CUDA graph re-captured per sweep (one-scene gs2_batch); 0: eager")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")

@@ -537,6 +537,15 @@ class Batch:
             keep=(cam_arrs, tgt_arrs, knn_arrs, scenes, targets))
         return prep
 
+    def set_targets(self, prep, i: int, targets):
+        """Point scene i's target list of a prepared batch at other device
+        images (None where a sweep reads none), e.g. per-sweep uploads."""
+        arr = prep["keep"][1][i]
+        assert len(targets) == len(arr)
+        for j, x in enumerate(targets):
+            arr[j] = _ptr(x)
+        prep["keep"][4][i] = list(targets)
+
     def sweep(self, prep, t, losses=None, n_failed=None, use_graph=False, stream=None):
         """use_graph: False (eager), True or 1 (one graph, re-captured and
         updated per call), 2 (graphs kept per scene and sweep inputs)."""

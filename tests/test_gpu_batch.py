@@ -186,3 +186,29 @@ def test_concurrent_views_equal_serial_views():
         torch.cuda.synchronize()
         ctx.check()
         _close(a, b, before)
+
+
+def test_set_targets_repoints_a_prepared_batch():
+    """Batch.set_targets rewrites a prepared batch's target pointers: a graph
+    sweep on copies of the targets placed elsewhere in memory equals the one
+    on the originals (first group's primary loss, before any step)."""
+    from paper_2501_13975_b300 import gs2
+    work, sizes, targets, knns = _setup(gs2)
+    w, tg, knn = work[0], targets[0], knns[0]
+    out = []
+    for repoint in (False, True):
+        batch = gs2.Batch([sizes[0]])
+        ds = gs2.DeviceScene.from_host(w["train"])
+        prep = batch.prepare([ds], [w["cams"]], [tg], [knn])
+        if repoint:
+            copies = [x.clone() for x in tg]
+            del tg[:]   # the prepared batch must not need the originals' list any more
+            batch.set_targets(prep, 0, copies)
+        losses = torch.zeros((1, 10), dtype=torch.float64, device="cuda")
+        batch.sweep(prep, [1], losses, use_graph=1)
+        batch.check()
+        out.append(losses.cpu().numpy())
+        batch.close()
+        if repoint:
+            tg.extend(copies)
+    np.testing.assert_allclose(out[1][0, :2], out[0][0, :2], rtol=1e-12)
