@@ -112,6 +112,12 @@ typedef struct {
     int32_t knn_k;          /* secondary targets per primary (3) */
     int32_t downsample;     /* secondary-target downsampling factor (2) */
     int32_t precision;      /* 0: FP32 path; 1: mixed (FP64 solve of ill-conditioned blocks) */
+    int32_t gauss_newton;   /* 0: full local Newton blocks (Eq. local_hessian_gradient); 1: drop the
+                               e d2c/dy2 terms, keeping sum h dc/dy dc/dy^T (local Gauss-Newton, the
+                               cheaper variant Sec. 6 proposes; positive semidefinite where h >= 0) */
+    int32_t group_order[5]; /* the groups of a sweep in the order run: a permutation of gs2_group
+                               (0 1 2 3 4 = position, rotation, scaling, opacity, colour: Sec. 4.2;
+                               Sec. 5 compares orders) */
 } gs2_config;
 
 void gs2_config_default(gs2_config *cfg);

@@ -85,6 +85,8 @@ typedef struct {
     double trust_pos;   /* |dp| <= trust_pos * max(s) */
     double trust_rot;   /* |theta| <= trust_rot */
     double trust_color; /* |dc_ch| <= trust_color (SH coefficient norm per channel) */
+    int gauss_newton;   /* 1: drop the e d2c/dy2 term of the blocks (Gauss-Newton) */
+    int group_order[5]; /* the groups of a sweep in the order run (a permutation of 0..4) */
 } orc_config;
 
 /* Trust radii (reading; the paper fixes step size 1 and gives no safeguard):
@@ -775,6 +777,9 @@ double orc_loss(const double *img, const double *tgt, int W, int H, const orc_co
  * Block assembly [Eq. local_hessian_gradient]:
  *   g_y += sum_p sum_ch e_ch(p) dc_ch(p)/dy
  *   H_y += sum_p sum_ch ( h_ch(p) dc_ch/dy dc_ch/dy^T + e_ch(p) d2c_ch/dy2 )
+ * With cfg->gauss_newton the second term is dropped: the Gauss-Newton block
+ * sum_p sum_ch h_ch(p) dc_ch/dy dc_ch/dy^T (a local Gauss-Newton variant per
+ * attribute, which the conclusion names as a cheaper position path).
  * where, for Gaussian k, c(p) = C_front + T_k (alpha_k c~_k + (1 - alpha_k) C_back_k)
  * (Eq. 3dgs regrouped around term k; T_k and C_back_k do not depend on y_k).
  * alpha_k and c~_k are evaluated as jets of y_k; the set of contributors is
@@ -889,7 +894,8 @@ static void accum_channelset(const orc_scene *sc, const orc_camera *cam, const o
                             tg[(size_t)a * n + k] += gv;
                             tga[(size_t)a * n + k] += fabs(gv);
                             for (int b = a; b < D; ++b, ++kk) {
-                                double t1 = hp[c] * cc.g[a] * cc.g[b], t2 = ep[c] * cc.h[kk];
+                                double t1 = hp[c] * cc.g[a] * cc.g[b];
+                                double t2 = cfg->gauss_newton ? 0.0 : ep[c] * cc.h[kk];
                                 tH[(size_t)kk * n + k] += t1 + t2;
                                 tHa[(size_t)kk * n + k] += fabs(t1) + fabs(t2);
                             }
@@ -1458,11 +1464,13 @@ void orc_downsample_image(const double *in, int W, int H, int f, double *out) {
 
 /* ---------------------------------------------------------------------------
  * One sweep for primary image t [Sec. 4.2 group order, Sec. 4.3 Eq. tildel]:
- * for each group in the order position, rotation, scaling, opacity, colour:
+ * for each group in cfg->group_order (the paper's order by default: position,
+ * rotation, scaling, opacity, colour):
  * render the primary (full resolution) and its K secondaries (downsampled),
  * accumulate the group's blocks over these views, solve, apply.
  * targets: ncam images [3][H][W] at full resolution (all cameras same size).
- * knn [ncam][K].  losses_out [5] = primary loss before each group's update.
+ * knn [ncam][K].  losses_out [5] = primary loss before each group's update
+ * (indexed by group, not by position in the order).
  * ------------------------------------------------------------------------- */
 int orc_sweep(orc_scene *sc, const orc_camera *cams, const double *targets, int ncam, const int *knn, int t,
               const orc_config *cfg, double *losses_out, int *nfail_out) {
@@ -1480,7 +1488,8 @@ int orc_sweep(orc_scene *sc, const orc_camera *cams, const double *targets, int 
     double *Hb = (double *)malloc(sizeof(double) * hmax);
     double *step = (double *)malloc(sizeof(double) * gmax);
     int nfail = 0;
-    for (int group = 0; group < 5; ++group) {
+    for (int gi = 0; gi < 5; ++gi) {
+        const int group = cfg->group_order[gi];
         memset(g, 0, sizeof(double) * gmax);
         memset(Hb, 0, sizeof(double) * hmax);
         for (int vi = 0; vi <= K; ++vi) {

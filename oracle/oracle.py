@@ -47,7 +47,7 @@ class OrcConfig(C.Structure):
                 ("ssim_c1", C.c_double), ("ssim_c2", C.c_double), ("ssim_sigma", C.c_double),
                 ("ssim_radius", C.c_int), ("knn_k", C.c_int), ("downsample", C.c_int),
                 ("scale_trust", C.c_double), ("trust_pos", C.c_double), ("trust_rot", C.c_double),
-                ("trust_color", C.c_double)]
+                ("trust_color", C.c_double), ("gauss_newton", C.c_int), ("group_order", C.c_int * 5)]
 
 
 def default_config(**kw) -> dict:
@@ -56,7 +56,8 @@ def default_config(**kw) -> dict:
                near_z=0.2, barrier_alpha=1e-6, frac_to_boundary=0.99, damping_mu0=1.0,
                damping_tries=6, scale_min=1e-7, ssim_c1=0.01 ** 2, ssim_c2=0.03 ** 2, ssim_sigma=1.5,
                ssim_radius=5, knn_k=3, downsample=2, scale_trust=2.0,
-               trust_pos=3.0, trust_rot=0.7853981633974483, trust_color=3.5449077018110318)
+               trust_pos=3.0, trust_rot=0.7853981633974483, trust_color=3.5449077018110318,
+               gauss_newton=0, group_order=(0, 1, 2, 3, 4))
     cfg.update(kw)
     return cfg
 
@@ -126,7 +127,13 @@ def cfg_struct(cfg: dict | None) -> OrcConfig:
     d = default_config() if cfg is None else default_config(**cfg)
     c = OrcConfig()
     for k, _ in OrcConfig._fields_:
-        setattr(c, k, d[k])
+        if k == "group_order":
+            order = [int(x) for x in d[k]]
+            if sorted(order) != [0, 1, 2, 3, 4]:
+                raise ValueError(f"group_order must be a permutation of 0..4: {order}")
+            c.group_order = (C.c_int * 5)(*order)
+        else:
+            setattr(c, k, d[k])
     return c
 
 

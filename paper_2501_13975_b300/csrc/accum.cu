@@ -145,9 +145,11 @@ struct PixState {
 
 // One active (pixel, Gaussian) pair: adds the group's payload into pl and
 // steps the pixel's state past the Gaussian.
+// gn (Gauss-Newton): the e-weighted second derivatives of the pixel colour
+// (e d2c/dz2 through the falloff, e d2c/dalpha dc~) are left out.
 template <int GROUP, int P>
 __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, const float4 &B, const float4 &C,
-                                              float G, float alpha, float dx, float dy, bool clamped,
+                                              float G, float alpha, float dx, float dy, bool clamped, bool gn,
                                               float (&pl)[P]) {
     const float Tk = __fdiv_rn(ps.T, __fsub_rn(1.f, alpha));
     const float w = alpha * Tk;
@@ -155,6 +157,7 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
     const float *e = ps.e, *h = ps.h;
     const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
     const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
+    const float Es = gn ? 0.f : Ea;   // weight of the second-derivative terms
     if (GROUP == GS2_OPACITY) {
         if (!clamped) {
             pl[0] += Ea * G;
@@ -178,7 +181,7 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int jx = i; jx < 3; ++jx)
-                    pl[3 + ut3(i, jx)] += Ah * sg * sg * gz[2 + i] * gz[2 + jx] + Ea * sg * gzz[ut5(2 + i, 2 + jx)];
+                    pl[3 + ut3(i, jx)] += Ah * sg * sg * gz[2 + i] * gz[2 + jx] + Es * sg * gzz[ut5(2 + i, 2 + jx)];
         }
     } else {  // position
         const float aa[3] = {a0, a1, a2};
@@ -194,10 +197,10 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
 #pragma unroll
             for (int i = 0; i < 5; ++i)
 #pragma unroll
-                for (int jx = i; jx < 5; ++jx) pl[5 + ut5(i, jx)] += Ah * az[i] * az[jx] + Ea * sg * gzz[ut5(i, jx)];
+                for (int jx = i; jx < 5; ++jx) pl[5 + ut5(i, jx)] += Ah * az[i] * az[jx] + Es * sg * gzz[ut5(i, jx)];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float xc = h[c] * aa[c] * w + e[c] * Tk;
+                const float xc = h[c] * aa[c] * w + (gn ? 0.f : e[c] * Tk);
 #pragma unroll
                 for (int i = 0; i < 5; ++i) pl[20 + c * 5 + i] += xc * az[i];
             }
@@ -219,8 +222,8 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS) k_accum(const uint2 *__restr
                                                            const uint32_t *__restrict__ ids, ProjView pv,
                                                            RasterView rv, const float *__restrict__ E,
                                                            const float *__restrict__ Hh, int W, int H, int tiles_x,
-                                                           float amin, float amax, ACC *__restrict__ zbuf, int n,
-                                                           unsigned long long *__restrict__ active_stat) {
+                                                           float amin, float amax, int gn, ACC *__restrict__ zbuf,
+                                                           int n, unsigned long long *__restrict__ active_stat) {
     constexpr int P = Payload<GROUP>::P;
     constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
     constexpr int PER = NB / GS2_PAIR_THREADS;        // entries each thread stages
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS) k_accum(const uint2 *__restr
             const float4 C = sC[buf][s];
 #pragma unroll
             for (int q = 0; q < 2; ++q)
-                if (act[q]) pixel_payload<GROUP, P>(ps[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], pl);
+                if (act[q]) pixel_payload<GROUP, P>(ps[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], gn != 0, pl);
             warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
         }
     }
@@ -422,9 +425,12 @@ __global__ void k_epi_color(DevScene sc, DevCam cam, const ProjView pv, ACC *zbu
     for (int i = 0; i < sc.S; ++i) slot[(size_t)(6 + i) * n + k] = sh_norm(i) * phi[i];
 }
 
+// gn (Gauss-Newton) in the epilogues: the terms g_z . d2z/dy2 (the
+// image-space gradient times the second derivatives of the projected
+// quantities) are left out.
 template <typename ACC>
 __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__restrict__ zbuf,
-                            float *__restrict__ blocks) {
+                            float *__restrict__ blocks, int gn) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
@@ -465,7 +471,7 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__r
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) hv += dS[j][a] * Hz[a][b] * dS[l][b];
-            if (j == l)
+            if (j == l && !gn)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) hv += z[a] * d2S[j][a];
             atomicAdd(&blocks[(size_t)(3 + ut3(j, l)) * n + k], hv);
@@ -474,7 +480,7 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__r
 
 template <typename ACC>
 __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjView pv, ACC *__restrict__ zbuf,
-                          float *__restrict__ blocks) {
+                          float *__restrict__ blocks, int gn) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
@@ -534,7 +540,7 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
     float gth = 0.f, hth = 0.f;
     for (int aa = 0; aa < 3; ++aa) {
         gth += z[aa] * d1[aa];
-        hth += z[aa] * d2[aa];
+        if (!gn) hth += z[aa] * d2[aa];
         for (int b = 0; b < 3; ++b) {
             const float hz = z[3 + (aa <= b ? ut3(aa, b) : ut3(b, aa))];
             hth += d1[aa] * hz * d1[b];
@@ -551,7 +557,7 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
 // chain rule through the intermediates (u, tau_x, tau_y).
 template <typename ACC, int S>
 __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, const ProjView pv,
-                                                    ACC *__restrict__ zbuf, float *__restrict__ blocks) {
+                                                    ACC *__restrict__ zbuf, float *__restrict__ blocks, int gn) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
@@ -708,8 +714,9 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
             float acc = 0.f;
 #pragma unroll
             for (int i = 0; i < 5; ++i) acc += Jzp[i][c] * HJ[i][d];
+            if (!gn)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc += V[a * 4 + c] * GW[a][d];
+                for (int a = 0; a < 3; ++a) acc += V[a * 4 + c] * GW[a][d];
             Hp[c][d] = acc;
         }
     // colour path: c~(p) through r(p)
@@ -755,7 +762,7 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
                 float h2 = Pm[a][0] * HPm[0][b] + Pm[a][1] * HPm[1][b] + Pm[a][2] * HPm[2][b];
                 // sum_m gr_m d2r_m/dp_a dp_b = (3 (gr.r) r_a r_b - gr_a r_b - gr_b r_a - d_ab (gr.r)) / rho^2
                 h2 += (3.f * gdr * r[a] * r[b] - gr[a] * r[b] - gr[b] * r[a] - (a == b ? gdr : 0.f)) * irho * irho;
-                Hp[a][b] += y[a] * gc[b] + gc[a] * y[b] + SS * gc[a] * gc[b] + WE * h2;
+                Hp[a][b] += y[a] * gc[b] + gc[a] * y[b] + SS * gc[a] * gc[b] + (gn ? 0.f : WE * h2);
             }
         }
     }
@@ -777,7 +784,8 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     unsigned long long *act = pc->prof_on ? pc->d_stats + 4 * group + 3 : nullptr;
 #define ACC_LAUNCH(G)                                                                                             \
     k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
-                                                   view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, zb, n, act)
+                                                   view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, cfg.gauss_newton, \
+                                                   zb, n, act)
     switch (group) {
     case GS2_POS: ACC_LAUNCH(GS2_POS); break;
     case GS2_ROT: ACC_LAUNCH(GS2_ROT); break;
@@ -793,18 +801,19 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     GS2_COUNT_LAUNCH(2);
     if (n == 0) return;
     const int eg = (n + 255) / 256;
+    const int gn = cfg.gauss_newton;
     float *b = (float *)blocks;
     switch (group) {
     case GS2_POS:
         switch (sc.S) {
-        case 1: k_epi_pos<ACC, 1><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
-        case 4: k_epi_pos<ACC, 4><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
-        case 9: k_epi_pos<ACC, 9><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
-        default: k_epi_pos<ACC, 16><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b); break;
+        case 1: k_epi_pos<ACC, 1><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b, gn); break;
+        case 4: k_epi_pos<ACC, 4><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b, gn); break;
+        case 9: k_epi_pos<ACC, 9><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b, gn); break;
+        default: k_epi_pos<ACC, 16><<<(n + 127) / 128, 128, 0, st>>>(sc, view, pv, zb, b, gn); break;
         }
         break;
-    case GS2_ROT: k_epi_rot<ACC><<<eg, 256, 0, st>>>(sc, view, primary, pv, zb, b); break;
-    case GS2_SCALE: k_epi_scale<ACC><<<eg, 256, 0, st>>>(sc, view, pv, zb, b); break;
+    case GS2_ROT: k_epi_rot<ACC><<<eg, 256, 0, st>>>(sc, view, primary, pv, zb, b, gn); break;
+    case GS2_SCALE: k_epi_scale<ACC><<<eg, 256, 0, st>>>(sc, view, pv, zb, b, gn); break;
     case GS2_OPACITY: k_epi_opacity<ACC><<<eg, 256, 0, st>>>(pv, zb, n, b); break;
     default: {
         float *slot = b + (size_t)view_slot * (6 + sc.S) * n;

@@ -54,6 +54,8 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->knn_k = 3;
     c->downsample = 2;
     c->precision = 0;
+    c->gauss_newton = 0;
+    for (int i = 0; i < 5; ++i) c->group_order[i] = i;
 }
 
 static bool cfg_ok(const gs2_config *c, std::string &err) {
@@ -68,6 +70,13 @@ static bool cfg_ok(const gs2_config *c, std::string &err) {
     if (!(c->scale_trust > 1.f) || !(c->scale_min > 0.f)) { err = "scale_trust > 1 and scale_min > 0 required"; return false; }
     if (!(c->frac_to_boundary > 0.f && c->frac_to_boundary < 1.f)) { err = "frac_to_boundary in (0,1)"; return false; }
     if (!(c->trust_pos > 0.f && c->trust_rot > 0.f && c->trust_color > 0.f)) { err = "trust radii must be > 0"; return false; }
+    if (c->gauss_newton != 0 && c->gauss_newton != 1) { err = "gauss_newton must be 0 or 1"; return false; }
+    int seen = 0;
+    for (int i = 0; i < 5; ++i) {
+        if (c->group_order[i] < 0 || c->group_order[i] > 4) { err = "group_order entries must be groups 0..4"; return false; }
+        seen |= 1 << c->group_order[i];
+    }
+    if (seen != 31) { err = "group_order must be a permutation of the five groups"; return false; }
     return true;
 }
 
@@ -589,7 +598,12 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             l->sort_rows = ctx->sort_rows;
         }
     }
-    for (int group = 0; group < 5; ++group) {
+    // the depth order of each view depends on the means and the camera only:
+    // the first pass without a valid order sorts and keeps it, later passes
+    // reuse it until a position step moves the means
+    bool order_valid = false;
+    for (int gi = 0; gi < 5; ++gi) {
+        const int group = ctx->cfg.group_order[gi];
         ctx->stat_slot = group;
         RET_CUDA(ctx, cudaMemsetAsync(ctx->sw_blocks, 0, blocks_bytes_impl(group, scene->n, scene->sh_degree, nv), st));
         if (lanes) {
@@ -615,14 +629,16 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             if (vid[i] < 0) continue;
             gs2_ctx *vc = (lanes && i > 0) ? ctx->lanes[i - 1] : ctx;
             cudaStream_t vs = (lanes && i > 0) ? ctx->lane_st[i - 1] : st;
-            // only the position group moves the means: the rotation pass sorts each
-            // view by depth and keeps the order, the scaling, opacity and colour
-            // passes reuse it (the same means and camera give the same order)
+            // only the position group moves the means: a pass that is not the
+            // position pass and finds no valid order sorts each view by depth and
+            // keeps the order; the following passes reuse it (the same means and
+            // camera give the same order)
             uint32_t *cache = ctx->order_cache + (size_t)i * ctx->max_n;
             gs2_status rc = lanes ? GS2_OK : do_project(vc, scene, &vcam[i], vc->sw_proj, vs);
             if (rc == GS2_OK)
                 rc = do_raster(vc, scene->n, &vcam[i], vc->sw_proj, vc->sw_image, vc->sw_rstate, vs,
-                               group >= GS2_SCALE ? cache : nullptr, group == GS2_ROT ? cache : nullptr);
+                               order_valid ? cache : nullptr,
+                               (!order_valid && group != GS2_POS) ? cache : nullptr);
             if (rc == GS2_OK)
                 rc = do_accum(vc, group, scene, &vcam[i], primary, vc->sw_proj, vc->sw_rstate, vc->sw_image, vtgt[i],
                               i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, vs);
@@ -637,6 +653,9 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
                 RET_CUDA(ctx, cudaStreamWaitEvent(st, ctx->lane_ev[i], 0));
             }
         }
+        // a non-position pass stored or reused the views' depth orders; the
+        // position step about to be applied invalidates them
+        order_valid = group != GS2_POS;
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
                                    ctx->sw_step, n_failed, ctx->flags, st));
         float *rec = records ? records + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;

@@ -49,7 +49,7 @@ class Config_(C.Structure):
                 ("trust_pos", C.c_float), ("trust_rot", C.c_float), ("trust_color", C.c_float),
                 ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
                 ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("gauss_newton", C.c_int32), ("group_order", C.c_int32 * 5)]
 
 
 class Tuning_(C.Structure):
@@ -138,10 +138,11 @@ def default_config(**kw) -> dict:
     c = Config_()
     _lib.gs2_config_default(C.byref(c))
     d = {k: getattr(c, k) for k, _ in Config_._fields_}
+    d["group_order"] = [int(x) for x in c.group_order]
     for k, v in kw.items():
         if k not in d:
             raise KeyError(k)
-        d[k] = v
+        d[k] = [int(x) for x in v] if k == "group_order" else v
     return d
 
 
@@ -149,7 +150,10 @@ def _config_struct(cfg: dict | None) -> Config_:
     d = default_config(**(cfg or {}))
     c = Config_()
     for k, _ in Config_._fields_:
-        setattr(c, k, d[k])
+        if k == "group_order":
+            c.group_order = (C.c_int32 * 5)(*[int(x) for x in d[k]])
+        else:
+            setattr(c, k, d[k])
     return c
 
 

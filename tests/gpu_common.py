@@ -6,14 +6,17 @@ import numpy as np
 GPU_CFG_KEYS = ("lambda_ssim", "alpha_min", "alpha_max", "t_min", "lowpass", "near_z", "barrier_alpha",
                 "frac_to_boundary", "damping_mu0", "damping_tries", "scale_min", "scale_trust", "trust_pos",
                 "trust_rot", "trust_color", "ssim_c1",
-                "ssim_c2", "ssim_sigma", "ssim_radius", "knn_k", "downsample")
+                "ssim_c2", "ssim_sigma", "ssim_radius", "knn_k", "downsample", "gauss_newton", "group_order")
 
 
 def oracle_cfg(gpu_cfg: dict) -> dict:
     out = {}
     for k in GPU_CFG_KEYS:
         v = gpu_cfg[k]
-        out[k] = int(v) if isinstance(v, (int, np.integer)) and not isinstance(v, bool) else float(np.float32(v))
+        if k == "group_order":
+            out[k] = [int(x) for x in v]
+        else:
+            out[k] = int(v) if isinstance(v, (int, np.integer)) and not isinstance(v, bool) else float(np.float32(v))
     return out
 
 

@@ -162,9 +162,9 @@ def _colour_full(blocks, n_views, S, n):
     return g, H
 
 
-def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128):
+def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, extra=None):
     sc, cams = _tiny(n=n, size=size, sh=sh)
-    ctx, gcfg, ocfg = _setup(gs2, sc, cams, dict(lambda_ssim=lam))
+    ctx, gcfg, ocfg = _setup(gs2, sc, cams, dict(lambda_ssim=lam, **(extra or {})))
     gt = synth.perturbed(sc, seed=2, sd=0.05)
     primary = cams[0]
     view = O.downsample_camera(cams[1], 2) if secondary else primary
@@ -209,6 +209,15 @@ def _check_blocks(r, gtol=1e-4, htol=1e-3):
 @pytest.mark.parametrize("lam", [0.0, 0.2])
 def test_blocks_parity_primary(gs2, group, lam):
     r = _blocks_case(gs2, group, sh=(1 if group == O.COLOR else 0), lam=lam)
+    _check_blocks(r)
+
+
+@pytest.mark.parametrize("group", [0, 1, 2])
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_blocks_parity_gauss_newton(gs2, group, lam):
+    """Gauss-Newton blocks (the e-weighted second derivatives left out, Sec. 6)
+    against the oracle's Gauss-Newton blocks."""
+    r = _blocks_case(gs2, group, lam=lam, extra=dict(gauss_newton=1))
     _check_blocks(r)
 
 
