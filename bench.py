@@ -491,6 +491,92 @@ def run_batched(args):
     }
 
 
+# ----------------------------------------------------------------------------- method variants
+
+def method_variants(args):
+    """The paper's two ablations and the Gauss-Newton variant on the object
+    workload, with the same kernels: 30 sweeps (primaries in a seeded
+    permutation, seed 5) from the workload's start for each of
+      paper        K = 3 secondaries, order position, rotation, scaling, opacity, colour
+      K=0, K=8     secondary targets per primary (Sec. 5, trade-off of secondary targets)
+      colour-first order colour, opacity, scaling, rotation, position (Sec. 5, optimisation order)
+      gauss-newton Gauss-Newton blocks: the e d2c/dy2 terms left out (Sec. 6)
+    PSNR over all 100 views after every sweep (outside the timed work) and the
+    sweeps' device time (CUDA events)."""
+    import torch
+    from paper_2501_13975_b300 import gs2
+
+    torch.cuda.set_device(0)
+    w, gt_host, start_host, cams = make_workload("object")
+    if args.variants_n:
+        # the same shell with fewer Gaussians: less overlap between them
+        w = dict(w, n=args.variants_n)
+        gt_host = synth.object_scene(seed=3, n=args.variants_n)
+        start_host = synth.perturbed(gt_host, seed=4, sd=0.02)
+    # mean overlap of the shell: Gaussians covering a point of it, taking each
+    # footprint as a disc of radius 2 s (s = its mean scale)
+    s_mean = np.exp(np.log(gt_host.scale.astype(np.float64)).mean(axis=0))
+    r_mean = np.linalg.norm(gt_host.mean.astype(np.float64), axis=0).mean()
+    overlap = float(np.sum(np.pi * (2.0 * s_mean) ** 2) / (4.0 * np.pi * r_mean ** 2))
+    ncam = len(cams)
+    W, H = w["width"], w["height"]
+    order = np.random.Generator(np.random.PCG64(5)).permutation(ncam)
+    variants = [("paper", {}), ("K=0", dict(knn_k=0)), ("K=8", dict(knn_k=8)),
+                ("colour-first", dict(group_order=(4, 3, 2, 1, 0))), ("gauss-newton", dict(gauss_newton=1))]
+    sweeps = 30
+    out = {}
+    for name, cfg in variants:
+        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], cfg)
+        gt = gs2.DeviceScene.from_host(gt_host)
+        proj = ctx.proj_buffer(w["n"])
+        targets = []
+        for c in cams:
+            ctx.project(gt, c, proj)
+            img, _ = ctx.raster_fwd(gt, c, proj)
+            targets.append(img.clone())
+        del gt
+        scene = gs2.DeviceScene.from_host(start_host)
+        sphere = ctx.bounding_sphere(scene).cpu().numpy()
+        centres = np.stack([c.center() for c in cams]).astype(np.float32)
+        knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
+        evl = torch.zeros((ncam, 2), dtype=torch.float64, device="cuda")
+        nfail = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+        def psnr():
+            evl.zero_()
+            for v, c in enumerate(cams):
+                ctx.project(scene, c, proj)
+                img, _ = ctx.raster_fwd(scene, c, proj)
+                ctx.loss_derivs(img, targets[v], loss=evl[v])
+            mse = 2.0 * evl[:, 0].cpu().numpy()
+            return float(np.mean(10.0 * np.log10(1.0 / np.maximum(mse, 1e-30))))
+
+        curve, ms = [psnr()], 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for i in range(sweeps):
+            e0.record()
+            ctx.sweep(scene, cams, targets, knn, int(order[i % ncam]), None, nfail)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            curve.append(psnr())
+        ctx.check()
+        out[name] = {"config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in cfg.items()},
+                     "psnr_start": round(curve[0], 4), "psnr_after_1": round(curve[1], 4),
+                     "psnr_after_30": round(curve[-1], 4), "best_psnr": round(max(curve), 4),
+                     "ms_per_sweep": round(ms / sweeps, 3), "failed_solves": int(nfail.item()),
+                     "psnr_curve": [round(x, 3) for x in curve]}
+        ctx.close()
+    return {"metric": "PSNR over all views after 30 sweeps, per method variant (object workload)",
+            "value": out["paper"]["psnr_after_30"], "unit": "dB", "higher_is_better": True,
+            "config": {"workload": f"object: {w['n']} Gaussians on a unit-sphere shell, SH degree 3, 100 cameras "
+                                   "800x800 on a hemisphere; start: means perturbed N(0, 0.02^2)",
+                       "gaussians": w["n"], "shell_overlap": round(overlap, 1),
+                       "primaries": "seeded permutation (seed 5)"},
+            "data": "synthetic", "dtype": "f32", "variants": out}
+
+
 # ----------------------------------------------------------------------------- time to PSNR
 
 def time_to_psnr(args):
@@ -789,6 +875,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: time sweeps as a CUDA graph re-captured per sweep (one-scene gs2_batch); 0: eager")
+    ap.add_argument("--variants", action="store_true",
+                    help="method variants on the object workload: K in {0, 3, 8}, colour-first order, Gauss-Newton")
+    ap.add_argument("--variants-n", type=int, default=0, help="Gaussians of the object shell for --variants")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")
@@ -807,6 +896,10 @@ def main():
     if args.ttp:
         if rank == 0:
             print(json.dumps(time_to_psnr(args)), flush=True)
+        return
+    if args.variants:
+        if rank == 0:
+            print(json.dumps(method_variants(args)), flush=True)
         return
     if args.workload == "batched" and args.impl == "gs2":
         if rank == 0:
