@@ -294,6 +294,31 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
 
+    # ---------------- the single-render variant (Jacobi over groups), timed
+    # beside the paper's in-series sweep on the same workload: a different
+    # method, reported apart from `value`
+    jacobi = None
+    if not args.no_variants:
+        cj = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=args.precision, group_jacobi=1))
+        cj.set_tuning(**{k: tuning[k] for k in ("sort_blocks", "sort_rows", "view_lanes")})
+        sj = scene.clone()
+        for i in range(2):
+            cj.sweep(sj, cams, targets, knn, i % ncam)
+        torch.cuda.synchronize()
+        j0 = torch.cuda.Event(enable_timing=True)
+        j1 = torch.cuda.Event(enable_timing=True)
+        j0.record(stream)
+        for i in range(args.steps):
+            cj.sweep(sj, cams, targets, knn, (args.warmup + i) % ncam)
+        j1.record(stream)
+        torch.cuda.synchronize()
+        cj.check()
+        jms = j0.elapsed_time(j1) / args.steps
+        jacobi = {"sweeps_per_s": round(1000.0 / jms, 3), "ms_per_sweep": round(jms, 3), "launch": "eager",
+                  "method": "every view rendered once per sweep; all groups solved at that state (group_jacobi)"}
+        cj.close()
+        del sj
+
     # ---------------- roofline of the accumulation kernel: bound by its per-pair
     # arithmetic (ALU), not HBM; the HBM figure with algorithmic bytes beside it
     peak, peak_kind = load_peaks()
@@ -368,6 +393,7 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roofline,
         "stages": stages,
+        "jacobi_groups": jacobi,
         "gpu_launches": int(launches),
         "tuning": tuning,
         "launch": "one CUDA graph per sweep (captured, updated in place)" if args.graph else "eager",
@@ -501,6 +527,8 @@ def method_variants(args):
       K=0, K=8     secondary targets per primary (Sec. 5, trade-off of secondary targets)
       colour-first order colour, opacity, scaling, rotation, position (Sec. 5, optimisation order)
       gauss-newton Gauss-Newton blocks: the e d2c/dy2 terms left out (Sec. 6)
+      jacobi-groups every view rendered once per sweep, all groups solved at that
+                   state and applied together (the single-render variant)
     PSNR over all 100 views after every sweep (outside the timed work) and the
     sweeps' device time (CUDA events)."""
     import torch
@@ -522,7 +550,8 @@ def method_variants(args):
     W, H = w["width"], w["height"]
     order = np.random.Generator(np.random.PCG64(5)).permutation(ncam)
     variants = [("paper", {}), ("K=0", dict(knn_k=0)), ("K=8", dict(knn_k=8)),
-                ("colour-first", dict(group_order=(4, 3, 2, 1, 0))), ("gauss-newton", dict(gauss_newton=1))]
+                ("colour-first", dict(group_order=(4, 3, 2, 1, 0))), ("gauss-newton", dict(gauss_newton=1)),
+                ("jacobi-groups", dict(group_jacobi=1))]
     sweeps = 30
     out = {}
     for name, cfg in variants:
@@ -877,6 +906,8 @@ def main():
                     help="1: time sweeps as a CUDA graph re-captured per sweep (one-scene gs2_batch); 0: eager")
     ap.add_argument("--variants", action="store_true",
                     help="method variants on the object workload: K in {0, 3, 8}, colour-first order, Gauss-Newton")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the single-render (Jacobi over groups) variant beside the headline")
     ap.add_argument("--variants-n", type=int, default=0, help="Gaussians of the object shell for --variants")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")

@@ -118,6 +118,12 @@ typedef struct {
     int32_t group_order[5]; /* the groups of a sweep in the order run: a permutation of gs2_group
                                (0 1 2 3 4 = position, rotation, scaling, opacity, colour: Sec. 4.2;
                                Sec. 5 compares orders) */
+    int32_t group_jacobi;   /* 0: the groups in series, every view re-rendered after each group's
+                               step (Sec. 4.2); 1: every view rendered once per sweep, all groups'
+                               blocks accumulated from it, solved at that state and applied together
+                               (Jacobi over groups, position applied last).  Setting it allocates
+                               the per-group blocks and steps in gs2_create / gs2_set_config; the
+                               step-scale network and the logged sweep need the series form. */
 } gs2_config;
 
 void gs2_config_default(gs2_config *cfg);

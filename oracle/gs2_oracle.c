@@ -87,6 +87,8 @@ typedef struct {
     double trust_color; /* |dc_ch| <= trust_color (SH coefficient norm per channel) */
     int gauss_newton;   /* 1: drop the e d2c/dy2 term of the blocks (Gauss-Newton) */
     int group_order[5]; /* the groups of a sweep in the order run (a permutation of 0..4) */
+    int group_jacobi;   /* 1: one render per view and sweep; every group solved at that state,
+                           the steps applied together (position last) */
 } orc_config;
 
 /* Trust radii (reading; the paper fixes step size 1 and gives no safeguard):
@@ -1488,6 +1490,56 @@ int orc_sweep(orc_scene *sc, const orc_camera *cams, const double *targets, int 
     double *Hb = (double *)malloc(sizeof(double) * hmax);
     double *step = (double *)malloc(sizeof(double) * gmax);
     int nfail = 0;
+    if (cfg->group_jacobi) {
+        /* Jacobi over groups (the single-render variant): every view rendered
+         * once, each group's g and H accumulated from that render, all groups
+         * solved at the start state, then applied: the other groups first and
+         * the position last (the rotation step turns about the primary's view
+         * direction through the centre before it moves).  losses_out: the
+         * primary loss in the slot of the first group of the order. */
+        double *gj[5], *Hj[5], *sj[5];
+        for (int q = 0; q < 5; ++q) {
+            gj[q] = (double *)calloc(gmax, sizeof(double));
+            Hj[q] = (double *)calloc(hmax, sizeof(double));
+            sj[q] = (double *)calloc(gmax, sizeof(double));
+        }
+        if (losses_out) for (int q = 0; q < 5; ++q) losses_out[q] = 0.0;
+        for (int vi = 0; vi <= K; ++vi) {
+            int v = (vi == 0) ? t : knn[t * K + (vi - 1)];
+            if (v < 0) continue;
+            orc_camera cv = cams[v];
+            const double *tgt = targets + (size_t)v * 3 * P;
+            int Wv = W, Hv = H;
+            if (vi > 0 && f > 1) {
+                orc_downsample_camera(&cams[v], f, &cv);
+                orc_downsample_image(tgt, W, H, f, tg);
+                tgt = tg;
+                Wv = cv.width;
+                Hv = cv.height;
+            }
+            orc_render(sc, &cv, cfg, img, NULL, NULL, NULL);
+            double L = orc_loss(img, tgt, Wv, Hv, cfg, e, h, NULL);
+            if (vi == 0 && losses_out) losses_out[cfg->group_order[0]] = L;
+            for (int q = 0; q < 5; ++q) orc_accum(q, sc, &cv, &cams[t], cfg, e, h, gj[q], Hj[q], NULL, NULL, NULL);
+        }
+        for (int gi = 0; gi < 5; ++gi) {
+            const int q = cfg->group_order[gi];
+            nfail += orc_solve(q, sc, &cams[t], cfg, gj[q], Hj[q], sj[q], NULL, NULL, NULL);
+        }
+        for (int gi = 0; gi < 5; ++gi) {
+            const int q = cfg->group_order[gi];
+            if (q != G_POS) orc_apply(q, sc, &cams[t], cfg, sj[q]);
+        }
+        orc_apply(G_POS, sc, &cams[t], cfg, sj[G_POS]);
+        for (int q = 0; q < 5; ++q) {
+            free(gj[q]);
+            free(Hj[q]);
+            free(sj[q]);
+        }
+        if (nfail_out) *nfail_out = nfail;
+        free(img); free(tg); free(e); free(h); free(g); free(Hb); free(step);
+        return 0;
+    }
     for (int gi = 0; gi < 5; ++gi) {
         const int group = cfg->group_order[gi];
         memset(g, 0, sizeof(double) * gmax);

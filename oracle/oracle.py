@@ -47,7 +47,8 @@ class OrcConfig(C.Structure):
                 ("ssim_c1", C.c_double), ("ssim_c2", C.c_double), ("ssim_sigma", C.c_double),
                 ("ssim_radius", C.c_int), ("knn_k", C.c_int), ("downsample", C.c_int),
                 ("scale_trust", C.c_double), ("trust_pos", C.c_double), ("trust_rot", C.c_double),
-                ("trust_color", C.c_double), ("gauss_newton", C.c_int), ("group_order", C.c_int * 5)]
+                ("trust_color", C.c_double), ("gauss_newton", C.c_int), ("group_order", C.c_int * 5),
+                ("group_jacobi", C.c_int)]
 
 
 def default_config(**kw) -> dict:
@@ -57,7 +58,7 @@ def default_config(**kw) -> dict:
                damping_tries=6, scale_min=1e-7, ssim_c1=0.01 ** 2, ssim_c2=0.03 ** 2, ssim_sigma=1.5,
                ssim_radius=5, knn_k=3, downsample=2, scale_trust=2.0,
                trust_pos=3.0, trust_rot=0.7853981633974483, trust_color=3.5449077018110318,
-               gauss_newton=0, group_order=(0, 1, 2, 3, 4))
+               gauss_newton=0, group_order=(0, 1, 2, 3, 4), group_jacobi=0)
     cfg.update(kw)
     return cfg
 

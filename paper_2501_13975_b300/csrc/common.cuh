@@ -161,6 +161,9 @@ struct gs2_ctx {
     float *g_prim;               // [3][max_n] gradient rows right after the view-slot-0 accumulation
     float *lg_phi;               // [max_n] phi1 accumulator of the logged sweep
     uint32_t *order_cache;       // [1 + knn_k][max_n] depth orders of a sweep's views (reused while means are fixed)
+    void *jb_mem;                // Jacobi over groups: one allocation holding ...
+    float *jb_blocks[5];         // ... every group's blocks (1 + knn_k view slots for colour) and ...
+    float *jb_step[5];           // ... every group's step
     // opt-in profile of the accumulation kernel: CUDA events around every launch
     // and per-group pair / visible-Gaussian totals counted on the device
     int prof_on;

@@ -56,6 +56,7 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->precision = 0;
     c->gauss_newton = 0;
     for (int i = 0; i < 5; ++i) c->group_order[i] = i;
+    c->group_jacobi = 0;
 }
 
 static bool cfg_ok(const gs2_config *c, std::string &err) {
@@ -77,6 +78,7 @@ static bool cfg_ok(const gs2_config *c, std::string &err) {
         seen |= 1 << c->group_order[i];
     }
     if (seen != 31) { err = "group_order must be a permutation of the five groups"; return false; }
+    if (c->group_jacobi != 0 && c->group_jacobi != 1) { err = "group_jacobi must be 0 or 1"; return false; }
     return true;
 }
 
@@ -129,12 +131,37 @@ static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->flags, c->g_prim, c->lg_phi,
-                    c->order_cache};
+                    c->order_cache, c->jb_mem};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
         for (int i = 0; i < 2 * GS2_PROF_POOL; ++i)
             if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+}
+
+// Jacobi over groups: every group's blocks and step at once (allocated when
+// the option is first set, from the host, never inside a stream capture)
+static bool ensure_jacobi(gs2_ctx *c) {
+    if (c->jb_mem) return true;
+    const int K = c->cfg.knn_k;
+    size_t off[11], tot = 0;
+    for (int g = 0; g < 5; ++g) {
+        off[g] = tot;
+        tot += align256(blocks_bytes_impl(g, c->max_n, c->max_sh, 1 + K));
+    }
+    for (int g = 0; g < 5; ++g) {
+        off[5 + g] = tot;
+        tot += align256(step_bytes_impl(g, c->max_n, c->max_sh));
+    }
+    if (cudaMalloc(&c->jb_mem, tot) != cudaSuccess) {
+        c->jb_mem = nullptr;
+        return false;
+    }
+    for (int g = 0; g < 5; ++g) {
+        c->jb_blocks[g] = (float *)((char *)c->jb_mem + off[g]);
+        c->jb_step[g] = (float *)((char *)c->jb_mem + off[5 + g]);
+    }
+    return true;
 }
 
 extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t max_n, int32_t max_w, int32_t max_h,
@@ -254,6 +281,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     }
     for (int i = 0; i <= nl && ok; ++i)
         ok = cudaEventCreateWithFlags(&c->lane_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok && c->cfg.group_jacobi) ok = ensure_jacobi(c);
     if (!ok) {
         free_ctx(c);
         delete c;
@@ -282,6 +310,12 @@ extern "C" gs2_status gs2_set_config(gs2_ctx *ctx, const gs2_config *cfg) {
     REQUIRE(ctx, cfg->downsample >= ctx->cfg.downsample, GS2_ERR_SHAPE,
             "downsample smaller than at gs2_create (sweep scratch sized for it)");
     const int K0 = ctx->cfg.knn_k, f0 = ctx->cfg.downsample;
+    if (cfg->group_jacobi && !ctx->jb_mem) {
+        const gs2_config keep = ctx->cfg;
+        ctx->cfg.knn_k = K0;   // sized for the knn_k of gs2_create, like the other sweep scratch
+        REQUIRE(ctx, ensure_jacobi(ctx), GS2_ERR_OOM, "cannot allocate the per-group blocks of group_jacobi");
+        ctx->cfg = keep;
+    }
     ctx->cfg = *cfg;
     ctx->cfg.knn_k = cfg->knn_k;
     (void)K0;
@@ -597,6 +631,78 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             l->nb_sort = ctx->nb_sort;
             l->sort_rows = ctx->sort_rows;
         }
+    }
+    if (ctx->cfg.group_jacobi) {
+        // Jacobi over groups: every view rendered once; all groups' blocks from
+        // that render; all solves at that state; then the steps applied, the
+        // position last (the rotation step turns about the primary's view
+        // direction through the unmoved centre)
+        REQUIRE(ctx, !records, GS2_ERR_UNSUPPORTED, "the logged sweep runs the groups in series");
+        REQUIRE(ctx, ctx->jb_mem != nullptr, GS2_ERR_ARG, "group_jacobi is set but its buffers are missing");
+        const DevScene dsc = make_devscene(scene);
+        for (int g = 0; g < 5; ++g)
+            RET_CUDA(ctx, cudaMemsetAsync(ctx->jb_blocks[g], 0, blocks_bytes_impl(g, scene->n, scene->sh_degree, nv),
+                                          st));
+        ctx->stat_slot = ctx->cfg.group_order[0];
+        if (lanes) {
+            ProjViews pvs;
+            pvs.nv = 0;
+            for (int i = 0; i < nv; ++i) {
+                if (vid[i] < 0) continue;
+                gs2_ctx *vc = i > 0 ? ctx->lanes[i - 1] : ctx;
+                pvs.cam[pvs.nv] = make_devcam(&vcam[i]);
+                pvs.pv[pvs.nv] = proj_view(vc->sw_proj, scene->n);
+                if (++pvs.nv == GS2_PROJ_VIEWS) {
+                    RET_CUDA(ctx, launch_project_views(dsc, pvs, ctx->cfg, st, ctx->d_status));
+                    pvs.nv = 0;
+                }
+            }
+            RET_CUDA(ctx, launch_project_views(dsc, pvs, ctx->cfg, st, ctx->d_status));
+            RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[0], st));
+            for (int i = 1; i < nv; ++i) RET_CUDA(ctx, cudaStreamWaitEvent(ctx->lane_st[i - 1], ctx->lane_ev[0], 0));
+        }
+        for (int i = 0; i < nv; ++i) {
+            if (vid[i] < 0) continue;
+            gs2_ctx *vc = (lanes && i > 0) ? ctx->lanes[i - 1] : ctx;
+            cudaStream_t vs = (lanes && i > 0) ? ctx->lane_st[i - 1] : st;
+            gs2_status rc = lanes ? GS2_OK : do_project(vc, scene, &vcam[i], vc->sw_proj, vs);
+            if (rc == GS2_OK) rc = do_raster(vc, scene->n, &vcam[i], vc->sw_proj, vc->sw_image, vc->sw_rstate, vs);
+            if (rc != GS2_OK) {
+                if (vc != ctx) ctx->err = vc->err;
+                return rc;
+            }
+            const int pe = prof_begin(vc, GS2_PROF_LOSS, vs);
+            RET_CUDA(ctx, launch_loss(vc->sw_image, vtgt[i], vcam[i].width, vcam[i].height, ctx->cfg, vc->pix_e,
+                                      vc->pix_h,
+                                      (i == 0 && losses_out) ? losses_out + 2 * ctx->cfg.group_order[0] : nullptr,
+                                      vs, ctx->d_status));
+            prof_end(vc, pe, vs);
+            const ProjView pv = proj_view(vc->sw_proj, scene->n);
+            const RasterView rv = raster_view(vc->sw_rstate, vcam[i].width, vcam[i].height);
+            for (int gi = 0; gi < 5; ++gi) {
+                const int g = ctx->cfg.group_order[gi];
+                RET_CUDA(ctx, launch_accum(vc, g, dsc, make_devcam(&vcam[i]), make_devcam(primary), pv, rv, ctx->cfg,
+                                           i, ctx->jb_blocks[g], vs));
+            }
+        }
+        if (lanes) {
+            for (int i = 1; i < nv; ++i) {
+                RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[i], ctx->lane_st[i - 1]));
+                RET_CUDA(ctx, cudaStreamWaitEvent(st, ctx->lane_ev[i], 0));
+            }
+        }
+        for (int gi = 0; gi < 5; ++gi) {
+            const int g = ctx->cfg.group_order[gi];
+            RET_CUDA(ctx, launch_solve(g, ctx->jb_blocks[g], nv, dsc, make_devcam(primary), ctx->cfg,
+                                       ctx->jb_step[g], n_failed, ctx->flags, st));
+        }
+        for (int gi = 0; gi < 5; ++gi) {
+            const int g = ctx->cfg.group_order[gi];
+            if (g != GS2_POS) RET_CUDA(ctx, launch_apply(g, ctx->jb_step[g], dsc, make_devcam(primary), ctx->cfg, st));
+        }
+        RET_CUDA(ctx, launch_apply(GS2_POS, ctx->jb_step[GS2_POS], dsc, make_devcam(primary), ctx->cfg, st));
+        ctx->stat_slot = 0;
+        return GS2_OK;
     }
     // the depth order of each view depends on the means and the camera only:
     // the first pass without a valid order sorts and keeps it, later passes

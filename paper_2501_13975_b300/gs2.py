@@ -49,7 +49,8 @@ class Config_(C.Structure):
                 ("trust_pos", C.c_float), ("trust_rot", C.c_float), ("trust_color", C.c_float),
                 ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
                 ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
-                ("precision", C.c_int32), ("gauss_newton", C.c_int32), ("group_order", C.c_int32 * 5)]
+                ("precision", C.c_int32), ("gauss_newton", C.c_int32), ("group_order", C.c_int32 * 5),
+                ("group_jacobi", C.c_int32)]
 
 
 class Tuning_(C.Structure):

@@ -62,6 +62,44 @@ def test_native_sweep_equals_call_sequence(order):
     assert torch.allclose(la, lb, rtol=1e-5, atol=0)
 
 
+def test_jacobi_over_groups_equals_call_sequence():
+    """group_jacobi: gs2_sweep = every view projected and rendered once, every
+    group accumulated from that render into its own blocks, all solved, and
+    the steps applied with the position last (individual C-ABI calls)."""
+    from paper_2501_13975_b300 import gs2
+    sc, gt, cams = _scene_setup()
+    ctx = gs2.Context(sc.n, 64, 64, 0, config=dict(group_jacobi=1))
+    ocfg = oracle_cfg(ctx.config)
+    targets = [torch.tensor(O.render(gt, c, ocfg)["image"].astype(np.float32), device="cuda") for c in cams]
+    centres = np.stack([c.center() for c in cams]).astype(np.float32)
+    sphere = ctx.bounding_sphere(gs2.DeviceScene.from_host(sc)).cpu().numpy()
+    knn = gs2.camera_knn(centres, sphere, 3)
+    t = 3
+    a = gs2.DeviceScene.from_host(sc)
+    ctx.sweep(a, cams, targets, knn, t)
+    b = gs2.DeviceScene.from_host(sc)
+    views = [t] + list(knn[t])
+    blocks = {g: ctx.blocks_buffer(g, sc.n, 0, 4) for g in gs2.GROUPS}
+    for slot, v in enumerate(views):
+        if slot == 0:
+            cam, tgt = cams[v], targets[v]
+        else:
+            cam, tgt = gs2.camera_downsample(cams[v], 2), ctx.downsample(targets[v], 2)
+        proj = ctx.project(b, cam)
+        img, rs = ctx.raster_fwd(b, cam, proj)
+        for g in gs2.GROUPS:
+            ctx.accum(g, b, cam, cams[t], proj, rs, img, tgt, slot, blocks[g])
+    steps = {g: ctx.solve(g, blocks[g], 4, b, cams[t]) for g in gs2.GROUPS}
+    for g in (gs2.ROT, gs2.SCALE, gs2.OPACITY, gs2.COLOR, gs2.POS):
+        ctx.apply(g, steps[g], b, cams[t])
+    torch.cuda.synchronize()
+    ctx.check()
+    for name in ("mean", "quat", "scale", "opacity", "sh"):
+        x, y = getattr(a, name), getattr(b, name)
+        d = float((x - y).abs().max())
+        assert d <= 1e-4 * max(1.0, float(y.abs().max())), (name, d)
+
+
 @pytest.mark.parametrize("lanes", [0, 1])
 def test_profile_counts_every_stage(lanes):
     """With profiling on, one sweep (4 views x 5 groups) times 20 binnings,
@@ -91,8 +129,9 @@ def test_profile_counts_every_stage(lanes):
     assert np.all(p["pairs"] > 0) and np.all(p["evaluations"] > 0)
 
 
-@pytest.mark.parametrize("variant", [{}, {"group_order": (4, 2, 0, 3, 1)}, {"gauss_newton": 1}],
-                         ids=["paper", "order-42031", "gauss-newton"])
+@pytest.mark.parametrize("variant", [{}, {"group_order": (4, 2, 0, 3, 1)}, {"gauss_newton": 1},
+                                     {"group_jacobi": 1}],
+                         ids=["paper", "order-42031", "gauss-newton", "jacobi-groups"])
 def test_sweep_parity_with_oracle(variant):
     """One full sweep on the GPU vs the oracle's sweep (FP64 state throughout):
     the primary loss seen by each group agrees to 1e-3 and the parameters move

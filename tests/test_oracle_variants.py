@@ -9,7 +9,11 @@ Newton blocks of the same scene are not.
 
 Group order (Sec. 5, optimisation order): a sweep with a permuted order equals
 the per-group steps (render every view, accumulate, solve, apply) composed in
-that order from the oracle's single-step routines."""
+that order from the oracle's single-step routines.
+
+Jacobi over groups (the single-render sweep variant): equals every view
+rendered once, every group accumulated and solved at that state, and the steps
+applied with the position last, composed from the same routines."""
 import numpy as np
 import pytest
 
@@ -120,3 +124,45 @@ def test_sweep_follows_group_order():
 def test_bad_group_order_rejected():
     with pytest.raises(ValueError):
         O.cfg_struct(dict(group_order=(0, 1, 2, 3, 3)))
+
+
+def _views(cams, targets, knn, t, cfg):
+    K, f = cfg["knn_k"], cfg["downsample"]
+    out = []
+    for vi in range(K + 1):
+        v = t if vi == 0 else int(knn[t, vi - 1])
+        cam, tgt = cams[v], targets[v]
+        if vi > 0 and f > 1:
+            cam, tgt = O.downsample_camera(cams[v], f), O.downsample_image(targets[v], f)
+        out.append((cam, tgt))
+    return out
+
+
+def test_jacobi_over_groups_sweep():
+    cfg = dict(O.default_config(), lambda_ssim=0.2, knn_k=2, downsample=2)
+    sc = micro_scene(5, 81, 1)
+    cams = [micro_camera(eye=(0.3 * np.cos(a), 0.3 * np.sin(a), 0.0), target=(0.0, 0.0, 4.0))
+            for a in np.linspace(0, 2 * np.pi, 4, endpoint=False)]
+    gt = micro_scene(5, 82, 1)
+    targets = np.stack([O.render(gt, c, cfg)["image"] for c in cams])
+    knn = np.array([[1, 3], [0, 2], [1, 3], [0, 2]], np.int32)
+    t = 1
+    got, losses, _ = O.sweep(sc, cams, targets, knn, t, dict(cfg, group_jacobi=1))
+    h0 = O._SceneHandle(O.scene_handle(sc))
+    acc = {q: None for q in O.GROUPS}
+    for vi, (cam, tgt) in enumerate(_views(cams, targets, knn, t, cfg)):
+        L = O.loss(O.render(h0, cam, cfg)["image"], tgt, cfg)
+        if vi == 0:
+            assert np.isclose(losses[0], L["loss"], rtol=1e-12) and np.all(losses[1:] == 0)
+        for q in O.GROUPS:
+            acc[q] = O.accum(q, h0, cam, cams[t], L["e"], L["h"], cfg, out=acc[q])
+    steps = {q: O.solve(q, h0, cams[t], acc[q]["g"], acc[q]["H"], cfg)["step"] for q in O.GROUPS}
+    want = h0
+    for q in (O.ROT, O.SCALE, O.OPACITY, O.COLOR, O.POS):
+        want = O.apply(q, want, cams[t], steps[q], cfg)
+    for name in ("mean", "quat", "scale", "opacity", "sh"):
+        a, b = getattr(got, name), getattr(want, name)
+        assert np.allclose(a, b, rtol=0, atol=1e-12 * max(1.0, np.abs(b).max())), name
+    # and it differs from the series sweep
+    ser, _, _ = O.sweep(sc, cams, targets, knn, t, cfg)
+    assert not np.allclose(ser.quat, got.quat, rtol=0, atol=1e-9)
