@@ -124,6 +124,10 @@ typedef struct {
                                (Jacobi over groups, position applied last).  Setting it allocates
                                the per-group blocks and steps in gs2_create / gs2_set_config; the
                                step-scale network and the logged sweep need the series form. */
+    float gd_lr[5];         /* per group (gs2_group index): 0 = the damped Newton step (the paper);
+                               > 0 = the first-order baseline, step -gd_lr g of the group's gradient
+                               (opacity with the barrier's), inside the same trust radii and bounds
+                               (position as a full 3D step) */
 } gs2_config;
 
 void gs2_config_default(gs2_config *cfg);

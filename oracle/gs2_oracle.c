@@ -89,6 +89,7 @@ typedef struct {
     int group_order[5]; /* the groups of a sweep in the order run (a permutation of 0..4) */
     int group_jacobi;   /* 1: one render per view and sweep; every group solved at that state,
                            the steps applied together (position last) */
+    double gd_lr[5];    /* > 0: that group takes the gradient step -gd_lr g instead of Newton's */
 } orc_config;
 
 /* Trust radii (reading; the paper fixes step size 1 and gives no safeguard):
@@ -1195,10 +1196,78 @@ static double cond_estimate(int N, const double *Hf, double damp) {
     return lmax * lmin_inv;
 }
 
+/* First-order baseline on the same blocks: the step -lr g of the group's
+ * gradient (g of Eq. local_hessian_gradient; opacity with the barrier's
+ * gradient added), kept inside the same trust radii and bounds as the Newton
+ * step: position |dp| <= trust_pos max(s) (full 3D step), rotation
+ * |theta| <= trust_rot, scaling within [s / kappa, kappa s], opacity by the
+ * fraction-to-boundary rule, colour per channel |dc| <= trust_color.  A
+ * Gaussian with no contributing pixel (g and H zero) does not move. */
+static int gradient_step(int group, const orc_scene *sc, const orc_config *cfg, const double *g, const double *Hb,
+                         double *step, int *status) {
+    const int n = sc->n, S = orc_sh_count(sc->sh_degree);
+    const double lr = cfg->gd_lr[group];
+    if (group == G_COLOR) {
+        const int NH = S * (S + 1) / 2;
+        for (int ch = 0; ch < 3; ++ch)
+            for (int k = 0; k < n; ++k) {
+                double x[16];
+                for (int i = 0; i < S; ++i) x[i] = -lr * g[((size_t)ch * S + i) * n + k];
+                trust_scale(S, x, cfg->trust_color);
+                for (int i = 0; i < S; ++i) step[((size_t)ch * S + i) * n + k] = x[i];
+                if (status) status[ch * n + k] = 0;
+                (void)NH;
+            }
+        return 0;
+    }
+    const int D = group_dims(group, S), NHg = D * (D + 1) / 2;
+    for (int k = 0; k < n; ++k) {
+        int none = 1;
+        for (int i = 0; i < D; ++i) if (g[(size_t)i * n + k] != 0.0) none = 0;
+        for (int i = 0; i < NHg; ++i) if (Hb[(size_t)i * n + k] != 0.0) none = 0;
+        for (int i = 0; i < D; ++i) step[(size_t)i * n + k] = 0.0;
+        if (status) status[k] = none ? 2 : 0;
+        if (none) continue;
+        if (group == G_POS) {
+            double x[3], smax = 0;
+            for (int i = 0; i < 3; ++i) {
+                x[i] = -lr * g[(size_t)i * n + k];
+                smax = fmax(smax, sc->scale[i * n + k]);
+            }
+            trust_scale(3, x, cfg->trust_pos * smax);
+            for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = x[i];
+        } else if (group == G_ROT) {
+            double x = -lr * g[k];
+            trust_scale(1, &x, cfg->trust_rot);
+            step[k] = x;
+        } else if (group == G_SCALE) {
+            for (int i = 0; i < 3; ++i) {
+                const double si = sc->scale[i * n + k];
+                double ns = si - lr * g[(size_t)i * n + k];
+                if (ns < si / cfg->scale_trust) ns = si / cfg->scale_trust;
+                if (ns > si * cfg->scale_trust) ns = si * cfg->scale_trust;
+                step[(size_t)i * n + k] = ns - si;
+            }
+        } else { /* opacity */
+            const double sg = sc->opacity[k], a = cfg->barrier_alpha, tau = cfg->frac_to_boundary;
+            double ns = sg - lr * (g[k] + a * (-1.0 / sg + 1.0 / (1.0 - sg)));
+            if (ns < sg - tau * sg) ns = sg - tau * sg;
+            if (ns > sg + tau * (1.0 - sg)) ns = sg + tau * (1.0 - sg);
+            step[k] = ns - sg;
+        }
+    }
+    return 0;
+}
+
 int orc_solve(int group, const orc_scene *sc, const orc_camera *primary, const orc_config *cfg, const double *g,
               const double *Hb, double *step, int *status, double *info, double *cond) {
     int n = sc->n, S = orc_sh_count(sc->sh_degree);
     int nfail = 0;
+    if (cfg->gd_lr[group] > 0.0) {
+        if (info) memset(info, 0, sizeof(double) * 3 * (size_t)n * (group == G_COLOR ? 3 : 1));
+        if (cond) memset(cond, 0, sizeof(double) * (size_t)n * (group == G_COLOR ? 3 : 1));
+        return gradient_step(group, sc, cfg, g, Hb, step, status);
+    }
     if (group == G_COLOR) {
         int NH = S * (S + 1) / 2;
         for (int ch = 0; ch < 3; ++ch)

@@ -48,7 +48,7 @@ class OrcConfig(C.Structure):
                 ("ssim_radius", C.c_int), ("knn_k", C.c_int), ("downsample", C.c_int),
                 ("scale_trust", C.c_double), ("trust_pos", C.c_double), ("trust_rot", C.c_double),
                 ("trust_color", C.c_double), ("gauss_newton", C.c_int), ("group_order", C.c_int * 5),
-                ("group_jacobi", C.c_int)]
+                ("group_jacobi", C.c_int), ("gd_lr", C.c_double * 5)]
 
 
 def default_config(**kw) -> dict:
@@ -58,7 +58,7 @@ def default_config(**kw) -> dict:
                damping_tries=6, scale_min=1e-7, ssim_c1=0.01 ** 2, ssim_c2=0.03 ** 2, ssim_sigma=1.5,
                ssim_radius=5, knn_k=3, downsample=2, scale_trust=2.0,
                trust_pos=3.0, trust_rot=0.7853981633974483, trust_color=3.5449077018110318,
-               gauss_newton=0, group_order=(0, 1, 2, 3, 4), group_jacobi=0)
+               gauss_newton=0, group_order=(0, 1, 2, 3, 4), group_jacobi=0, gd_lr=(0.0, 0.0, 0.0, 0.0, 0.0))
     cfg.update(kw)
     return cfg
 
@@ -133,6 +133,8 @@ def cfg_struct(cfg: dict | None) -> OrcConfig:
             if sorted(order) != [0, 1, 2, 3, 4]:
                 raise ValueError(f"group_order must be a permutation of 0..4: {order}")
             c.group_order = (C.c_int * 5)(*order)
+        elif k == "gd_lr":
+            c.gd_lr = (C.c_double * 5)(*[float(x) for x in d[k]])
         else:
             setattr(c, k, d[k])
     return c

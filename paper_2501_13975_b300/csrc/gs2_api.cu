@@ -57,6 +57,7 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->gauss_newton = 0;
     for (int i = 0; i < 5; ++i) c->group_order[i] = i;
     c->group_jacobi = 0;
+    for (int i = 0; i < 5; ++i) c->gd_lr[i] = 0.f;
 }
 
 static bool cfg_ok(const gs2_config *c, std::string &err) {
@@ -79,6 +80,8 @@ static bool cfg_ok(const gs2_config *c, std::string &err) {
     }
     if (seen != 31) { err = "group_order must be a permutation of the five groups"; return false; }
     if (c->group_jacobi != 0 && c->group_jacobi != 1) { err = "group_jacobi must be 0 or 1"; return false; }
+    for (int i = 0; i < 5; ++i)
+        if (!(c->gd_lr[i] >= 0.f) || !isfinite(c->gd_lr[i])) { err = "gd_lr entries must be finite and >= 0"; return false; }
     return true;
 }
 
@@ -639,6 +642,8 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         // direction through the unmoved centre)
         REQUIRE(ctx, !records, GS2_ERR_UNSUPPORTED, "the logged sweep runs the groups in series");
         REQUIRE(ctx, ctx->jb_mem != nullptr, GS2_ERR_ARG, "group_jacobi is set but its buffers are missing");
+        REQUIRE(ctx, ctx->mlp_w == nullptr, GS2_ERR_UNSUPPORTED,
+                "the step-scale network is trained on the in-series sweep; remove it for group_jacobi");
         const DevScene dsc = make_devscene(scene);
         for (int g = 0; g < 5; ++g)
             RET_CUDA(ctx, cudaMemsetAsync(ctx->jb_blocks[g], 0, blocks_bytes_impl(g, scene->n, scene->sh_degree, nv),

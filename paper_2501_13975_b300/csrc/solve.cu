@@ -558,6 +558,59 @@ __global__ void __launch_bounds__(64) k_solve_color_qr64(DevScene sc, const floa
     }
 }
 
+// First-order baseline on the same blocks: step = -lr g (opacity: g plus the
+// barrier's gradient), inside the Newton step's trust radii and bounds
+// (position as a full 3D step; colour's gradient sum_v a_v b_v rebuilt from
+// the per-view slots).  No contributing pixel (g and H zero): no step.
+__global__ void k_solve_gradient(int group, DevScene sc, const float *__restrict__ B, int n_views, float lr,
+                                 gs2_config cfg, float *step) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sc.n, S = sc.S;
+    if (k >= n) return;
+    if (group == GS2_COLOR) {
+        const size_t slot = (size_t)(6 + S) * n;
+        for (int ch = 0; ch < 3; ++ch) {
+            float x[GS2_MAX_SH];
+            for (int i = 0; i < S; ++i) x[i] = 0.f;
+            for (int v = 0; v < n_views; ++v) {
+                const float *Bv = B + v * slot;
+                const float a = Bv[(size_t)ch * n + k];
+                if (a == 0.f) continue;
+                for (int i = 0; i < S; ++i) x[i] -= lr * a * Bv[(size_t)(6 + i) * n + k];
+            }
+            trust_scale(S, x, cfg.trust_color);
+            for (int i = 0; i < S; ++i) step[(size_t)(ch * S + i) * n + k] = x[i];
+        }
+        return;
+    }
+    const int D = (group == GS2_POS || group == GS2_SCALE) ? 3 : 1, NH = D * (D + 1) / 2;
+    bool none = true;
+    for (int i = 0; i < D + NH; ++i) none = none && B[(size_t)i * n + k] == 0.f;
+    for (int i = 0; i < D; ++i) step[(size_t)i * n + k] = 0.f;
+    if (none) return;
+    if (group == GS2_POS) {
+        float x[3];
+        for (int i = 0; i < 3; ++i) x[i] = -lr * B[(size_t)i * n + k];
+        const float smax = fmaxf(sc.scale[k], fmaxf(sc.scale[n + k], sc.scale[2 * n + k]));
+        trust_scale(3, x, cfg.trust_pos * smax);
+        for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = x[i];
+    } else if (group == GS2_ROT) {
+        float x = -lr * B[k];
+        trust_scale(1, &x, cfg.trust_rot);
+        step[k] = x;
+    } else if (group == GS2_SCALE) {
+        for (int i = 0; i < 3; ++i) {
+            const float si = sc.scale[(size_t)i * n + k];
+            const float ds = -lr * B[(size_t)i * n + k];
+            step[(size_t)i * n + k] = fminf(fmaxf(ds, si / cfg.scale_trust - si), si * cfg.scale_trust - si);
+        }
+    } else {
+        const float sg = sc.opacity[k], tau = cfg.frac_to_boundary;
+        const float g = B[k] + cfg.barrier_alpha * (-1.f / sg + 1.f / (1.f - sg));
+        step[k] = fminf(fmaxf(-lr * g, -tau * sg), tau * (1.f - sg));
+    }
+}
+
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st) {
     const int n = sc.n;
@@ -565,6 +618,11 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
     const float *B = (const float *)blocks;
     float *s = (float *)step;
     const int g = (n + 255) / 256;
+    if (cfg.gd_lr[group] > 0.f) {
+        k_solve_gradient<<<g, 256, 0, st>>>(group, sc, B, n_views, cfg.gd_lr[group], cfg, s);
+        GS2_COUNT_LAUNCH(1);
+        return cudaGetLastError();
+    }
     switch (group) {
     case GS2_POS:
         k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_pos, s,

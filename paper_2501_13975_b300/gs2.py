@@ -50,7 +50,7 @@ class Config_(C.Structure):
                 ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
                 ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
                 ("precision", C.c_int32), ("gauss_newton", C.c_int32), ("group_order", C.c_int32 * 5),
-                ("group_jacobi", C.c_int32)]
+                ("group_jacobi", C.c_int32), ("gd_lr", C.c_float * 5)]
 
 
 class Tuning_(C.Structure):
@@ -140,10 +140,11 @@ def default_config(**kw) -> dict:
     _lib.gs2_config_default(C.byref(c))
     d = {k: getattr(c, k) for k, _ in Config_._fields_}
     d["group_order"] = [int(x) for x in c.group_order]
+    d["gd_lr"] = [float(x) for x in c.gd_lr]
     for k, v in kw.items():
         if k not in d:
             raise KeyError(k)
-        d[k] = [int(x) for x in v] if k == "group_order" else v
+        d[k] = [int(x) for x in v] if k == "group_order" else [float(x) for x in v] if k == "gd_lr" else v
     return d
 
 
@@ -153,6 +154,8 @@ def _config_struct(cfg: dict | None) -> Config_:
     for k, _ in Config_._fields_:
         if k == "group_order":
             c.group_order = (C.c_int32 * 5)(*[int(x) for x in d[k]])
+        elif k == "gd_lr":
+            c.gd_lr = (C.c_float * 5)(*[float(x) for x in d[k]])
         else:
             setattr(c, k, d[k])
     return c

@@ -7,7 +7,7 @@ GPU_CFG_KEYS = ("lambda_ssim", "alpha_min", "alpha_max", "t_min", "lowpass", "ne
                 "frac_to_boundary", "damping_mu0", "damping_tries", "scale_min", "scale_trust", "trust_pos",
                 "trust_rot", "trust_color", "ssim_c1",
                 "ssim_c2", "ssim_sigma", "ssim_radius", "knn_k", "downsample", "gauss_newton", "group_order",
-                "group_jacobi")
+                "group_jacobi", "gd_lr")
 
 
 def oracle_cfg(gpu_cfg: dict) -> dict:
@@ -16,6 +16,8 @@ def oracle_cfg(gpu_cfg: dict) -> dict:
         v = gpu_cfg[k]
         if k == "group_order":
             out[k] = [int(x) for x in v]
+        elif k == "gd_lr":
+            out[k] = [float(np.float32(x)) for x in v]
         else:
             out[k] = int(v) if isinstance(v, (int, np.integer)) and not isinstance(v, bool) else float(np.float32(v))
     return out

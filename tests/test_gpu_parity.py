@@ -324,6 +324,45 @@ def _random_blocks(group, n, S, rng):
 
 
 @pytest.mark.parametrize("group", [0, 1, 2, 3, 4])
+def test_gradient_step_parity_same_inputs(gs2, group):
+    """First-order baseline (gd_lr): GPU FP32 gradient step vs the oracle's
+    FP64 one on identical (FP32) blocks, with the learning rate chosen so that
+    some steps are clipped by the trust radii or bounds and some are not."""
+    rng = np.random.default_rng(200 + group)
+    n = 3000
+    sh = 3 if group == O.COLOR else 0
+    S = (sh + 1) ** 2
+    sc = synth.tiny_scene(n=n, seed=4, sh_degree=sh)
+    cams = synth.ring_cameras(4, 64)
+    primary = cams[2]
+    lr = [0.0] * 5
+    lr[group] = {0: 0.05, 1: 0.3, 2: 0.02, 3: 0.05, 4: 0.5}[group]
+    ctx, gcfg, ocfg = _setup(gs2, sc, cams, dict(gd_lr=lr))
+    ds = gs2.DeviceScene.from_host(sc)
+    if group == O.COLOR:
+        nv = 4
+        slots = np.zeros((nv, 6 + S, n), np.float32)
+        slots[:, 0:3] = rng.standard_normal((nv, 3, n))
+        slots[:, 3:6] = 10.0 ** rng.uniform(-2, 1, (nv, 3, n))
+        slots[:, 6:] = rng.standard_normal((nv, S, n))
+        g, H = _colour_full(slots.reshape(-1), nv, S, n)
+        ref = O.solve(group, sc, primary, g, H, ocfg)["step"]
+        got = ctx.solve(group, torch.tensor(slots.reshape(-1), device="cuda"), nv, ds, primary)
+        got = got.cpu().numpy()[: 3 * S * n].reshape(3, S, n)
+    else:
+        g, Hp = _random_blocks(group, n, S, rng)
+        g[:, ::17] = 0.0
+        Hp[:, ::17] = 0.0
+        blocks = torch.tensor(np.concatenate([g.reshape(-1), Hp.reshape(-1)]), device="cuda")
+        got = ctx.solve(group, blocks, 1, ds, primary).cpu().numpy().reshape(-1, n)
+        ref = O.solve(group, sc, primary, g.astype(np.float64), Hp.astype(np.float64), ocfg)["step"]
+        assert np.all(got[:, ::17] == 0)
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert np.abs(got - ref).max() <= 1e-5 * scale + 1e-30
+
+
+@pytest.mark.parametrize("group", [0, 1, 2, 3, 4])
 def test_solver_parity_same_inputs(gs2, group):
     """GPU FP32 solve vs the oracle's FP64 solve on identical (FP32) blocks:
     steps within max(1e-3, 1e-5 cond) relative; identical status decisions

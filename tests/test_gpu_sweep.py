@@ -130,8 +130,8 @@ def test_profile_counts_every_stage(lanes):
 
 
 @pytest.mark.parametrize("variant", [{}, {"group_order": (4, 2, 0, 3, 1)}, {"gauss_newton": 1},
-                                     {"group_jacobi": 1}],
-                         ids=["paper", "order-42031", "gauss-newton", "jacobi-groups"])
+                                     {"group_jacobi": 1}, {"gd_lr": (2.0, 20.0, 0.5, 2.0, 20.0)}],
+                         ids=["paper", "order-42031", "gauss-newton", "jacobi-groups", "gradient-steps"])
 def test_sweep_parity_with_oracle(variant):
     """One full sweep on the GPU vs the oracle's sweep (FP64 state throughout):
     the primary loss seen by each group agrees to 1e-3 and the parameters move

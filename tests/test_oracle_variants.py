@@ -166,3 +166,45 @@ def test_jacobi_over_groups_sweep():
     # and it differs from the series sweep
     ser, _, _ = O.sweep(sc, cams, targets, knn, t, cfg)
     assert not np.allclose(ser.quat, got.quat, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("group", O.GROUPS)
+def test_gradient_step_is_minus_lr_times_gradient(group):
+    """First-order baseline: where no trust radius or bound binds, the step is
+    exactly -lr g of the (finite-difference pinned) gradient; for opacity the
+    barrier's gradient a (-1/s + 1/(1 - s)) is included."""
+    sh = 1 if group == O.COLOR else 0
+    cfg = dict(NOTHRESH, lambda_ssim=0.2, trust_pos=1e9, trust_rot=1e9, trust_color=1e9, scale_trust=1e9,
+               frac_to_boundary=0.999999)
+    sc = micro_scene(4, 91, sh)
+    cam = micro_camera()
+    target = O.render(micro_scene(4, 191, sh), cam, cfg)["image"]
+    h = O.scene_handle(sc)
+    L = O.loss(O.render(h, cam, cfg)["image"], target, cfg)
+    blk = O.accum(group, h, cam, cam, L["e"], L["h"], cfg)
+    lr = [0.0] * 5
+    lr[group] = 1e-3
+    st = O.solve(group, h, cam, blk["g"], blk["H"], dict(cfg, gd_lr=lr))["step"]
+    want = -1e-3 * blk["g"]
+    if group == O.OPACITY:
+        s = h.opacity
+        want = -1e-3 * (blk["g"] + O.default_config(**cfg)["barrier_alpha"] * (-1.0 / s + 1.0 / (1.0 - s)))
+    assert np.abs(st.reshape(want.shape) - want).max() <= 1e-14 + 1e-12 * np.abs(want).max()
+
+
+def test_small_gradient_step_lowers_the_loss():
+    """The sign: a small step along -g lowers the loss of every group."""
+    cfg = dict(NOTHRESH, lambda_ssim=0.2)
+    sc = micro_scene(4, 93, 1)
+    cam = micro_camera()
+    target = O.render(micro_scene(4, 193, 1), cam, cfg)["image"]
+    h = O.scene_handle(sc)
+    L0 = O.loss(O.render(h, cam, cfg)["image"], target, cfg)
+    for group in O.GROUPS:
+        blk = O.accum(group, h, cam, cam, L0["e"], L0["h"], cfg)
+        lr = [0.0] * 5
+        lr[group] = 1e-2 / max(np.abs(blk["g"]).max(), 1e-12) * 1e-3
+        st = O.solve(group, h, cam, blk["g"], blk["H"], dict(cfg, gd_lr=lr))["step"]
+        h1 = O.apply(group, h, cam, st, cfg)
+        L1 = O.loss(O.render(h1, cam, cfg)["image"], target, cfg, derivs=False)["loss"]
+        assert L1 < L0["loss"], (group, L1, L0["loss"])
