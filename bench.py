@@ -979,7 +979,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v6"
+KERNEL_REV = "accum-v7"
 
 
 def main():
