@@ -238,12 +238,20 @@ gs2_status gs2_bounding_sphere(gs2_ctx *ctx, const gs2_scene *scene, float *sphe
 gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const float *sphere, int32_t k, int32_t *out);
 
 /* One sweep for primary image t (Sec. 4.2 group order, Sec. 4.3 Eq. tildel):
- * for each group in order, render the primary (full resolution) and its k
- * secondaries (downsampled), accumulate, solve, apply.  Uses only ctx
+ * for each group in cfg.group_order, render the primary (full resolution) and
+ * its k secondaries (downsampled), accumulate, solve, apply.  The views of a
+ * group run concurrently on the context's view lanes (tuning.view_lanes).
+ * The configuration selects the variants: cfg.gauss_newton (Gauss-Newton
+ * blocks), cfg.gd_lr (gradient steps instead of Newton's for the groups with
+ * a positive rate), cfg.group_jacobi (every view rendered once, all groups
+ * solved at that state and applied together, position last).  Uses only ctx
  * scratch.  cams: host [ncam]; targets: host array of ncam device pointers to
- * full-resolution [3][H][W] images; knn: host [ncam][knn_k].
+ * full-resolution [3][H][W] images (only the primary's and its secondaries'
+ * entries are read); knn: host [ncam][knn_k].
  * losses_out: device double[5][2], (L2, L_S) of the primary view seen by each
- * group (+=), may be NULL.  n_failed: device int (+=), may be NULL. */
+ * group, indexed by group (+=; with group_jacobi only the slot of the first
+ * group of the order, from the sweep's single render), may be NULL.
+ * n_failed: device int (+=), may be NULL. */
 gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                      const float *const *targets, const int32_t *knn, int32_t t, double *losses_out,
                      int32_t *n_failed, gs2_stream stream);
