@@ -343,12 +343,12 @@ gs2_status gs2_mlp_adam(float *master, uint16_t *w_bf16, const float *partial, c
 /* Kernel tuning of a context (no effect on results beyond the order of
  * floating-point additions: the sort is stable and exact for every setting).
  *   sort_blocks: CTAs of every radix-sort pass (1..1024; default 592)
- *   sort_rows:   keys per thread per scatter round (2, 4 or 8; default 4)
+ *   sort_rows:   keys per thread per scatter round (2, 4, 8 or 16; default 4)
  *   view_lanes:  1 (default): a sweep runs the views of each group
  *                concurrently on streams of the context (one per secondary);
  *                0: one after another on the caller's stream
  * gs2_autotune times `reps` sweeps with primary t for every candidate
- * (sort_blocks 296, 592, 888 x sort_rows 2, 4, 8; view_lanes kept) on a scratch copy of the
+ * (sort_blocks 296, 592, 888 x sort_rows 2, 4, 8, 16; view_lanes kept) on a scratch copy of the
  * scene (the caller's scene is not changed), keeps the fastest in ctx and
  * returns it and its ms per sweep (host outputs, may be NULL).  It allocates
  * the copy, synchronises the stream and must not run under stream capture. */

@@ -55,7 +55,7 @@ extern "C" gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out) {
 extern "C" gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *t) {
     if (!ctx || !t) return GS2_ERR_ARG;
     if (t->sort_blocks < 1 || t->sort_blocks > GS2_SORT_BLOCKS_MAX) return GS2_ERR_ARG;
-    if (t->sort_rows != 2 && t->sort_rows != 4 && t->sort_rows != 8) return GS2_ERR_ARG;
+    if (t->sort_rows != 2 && t->sort_rows != 4 && t->sort_rows != 8 && t->sort_rows != 16) return GS2_ERR_ARG;
     if (t->view_lanes != 0 && t->view_lanes != 1) return GS2_ERR_ARG;
     ctx->nb_sort = t->sort_blocks;
     ctx->sort_rows = t->sort_rows;
@@ -93,10 +93,10 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
     gs2_tuning best = keep;
     float best_ms = 1e30f;
     const int blocks[3] = {148 * 2, 148 * 4, 148 * 6};
-    const int rows[3] = {2, 4, 8};
+    const int rows[4] = {2, 4, 8, 16};
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = GS2_ERR_CUDA;
     for (int bi = 0; bi < 3 && rc == GS2_OK; ++bi)
-        for (int ri = 0; ri < 3 && rc == GS2_OK; ++ri) {
+        for (int ri = 0; ri < 4 && rc == GS2_OK; ++ri) {
             ctx->nb_sort = blocks[bi];
             ctx->sort_rows = rows[ri];
             if (!reset()) { rc = GS2_ERR_CUDA; break; }

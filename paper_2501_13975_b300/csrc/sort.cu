@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *ghist, int nb, ui
     if (t == 0) dtot[d] = tot;
 }
 
-// ROWS keys per thread per 256-thread round (a tuning parameter: 2, 4 or 8)
+// ROWS keys per thread per 256-thread round (a tuning parameter: 2, 4, 8 or 16)
 template <int ROWS>
 __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
@@ -328,6 +328,9 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
         else if (rows == 8)
             k_scatter<8><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
                                                       ghist, nb, dtot);
+        else if (rows == 16)
+            k_scatter<16><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
+                                                       ghist, nb, dtot);
         else
             k_scatter<4><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
                                                       ghist, nb, dtot);

@@ -140,7 +140,7 @@ def test_autotune_keeps_scene_and_results():
     _close(ds, ref, before)
 
 
-@pytest.mark.parametrize("blocks,rows", [(148, 2), (296, 8), (1024, 4), (7, 4)])
+@pytest.mark.parametrize("blocks,rows", [(148, 2), (296, 8), (1024, 4), (7, 4), (592, 16), (3, 16)])
 def test_tuning_does_not_change_binning(blocks, rows):
     """The radix sort is exact for every tuning: identical tile lists."""
     from paper_2501_13975_b300 import gs2
