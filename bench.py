@@ -536,11 +536,13 @@ def method_variants(args):
 
     torch.cuda.set_device(0)
     w, gt_host, start_host, cams = make_workload("object")
-    if args.variants_n:
-        # the same shell with fewer Gaussians: less overlap between them
-        w = dict(w, n=args.variants_n)
-        gt_host = synth.object_scene(seed=3, n=args.variants_n)
-        start_host = synth.perturbed(gt_host, seed=4, sd=0.02)
+    if args.variants_n or args.variants_sd:
+        # the same shell with fewer Gaussians (less overlap between them) and/or
+        # a start closer to the target (smaller perturbation of the means)
+        if args.variants_n:
+            w = dict(w, n=args.variants_n)
+            gt_host = synth.object_scene(seed=3, n=args.variants_n)
+        start_host = synth.perturbed(gt_host, seed=4, sd=args.variants_sd or 0.02)
     # mean overlap of the shell: Gaussians covering a point of it, taking each
     # footprint as a disc of radius 2 s (s = its mean scale)
     s_mean = np.exp(np.log(gt_host.scale.astype(np.float64)).mean(axis=0))
@@ -552,6 +554,13 @@ def method_variants(args):
     variants = [("paper", {}), ("K=0", dict(knn_k=0)), ("K=8", dict(knn_k=8)),
                 ("colour-first", dict(group_order=(4, 3, 2, 1, 0))), ("gauss-newton", dict(gauss_newton=1)),
                 ("jacobi-groups", dict(group_jacobi=1))]
+    if args.variants_only:
+        variants = [v for v in variants if v[0] in args.variants_only.split(",")]
+    extra = {}
+    for kv in filter(None, args.variants_cfg.split(",")):
+        k, v = kv.split("=")
+        extra[k] = float(v) if "." in v or "e" in v else int(v)
+    variants = [(name, dict(extra, **cfg)) for name, cfg in variants]
     sweeps = 30
     out = {}
     for name, cfg in variants:
@@ -600,7 +609,7 @@ def method_variants(args):
     return {"metric": "PSNR over all views after 30 sweeps, per method variant (object workload)",
             "value": out["paper"]["psnr_after_30"], "unit": "dB", "higher_is_better": True,
             "config": {"workload": f"object: {w['n']} Gaussians on a unit-sphere shell, SH degree 3, 100 cameras "
-                                   "800x800 on a hemisphere; start: means perturbed N(0, 0.02^2)",
+                                   f"800x800 on a hemisphere; start: means perturbed N(0, {args.variants_sd or 0.02}^2)",
                        "gaussians": w["n"], "shell_overlap": round(overlap, 1),
                        "primaries": "seeded permutation (seed 5)"},
             "data": "synthetic", "dtype": "f32", "variants": out}
@@ -1004,6 +1013,10 @@ def main():
     ap.add_argument("--gd", action="store_true",
                     help="first-order baseline (gradient steps) on the object workload vs one Newton sweep")
     ap.add_argument("--variants-n", type=int, default=0, help="Gaussians of the object shell for --variants")
+    ap.add_argument("--variants-sd", type=float, default=0.0,
+                    help="perturbation of the start's means for --variants (default 0.02, the workload's)")
+    ap.add_argument("--variants-only", default="", help="comma-separated variant names for --variants")
+    ap.add_argument("--variants-cfg", default="", help="config overrides for every variant, key=value,...")
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")

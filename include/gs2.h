@@ -102,10 +102,10 @@ typedef struct {
     float damping_mu0;      /* first damping factor mu0 (1.0) */
     int32_t damping_tries;  /* extra x10 damping attempts (6) */
     float scale_min;        /* floor of any scale (1e-7) */
-    float scale_trust;      /* scale update bounded to [s/k, k s] (2.0) */
-    float trust_pos;        /* |dp| <= trust_pos * max(s) (3.0) */
-    float trust_rot;        /* |theta| <= trust_rot (pi/4) */
-    float trust_color;      /* per-channel SH step norm <= trust_color (2 sqrt(pi)) */
+    float scale_trust;      /* scale update bounded to [s/k, k s] (1.05) */
+    float trust_pos;        /* |dp| <= trust_pos * max(s) (0.05) */
+    float trust_rot;        /* |theta| <= trust_rot (0.05) */
+    float trust_color;      /* per-channel SH step norm <= trust_color (0.05) */
     float ssim_c1, ssim_c2; /* 0.01^2, 0.03^2 */
     float ssim_sigma;       /* Gaussian window sigma (1.5) */
     int32_t ssim_radius;    /* window radius (5: 11x11); only 5 is supported */

@@ -56,8 +56,8 @@ def default_config(**kw) -> dict:
     cfg = dict(lambda_ssim=0.2, alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, lowpass=0.3,
                near_z=0.2, barrier_alpha=1e-6, frac_to_boundary=0.99, damping_mu0=1.0,
                damping_tries=6, scale_min=1e-7, ssim_c1=0.01 ** 2, ssim_c2=0.03 ** 2, ssim_sigma=1.5,
-               ssim_radius=5, knn_k=3, downsample=2, scale_trust=2.0,
-               trust_pos=3.0, trust_rot=0.7853981633974483, trust_color=3.5449077018110318,
+               ssim_radius=5, knn_k=3, downsample=2, scale_trust=1.05,
+               trust_pos=0.05, trust_rot=0.05, trust_color=0.05,
                gauss_newton=0, group_order=(0, 1, 2, 3, 4), group_jacobi=0, gd_lr=(0.0, 0.0, 0.0, 0.0, 0.0))
     cfg.update(kw)
     return cfg

@@ -43,10 +43,10 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->damping_mu0 = 1.0f;
     c->damping_tries = 6;
     c->scale_min = 1e-7f;
-    c->scale_trust = 2.0f;
-    c->trust_pos = 3.0f;
-    c->trust_rot = 0.78539816339744831f;
-    c->trust_color = 3.5449077018110318f;
+    c->scale_trust = 1.05f;
+    c->trust_pos = 0.05f;
+    c->trust_rot = 0.05f;
+    c->trust_color = 0.05f;
     c->ssim_c1 = 1e-4f;
     c->ssim_c2 = 9e-4f;
     c->ssim_sigma = 1.5f;

@@ -316,7 +316,7 @@ def test_learned_step_bounds_and_fallback():
     d[:, :5] *= 0.5                                            # |d| = max(s) for half
     p = np.zeros(Lr.NPARAM)
     p[Lr.OFF_B3] = 40.0                                        # alpha = 2 to double precision
-    cfg = O.default_config()
+    cfg = O.default_config(trust_pos=3.0)                      # |d| and 2|d| on either side of it
     out = Lr.learned_step(O.POS, g, Hu, d, sc, cfg, p)
     n_out = np.linalg.norm(out, axis=0)
     assert np.allclose(n_out[:5], 2.0 * smax[:5], rtol=1e-12)

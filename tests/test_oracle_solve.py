@@ -3,6 +3,7 @@ position / scaling / rotation / opacity / colour solves of Sec. 4.2)."""
 import math
 
 import numpy as np
+import pytest
 import scipy.linalg
 from scipy.spatial.transform import Rotation
 
@@ -197,7 +198,9 @@ def _isolated(group, sh_degree=0):
     tgt.mean[:, 0] = [0.05, -0.03, 4.0]
     tgt.scale = sc.scale.copy()
     tgt.quat = sc.quat.copy()
-    cfg = dict(NOTHRESH, lambda_ssim=0.0, barrier_alpha=0.0, damping_mu0=0.0)
+    # the undamped Newton step, no trust radius in the way (these pins are about the step itself)
+    cfg = dict(NOTHRESH, lambda_ssim=0.0, barrier_alpha=0.0, damping_mu0=0.0, trust_pos=1e30, trust_rot=1e30,
+               trust_color=1e30, scale_trust=1e30)
     target = O.render(tgt, cam, cfg)["image"]
     return cam, sc, target, cfg
 
@@ -273,14 +276,21 @@ def test_barrier_terms():
     assert math.isclose(r["step"][0, 0], -(0.2 + Bp) / (3.0 + Bpp), rel_tol=1e-12)
 
 
-def test_sweep_reduces_loss_tiny():
+@pytest.mark.parametrize("radii,factor", [({}, 0.8),
+                                          (dict(trust_pos=3.0, scale_trust=2.0, trust_rot=0.785,
+                                                trust_color=3.545), 0.5)],
+                         ids=["default-radii", "loose-radii"])
+def test_sweep_reduces_loss_tiny(radii, factor):
     """Behaviour (not a parity pin): a few sweeps on a small tiny-scene variant
-    reduce the total L2+SSIM loss over the training views (default damping
-    mu0 = 1 and scale trust 2; mu0 = 1e-4 diverges on this scene)."""
+    reduce the total L2+SSIM loss over the training views (damping mu0 = 1;
+    mu0 = 1e-4 diverges on this scene).  The default trust radii bound every
+    step tightly (they keep the object workload converging), so four sweeps
+    cut the loss less than with looser radii, which this small scene also
+    tolerates."""
     sc = synth.tiny_scene(n=300)
     gt = synth.perturbed(sc, seed=2, sd=0.05)
     cams = synth.ring_cameras(4, 64)
-    cfg = dict(knn_k=3)
+    cfg = dict(knn_k=3, **radii)
     targets = np.stack([O.render(gt, c, cfg)["image"] for c in cams])
     sphere = O.bounding_sphere(sc)
     nb, _ = O.knn(np.stack([c.center() for c in cams]), sphere, 3)
@@ -294,7 +304,7 @@ def test_sweep_reduces_loss_tiny():
     for t in range(4):
         h, losses, nfail = O.sweep(h, cams, targets, nb, t, cfg)
     L1 = total(h)
-    assert L1 < 0.5 * L0, (L0, L1)
+    assert L1 < factor * L0, (L0, L1)
 
 
 def test_trust_radii_scale_steps_down():
