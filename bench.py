@@ -42,8 +42,10 @@ GROUP_NAMES = ("position", "rotation", "scaling", "opacity", "colour")
 # FP32 operations of the accumulation per evaluated (pixel, Gaussian) pair:
 # 46 common (falloff and alpha 14, T_k 2, weight 1, colour-behind terms 6,
 # e.a 5, h.a^2 8, C_back update 10) + the group's payload + its P warp-sum adds:
-# position 232 + 41, rotation / scaling 124 + 9, opacity 3 + 2, colour 9 + 6
-EVAL_FLOPS = (319, 179, 179, 51, 61)
+# position 197 + 41 (falloff derivatives over G 61, scaled terms 20, Hessian
+# entries 61, colour cross terms 42, colour 13), rotation / scaling 80 + 9
+# (falloff derivatives 43, payload 37), opacity 3 + 2, colour 9 + 6
+EVAL_FLOPS = (284, 135, 135, 51, 61)
 # FP32 peak: 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 PAYLOAD_FLOATS = (41, 9, 9, 2, 6)       # image-space accumulator floats per Gaussian and view
@@ -988,7 +990,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v7"
+KERNEL_REV = "accum-v8"
 
 
 def main():

@@ -20,11 +20,13 @@
 #include "sh.cuh"
 
 template <int G> struct Payload;
-template <> struct Payload<GS2_POS> { static constexpr int P = 41; };
-template <> struct Payload<GS2_ROT> { static constexpr int P = 9; };
-template <> struct Payload<GS2_SCALE> { static constexpr int P = 9; };
-template <> struct Payload<GS2_OPACITY> { static constexpr int P = 2; };
-template <> struct Payload<GS2_COLOR> { static constexpr int P = 6; };
+// P: accumulator floats per Gaussian and view; MIN_CTAS: resident CTAs per SM
+// the register allocation is held to (65536 / (MIN_CTAS x 128) registers a thread)
+template <> struct Payload<GS2_POS> { static constexpr int P = 41, MIN_CTAS = 4; };
+template <> struct Payload<GS2_ROT> { static constexpr int P = 9, MIN_CTAS = 7; };
+template <> struct Payload<GS2_SCALE> { static constexpr int P = 9, MIN_CTAS = 7; };
+template <> struct Payload<GS2_OPACITY> { static constexpr int P = 2, MIN_CTAS = 8; };
+template <> struct Payload<GS2_COLOR> { static constexpr int P = 6, MIN_CTAS = 8; };
 
 // packed upper-triangle index of a 5x5 / 3x3 symmetric matrix
 __host__ __device__ constexpr int ut5(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i); }
@@ -32,41 +34,44 @@ __host__ __device__ constexpr int ut3(int i, int j) { return i * 3 - i * (i - 1)
 
 // Derivatives of G = exp(-1/2 d^T A d), d = x - pi, A = Sigma^{-1}, w.r.t.
 // pi (2) and the covariance parameters (Sxx, Sxy, Syy) (Sxy counted once, the
-// matrix entries (0,1) and (1,0) both move):
+// matrix entries (0,1) and (1,0) both move), returned divided by G:
 //   u = A d; dG/dpi = G u; d2G/dpi2 = G (u u^T - A);
-//   q_t = -u^T E_t u, dG/dS_t = -G q_t / 2;
-//   d2G/dS_t dS_f = G (q_t q_f / 4 - v_t^T A v_f), v_t = E_t u;
-//   d2G/dpi dS_t = G (-u q_t / 2 - A v_t).
+//   r_t = u^T E_t u / 2 (r = (ux^2/2, ux uy, uy^2/2)), dG/dS_t = G r_t;
+//   d2G/dS_t dS_f = G (r_t r_f - v_t^T A v_f), v_t = E_t u
+//     (v_0 = (ux, 0), v_1 = (uy, ux), v_2 = (0, uy));
+//   d2G/dpi_a dS_t = G (u_a r_t - (A v_t)_a).
+// The zero components of v_t are left out of the products, and the common
+// factor G is applied by the caller together with sigma (sigma G = alpha).
 template <bool WITH_PI>
-__device__ __forceinline__ void falloff_derivs(float G, float ca, float cb, float cc, float dx, float dy, float gz[5],
-                                               float gzz[15]) {
+__device__ __forceinline__ void falloff_unit(float ca, float cb, float cc, float dx, float dy, float gz[5],
+                                             float gzz[15]) {
     const float ux = ca * dx + cb * dy, uy = cb * dx + cc * dy;
-    const float q[3] = {-ux * ux, -2.f * ux * uy, -uy * uy};
-    const float v[3][2] = {{ux, 0.f}, {uy, ux}, {0.f, uy}};
-    float Av[3][2];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        Av[t][0] = ca * v[t][0] + cb * v[t][1];
-        Av[t][1] = cb * v[t][0] + cc * v[t][1];
-    }
-#pragma unroll
-    for (int t = 0; t < 3; ++t) gz[2 + t] = -0.5f * G * q[t];
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-#pragma unroll
-        for (int f = t; f < 3; ++f)
-            gzz[ut5(2 + t, 2 + f)] = G * (0.25f * q[t] * q[f] - (v[t][0] * Av[f][0] + v[t][1] * Av[f][1]));
+    const float r0 = 0.5f * ux * ux, r1 = ux * uy, r2 = 0.5f * uy * uy;
+    // A v_t
+    const float a0x = ca * ux, a0y = cb * ux;
+    const float a1x = ca * uy + cb * ux, a1y = cb * uy + cc * ux;
+    const float a2x = cb * uy, a2y = cc * uy;
+    gz[2] = r0;
+    gz[3] = r1;
+    gz[4] = r2;
+    gzz[ut5(2, 2)] = r0 * r0 - ux * a0x;
+    gzz[ut5(2, 3)] = r0 * r1 - ux * a1x;
+    gzz[ut5(2, 4)] = r0 * r2 - ux * a2x;
+    gzz[ut5(3, 3)] = r1 * r1 - (uy * a1x + ux * a1y);
+    gzz[ut5(3, 4)] = r1 * r2 - (uy * a2x + ux * a2y);
+    gzz[ut5(4, 4)] = r2 * r2 - uy * a2y;
     if (WITH_PI) {
-        gz[0] = G * ux;
-        gz[1] = G * uy;
-        gzz[ut5(0, 0)] = G * (ux * ux - ca);
-        gzz[ut5(0, 1)] = G * (ux * uy - cb);
-        gzz[ut5(1, 1)] = G * (uy * uy - cc);
-        const float u[2] = {ux, uy};
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int t = 0; t < 3; ++t) gzz[ut5(a, 2 + t)] = G * (-0.5f * u[a] * q[t] - Av[t][a]);
+        gz[0] = ux;
+        gz[1] = uy;
+        gzz[ut5(0, 0)] = ux * ux - ca;
+        gzz[ut5(0, 1)] = ux * uy - cb;
+        gzz[ut5(1, 1)] = uy * uy - cc;
+        gzz[ut5(0, 2)] = ux * r0 - a0x;
+        gzz[ut5(0, 3)] = ux * r1 - a1x;
+        gzz[ut5(0, 4)] = ux * r2 - a2x;
+        gzz[ut5(1, 2)] = uy * r0 - a0y;
+        gzz[ut5(1, 3)] = uy * r1 - a1y;
+        gzz[ut5(1, 4)] = uy * r2 - a2y;
     }
 }
 
@@ -172,32 +177,40 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
         pl[5] += w * w * h[2];
     } else if (GROUP == GS2_ROT || GROUP == GS2_SCALE) {
         if (!clamped) {
+            // not clamped: alpha = sigma G, the factor of every falloff derivative
             float gz[5], gzz[15];
-            falloff_derivs<false>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
-            const float sg = B.y;
+            falloff_unit<false>(A.z, A.w, B.x, dx, dy, gz, gzz);
+            float az[3], bz[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) pl[i] += Ea * sg * gz[2 + i];
+            for (int i = 0; i < 3; ++i) {
+                az[i] = alpha * gz[2 + i];
+                bz[i] = Ah * az[i];
+                pl[i] += Ea * az[i];
+            }
+            const float ez = Es * alpha;
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int jx = i; jx < 3; ++jx)
-                    pl[3 + ut3(i, jx)] += Ah * sg * sg * gz[2 + i] * gz[2 + jx] + Es * sg * gzz[ut5(2 + i, 2 + jx)];
+                    pl[3 + ut3(i, jx)] += bz[i] * az[jx] + ez * gzz[ut5(2 + i, 2 + jx)];
         }
     } else {  // position
         const float aa[3] = {a0, a1, a2};
         if (!clamped) {
             float gz[5], gzz[15];
-            falloff_derivs<true>(G, A.z, A.w, B.x, dx, dy, gz, gzz);
-            const float sg = B.y;
-            float az[5];
+            falloff_unit<true>(A.z, A.w, B.x, dx, dy, gz, gzz);
+            float az[5], bz[5];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) az[i] = sg * gz[i];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) pl[i] += Ea * az[i];
+            for (int i = 0; i < 5; ++i) {
+                az[i] = alpha * gz[i];
+                bz[i] = Ah * az[i];
+                pl[i] += Ea * az[i];
+            }
+            const float ez = Es * alpha;
 #pragma unroll
             for (int i = 0; i < 5; ++i)
 #pragma unroll
-                for (int jx = i; jx < 5; ++jx) pl[5 + ut5(i, jx)] += Ah * az[i] * az[jx] + Es * sg * gzz[ut5(i, jx)];
+                for (int jx = i; jx < 5; ++jx) pl[5 + ut5(i, jx)] += bz[i] * az[jx] + ez * gzz[ut5(i, jx)];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float xc = h[c] * aa[c] * w + (gn ? 0.f : e[c] * Tk);
@@ -218,7 +231,7 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
 }
 
 template <int GROUP, typename ACC>
-__global__ void __launch_bounds__(GS2_PAIR_THREADS) k_accum(const uint2 *__restrict__ ranges,
+__global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_accum(const uint2 *__restrict__ ranges,
                                                            const uint32_t *__restrict__ ids, ProjView pv,
                                                            RasterView rv, const float *__restrict__ E,
                                                            const float *__restrict__ Hh, int W, int H, int tiles_x,
