@@ -328,7 +328,7 @@ def run_gpu(args, rank, world, local_rank):
     n_acc = int(prof["accum_launches"].sum())
     alg_bytes = 0.0
     for g in range(5):
-        alg_bytes += (PIXEL_BYTES * float(prof["pixels"][g]) + RECORD_BYTES * float(prof["pairs"][g])
+        alg_bytes += (PIXEL_BYTES * float(prof["pixels"][g]) + RECORD_BYTES * float(prof["listed"][g])
                       + 8.0 * PAYLOAD_FLOATS[g] * float(prof["visible"][g]))
     flops = sum(EVAL_FLOPS[g] * float(prof["evaluations"][g]) for g in range(5))
     hbm_gbs = alg_bytes / (accum_ms * 1e-3) / 1e9 if accum_ms > 0 else 0.0
@@ -355,19 +355,24 @@ def run_gpu(args, rank, world, local_rank):
                 "measured_in": "untimed pass with the views of a group one after another "
                                f"({ms_serial / args.steps:.2f} ms/sweep; the timed sweeps run them concurrently)",
                 "pairs_per_sweep": int(prof["pairs"].sum()) // max(args.steps, 1),
+                "listed_pairs_per_sweep": int(prof["listed"].sum()) // max(args.steps, 1),
                 "visible_per_binning": int(prof["visible"].sum()) // max(int(prof["binnings"].sum()), 1)}
     # ---------------- the other stages, reported separately (same serial pass):
     # algorithmic bytes per sweep against the measured HBM peak
     binn = prof["binnings"].astype(np.float64)
-    pairs = float(prof["pairs"].sum())
+    pairs = float(prof["pairs"].sum())       # sorted: one per tile of each support rectangle
+    listed = float(prof["listed"].sum())     # in the tile lists: tiles the support ellipse reaches
+    visible = float(prof["visible"].sum())
     pixels = float(prof["pixels"].sum())
     depth_sorts = float(binn[0] + binn[1])   # the position and rotation passes sort by depth
     stage_bytes = {
         # emit 8 B, two tile radix passes (4 B histogram read + 8 B read + 8 B written), ranges 4 B per
-        # pair; four depth radix passes of 20 B per Gaussian; tiles-touched gather and offsets 12 B
-        "binning": pairs * (8 + 2 * 20 + 4) + depth_sorts * w["n"] * 4 * 20 + float(binn.sum()) * w["n"] * 12,
+        # sorted pair; four depth radix passes of 20 B per Gaussian; tiles-touched gather and offsets
+        # 12 B per Gaussian; the support ellipse's parameters read by the emission, 24 B per visible one
+        "binning": pairs * (8 + 2 * 20 + 4) + depth_sorts * w["n"] * 4 * 20 + float(binn.sum()) * w["n"] * 12
+                   + visible * 24,
         # per pixel 12 B image + 8 B state written; per listed pair 4 B id + 48 B staged record
-        "compositing": pixels * 20 + pairs * 52,
+        "compositing": pixels * 20 + listed * 52,
         # per pixel c, target read (24 B), e, h written (24 B)
         "loss": pixels * 48,
     }

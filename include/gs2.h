@@ -408,9 +408,11 @@ gs2_status gs2_batch_sweep(gs2_batch *batch, gs2_scene *scenes, const gs2_camera
  *   stops.  Synchronises the device.  Event durations of views that run
  *   concurrently overlap: time with tuning.view_lanes = 0 for per-stage
  *   figures.
- * gs2_profile_read: per group (host arrays [5], stats [5][5]: pairs, visible
- *   Gaussians, binnings, pixels, accumulation evaluations = (pixel, Gaussian)
- *   pairs with alpha >= alpha_min that the accumulation processed) after
+ * gs2_profile_read: per group (host arrays [5], stats [5][6]: sorted pairs
+ *   (one per tile of each support rectangle), visible Gaussians, binnings,
+ *   pixels, accumulation evaluations = (pixel, Gaussian) pairs with alpha >=
+ *   alpha_min that the accumulation processed, listed pairs (those whose tile
+ *   the support ellipse reaches: the tile lists' total length)) after
  *   synchronising the device.
  * gs2_profile_read_stages: host arrays [3] (binning, compositing, loss
  *   derivatives): summed event milliseconds and the number of timed stages,

@@ -794,7 +794,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     const int n = sc.n;
     ACC *zb = (ACC *)ctx->zbuf;
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
-    unsigned long long *act = pc->prof_on ? pc->d_stats + 4 * group + 3 : nullptr;
+    unsigned long long *act = pc->prof_on ? pc->d_stats + 5 * group + 3 : nullptr;
 #define ACC_LAUNCH(G)                                                                                             \
     k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
                                                    view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, cfg.gauss_newton, \

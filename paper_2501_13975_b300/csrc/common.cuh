@@ -35,16 +35,68 @@ static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Layout of the caller-owned projection buffer (opaque to callers).
 struct ProjView {
     float4 *recA;      // (pi_x, pi_y, conic_xx, conic_xy)
-    float4 *recB;      // (conic_yy, sigma, depth, 0)
-    float4 *col;       // (c~_r, c~_g, c~_b, 0)
+    float4 *recB;      // (conic_yy, sigma, depth, k2 = det Sigma / Sigma_yy^2)
+    float4 *col;       // (c~_r, c~_g, c~_b, ry = padded half height of the support)
     uint2 *rect;       // tile rectangle: x = tx0 | ty0 << 16, y = tx1 | ty1 << 16 (exclusive ends)
-    uint32_t *touched; // number of tiles in rect (0 = not rendered)
+    uint32_t *touched; // tiles of rect that the support ellipse reaches (0 = not rendered)
     uint32_t *key;     // FP32 bit pattern of the camera depth (positive)
     uint32_t *offs;    // exclusive prefix sum of touched, in depth-rank order
     uint32_t *dk[2];   // depth-sort keys (ping-pong)
     uint32_t *dv[2];   // depth-sort values: Gaussian ids, finally in depth-rank order
     uint32_t *tsort;   // touched in depth-rank order
 };
+
+// ----------------------------------------------------- support ellipse per tile row
+// The support of a Gaussian, { d : d^T Sigma^-1 d <= l }, l = 2 ln(sigma / alpha_min),
+// is the pixel set where alpha >= alpha_min.  Row by row (y relative to the centre)
+// it is |x - k1 y| <= sqrt(k2 (ry^2 - y^2)) with k1 = Sigma_xy / Sigma_yy = -conic_xy /
+// conic_xx, k2 = det Sigma / Sigma_yy^2 and ry^2 = l Sigma_yy (padded: ry carries the
+// tile rectangle's margin).  Over the band of pixel rows of one tile row, the largest
+// x is reached at the row nearest the rightmost point of the ellipse (y* = k1 ry /
+// sqrt(k2 + k1^2); x is concave in y there) and the smallest at the row nearest
+// -y*.  A margin of 1e-3 of the extents + 0.05 px covers FP32 rounding of Sigma
+// and of this evaluation, so a tile is dropped only when no pixel of it can
+// reach alpha_min.
+struct SupportRows {
+    float px, py, k1, k2, ry, ystar, marg;
+};
+
+// sqrt.approx (exact 0 at 0); its error is far inside the margin
+__device__ __forceinline__ float approx_sqrt(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ SupportRows support_rows(float px, float py, float ca, float cb, float k2, float ry) {
+    SupportRows s;
+    s.px = px;
+    s.py = py;
+    s.k2 = k2;
+    s.ry = ry;
+    s.k1 = __fdividef(-cb, ca);
+    s.ystar = s.k1 * ry * rsqrtf(k2 + s.k1 * s.k1);
+    s.marg = 0.05f + 1e-3f * (fabsf(s.k1) + approx_sqrt(k2)) * ry;
+    return s;
+}
+
+// Does the support reach a pixel of tile (tx, ty)?
+__device__ __forceinline__ bool support_reaches(const SupportRows &s, uint32_t tx, uint32_t ty) {
+    const float ylo = fmaxf((float)(ty * GS2_TILE), ceilf(s.py - s.ry));
+    const float yhi = fminf((float)(ty * GS2_TILE + GS2_TILE - 1), floorf(s.py + s.ry));
+    if (!(ylo <= yhi)) return false;
+    const float ya = ylo - s.py, yb = yhi - s.py;
+    const float yr = fminf(fmaxf(s.ystar, ya), yb), yl = fminf(fmaxf(-s.ystar, ya), yb);
+    const float r2 = s.ry * s.ry;
+    const float hr = approx_sqrt(fmaxf(s.k2 * (r2 - yr * yr), 0.f));
+    const float hl = approx_sqrt(fmaxf(s.k2 * (r2 - yl * yl), 0.f));
+    const float xr = s.px + s.k1 * yr + hr + s.marg;   // rightmost reach in the band
+    const float xl = s.px + s.k1 * yl - hl - s.marg;   // leftmost
+    // some integer pixel column of the tile lies in [xl, xr]
+    const float c0 = fmaxf(ceilf(xl), (float)(tx * GS2_TILE));
+    const float c1 = fminf(floorf(xr), (float)(tx * GS2_TILE + GS2_TILE - 1));
+    return c0 <= c1;
+}
 
 static inline size_t proj_bytes_impl(int64_t n) {
     size_t b = 0;

@@ -231,7 +231,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     c->sw_step_bytes = sizeof(float) * 3 * (size_t)S * max_n;
     A(&c->sw_step, c->sw_step_bytes);
     A((void **)&c->d_status, sizeof(uint32_t) * 4);
-    A((void **)&c->d_stats, sizeof(unsigned long long) * 5 * 4);
+    A((void **)&c->d_stats, sizeof(unsigned long long) * 5 * 5);
     A((void **)&c->flags, (size_t)max_n);
     A((void **)&c->g_prim, sizeof(float) * 3 * (size_t)max_n);
     A((void **)&c->lg_phi, sizeof(float) * (size_t)max_n);
@@ -239,7 +239,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(double) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
-    if (ok) ok = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 20) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 25) == cudaSuccess;
     // view lanes for the secondaries of a sweep
     c->owner = nullptr;
     c->n_lanes = 0;
@@ -391,7 +391,7 @@ static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const vo
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // statistics (shared by a sweep's view lanes)
     int pe = prof_begin(ctx, GS2_PROF_BIN, st);
     RET_CUDA(ctx, launch_bin_sort(ctx, pv, n, ctx->tiles_x, ctx->tiles_y, st,
-                                  pc->prof_on ? pc->d_stats + 4 * pc->stat_slot : nullptr, order_in, order_out));
+                                  pc->prof_on ? pc->d_stats + 5 * pc->stat_slot : nullptr, order_in, order_out));
     prof_end(ctx, pe, st);
     if (pc->prof_on) pc->h_pixels[pc->stat_slot] += (unsigned long long)cam->width * cam->height;
     pe = prof_begin(ctx, GS2_PROF_RASTER, st);
@@ -828,7 +828,7 @@ extern "C" gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable) {
     ctx->prof_n = 0;
     ctx->stat_slot = 0;
     for (int g = 0; g < 5; ++g) ctx->h_pixels[g] = 0;
-    RET_CUDA(ctx, cudaMemset(ctx->d_stats, 0, sizeof(unsigned long long) * 20));
+    RET_CUDA(ctx, cudaMemset(ctx->d_stats, 0, sizeof(unsigned long long) * 25));
     return GS2_OK;
 }
 
@@ -846,14 +846,15 @@ extern "C" gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *
         accum_ms[ctx->prof_group[i]] += ms;
         accum_launches[ctx->prof_group[i]] += 1;
     }
-    unsigned long long h[20];
+    unsigned long long h[25];
     RET_CUDA(ctx, cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
     for (int g = 0; g < 5; ++g) {
-        stats[5 * g + 0] = h[4 * g + 0];
-        stats[5 * g + 1] = h[4 * g + 1];
-        stats[5 * g + 2] = h[4 * g + 2];
-        stats[5 * g + 3] = ctx->h_pixels[g];
-        stats[5 * g + 4] = h[4 * g + 3];
+        stats[6 * g + 0] = h[5 * g + 0];
+        stats[6 * g + 1] = h[5 * g + 1];
+        stats[6 * g + 2] = h[5 * g + 2];
+        stats[6 * g + 3] = ctx->h_pixels[g];
+        stats[6 * g + 4] = h[5 * g + 3];
+        stats[6 * g + 5] = h[5 * g + 4];
     }
     return GS2_OK;
 }

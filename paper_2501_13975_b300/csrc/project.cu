@@ -98,6 +98,10 @@ __device__ __forceinline__ void project_one(const DevCam &cam, const ProjView &p
     const float ry = sqrtf(fmaxf(l * syy, 0.f)) * 1.0005f + 0.02f;
     const float fx0 = fmaxf(ceilf(pix_x - rx), 0.f), fx1 = fminf(floorf(pix_x + rx), (float)(cam.w - 1));
     const float fy0 = fmaxf(ceilf(pix_y - ry), 0.f), fy1 = fminf(floorf(pix_y + ry), (float)(cam.h - 1));
+    // det Sigma / Sigma_yy^2: with k1 = -conic_xy / conic_xx and ry it gives the
+    // support's extent in x row by row (the pair emission keeps only the tiles
+    // of the rectangle that the ellipse reaches)
+    const float k2 = det / (syy * syy);
     uint32_t touched = 0u;
     uint2 rect = make_uint2(0u, 0u);
     if (fx0 <= fx1 && fy0 <= fy1) {
@@ -123,9 +127,9 @@ __device__ __forceinline__ void project_one(const DevCam &cam, const ProjView &p
         for (int i = 0; i < S; ++i) acc = fmaf(sh_norm(i) * phi[i], shc[c * S + i], acc);
         col[c] = acc;
     }
-    // recB.w, col.w: the support's half extents in pixels
+    // recB.w, col.w: the support's row parameters k2 and ry (tile emission)
     pv.recA[k] = make_float4(pix_x, pix_y, ca, cb);
-    pv.recB[k] = make_float4(cc, sigma, tz, rx);
+    pv.recB[k] = make_float4(cc, sigma, tz, k2);
     pv.col[k] = make_float4(col[0], col[1], col[2], ry);
 }
 

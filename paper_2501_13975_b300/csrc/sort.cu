@@ -104,15 +104,20 @@ __global__ void k_gather_touched(ProjView pv, const uint32_t *__restrict__ order
 }
 
 // ---------------------------------------------------------------- emit
-// One CTA per 256 consecutive ranks: their pairs occupy one contiguous output
-// range, which the CTA writes with all threads striding (coalesced, balanced
-// even when one Gaussian covers thousands of tiles); a pair finds its rank by
-// binary search over the CTA's offsets in shared memory.
+// One CTA per 256 consecutive ranks: their pairs (one per tile of each
+// Gaussian's rectangle) occupy one contiguous output range, which the CTA
+// writes with all threads striding (coalesced, balanced even when one Gaussian
+// covers thousands of tiles); a pair finds its rank by binary search over the
+// CTA's offsets in shared memory.  A tile of the rectangle that the Gaussian's
+// support ellipse does not reach gets the key ntiles: it sorts after every
+// tile and the range pass leaves it out of the lists, so the compositing and
+// the accumulation never walk it.
 __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__restrict__ order, int n, int tiles_x,
-                                              uint32_t cap, uint32_t *keys, uint32_t *vals,
+                                              uint32_t ntiles, uint32_t cap, uint32_t *keys, uint32_t *vals,
                                               unsigned long long *stats) {
     __shared__ uint32_t s_off[256];
     __shared__ uint2 s_rect[256];
+    __shared__ SupportRows s_sr[256];
     __shared__ uint32_t s_id[256];
     __shared__ uint32_t s_beg, s_end;
     const int t = threadIdx.x;
@@ -127,6 +132,10 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
     s_off[t] = (r < n) ? off : 0xFFFFFFFFu;
     s_rect[t] = (r < n) ? pv.rect[id] : make_uint2(0u, 0u);
     s_id[t] = id;
+    if (cnt != 0u) {
+        const float4 A = pv.recA[id];
+        s_sr[t] = support_rows(A.x, A.y, A.z, A.w, pv.recB[id].w, pv.col[id].w);
+    }
     const int last = min(n - 1, blockIdx.x * 256 + 255) - blockIdx.x * 256;
     if (t == last) s_end = min(off + cnt, cap);   // offsets are already clamped to cap
     if (t == 0) s_beg = off;
@@ -142,7 +151,8 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
         const uint2 rc = s_rect[lo];
         const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
         const uint32_t wdt = tx1 - tx0, rel = j - s_off[lo];
-        keys[j] = (ty0 + rel / wdt) * (uint32_t)tiles_x + tx0 + rel % wdt;
+        const uint32_t tx = tx0 + rel % wdt, ty = ty0 + rel / wdt;
+        keys[j] = support_reaches(s_sr[lo], tx, ty) ? ty * (uint32_t)tiles_x + tx : ntiles;
         vals[j] = s_id[lo];
     }
 }
@@ -341,14 +351,16 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
 }
 
 // [start, end) of every tile: each thread checks four consecutive sorted keys
-// (one 16-byte load when aligned) against their successors
-__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *count, uint2 *ranges,
+// (one 16-byte load when aligned) against their successors; keys >= ntiles
+// (tiles of a rectangle that the support ellipse misses) are not tiles and are skipped
+__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *count, uint2 *ranges, uint32_t ntiles,
                          unsigned long long *stats) {
     const uint32_t M = count[0];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0) {   // atomic: concurrent views share the counters
         atomicAdd(&stats[0], (unsigned long long)M);
         atomicAdd(&stats[2], 1ull);
     }
+    // listed pairs: the end of the last tile (pairs past it are not tiles)
     const uint32_t nq = (M + 3u) / 4u;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         const uint32_t j0 = 4u * q;
@@ -360,17 +372,19 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *coun
             for (int i = 0; i < 4; ++i) k[i] = (j0 + i < M) ? keys[j0 + i] : 0u;
         }
         k[4] = (j0 + 4u < M) ? keys[j0 + 4u] : 0u;
-        if (j0 == 0u) ranges[k[0]].x = 0u;
+        if (j0 == 0u && k[0] < ntiles) ranges[k[0]].x = 0u;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint32_t j = j0 + i;
             if (j >= M) break;
             if (j + 1u == M) {
-                ranges[k[i]].y = M;
+                if (k[i] < ntiles) ranges[k[i]].y = M;
             } else if (k[i + 1] != k[i]) {
-                ranges[k[i]].y = j + 1u;
-                ranges[k[i + 1]].x = j + 1u;
+                if (k[i] < ntiles) ranges[k[i]].y = j + 1u;
+                if (k[i + 1] < ntiles) ranges[k[i + 1]].x = j + 1u;
             }
+            if (stats && k[i] < ntiles && (j + 1u == M || k[i + 1] >= ntiles))
+                atomicAdd(&stats[4], (unsigned long long)(j + 1u));
         }
     }
 }
@@ -408,14 +422,16 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     k_scan_blocks<<<1, SCAN_BLOCKS, 0, st>>>(bsum, ctx->d_count, cap, ctx->d_status);
     k_scan_down<<<SCAN_BLOCKS, 256, 0, st>>>(pv.tsort, n, bsum, cap, pv.offs);
     // 3. pairs in rank order
-    k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n, tiles_x, cap, ctx->keys[0], ctx->vals[0], stats);
-    // 4. stable sort by tile id
+    k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n, tiles_x, (uint32_t)ntiles, cap, ctx->keys[0],
+                                            ctx->vals[0], stats);
+    // 4. stable sort by tile id (keys 0..ntiles: one more value than there are tiles)
     int tile_bits = 1;
-    while ((1 << tile_bits) < ntiles) ++tile_bits;
+    while ((1 << tile_bits) <= ntiles) ++tile_bits;
     ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, tile_bits, ctx->ghist, nb, ctx->sort_rows, st,
                              &launches);
     // 5. tile ranges
-    k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, stats);
+    k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, (uint32_t)ntiles,
+                                       stats);
     GS2_COUNT_LAUNCH(launches + 7);
     return cudaGetLastError();
 }

@@ -429,7 +429,7 @@ class Context:
     def profile_read(self):
         ms = np.zeros(5, np.float64)
         cnt = np.zeros(5, np.int64)
-        stats = np.zeros((5, 5), np.uint64)
+        stats = np.zeros((5, 6), np.uint64)
         self._ok(_lib.gs2_profile_read(self.h, ms.ctypes.data_as(_vp), cnt.ctypes.data_as(_vp),
                                        stats.ctypes.data_as(_vp)), "gs2_profile_read")
         sms = np.zeros(3, np.float64)
@@ -437,7 +437,7 @@ class Context:
         self._ok(_lib.gs2_profile_read_stages(self.h, sms.ctypes.data_as(_vp), scnt.ctypes.data_as(_vp)),
                  "gs2_profile_read_stages")
         return dict(accum_ms=ms, accum_launches=cnt, pairs=stats[:, 0], visible=stats[:, 1],
-                    binnings=stats[:, 2], pixels=stats[:, 3], evaluations=stats[:, 4],
+                    binnings=stats[:, 2], pixels=stats[:, 3], evaluations=stats[:, 4], listed=stats[:, 5],
                     stage_ms=dict(binning=sms[0], compositing=sms[1], loss=sms[2]),
                     stage_count=dict(binning=int(scnt[0]), compositing=int(scnt[1]), loss=int(scnt[2])))
 

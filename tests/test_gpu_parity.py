@@ -26,11 +26,11 @@ def gs2():
     return m
 
 
-def _setup(gs2, scene, cams, cfg=None, max_sh=3):
+def _setup(gs2, scene, cams, cfg=None, max_sh=3, max_pairs=0):
     gcfg = gs2.default_config(**(cfg or {}))
     W = max(c.width for c in cams)
     H = max(c.height for c in cams)
-    ctx = gs2.Context(scene.n, W, H, max_sh, 0, gcfg)
+    ctx = gs2.Context(scene.n, W, H, max_sh, max_pairs, gcfg)
     return ctx, gcfg, oracle_cfg(gcfg)
 
 
@@ -74,33 +74,61 @@ def test_project_parity_and_keys(gs2, size):
         assert rel_err(out[6:9, vis], pr["color"][:, vis], 1.0) < 1e-5
 
 
-@pytest.mark.parametrize("size,n", [(128, 1000), (100, 700), (40, 300)])
-def test_binning_and_sort_bit_exact(gs2, size, n):
-    """Every tile list is sorted by (FP32 depth key, index) and holds every
-    Gaussian that has a pixel with alpha >= alpha_min in the tile; an extra entry
-    lies within the Gaussian's support box (a conservative cover)."""
-    sc, cams = _tiny(n=n, size=size)
-    ctx, gcfg, ocfg = _setup(gs2, sc, cams)
+@pytest.mark.parametrize("size,n,big", [(128, 1000, False), (100, 700, False), (40, 300, False), (512, 300, True)])
+def test_binning_and_sort_bit_exact(gs2, size, n, big):
+    """Every tile list is sorted by (FP32 depth key, index), holds every
+    Gaussian that has a pixel with alpha >= alpha_min in the tile, and no
+    Gaussian twice; an extra entry lies within the Gaussian's support box and
+    within a fraction of a pixel of its support ellipse (the lists follow the
+    ellipse, not its box).  The large case has footprints of about 20 tile rows,
+    where a box holds many tiles the ellipse misses."""
+    if big:
+        sc = synth.tiny_scene(seed=4, n=n, sh_degree=0, log_scale=(-1.0, 0.3))
+        cams = synth.ring_cameras(4, size)
+    else:
+        sc, cams = _tiny(n=n, size=size)
+    ntile = ((size + 15) // 16) ** 2
+    ctx, gcfg, ocfg = _setup(gs2, sc, cams, max_pairs=n * ntile if big else 0)
     cam = cams[0]
     ds, proj, img, rs, orc = _render_both(gs2, ctx, ocfg, sc, cam)
-    ranges, ids, m = ctx.debug_tiles(cam.width, cam.height, capacity=16 * n)
+    ranges, ids, m = ctx.debug_tiles(cam.width, cam.height, capacity=n * ntile if big else 16 * n)
     ranges = ranges.cpu().numpy()
     ids = ids.cpu().numpy()
     touch, rect = O.tile_touch(sc, cam, 16, ocfg)
     pr = O.project(sc, cam, ocfg)
     key = pr["key"]
     tx = (cam.width + 15) // 16
-    assert m == ranges[:, 1].max()
+    listed = int(ranges[:, 1].max())   # sorted pairs past it are tiles the ellipses miss
+    assert listed <= m
     for t in range(ranges.shape[0]):
         lst = ids[ranges[t, 0]:ranges[t, 1]]
         order = sorted(lst.tolist(), key=lambda k: (key[k], k))
         assert lst.tolist() == order, f"tile {t} not in (key, index) order"
         need = set(np.nonzero(touch[t] == 1)[0].tolist())
         assert need <= set(lst.tolist()), f"tile {t} misses {need - set(lst.tolist())}"
+        assert len(set(lst.tolist())) == len(lst), f"tile {t} lists a Gaussian twice"
         x0, y0 = (t % tx) * 16, (t // tx) * 16
+        gx, gy = np.meshgrid(np.arange(x0, min(x0 + 16, cam.width)), np.arange(y0, min(y0 + 16, cam.height)))
         for k in set(lst.tolist()) - need:
             r = rect[:, k]
             assert r[0] - 1 <= x0 + 15 and r[2] + 1 >= x0 and r[1] - 1 <= y0 + 15 and r[3] + 1 >= y0, (t, k)
+            # an extra entry is a tile the support ellipse nearly reaches: some
+            # pixel lies within delta of { d^T A d <= l } (sqrt(q) is a norm
+            # with Lipschitz constant sqrt(lambda_max(A)))
+            a, b, c = pr["conic"][:, k]
+            dx, dy = gx - pr["pix"][0, k], gy - pr["pix"][1, k]
+            q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+            lam = 0.5 * (a + c) + np.hypot(0.5 * (a - c), b)
+            ell = 2 * np.log(pr["opacity"][k] / ocfg["alpha_min"])
+            delta = 0.2 + 5e-3 * (r[2] - r[0] + r[3] - r[1])
+            assert np.sqrt(q.min()) <= np.sqrt(ell) + delta * np.sqrt(lam), (t, k, q.min(), ell)
+    # the lists cover the support ellipses, not their bounding rectangles
+    with np.errstate(invalid="ignore"):
+        px0, py0 = np.maximum(np.ceil(rect[0]), 0), np.maximum(np.ceil(rect[1]), 0)
+        px1, py1 = np.minimum(np.floor(rect[2]), cam.width - 1), np.minimum(np.floor(rect[3]), cam.height - 1)
+        vis = (~pr["culled"]) & (pr["opacity"] > ocfg["alpha_min"]) & (px0 <= px1) & (py0 <= py1)
+    box = (px1 // 16 - px0 // 16 + 1) * (py1 // 16 - py0 // 16 + 1)
+    assert listed < box[vis].sum(), (listed, box[vis].sum())
 
 
 @pytest.mark.parametrize("size,n,sh", [(128, 1000, 0), (100, 700, 3), (33, 200, 1)])

@@ -127,6 +127,8 @@ def test_profile_counts_every_stage(lanes):
     assert list(p["binnings"]) == [4, 4, 4, 4, 4]
     assert list(p["pixels"]) == [64 * 64 + 3 * 32 * 32] * 5
     assert np.all(p["pairs"] > 0) and np.all(p["evaluations"] > 0)
+    # the tile lists keep the tiles the support ellipses reach: a subset of the sorted pairs
+    assert np.all(p["listed"] > 0) and np.all(p["listed"] <= p["pairs"])
 
 
 @pytest.mark.parametrize("variant", [{}, {"group_order": (4, 2, 0, 3, 1)}, {"gauss_newton": 1},
