@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
                                               unsigned long long *stats) {
     __shared__ uint32_t s_off[256];
     __shared__ uint2 s_rect[256];
+    __shared__ float s_inv[256];      // 1 / rectangle width
     __shared__ SupportRows s_sr[256];
     __shared__ uint32_t s_id[256];
     __shared__ uint32_t s_beg, s_end;
@@ -135,6 +136,8 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
     if (cnt != 0u) {
         const float4 A = pv.recA[id];
         s_sr[t] = support_rows(A.x, A.y, A.z, A.w, pv.recB[id].w, pv.col[id].w);
+        const uint2 rc = s_rect[t];
+        s_inv[t] = 1.f / (float)((rc.y & 0xFFFFu) - (rc.x & 0xFFFFu));
     }
     const int last = min(n - 1, blockIdx.x * 256 + 255) - blockIdx.x * 256;
     if (t == last) s_end = min(off + cnt, cap);   // offsets are already clamped to cap
@@ -151,7 +154,18 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
         const uint2 rc = s_rect[lo];
         const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
         const uint32_t wdt = tx1 - tx0, rel = j - s_off[lo];
-        const uint32_t tx = tx0 + rel % wdt, ty = ty0 + rel / wdt;
+        // rel / wdt: the float product is within 0.25 of the quotient (rel < 2^20
+        // tiles), so one step either way makes it exact
+        uint32_t row = (uint32_t)((float)rel * s_inv[lo]);
+        int rem = (int)rel - (int)(row * wdt);
+        if (rem < 0) {
+            --row;
+            rem += (int)wdt;
+        } else if (rem >= (int)wdt) {
+            ++row;
+            rem -= (int)wdt;
+        }
+        const uint32_t tx = tx0 + (uint32_t)rem, ty = ty0 + row;
         keys[j] = support_reaches(s_sr[lo], tx, ty) ? ty * (uint32_t)tiles_x + tx : ntiles;
         vals[j] = s_id[lo];
     }
