@@ -185,7 +185,7 @@ struct gs2_ctx {
     int max_w, max_h, max_sh;
     int64_t max_pairs;
     int nb_sort;                 // blocks of the radix sort grid (tuning, <= GS2_SORT_BLOCKS_MAX)
-    int sort_rows;               // keys per thread per scatter round (tuning: 2, 4, 8)
+    int sort_rows;               // keys per thread per scatter round (tuning: 2, 4, 8 or 16)
     int view_lanes;              // run a sweep's views concurrently (tuning: 0, 1)
     // sorting
     uint32_t *keys[2];           // pair keys: tile id
