@@ -135,7 +135,10 @@ void gs2_config_default(gs2_config *cfg);
 /* Context: owns only scratch (sorting buffers, tile ranges, per-view
  * image-space accumulators, per-pixel loss derivatives, sweep buffers).
  * max_pairs: capacity of the (tile, Gaussian) pair list per view (0 picks
- * 16 * max_gaussians).  Returns GS2_ERR_OOM if scratch cannot be allocated.
+ * 16 * max_gaussians).  Limits: max_width * max_height <= 2^28 pixels and
+ * each side at most 1,048,560 pixels (65,535 tiles of 16: tile coordinates
+ * are 16-bit), else GS2_ERR_SHAPE, checked before any device call.  Returns
+ * GS2_ERR_OOM if scratch cannot be allocated.
  * Creates scratch on the current CUDA device. */
 gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t max_gaussians, int32_t max_width,
                       int32_t max_height, int32_t max_sh_degree, int64_t max_pairs);

@@ -174,6 +174,8 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     if (max_n < 1 || max_w < 1 || max_h < 1 || max_sh < 0) return GS2_ERR_ARG;
     if (max_sh > 3) return GS2_ERR_UNSUPPORTED;
     if (max_n > (int64_t)0x7FFFFFFF || (int64_t)max_w * max_h > (int64_t)1 << 28) return GS2_ERR_SHAPE;
+    // tile rectangles hold 16-bit tile coordinates
+    if (max_w > 0xFFFF * GS2_TILE || max_h > 0xFFFF * GS2_TILE) return GS2_ERR_SHAPE;
     gs2_ctx *c = new (std::nothrow) gs2_ctx();
     if (!c) return GS2_ERR_OOM;
     if (cfg) c->cfg = *cfg;

@@ -61,3 +61,17 @@ def test_create_without_device_fails_cleanly():
     except gs2.GS2Error:
         return
     raise AssertionError("expected GS2Error")
+
+
+def test_create_rejects_shapes_beyond_the_tile_coordinates():
+    """A side longer than 65,535 tiles of 16 pixels cannot be binned (tile
+    coordinates are 16-bit): gs2_create refuses it before any device call."""
+    lib = ctypes.CDLL(B.build())
+    lib.gs2_create.restype = ctypes.c_int
+    lib.gs2_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+    h = ctypes.c_void_p()
+    shape_err = 2
+    for w, hh in ((0xFFFF * 16 + 1, 1), (1, 0xFFFF * 16 + 1), (1 << 15, (1 << 13) + 1)):
+        assert lib.gs2_create(ctypes.byref(h), None, 100, w, hh, 0, 0) == shape_err, (w, hh)
+        assert not h.value
