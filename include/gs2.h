@@ -437,9 +437,14 @@ gs2_status gs2_profile_read_stages(gs2_ctx *ctx, double *ms_out, int64_t *count_
  *   Limits: at most GS2_NOALLOC_MAX_TILES 16x16 tiles (GS2_ERR_SHAPE beyond)
  *   and GS2_NOALLOC_MAX_PAIRS (tile, Gaussian) pairs; more pairs set
  *   GS2_ERR_CAPACITY's bit (1) in *status_out and the image is then incomplete.
- *   cfg: host, NULL for the defaults.  proj: device, gs2_proj_bytes(n);
- *   image, raster_state: device outputs as for gs2_raster_fwd; status_out:
- *   device uint32 (0 = OK), may be NULL.
+ *   cfg: host, NULL for the defaults; a configuration that gs2_create would
+ *   refuse returns GS2_ERR_ARG before any device call.  proj: device,
+ *   gs2_proj_bytes(n); image, raster_state: device outputs as for
+ *   gs2_raster_fwd; status_out: device uint32, written by every call (0 = OK,
+ *   else the status bits of this call only).  status_out may be NULL, but then
+ *   a pair overflow cannot be detected at all (there is no context for
+ *   gs2_check): an incomplete image still returns GS2_OK.  Pass a status word
+ *   unless the scene is known to stay within the limits.
  *   The first call on a device looks up the array's device address with that
  *   device current; make it before any stream capture.  All calls share the
  *   array and leave their contents in it: calls that overlap on the GPU race

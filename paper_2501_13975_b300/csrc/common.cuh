@@ -276,6 +276,9 @@ cudaError_t prepare_loss_kernels();
 // unless profiling is on and the pool has room); returns the pair index or -1
 int prof_begin(gs2_ctx *ctx, int tag, cudaStream_t st);
 void prof_end(gs2_ctx *ctx, int idx, cudaStream_t st);
+// validation of a configuration (gs2_create, gs2_set_config, gs2_render_noalloc):
+// false with a message in err when a field is out of its range
+bool cfg_ok(const gs2_config *c, std::string &err);
 // one sweep on ctx (gs2_sweep / gs2_sweep_logged; records may be NULL)
 gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                      const float *const *targets, const int32_t *knn, int32_t t, float *records, double *losses_out,

@@ -60,7 +60,7 @@ extern "C" void gs2_config_default(gs2_config *c) {
     for (int i = 0; i < 5; ++i) c->gd_lr[i] = 0.f;
 }
 
-static bool cfg_ok(const gs2_config *c, std::string &err) {
+bool cfg_ok(const gs2_config *c, std::string &err) {
     if (!(c->alpha_min > 0.f && c->alpha_min < 1.f)) { err = "alpha_min must be in (0,1)"; return false; }
     if (!(c->alpha_max >= c->alpha_min && c->alpha_max <= 1.f)) { err = "alpha_max must be in [alpha_min,1]"; return false; }
     if (!(c->t_min >= 0.f && c->t_min < 1.f)) { err = "t_min must be in [0,1)"; return false; }

@@ -75,8 +75,13 @@ extern "C" gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene 
     const int tiles_x = (cam->width + GS2_TILE - 1) / GS2_TILE, tiles_y = (cam->height + GS2_TILE - 1) / GS2_TILE;
     if ((long long)tiles_x * tiles_y > GS2_NOALLOC_MAX_TILES) return GS2_ERR_SHAPE;
     gs2_config c;
-    if (cfg) c = *cfg;
-    else gs2_config_default(&c);
+    if (cfg) {
+        std::string err;   // the same checks as gs2_create / gs2_set_config, before any device call
+        if (!cfg_ok(cfg, err)) return GS2_ERR_ARG;
+        c = *cfg;
+    } else {
+        gs2_config_default(&c);
+    }
     unsigned char *base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return GS2_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

@@ -75,3 +75,22 @@ def test_create_rejects_shapes_beyond_the_tile_coordinates():
     for w, hh in ((0xFFFF * 16 + 1, 1), (1, 0xFFFF * 16 + 1), (1 << 15, (1 << 13) + 1)):
         assert lib.gs2_create(ctypes.byref(h), None, 100, w, hh, 0, 0) == shape_err, (w, hh)
         assert not h.value
+
+
+def test_render_noalloc_refuses_a_bad_config_before_any_device_call():
+    """gs2_render_noalloc validates a caller's configuration exactly as
+    gs2_create does (alpha_min must lie in (0, 1), near_z > 0, ...) and returns
+    GS2_ERR_ARG before it touches a device; the pointers below are never
+    dereferenced, so this runs without a GPU."""
+    import ctypes as C
+
+    from paper_2501_13975_b300 import gs2
+    lib = gs2._lib
+    fake = 0x1000
+    scene = gs2.Scene_(10, 0, fake, fake, fake, fake, fake)
+    cam = gs2.Camera_()
+    cam.width, cam.height, cam.fx, cam.fy = 64, 64, 50.0, 50.0
+    for field, value in (("alpha_min", 0.0), ("alpha_min", float("nan")), ("near_z", 0.0), ("near_z", -1.0)):
+        cfg = gs2._config_struct({field: value})
+        st = lib.gs2_render_noalloc(C.byref(cfg), C.byref(scene), C.byref(cam), fake, fake, fake, None, None)
+        assert st == 1, (field, value, st)   # GS2_ERR_ARG

@@ -50,3 +50,26 @@ def test_render_noalloc_rejects_too_many_tiles():
     rs = gs2.Context.empty_bytes(gs2._lib.gs2_raster_state_bytes(1040, 1040))
     with pytest.raises(gs2.GS2Error, match="ERR_SHAPE"):
         gs2.render_noalloc(ds, cam, proj, img, rs)
+
+
+def test_render_noalloc_reports_pair_overflow_per_call():
+    """More (tile, Gaussian) pairs than GS2_NOALLOC_MAX_PAIRS: the call still
+    returns GS2_OK, with GS2_ERR_CAPACITY's bit (1) in the status word, and the
+    next call within the limits reports 0 (each call writes its own status).
+    1,000 Gaussians with scales near 0.5 seen from 3 units at 1024x1024 list
+    about 2.3M pairs against a limit of 524,288."""
+    from paper_2501_13975_b300 import gs2
+    big = synth.tiny_scene(n=1000, seed=7, log_scale=(-0.7, 0.1))
+    small = synth.tiny_scene(n=1000, seed=5, sh_degree=1)
+    cam_big = synth.ring_cameras(4, 1024)[0]
+    cam_small = synth.ring_cameras(4, 128)[0]
+    status = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    for sc, cam, want in ((big, cam_big, 1), (small, cam_small, 0), (big, cam_big, 1), (small, cam_small, 0)):
+        ds = gs2.DeviceScene.from_host(sc)
+        proj = gs2.Context.empty_bytes(gs2._lib.gs2_proj_bytes(sc.n))
+        img = torch.empty((3, cam.height, cam.width), device="cuda")
+        rs = gs2.Context.empty_bytes(gs2._lib.gs2_raster_state_bytes(cam.width, cam.height))
+        gs2.render_noalloc(ds, cam, proj, img, rs, status)   # raises unless GS2_OK
+        torch.cuda.synchronize()
+        assert int(status.item()) == want, (cam.width, int(status.item()))
+        assert bool(torch.isfinite(img).all())
