@@ -693,6 +693,50 @@ static sj1 ssim_of(sj1 mu, double mut, sj1 ecc, double ett, sj1 ect, double C1, 
     return j1div(j1mul(f0, f1), j1mul(f2, f3));
 }
 
+/* Window moments of one channel at every centre p (zero padding outside the
+ * image): mom[0..4][p] = sum_q w(q - p) (x_q, y_q, x_q^2, y_q^2, x_q y_q), w the
+ * separable normalised Gaussian window of ssim_window. */
+static void ssim_moments(const double *X, const double *Y, int W, int H, int R, const double *w1, double *mom) {
+    size_t P = (size_t)W * H;
+#pragma omp parallel for schedule(static)
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            double m[5] = {0, 0, 0, 0, 0};
+            for (int dy = -R; dy <= R; ++dy) {
+                int qy = py + dy;
+                if (qy < 0 || qy >= H) continue;
+                for (int dx = -R; dx <= R; ++dx) {
+                    int qx = px + dx;
+                    if (qx < 0 || qx >= W) continue;
+                    double w = w1[dy + R] * w1[dx + R];
+                    double x = X[(size_t)qy * W + qx], y = Y[(size_t)qy * W + qx];
+                    m[0] += w * x; m[1] += w * y; m[2] += w * x * x; m[3] += w * y * y; m[4] += w * x * y;
+                }
+            }
+            for (int i = 0; i < 5; ++i) mom[i * P + (size_t)py * W + px] = m[i];
+        }
+}
+
+/* Exported.  Per-pixel SSIM of every channel (the quantity L_S averages):
+ * ssim [3][H][W] out; mom (may be NULL) [3][5][H][W] out, the window moments
+ * (mu_x, mu_y, E x^2, E y^2, E xy) it is formed from. */
+void orc_ssim_map(const double *img, const double *tgt, int W, int H, const orc_config *cfg, double *ssim,
+                  double *mom_out) {
+    size_t P = (size_t)W * H;
+    int R = cfg->ssim_radius;
+    double w1[64];
+    ssim_window(cfg, w1);
+    double *mom = (double *)malloc(sizeof(double) * 5 * P);
+    for (int c = 0; c < 3; ++c) {
+        ssim_moments(img + c * P, tgt + c * P, W, H, R, w1, mom);
+        for (size_t p = 0; p < P; ++p)
+            ssim[c * P + p] = ssim_of(j1c(mom[p]), mom[P + p], j1c(mom[2 * P + p]), mom[3 * P + p],
+                                      j1c(mom[4 * P + p]), cfg->ssim_c1, cfg->ssim_c2).v;
+        if (mom_out) memcpy(mom_out + 5 * P * c, mom, sizeof(double) * 5 * P);
+    }
+    free(mom);
+}
+
 /* Exported.  img, tgt: [3][H][W].  e, h: [3][H][W] out.  parts[0] = L2, parts[1] = L_S.
  * Returns L = L2 + lambda L_S. */
 double orc_loss(const double *img, const double *tgt, int W, int H, const orc_config *cfg, double *e, double *h,
@@ -716,24 +760,7 @@ double orc_loss(const double *img, const double *tgt, int W, int H, const orc_co
         double *mom = (double *)malloc(sizeof(double) * 5 * P);
         for (int c = 0; c < 3; ++c) {
             const double *X = img + c * P, *Y = tgt + c * P;
-            /* window moments at every centre p (zero padding) */
-#pragma omp parallel for schedule(static)
-            for (int py = 0; py < H; ++py)
-                for (int px = 0; px < W; ++px) {
-                    double m[5] = {0, 0, 0, 0, 0};
-                    for (int dy = -R; dy <= R; ++dy) {
-                        int qy = py + dy;
-                        if (qy < 0 || qy >= H) continue;
-                        for (int dx = -R; dx <= R; ++dx) {
-                            int qx = px + dx;
-                            if (qx < 0 || qx >= W) continue;
-                            double w = w1[dy + R] * w1[dx + R];
-                            double x = X[(size_t)qy * W + qx], y = Y[(size_t)qy * W + qx];
-                            m[0] += w * x; m[1] += w * y; m[2] += w * x * x; m[3] += w * y * y; m[4] += w * x * y;
-                        }
-                    }
-                    for (int i = 0; i < 5; ++i) mom[i * P + (size_t)py * W + px] = m[i];
-                }
+            ssim_moments(X, Y, W, H, R, w1, mom);
             double lsum = 0.0;
             for (size_t p = 0; p < P; ++p) {
                 sj1 s = ssim_of(j1c(mom[p]), mom[P + p], j1c(mom[2 * P + p]), mom[3 * P + p], j1c(mom[4 * P + p]), C1, C2);

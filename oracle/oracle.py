@@ -191,6 +191,18 @@ def loss(image, target, cfg=None, derivs=True):
     return dict(loss=L, l2=parts[0], lssim=parts[1], e=e, h=h)
 
 
+def ssim_map(image, target, cfg=None):
+    """Per-pixel SSIM [3][H][W] and its window moments [3][5][H][W]
+    (mu_x, mu_y, E x^2, E y^2, E xy), as L_S averages them."""
+    image = np.ascontiguousarray(image, np.float64)
+    target = np.ascontiguousarray(target, np.float64)
+    _, H, W = image.shape
+    out = np.zeros_like(image)
+    mom = np.zeros((3, 5, H, W))
+    lib().orc_ssim_map(_d(image), _d(target), C.c_int(W), C.c_int(H), C.byref(cfg_struct(cfg)), _d(out), _d(mom))
+    return out, mom
+
+
 def block_shapes(group: int, n: int, S: int):
     if group == COLOR:
         return (3, S, n), (3, S * (S + 1) // 2, n)
