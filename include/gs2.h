@@ -462,8 +462,14 @@ gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32_t *ids_out
                            int64_t *n_pairs_out, gs2_stream stream);
 /* Depth keys (FP32 bit patterns) written by the last gs2_project into proj. */
 gs2_status gs2_debug_keys(const void *proj, int64_t n, uint32_t *keys_out, gs2_stream stream);
-/* Unpacks proj into planar FP32 [12][n]: pix_x pix_y conic_xx conic_xy conic_yy
- * sigma col0 col1 col2 depth tiles_touched(as float) 0. */
+/* Unpacks proj into planar FP32 [GS2_DEBUG_PROJ_ROWS][n]: pix_x pix_y conic_xx
+ * conic_xy conic_yy sigma col0 col1 col2 depth tiles_touched(as float) l lmax
+ * k2 ry rect.x rect.y 0, where l, lmax are the thresholds of the quadratic
+ * form (composited iff q <= l, clamped iff q < lmax), k2 = det Sigma2D /
+ * Sigma_yy^2, ry the padded half height of the support box and rect.x, rect.y
+ * the tile rectangle's two words (tx0 | ty0 << 16, tx1 | ty1 << 16, exclusive
+ * ends) stored as their bit patterns. */
+#define GS2_DEBUG_PROJ_ROWS 18
 gs2_status gs2_debug_proj(const void *proj, int64_t n, float *out, gs2_stream stream);
 
 #ifdef __cplusplus

@@ -449,6 +449,186 @@ static void project_one(const orc_camera *cam, const orc_config *cfg, int S, gpa
 }
 
 /* ---------------------------------------------------------------------------
+ * FP32 decisions [Sec. 3, Eq. 3dgs].  Three outcomes of the forward pass are
+ * discrete: whether a (pixel, Gaussian) term is composited (sigma G >=
+ * alpha_min), whether its alpha is clamped (sigma G > alpha_max), and which
+ * screen tiles list the Gaussian.  Floating point decides them, so (reading)
+ * they are taken in the kernel's precision: FP32, from the FP32 parameters and
+ * camera, with correctly rounded operations only (+, -, *, fma, /, sqrt;
+ * floor, ceil, min, max are exact) in the order written below, and a
+ * logarithm taken by the atanh (Gregory) series instead of a library call.
+ * Every IEEE FP32 evaluation of these steps gives the same bits.  In terms of
+ * the quadratic form q = d^T Sigma^-1 d of the pixel offset d:
+ *   composited <=> q <= l = 2 ln(sigma / alpha_min),
+ *   clamped    <=> q <  lmax = 2 ln(sigma / alpha_max) (-1 if sigma <= alpha_max),
+ * the same sets as in exact arithmetic.  Everything the oracle computes with
+ * those decisions (alpha, T, colours, derivatives) stays FP64.  The oracle
+ * file is compiled with -ffp-contract=off, so a * b + c below is two rounded
+ * operations and fmaf is one.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    float px, py, ca, cb, cc, sxx, syy, k2, l, lmax, rx, ry;
+    unsigned rect_lo, rect_hi; /* tile box: tx0 | ty0 << 16, tx1 | ty1 << 16 (exclusive ends) */
+    unsigned touched;          /* tiles of the box */
+} dec32;
+
+/* ln x for finite x >= 1: x = 2^e m with m in [sqrt(1/2), sqrt(2)],
+ * ln m = 2 atanh(u) = 2 u (1 + u^2/3 + u^4/5 + u^6/7 + u^8/9), u = (m-1)/(m+1). */
+static float d_ln(float x) {
+    int e = 0;
+    float m = frexpf(x, &e); /* x = m 2^e, m in [1/2, 1) */
+    m = m * 2.0f;
+    e -= 1;
+    if (m > 0x1.6a09e6p+0f) {
+        m = m * 0.5f;
+        e += 1;
+    }
+    float u = (m - 1.0f) / (m + 1.0f);
+    float s = u * u;
+    float p = 0x1.c71c72p-4f;
+    p = fmaf(p, s, 0x1.24924ap-3f);
+    p = fmaf(p, s, 0x1.99999ap-3f);
+    p = fmaf(p, s, 0x1.555556p-2f);
+    p = fmaf(p, s, 1.0f);
+    float lm = (2.0f * u) * p;
+    return fmaf((float)e, 0x1.62e430p-1f, lm);
+}
+
+/* q = dx (ca dx + 2 cb dy) + cc dy^2 as fma(dx, fma(cb, dy, fma(ca, dx, cb dy)), (cc dy) dy) */
+static float d_quad(float ca, float cb, float cc, float dx, float dy) {
+    float a = fmaf(ca, dx, cb * dy);
+    a = fmaf(cb, dy, a);
+    return fmaf(dx, a, (cc * dy) * dy);
+}
+
+static float fmin32(float a, float b) { return a < b ? a : b; }
+static float fmax32(float a, float b) { return a > b ? a : b; }
+
+/* The FP32 projection of one Gaussian in front of the camera (tz the FP32
+ * depth key, sigma >= alpha_min): screen centre, EWA covariance and conic,
+ * the thresholds, the padded support box and its tile rectangle. */
+static void dec32_project(const orc_camera *cam, const orc_config *cfg, const float p[3], float tz, const float q[4],
+                          const float sc[3], float sigma, int tile, dec32 *r) {
+    float V[12];
+    for (int i = 0; i < 12; ++i) V[i] = (float)cam->viewmat[i];
+    const float fx = (float)cam->fx, fy = (float)cam->fy, cx = (float)cam->cx, cy = (float)cam->cy;
+    const float Lx = (float)clip_lim(cam, 0), Ly = (float)clip_lim(cam, 1);
+    const float lowpass = (float)cfg->lowpass, amin = (float)cfg->alpha_min, amax = (float)cfg->alpha_max;
+    /* camera-space centre and the 2x3 T = J Wr */
+    float tx = fmaf(V[0], p[0], fmaf(V[1], p[1], fmaf(V[2], p[2], V[3])));
+    float ty = fmaf(V[4], p[0], fmaf(V[5], p[1], fmaf(V[6], p[2], V[7])));
+    float itz = 1.0f / tz;
+    float taux = fmin32(fmax32(tx * itz, -Lx), Lx);
+    float tauy = fmin32(fmax32(ty * itz, -Ly), Ly);
+    float j00 = fx * itz, j02 = ((-fx) * taux) * itz;
+    float j11 = fy * itz, j12 = ((-fy) * tauy) * itz;
+    float T0[3], T1[3];
+    for (int j = 0; j < 3; ++j) {
+        T0[j] = fmaf(j00, V[j], j02 * V[8 + j]);
+        T1[j] = fmaf(j11, V[4 + j], j12 * V[8 + j]);
+    }
+    /* rotation of the normalised quaternion */
+    float qq = fmaf(q[0], q[0], fmaf(q[1], q[1], fmaf(q[2], q[2], q[3] * q[3])));
+    float qn = 1.0f / sqrtf(qq);
+    float w = q[0] * qn, x = q[1] * qn, y = q[2] * qn, z = q[3] * qn;
+    float R[3][3];
+    R[0][0] = 1.0f - 2.0f * fmaf(y, y, z * z);
+    R[0][1] = 2.0f * (x * y - w * z);
+    R[0][2] = 2.0f * (x * z + w * y);
+    R[1][0] = 2.0f * (x * y + w * z);
+    R[1][1] = 1.0f - 2.0f * fmaf(x, x, z * z);
+    R[1][2] = 2.0f * (y * z - w * x);
+    R[2][0] = 2.0f * (x * z - w * y);
+    R[2][1] = 2.0f * (y * z + w * x);
+    R[2][2] = 1.0f - 2.0f * fmaf(x, x, y * y);
+    /* Sigma2D = sum_j s_j^2 m_j m_j^T with m_j = T R e_j */
+    float ss[3] = {sc[0] * sc[0], sc[1] * sc[1], sc[2] * sc[2]};
+    float m0[3], m1[3], sxx = 0.0f, sxy = 0.0f, syy = 0.0f;
+    for (int j = 0; j < 3; ++j) {
+        m0[j] = fmaf(T0[0], R[0][j], fmaf(T0[1], R[1][j], T0[2] * R[2][j]));
+        m1[j] = fmaf(T1[0], R[0][j], fmaf(T1[1], R[1][j], T1[2] * R[2][j]));
+        float a0 = ss[j] * m0[j];
+        sxx = fmaf(a0, m0[j], sxx);
+        sxy = fmaf(a0, m1[j], sxy);
+        syy = fmaf(ss[j] * m1[j], m1[j], syy);
+    }
+    /* det(A + l I) = det A + l tr A + l^2; det A by Cauchy-Binet */
+    float detA = 0.0f;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) {
+            float cr = fmaf(m0[i], m1[j], -(m1[i] * m0[j]));
+            detA = fmaf((ss[i] * ss[j]) * cr, cr, detA);
+        }
+    float det = (detA + lowpass * (sxx + syy)) + lowpass * lowpass;
+    sxx = sxx + lowpass;
+    syy = syy + lowpass;
+    float idet = 1.0f / det;
+    r->ca = syy * idet;
+    r->cb = (-sxy) * idet;
+    r->cc = sxx * idet;
+    r->sxx = sxx;
+    r->syy = syy;
+    r->k2 = det / (syy * syy);
+    r->px = fmaf(fx * tx, itz, cx);
+    r->py = fmaf(fy * ty, itz, cy);
+    /* alpha_min = 0 (every threshold off, a setting of the smooth oracle pins
+     * only; the library requires alpha_min > 0): every term is composited */
+    r->l = amin > 0.0f ? 2.0f * d_ln(sigma / amin) : INFINITY;
+    r->lmax = sigma > amax ? 2.0f * d_ln(sigma / amax) : -1.0f;
+    r->rx = fmaf(sqrtf(fmax32(r->l * sxx, 0.0f)), 1.0005f, 0.02f);
+    r->ry = fmaf(sqrtf(fmax32(r->l * syy, 0.0f)), 1.0005f, 0.02f);
+    /* tile rectangle of the support box */
+    float fx0 = fmax32(ceilf(r->px - r->rx), 0.0f), fx1 = fmin32(floorf(r->px + r->rx), (float)(cam->width - 1));
+    float fy0 = fmax32(ceilf(r->py - r->ry), 0.0f), fy1 = fmin32(floorf(r->py + r->ry), (float)(cam->height - 1));
+    r->rect_lo = r->rect_hi = 0u;
+    r->touched = 0u;
+    if (fx0 <= fx1 && fy0 <= fy1) {
+        unsigned tx0 = (unsigned)fx0 / tile, tx1 = (unsigned)fx1 / tile + 1u;
+        unsigned ty0 = (unsigned)fy0 / tile, ty1 = (unsigned)fy1 / tile + 1u;
+        r->touched = (tx1 - tx0) * (ty1 - ty0);
+        r->rect_lo = tx0 | (ty0 << 16);
+        r->rect_hi = tx1 | (ty1 << 16);
+    }
+}
+
+/* Does the support { q <= l } reach a pixel of the tile with columns
+ * [x0, x0 + t) and rows [y0, y0 + t)?  Row by row (y relative to the centre)
+ * the support is |x - k1 y| <= sqrt(k2 (ry^2 - y^2)), k1 = -cb / ca; over the
+ * tile's rows the extreme x lie at the rows nearest +-y*, y* = k1 ry /
+ * sqrt(k2 + k1^2); the reach is widened by 1e-3 (|k1| + sqrt(k2)) ry + 0.05 px. */
+static int d_support_reaches(const dec32 *d, float x0, float y0, float t) {
+    float k1 = (-d->cb) / d->ca;
+    float ystar = (k1 * d->ry) / sqrtf(fmaf(k1, k1, d->k2));
+    float marg = fmaf(1e-3f, (fabsf(k1) + sqrtf(d->k2)) * d->ry, 0.05f);
+    float ylo = fmax32(y0, ceilf(d->py - d->ry));
+    float yhi = fmin32((y0 + t) - 1.0f, floorf(d->py + d->ry));
+    if (!(ylo <= yhi)) return 0;
+    float ya = ylo - d->py, yb = yhi - d->py;
+    float yr = fmin32(fmax32(ystar, ya), yb), yl = fmin32(fmax32(-ystar, ya), yb);
+    float r2 = d->ry * d->ry;
+    float hr = sqrtf(fmax32(d->k2 * (r2 - yr * yr), 0.0f));
+    float hl = sqrtf(fmax32(d->k2 * (r2 - yl * yl), 0.0f));
+    float xr = (fmaf(k1, yr, d->px) + hr) + marg;
+    float xl = (fmaf(k1, yl, d->px) - hl) - marg;
+    float c0 = fmax32(ceilf(xl), x0);
+    float c1 = fmin32(floorf(xr), (x0 + t) - 1.0f);
+    return c0 <= c1;
+}
+
+/* the decision record of Gaussian k from the scene's (FP32-valued) parameters */
+static void dec32_of(const orc_scene *sc, const orc_camera *cam, const orc_config *cfg, int k, float tz, int tile,
+                     dec32 *r) {
+    int n = sc->n;
+    float p[3], q[4], s3[3];
+    for (int i = 0; i < 3; ++i) {
+        p[i] = (float)sc->mean[i * n + k];
+        s3[i] = (float)sc->scale[i * n + k];
+    }
+    for (int i = 0; i < 4; ++i) q[i] = (float)sc->quat[i * n + k];
+    dec32_project(cam, cfg, p, tz, q, s3, (float)sc->opacity[k], tile, r);
+}
+
+/* ---------------------------------------------------------------------------
  * Per-view projected set, packed; plus the global depth order.
  * ------------------------------------------------------------------------- */
 #define NPJ 9 /* packed jets: pix0 pix1 con0 con1 con2 op col0 col1 col2 */
@@ -464,6 +644,7 @@ typedef struct {
     int *culled;     /* [n] */
     int *order;      /* sorted non-culled Gaussians with sigma >= alpha_min */
     int norder;
+    dec32 *dec;      /* [n] FP32 decision records of the ordered Gaussians (16x16 tiles) */
 } viewset;
 
 static const float *g_sort_key;
@@ -477,7 +658,7 @@ static int cmp_order(const void *a, const void *b) {
 
 static void viewset_free(viewset *vs) {
     free(vs->jets); free(vs->plain); free(vs->sig); free(vs->tz); free(vs->key);
-    free(vs->culled); free(vs->order);
+    free(vs->culled); free(vs->order); free(vs->dec);
 }
 
 /* Project every Gaussian with the variable assignment of (group, ch). */
@@ -494,6 +675,7 @@ static void viewset_build(viewset *vs, const orc_scene *sc, const orc_camera *ca
     vs->key = (float *)malloc(sizeof(float) * n);
     vs->culled = (int *)malloc(sizeof(int) * n);
     vs->order = (int *)malloc(sizeof(int) * n);
+    vs->dec = (dec32 *)calloc((size_t)n, sizeof(dec32));
     double o[3];
     cam_center(primary, o);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -534,6 +716,8 @@ static void viewset_build(viewset *vs, const orc_scene *sc, const orc_camera *ca
     for (int k = 0; k < n; ++k)
         if (!vs->culled[k] && vs->plain[k * NPJ + 5] >= cfg->alpha_min) vs->order[m++] = k;
     vs->norder = m;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < m; ++i) dec32_of(sc, cam, cfg, vs->order[i], vs->key[vs->order[i]], 16, &vs->dec[vs->order[i]]);
     g_sort_key = vs->key;
     qsort(vs->order, m, sizeof(int), cmp_order);
 }
@@ -544,8 +728,11 @@ static void viewset_build(viewset *vs, const orc_scene *sc, const orc_camera *ca
  *   alpha = min(sigma G, alpha_max); a term with alpha < alpha_min is skipped;
  *   compositing stops before the term that would take T below t_min;
  *   black background.
+ * Whether a term is skipped or clamped is the FP32 decision of its record
+ * (q <= l, q < lmax: see "FP32 decisions"); alpha, T and the colour are FP64.
  * Records every contributor (index, alpha, T before it) and the smallest
- * relative distance of any of these decisions from its threshold.
+ * relative distance of the early-stop decision (the one decision still taken
+ * in FP64 here) from its threshold.
  * ------------------------------------------------------------------------- */
 typedef struct {
     int k;
@@ -560,17 +747,14 @@ static int pixel_pass(const viewset *vs, const orc_config *cfg, double px, doubl
     for (int oi = 0; oi < vs->norder; ++oi) {
         int k = vs->order[oi];
         const double *pl = vs->plain + k * NPJ;
+        const dec32 *D = vs->dec + k;
+        float q32 = d_quad(D->ca, D->cb, D->cc, (float)px - D->px, (float)py - D->py);
+        if (!(q32 <= D->l)) continue;  /* sigma G < alpha_min */
+        int clamped = q32 < D->lmax;    /* sigma G > alpha_max */
         double dx = px - pl[0], dy = py - pl[1];
         double power = -0.5 * (pl[2] * dx * dx + 2.0 * pl[3] * dx * dy + pl[4] * dy * dy);
         double G = exp(power);
-        double araw = pl[5] * G;
-        double m1 = fabs(araw - cfg->alpha_min) / cfg->alpha_min;
-        if (m1 < mg) mg = m1;
-        double m2 = fabs(araw - cfg->alpha_max) / cfg->alpha_max;
-        if (m2 < mg) mg = m2;
-        int clamped = araw > cfg->alpha_max;
-        double alpha = clamped ? cfg->alpha_max : araw;
-        if (alpha < cfg->alpha_min) continue;
+        double alpha = clamped ? cfg->alpha_max : pl[5] * G;
         double testT = T * (1.0 - alpha);
         if (cfg->t_min > 0) {
             double m3 = fabs(testT - cfg->t_min) / cfg->t_min;
@@ -1164,6 +1348,44 @@ static int scale_basis(const orc_camera *cam, const orc_config *cfg, const doubl
     return 0;
 }
 
+/* Exported.  The 3x2 basis B of each Gaussian's reduced solve (tests use it
+ * to propagate block tolerances to steps): POS the orthonormal U
+ * perpendicular to the primary view ray [Sec. 4.2 position solve], SCALE
+ * Q = Tt^T (Tt Tt^T)^-1 [Sec. 4.2 scaling solve].  B_out [n][3][2] (row i,
+ * column a at 6k + 2i + a); status [n]: 0 ok, 3 undefined (scaling: behind
+ * the primary camera or rank-deficient Tt); gap_out [n] (may be NULL): for
+ * scaling how close its reduction is to degenerate (the smaller of the
+ * relative eigenvalue gap of the projected covariance and det(Tt Tt^T) /
+ * (|t1|^2 |t2|^2)), infinity for position.  Returns 0, or -1 for another
+ * group. */
+int orc_reduced_basis(int group, const orc_scene *sc, const orc_camera *primary, const orc_config *cfg,
+                      double *B_out, int *status, double *gap_out) {
+    if (group != G_POS && group != G_SCALE) return -1;
+    int n = sc->n;
+    for (int k = 0; k < n; ++k) {
+        double p[3], q[4], s[3], B[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int i = 0; i < 3; ++i) {
+            p[i] = sc->mean[i * n + k];
+            s[i] = sc->scale[i * n + k];
+        }
+        for (int i = 0; i < 4; ++i) q[i] = sc->quat[i * n + k];
+        int st = 0;
+        double gap = INFINITY;
+        if (group == G_POS) {
+            double r[3];
+            view_dir(primary, p, r);
+            position_basis(r, B);
+        } else {
+            st = scale_basis(primary, cfg, p, q, s, B, &gap);
+        }
+        if (gap_out) gap_out[k] = gap;
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < 2; ++a) B_out[6 * (size_t)k + 2 * i + a] = B[i][a];
+        status[k] = st;
+    }
+    return 0;
+}
+
 /* Exported solve.  g/H layouts as orc_accum.  step: POS [3][n], ROT [1][n],
  * SCALE [3][n], OPACITY [1][n], COLOR [3][S][n].
  * status [n] (COLOR: [3][n]): 0 ok, 1 damping failed, 2 no contribution,
@@ -1668,8 +1890,8 @@ int orc_sweep(orc_scene *sc, const orc_camera *cams, const double *targets, int 
 
 /* ---------------------------------------------------------------------------
  * Tile coverage for the binning pin.  touch [ntiles][n]: 1 if some pixel of
- * the tile has sigma G >= alpha_min by a relative margin of at least 1e-6,
- * 2 if only within that margin (ambiguous), else 0.  rect [4][n]: the
+ * the tile composites the Gaussian (the FP32 decision q <= l), else 0.
+ * rect [4][n]: the
  * support box in pixels from the reading "support = { sigma G >= alpha_min }"
  * (half extents sqrt(2 ln(sigma / alpha_min) Sigma_ii)) as x0 y0 x1 y1.
  * ------------------------------------------------------------------------- */
@@ -1702,18 +1924,94 @@ int orc_tile_touch(const orc_scene *sc, const orc_camera *cam, const orc_config 
             for (int x = x0; x < x0 + tile && x < W; ++x)
                 for (int oi = 0; oi < vs.norder; ++oi) {
                     int k = vs.order[oi];
-                    const double *pl = vs.plain + k * NPJ;
-                    double dx = x - pl[0], dy = y - pl[1];
-                    double G = exp(-0.5 * (pl[2] * dx * dx + 2.0 * pl[3] * dx * dy + pl[4] * dy * dy));
-                    double a = pl[5] * G;
-                    unsigned char *tt = touch + (size_t)tid * n + k;
-                    if (a >= cfg->alpha_min * (1 + 1e-6)) *tt = 1;
-                    else if (a >= cfg->alpha_min * (1 - 1e-6) && *tt == 0) *tt = 2;
+                    const dec32 *D = vs.dec + k;
+                    float q32 = d_quad(D->ca, D->cb, D->cc, (float)x - D->px, (float)y - D->py);
+                    if (q32 <= D->l) touch[(size_t)tid * n + k] = 1;
                 }
     }
     viewset_free(&vs);
     JD = save;
     return 0;
+}
+
+/* Exported.  The FP32 decision records of a view, out [18][n] in the row
+ * layout of the library's projection dump: pix_x pix_y ca cb cc sigma, three
+ * zero rows (colour is not a decision), depth key, touched, l, lmax, k2, ry,
+ * the two tile-rectangle words (bit patterns) and 0; Gaussians that are culled
+ * or below alpha_min have all-zero rows except the depth key. */
+int orc_dec32(const orc_scene *sc, const orc_camera *cam, const orc_config *cfg, float *out) {
+    int save = JD;
+    JD = 0;
+    viewset vs;
+    viewset_build(&vs, sc, cam, cam, cfg, G_VALUES, 0);
+    int n = sc->n;
+    memset(out, 0, sizeof(float) * 18 * (size_t)n);
+    for (int k = 0; k < n; ++k) out[9 * (size_t)n + k] = vs.key[k];
+    for (int i = 0; i < vs.norder; ++i) {
+        int k = vs.order[i];
+        const dec32 *D = vs.dec + k;
+        unsigned lo = D->rect_lo, hi = D->rect_hi;
+        float rl, rh;
+        memcpy(&rl, &lo, 4);
+        memcpy(&rh, &hi, 4);
+        float v[18] = {D->px, D->py, D->ca, D->cb, D->cc, (float)sc->opacity[k], 0, 0, 0, vs.key[k],
+                       (float)D->touched, D->l, D->lmax, D->k2, D->ry, rl, rh, 0};
+        for (int r = 0; r < 18; ++r) out[(size_t)r * n + k] = v[r];
+    }
+    viewset_free(&vs);
+    JD = save;
+    return 0;
+}
+
+/* Exported.  Tile binning and per-tile depth order [Sec. 3], by plain loops:
+ * for every Gaussian in the global (key, index) order and every 16x16 tile of
+ * its support box, the tile lists the Gaussian when the FP32 support test
+ * reaches one of the tile's pixels.  ranges [ntiles][2] = [start, end) into
+ * ids (capacity cap).  Returns the number of listed pairs (may exceed cap:
+ * then only the first cap are written). */
+long long orc_tile_lists(const orc_scene *sc, const orc_camera *cam, const orc_config *cfg, unsigned *ranges,
+                         unsigned *ids, long long cap) {
+    int save = JD;
+    JD = 0;
+    viewset vs;
+    viewset_build(&vs, sc, cam, cam, cfg, G_VALUES, 0);
+    const int T = 16, tx = (cam->width + T - 1) / T, ty = (cam->height + T - 1) / T, nt = tx * ty;
+    long long *cnt = (long long *)calloc((size_t)nt + 1, sizeof(long long));
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) { /* exclusive prefix sums -> starts */
+            long long acc = 0;
+            for (int t = 0; t < nt; ++t) {
+                long long c = cnt[t];
+                ranges[2 * t] = (unsigned)acc;
+                ranges[2 * t + 1] = (unsigned)(acc + c);
+                cnt[t] = acc;
+                acc += c;
+            }
+            cnt[nt] = acc;
+        }
+        for (int i = 0; i < vs.norder; ++i) {
+            int k = vs.order[i];
+            const dec32 *D = vs.dec + k;
+            if (D->touched == 0u) continue;
+            unsigned x0 = D->rect_lo & 0xFFFFu, y0 = D->rect_lo >> 16, x1 = D->rect_hi & 0xFFFFu, y1 = D->rect_hi >> 16;
+            for (unsigned yy = y0; yy < y1; ++yy)
+                for (unsigned xx = x0; xx < x1; ++xx) {
+                    if (!d_support_reaches(D, (float)(xx * T), (float)(yy * T), (float)T)) continue;
+                    int t = (int)(yy * (unsigned)tx + xx);
+                    if (pass == 0) cnt[t]++;
+                    else {
+                        if (cnt[t] < cap) ids[cnt[t]] = (unsigned)k;
+                        cnt[t]++;
+                    }
+                }
+        }
+    }
+    long long total = 0;
+    for (int t = 0; t < nt; ++t) total += ranges[2 * t + 1] - ranges[2 * t];
+    free(cnt);
+    viewset_free(&vs);
+    JD = save;
+    return total;
 }
 
 /* exported for tests: the sorted global order of a view */

@@ -247,6 +247,20 @@ def solve(group, scene, primary, g, H, cfg=None):
     return dict(step=step, status=status, info=info, cond=cond, nfail=nfail)
 
 
+def reduced_basis(group, scene, primary, cfg=None):
+    """[n][3][2] basis of the reduced position / scaling solve, its status [n]
+    and, for scaling, how close the reduction is to degenerate [n]."""
+    sh = scene_handle(scene)
+    B = np.zeros((sh.n, 3, 2))
+    st = np.zeros(sh.n, np.int32)
+    gap = np.zeros(sh.n)
+    r = lib().orc_reduced_basis(C.c_int(group), C.byref(sh.c), C.byref(cam_struct(primary)),
+                                C.byref(cfg_struct(cfg)), _d(B), st.ctypes.data_as(_ip), _d(gap))
+    if r != 0:
+        raise ValueError("reduced_basis: position or scaling only")
+    return B, st, gap
+
+
 def apply(group, scene, primary, step, cfg=None):
     """Returns a new FP64 scene handle with the step applied."""
     src = scene_handle(scene)
@@ -318,6 +332,34 @@ def tile_touch(scene, cam, tile, cfg=None):
     lib().orc_tile_touch(C.byref(sh.c), C.byref(cam_struct(cam)), C.byref(cfg_struct(cfg)), C.c_int(tile),
                          touch.ctypes.data_as(C.POINTER(C.c_ubyte)), _d(rect))
     return touch, rect
+
+
+def dec32(scene, cam, cfg=None):
+    """FP32 decision records [18][n] (the layout of the library's projection dump;
+    rows 15, 16 hold the tile rectangle's words as bit patterns)."""
+    sh = scene_handle(scene)
+    out = np.zeros((18, sh.n), np.float32)
+    lib().orc_dec32(C.byref(sh.c), C.byref(cam_struct(cam)), C.byref(cfg_struct(cfg)), out.ctypes.data_as(_fp))
+    return out
+
+
+def tile_lists(scene, cam, cfg=None):
+    """Tile lists of 16x16 tiles by plain loops: (ranges [ntiles][2], ids)."""
+    sh = scene_handle(scene)
+    W, H = int(cam.width), int(cam.height)
+    nt = ((W + 15) // 16) * ((H + 15) // 16)
+    ranges = np.zeros((nt, 2), np.uint32)
+    L = lib()
+    L.orc_tile_lists.restype = C.c_longlong
+    up = C.POINTER(C.c_uint)
+    cap = 1 << 16
+    while True:
+        ids = np.zeros(cap, np.uint32)
+        m = L.orc_tile_lists(C.byref(sh.c), C.byref(cam_struct(cam)), C.byref(cfg_struct(cfg)),
+                             ranges.ctypes.data_as(up), ids.ctypes.data_as(up), C.c_longlong(cap))
+        if m <= cap:
+            return ranges, ids[:m]
+        cap = int(m)
 
 
 def order(scene, cam, cfg=None):

@@ -337,11 +337,11 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                 clamped[q] = false;
                 if (act[q]) {
                     dy[q] = __fsub_rn(q ? fy1 : fy0, A.y);
-                    G[q] = gs2_gauss(A.z, A.w, B.x, dx, dy[q]);
-                    const float araw = __fmul_rn(B.y, G[q]);
-                    clamped[q] = araw > amax;
-                    alpha[q] = fminf(araw, amax);
-                    if (alpha[q] < amin) act[q] = false;
+                    const float qf = dec_quad(A.z, A.w, B.x, dx, dy[q]);
+                    G[q] = gs2_falloff(qf);
+                    clamped[q] = qf < B.w;
+                    alpha[q] = clamped[q] ? amax : __fmul_rn(B.y, G[q]);
+                    if (!(qf <= B.z)) act[q] = false;   // not composited (the same decision as k_raster)
                 }
             }
             if (!__any_sync(0xFFFFFFFFu, act[0] || act[1])) continue;

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "../../include/gs2.h"
+#include "decide.cuh"
 
 #define GS2_TILE 16                  // screen tile edge in pixels
 #define GS2_SORT_BLOCKS_MAX 1024     // the per-digit scan runs one 1024-thread CTA per digit
@@ -35,8 +36,9 @@ static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Layout of the caller-owned projection buffer (opaque to callers).
 struct ProjView {
     float4 *recA;      // (pi_x, pi_y, conic_xx, conic_xy)
-    float4 *recB;      // (conic_yy, sigma, depth, k2 = det Sigma / Sigma_yy^2)
+    float4 *recB;      // (conic_yy, sigma, l, lmax): the thresholds of q (decide.cuh)
     float4 *col;       // (c~_r, c~_g, c~_b, ry = padded half height of the support)
+    float *k2;         // det Sigma / Sigma_yy^2 (row extent of the support ellipse)
     uint2 *rect;       // tile rectangle: x = tx0 | ty0 << 16, y = tx1 | ty1 << 16 (exclusive ends)
     uint32_t *touched; // tiles of rect that the support ellipse reaches (0 = not rendered)
     uint32_t *key;     // FP32 bit pattern of the camera depth (positive)
@@ -46,63 +48,11 @@ struct ProjView {
     uint32_t *tsort;   // touched in depth-rank order
 };
 
-// ----------------------------------------------------- support ellipse per tile row
-// The support of a Gaussian, { d : d^T Sigma^-1 d <= l }, l = 2 ln(sigma / alpha_min),
-// is the pixel set where alpha >= alpha_min.  Row by row (y relative to the centre)
-// it is |x - k1 y| <= sqrt(k2 (ry^2 - y^2)) with k1 = Sigma_xy / Sigma_yy = -conic_xy /
-// conic_xx, k2 = det Sigma / Sigma_yy^2 and ry^2 = l Sigma_yy (padded: ry carries the
-// tile rectangle's margin).  Over the band of pixel rows of one tile row, the largest
-// x is reached at the row nearest the rightmost point of the ellipse (y* = k1 ry /
-// sqrt(k2 + k1^2); x is concave in y there) and the smallest at the row nearest
-// -y*.  A margin of 1e-3 of the extents + 0.05 px covers FP32 rounding of Sigma
-// and of this evaluation, so a tile is dropped only when no pixel of it can
-// reach alpha_min.
-struct SupportRows {
-    float px, py, k1, k2, ry, ystar, marg;
-};
-
-// sqrt.approx (exact 0 at 0); its error is far inside the margin
-__device__ __forceinline__ float approx_sqrt(float x) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ SupportRows support_rows(float px, float py, float ca, float cb, float k2, float ry) {
-    SupportRows s;
-    s.px = px;
-    s.py = py;
-    s.k2 = k2;
-    s.ry = ry;
-    s.k1 = __fdividef(-cb, ca);
-    s.ystar = s.k1 * ry * rsqrtf(k2 + s.k1 * s.k1);
-    s.marg = 0.05f + 1e-3f * (fabsf(s.k1) + approx_sqrt(k2)) * ry;
-    return s;
-}
-
-// Does the support reach a pixel of tile (tx, ty)?
-__device__ __forceinline__ bool support_reaches(const SupportRows &s, uint32_t tx, uint32_t ty) {
-    const float ylo = fmaxf((float)(ty * GS2_TILE), ceilf(s.py - s.ry));
-    const float yhi = fminf((float)(ty * GS2_TILE + GS2_TILE - 1), floorf(s.py + s.ry));
-    if (!(ylo <= yhi)) return false;
-    const float ya = ylo - s.py, yb = yhi - s.py;
-    const float yr = fminf(fmaxf(s.ystar, ya), yb), yl = fminf(fmaxf(-s.ystar, ya), yb);
-    const float r2 = s.ry * s.ry;
-    const float hr = approx_sqrt(fmaxf(s.k2 * (r2 - yr * yr), 0.f));
-    const float hl = approx_sqrt(fmaxf(s.k2 * (r2 - yl * yl), 0.f));
-    const float xr = s.px + s.k1 * yr + hr + s.marg;   // rightmost reach in the band
-    const float xl = s.px + s.k1 * yl - hl - s.marg;   // leftmost
-    // some integer pixel column of the tile lies in [xl, xr]
-    const float c0 = fmaxf(ceilf(xl), (float)(tx * GS2_TILE));
-    const float c1 = fminf(floorf(xr), (float)(tx * GS2_TILE + GS2_TILE - 1));
-    return c0 <= c1;
-}
-
 static inline size_t proj_bytes_impl(int64_t n) {
     size_t b = 0;
     b += align256(16 * (size_t)n) * 3;
     b += align256(8 * (size_t)n);
-    b += align256(4 * (size_t)n) * 8;
+    b += align256(4 * (size_t)n) * 9;
     return b;
 }
 
@@ -112,6 +62,7 @@ static inline ProjView proj_view(void *base, int64_t n) {
     v.recA = (float4 *)p; p += align256(16 * (size_t)n);
     v.recB = (float4 *)p; p += align256(16 * (size_t)n);
     v.col = (float4 *)p; p += align256(16 * (size_t)n);
+    v.k2 = (float *)p; p += align256(4 * (size_t)n);
     v.rect = (uint2 *)p; p += align256(8 * (size_t)n);
     v.touched = (uint32_t *)p; p += align256(4 * (size_t)n);
     v.key = (uint32_t *)p; p += align256(4 * (size_t)n);
@@ -324,18 +275,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Gaussian falloff G = exp(-q/2) at pixel offset (dx, dy), where
-// q = ca dx^2 + 2 cb dx dy + cc dy^2 (the conic's quadratic form).  q is formed
-// by explicitly rounded multiplies and fused multiply-adds in a fixed order
-// (no contraction choice is left to the compiler), and exp(-q/2) is taken as
+// Gaussian falloff G = exp(-q/2) of a quadratic form q (dec_quad), taken as
 // 2^(-q / (2 ln 2)) with the hardware base-2 exponential (relative error
 // ~2^-22, flushed to 0 below the normal range: far inside the image and
-// derivative tolerances).  The compositing and the accumulation both call
-// this function, so their alpha decisions stay identical bit for bit.
-__device__ __forceinline__ float gs2_gauss(float ca, float cb, float cc, float dx, float dy) {
-    float a = __fmaf_rn(ca, dx, __fmul_rn(cb, dy));   // ca dx + cb dy
-    a = __fmaf_rn(cb, dy, a);                         // ca dx + 2 cb dy
-    const float q = __fmaf_rn(dx, a, __fmul_rn(__fmul_rn(cc, dy), dy));
+// derivative tolerances).  It gives the composited values only; whether a term
+// is composited or clamped is decided from q itself (decide.cuh), identically
+// in the compositing and the accumulation.
+__device__ __forceinline__ float gs2_falloff(float q) {
     const float x = __fmul_rn(q, -0.72134752044448170368f);   // -1 / (2 ln 2)
     float g;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(x));

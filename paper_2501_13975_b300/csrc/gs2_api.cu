@@ -899,8 +899,11 @@ __global__ void k_unpack_proj(ProjView pv, int n, float *out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float4 a = pv.recA[k], b = pv.recB[k], c = pv.col[k];
-    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, c.x, c.y, c.z, b.z, (float)pv.touched[k], 0.f};
-    for (int i = 0; i < 12; ++i) out[(size_t)i * n + k] = v[i];
+    const uint2 r = pv.rect[k];
+    const float v[GS2_DEBUG_PROJ_ROWS] = {a.x, a.y, a.z, a.w, b.x, b.y, c.x, c.y, c.z, __uint_as_float(pv.key[k]),
+                                          (float)pv.touched[k], b.z, b.w, pv.k2[k], c.w, __uint_as_float(r.x),
+                                          __uint_as_float(r.y), 0.f};
+    for (int i = 0; i < GS2_DEBUG_PROJ_ROWS; ++i) out[(size_t)i * n + k] = v[i];
 }
 
 extern "C" gs2_status gs2_debug_proj(const void *proj, int64_t n, float *out, gs2_stream stream) {

@@ -12,9 +12,10 @@
 // 4-byte loads across the warp), writes 3 float4 records + rect + counts per
 // view.  HBM-bound; FP64 is used only for the depth key (4 DFMA-equivalent
 // ops).  One launch projects up to GS2_PROJ_VIEWS views of the same scene
-// (the views of a sweep group): the parameters are read once and the
-// rotation is formed once, so four views cost 244 + 4 x 64 bytes per
-// Gaussian instead of 4 x (244 + 64).  The kernel is instantiated per SH
+// (the views of a sweep group): the parameters are read once, so four views
+// cost 244 + 4 x 68 bytes per Gaussian instead of 4 x (244 + 68).  The
+// covariance, conic, thresholds and support box come from the reproducible
+// FP32 projection of decide.cuh (explicitly rounded operations only).  The kernel is instantiated per SH
 // count S, so every parameter load of a visible Gaussian (4 + 3 + 3S rows) is
 // unrolled and issued before the arithmetic: a warp keeps all of them in
 // flight at once instead of meeting the memory latency once per loop
@@ -28,6 +29,7 @@ __device__ __forceinline__ void write_invisible(const ProjView &pv, int k) {
     pv.recA[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     pv.recB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     pv.col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    pv.k2[k] = 0.f;
 }
 
 // depth along the view axis: FP64, fixed summation order (products of FP32
@@ -40,68 +42,21 @@ __device__ __forceinline__ double view_depth(const DevCam &cam, float px, float 
     return d + (double)cam.V[11];
 }
 
-// One visible Gaussian in one view: EWA covariance, conic, tile rectangle,
+// One visible Gaussian in one view: EWA covariance, conic, thresholds and tile
+// rectangle by the reproducible FP32 projection of decide.cuh, then the
 // view-dependent colour; writes its records.
 template <int S>
 __device__ __forceinline__ void project_one(const DevCam &cam, const ProjView &pv, int k, float px, float py, float pz,
-                                            float tz, float sigma, const float (&R)[3][3], const float (&ss)[3],
-                                            const float (&shc)[3 * S], float lowpass, float alpha_min) {
-    const float *V = cam.V;
-    const float tx = fmaf(V[0], px, fmaf(V[1], py, fmaf(V[2], pz, V[3])));
-    const float ty = fmaf(V[4], px, fmaf(V[5], py, fmaf(V[6], pz, V[7])));
-    // T = J Wr (2x3); J uses tx/tz, ty/tz clamped to the camera's frustum limits
-    const float itz = 1.f / tz;
-    const float taux = fminf(fmaxf(tx * itz, -cam.Lx), cam.Lx), tauy = fminf(fmaxf(ty * itz, -cam.Ly), cam.Ly);
-    const float j00 = cam.fx * itz, j02 = -cam.fx * taux * itz;
-    const float j11 = cam.fy * itz, j12 = -cam.fy * tauy * itz;
-    float T0[3], T1[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        T0[j] = j00 * V[j] + j02 * V[8 + j];
-        T1[j] = j11 * V[4 + j] + j12 * V[8 + j];
-    }
-    // Sigma2D = sum_j s_j^2 m_j m_j^T, m_j = T R e_j
-    float m0[3], m1[3];
-    float sxx = 0.f, sxy = 0.f, syy = 0.f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        m0[j] = T0[0] * R[0][j] + T0[1] * R[1][j] + T0[2] * R[2][j];
-        m1[j] = T1[0] * R[0][j] + T1[1] * R[1][j] + T1[2] * R[2][j];
-        sxx = fmaf(ss[j] * m0[j], m0[j], sxx);
-        sxy = fmaf(ss[j] * m0[j], m1[j], sxy);
-        syy = fmaf(ss[j] * m1[j], m1[j], syy);
-    }
-    // det(A + l I) = det A + l tr A + l^2 with det A by Cauchy-Binet,
-    // sum_{i<j} s_i^2 s_j^2 (m_i x m_j)^2: a sum of non-negative terms, so no
-    // cancellation for thin, elongated screen-space ellipses (where
-    // sxx syy - sxy^2 loses all FP32 digits)
-    float detA = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i + 1; j < 3; ++j) {
-            const float cr = m0[i] * m1[j] - m1[i] * m0[j];
-            detA = fmaf(ss[i] * ss[j] * cr, cr, detA);
-        }
-    const float det = detA + lowpass * (sxx + syy) + lowpass * lowpass;
-    sxx += lowpass;
-    syy += lowpass;
-    const float idet = 1.f / det;
-    const float ca = syy * idet, cb = -sxy * idet, cc = sxx * idet;
-    const float pix_x = fmaf(cam.fx * tx, itz, cam.cx);
-    const float pix_y = fmaf(cam.fy * ty, itz, cam.cy);
-
-    // tile rectangle of the support ellipse (half extents sqrt(2 ln(sigma/alpha_min) Sigma_ii)),
-    // widened slightly so FP32 rounding can only add tiles, never drop one
-    const float l = 2.f * logf(sigma / alpha_min);
-    const float rx = sqrtf(fmaxf(l * sxx, 0.f)) * 1.0005f + 0.02f;
-    const float ry = sqrtf(fmaxf(l * syy, 0.f)) * 1.0005f + 0.02f;
-    const float fx0 = fmaxf(ceilf(pix_x - rx), 0.f), fx1 = fminf(floorf(pix_x + rx), (float)(cam.w - 1));
-    const float fy0 = fmaxf(ceilf(pix_y - ry), 0.f), fy1 = fminf(floorf(pix_y + ry), (float)(cam.h - 1));
-    // det Sigma / Sigma_yy^2: with k1 = -conic_xy / conic_xx and ry it gives the
-    // support's extent in x row by row (the pair emission keeps only the tiles
-    // of the rectangle that the ellipse reaches)
-    const float k2 = det / (syy * syy);
+                                            float tz, float sigma, const float (&q)[4], const float (&s)[3],
+                                            const float (&shc)[3 * S], float lowpass, float alpha_min,
+                                            float alpha_max) {
+    const DecRec d = dec_project(cam.V, cam.fx, cam.fy, cam.cx, cam.cy, cam.Lx, cam.Ly, px, py, pz, tz, q[0], q[1],
+                                 q[2], q[3], s[0], s[1], s[2], sigma, lowpass, alpha_min, alpha_max);
+    // tile rectangle of the padded support box (exclusive ends)
+    const float fx0 = fmaxf(ceilf(__fsub_rn(d.px, d.rx)), 0.f);
+    const float fx1 = fminf(floorf(__fadd_rn(d.px, d.rx)), (float)(cam.w - 1));
+    const float fy0 = fmaxf(ceilf(__fsub_rn(d.py, d.ry)), 0.f);
+    const float fy1 = fminf(floorf(__fadd_rn(d.py, d.ry)), (float)(cam.h - 1));
     uint32_t touched = 0u;
     uint2 rect = make_uint2(0u, 0u);
     if (fx0 <= fx1 && fy0 <= fy1) {
@@ -127,15 +82,16 @@ __device__ __forceinline__ void project_one(const DevCam &cam, const ProjView &p
         for (int i = 0; i < S; ++i) acc = fmaf(sh_norm(i) * phi[i], shc[c * S + i], acc);
         col[c] = acc;
     }
-    // recB.w, col.w: the support's row parameters k2 and ry (tile emission)
-    pv.recA[k] = make_float4(pix_x, pix_y, ca, cb);
-    pv.recB[k] = make_float4(cc, sigma, tz, k2);
-    pv.col[k] = make_float4(col[0], col[1], col[2], ry);
+    pv.recA[k] = make_float4(d.px, d.py, d.ca, d.cb);
+    pv.recB[k] = make_float4(d.cc, sigma, d.l, d.lmax);
+    pv.col[k] = make_float4(col[0], col[1], col[2], d.ry);
+    pv.k2[k] = d.k2;
 }
 
 template <int S>
 __global__ void __launch_bounds__(256) k_project(DevScene sc, ProjViews views, float lowpass, float near_z,
-                                                 float alpha_min, uint32_t *__restrict__ status) {
+                                                 float alpha_min, float alpha_max,
+                                                 uint32_t *__restrict__ status) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= sc.n) return;
     const int n = sc.n, nv = views.nv;
@@ -169,7 +125,7 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, ProjViews views, f
     float shc[3 * S];
 #pragma unroll
     for (int i = 0; i < 3 * S; ++i) shc[i] = __ldcs(sc.sh + (size_t)i * n + k);
-    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
+    const float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
     const float s0 = sc.scale[k], s1 = sc.scale[n + k], s2 = sc.scale[2 * n + k];
     if (!(isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(s0) && isfinite(s1) &&
           isfinite(s2))) {
@@ -179,19 +135,12 @@ __global__ void __launch_bounds__(256) k_project(DevScene sc, ProjViews views, f
             if (v < nv) write_invisible(views.pv[v], k);
         return;
     }
-    // rotation from the normalised quaternion (shared by the views)
-    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-    float R[3][3];
-    R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
-    R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
-    R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
-    const float ss[3] = {s0 * s0, s1 * s1, s2 * s2};
-#pragma unroll
+    const float qv[4] = {qw, qx, qy, qz}, sv[3] = {s0, s1, s2};
     for (int v = 0; v < GS2_PROJ_VIEWS; ++v) {
         if (v >= nv) break;
         if (vis[v])
-            project_one<S>(views.cam[v], views.pv[v], k, px, py, pz, tz[v], sigma, R, ss, shc, lowpass, alpha_min);
+            project_one<S>(views.cam[v], views.pv[v], k, px, py, pz, tz[v], sigma, qv, sv, shc, lowpass, alpha_min,
+                           alpha_max);
         else
             write_invisible(views.pv[v], k);
     }
@@ -202,10 +151,10 @@ cudaError_t launch_project_views(const DevScene &sc, const ProjViews &views, con
     if (sc.n == 0 || views.nv == 0) return cudaSuccess;
     const unsigned grid = (sc.n + 255) / 256;
     switch (sc.S) {
-    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
-    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
-    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
-    default: k_project<16><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, status); break;
+    case 1: k_project<1><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, cfg.alpha_max, status); break;
+    case 4: k_project<4><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, cfg.alpha_max, status); break;
+    case 9: k_project<9><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, cfg.alpha_max, status); break;
+    default: k_project<16><<<grid, 256, 0, st>>>(sc, views, cfg.lowpass, cfg.near_z, cfg.alpha_min, cfg.alpha_max, status); break;
     }
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();

@@ -4,7 +4,9 @@
 // batch, copied asynchronously into the second buffer while the first is
 // walked; the per-pixel inner loop reads shared memory only).
 //   alpha = min(sigma G, alpha_max); skip alpha < alpha_min; stop before
-//   T (1 - alpha) < t_min; c += alpha T c~; black background.
+//   T (1 - alpha) < t_min; c += alpha T c~; black background.  Whether a term
+//   is skipped or clamped is decided from its quadratic form q against the
+//   Gaussian's thresholds l, lmax (decide.cuh), reproducibly.
 // Writes the planar image, the final transmittance and the list position
 // after the last contributor (consumed by the accumulation pass).
 #include "common.cuh"
@@ -54,9 +56,9 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
         for (int i = 0; i < m && !done; ++i) {
             const float4 A = sA[buf][i];
             const float4 B = sB[buf][i];
-            const float G = gs2_gauss(A.z, A.w, B.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
-            const float alpha = fminf(__fmul_rn(B.y, G), amax);
-            if (alpha < amin) continue;
+            const float q = dec_quad(A.z, A.w, B.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
+            if (!(q <= B.z)) continue;   // sigma G < alpha_min
+            const float alpha = q < B.w ? amax : __fmul_rn(B.y, gs2_falloff(q));
             const float tt = __fmul_rn(T, __fsub_rn(1.f, alpha));
             if (tt < tmin) {
                 done = true;

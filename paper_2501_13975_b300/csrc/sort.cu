@@ -111,7 +111,9 @@ __global__ void k_gather_touched(ProjView pv, const uint32_t *__restrict__ order
 // CTA's offsets in shared memory.  A tile of the rectangle that the Gaussian's
 // support ellipse does not reach gets the key ntiles: it sorts after every
 // tile and the range pass leaves it out of the lists, so the compositing and
-// the accumulation never walk it.
+// the accumulation never walk it.  The tile test is the reproducible FP32
+// support_reaches of decide.cuh, so the lists are a function of the FP32
+// parameters and camera alone, bit for bit.
 __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__restrict__ order, int n, int tiles_x,
                                               uint32_t ntiles, uint32_t cap, uint32_t *keys, uint32_t *vals,
                                               unsigned long long *stats) {
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
     s_id[t] = id;
     if (cnt != 0u) {
         const float4 A = pv.recA[id];
-        s_sr[t] = support_rows(A.x, A.y, A.z, A.w, pv.recB[id].w, pv.col[id].w);
+        s_sr[t] = support_rows(A.x, A.y, A.z, A.w, pv.k2[id], pv.col[id].w);
         const uint2 rc = s_rect[t];
         s_inv[t] = 1.f / (float)((rc.y & 0xFFFFu) - (rc.x & 0xFFFFu));
     }
@@ -166,7 +168,9 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
             rem -= (int)wdt;
         }
         const uint32_t tx = tx0 + (uint32_t)rem, ty = ty0 + row;
-        keys[j] = support_reaches(s_sr[lo], tx, ty) ? ty * (uint32_t)tiles_x + tx : ntiles;
+        keys[j] = support_reaches(s_sr[lo], (float)(tx * GS2_TILE), (float)(ty * GS2_TILE), (float)GS2_TILE)
+                      ? ty * (uint32_t)tiles_x + tx
+                      : ntiles;
         vals[j] = s_id[lo];
     }
 }

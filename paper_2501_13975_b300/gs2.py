@@ -129,6 +129,7 @@ EXPORTED = tuple(_sigs)
 
 # learned step scale (include/gs2.h)
 MLP_NFEAT, MLP_HIDDEN, MLP_NPARAM, MLP_GRID, REC_ROWS = 8, 64, 4801, 148, 11
+DEBUG_PROJ_ROWS = 18   # gs2_debug_proj rows (include/gs2.h)
 
 
 class GS2Error(RuntimeError):
@@ -452,7 +453,7 @@ class Context:
 
     @staticmethod
     def debug_proj(proj, n, stream=None):
-        out = torch.empty((12, n), dtype=torch.float32, device="cuda")
+        out = torch.empty((DEBUG_PROJ_ROWS, n), dtype=torch.float32, device="cuda")
         keys = torch.empty(n, dtype=torch.int32, device="cuda")
         assert _lib.gs2_debug_proj(_ptr(proj), int(n), _ptr(out), _stream(stream)) == 0
         assert _lib.gs2_debug_keys(_ptr(proj), int(n), _ptr(keys), _stream(stream)) == 0

@@ -1,13 +1,14 @@
 """GPU (CUDA path through the C ABI) vs FP64 oracle, element by element on the
 same seeded inputs.
 
-Tolerances (stated by the build target): images <= 1e-5 max abs, gradients
-<= 1e-4 relative, Hessian blocks <= 1e-3 relative, tile binning and sort
-order bit-exact.  "Relative" for a block entry is relative to the oracle's sum
+Tolerances: images <= 1e-5 max abs, gradients <= 1e-4 relative, Hessian
+blocks <= 1e-3 relative, tile binning and sort order bit-exact.  "Relative" for a block entry is relative to the oracle's sum
 of absolute per-pixel terms of that entry (the scale FP32 accumulation error
-grows with), floored at 1e-6 of the largest such scale.  Decisions that sit
-within 1e-4 (relative) of a threshold in the oracle are excluded and counted
-(the result of such a decision is not unique between FP32 and FP64)."""
+grows with), floored at 1e-6 of the largest such scale.  Whether a term is
+composited or clamped, and which tiles list a Gaussian, are FP32 decisions
+that the oracle takes identically; only the early stop at t_min is taken in
+FP64 by the oracle, and terms within 2e-5 (relative) of it are excluded and
+counted (the result of such a decision is not unique between FP32 and FP64)."""
 import numpy as np
 import pytest
 
@@ -55,33 +56,39 @@ def _render_both(gs2, ctx, ocfg, sc, cam):
 
 @pytest.mark.parametrize("size", [128, 100])
 def test_project_parity_and_keys(gs2, size):
+    """The projection's decision fields (centre, conic, thresholds l and lmax,
+    k2, padded ry, tile rectangle, tiles touched, depth key) are bit-identical
+    to the oracle's FP32 decision record; the colour matches the FP64 oracle."""
     sc, cams = _tiny(sh=3, size=size)
     ctx, gcfg, ocfg = _setup(gs2, sc, cams)
     ds = gs2.DeviceScene.from_host(sc)
     for cam in cams[:2]:
         proj = ctx.project(ds, cam)
         out, keys = ctx.debug_proj(proj, sc.n)
-        out = out.cpu().numpy().astype(np.float64)
+        out = out.cpu().numpy()
         keys = keys.cpu().numpy().view(np.uint32)
         pr = O.project(sc, cam, ocfg)
+        dec = O.dec32(sc, cam, ocfg)
         vis = (~pr["culled"]) & (pr["opacity"] >= ocfg["alpha_min"])
         assert (out[10] > 0).sum() > 100
         assert np.all(out[10][~vis] == 0)
-        assert np.array_equal(keys[vis], pr["key"][vis].view(np.uint32))
-        assert rel_err(out[0:2, vis], pr["pix"][:, vis], 1.0) < 2e-4          # pixels
-        con = pr["conic"][:, vis]
-        assert rel_err(out[2:5, vis], con, np.abs(con).max(0)) < 1e-4
+        assert np.array_equal(keys, pr["key"].view(np.uint32))
+        for row in (0, 1, 2, 3, 4, 5, 10, 11, 12, 13, 14, 15, 16):
+            a, b = out[row][vis].view(np.uint32), dec[row][vis].view(np.uint32)
+            assert np.array_equal(a, b), (row, np.nonzero(a != b)[0][:5])
         assert rel_err(out[6:9, vis], pr["color"][:, vis], 1.0) < 1e-5
+
+
+def _lists(ranges, ids):
+    return [ids[r0:r1].tolist() for r0, r1 in ranges]
 
 
 @pytest.mark.parametrize("size,n,big", [(128, 1000, False), (100, 700, False), (40, 300, False), (512, 300, True)])
 def test_binning_and_sort_bit_exact(gs2, size, n, big):
-    """Every tile list is sorted by (FP32 depth key, index), holds every
-    Gaussian that has a pixel with alpha >= alpha_min in the tile, and no
-    Gaussian twice; an extra entry lies within the Gaussian's support box and
-    within a fraction of a pixel of its support ellipse (the lists follow the
-    ellipse, not its box).  The large case has footprints of about 20 tile rows,
-    where a box holds many tiles the ellipse misses."""
+    """Every tile list equals the oracle's plain-loop binning of the same FP32
+    support test, Gaussian for Gaussian and in the same (depth key, index)
+    order.  The large case has footprints of about 20 tile rows, where a box
+    holds many tiles the ellipse misses."""
     if big:
         sc = synth.tiny_scene(seed=4, n=n, sh_degree=0, log_scale=(-1.0, 0.3))
         cams = synth.ring_cameras(4, size)
@@ -89,46 +96,16 @@ def test_binning_and_sort_bit_exact(gs2, size, n, big):
         sc, cams = _tiny(n=n, size=size)
     ntile = ((size + 15) // 16) ** 2
     ctx, gcfg, ocfg = _setup(gs2, sc, cams, max_pairs=n * ntile if big else 0)
-    cam = cams[0]
-    ds, proj, img, rs, orc = _render_both(gs2, ctx, ocfg, sc, cam)
-    ranges, ids, m = ctx.debug_tiles(cam.width, cam.height, capacity=n * ntile if big else 16 * n)
-    ranges = ranges.cpu().numpy()
-    ids = ids.cpu().numpy()
-    touch, rect = O.tile_touch(sc, cam, 16, ocfg)
-    pr = O.project(sc, cam, ocfg)
-    key = pr["key"]
-    tx = (cam.width + 15) // 16
-    listed = int(ranges[:, 1].max())   # sorted pairs past it are tiles the ellipses miss
-    assert listed <= m
-    for t in range(ranges.shape[0]):
-        lst = ids[ranges[t, 0]:ranges[t, 1]]
-        order = sorted(lst.tolist(), key=lambda k: (key[k], k))
-        assert lst.tolist() == order, f"tile {t} not in (key, index) order"
-        need = set(np.nonzero(touch[t] == 1)[0].tolist())
-        assert need <= set(lst.tolist()), f"tile {t} misses {need - set(lst.tolist())}"
-        assert len(set(lst.tolist())) == len(lst), f"tile {t} lists a Gaussian twice"
-        x0, y0 = (t % tx) * 16, (t // tx) * 16
-        gx, gy = np.meshgrid(np.arange(x0, min(x0 + 16, cam.width)), np.arange(y0, min(y0 + 16, cam.height)))
-        for k in set(lst.tolist()) - need:
-            r = rect[:, k]
-            assert r[0] - 1 <= x0 + 15 and r[2] + 1 >= x0 and r[1] - 1 <= y0 + 15 and r[3] + 1 >= y0, (t, k)
-            # an extra entry is a tile the support ellipse nearly reaches: some
-            # pixel lies within delta of { d^T A d <= l } (sqrt(q) is a norm
-            # with Lipschitz constant sqrt(lambda_max(A)))
-            a, b, c = pr["conic"][:, k]
-            dx, dy = gx - pr["pix"][0, k], gy - pr["pix"][1, k]
-            q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
-            lam = 0.5 * (a + c) + np.hypot(0.5 * (a - c), b)
-            ell = 2 * np.log(pr["opacity"][k] / ocfg["alpha_min"])
-            delta = 0.2 + 5e-3 * (r[2] - r[0] + r[3] - r[1])
-            assert np.sqrt(q.min()) <= np.sqrt(ell) + delta * np.sqrt(lam), (t, k, q.min(), ell)
-    # the lists cover the support ellipses, not their bounding rectangles
-    with np.errstate(invalid="ignore"):
-        px0, py0 = np.maximum(np.ceil(rect[0]), 0), np.maximum(np.ceil(rect[1]), 0)
-        px1, py1 = np.minimum(np.floor(rect[2]), cam.width - 1), np.minimum(np.floor(rect[3]), cam.height - 1)
-        vis = (~pr["culled"]) & (pr["opacity"] > ocfg["alpha_min"]) & (px0 <= px1) & (py0 <= py1)
-    box = (px1 // 16 - px0 // 16 + 1) * (py1 // 16 - py0 // 16 + 1)
-    assert listed < box[vis].sum(), (listed, box[vis].sum())
+    for cam in cams[:2]:
+        ds, proj, img, rs, orc = _render_both(gs2, ctx, ocfg, sc, cam)
+        ranges, ids, m = ctx.debug_tiles(cam.width, cam.height, capacity=n * ntile if big else 16 * n)
+        got = _lists(ranges.cpu().numpy(), ids.cpu().numpy())
+        oranges, oids = O.tile_lists(sc, cam, ocfg)
+        want = _lists(oranges, oids)
+        assert len(got) == len(want)
+        bad = [t for t in range(len(want)) if got[t] != want[t]]
+        assert not bad, (bad[:5], got[bad[0]], want[bad[0]])
+        assert int(ranges[:, 1].max()) == len(oids) <= m   # sorted pairs past the lists are box tiles the ellipses miss
 
 
 @pytest.mark.parametrize("size,n,sh", [(128, 1000, 0), (100, 700, 3), (33, 200, 1)])
@@ -220,15 +197,30 @@ def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, e
 
 
 def _check_blocks(r, gtol=1e-4, htol=1e-3):
+    """Entries relative to the oracle's sum of absolute per-pixel terms (the
+    scale the FP32 accumulation error grows with; floored at 1e-6 of the
+    largest), plus the plain relative error |got - want| / |want| on the
+    entries that do not cancel (|want| >= half their absolute-term sum), where
+    it is at most twice the first.  Gaussians touched by an ambiguous
+    decision are excluded, counted, and held to 5% of the contributors."""
     ob, amb = r["ob"], r["amb"]
-    keep = ~amb & (ob["npix"] > 0)
-    assert keep.sum() >= 0.5 * (ob["npix"] > 0).sum(), (keep.sum(), amb.sum())
+    contrib = ob["npix"] > 0
+    keep = ~amb & contrib
+    excl = int((amb & contrib).sum())
     gs = np.maximum(ob["gabs"], 1e-6 * ob["gabs"].max())
     hs = np.maximum(ob["Habs"], 1e-6 * ob["Habs"].max())
     eg = rel_err(r["g"][..., keep], ob["g"][..., keep], gs[..., keep])
     eh = rel_err(r["H"][..., keep], ob["H"][..., keep], hs[..., keep])
+    plain = {}
+    for name, got, want, absv in (("g", r["g"], ob["g"], ob["gabs"]), ("H", r["H"], ob["H"], ob["Habs"])):
+        sel = (np.abs(want) >= 0.5 * absv) & (absv > 1e-6 * absv.max()) & keep
+        plain[name] = float(np.max(np.abs(got[sel] - want[sel]) / np.abs(want[sel]))) if sel.any() else 0.0
+    print(f"excluded {excl} of {int(contrib.sum())} contributors; scaled g {eg:.2e} H {eh:.2e}; "
+          f"plain relative on non-cancelling entries g {plain['g']:.2e} H {plain['H']:.2e}")
+    assert excl <= 0.05 * contrib.sum(), (excl, int(contrib.sum()))
     assert eg <= gtol, eg
     assert eh <= htol, eh
+    assert plain["g"] <= 2 * gtol and plain["H"] <= 2 * htol, plain
     # zero where the oracle has no contribution
     assert np.all(r["g"][..., ob["npix"] == 0] == 0)
 
@@ -263,73 +255,6 @@ def test_blocks_parity_secondary_sh3(gs2, group):
     """Downsampled secondary view, primary-view axes, SH degree 3 colour path."""
     r = _blocks_case(gs2, group, sh=3, lam=0.2, secondary=True, n=1500, size=96)
     _check_blocks(r)
-
-
-def _damped(Hf, mu0, tries):
-    """The oracle's accepted damping shift for a dense block (numpy, for tolerance scales)."""
-    m = np.abs(np.diag(Hf)).mean()
-    mu = mu0
-    for _ in range(tries + 1):
-        A = Hf + mu * m * np.eye(Hf.shape[0])
-        if np.linalg.eigvalsh(A).min() > 0:
-            return A
-        mu *= 10
-    return None
-
-
-def _full(Hp, D):
-    H = np.zeros((D, D))
-    iu = np.triu_indices(D)
-    H[iu] = Hp
-    H[(iu[1], iu[0])] = Hp
-    return H
-
-
-@pytest.mark.parametrize("group", [1, 3, 4])
-def test_newton_steps_end_to_end(gs2, group):
-    """Blocks accumulated on the GPU and solved on the GPU vs the oracle doing
-    both: the step error bound is the block tolerances (g 1e-4, H 1e-3 of their
-    absolute-term scales) propagated through the damped inverse,
-    |dx| <= 1e-3 |x| + |H~^-1| (1e-4 |gabs| + 1e-3 |Habs| |x|)."""
-    sh = 1 if group == O.COLOR else 0
-    r = _blocks_case(gs2, group, sh=sh, lam=0.2)
-    ctx, ds, primary, ob, ocfg = r["ctx"], r["ds"], r["primary"], r["ob"], r["ocfg"]
-    step = ctx.solve(group, r["blocks"], 1, ds, primary).cpu().numpy()
-    os_ = O.solve(group, r["sc"], primary, ob["g"], ob["H"], ocfg)
-    n, S = r["sc"].n, (sh + 1) ** 2
-    keep = ~r["amb"] & (ob["npix"] > 0)
-    checked = 0
-    for k in np.nonzero(keep)[0]:
-        chans = range(3) if group == O.COLOR else [None]
-        for ch in chans:
-            if group == O.COLOR:
-                st = os_["status"][ch, k]
-                if st != 0 or os_["info"][ch, 1, k] < 1e-3:
-                    continue
-                Hf = _full(ob["H"][ch, :, k], S)
-                ga, Ha = np.abs(ob["gabs"][ch, :, k]).sum(), np.abs(ob["Habs"][ch, :, k]).sum()
-                x = os_["step"][ch, :, k]
-                y = step[(ch * S) * n + k: (ch * S + S) * n + k: n]
-            else:
-                st = os_["status"][k]
-                if st != 0 or os_["info"][1, k] < 1e-3:
-                    continue
-                Hf = ob["H"][:, k].reshape(1, 1).copy()
-                if group == O.OPACITY:
-                    sg = float(r["sc"].opacity[k])
-                    a = ocfg["barrier_alpha"]
-                    Hf += a * (1 / sg ** 2 + 1 / (1 - sg) ** 2)
-                ga, Ha = ob["gabs"][0, k], ob["Habs"][0, k]
-                x = os_["step"][:, k]
-                y = step[k:k + 1]
-            A = _damped(Hf, ocfg["damping_mu0"], ocfg["damping_tries"])
-            inv = np.linalg.norm(np.linalg.inv(A), 2)
-            bound = 1e-3 * np.linalg.norm(x) + inv * (1e-4 * ga + 1e-3 * Ha * np.linalg.norm(x))
-            if group == O.OPACITY:   # fraction-to-boundary clipping is 1-Lipschitz
-                bound += 1e-6
-            assert np.linalg.norm(y - x) <= bound, (k, ch, y, x, bound)
-            checked += 1
-    assert checked > 100
 
 
 def _random_blocks(group, n, S, rng):

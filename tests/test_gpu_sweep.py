@@ -216,6 +216,33 @@ def test_full_size_render_sampled(scene_workload):
     assert worst[0][0] <= 1e-5, worst[:8]
 
 
+def test_full_size_tile_lists_bit_exact(scene_workload):
+    """Scene workload at full size (1M Gaussians, 1600x1040, about 15M listed
+    pairs): the GPU's tile lists equal the oracle's plain-loop binning, every
+    tile, Gaussian for Gaussian, in (depth key, index) order."""
+    from paper_2501_13975_b300 import gs2
+    gt, cams = scene_workload
+    cam = cams[17]
+    ctx = gs2.Context(gt.n, cam.width, cam.height, 3, 48_000_000)
+    ocfg = oracle_cfg(ctx.config)
+    ds = gs2.DeviceScene.from_host(gt)
+    proj = ctx.project(ds, cam)
+    ctx.raster_fwd(ds, cam, proj)
+    torch.cuda.synchronize()
+    ctx.check()
+    ranges, ids, m = ctx.debug_tiles(cam.width, cam.height, capacity=48_000_000)
+    ranges = ranges.cpu().numpy().astype(np.int64)
+    ids = ids.cpu().numpy().view(np.uint32)
+    oranges, oids = O.tile_lists(gt, cam, ocfg)
+    oranges = oranges.astype(np.int64)
+    glen, olen = ranges[:, 1] - ranges[:, 0], oranges[:, 1] - oranges[:, 0]
+    assert len(oids) > 5_000_000
+    assert np.array_equal(glen, olen), np.nonzero(glen != olen)[0][:5]
+    ne = olen > 0
+    assert np.array_equal(ranges[ne, 0], oranges[ne, 0])
+    assert np.array_equal(ids[:len(oids)], oids)
+
+
 @pytest.mark.parametrize("group", [0, 2])
 def test_full_size_blocks_on_crop_view(scene_workload, group):
     """All 1M Gaussians (SH degree 3) against a 32x24 crop view of a scene
