@@ -293,6 +293,64 @@ def run_gpu(args, rank, world, local_rank):
     ms_e2e = e0.elapsed_time(e1)
     check()
 
+    # the extra timings below use the device-resident targets again
+    if batch is not None:
+        batch.set_targets(prep, 0, targets)
+    # ---------------- the plain FP32 path on the same workload, timed the same
+    # way (device-resident, one graph per sweep), beside the precision form
+    fp32_path = None
+    if args.precision == 1 and not args.no_fp32_path:
+        if batch is not None:
+            batch.set_config(0, precision=0)
+        ctx.set_config(precision=0)
+        for i in range(2):
+            sweep(2000 + i)
+        torch.cuda.synchronize()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(args.steps):
+            sweep(2002 + i)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        check()
+        fms = f0.elapsed_time(f1) / args.steps
+        fp32_path = {"sweeps_per_s": round(1000.0 / fms, 4), "ms_per_sweep": round(fms, 3),
+                     "what": "the same sweeps with precision 0 (FP32 accumulation, FP32 solves only)"}
+        if batch is not None:
+            batch.set_config(0, precision=args.precision)
+        ctx.set_config(precision=args.precision)
+
+    # ---------------- deterministic mode (identical bytes on every run: per-entry
+    # partials, fixed-order sums, views one after another), timed the same way
+    det_path = None
+    if not args.no_det_path:
+        if batch is not None:
+            batch.set_config(0, deterministic=1)
+        ctx.set_config(deterministic=1)
+        for i in range(2):
+            sweep(3000 + i)
+        torch.cuda.synchronize()
+        barrier()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        nd = max(1, min(args.steps, 5))
+        d0.record(stream)
+        for i in range(nd):
+            sweep(3002 + i)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        check()
+        dms = d0.elapsed_time(d1) / nd
+        det_path = {"sweeps_per_s": round(1000.0 / dms, 4), "ms_per_sweep": round(dms, 3), "sweeps": nd,
+                    "what": "deterministic = 1 with the headline's precision (bit-identical blocks and parameters)"}
+        if batch is not None:
+            batch.set_config(0, deterministic=0)
+        ctx.set_config(deterministic=0)
+
     if world > 1:
         ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
 
@@ -401,6 +459,8 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": roofline,
         "stages": stages,
         "jacobi_groups": jacobi,
+        "fp32_path": fp32_path,
+        "deterministic_path": det_path,
         "gpu_launches": int(launches),
         "tuning": tuning,
         "launch": "one CUDA graph per sweep (captured, updated in place)" if args.graph else "eager",
@@ -1024,7 +1084,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v8"
+KERNEL_REV = "accum-v9"
 
 
 def main():
@@ -1037,7 +1097,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-crop", type=int, default=12)
     ap.add_argument("--ref-crop", type=int, default=8)
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the precision form of the scene workload (FP64 accumulation of FP32 "
+                         "partials, FP64 re-solve of blocks with condition estimate > 1e6); 0: FP32 only")
+    ap.add_argument("--no-fp32-path", action="store_true", help="skip timing the FP32 path beside the mixed one")
+    ap.add_argument("--no-det-path", action="store_true", help="skip timing the deterministic mode")
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (profiling captures)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],

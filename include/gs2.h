@@ -128,6 +128,14 @@ typedef struct {
                                > 0 = the first-order baseline, step -gd_lr g of the group's gradient
                                (opacity with the barrier's), inside the same trust radii and bounds
                                (position as a full 3D step) */
+    int32_t deterministic;  /* 0: block sums with float atomics (order of additions not fixed);
+                               1: identical bytes on every run: each (tile, Gaussian) entry of the
+                               tile lists gets its own partial sum (the tile's four warp sums added
+                               in warp order, no atomics), each Gaussian's entries are then summed in
+                               emission order (compensated FP32, or FP64 with precision = 1), and the
+                               views of a sweep run one after another.  Setting it allocates
+                               max_pairs x 41 floats of partials and three max_pairs index arrays in
+                               gs2_create / gs2_set_config (7.9 GB at 48M pairs). */
 } gs2_config;
 
 void gs2_config_default(gs2_config *cfg);
@@ -424,6 +432,14 @@ uint64_t gs2_launch_count(void);
 gs2_status gs2_profile(gs2_ctx *ctx, int32_t enable);
 gs2_status gs2_profile_read(gs2_ctx *ctx, double *accum_ms, int64_t *accum_launches, uint64_t *stats);
 gs2_status gs2_profile_read_stages(gs2_ctx *ctx, double *ms_out, int64_t *count_out);
+
+/* Mixed precision (config.precision = 1): the number of blocks (colour: of
+ * channels) that gs2_solve_step and the sweeps of this context solved again in
+ * FP64 because the FP32 factor's condition estimate (max L_ii / min L_ii)^2
+ * exceeded 1e6 or the FP32 damping ladder failed, per group (host out[5]),
+ * since creation or the last reset (reset != 0 clears them).  Synchronises the
+ * device. */
+gs2_status gs2_fp64_resolves(gs2_ctx *ctx, uint64_t *out, int32_t reset);
 
 /* No-allocation render (the paper has no counterpart; this serves callers).
  * Some callers cannot call cudaMalloc: a plugin or callback run by a host

@@ -89,9 +89,11 @@ template <int P> struct Pad { static constexpr int PP = P <= 2 ? 2 : P <= 4 ? 4 
 // TOP: first butterfly offset; 16 reduces over the whole warp, 8 over each
 // half-warp separately (one step fewer, twice the atomics -- measured slower
 // for the position payload on the scene workload, so 16 is used)
-template <int Q, int OFF, int P, typename ACC, int TOP = 16>
+// STORE (deterministic mode): instead of the atomics, every reduced entry
+// (zeros included) is stored to row[OFF + idx] (shared memory).
+template <int Q, int OFF, int P, typename ACC, int TOP = 16, bool STORE = false>
 __device__ __forceinline__ void reduce_scatter_part(const float (&pl)[P], int lane, ACC *__restrict__ zbuf, int n,
-                                                    uint32_t k) {
+                                                    uint32_t k, float *row = nullptr) {
     constexpr int PP = Pad<Q>::PP;
     constexpr int GROUP_LANES = 2 * TOP;   // lanes that end up sharing one reduction
     float v[PP];
@@ -124,7 +126,11 @@ __device__ __forceinline__ void reduce_scatter_part(const float (&pl)[P], int la
 #pragma unroll
         for (int j = 0; j < (PP >= GROUP_LANES ? PP / GROUP_LANES : 1); ++j) {
             const int idx = off + j;
-            if (idx < Q && v[j] != 0.f) atomicAdd(&zbuf[(size_t)(OFF + idx) * n + k], (ACC)v[j]);
+            if constexpr (STORE) {
+                if (idx < Q) row[OFF + idx] = v[j];
+            } else {
+                if (idx < Q && v[j] != 0.f) atomicAdd(&zbuf[(size_t)(OFF + idx) * n + k], (ACC)v[j]);
+            }
         }
     }
 }
@@ -139,6 +145,20 @@ __device__ __forceinline__ void warp_reduce_scatter_add(const float (&pl)[P], in
         reduce_scatter_part<P, 0, P, ACC>(pl, lane, zbuf, n, k);
     }
 }
+
+// The warp sum of the payload stored to row[0 .. P) (deterministic mode).
+template <int P>
+__device__ __forceinline__ void warp_reduce_scatter_store(const float (&pl)[P], int lane, float *row) {
+    if constexpr (P > 32) {
+        reduce_scatter_part<32, 0, P, float, 16, true>(pl, lane, nullptr, 0, 0u, row);
+        reduce_scatter_part<P - 32, 32, P, float, 16, true>(pl, lane, nullptr, 0, 0u, row);
+    } else {
+        reduce_scatter_part<P, 0, P, float, 16, true>(pl, lane, nullptr, 0, 0u, row);
+    }
+}
+
+// Deterministic mode: list entries per flush of the per-warp sums
+#define GS2_DET_CHUNK 32
 
 // back-to-front state of one pixel
 struct PixState {
@@ -230,13 +250,19 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
     ps.T = Tk;
 }
 
-template <int GROUP, typename ACC>
+// DET (deterministic mode): no atomics.  Every list entry's payload is the
+// sum of the tile's four warp sums taken in warp order, written to
+// det_part[sorted position][P] (entries past the tile's last contributor
+// get zero rows); k_det_reduce then sums each Gaussian's entries in a fixed
+// order into zbuf.
+template <int GROUP, typename ACC, bool DET = false>
 __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_accum(const uint2 *__restrict__ ranges,
                                                            const uint32_t *__restrict__ ids, ProjView pv,
                                                            RasterView rv, const float *__restrict__ E,
                                                            const float *__restrict__ Hh, int W, int H, int tiles_x,
                                                            float amin, float amax, int gn, ACC *__restrict__ zbuf,
-                                                           int n, unsigned long long *__restrict__ active_stat) {
+                                                           int n, unsigned long long *__restrict__ active_stat,
+                                                           float *__restrict__ det_part) {
     constexpr int P = Payload<GROUP>::P;
     constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
     constexpr int PER = NB / GS2_PAIR_THREADS;        // entries each thread stages
@@ -244,7 +270,11 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
+    __shared__ float sDet[DET ? 4 : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
     const int t = threadIdx.x, lane = t & 31;
+    if constexpr (DET) {
+        for (int q = t; q < 4 * GS2_DET_CHUNK * P; q += GS2_PAIR_THREADS) (&sDet[0][0][0])[q] = 0.f;
+    }
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
     const int px = blockIdx.x * GS2_TILE + gs2_pair_px(t), py = blockIdx.y * GS2_TILE + gs2_pair_py(t);
     const size_t PI = (size_t)W * H;
@@ -322,7 +352,9 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
         const int buf = b & 1;
         const int bend = maxlast - NB * b, bbeg = max(0, bend - NB);
         const int base = bend - NB;   // list index of slot 0 of this batch (may be negative)
-        for (int jj = min(bend, wlast) - 1; jj >= bbeg; --jj) {
+        // one list entry (back to front): its payload, then the warp sum
+        // (atomics, or stored to `row` in deterministic mode)
+        auto entry = [&](int jj, float *row) {
             const int s = jj - base;
             const float4 A = sA[buf][s], B = sB[buf][s];
             const float dx = __fsub_rn(fx, A.x);
@@ -344,7 +376,7 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                     if (!(qf <= B.z)) act[q] = false;   // not composited (the same decision as k_raster)
                 }
             }
-            if (!__any_sync(0xFFFFFFFFu, act[0] || act[1])) continue;
+            if (!__any_sync(0xFFFFFFFFu, act[0] || act[1])) return;
             nact += (act[0] ? 1u : 0u) + (act[1] ? 1u : 0u);
             float pl[P];
 #pragma unroll
@@ -353,8 +385,36 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
 #pragma unroll
             for (int q = 0; q < 2; ++q)
                 if (act[q]) pixel_payload<GROUP, P>(ps[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], gn != 0, pl);
-            warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
+            if constexpr (DET)
+                warp_reduce_scatter_store<P>(pl, lane, row);
+            else
+                warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
+        };
+        if constexpr (DET) {
+            const int w = t >> 5;
+            for (int c1 = bend; c1 > bbeg; c1 -= GS2_DET_CHUNK) {   // CTA-uniform chunks
+                const int c0 = max(bbeg, c1 - GS2_DET_CHUNK);
+                for (int jj = min(c1, wlast) - 1; jj >= c0; --jj) entry(jj, &sDet[w][jj - c0][0]);
+                __syncthreads();
+                const int cnt = (c1 - c0) * P;
+                for (int q = t; q < cnt; q += GS2_PAIR_THREADS) {
+                    const int e = q / P, i = q - e * P;
+                    float v = sDet[0][e][i];
+                    v = __fadd_rn(v, sDet[1][e][i]);
+                    v = __fadd_rn(v, sDet[2][e][i]);
+                    v = __fadd_rn(v, sDet[3][e][i]);
+                    sDet[0][e][i] = sDet[1][e][i] = sDet[2][e][i] = sDet[3][e][i] = 0.f;
+                    det_part[(size_t)(r.x + (uint32_t)(c0 + e)) * P + i] = v;
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int jj = min(bend, wlast) - 1; jj >= bbeg; --jj) entry(jj, nullptr);
         }
+    }
+    if constexpr (DET) {   // entries past the last contributor of every pixel contribute nothing
+        const int nl = (int)(r.y - r.x);
+        for (int q = t + maxlast * P; q < nl * P; q += GS2_PAIR_THREADS) det_part[(size_t)r.x * P + q] = 0.f;
     }
     if (active_stat) {
         unsigned long long c = nact;
@@ -787,6 +847,54 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
         for (int b = a; b < 3; ++b) atomicAdd(&blocks[(size_t)(3 + ut3(a, b)) * n + k], Hp[a][b]);
 }
 
+// Deterministic mode: each Gaussian's image-space payload is the sum of its
+// list entries' partials (det_part rows) taken in emission order (the tiles of
+// its rectangle row by row), written to zbuf[P][n] for the epilogues.  FP32
+// sums are compensated (Kahan: the rounding error of every addition is carried
+// into the next); with mixed precision (ACC = double) the sum is FP64.  One
+// thread per depth rank r (Gaussian order[r]); emitted pairs past the pair
+// capacity and box tiles the support ellipse misses (sorted key >= ntiles)
+// hold no entry and are skipped.
+template <int P, typename ACC>
+__global__ void __launch_bounds__(128) k_det_reduce(const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
+                                                    const uint32_t *__restrict__ tsort, int n,
+                                                    const uint32_t *__restrict__ count,
+                                                    const uint32_t *__restrict__ inv,
+                                                    const uint32_t *__restrict__ skeys, uint32_t ntiles,
+                                                    const float *__restrict__ part, ACC *__restrict__ zbuf) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t cnt = tsort[r];
+    if (cnt == 0u) return;
+    const uint32_t id = order[r], M = count[0];
+    const uint32_t j0 = offs[r], j1 = min(j0 + cnt, M);
+    ACC acc[P];
+    float comp[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        acc[i] = 0;
+        comp[i] = 0.f;
+    }
+    for (uint32_t j = j0; j < j1; ++j) {
+        const uint32_t sp = inv[j];
+        if (skeys[sp] >= ntiles) continue;
+        const float *row = part + (size_t)sp * P;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if constexpr (sizeof(ACC) == sizeof(float)) {
+                const float y = __fsub_rn(row[i], comp[i]);
+                const float t = __fadd_rn((float)acc[i], y);
+                comp[i] = __fsub_rn(__fsub_rn(t, (float)acc[i]), y);
+                acc[i] = t;
+            } else {
+                acc[i] += (ACC)row[i];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) zbuf[(size_t)i * n + id] = acc[i];
+}
+
 template <typename ACC>
 static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                            ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks, dim3 grid,
@@ -795,10 +903,25 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     ACC *zb = (ACC *)ctx->zbuf;
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
     unsigned long long *act = pc->prof_on ? pc->d_stats + 5 * group + 3 : nullptr;
+    const bool det = cfg.deterministic != 0 && ctx->det_part && ctx->det_order;
+    const uint32_t ntiles = (uint32_t)(ctx->tiles_x * ctx->tiles_y);
 #define ACC_LAUNCH(G)                                                                                             \
-    k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w,       \
-                                                   view.h, ctx->tiles_x, cfg.alpha_min, cfg.alpha_max, cfg.gauss_newton, \
-                                                   zb, n, act)
+    do {                                                                                                          \
+        if (det) {                                                                                                \
+            k_accum<G, float, true><<<grid, GS2_PAIR_THREADS, 0, st>>>(                                           \
+                ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,    \
+                cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part);                        \
+            if (n > 0)                                                                                            \
+                k_det_reduce<Payload<G>::P, ACC><<<(n + 127) / 128, 128, 0, st>>>(                                \
+                    ctx->det_order, pv.offs, pv.tsort, n, ctx->d_count, ctx->det_inv, ctx->keys[ctx->sorted],     \
+                    ntiles, ctx->det_part, zb);                                                                   \
+        } else {                                                                                                  \
+            k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h,  \
+                                                               view.w, view.h, ctx->tiles_x, cfg.alpha_min,       \
+                                                               cfg.alpha_max, cfg.gauss_newton, zb, n, act,       \
+                                                               (float *)nullptr);                                 \
+        }                                                                                                         \
+    } while (0)
     switch (group) {
     case GS2_POS: ACC_LAUNCH(GS2_POS); break;
     case GS2_ROT: ACC_LAUNCH(GS2_ROT); break;
@@ -807,6 +930,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     default: ACC_LAUNCH(GS2_COLOR); break;
     }
 #undef ACC_LAUNCH
+    if (det) GS2_COUNT_LAUNCH(1);
     if (prof) {
         cudaEventRecord(pc->prof_ev[2 * pc->prof_n + 1], st);
         pc->prof_n++;
@@ -839,7 +963,7 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st) {
     dim3 grid(ctx->tiles_x, ctx->tiles_y);
-    const uint32_t *ids = ctx->vals[ctx->sorted];
+    const uint32_t *ids = ctx->list_ids;
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool (shared by a sweep's view lanes)
     const bool prof = pc->prof_on && pc->prof_n < GS2_PROF_POOL;
     if (prof) {

@@ -146,6 +146,14 @@ struct gs2_ctx {
     uint32_t *d_count;           // [0] clamped pair count, [1] raw count, [2] Gaussian count (depth sort)
     uint2 *ranges;               // [max tiles]
     int sorted;                  // which of keys/vals holds the sorted pairs
+    const uint32_t *list_ids;    // Gaussian ids of the sorted tile lists (vals[sorted], or det_list)
+    // deterministic mode (cfg.deterministic): per-list-entry partials instead
+    // of float atomics, reduced per Gaussian in a fixed order
+    float *det_part;             // [max_pairs][GS2_ZPOS] image-space payload of every (tile, Gaussian) entry
+    uint32_t *det_ids;           // [max_pairs] Gaussian id of every emitted pair (emission order)
+    uint32_t *det_inv;           // [max_pairs] sorted position of every emitted pair
+    uint32_t *det_list;          // [max_pairs] Gaussian ids in sorted order
+    const uint32_t *det_order;   // depth (rank) order of the last binning
     int tiles_x, tiles_y;        // of the last gs2_raster_fwd
     // accumulation
     float *zbuf;                 // [GS2_ZPOS][max_n], zero between uses
@@ -174,6 +182,7 @@ struct gs2_ctx {
     cudaEvent_t prof_ev[2 * GS2_PROF_POOL];
     int prof_group[GS2_PROF_POOL];   // 0..4: accumulation of that group; GS2_PROF_BIN/RASTER/LOSS: stages
     unsigned long long *d_stats; // [5][4]: pairs, visible Gaussians, binnings, accumulation evaluations
+    unsigned long long *d_resolves; // [5]: blocks (colour: channels) solved again in FP64, per group
     int stat_slot;               // group slot the binning statistics go to
     unsigned long long h_pixels[5];
     std::string err;
@@ -218,7 +227,8 @@ cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevC
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st);
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
-                         const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st);
+                         const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st,
+                         unsigned long long *resolves);
 cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);

@@ -58,6 +58,7 @@ extern "C" void gs2_config_default(gs2_config *c) {
     for (int i = 0; i < 5; ++i) c->group_order[i] = i;
     c->group_jacobi = 0;
     for (int i = 0; i < 5; ++i) c->gd_lr[i] = 0.f;
+    c->deterministic = 0;
 }
 
 bool cfg_ok(const gs2_config *c, std::string &err) {
@@ -82,6 +83,7 @@ bool cfg_ok(const gs2_config *c, std::string &err) {
     if (c->group_jacobi != 0 && c->group_jacobi != 1) { err = "group_jacobi must be 0 or 1"; return false; }
     for (int i = 0; i < 5; ++i)
         if (!(c->gd_lr[i] >= 0.f) || !isfinite(c->gd_lr[i])) { err = "gd_lr entries must be finite and >= 0"; return false; }
+    if (c->deterministic != 0 && c->deterministic != 1) { err = "deterministic must be 0 or 1"; return false; }
     return true;
 }
 
@@ -133,8 +135,8 @@ static void free_ctx(gs2_ctx *c) {
         if (c->lane_ev[i]) cudaEventDestroy(c->lane_ev[i]);
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
-                    c->sw_step, c->d_status, c->d_stats, c->flags, c->g_prim, c->lg_phi,
-                    c->order_cache, c->jb_mem};
+                    c->sw_step, c->d_status, c->d_stats, c->d_resolves, c->flags, c->g_prim, c->lg_phi,
+                    c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
@@ -164,6 +166,28 @@ static bool ensure_jacobi(gs2_ctx *c) {
         c->jb_blocks[g] = (float *)((char *)c->jb_mem + off[g]);
         c->jb_step[g] = (float *)((char *)c->jb_mem + off[5 + g]);
     }
+    return true;
+}
+
+// deterministic mode: the per-entry partials and the index arrays (allocated
+// when the option is first set, from the host, never inside a stream capture)
+static bool ensure_det(gs2_ctx *c) {
+    if (c->det_part) return true;
+    const size_t M = (size_t)c->max_pairs;
+    void *p[4] = {nullptr, nullptr, nullptr, nullptr};
+    const size_t bytes[4] = {sizeof(float) * GS2_ZPOS * M, sizeof(uint32_t) * M, sizeof(uint32_t) * M,
+                             sizeof(uint32_t) * M};
+    for (int i = 0; i < 4; ++i)
+        if (cudaMalloc(&p[i], bytes[i]) != cudaSuccess) {
+            for (int j = 0; j < 4; ++j)
+                if (p[j]) cudaFree(p[j]);
+            cudaGetLastError();
+            return false;
+        }
+    c->det_part = (float *)p[0];
+    c->det_ids = (uint32_t *)p[1];
+    c->det_inv = (uint32_t *)p[2];
+    c->det_list = (uint32_t *)p[3];
     return true;
 }
 
@@ -234,6 +258,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A(&c->sw_step, c->sw_step_bytes);
     A((void **)&c->d_status, sizeof(uint32_t) * 4);
     A((void **)&c->d_stats, sizeof(unsigned long long) * 5 * 5);
+    A((void **)&c->d_resolves, sizeof(unsigned long long) * 5);
     A((void **)&c->flags, (size_t)max_n);
     A((void **)&c->g_prim, sizeof(float) * 3 * (size_t)max_n);
     A((void **)&c->lg_phi, sizeof(float) * (size_t)max_n);
@@ -242,6 +267,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 25) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->d_resolves, 0, sizeof(unsigned long long) * 5) == cudaSuccess;
     // view lanes for the secondaries of a sweep
     c->owner = nullptr;
     c->n_lanes = 0;
@@ -280,6 +306,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         if (ok) ok = cudaMemset(l->d_count, 0, sizeof(uint32_t) * 4) == cudaSuccess;
         l->d_status = c->d_status;
         l->d_stats = c->d_stats;
+        l->d_resolves = c->d_resolves;
         l->order_cache = c->order_cache;
         l->owner = c;
         if (ok) ok = cudaStreamCreateWithFlags(&c->lane_st[i], cudaStreamNonBlocking) == cudaSuccess;
@@ -287,6 +314,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     for (int i = 0; i <= nl && ok; ++i)
         ok = cudaEventCreateWithFlags(&c->lane_ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (ok && c->cfg.group_jacobi) ok = ensure_jacobi(c);
+    if (ok && c->cfg.deterministic) ok = ensure_det(c);
     if (!ok) {
         free_ctx(c);
         delete c;
@@ -321,6 +349,8 @@ extern "C" gs2_status gs2_set_config(gs2_ctx *ctx, const gs2_config *cfg) {
         REQUIRE(ctx, ensure_jacobi(ctx), GS2_ERR_OOM, "cannot allocate the per-group blocks of group_jacobi");
         ctx->cfg = keep;
     }
+    if (cfg->deterministic && !ctx->det_part)
+        REQUIRE(ctx, ensure_det(ctx), GS2_ERR_OOM, "cannot allocate the partials of deterministic mode");
     ctx->cfg = *cfg;
     ctx->cfg.knn_k = cfg->knn_k;
     (void)K0;
@@ -473,7 +503,7 @@ extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *
     REQUIRE(ctx, blocks && step, GS2_ERR_ARG, "null buffer");
     REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
     RET_CUDA(ctx, launch_solve(group, blocks, n_views, make_devscene(scene), make_devcam(primary), ctx->cfg, step,
-                               n_failed, ctx->flags, (cudaStream_t)stream));
+                               n_failed, ctx->flags, (cudaStream_t)stream, ctx->d_resolves));
     RET_CUDA(ctx, launch_learned_scale(group, blocks, n_views, make_devscene(scene), step, ctx->g_prim, ctx->cfg,
                                        ctx->mlp_w, (cudaStream_t)stream));
     return GS2_OK;
@@ -628,7 +658,8 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
     // slot i >= 1 on view lane i - 1 (forked and joined with events); their
     // epilogues add into the shared blocks atomically (the logged sweep keeps
     // one stream: its label passes reuse slot 0's scratch)
-    const bool lanes = ctx->view_lanes && !records && nv > 1 && ctx->n_lanes >= nv - 1;
+    // concurrent views add their epilogues atomically: deterministic mode runs them one after another
+    const bool lanes = ctx->view_lanes && !records && nv > 1 && ctx->n_lanes >= nv - 1 && !ctx->cfg.deterministic;
     if (lanes) {
         for (int i = 0; i < nv - 1; ++i) {
             gs2_ctx *l = ctx->lanes[i];
@@ -701,7 +732,7 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         for (int gi = 0; gi < 5; ++gi) {
             const int g = ctx->cfg.group_order[gi];
             RET_CUDA(ctx, launch_solve(g, ctx->jb_blocks[g], nv, dsc, make_devcam(primary), ctx->cfg,
-                                       ctx->jb_step[g], n_failed, ctx->flags, st));
+                                       ctx->jb_step[g], n_failed, ctx->flags, st, ctx->d_resolves));
         }
         for (int gi = 0; gi < 5; ++gi) {
             const int g = ctx->cfg.group_order[gi];
@@ -770,7 +801,7 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         // position step about to be applied invalidates them
         order_valid = group != GS2_POS;
         RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
-                                   ctx->sw_step, n_failed, ctx->flags, st));
+                                   ctx->sw_step, n_failed, ctx->flags, st, ctx->d_resolves));
         float *rec = records ? records + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;
         const DevScene dsc = make_devscene(scene);
         if (!rec) {
@@ -894,6 +925,16 @@ void prof_end(gs2_ctx *ctx, int idx, cudaStream_t st) {
     cudaEventRecord(pc->prof_ev[2 * idx + 1], st);
 }
 
+extern "C" gs2_status gs2_fp64_resolves(gs2_ctx *ctx, uint64_t *out, int32_t reset) {
+    if (!ctx || !out) return GS2_ERR_ARG;
+    unsigned long long h[5];
+    RET_CUDA(ctx, cudaDeviceSynchronize());
+    RET_CUDA(ctx, cudaMemcpy(h, ctx->d_resolves, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < 5; ++g) out[g] = h[g];
+    if (reset) RET_CUDA(ctx, cudaMemset(ctx->d_resolves, 0, sizeof(h)));
+    return GS2_OK;
+}
+
 // ------------------------------------------------------------------ introspection
 __global__ void k_unpack_proj(ProjView pv, int n, float *out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -934,7 +975,7 @@ extern "C" gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32
     const size_t ntiles = (size_t)ctx->tiles_x * ctx->tiles_y;
     RET_CUDA(ctx, cudaMemcpyAsync(ranges_out, ctx->ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
     const size_t m = std::min<size_t>(cnt[0], (size_t)std::max<int64_t>(capacity, 0));
-    if (m) RET_CUDA(ctx, cudaMemcpyAsync(ids_out, ctx->vals[ctx->sorted], sizeof(uint32_t) * m,
+    if (m) RET_CUDA(ctx, cudaMemcpyAsync(ids_out, ctx->list_ids, sizeof(uint32_t) * m,
                                          cudaMemcpyDeviceToDevice, st));
     return GS2_OK;
 }

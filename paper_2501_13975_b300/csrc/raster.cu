@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
 cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
                           RasterView rv, cudaStream_t st) {
     dim3 grid(ctx->tiles_x, ctx->tiles_y);
-    k_raster<<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->vals[ctx->sorted], pv, cam.w, cam.h, ctx->tiles_x,
+    k_raster<<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->list_ids, pv, cam.w, cam.h, ctx->tiles_x,
                                             cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();

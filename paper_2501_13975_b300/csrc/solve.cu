@@ -18,8 +18,8 @@
 // size <= 3 live in registers, the 16x16 colour factor in local memory.
 #include "common.cuh"
 
-template <int NMAX, typename T>
-__device__ int damped_solve_t(int N, const float *H, const float *g, float mu0, int tries, T *x, float *kappa) {
+template <int NMAX, typename T, typename TI = float>
+__device__ int damped_solve_t(int N, const TI *H, const TI *g, float mu0, int tries, T *x, float *kappa) {
     T m = 0, gz = 0;
     for (int i = 0; i < N; ++i) {
         m += fabs((T)H[i * N + i]);
@@ -78,34 +78,39 @@ __device__ int damped_solve_t(int N, const float *H, const float *g, float mu0, 
 
 // FP32 damped solve; with mixed precision (precision = 1) a block whose
 // condition estimate exceeds 1e6 is solved again in FP64.
+// resolves (may be NULL) counts the blocks solved again in FP64.
 template <int NMAX>
-__device__ int damped_solve(int N, const float *H, const float *g, float mu0, int tries, float *x, int precision) {
+__device__ int damped_solve(int N, const float *H, const float *g, float mu0, int tries, float *x, int precision,
+                            unsigned long long *resolves) {
     float kappa = 1.f;
     int st = damped_solve_t<NMAX, float>(N, H, g, mu0, tries, x, &kappa);
     if (precision != 0 && st != 2 && (st == 1 || kappa > 1e6f)) {
         double xd[NMAX];
         st = damped_solve_t<NMAX, double>(N, H, g, mu0, tries, xd, nullptr);
         for (int i = 0; i < N; ++i) x[i] = (float)xd[i];
+        if (resolves) atomicAdd(resolves, 1ull);
     }
     return st;
 }
 
 // Trust radius: a step longer than `radius` is scaled down to it (direction
 // kept); a non-finite step becomes zero and reports failure.
-__device__ __forceinline__ bool trust_scale(int N, float *x, float radius) {
-    float nn = 0.f;
+template <typename T>
+__device__ __forceinline__ bool trust_scale_t(int N, T *x, T radius) {
+    T nn = 0;
     for (int i = 0; i < N; ++i) nn += x[i] * x[i];
-    nn = sqrtf(nn);
+    nn = sqrt(nn);
     if (!isfinite(nn)) {
-        for (int i = 0; i < N; ++i) x[i] = 0.f;
+        for (int i = 0; i < N; ++i) x[i] = 0;
         return true;
     }
     if (nn > radius) {
-        const float f = radius / nn;
+        const T f = radius / nn;
         for (int i = 0; i < N; ++i) x[i] *= f;
     }
     return false;
 }
+__device__ __forceinline__ bool trust_scale(int N, float *x, float radius) { return trust_scale_t<float>(N, x, radius); }
 
 __device__ __forceinline__ void unit_dir(const DevCam &cam, const float p[3], float r[3]) {
     r[0] = p[0] - cam.o[0];
@@ -115,58 +120,83 @@ __device__ __forceinline__ void unit_dir(const DevCam &cam, const float p[3], fl
     r[0] *= in; r[1] *= in; r[2] *= in;
 }
 
+// Basis U = [u_x, u_y] of the plane perpendicular to the primary view ray r
+// and the reduced problem g_v = U^T g, H_v = U^T H U, in the precision T.
+template <typename T>
+__device__ __forceinline__ void pos_reduce(const DevCam &pr, const float p[3], const float g[3], const float (&Hm)[3][3],
+                                           T ux[3], T uy[3], T gv[2], T Hv[4]) {
+    T r[3] = {(T)p[0] - (T)pr.o[0], (T)p[1] - (T)pr.o[1], (T)p[2] - (T)pr.o[2]};
+    const T in = (T)1 / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    r[0] *= in; r[1] *= in; r[2] *= in;
+    T e[3] = {0, 1, 0};
+    if (fabs(r[1]) > (T)0.999) { e[0] = 1; e[1] = 0; }
+    const T d = r[0] * e[0] + r[1] * e[1] + r[2] * e[2];
+    T v[3] = {e[0] - d * r[0], e[1] - d * r[1], e[2] - d * r[2]};
+    const T un = (T)1 / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int i = 0; i < 3; ++i) uy[i] = v[i] * un;
+    ux[0] = r[1] * uy[2] - r[2] * uy[1];
+    ux[1] = r[2] * uy[0] - r[0] * uy[2];
+    ux[2] = r[0] * uy[1] - r[1] * uy[0];
+    const T *U[2] = {ux, uy};
+    for (int a = 0; a < 2; ++a) {
+        gv[a] = U[a][0] * (T)g[0] + U[a][1] * (T)g[1] + U[a][2] * (T)g[2];
+        for (int b = 0; b < 2; ++b) {
+            T acc = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += U[a][i] * (T)Hm[i][j] * U[b][j];
+            Hv[a * 2 + b] = acc;
+        }
+    }
+}
+
+// Position step: the damped 2x2 solve in the plane perpendicular to the view
+// ray.  With mixed precision a block whose FP32 condition estimate exceeds
+// 1e6 (or whose FP32 ladder failed) is solved again with its basis,
+// reduction, factorisation and step all in FP64.
 __global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries, float trust,
-                            float *step, int32_t *nfail, int prec) {
+                            float *step, int32_t *nfail, int prec, unsigned long long *resolves) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
-    float p[3] = {sc.mean[k], sc.mean[n + k], sc.mean[2 * n + k]};
-    float r[3];
-    unit_dir(pr, p, r);
-    float e[3] = {0.f, 1.f, 0.f};
-    if (fabsf(r[1]) > 0.999f) { e[0] = 1.f; e[1] = 0.f; }
-    const float d = r[0] * e[0] + r[1] * e[1] + r[2] * e[2];
-    float uy[3] = {e[0] - d * r[0], e[1] - d * r[1], e[2] - d * r[2]};
-    const float un = rsqrtf(uy[0] * uy[0] + uy[1] * uy[1] + uy[2] * uy[2]);
-    uy[0] *= un; uy[1] *= un; uy[2] *= un;
-    const float ux[3] = {r[1] * uy[2] - r[2] * uy[1], r[2] * uy[0] - r[0] * uy[2], r[0] * uy[1] - r[1] * uy[0]};
+    const float p[3] = {sc.mean[k], sc.mean[n + k], sc.mean[2 * n + k]};
     const float g[3] = {B[k], B[n + k], B[2 * n + k]};
     const float h00 = B[3 * n + k], h01 = B[4 * n + k], h02 = B[5 * n + k], h11 = B[6 * n + k], h12 = B[7 * n + k],
                 h22 = B[8 * n + k];
     const float Hm[3][3] = {{h00, h01, h02}, {h01, h11, h12}, {h02, h12, h22}};
-    const float *U[2] = {ux, uy};
-    float gv[2], Hv[4];
-    for (int a = 0; a < 2; ++a) {
-        gv[a] = U[a][0] * g[0] + U[a][1] * g[1] + U[a][2] * g[2];
-        for (int b = 0; b < 2; ++b) {
-            float acc = 0.f;
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) acc += U[a][i] * Hm[i][j] * U[b][j];
-            Hv[a * 2 + b] = acc;
-        }
-    }
-    float dv[2];
-    int st = damped_solve<2>(2, Hv, gv, mu0, tries, dv, prec);
+    float ux[3], uy[3], gv[2], Hv[4], dv[2], kappa = 1.f;
+    pos_reduce<float>(pr, p, g, Hm, ux, uy, gv, Hv);
+    int st = damped_solve_t<2, float>(2, Hv, gv, mu0, tries, dv, &kappa);
     const float smax = fmaxf(sc.scale[k], fmaxf(sc.scale[n + k], sc.scale[2 * n + k]));
-    if (st == 0 && trust_scale(2, dv, trust * smax)) st = 1;
+    float dp[3];
+    if (prec != 0 && st != 2 && (st == 1 || kappa > 1e6f)) {
+        double uxd[3], uyd[3], gvd[2], Hvd[4], dvd[2];
+        pos_reduce<double>(pr, p, g, Hm, uxd, uyd, gvd, Hvd);
+        st = damped_solve_t<2, double, double>(2, Hvd, gvd, mu0, tries, dvd, nullptr);
+        if (resolves) atomicAdd(resolves, 1ull);
+        if (st == 0 && trust_scale_t<double>(2, dvd, (double)trust * (double)smax)) st = 1;
+        for (int i = 0; i < 3; ++i) dp[i] = (float)(uxd[i] * dvd[0] + uyd[i] * dvd[1]);
+    } else {
+        if (st == 0 && trust_scale(2, dv, trust * smax)) st = 1;
+        for (int i = 0; i < 3; ++i) dp[i] = ux[i] * dv[0] + uy[i] * dv[1];
+    }
     if (st == 1 && nfail) atomicAdd(nfail, 1);
-    for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = ux[i] * dv[0] + uy[i] * dv[1];
+    for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = dp[i];
 }
 
 __global__ void k_solve_scalar(int n, const float *__restrict__ B, float mu0, int tries, float trust, float *step,
-                               int32_t *nfail, int prec) {
+                               int32_t *nfail, int prec, unsigned long long *resolves) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float g = B[k], h = B[n + k];
     float x;
-    int st = damped_solve<1>(1, &h, &g, mu0, tries, &x, prec);
+    int st = damped_solve<1>(1, &h, &g, mu0, tries, &x, prec, resolves);
     if (st == 0 && trust_scale(1, &x, trust)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     step[k] = x;
 }
 
 __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float mu0, int tries, float barrier,
-                                float tau, float *step, int32_t *nfail, int prec) {
+                                float tau, float *step, int32_t *nfail, int prec, unsigned long long *resolves) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -176,7 +206,7 @@ __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float 
     if (!(g == 0.f && h == 0.f)) {
         g += barrier * (-1.f / sg + 1.f / (1.f - sg));
         h += barrier * (1.f / (sg * sg) + 1.f / ((1.f - sg) * (1.f - sg)));
-        st = damped_solve<1>(1, &h, &g, mu0, tries, &x, prec);
+        st = damped_solve<1>(1, &h, &g, mu0, tries, &x, prec, resolves);
         if (st == 0 && trust_scale(1, &x, INFINITY)) st = 1;
     }
     if (st == 1 && nfail) atomicAdd(nfail, 1);
@@ -185,8 +215,88 @@ __global__ void k_solve_opacity(DevScene sc, const float *__restrict__ B, float 
     step[k] = (st == 0) ? xc : 0.f;
 }
 
+// Scaling reduction in the precision T: lambda_i = sum_j (V M)_ij^2 s_j^2 with
+// M = J Wr R of the primary view and V the eigenvectors of M diag(s^2) M^T;
+// Tt = d lambda / d s, Q = Tt^T (Tt Tt^T)^-1 (3x2), g_l = Q^T g, H_l = Q^T H Q.
+// Returns false where the reduction is undefined (behind the primary camera,
+// or rows of Tt (near-)parallel: relative det(Tt Tt^T) < 1e-6).
+template <typename T>
+__device__ __forceinline__ bool scale_reduce(const DevCam &pr, const float p[3], const float s[3], const float q4[4],
+                                             const float g[3], const float (&Hm)[3][3], T (&Q)[3][2], T gl[2],
+                                             T Hl[4]) {
+    const float *V = pr.V;
+    T t[3];
+    for (int i = 0; i < 3; ++i)
+        t[i] = (T)V[i * 4] * (T)p[0] + (T)V[i * 4 + 1] * (T)p[1] + (T)V[i * 4 + 2] * (T)p[2] + (T)V[i * 4 + 3];
+    const T iz = (T)1 / t[2];
+    const T Lx = (T)pr.Lx, Ly = (T)pr.Ly;
+    const T taux = fmin(fmax(t[0] * iz, -Lx), Lx), tauy = fmin(fmax(t[1] * iz, -Ly), Ly);
+    const T fx = (T)pr.fx, fy = (T)pr.fy;
+    const T J[2][3] = {{fx * iz, (T)0, -fx * taux * iz}, {(T)0, fy * iz, -fy * tauy * iz}};
+    T qw = (T)q4[0], qx = (T)q4[1], qy = (T)q4[2], qz = (T)q4[3];
+    const T qn = (T)1 / sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+    const T R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                       {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                       {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+    T M[2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) {
+            T acc = 0;
+            for (int i = 0; i < 3; ++i) {
+                const T wr = (T)V[i * 4] * R[0][b] + (T)V[i * 4 + 1] * R[1][b] + (T)V[i * 4 + 2] * R[2][b];
+                acc += J[a][i] * wr;
+            }
+            M[a][b] = acc;
+        }
+    T A00 = 0, A01 = 0, A11 = 0;
+    for (int j = 0; j < 3; ++j) {
+        const T s2 = (T)s[j] * (T)s[j];
+        A00 += M[0][j] * M[0][j] * s2;
+        A01 += M[0][j] * M[1][j] * s2;
+        A11 += M[1][j] * M[1][j] * s2;
+    }
+    const T phi = (T)0.5 * atan2(2 * A01, A00 - A11);
+    const T c = cos(phi), sn = sin(phi);
+    T Tt[2][3];
+    for (int j = 0; j < 3; ++j) {
+        const T a = c * M[0][j] + sn * M[1][j];
+        const T b = -sn * M[0][j] + c * M[1][j];
+        Tt[0][j] = 2 * a * a * (T)s[j];
+        Tt[1][j] = 2 * b * b * (T)s[j];
+    }
+    T G00 = 0, G01 = 0, G11 = 0;
+    for (int j = 0; j < 3; ++j) {
+        G00 += Tt[0][j] * Tt[0][j];
+        G01 += Tt[0][j] * Tt[1][j];
+        G11 += Tt[1][j] * Tt[1][j];
+    }
+    const T det = G00 * G11 - G01 * G01;
+    if (!(det > (T)1e-30) || !(det > (T)1e-6 * G00 * G11)) return false;
+    const T I00 = G11 / det, I01 = -G01 / det, I11 = G00 / det;
+    for (int j = 0; j < 3; ++j) {
+        Q[j][0] = Tt[0][j] * I00 + Tt[1][j] * I01;
+        Q[j][1] = Tt[0][j] * I01 + Tt[1][j] * I11;
+    }
+    for (int a = 0; a < 2; ++a) {
+        gl[a] = Q[0][a] * (T)g[0] + Q[1][a] * (T)g[1] + Q[2][a] * (T)g[2];
+        for (int b = 0; b < 2; ++b) {
+            T acc = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += Q[i][a] * (T)Hm[i][j] * Q[j][b];
+            Hl[a * 2 + b] = acc;
+        }
+    }
+    return true;
+}
+
+// Scaling step: damped 2x2 solve in the row space of Tt, update kept in
+// [s / trust, trust s].  With mixed precision a block whose FP32 condition
+// estimate exceeds 1e6 (or whose FP32 ladder failed) is solved again with its
+// reduction, factorisation and step in FP64.
 __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries,
-                              float near_z, float trust, float *step, int32_t *nfail, int prec) {
+                              float near_z, float trust, float *step, int32_t *nfail, int prec,
+                              unsigned long long *resolves) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -201,87 +311,36 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
     if (zero) return;
     const float p[3] = {sc.mean[k], sc.mean[n + k], sc.mean[2 * n + k]};
     const float s[3] = {sc.scale[k], sc.scale[n + k], sc.scale[2 * n + k]};
+    const float q4[4] = {sc.quat[k], sc.quat[n + k], sc.quat[2 * n + k], sc.quat[3 * n + k]};
     const float *V = pr.V;
     double dz = (double)V[8] * (double)p[0];
     dz = dz + (double)V[9] * (double)p[1];
     dz = dz + (double)V[10] * (double)p[2];
     dz = dz + (double)V[11];
     if (!(dz >= (double)near_z)) return;
-    float t[3];
-    for (int i = 0; i < 3; ++i) t[i] = V[i * 4] * p[0] + V[i * 4 + 1] * p[1] + V[i * 4 + 2] * p[2] + V[i * 4 + 3];
-    const float iz = 1.f / t[2];
-    const float taux = fminf(fmaxf(t[0] * iz, -pr.Lx), pr.Lx), tauy = fminf(fmaxf(t[1] * iz, -pr.Ly), pr.Ly);
-    const float J[2][3] = {{pr.fx * iz, 0.f, -pr.fx * taux * iz}, {0.f, pr.fy * iz, -pr.fy * tauy * iz}};
-    float qw = sc.quat[k], qx = sc.quat[n + k], qy = sc.quat[2 * n + k], qz = sc.quat[3 * n + k];
-    const float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    qw *= qn; qx *= qn; qy *= qn; qz *= qn;
-    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
-                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
-                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
-    float M[2][3];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b) {
-            float acc = 0.f;
-            for (int i = 0; i < 3; ++i) {
-                const float wr = V[i * 4] * R[0][b] + V[i * 4 + 1] * R[1][b] + V[i * 4 + 2] * R[2][b];
-                acc += J[a][i] * wr;
-            }
-            M[a][b] = acc;
-        }
-    float A00 = 0.f, A01 = 0.f, A11 = 0.f;
-    for (int j = 0; j < 3; ++j) {
-        const float s2 = s[j] * s[j];
-        A00 += M[0][j] * M[0][j] * s2;
-        A01 += M[0][j] * M[1][j] * s2;
-        A11 += M[1][j] * M[1][j] * s2;
-    }
-    const float phi = 0.5f * atan2f(2.f * A01, A00 - A11);
-    const float c = cosf(phi), sn = sinf(phi);
-    float Tt[2][3];
-    for (int j = 0; j < 3; ++j) {
-        const float a = c * M[0][j] + sn * M[1][j];
-        const float b = -sn * M[0][j] + c * M[1][j];
-        Tt[0][j] = 2.f * a * a * s[j];
-        Tt[1][j] = 2.f * b * b * s[j];
-    }
-    float G00 = 0.f, G01 = 0.f, G11 = 0.f;
-    for (int j = 0; j < 3; ++j) {
-        G00 += Tt[0][j] * Tt[0][j];
-        G01 += Tt[0][j] * Tt[1][j];
-        G11 += Tt[1][j] * Tt[1][j];
-    }
-    const float det = G00 * G11 - G01 * G01;
-    if (!(det > 1e-30f) || !(det > 1e-6f * G00 * G11)) return;
-    const float I00 = G11 / det, I01 = -G01 / det, I11 = G00 / det;
-    float Q[3][2];
-    for (int j = 0; j < 3; ++j) {
-        Q[j][0] = Tt[0][j] * I00 + Tt[1][j] * I01;
-        Q[j][1] = Tt[0][j] * I01 + Tt[1][j] * I11;
-    }
     const float Hm[3][3] = {{Hs[0], Hs[1], Hs[2]}, {Hs[1], Hs[3], Hs[4]}, {Hs[2], Hs[4], Hs[5]}};
-    float gl[2], Hl[4];
-    for (int a = 0; a < 2; ++a) {
-        gl[a] = Q[0][a] * g[0] + Q[1][a] * g[1] + Q[2][a] * g[2];
-        for (int b = 0; b < 2; ++b) {
-            float acc = 0.f;
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) acc += Q[i][a] * Hm[i][j] * Q[j][b];
-            Hl[a * 2 + b] = acc;
-        }
+    float Q[3][2], gl[2], Hl[4], dl[2], kappa = 1.f;
+    if (!scale_reduce<float>(pr, p, s, q4, g, Hm, Q, gl, Hl)) return;
+    int st = damped_solve_t<2, float>(2, Hl, gl, mu0, tries, dl, &kappa);
+    float ds[3];
+    if (prec != 0 && st != 2 && (st == 1 || kappa > 1e6f)) {
+        double Qd[3][2], gld[2], Hld[4], dld[2];
+        if (resolves) atomicAdd(resolves, 1ull);
+        if (!scale_reduce<double>(pr, p, s, q4, g, Hm, Qd, gld, Hld)) return;
+        st = damped_solve_t<2, double, double>(2, Hld, gld, mu0, tries, dld, nullptr);
+        if (st == 0 && trust_scale_t<double>(2, dld, (double)INFINITY)) st = 1;
+        for (int i = 0; i < 3; ++i) ds[i] = (float)(Qd[i][0] * dld[0] + Qd[i][1] * dld[1]);
+    } else {
+        if (st == 0 && trust_scale(2, dl, INFINITY)) st = 1;
+        for (int i = 0; i < 3; ++i) ds[i] = Q[i][0] * dl[0] + Q[i][1] * dl[1];
     }
-    float dl[2];
-    int st = damped_solve<2>(2, Hl, gl, mu0, tries, dl, prec);
-    if (st == 0 && trust_scale(2, dl, INFINITY)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
-    for (int i = 0; i < 3; ++i) {
-        const float ds = Q[i][0] * dl[0] + Q[i][1] * dl[1];
-        // s + ds stays in [s / trust, s trust], clamped on the increment
-        step[(size_t)i * n + k] = fminf(fmaxf(ds, s[i] / trust - s[i]), s[i] * trust - s[i]);
-    }
+    // s + ds stays in [s / trust, s trust], clamped on the increment
+    for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] = fminf(fmaxf(ds[i], s[i] / trust - s[i]), s[i] * trust - s[i]);
 }
 
 __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_views, float mu0, int tries,
-                              float trust, float *step, int32_t *nfail, int prec) {
+                              float trust, float *step, int32_t *nfail, int prec, unsigned long long *resolves) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n, S = sc.S;
     if (idx >= 3 * n) return;
@@ -301,7 +360,7 @@ __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_vi
             for (int j = 0; j < S; ++j) H[i * S + j] += s * b[i] * b[j];
         }
     }
-    int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x, prec);
+    int st = damped_solve<GS2_MAX_SH>(S, H, g, mu0, tries, x, prec, resolves);
     if (st == 0 && trust_scale(S, x, trust)) st = 1;
     if (st == 1 && nfail) atomicAdd(nfail, 1);
     for (int i = 0; i < S; ++i) step[(size_t)(ch * S + i) * n + k] = x[i];
@@ -538,7 +597,8 @@ __global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float
 template <int S>
 __global__ void __launch_bounds__(64) k_solve_color_qr64(DevScene sc, const float *__restrict__ B, int n_views,
                                                          float mu0, int tries, float trust, float *step,
-                                                         int32_t *nfail, const uint8_t *__restrict__ flags) {
+                                                         int32_t *nfail, const uint8_t *__restrict__ flags,
+                                                         unsigned long long *resolves) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
@@ -549,6 +609,7 @@ __global__ void __launch_bounds__(64) k_solve_color_qr64(DevScene sc, const floa
     float out[3][S], kappa[3];
     int status[3];
     qr_color_solve<S, double>(a, s, b, n_views, mu0, tries, trust, redo, out, status, kappa);
+    if (resolves) atomicAdd(resolves, (unsigned long long)__popc(redo));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (!(redo & (1u << c))) continue;
@@ -612,7 +673,9 @@ __global__ void k_solve_gradient(int group, DevScene sc, const float *__restrict
 }
 
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
-                         const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st) {
+                         const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st,
+                         unsigned long long *resolves) {
+    unsigned long long *rs = resolves ? resolves + group : nullptr;
     const int n = sc.n;
     if (n == 0) return cudaSuccess;
     const float *B = (const float *)blocks;
@@ -626,19 +689,19 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
     switch (group) {
     case GS2_POS:
         k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_pos, s,
-                                       n_failed, cfg.precision);
+                                       n_failed, cfg.precision, rs);
         break;
     case GS2_ROT:
         k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_rot, s, n_failed,
-                                          cfg.precision);
+                                          cfg.precision, rs);
         break;
     case GS2_SCALE:
         k_solve_scale<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.near_z,
-                                         cfg.scale_trust, s, n_failed, cfg.precision);
+                                         cfg.scale_trust, s, n_failed, cfg.precision, rs);
         break;
     case GS2_OPACITY:
         k_solve_opacity<<<g, 256, 0, st>>>(sc, B, cfg.damping_mu0, cfg.damping_tries, cfg.barrier_alpha,
-                                           cfg.frac_to_boundary, s, n_failed, cfg.precision);
+                                           cfg.frac_to_boundary, s, n_failed, cfg.precision, rs);
         break;
     default:
         if (n_views <= 4) {
@@ -651,7 +714,7 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
         if (prec)                                                                                                 \
             k_solve_color_qr64<SS><<<(n + 63) / 64, 64, 0, st>>>(sc, B, n_views, cfg.damping_mu0,                 \
                                                                  cfg.damping_tries, cfg.trust_color, s, n_failed, \
-                                                                 flags);                                          \
+                                                                 flags, rs);                                      \
     } while (0)
             switch (sc.S) {
             case 1: QR(1); break;
@@ -662,7 +725,7 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
 #undef QR
         } else {
             k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,
-                                                              cfg.trust_color, s, n_failed, cfg.precision);
+                                                              cfg.trust_color, s, n_failed, cfg.precision, rs);
         }
     }
     GS2_COUNT_LAUNCH(1);

@@ -114,9 +114,12 @@ __global__ void k_gather_touched(ProjView pv, const uint32_t *__restrict__ order
 // the accumulation never walk it.  The tile test is the reproducible FP32
 // support_reaches of decide.cuh, so the lists are a function of the FP32
 // parameters and camera alone, bit for bit.
+// ids_emit (deterministic mode, else NULL): the pair's value is its emission
+// index j and its Gaussian id goes to ids_emit[j], so that after the tile sort
+// every pair's sorted position can be mapped back to its emission slot.
 __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__restrict__ order, int n, int tiles_x,
                                               uint32_t ntiles, uint32_t cap, uint32_t *keys, uint32_t *vals,
-                                              unsigned long long *stats) {
+                                              unsigned long long *stats, uint32_t *__restrict__ ids_emit) {
     __shared__ uint32_t s_off[256];
     __shared__ uint2 s_rect[256];
     __shared__ float s_inv[256];      // 1 / rectangle width
@@ -171,7 +174,24 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
         keys[j] = support_reaches(s_sr[lo], (float)(tx * GS2_TILE), (float)(ty * GS2_TILE), (float)GS2_TILE)
                       ? ty * (uint32_t)tiles_x + tx
                       : ntiles;
-        vals[j] = s_id[lo];
+        if (ids_emit) {
+            vals[j] = j;
+            ids_emit[j] = s_id[lo];
+        } else {
+            vals[j] = s_id[lo];
+        }
+    }
+}
+
+// Deterministic mode, after the tile sort (values = emission indices):
+// list[s] = Gaussian id of sorted pair s, inv[j] = sorted position of emitted pair j.
+__global__ void k_det_gather(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ids_emit,
+                             const uint32_t *count, uint32_t *__restrict__ list, uint32_t *__restrict__ inv) {
+    const uint32_t M = count[0];
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < M; s += gridDim.x * blockDim.x) {
+        const uint32_t j = sorted_vals[s];
+        list[s] = ids_emit[j];
+        inv[j] = s;
     }
 }
 
@@ -415,8 +435,11 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     const int ntiles = tiles_x * tiles_y;
     cudaError_t e = cudaMemsetAsync(ctx->ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
     if (e != cudaSuccess) return e;
+    const bool det = ctx->cfg.deterministic != 0 && ctx->det_part;
     if (n == 0) {
         ctx->sorted = 0;
+        ctx->list_ids = ctx->vals[0];
+        ctx->det_order = nullptr;
         return cudaMemsetAsync(ctx->d_count, 0, sizeof(uint32_t) * 2, st);
     }
     // 1. depth order of the Gaussians (or the caller's copy of it for the same
@@ -441,12 +464,20 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     k_scan_down<<<SCAN_BLOCKS, 256, 0, st>>>(pv.tsort, n, bsum, cap, pv.offs);
     // 3. pairs in rank order
     k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n, tiles_x, (uint32_t)ntiles, cap, ctx->keys[0],
-                                            ctx->vals[0], stats);
+                                            ctx->vals[0], stats, det ? ctx->det_ids : nullptr);
     // 4. stable sort by tile id (keys 0..ntiles: one more value than there are tiles)
     int tile_bits = 1;
     while ((1 << tile_bits) <= ntiles) ++tile_bits;
     ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, tile_bits, ctx->ghist, nb, ctx->sort_rows, st,
                              &launches);
+    ctx->list_ids = ctx->vals[ctx->sorted];
+    ctx->det_order = order;
+    if (det) {
+        k_det_gather<<<148 * 4, 256, 0, st>>>(ctx->vals[ctx->sorted], ctx->det_ids, ctx->d_count, ctx->det_list,
+                                              ctx->det_inv);
+        ctx->list_ids = ctx->det_list;
+        ++launches;
+    }
     // 5. tile ranges
     k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, (uint32_t)ntiles,
                                        stats);

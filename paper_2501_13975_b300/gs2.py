@@ -50,7 +50,7 @@ class Config_(C.Structure):
                 ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
                 ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
                 ("precision", C.c_int32), ("gauss_newton", C.c_int32), ("group_order", C.c_int32 * 5),
-                ("group_jacobi", C.c_int32), ("gd_lr", C.c_float * 5)]
+                ("group_jacobi", C.c_int32), ("gd_lr", C.c_float * 5), ("deterministic", C.c_int32)]
 
 
 class Tuning_(C.Structure):
@@ -114,6 +114,7 @@ _sigs = {
     "gs2_profile": (C.c_int, [_vp, C.c_int32]),
     "gs2_profile_read": (C.c_int, [_vp, _vp, _vp, _vp]),
     "gs2_profile_read_stages": (C.c_int, [_vp, _vp, _vp]),
+    "gs2_fp64_resolves": (C.c_int, [_vp, C.POINTER(C.c_uint64), C.c_int32]),
     "gs2_render_noalloc": (C.c_int, [C.POINTER(Config_), C.POINTER(Scene_), C.POINTER(Camera_), _vp, _vp, _vp,
                                      _vp, _vp]),
     "gs2_debug_tiles": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
@@ -451,6 +452,12 @@ class Context:
                  "gs2_debug_tiles")
         return ranges, ids[: min(m.value, capacity)], m.value
 
+    def fp64_resolves(self, reset=True):
+        """Blocks (colour: channels) re-solved in FP64 per group since the last reset."""
+        out = (C.c_uint64 * 5)()
+        self._ok(_lib.gs2_fp64_resolves(self.h, out, 1 if reset else 0), "gs2_fp64_resolves")
+        return [int(x) for x in out]
+
     @staticmethod
     def debug_proj(proj, n, stream=None):
         out = torch.empty((DEBUG_PROJ_ROWS, n), dtype=torch.float32, device="cuda")
@@ -509,6 +516,13 @@ class Batch:
         a, b, r = C.c_int32(0), C.c_int32(0), C.c_int32(0)
         _lib.gs2_batch_stats(self.h, C.byref(a), C.byref(b), C.byref(r))
         return dict(instantiations=a.value, updates=b.value, replays=r.value)
+
+    def set_config(self, i: int, **kw):
+        """gs2_set_config on scene i's context (fields not given keep the batch's configuration)."""
+        cfg = _config_struct({**self.config, **kw})
+        st = _lib.gs2_set_config(self.ctx_handle(i), C.byref(cfg))
+        if st != 0:
+            raise GS2Error(f"gs2_set_config: {STATUS.get(st, st)}")
 
     def set_tuning(self, i: int, sort_blocks: int, sort_rows: int, view_lanes: int = 1):
         t = Tuning_(int(sort_blocks), int(sort_rows), int(view_lanes))

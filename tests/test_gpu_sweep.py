@@ -135,10 +135,14 @@ def test_profile_counts_every_stage(lanes):
                                      {"group_jacobi": 1}, {"gd_lr": (2.0, 20.0, 0.5, 2.0, 20.0)}],
                          ids=["paper", "order-42031", "gauss-newton", "jacobi-groups", "gradient-steps"])
 def test_sweep_parity_with_oracle(variant):
-    """One full sweep on the GPU vs the oracle's sweep (FP64 state throughout):
-    the primary loss seen by each group agrees to 1e-3 and the parameters move
-    by the same update (99% of Gaussians within 2e-3 of their update).  Also
-    for a permuted group order and for Gauss-Newton blocks."""
+    """One full native sweep on the GPU vs the oracle's sweep (FP64 state
+    throughout, so the two drift apart by FP32 rounding from group to group):
+    the primary loss seen by each group agrees to 1e-3 and every parameter row,
+    the quaternions included, moves by the same update: every Gaussian within
+    2e-3 of its update (the lockstep test of test_gpu_steps checks each
+    group's step against its propagated bound).  Also for a
+    permuted group order, Gauss-Newton blocks, Jacobi over groups and
+    gradient steps."""
     from paper_2501_13975_b300 import gs2
     sc, gt, cams = _scene_setup(n=300, size=64)
     ctx = gs2.Context(sc.n, 64, 64, 0, config=variant)
@@ -160,14 +164,21 @@ def test_sweep_parity_with_oracle(variant):
     gl = gl[:, 0] + ocfg["lambda_ssim"] * gl[:, 1]
     assert np.allclose(gl, olosses, rtol=1e-3), (gl, olosses)
     got = ds.to_host()
-    for name in ("mean", "scale", "opacity", "sh"):
+    fr = {}
+    for name in ("mean", "quat", "scale", "opacity", "sh"):
         x0 = getattr(sc, name).astype(np.float64).reshape(-1, sc.n)
         xo = getattr(h, name).reshape(-1, sc.n)
         xg = getattr(got, name).astype(np.float64).reshape(-1, sc.n)
+        if name == "quat":   # q and -q are the same rotation; compare unit quaternions
+            xg = xg / np.linalg.norm(xg, axis=0)
+            xo = xo / np.linalg.norm(xo, axis=0)
         upd = np.linalg.norm(xo - x0, axis=0)
         err = np.linalg.norm(xg - xo, axis=0)
         ok = err <= 2e-3 * upd + 1e-6
-        assert ok.mean() >= 0.99, (name, ok.mean())
+        fr[name] = float(ok.mean())
+    print(variant, "fraction of Gaussians within 2e-3 of their update:", fr)
+    for name, f in fr.items():
+        assert f == 1.0, (name, f)
 
 
 def _crop(cam, x0, y0, w, h):
