@@ -136,6 +136,10 @@ typedef struct {
                                views of a sweep run one after another.  Setting it allocates
                                max_pairs x 41 floats of partials and three max_pairs index arrays in
                                gs2_create / gs2_set_config (7.9 GB at 48M pairs). */
+    float learned_trust;    /* with a step-scale network installed: the learned step alpha d may reach
+                               learned_trust times the trust radii (scale bounds [s / k^lt, k^lt s]),
+                               so that it can lengthen a step the plain radius clipped (2; 1 keeps the
+                               plain radii) */
 } gs2_config;
 
 void gs2_config_default(gs2_config *cfg);

@@ -287,8 +287,10 @@ def phi(group, g, d):
 
 
 def learned_step(group, g, H, d, scene, cfg, p, g_primary=None):
-    """alpha d (alpha from the network on the step's record) inside the plain
-    step's trust radii and bounds; d where the record is unusable."""
+    """alpha d (alpha from the network on the step's record) inside
+    learned_trust times the plain step's trust radii (scale bounds with
+    k^learned_trust) and the opacity fraction-to-boundary; d where the record
+    is unusable."""
     cfg = O.default_config(**(cfg or {}))
     sc = O.scene_handle(scene)
     n, S = sc.n, O.sh_count(sc.sh_degree)
@@ -300,23 +302,24 @@ def learned_step(group, g, H, d, scene, cfg, p, g_primary=None):
     scale = np.asarray(sc.scale, np.float64).reshape(3, n)
     sigma = np.asarray(sc.opacity, np.float64).reshape(n)
     d = np.asarray(d, np.float64)
+    lt = cfg["learned_trust"]
     if group == O.POS:
-        lim = cfg["trust_pos"] * scale.max(0)
+        lim = lt * cfg["trust_pos"] * scale.max(0)
         dn = a * np.linalg.norm(d, axis=0)
         m = np.where(dn > lim, a * lim / np.where(dn > 0, dn, 1.0), a)
         out = d * m
     elif group == O.SCALE:
-        k = cfg["scale_trust"]
+        k = cfg["scale_trust"] ** lt
         out = np.clip(a * d, scale / k - scale, k * scale - scale)
     elif group == O.ROT:
-        out = np.clip(a * d, -cfg["trust_rot"], cfg["trust_rot"])
+        out = np.clip(a * d, -lt * cfg["trust_rot"], lt * cfg["trust_rot"])
     elif group == O.OPACITY:
         tau = cfg["frac_to_boundary"]
         out = np.clip(a * d.reshape(1, n), -tau * sigma, tau * (1.0 - sigma))
     else:
         dc = d.reshape(3, S, n)
         cn = a * np.linalg.norm(dc, axis=1)                     # (3, n)
-        m = np.where(cn > cfg["trust_color"], a * cfg["trust_color"] / np.where(cn > 0, cn, 1.0), a)
+        m = np.where(cn > lt * cfg["trust_color"], a * lt * cfg["trust_color"] / np.where(cn > 0, cn, 1.0), a)
         out = dc * m[:, None, :]
     return np.where(ok, out.reshape(d.shape), d)
 

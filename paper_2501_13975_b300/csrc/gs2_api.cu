@@ -59,6 +59,7 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->group_jacobi = 0;
     for (int i = 0; i < 5; ++i) c->gd_lr[i] = 0.f;
     c->deterministic = 0;
+    c->learned_trust = 2.f;
 }
 
 bool cfg_ok(const gs2_config *c, std::string &err) {
@@ -84,6 +85,7 @@ bool cfg_ok(const gs2_config *c, std::string &err) {
     for (int i = 0; i < 5; ++i)
         if (!(c->gd_lr[i] >= 0.f) || !isfinite(c->gd_lr[i])) { err = "gd_lr entries must be finite and >= 0"; return false; }
     if (c->deterministic != 0 && c->deterministic != 1) { err = "deterministic must be 0 or 1"; return false; }
+    if (!(c->learned_trust >= 1.f && c->learned_trust <= 16.f)) { err = "learned_trust must be in [1, 16]"; return false; }
     return true;
 }
 

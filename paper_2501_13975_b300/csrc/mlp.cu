@@ -275,8 +275,13 @@ __device__ __forceinline__ void load_weights(float *sw, const __nv_bfloat16 *__r
     for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
 }
 
-// step <- alpha d inside the plain step's trust radii and bounds; the plain
-// step stays where the record is unusable or alpha is not finite
+// step <- alpha d inside learned_trust times the plain step's trust radii
+// (position, rotation, colour; scale bounds [s / k^lt, k^lt s], lt =
+// learned_trust) and the opacity fraction-to-boundary; the plain step stays
+// where the record is unusable or alpha is not finite.  With learned_trust > 1
+// a step the plain radius clipped can be lengthened (alpha > 1) up to the
+// wider radius: where the radii bind, the scale acts as a learned per-Gaussian
+// trust radius.
 __global__ void __launch_bounds__(128) k_learned_scale(int group, const float *__restrict__ B, int n_views,
                                                        DevScene sc, float *__restrict__ step,
                                                        const float *__restrict__ gp, gs2_config cfg,
@@ -293,18 +298,20 @@ __global__ void __launch_bounds__(128) k_learned_scale(int group, const float *_
     if (!step_features(group, st, sc.opacity[k], smax, f)) return;
     const float a = scale_of(mlp_eval(sw, f));
     if (!isfinite(a)) return;
+    const float lt = cfg.learned_trust;
     if (group == GS2_POS) {
-        const float lim = cfg.trust_pos * smax, dn = a * sqrtf(st.dd);
+        const float lim = lt * cfg.trust_pos * smax, dn = a * sqrtf(st.dd);
         const float m = (dn > lim) ? a * lim / dn : a;
         for (int i = 0; i < 3; ++i) step[(size_t)i * n + k] *= m;
     } else if (group == GS2_SCALE) {
+        const float kk = powf(cfg.scale_trust, lt);
         for (int i = 0; i < 3; ++i) {
             const float s = sc.scale[(size_t)i * n + k];
-            const float lo = s / cfg.scale_trust - s, hi = cfg.scale_trust * s - s;
+            const float lo = s / kk - s, hi = kk * s - s;
             step[(size_t)i * n + k] = fminf(fmaxf(a * step[(size_t)i * n + k], lo), hi);
         }
     } else if (group == GS2_ROT) {
-        step[k] = fminf(fmaxf(a * step[k], -cfg.trust_rot), cfg.trust_rot);
+        step[k] = fminf(fmaxf(a * step[k], -lt * cfg.trust_rot), lt * cfg.trust_rot);
     } else if (group == GS2_OPACITY) {
         const float sg = sc.opacity[k], tau = cfg.frac_to_boundary;
         step[k] = fminf(fmaxf(a * step[k], -tau * sg), tau * (1.f - sg));
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(128) k_learned_scale(int group, const float *_
                 dn += x * x;
             }
             dn = a * sqrtf(dn);
-            const float m = (dn > cfg.trust_color) ? a * cfg.trust_color / dn : a;
+            const float m = (dn > lt * cfg.trust_color) ? a * lt * cfg.trust_color / dn : a;
             for (int i = 0; i < S; ++i) step[(size_t)(c * S + i) * n + k] *= m;
         }
     }

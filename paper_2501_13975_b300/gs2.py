@@ -50,7 +50,8 @@ class Config_(C.Structure):
                 ("ssim_c1", C.c_float), ("ssim_c2", C.c_float), ("ssim_sigma", C.c_float),
                 ("ssim_radius", C.c_int32), ("knn_k", C.c_int32), ("downsample", C.c_int32),
                 ("precision", C.c_int32), ("gauss_newton", C.c_int32), ("group_order", C.c_int32 * 5),
-                ("group_jacobi", C.c_int32), ("gd_lr", C.c_float * 5), ("deterministic", C.c_int32)]
+                ("group_jacobi", C.c_int32), ("gd_lr", C.c_float * 5), ("deterministic", C.c_int32),
+                ("learned_trust", C.c_float)]
 
 
 class Tuning_(C.Structure):

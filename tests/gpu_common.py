@@ -7,7 +7,7 @@ GPU_CFG_KEYS = ("lambda_ssim", "alpha_min", "alpha_max", "t_min", "lowpass", "ne
                 "frac_to_boundary", "damping_mu0", "damping_tries", "scale_min", "scale_trust", "trust_pos",
                 "trust_rot", "trust_color", "ssim_c1",
                 "ssim_c2", "ssim_sigma", "ssim_radius", "knn_k", "downsample", "gauss_newton", "group_order",
-                "group_jacobi", "gd_lr")
+                "group_jacobi", "gd_lr", "learned_trust")
 
 
 def oracle_cfg(gpu_cfg: dict) -> dict:

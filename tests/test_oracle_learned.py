@@ -304,9 +304,9 @@ def test_rejected_step_has_label_zero():
 
 
 def test_learned_step_bounds_and_fallback():
-    """alpha -> 2 (large output bias): the step doubles inside the trust
-    radius and is cut back to it outside; a non-finite network leaves the
-    plain step."""
+    """alpha -> 2 (large output bias): the step doubles inside learned_trust
+    times the trust radius and is cut back to it outside (learned_trust 2 and
+    1); a non-finite network leaves the plain step."""
     rng = np.random.default_rng(15)
     sc = _scene_for(10)
     g, Hu, d, _ = _pos_blocks(rng, 10, mu=1.0)
@@ -316,12 +316,15 @@ def test_learned_step_bounds_and_fallback():
     d[:, :5] *= 0.5                                            # |d| = max(s) for half
     p = np.zeros(Lr.NPARAM)
     p[Lr.OFF_B3] = 40.0                                        # alpha = 2 to double precision
-    cfg = O.default_config(trust_pos=3.0)                      # |d| and 2|d| on either side of it
-    out = Lr.learned_step(O.POS, g, Hu, d, sc, cfg, p)
-    n_out = np.linalg.norm(out, axis=0)
-    assert np.allclose(n_out[:5], 2.0 * smax[:5], rtol=1e-12)
-    assert np.allclose(n_out[5:], cfg["trust_pos"] * smax[5:], rtol=1e-12)
-    assert np.allclose(out / n_out, d / np.linalg.norm(d, axis=0), rtol=1e-12)
+    for cfg in (O.default_config(trust_pos=1.5),                        # learned_trust 2: 3 max(s)
+                O.default_config(trust_pos=3.0, learned_trust=1.0)):       # the plain radius, 3 max(s)
+        # the cap, 3 max(s), lies between 2|d| of the two halves
+        assert cfg["learned_trust"] * cfg["trust_pos"] == 3.0
+        out = Lr.learned_step(O.POS, g, Hu, d, sc, cfg, p)
+        n_out = np.linalg.norm(out, axis=0)
+        assert np.allclose(n_out[:5], 2.0 * smax[:5], rtol=1e-12)
+        assert np.allclose(n_out[5:], 3.0 * smax[5:], rtol=1e-12)
+        assert np.allclose(out / n_out, d / np.linalg.norm(d, axis=0), rtol=1e-12)
     p_nan = p.copy()
     p_nan[Lr.OFF_B3] = np.nan
     assert np.array_equal(Lr.learned_step(O.POS, g, Hu, d, sc, cfg, p_nan), d)
