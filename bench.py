@@ -822,8 +822,9 @@ def time_to_psnr(args):
         held_stats[name] = {"records": cnt, "label_loss_plain": round(pl, 5), "label_loss_network": round(nl, 5),
                             "line_loss_plain": float(f"{pll:.5g}"), "line_loss_network": float(f"{nll:.5g}")}
 
-    def run(start_host, precision, use_model, max_sweeps, target_psnr=None):
-        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision))
+    def run(start_host, precision, use_model, max_sweeps, target_psnr=None, learned_trust=None):
+        lt = args.ttp_learned_trust if learned_trust is None else learned_trust
+        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision, learned_trust=lt))
         gt = gs2.DeviceScene.from_host(gt_host)
         proj = ctx.proj_buffer(w["n"])
         targets = []
@@ -876,7 +877,8 @@ def time_to_psnr(args):
         inference and of the precision policy on one scene state (the runs
         above move through different states, so their per-sweep times also
         reflect how far each has diverged)."""
-        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision))
+        ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"],
+                          dict(precision=precision, learned_trust=args.ttp_learned_trust))
         gt = gs2.DeviceScene.from_host(gt_host)
         proj = ctx.proj_buffer(w["n"])
         targets = []
@@ -916,8 +918,9 @@ def time_to_psnr(args):
         plain = run(host, 0, False, 30)
         target = plain["psnr"][30]
         runs = {"plain_fp32": plain}
-        for name, prec, use in (("learned_mixed", 1, True), ("learned_fp32", 0, True), ("plain_mixed", 1, False)):
-            runs[name] = run(host, prec, use, max(args.ttp_max, 30), target)
+        for name, prec, use, lt in (("learned_mixed", 1, True, None), ("learned_fp32", 0, True, None),
+                                    ("learned_mixed_radii_x2", 1, True, 2.0), ("plain_mixed", 1, False, None)):
+            runs[name] = run(host, prec, use, max(args.ttp_max, 30), target, lt)
         lm = runs["learned_mixed"]
         t_plain = plain["ms"][30] * 1e-3
         t_lm = lm["ms"][lm["reached"]] * 1e-3 if lm["reached"] is not None else None
@@ -939,7 +942,8 @@ def time_to_psnr(args):
         "value": head["learned_mixed_seconds"], "unit": "s", "higher_is_better": False,
         "starts": starts,
         "first_sweep_ms": first,
-        "network": {"objective": args.ttp_objective, "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell,
+        "network": {"objective": args.ttp_objective, "learned_trust": args.ttp_learned_trust,
+                    "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell,
                     "records": tiny.n + shell.n,
                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
                     "heldout": held_stats},
@@ -1123,6 +1127,8 @@ def main():
     ap.add_argument("--ttp-shell", type=int, default=24, help="shell-scene record runs (4 sweeps each)")
     ap.add_argument("--ttp-epochs", type=int, default=3)
     ap.add_argument("--ttp-max", type=int, default=60)
+    ap.add_argument("--ttp-learned-trust", type=float, default=1.0,
+                    help="learned_trust of the learned paths (the learned step may reach this many trust radii)")
     ap.add_argument("--ttp-objective", default="line", choices=["line", "labels"],
                     help="training loss of the step-scale network")
     args = ap.parse_args()

@@ -138,8 +138,8 @@ typedef struct {
                                gs2_create / gs2_set_config (7.9 GB at 48M pairs). */
     float learned_trust;    /* with a step-scale network installed: the learned step alpha d may reach
                                learned_trust times the trust radii (scale bounds [s / k^lt, k^lt s]),
-                               so that it can lengthen a step the plain radius clipped (2; 1 keeps the
-                               plain radii) */
+                               so that it can lengthen a step the plain radius clipped (1: the plain
+                               radii; 2 measured worse on the object workload) */
 } gs2_config;
 
 void gs2_config_default(gs2_config *cfg);

@@ -59,7 +59,7 @@ def default_config(**kw) -> dict:
                ssim_radius=5, knn_k=3, downsample=2, scale_trust=1.05,
                trust_pos=0.05, trust_rot=0.05, trust_color=0.05,
                gauss_newton=0, group_order=(0, 1, 2, 3, 4), group_jacobi=0, gd_lr=(0.0, 0.0, 0.0, 0.0, 0.0),
-               learned_trust=2.0)
+               learned_trust=1.0)
     cfg.update(kw)
     return cfg
 

@@ -5,6 +5,9 @@
 Each translation unit is compiled to an object under _build/ (in parallel, one
 nvcc per source), then the objects are linked into the shared library.  An
 object is rebuilt when its source, any csrc header or include/gs2.h is newer.
+
+The environment variable GS2_TILE=8 builds the 8x8-tile variant (for
+measurement; use --force when switching, the default is 16).
 """
 from __future__ import annotations
 
@@ -22,6 +25,8 @@ OBJDIR = os.path.join(os.path.dirname(HERE), "_build", "gs2")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+if os.environ.get("GS2_TILE"):
+    FLAGS.append("-DGS2_TILE=" + str(int(os.environ["GS2_TILE"])))
 
 
 def sources():

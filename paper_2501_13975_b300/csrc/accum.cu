@@ -1,6 +1,6 @@
 // gs2_accum_newton_blocks (Eq. local_hessian_gradient, full Newton).
 //
-// Pass 1 (k_accum, one 16x16 CTA per tile, one thread per two pixels): walk the
+// Pass 1 (k_accum, one CTA per screen tile, one thread per two pixels): walk the
 // tile's depth-sorted list back to front (the order that yields the colour
 // behind each Gaussian, C_back, and its transmittance T_k = T_after/(1-alpha)).
 // For pixel c = C_front + T_k (alpha_k c~_k + (1 - alpha_k) C_back):
@@ -270,10 +270,10 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
-    __shared__ float sDet[DET ? 4 : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
+    __shared__ float sDet[DET ? GS2_PAIR_WARPS : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
     const int t = threadIdx.x, lane = t & 31;
     if constexpr (DET) {
-        for (int q = t; q < 4 * GS2_DET_CHUNK * P; q += GS2_PAIR_THREADS) (&sDet[0][0][0])[q] = 0.f;
+        for (int q = t; q < GS2_PAIR_WARPS * GS2_DET_CHUNK * P; q += GS2_PAIR_THREADS) (&sDet[0][0][0])[q] = 0.f;
     }
     const int tile = blockIdx.y * tiles_x + blockIdx.x;
     const int px = blockIdx.x * GS2_TILE + gs2_pair_px(t), py = blockIdx.y * GS2_TILE + gs2_pair_py(t);
@@ -400,10 +400,12 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                 for (int q = t; q < cnt; q += GS2_PAIR_THREADS) {
                     const int e = q / P, i = q - e * P;
                     float v = sDet[0][e][i];
-                    v = __fadd_rn(v, sDet[1][e][i]);
-                    v = __fadd_rn(v, sDet[2][e][i]);
-                    v = __fadd_rn(v, sDet[3][e][i]);
-                    sDet[0][e][i] = sDet[1][e][i] = sDet[2][e][i] = sDet[3][e][i] = 0.f;
+                    sDet[0][e][i] = 0.f;
+#pragma unroll
+                    for (int ww = 1; ww < GS2_PAIR_WARPS; ++ww) {   // warp order
+                        v = __fadd_rn(v, sDet[ww][e][i]);
+                        sDet[ww][e][i] = 0.f;
+                    }
                     det_part[(size_t)(r.x + (uint32_t)(c0 + e)) * P + i] = v;
                 }
                 __syncthreads();
@@ -852,9 +854,10 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
 // its rectangle row by row), written to zbuf[P][n] for the epilogues.  FP32
 // sums are compensated (Kahan: the rounding error of every addition is carried
 // into the next); with mixed precision (ACC = double) the sum is FP64.  One
-// thread per depth rank r (Gaussian order[r]); emitted pairs past the pair
-// capacity and box tiles the support ellipse misses (sorted key >= ntiles)
-// hold no entry and are skipped.
+// warp per depth rank r (Gaussian order[r]), lane i summing payload entry i
+// (and i + 32), so every partial row is read by one coalesced access; emitted
+// pairs past the pair capacity and box tiles the support ellipse misses
+// (sorted key >= ntiles) hold no entry and are skipped.
 template <int P, typename ACC>
 __global__ void __launch_bounds__(128) k_det_reduce(const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
                                                     const uint32_t *__restrict__ tsort, int n,
@@ -862,37 +865,46 @@ __global__ void __launch_bounds__(128) k_det_reduce(const uint32_t *__restrict__
                                                     const uint32_t *__restrict__ inv,
                                                     const uint32_t *__restrict__ skeys, uint32_t ntiles,
                                                     const float *__restrict__ part, ACC *__restrict__ zbuf) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int NE = (P + 31) / 32;   // entries per lane
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= n) return;
     const uint32_t cnt = tsort[r];
     if (cnt == 0u) return;
     const uint32_t id = order[r], M = count[0];
     const uint32_t j0 = offs[r], j1 = min(j0 + cnt, M);
-    ACC acc[P];
-    float comp[P];
+    ACC acc[NE];
+    float comp[NE];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-        acc[i] = 0;
-        comp[i] = 0.f;
+    for (int e = 0; e < NE; ++e) {
+        acc[e] = 0;
+        comp[e] = 0.f;
     }
     for (uint32_t j = j0; j < j1; ++j) {
         const uint32_t sp = inv[j];
         if (skeys[sp] >= ntiles) continue;
         const float *row = part + (size_t)sp * P;
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            if constexpr (sizeof(ACC) == sizeof(float)) {
-                const float y = __fsub_rn(row[i], comp[i]);
-                const float t = __fadd_rn((float)acc[i], y);
-                comp[i] = __fsub_rn(__fsub_rn(t, (float)acc[i]), y);
-                acc[i] = t;
-            } else {
-                acc[i] += (ACC)row[i];
+        for (int e = 0; e < NE; ++e) {
+            const int i = lane + 32 * e;
+            if (i < P) {
+                const float v = row[i];
+                if constexpr (sizeof(ACC) == sizeof(float)) {
+                    const float y = __fsub_rn(v, comp[e]);
+                    const float t = __fadd_rn((float)acc[e], y);
+                    comp[e] = __fsub_rn(__fsub_rn(t, (float)acc[e]), y);
+                    acc[e] = t;
+                } else {
+                    acc[e] += (ACC)v;
+                }
             }
         }
     }
 #pragma unroll
-    for (int i = 0; i < P; ++i) zbuf[(size_t)i * n + id] = acc[i];
+    for (int e = 0; e < NE; ++e) {
+        const int i = lane + 32 * e;
+        if (i < P) zbuf[(size_t)i * n + id] = acc[e];
+    }
 }
 
 template <typename ACC>
@@ -912,7 +924,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
                 ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,    \
                 cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part);                        \
             if (n > 0)                                                                                            \
-                k_det_reduce<Payload<G>::P, ACC><<<(n + 127) / 128, 128, 0, st>>>(                                \
+                k_det_reduce<Payload<G>::P, ACC><<<(n + 3) / 4, 128, 0, st>>>(                                    \
                     ctx->det_order, pv.offs, pv.tsort, n, ctx->d_count, ctx->det_inv, ctx->keys[ctx->sorted],     \
                     ntiles, ctx->det_part, zb);                                                                   \
         } else {                                                                                                  \

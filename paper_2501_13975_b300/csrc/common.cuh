@@ -12,7 +12,14 @@
 #include "../../include/gs2.h"
 #include "decide.cuh"
 
-#define GS2_TILE 16                  // screen tile edge in pixels
+// screen tile edge in pixels: 16, or 8 in a build with -DGS2_TILE=8 (a
+// measurement variant; the tile size is fixed per build)
+#ifndef GS2_TILE
+#define GS2_TILE 16
+#endif
+#if GS2_TILE != 8 && GS2_TILE != 16
+#error "GS2_TILE must be 8 or 16"
+#endif
 #define GS2_SORT_BLOCKS_MAX 1024     // the per-digit scan runs one 1024-thread CTA per digit
 // profiling pool (event pairs) and the stage tags beside the accumulation groups
 #define GS2_PROF_POOL 2048
@@ -259,23 +266,25 @@ cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t 
 // the same alpha decisions bit for bit, so the Gaussian falloff is evaluated
 // with explicitly rounded operations (no compiler contraction choices).
 #ifdef __CUDACC__
-// Pixel of thread t in its 16x16 tile (compositing, 256 threads): warp w
-// covers the 8x4 block (w % 2, w / 2) of the tile, lane l its pixel
+// Pixel of thread t in its tile (compositing, one thread per pixel): warp w
+// covers the 8x4 block (w % (T/8), w / (T/8)) of the tile, lane l its pixel
 // (l % 8, l / 8) -- compact warp blocks keep more of a warp's lanes inside a
-// small Gaussian footprint than 16x2 rows do.
-__device__ __forceinline__ int gs2_tile_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
-__device__ __forceinline__ int gs2_tile_py(int t) { return (t >> 6) * 4 + ((t >> 3) & 3); }
+// small Gaussian footprint than T x 2 rows do.
+#define GS2_WPR (GS2_TILE / 8)       // 8-pixel-wide warp blocks per tile row
+__device__ __forceinline__ int gs2_tile_px(int t) { return ((t >> 5) % GS2_WPR) * 8 + (t & 7); }
+__device__ __forceinline__ int gs2_tile_py(int t) { return ((t >> 5) / GS2_WPR) * 4 + ((t >> 3) & 3); }
 
-// Two pixels per thread (accumulation, GS2_PAIR_THREADS = 128 per tile):
-// warp w covers the 8x8 block ((w & 1) 8, (w >> 1) 8), lane l the pixels
+// Two pixels per thread (accumulation, GS2_PAIR_THREADS per tile): warp w
+// covers the 8x8 block ((w % (T/8)) 8, (w / (T/8)) 8), lane l the pixels
 // (l % 8, l / 8) and (l % 8, l / 8 + 4) of it.  One warp reduction serves
 // both pixels of a lane (a Gaussian that reaches one 8x4 half of such a
 // block nearly always reaches the other).  The compositing keeps one pixel
 // per thread: there a lane would run on until both of its pixels saturate
 // (measured slower).
-#define GS2_PAIR_THREADS 128
-__device__ __forceinline__ int gs2_pair_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
-__device__ __forceinline__ int gs2_pair_py(int t) { return (t >> 6) * 8 + ((t >> 3) & 3); }
+#define GS2_PAIR_THREADS (GS2_TILE_PIX / 2)
+#define GS2_PAIR_WARPS (GS2_PAIR_THREADS / 32)
+__device__ __forceinline__ int gs2_pair_px(int t) { return ((t >> 5) % GS2_WPR) * 8 + (t & 7); }
+__device__ __forceinline__ int gs2_pair_py(int t) { return ((t >> 5) / GS2_WPR) * 8 + ((t >> 3) & 3); }
 
 // asynchronous 16-byte global -> shared copies (the batch staging pipeline)
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {

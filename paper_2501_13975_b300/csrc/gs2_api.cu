@@ -59,7 +59,7 @@ extern "C" void gs2_config_default(gs2_config *c) {
     c->group_jacobi = 0;
     for (int i = 0; i < 5; ++i) c->gd_lr[i] = 0.f;
     c->deterministic = 0;
-    c->learned_trust = 2.f;
+    c->learned_trust = 1.f;
 }
 
 bool cfg_ok(const gs2_config *c, std::string &err) {

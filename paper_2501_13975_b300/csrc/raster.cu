@@ -1,4 +1,4 @@
-// gs2_raster_fwd compositing (Eq. 3dgs): one 16x16 CTA per screen tile, one
+// gs2_raster_fwd compositing (Eq. 3dgs): one CTA per screen tile (16x16), one
 // thread per pixel, the tile's depth-sorted Gaussian list staged through
 // shared memory in batches of 256 records (one record gather per thread per
 // batch, copied asynchronously into the second buffer while the first is
