@@ -316,7 +316,7 @@ def test_learned_step_bounds_and_fallback():
     d[:, :5] *= 0.5                                            # |d| = max(s) for half
     p = np.zeros(Lr.NPARAM)
     p[Lr.OFF_B3] = 40.0                                        # alpha = 2 to double precision
-    for cfg in (O.default_config(trust_pos=1.5),                        # learned_trust 2: 3 max(s)
+    for cfg in (O.default_config(trust_pos=1.5, learned_trust=2.0),    # 2 x 1.5 max(s)
                 O.default_config(trust_pos=3.0, learned_trust=1.0)):       # the plain radius, 3 max(s)
         # the cap, 3 max(s), lies between 2|d| of the two halves
         assert cfg["learned_trust"] * cfg["trust_pos"] == 3.0
