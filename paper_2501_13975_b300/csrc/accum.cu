@@ -176,7 +176,10 @@ template <int GROUP, int P>
 __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, const float4 &B, const float4 &C,
                                               float G, float alpha, float dx, float dy, bool clamped, bool gn,
                                               float (&pl)[P]) {
-    const float Tk = __fdiv_rn(ps.T, __fsub_rn(1.f, alpha));
+    // T_k = T_after / (1 - alpha) undoes one rounded product of the forward
+    // pass; a 2-ulp division (reciprocal + multiply) is far inside the tolerances
+    const float om = __fsub_rn(1.f, alpha);
+    const float Tk = __fdividef(ps.T, om);
     const float w = alpha * Tk;
     const float a0 = Tk * (C.x - ps.cb0), a1 = Tk * (C.y - ps.cb1), a2 = Tk * (C.z - ps.cb2);
     const float *e = ps.e, *h = ps.h;
@@ -244,9 +247,9 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
             pl[38 + c] += w * w * h[c];
         }
     }
-    ps.cb0 = alpha * C.x + (1.f - alpha) * ps.cb0;
-    ps.cb1 = alpha * C.y + (1.f - alpha) * ps.cb1;
-    ps.cb2 = alpha * C.z + (1.f - alpha) * ps.cb2;
+    ps.cb0 = alpha * C.x + om * ps.cb0;
+    ps.cb1 = alpha * C.y + om * ps.cb1;
+    ps.cb2 = alpha * C.z + om * ps.cb2;
     ps.T = Tk;
 }
 
@@ -370,10 +373,13 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                 if (act[q]) {
                     dy[q] = __fsub_rn(q ? fy1 : fy0, A.y);
                     const float qf = dec_quad(A.z, A.w, B.x, dx, dy[q]);
-                    G[q] = gs2_falloff(qf);
-                    clamped[q] = qf < B.w;
-                    alpha[q] = clamped[q] ? amax : __fmul_rn(B.y, G[q]);
-                    if (!(qf <= B.z)) act[q] = false;   // not composited (the same decision as k_raster)
+                    if (qf <= B.z) {   // composited (the same decision as k_raster)
+                        G[q] = gs2_falloff(qf);
+                        clamped[q] = qf < B.w;
+                        alpha[q] = clamped[q] ? amax : __fmul_rn(B.y, G[q]);
+                    } else {
+                        act[q] = false;
+                    }
                 }
             }
             if (!__any_sync(0xFFFFFFFFu, act[0] || act[1])) return;

@@ -304,14 +304,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
             const uint32_t idx = base + (uint32_t)(w * (32 * ROWS) + r * 32 + lane);
             const bool valid = idx < end;
             dig[r] = valid ? ((key[r] >> shift) & mask) : 256u;
-            // lanes with the same 9-bit digit value, from one ballot per bit
-            uint32_t peers = 0xFFFFFFFFu;
-#pragma unroll
-            for (int b = 0; b < 9; ++b) {
-                const bool bit = (dig[r] >> b) & 1u;
-                const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
-                peers &= bit ? m : ~m;
-            }
+            // lanes with the same digit value (256 marks a slot past the end)
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[r]);
             const uint32_t rank = __popc(peers & lt_mask);
             uint32_t cnt = 0u;
             if (valid) cnt = s_wc[w][dig[r]];
