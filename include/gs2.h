@@ -215,6 +215,10 @@ gs2_status gs2_loss_derivs(gs2_ctx *ctx, const float *image, const float *target
  *   COLOR: slot v (= view_slot) of n_views: [a_ch (3), s_ch (3), b (S)][n] with
  *          a_ch = sum_p w e_ch, s_ch = sum_p w^2 h_ch, b = B Phi(r_v); the
  *          channel block is H_ch = sum_v s_ch b b^T, g_ch = sum_v a_ch b.
+ *          The dense S x S block is never formed: gs2_solve_step solves each
+ *          channel in the range of the (at most 4) view bases b_v, an r x r
+ *          system, so the SH J^T J contraction has no dense product to put on
+ *          the tensor cores (BF16 or otherwise).
  *          The slot is overwritten, other groups accumulate (+=). */
 gs2_status gs2_accum_newton_blocks(gs2_ctx *ctx, gs2_group group, const gs2_scene *scene,
                                    const gs2_camera *view, const gs2_camera *primary, const void *proj,
