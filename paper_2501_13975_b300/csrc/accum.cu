@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                                                            const float *__restrict__ Hh, int W, int H, int tiles_x,
                                                            float amin, float amax, int gn, ACC *__restrict__ zbuf,
                                                            int n, unsigned long long *__restrict__ active_stat,
-                                                           float *__restrict__ det_part) {
+                                                           float *__restrict__ det_part,
+                                                           const uint32_t *__restrict__ tile_order) {
     constexpr int P = Payload<GROUP>::P;
     constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
     constexpr int PER = NB / GS2_PAIR_THREADS;        // entries each thread stages
@@ -278,8 +279,9 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
     if constexpr (DET) {
         for (int q = t; q < GS2_PAIR_WARPS * GS2_DET_CHUNK * P; q += GS2_PAIR_THREADS) (&sDet[0][0][0])[q] = 0.f;
     }
-    const int tile = blockIdx.y * tiles_x + blockIdx.x;
-    const int px = blockIdx.x * GS2_TILE + gs2_pair_px(t), py = blockIdx.y * GS2_TILE + gs2_pair_py(t);
+    const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
+    const int tcol = tile % tiles_x, trow = tile / tiles_x;
+    const int px = tcol * GS2_TILE + gs2_pair_px(t), py = trow * GS2_TILE + gs2_pair_py(t);
     const size_t PI = (size_t)W * H;
     PixState ps[2];
 #pragma unroll
@@ -928,7 +930,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
         if (det) {                                                                                                \
             k_accum<G, float, true><<<grid, GS2_PAIR_THREADS, 0, st>>>(                                           \
                 ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,    \
-                cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part);                        \
+                cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part, ctx->tile_order);       \
             if (n > 0)                                                                                            \
                 k_det_reduce<Payload<G>::P, ACC><<<(n + 3) / 4, 128, 0, st>>>(                                    \
                     ctx->det_order, pv.offs, pv.tsort, n, ctx->d_count, ctx->det_inv, ctx->keys[ctx->sorted],     \
@@ -937,7 +939,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
             k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h,  \
                                                                view.w, view.h, ctx->tiles_x, cfg.alpha_min,       \
                                                                cfg.alpha_max, cfg.gauss_newton, zb, n, act,       \
-                                                               (float *)nullptr);                                 \
+                                                               (float *)nullptr, ctx->tile_order);                \
         }                                                                                                         \
     } while (0)
     switch (group) {
@@ -980,7 +982,7 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
 cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st) {
-    dim3 grid(ctx->tiles_x, ctx->tiles_y);
+    dim3 grid((unsigned)(ctx->tiles_x * ctx->tiles_y));
     const uint32_t *ids = ctx->list_ids;
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool (shared by a sweep's view lanes)
     const bool prof = pc->prof_on && pc->prof_n < GS2_PROF_POOL;

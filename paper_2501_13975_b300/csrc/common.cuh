@@ -154,6 +154,8 @@ struct gs2_ctx {
     uint2 *ranges;               // [max tiles]
     int sorted;                  // which of keys/vals holds the sorted pairs
     const uint32_t *list_ids;    // Gaussian ids of the sorted tile lists (vals[sorted], or det_list)
+    uint32_t *tile_order;        // [max tiles] tiles by descending list length (launch order of the
+                                 // compositing and accumulation grids), or NULL: row-major order
     // deterministic mode (cfg.deterministic): per-list-entry partials instead
     // of float atomics, reduced per Gaussian in a fixed order
     float *det_part;             // [max_pairs][GS2_ZPOS] image-space payload of every (tile, Gaussian) entry

@@ -120,7 +120,7 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 // a view lane's own scratch (the rest is shared with its owner)
 static void free_lane(gs2_ctx *l) {
     void *ptrs[] = {l->keys[0], l->keys[1], l->vals[0], l->vals[1], l->ghist, l->bsum, l->d_count, l->ranges,
-                    l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image};
+                    l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image, l->tile_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -138,7 +138,7 @@ static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->d_resolves, c->flags, c->g_prim, c->lg_phi,
-                    c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list};
+                    c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list, c->tile_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
@@ -245,6 +245,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A((void **)&c->bsum, sizeof(unsigned long long) * 1024);
     A((void **)&c->d_count, sizeof(uint32_t) * 4);
     A((void **)&c->ranges, sizeof(uint2) * (size_t)tiles);
+    A((void **)&c->tile_order, sizeof(uint32_t) * (size_t)tiles);
     A((void **)&c->zbuf, sizeof(double) * GS2_ZPOS * (size_t)max_n);   // FP64 with precision = 1
     A((void **)&c->pix_e, sizeof(float) * 3 * P);
     A((void **)&c->pix_h, sizeof(float) * 3 * P);
@@ -298,6 +299,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         A((void **)&l->bsum, sizeof(unsigned long long) * 1024);
         A((void **)&l->d_count, sizeof(uint32_t) * 4);
         A((void **)&l->ranges, sizeof(uint2) * (size_t)tiles);
+        A((void **)&l->tile_order, sizeof(uint32_t) * (size_t)tiles);
         A((void **)&l->zbuf, sizeof(double) * GS2_ZPOS * (size_t)max_n);
         A((void **)&l->pix_e, sizeof(float) * 3 * P);
         A((void **)&l->pix_h, sizeof(float) * 3 * P);

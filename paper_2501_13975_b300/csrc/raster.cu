@@ -14,12 +14,14 @@
 __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ ids, ProjView pv, int W, int H,
                                                          int tiles_x, float amin, float amax, float tmin,
-                                                         float *__restrict__ image, RasterView rv) {
+                                                         float *__restrict__ image, RasterView rv,
+                                                         const uint32_t *__restrict__ tile_order) {
     // two staging buffers: batch b + 1 is copied in (cp.async) while batch b is walked
     __shared__ float4 sA[2][GS2_TILE_PIX], sB[2][GS2_TILE_PIX], sC[2][GS2_TILE_PIX];
     const int t = threadIdx.x;
-    const int tile = blockIdx.y * tiles_x + blockIdx.x;
-    const int px = blockIdx.x * GS2_TILE + gs2_tile_px(t), py = blockIdx.y * GS2_TILE + gs2_tile_py(t);
+    const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
+    const int tcol = tile % tiles_x, trow = tile / tiles_x;
+    const int px = tcol * GS2_TILE + gs2_tile_px(t), py = trow * GS2_TILE + gs2_tile_py(t);
     const bool inside = px < W && py < H;
     bool done = !inside;
     const uint2 r = ranges[tile];
@@ -85,9 +87,9 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
 
 cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
                           RasterView rv, cudaStream_t st) {
-    dim3 grid(ctx->tiles_x, ctx->tiles_y);
+    const unsigned grid = (unsigned)(ctx->tiles_x * ctx->tiles_y);
     k_raster<<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->list_ids, pv, cam.w, cam.h, ctx->tiles_x,
-                                            cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv);
+                                            cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv, ctx->tile_order);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

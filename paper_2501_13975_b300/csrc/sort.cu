@@ -421,6 +421,37 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *coun
     }
 }
 
+// Launch order of the tiles for the compositing and the accumulation: by
+// descending list length, in buckets of floor(log2(length)) (order within a
+// bucket arbitrary, empty tiles last), so the longest tiles start in the
+// first waves and the last wave is short.  The order changes no result: tiles
+// are independent.  One CTA: a shared-memory histogram of the buckets, a scan,
+// and a scatter by shared atomics.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, int ntiles,
+                                                     uint32_t *__restrict__ order) {
+    __shared__ uint32_t cnt[33];
+    const int t = threadIdx.x;
+    if (t < 33) cnt[t] = 0u;
+    __syncthreads();
+    auto bucket = [&](int i) {
+        const uint2 r = ranges[i];
+        const uint32_t len = r.y - r.x;
+        return len ? (uint32_t)__clz(len) : 32u;   // 0 for the longest lists, 32 for empty tiles
+    };
+    for (int i = t; i < ntiles; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1u);
+    __syncthreads();
+    if (t == 0) {
+        uint32_t acc = 0u;
+        for (int b = 0; b < 33; ++b) {
+            const uint32_t c = cnt[b];
+            cnt[b] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < ntiles; i += blockDim.x) order[atomicAdd(&cnt[bucket(i)], 1u)] = (uint32_t)i;
+}
+
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
                             unsigned long long *stats, const uint32_t *order_in, uint32_t *order_out) {
     const uint32_t cap = (uint32_t)ctx->max_pairs;
@@ -434,6 +465,10 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
         ctx->sorted = 0;
         ctx->list_ids = ctx->vals[0];
         ctx->det_order = nullptr;
+        if (ctx->tile_order) {   // every tile empty: any order
+            k_tile_order<<<1, 1024, 0, st>>>(ctx->ranges, ntiles, ctx->tile_order);
+            GS2_COUNT_LAUNCH(1);
+        }
         return cudaMemsetAsync(ctx->d_count, 0, sizeof(uint32_t) * 2, st);
     }
     // 1. depth order of the Gaussians (or the caller's copy of it for the same
@@ -475,6 +510,10 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
     // 5. tile ranges
     k_ranges<<<148 * 4, 256, 0, st>>>(ctx->keys[ctx->sorted], ctx->d_count, ctx->ranges, (uint32_t)ntiles,
                                        stats);
+    if (ctx->tile_order) {
+        k_tile_order<<<1, 1024, 0, st>>>(ctx->ranges, ntiles, ctx->tile_order);
+        ++launches;
+    }
     GS2_COUNT_LAUNCH(launches + 7);
     return cudaGetLastError();
 }
