@@ -39,16 +39,19 @@ if ROOT not in sys.path:
 from paper_2501_13975_b300 import synth  # noqa: E402
 
 GROUP_NAMES = ("position", "rotation", "scaling", "opacity", "colour")
-# FP32 operations of the accumulation per evaluated (pixel, Gaussian) pair:
-# 46 common (falloff and alpha 14, T_k 2, weight 1, colour-behind terms 6,
-# e.a 5, h.a^2 8, C_back update 10) + the group's payload + its P warp-sum adds:
-# position 197 + 41 (falloff derivatives over G 61, scaled terms 20, Hessian
-# entries 61, colour cross terms 42, colour 13), rotation / scaling 80 + 9
-# (falloff derivatives 43, payload 37), opacity 3 + 2, colour 9 + 6
-EVAL_FLOPS = (284, 135, 135, 51, 61)
+# FP32 operations of the accumulation per evaluated (pixel, Gaussian) pair
+# (a fused multiply-add counts 2): 46 common (falloff and alpha 14, T_k 2,
+# weight 1, colour-behind terms 6, e.a 5, h.a^2 8, C_back update 10) + the
+# group's payload + its P warp-sum adds.  The geometric payloads are moments
+# of the per-pixel weights over monomials of u = Sigma^-1 d: position 132 + 48
+# (u 6, monomials 12, weights 3, W1 moments 24, W2 moments 29, colour-path
+# weights 15 and moments 30, colour 13), rotation / scaling 43 + 13 (u 6,
+# monomials 8, weights 3, W1 moments 10, W2 moments 16), opacity 3 + 2,
+# colour 9 + 6
+EVAL_FLOPS = (226, 102, 102, 51, 61)
 # FP32 peak: 148 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.032 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-PAYLOAD_FLOATS = (41, 9, 9, 2, 6)       # image-space accumulator floats per Gaussian and view
+PAYLOAD_FLOATS = (48, 13, 13, 2, 6)     # image-space accumulator floats per Gaussian and view
 RECORD_BYTES = 40                        # per (tile, Gaussian) pair: id (4) + pi, conic, sigma, c~ (36)
 PIXEL_BYTES = 32                         # per pixel: e, h (24) + T_final, last (8)
 
@@ -1088,7 +1091,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v9"
+KERNEL_REV = "accum-v10"
 
 
 def main():

@@ -7,10 +7,20 @@
 //   dc/dalpha = T_k (c~ - C_back) =: a,  dc/dc~ = alpha T_k =: w,
 //   d2c/dalpha2 = 0, d2c/dalpha dc~ = T_k,
 // and alpha = sigma G(z), z = (pi_x, pi_y, Sxx, Sxy, Syy).  Each pixel forms
-// the group's image-space payload (position 41 floats: g_z, H_zz, cross
-// terms, colour sums; scale/rotation 9; opacity 2; colour 6), the warp sums
-// it with shuffles and lane 0 adds it with atomics into a per-view,
-// per-Gaussian buffer zbuf[P][n] (L2-resident at the working-set sizes).
+// the group's image-space payload, the warp sums it with shuffles and the
+// lanes add it with atomics into a per-view, per-Gaussian buffer zbuf[P][n]
+// (L2-resident at the working-set sizes).  Every z-derivative of G is G times
+// a polynomial of degree <= 4 in u = Sigma^-1 d (d the pixel offset) whose
+// coefficients are the conic's, constant per Gaussian, so the geometric
+// payloads are moments sum_p W u_x^i u_y^j of the per-pixel weights
+// W1 = A_h alpha^2 (the Gauss-Newton part), W2 = E_a alpha (gradient and
+// e-weighted curvature) and, for position, alpha times the colour-path weights:
+// position 48 floats (W1 x 12 monomials, W2 x 15, cross 3 x 5, colour 6),
+// scale/rotation 13 (W1 x 5, W2 x 8), opacity 2, colour 6.  The epilogue
+// rebuilds the z-space gradient and Hessian from the moments and the conic
+// (pos_moments_to_z, sigma_moments_to_z): about a third less arithmetic per
+// (pixel, Gaussian) than forming the 20 (position) or 9 derivative terms per
+// pixel, in the same number of padded reduction slots.
 //
 // Pass 2 (k_epi_*, one thread per Gaussian): chain rule from z to the group's
 // parameters with the per-view constant Jacobians (dz/dp, d2z/dp2, dc~/dp,
@@ -22,9 +32,9 @@
 template <int G> struct Payload;
 // P: accumulator floats per Gaussian and view; MIN_CTAS: resident CTAs per SM
 // the register allocation is held to (65536 / (MIN_CTAS x 128) registers a thread)
-template <> struct Payload<GS2_POS> { static constexpr int P = 41, MIN_CTAS = 4; };
-template <> struct Payload<GS2_ROT> { static constexpr int P = 9, MIN_CTAS = 7; };
-template <> struct Payload<GS2_SCALE> { static constexpr int P = 9, MIN_CTAS = 7; };
+template <> struct Payload<GS2_POS> { static constexpr int P = GS2_ZPOS, MIN_CTAS = 4; };
+template <> struct Payload<GS2_ROT> { static constexpr int P = 13, MIN_CTAS = 7; };
+template <> struct Payload<GS2_SCALE> { static constexpr int P = 13, MIN_CTAS = 7; };
 template <> struct Payload<GS2_OPACITY> { static constexpr int P = 2, MIN_CTAS = 8; };
 template <> struct Payload<GS2_COLOR> { static constexpr int P = 6, MIN_CTAS = 8; };
 
@@ -32,46 +42,100 @@ template <> struct Payload<GS2_COLOR> { static constexpr int P = 6, MIN_CTAS = 8
 __host__ __device__ constexpr int ut5(int i, int j) { return i * 5 - i * (i - 1) / 2 + (j - i); }
 __host__ __device__ constexpr int ut3(int i, int j) { return i * 3 - i * (i - 1) / 2 + (j - i); }
 
-// Derivatives of G = exp(-1/2 d^T A d), d = x - pi, A = Sigma^{-1}, w.r.t.
-// pi (2) and the covariance parameters (Sxx, Sxy, Syy) (Sxy counted once, the
-// matrix entries (0,1) and (1,0) both move), returned divided by G:
-//   u = A d; dG/dpi = G u; d2G/dpi2 = G (u u^T - A);
-//   r_t = u^T E_t u / 2 (r = (ux^2/2, ux uy, uy^2/2)), dG/dS_t = G r_t;
-//   d2G/dS_t dS_f = G (r_t r_f - v_t^T A v_f), v_t = E_t u
-//     (v_0 = (ux, 0), v_1 = (uy, ux), v_2 = (0, uy));
-//   d2G/dpi_a dS_t = G (u_a r_t - (A v_t)_a).
-// The zero components of v_t are left out of the products, and the common
-// factor G is applied by the caller together with sigma (sigma G = alpha).
-template <bool WITH_PI>
-__device__ __forceinline__ void falloff_unit(float ca, float cb, float cc, float dx, float dy, float gz[5],
-                                             float gzz[15]) {
-    const float ux = ca * dx + cb * dy, uy = cb * dx + cc * dy;
-    const float r0 = 0.5f * ux * ux, r1 = ux * uy, r2 = 0.5f * uy * uy;
-    // A v_t
-    const float a0x = ca * ux, a0y = cb * ux;
-    const float a1x = ca * uy + cb * ux, a1y = cb * uy + cc * ux;
-    const float a2x = cb * uy, a2y = cc * uy;
-    gz[2] = r0;
-    gz[3] = r1;
-    gz[4] = r2;
-    gzz[ut5(2, 2)] = r0 * r0 - ux * a0x;
-    gzz[ut5(2, 3)] = r0 * r1 - ux * a1x;
-    gzz[ut5(2, 4)] = r0 * r2 - ux * a2x;
-    gzz[ut5(3, 3)] = r1 * r1 - (uy * a1x + ux * a1y);
-    gzz[ut5(3, 4)] = r1 * r2 - (uy * a2x + ux * a2y);
-    gzz[ut5(4, 4)] = r2 * r2 - uy * a2y;
-    if (WITH_PI) {
-        gz[0] = ux;
-        gz[1] = uy;
-        gzz[ut5(0, 0)] = ux * ux - ca;
-        gzz[ut5(0, 1)] = ux * uy - cb;
-        gzz[ut5(1, 1)] = uy * uy - cc;
-        gzz[ut5(0, 2)] = ux * r0 - a0x;
-        gzz[ut5(0, 3)] = ux * r1 - a1x;
-        gzz[ut5(0, 4)] = ux * r2 - a2x;
-        gzz[ut5(1, 2)] = uy * r0 - a0y;
-        gzz[ut5(1, 3)] = uy * r1 - a1y;
-        gzz[ut5(1, 4)] = uy * r2 - a2y;
+// Moments of the geometric payloads and their conversion to the z-space sums.
+// With A = Sigma^-1 = [[a, b], [b, c]] and u = A d (d = pixel - pi), the
+// derivatives of G w.r.t. z = (pi_x, pi_y, S_xx, S_xy, S_yy) (S_xy counted once),
+// divided by G, are
+//   dG/dz = (u_x, u_y, u_x^2/2, u_x u_y, u_y^2/2) =: gz,
+//   d2G/dz_i dz_j = gz_i gz_j - (the terms of A), e.g. (pi_x, pi_x): u_x^2 - a,
+//   (S_xx, S_xx): u_x^4/4 - a u_x^2, (S_xy, S_xy): u_x^2 u_y^2 - a u_y^2 - 2 b u_x u_y - c u_x^2
+// (see the conversions below for every entry).  The image-space sums
+//   g_z = sum W2 gz,  H_zz = sum W1 gz gz^T + W2 d2G/dz2 (W2 terms left out
+//   for Gauss-Newton),  cross_c = sum X_c gz
+// are therefore linear in the moments of W1, W2, X_c over monomials of u.
+// Monomial order of the W1 list: xx xy yy xxx xxy xyy yyy x4 x3y x2y2 xy3 y4
+// (x = u_x, y = u_y); the W2 list prepends 1, x, y.
+enum { MXX, MXY, MYY, MXXX, MXXY, MXYY, MYYY, MX4, MX3Y, MX2Y2, MXY3, MY4 };
+
+// position: m[48] = W1 [12] | W2 [15] | X_c [3][5] (x, y, xx, xy, yy) | colour [6]
+// -> z[41] = g_z [5] | H_zz [15] (upper, ut5) | cross [3][5] | colour [6]
+__device__ __forceinline__ void pos_moments_to_z(const float (&m)[GS2_ZPOS], float a, float b, float c, bool gn,
+                                                 float (&z)[GS2_ZSUM]) {
+    const float *M1 = m, *M2 = m + 15;   // M2[i] = W2 moment of W1-list monomial i
+    const float w0 = m[12], wx = m[13], wy = m[14];
+    z[0] = wx;
+    z[1] = wy;
+    z[2] = 0.5f * M2[MXX];
+    z[3] = M2[MXY];
+    z[4] = 0.5f * M2[MYY];
+    float H[15];
+    H[0] = M1[MXX];                  // (0,0)
+    H[1] = M1[MXY];                  // (0,1)
+    H[2] = 0.5f * M1[MXXX];          // (0,2)
+    H[3] = M1[MXXY];                 // (0,3)
+    H[4] = 0.5f * M1[MXYY];          // (0,4)
+    H[5] = M1[MYY];                  // (1,1)
+    H[6] = 0.5f * M1[MXXY];          // (1,2)
+    H[7] = M1[MXYY];                 // (1,3)
+    H[8] = 0.5f * M1[MYYY];          // (1,4)
+    H[9] = 0.25f * M1[MX4];          // (2,2)
+    H[10] = 0.5f * M1[MX3Y];         // (2,3)
+    H[11] = 0.25f * M1[MX2Y2];       // (2,4)
+    H[12] = M1[MX2Y2];               // (3,3)
+    H[13] = 0.5f * M1[MXY3];         // (3,4)
+    H[14] = 0.25f * M1[MY4];         // (4,4)
+    if (!gn) {
+        H[0] += M2[MXX] - a * w0;
+        H[1] += M2[MXY] - b * w0;
+        H[2] += 0.5f * M2[MXXX] - a * wx;
+        H[3] += M2[MXXY] - a * wy - b * wx;
+        H[4] += 0.5f * M2[MXYY] - b * wy;
+        H[5] += M2[MYY] - c * w0;
+        H[6] += 0.5f * M2[MXXY] - b * wx;
+        H[7] += M2[MXYY] - b * wy - c * wx;
+        H[8] += 0.5f * M2[MYYY] - c * wy;
+        H[9] += 0.25f * M2[MX4] - a * M2[MXX];
+        H[10] += 0.5f * M2[MX3Y] - a * M2[MXY] - b * M2[MXX];
+        H[11] += 0.25f * M2[MX2Y2] - b * M2[MXY];
+        H[12] += M2[MX2Y2] - a * M2[MYY] - 2.f * b * M2[MXY] - c * M2[MXX];
+        H[13] += 0.5f * M2[MXY3] - b * M2[MYY] - c * M2[MXY];
+        H[14] += 0.25f * M2[MY4] - c * M2[MYY];
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) z[5 + i] = H[i];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float *X = m + 27 + 5 * ch;
+        z[20 + 5 * ch + 0] = X[0];
+        z[20 + 5 * ch + 1] = X[1];
+        z[20 + 5 * ch + 2] = 0.5f * X[2];
+        z[20 + 5 * ch + 3] = X[3];
+        z[20 + 5 * ch + 4] = 0.5f * X[4];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) z[35 + i] = m[42 + i];
+}
+
+// scaling / rotation: m[13] = W1 [x4 x3y x2y2 xy3 y4] | W2 [xx xy yy x4 x3y x2y2 xy3 y4]
+// -> z[9] = g over (S_xx, S_xy, S_yy) [3] | H [6] (upper, ut3)
+__device__ __forceinline__ void sigma_moments_to_z(const float (&m)[13], float a, float b, float c, bool gn,
+                                                   float (&z)[9]) {
+    z[0] = 0.5f * m[5];
+    z[1] = m[6];
+    z[2] = 0.5f * m[7];
+    z[3] = 0.25f * m[0];
+    z[4] = 0.5f * m[1];
+    z[5] = 0.25f * m[2];
+    z[6] = m[2];
+    z[7] = 0.5f * m[3];
+    z[8] = 0.25f * m[4];
+    if (!gn) {
+        z[3] += 0.25f * m[8] - a * m[5];
+        z[4] += 0.5f * m[9] - a * m[6] - b * m[5];
+        z[5] += 0.25f * m[10] - b * m[6];
+        z[6] += m[10] - a * m[7] - 2.f * b * m[6] - c * m[5];
+        z[7] += 0.5f * m[11] - b * m[7] - c * m[6];
+        z[8] += 0.25f * m[12] - c * m[7];
     }
 }
 
@@ -185,7 +249,6 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
     const float *e = ps.e, *h = ps.h;
     const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
     const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
-    const float Es = gn ? 0.f : Ea;   // weight of the second-derivative terms
     if (GROUP == GS2_OPACITY) {
         if (!clamped) {
             pl[0] += Ea * G;
@@ -199,52 +262,48 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
         pl[4] += w * w * h[1];
         pl[5] += w * w * h[2];
     } else if (GROUP == GS2_ROT || GROUP == GS2_SCALE) {
-        if (!clamped) {
-            // not clamped: alpha = sigma G, the factor of every falloff derivative
-            float gz[5], gzz[15];
-            falloff_unit<false>(A.z, A.w, B.x, dx, dy, gz, gzz);
-            float az[3], bz[3];
+        if (!clamped) {   // not clamped: alpha = sigma G, the factor of every falloff derivative
+            const float ux = A.z * dx + A.w * dy, uy = A.w * dx + B.x * dy;
+            const float xx = ux * ux, xy = ux * uy, yy = uy * uy;
+            const float m4[5] = {xx * xx, xx * xy, xx * yy, xy * yy, yy * yy};
+            const float W1 = Ah * alpha * alpha, W2 = Ea * alpha;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                az[i] = alpha * gz[2 + i];
-                bz[i] = Ah * az[i];
-                pl[i] += Ea * az[i];
-            }
-            const float ez = Es * alpha;
+            for (int i = 0; i < 5; ++i) pl[i] += W1 * m4[i];
+            pl[5] += W2 * xx;
+            pl[6] += W2 * xy;
+            pl[7] += W2 * yy;
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int jx = i; jx < 3; ++jx)
-                    pl[3 + ut3(i, jx)] += bz[i] * az[jx] + ez * gzz[ut5(2 + i, 2 + jx)];
+            for (int i = 0; i < 5; ++i) pl[8 + i] += W2 * m4[i];
         }
     } else {  // position
         const float aa[3] = {a0, a1, a2};
         if (!clamped) {
-            float gz[5], gzz[15];
-            falloff_unit<true>(A.z, A.w, B.x, dx, dy, gz, gzz);
-            float az[5], bz[5];
+            const float ux = A.z * dx + A.w * dy, uy = A.w * dx + B.x * dy;
+            const float xx = ux * ux, xy = ux * uy, yy = uy * uy;
+            const float mono[12] = {xx,      xy,      yy,      xx * ux, xx * uy, xy * uy,
+                                    yy * uy, xx * xx, xx * xy, xx * yy, xy * yy, yy * yy};
+            const float W1 = Ah * alpha * alpha, W2 = Ea * alpha;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                az[i] = alpha * gz[i];
-                bz[i] = Ah * az[i];
-                pl[i] += Ea * az[i];
-            }
-            const float ez = Es * alpha;
+            for (int i = 0; i < 12; ++i) pl[i] += W1 * mono[i];
+            pl[12] += W2;
+            pl[13] += W2 * ux;
+            pl[14] += W2 * uy;
 #pragma unroll
-            for (int i = 0; i < 5; ++i)
+            for (int i = 0; i < 12; ++i) pl[15 + i] += W2 * mono[i];
 #pragma unroll
-                for (int jx = i; jx < 5; ++jx) pl[5 + ut5(i, jx)] += bz[i] * az[jx] + ez * gzz[ut5(i, jx)];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float xc = h[c] * aa[c] * w + (gn ? 0.f : e[c] * Tk);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) pl[20 + c * 5 + i] += xc * az[i];
+            for (int ch = 0; ch < 3; ++ch) {
+                const float X = (h[ch] * aa[ch] * w + (gn ? 0.f : e[ch] * Tk)) * alpha;
+                pl[27 + 5 * ch + 0] += X * ux;
+                pl[27 + 5 * ch + 1] += X * uy;
+                pl[27 + 5 * ch + 2] += X * xx;
+                pl[27 + 5 * ch + 3] += X * xy;
+                pl[27 + 5 * ch + 4] += X * yy;
             }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            pl[35 + c] += w * e[c];
-            pl[38 + c] += w * w * h[c];
+        for (int ch = 0; ch < 3; ++ch) {
+            pl[42 + ch] += w * e[ch];
+            pl[45 + ch] += w * w * h[ch];
         }
     }
     ps.cb0 = alpha * C.x + om * ps.cb0;
@@ -519,13 +578,15 @@ __global__ void k_epi_scale(DevScene sc, DevCam cam, const ProjView pv, ACC *__r
     if (k >= n || pv.touched[k] == 0u) return;
     // every load first (accumulators, the block entries updated, parameters):
     // they are then in flight together instead of one memory latency each
-    float z[9];
+    float mo[13], z[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
+    for (int i = 0; i < 13; ++i) mo[i] = (float)zbuf[(size_t)i * n + k];
+    const float4 cA = pv.recA[k], cB = pv.recB[k];   // conic (a, b) and c
     GaussGeo g;
     load_geo(sc, k, g);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
+    for (int i = 0; i < 13; ++i) zbuf[(size_t)i * n + k] = 0.f;
+    sigma_moments_to_z(mo, cA.z, cA.w, cB.x, gn != 0, z);
     float t[3], T[2][3];
     cam_T(cam, g.p, t, T);
     float dS[3][3], d2S[3][3];  // [param j][(xx,xy,yy)]
@@ -567,13 +628,15 @@ __global__ void k_epi_rot(DevScene sc, DevCam cam, DevCam primary, const ProjVie
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
-    float z[9];
+    float mo[13], z[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
+    for (int i = 0; i < 13; ++i) mo[i] = (float)zbuf[(size_t)i * n + k];
+    const float4 cA = pv.recA[k], cB = pv.recB[k];   // conic (a, b) and c
     GaussGeo g;
     load_geo(sc, k, g);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) zbuf[(size_t)i * n + k] = 0.f;
+    for (int i = 0; i < 13; ++i) zbuf[(size_t)i * n + k] = 0.f;
+    sigma_moments_to_z(mo, cA.z, cA.w, cB.x, gn != 0, z);
     float t[3], T[2][3];
     cam_T(cam, g.p, t, T);
     // Sigma3 = R diag(s^2) R^T; K = [a]x with a the primary view direction
@@ -644,12 +707,17 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n || pv.touched[k] == 0u) return;
-    float z[GS2_ZPOS];
-    // all loads first, then the clears (interleaving them serialises the loads)
+    float z[GS2_ZSUM];
+    {
+        float mo[GS2_ZPOS];
+        // all loads first, then the clears (interleaving them serialises the loads)
 #pragma unroll
-    for (int i = 0; i < GS2_ZPOS; ++i) z[i] = (float)zbuf[(size_t)i * n + k];
+        for (int i = 0; i < GS2_ZPOS; ++i) mo[i] = (float)zbuf[(size_t)i * n + k];
+        const float4 cA = pv.recA[k], cB = pv.recB[k];   // conic (a, b) and c
 #pragma unroll
-    for (int i = 0; i < GS2_ZPOS; ++i) zbuf[(size_t)i * n + k] = 0.f;
+        for (int i = 0; i < GS2_ZPOS; ++i) zbuf[(size_t)i * n + k] = 0.f;
+        pos_moments_to_z(mo, cA.z, cA.w, cB.x, gn != 0, z);
+    }
     GaussGeo g;
     load_geo(sc, k, g);
     const float *V = cam.V;

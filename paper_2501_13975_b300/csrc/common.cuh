@@ -28,7 +28,8 @@
 #define GS2_PROF_LOSS 7
 #define GS2_MAX_LANES 16             // concurrent views per group in a sweep (secondaries)
 #define GS2_TILE_PIX (GS2_TILE * GS2_TILE)
-#define GS2_ZPOS 41                  // image-space payload of the position group
+#define GS2_ZPOS 48                  // image-space payload (moments) of the position group, the largest
+#define GS2_ZSUM 41                  // the position group's z-space sums rebuilt from it (g, H, cross, colour)
 #define GS2_MAX_SH 16
 
 // device status bits
