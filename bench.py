@@ -189,6 +189,9 @@ def run_gpu(args, rank, world, local_rank):
     losses = torch.zeros(10, dtype=torch.float64, device=dev)
     nfail = torch.zeros(1, dtype=torch.int32, device=dev)
     tuning = ctx.autotune(scene, cams, targets, knn, 0, reps=2) if not args.no_autotune else ctx.tuning()
+    if args.accum_px:
+        ctx.set_tuning(accum_px=args.accum_px)
+        tuning = dict(tuning, accum_px=args.accum_px)
 
     # the timed sweeps: through a one-scene gs2_batch captured as a CUDA graph
     # per sweep (re-captured and updated in place: no priming, any primary
@@ -197,7 +200,7 @@ def run_gpu(args, rank, world, local_rank):
     if args.graph:
         batch = gs2.Batch([dict(max_gaussians=w["n"], max_width=W, max_height=H, max_sh_degree=w["sh"],
                                 max_pairs=w["max_pairs"])], dict(precision=args.precision))
-        batch.set_tuning(0, tuning["sort_blocks"], tuning["sort_rows"], tuning["view_lanes"])
+        batch.set_tuning(0, tuning["sort_blocks"], tuning["sort_rows"], tuning["view_lanes"], tuning["accum_px"])
         prep = batch.prepare([scene], [cams], [targets], [knn])
 
     def sweep(i, tg=None):
@@ -363,7 +366,7 @@ def run_gpu(args, rank, world, local_rank):
     jacobi = None
     if not args.no_variants:
         cj = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=args.precision, group_jacobi=1))
-        cj.set_tuning(**{k: tuning[k] for k in ("sort_blocks", "sort_rows", "view_lanes")})
+        cj.set_tuning(**{k: tuning[k] for k in ("sort_blocks", "sort_rows", "view_lanes", "accum_px")})
         sj = scene.clone()
         for i in range(2):
             cj.sweep(sj, cams, targets, knn, i % ncam)
@@ -1111,6 +1114,8 @@ def main():
     ap.add_argument("--no-det-path", action="store_true", help="skip timing the deterministic mode")
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (profiling captures)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning")
+    ap.add_argument("--accum-px", type=int, default=0, choices=[0, 2, 4],
+                    help="pixels per thread of the position accumulation (overrides the tuning; 0: keep)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: time sweeps as a CUDA graph re-captured per sweep (one-scene gs2_batch); 0: eager")
     ap.add_argument("--variants", action="store_true",

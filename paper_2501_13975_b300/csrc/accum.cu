@@ -1,6 +1,7 @@
 // gs2_accum_newton_blocks (Eq. local_hessian_gradient, full Newton).
 //
-// Pass 1 (k_accum, one CTA per screen tile, one thread per two pixels): walk the
+// Pass 1 (k_accum, one CTA per screen tile, one thread per two pixels, or four
+// for the position payload): walk the
 // tile's depth-sorted list back to front (the order that yields the colour
 // behind each Gaussian, C_back, and its transmittance T_k = T_after/(1-alpha)).
 // For pixel c = C_front + T_k (alpha_k c~_k + (1 - alpha_k) C_back):
@@ -317,8 +318,21 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
 // det_part[sorted position][P] (entries past the tile's last contributor
 // get zero rows); k_det_reduce then sums each Gaussian's entries in a fixed
 // order into zbuf.
-template <int GROUP, typename ACC, bool DET = false>
-__global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_accum(const uint2 *__restrict__ ranges,
+// NQ: pixels per thread (2, or 4 for the position payload, whose warp
+// reduction costs about as much as the payload itself: four pixels a lane
+// pay it once per 128 pixels).  NQ = 2: NT threads, warp w
+// covers an 8x8 block, lane l the pixels (l % 8, l / 8 + 4 q); NQ = 4: two
+// warps per 16x16 tile, each an 8-wide column of the tile, lane l the pixels
+// (l % 8, l / 8 + 4 q), q = 0..3.
+template <int GROUP, int NQ> struct AccumShape {
+    static constexpr int NT = GS2_TILE_PIX / NQ;   // threads per tile
+    static constexpr int NW = NT / 32;
+    static constexpr int MIN_CTAS = NQ == 2 ? Payload<GROUP>::MIN_CTAS : 6;
+    static_assert(NT % 32 == 0, "a tile holds whole warps");
+};
+
+template <int GROUP, typename ACC, bool DET = false, int NQ = 2>
+__global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, NQ>::MIN_CTAS) k_accum(const uint2 *__restrict__ ranges,
                                                            const uint32_t *__restrict__ ids, ProjView pv,
                                                            RasterView rv, const float *__restrict__ E,
                                                            const float *__restrict__ Hh, int W, int H, int tiles_x,
@@ -327,24 +341,27 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                                                            float *__restrict__ det_part,
                                                            const uint32_t *__restrict__ tile_order) {
     constexpr int P = Payload<GROUP>::P;
+    constexpr int NT = AccumShape<GROUP, NQ>::NT, NW = AccumShape<GROUP, NQ>::NW;
     constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
-    constexpr int PER = NB / GS2_PAIR_THREADS;        // entries each thread stages
+    constexpr int PER = NB / NT;                      // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
-    __shared__ float sDet[DET ? GS2_PAIR_WARPS : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
+    __shared__ float sDet[DET ? NW : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
     const int t = threadIdx.x, lane = t & 31;
     if constexpr (DET) {
-        for (int q = t; q < GS2_PAIR_WARPS * GS2_DET_CHUNK * P; q += GS2_PAIR_THREADS) (&sDet[0][0][0])[q] = 0.f;
+        for (int q = t; q < NW * GS2_DET_CHUNK * P; q += NT) (&sDet[0][0][0])[q] = 0.f;
     }
     const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
     const int tcol = tile % tiles_x, trow = tile / tiles_x;
-    const int px = tcol * GS2_TILE + gs2_pair_px(t), py = trow * GS2_TILE + gs2_pair_py(t);
+    const int wb = t >> 5;   // warp block: (wb % GS2_WPR) 8 columns, (wb / GS2_WPR) 4 NQ rows
+    const int px = tcol * GS2_TILE + (wb % GS2_WPR) * 8 + (t & 7);
+    const int py = trow * GS2_TILE + (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
     const size_t PI = (size_t)W * H;
-    PixState ps[2];
+    PixState ps[NQ];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         const int y = py + 4 * q;
         PixState &s = ps[q];
         s.inside = px < W && y < H;
@@ -364,7 +381,9 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
             }
         }
     }
-    const uint32_t last2 = max(ps[0].last, ps[1].last);
+    uint32_t last2 = ps[0].last;
+#pragma unroll
+    for (int q = 1; q < NQ; ++q) last2 = max(last2, ps[q].last);
     if (t == 0) sMax = 0u;
     __syncthreads();
     atomicMax(&sMax, last2);
@@ -373,11 +392,11 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
     // this warp's own end of list: its lanes have nothing to do beyond it
     const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last2);
     const uint2 r = ranges[tile];
-    const float fx = (float)px, fy0 = (float)py, fy1 = (float)(py + 4);
+    const float fx = (float)px;
     uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
     // batches back to front: batch b covers [max(0, maxlast - NB (b + 1)), maxlast - NB b)
     const int nbat = (maxlast + NB - 1) / NB;
-    auto list_index = [&](int b, int i) { return maxlast - NB * (b + 1) + t + i * GS2_PAIR_THREADS; };
+    auto list_index = [&](int b, int i) { return maxlast - NB * (b + 1) + t + i * NT; };
     uint32_t knext[PER];
     auto fetch = [&](int b) {
 #pragma unroll
@@ -390,7 +409,7 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
         const int buf = b & 1;
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            const int j = t + i * GS2_PAIR_THREADS;
+            const int j = t + i * NT;
             if (list_index(b, i) >= 0) {
                 const uint32_t k = knext[i];
                 sId[buf][j] = k;
@@ -422,17 +441,18 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
             const int s = jj - base;
             const float4 A = sA[buf][s], B = sB[buf][s];
             const float dx = __fsub_rn(fx, A.x);
-            bool act[2], clamped[2];
-            float G[2], alpha[2], dy[2];
+            bool act[NQ], clamped[NQ];
+            float G[NQ], alpha[NQ], dy[NQ];
+            bool any = false;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 act[q] = ps[q].inside && (uint32_t)jj < ps[q].last;
                 G[q] = 0.f;
                 alpha[q] = 0.f;
                 dy[q] = 0.f;
                 clamped[q] = false;
                 if (act[q]) {
-                    dy[q] = __fsub_rn(q ? fy1 : fy0, A.y);
+                    dy[q] = __fsub_rn((float)(py + 4 * q), A.y);
                     const float qf = dec_quad(A.z, A.w, B.x, dx, dy[q]);
                     if (qf <= B.z) {   // composited (the same decision as k_raster)
                         G[q] = gs2_falloff(qf);
@@ -442,15 +462,16 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                         act[q] = false;
                     }
                 }
+                any = any || act[q];
+                nact += act[q] ? 1u : 0u;
             }
-            if (!__any_sync(0xFFFFFFFFu, act[0] || act[1])) return;
-            nact += (act[0] ? 1u : 0u) + (act[1] ? 1u : 0u);
+            if (!__any_sync(0xFFFFFFFFu, any)) return;
             float pl[P];
 #pragma unroll
             for (int i = 0; i < P; ++i) pl[i] = 0.f;
             const float4 C = sC[buf][s];
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < NQ; ++q)
                 if (act[q]) pixel_payload<GROUP, P>(ps[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], gn != 0, pl);
             if constexpr (DET)
                 warp_reduce_scatter_store<P>(pl, lane, row);
@@ -464,12 +485,12 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
                 for (int jj = min(c1, wlast) - 1; jj >= c0; --jj) entry(jj, &sDet[w][jj - c0][0]);
                 __syncthreads();
                 const int cnt = (c1 - c0) * P;
-                for (int q = t; q < cnt; q += GS2_PAIR_THREADS) {
+                for (int q = t; q < cnt; q += NT) {
                     const int e = q / P, i = q - e * P;
                     float v = sDet[0][e][i];
                     sDet[0][e][i] = 0.f;
 #pragma unroll
-                    for (int ww = 1; ww < GS2_PAIR_WARPS; ++ww) {   // warp order
+                    for (int ww = 1; ww < NW; ++ww) {   // warp order
                         v = __fadd_rn(v, sDet[ww][e][i]);
                         sDet[ww][e][i] = 0.f;
                     }
@@ -483,7 +504,7 @@ __global__ void __launch_bounds__(GS2_PAIR_THREADS, Payload<GROUP>::MIN_CTAS) k_
     }
     if constexpr (DET) {   // entries past the last contributor of every pixel contribute nothing
         const int nl = (int)(r.y - r.x);
-        for (int q = t + maxlast * P; q < nl * P; q += GS2_PAIR_THREADS) det_part[(size_t)r.x * P + q] = 0.f;
+        for (int q = t + maxlast * P; q < nl * P; q += NT) det_part[(size_t)r.x * P + q] = 0.f;
     }
     if (active_stat) {
         unsigned long long c = nact;
@@ -1011,7 +1032,17 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
         }                                                                                                         \
     } while (0)
     switch (group) {
-    case GS2_POS: ACC_LAUNCH(GS2_POS); break;
+    case GS2_POS:
+#if GS2_TILE == 16
+        if (!det && ctx->accum_px == 4) {   // four pixels per thread: two warps per tile
+            k_accum<GS2_POS, ACC, false, 4><<<grid, AccumShape<GS2_POS, 4>::NT, 0, st>>>(
+                ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,
+                cfg.alpha_max, cfg.gauss_newton, zb, n, act, (float *)nullptr, ctx->tile_order);
+            break;
+        }
+#endif
+        ACC_LAUNCH(GS2_POS);
+        break;
     case GS2_ROT: ACC_LAUNCH(GS2_ROT); break;
     case GS2_SCALE: ACC_LAUNCH(GS2_SCALE); break;
     case GS2_OPACITY: ACC_LAUNCH(GS2_OPACITY); break;

@@ -49,6 +49,7 @@ extern "C" gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out) {
     out->sort_blocks = ctx->nb_sort;
     out->sort_rows = ctx->sort_rows;
     out->view_lanes = ctx->view_lanes;
+    out->accum_px = ctx->accum_px;
     return GS2_OK;
 }
 
@@ -57,9 +58,11 @@ extern "C" gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *t) {
     if (t->sort_blocks < 1 || t->sort_blocks > GS2_SORT_BLOCKS_MAX) return GS2_ERR_ARG;
     if (t->sort_rows != 2 && t->sort_rows != 4 && t->sort_rows != 8 && t->sort_rows != 16) return GS2_ERR_ARG;
     if (t->view_lanes != 0 && t->view_lanes != 1) return GS2_ERR_ARG;
+    if (t->accum_px != 2 && !(t->accum_px == 4 && GS2_TILE == 16)) return GS2_ERR_ARG;
     ctx->nb_sort = t->sort_blocks;
     ctx->sort_rows = t->sort_rows;
     ctx->view_lanes = t->view_lanes;
+    ctx->accum_px = t->accum_px;
     return GS2_OK;
 }
 
@@ -89,33 +92,41 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gs2_status rc = GS2_OK;
-    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows, ctx->view_lanes};
+    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows, ctx->view_lanes, ctx->accum_px};
     gs2_tuning best = keep;
     float best_ms = 1e30f;
     const int blocks[3] = {148 * 2, 148 * 4, 148 * 6};
     const int rows[4] = {2, 4, 8, 16};
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = GS2_ERR_CUDA;
-    for (int bi = 0; bi < 3 && rc == GS2_OK; ++bi)
-        for (int ri = 0; ri < 4 && rc == GS2_OK; ++ri) {
-            ctx->nb_sort = blocks[bi];
-            ctx->sort_rows = rows[ri];
-            if (!reset()) { rc = GS2_ERR_CUDA; break; }
-            // one untimed sweep (first-touch effects), then the timed ones
+    // ms per sweep of one candidate (one untimed sweep for first-touch effects, then `reps` timed)
+    auto trial = [&](const gs2_tuning &c) {
+        ctx->nb_sort = c.sort_blocks;
+        ctx->sort_rows = c.sort_rows;
+        ctx->accum_px = c.accum_px;
+        if (!reset()) { rc = GS2_ERR_CUDA; return; }
+        rc = sweep_run(ctx, &cp, cams, ncam, targets, knn, t, nullptr, nullptr, nullptr, st);
+        if (rc != GS2_OK) return;
+        if (!reset() || cudaEventRecord(e0, st) != cudaSuccess) { rc = GS2_ERR_CUDA; return; }
+        for (int r = 0; r < reps && rc == GS2_OK; ++r)
             rc = sweep_run(ctx, &cp, cams, ncam, targets, knn, t, nullptr, nullptr, nullptr, st);
-            if (rc != GS2_OK) break;
-            if (!reset() || cudaEventRecord(e0, st) != cudaSuccess) { rc = GS2_ERR_CUDA; break; }
-            for (int r = 0; r < reps && rc == GS2_OK; ++r)
-                rc = sweep_run(ctx, &cp, cams, ncam, targets, knn, t, nullptr, nullptr, nullptr, st);
-            if (rc != GS2_OK) break;
-            float ms = 0.f;
-            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = GS2_ERR_CUDA; break; }
-            ms /= (float)reps;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = {blocks[bi], rows[ri], ctx->view_lanes};
-            }
+        if (rc != GS2_OK) return;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = GS2_ERR_CUDA; return; }
+        ms /= (float)reps;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
         }
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = GS2_ERR_CUDA;
+    // the sort grid first (at the current accumulation shape), then the
+    // accumulation's pixels per thread at the best sort setting
+    for (int bi = 0; bi < 3 && rc == GS2_OK; ++bi)
+        for (int ri = 0; ri < 4 && rc == GS2_OK; ++ri)
+            trial({blocks[bi], rows[ri], ctx->view_lanes, keep.accum_px});
+    const int pxs[2] = {2, 4};
+    for (int pi = 0; pi < (GS2_TILE == 16 ? 2 : 1) && rc == GS2_OK; ++pi)
+        if (pxs[pi] != keep.accum_px) trial({best.sort_blocks, best.sort_rows, best.view_lanes, pxs[pi]});
     cudaStreamSynchronize(st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -123,10 +134,12 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
     if (rc != GS2_OK) {
         ctx->nb_sort = keep.sort_blocks;
         ctx->sort_rows = keep.sort_rows;
+        ctx->accum_px = keep.accum_px;
         return rc;
     }
     ctx->nb_sort = best.sort_blocks;
     ctx->sort_rows = best.sort_rows;
+    ctx->accum_px = best.accum_px;
     if (best_out) *best_out = best;
     if (best_ms_out) *best_ms_out = best_ms;
     return GS2_OK;
@@ -252,6 +265,7 @@ static uint64_t sweep_key(const gs2_ctx *c, const gs2_scene *scene, const gs2_ca
     fnv(h, &c->nb_sort, sizeof(c->nb_sort));
     fnv(h, &c->sort_rows, sizeof(c->sort_rows));
     fnv(h, &c->view_lanes, sizeof(c->view_lanes));
+    fnv(h, &c->accum_px, sizeof(c->accum_px));
     return h;
 }
 

@@ -146,6 +146,7 @@ struct gs2_ctx {
     int nb_sort;                 // blocks of the radix sort grid (tuning, <= GS2_SORT_BLOCKS_MAX)
     int sort_rows;               // keys per thread per scatter round (tuning: 2, 4, 8 or 16)
     int view_lanes;              // run a sweep's views concurrently (tuning: 0, 1)
+    int accum_px;                // pixels per thread of the position accumulation (tuning: 2 or 4)
     // sorting
     uint32_t *keys[2];           // pair keys: tile id
     uint32_t *vals[2];           // pair values: Gaussian id

@@ -225,6 +225,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     c->nb_sort = SORT_BLOCKS;
     c->sort_rows = 4;
     c->view_lanes = 1;
+    c->accum_px = GS2_TILE == 16 ? 4 : 2;   // measured: position accumulation 3.77 -> 3.20 ms per sweep
     const size_t P = (size_t)max_w * max_h;
     const int tiles = ((max_w + GS2_TILE - 1) / GS2_TILE) * ((max_h + GS2_TILE - 1) / GS2_TILE);
     const int K = c->cfg.knn_k, f = c->cfg.downsample;
@@ -291,6 +292,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         l->max_pairs = max_pairs;
         l->nb_sort = c->nb_sort;
         l->sort_rows = c->sort_rows;
+        l->accum_px = c->accum_px;
         for (int j = 0; j < 2; ++j) {
             A((void **)&l->keys[j], sizeof(uint32_t) * (size_t)max_pairs);
             A((void **)&l->vals[j], sizeof(uint32_t) * (size_t)max_pairs);
@@ -670,6 +672,7 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             l->cfg = ctx->cfg;
             l->nb_sort = ctx->nb_sort;
             l->sort_rows = ctx->sort_rows;
+            l->accum_px = ctx->accum_px;
         }
     }
     if (ctx->cfg.group_jacobi) {

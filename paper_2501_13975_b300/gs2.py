@@ -55,7 +55,12 @@ class Config_(C.Structure):
 
 
 class Tuning_(C.Structure):
-    _fields_ = [("sort_blocks", C.c_int32), ("sort_rows", C.c_int32), ("view_lanes", C.c_int32)]
+    _fields_ = [("sort_blocks", C.c_int32), ("sort_rows", C.c_int32), ("view_lanes", C.c_int32),
+                ("accum_px", C.c_int32)]
+
+
+def _tuning_dict(t) -> dict:
+    return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows, view_lanes=t.view_lanes, accum_px=t.accum_px)
 
 
 class BatchScene_(C.Structure):
@@ -404,13 +409,15 @@ class Context:
     def tuning(self) -> dict:
         t = Tuning_()
         self._ok(_lib.gs2_get_tuning(self.h, C.byref(t)), "gs2_get_tuning")
-        return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows, view_lanes=t.view_lanes)
+        return _tuning_dict(t)
 
-    def set_tuning(self, sort_blocks: int | None = None, sort_rows: int | None = None, view_lanes: int | None = None):
+    def set_tuning(self, sort_blocks: int | None = None, sort_rows: int | None = None, view_lanes: int | None = None,
+                   accum_px: int | None = None):
         cur = self.tuning()
         t = Tuning_(int(cur["sort_blocks"] if sort_blocks is None else sort_blocks),
                     int(cur["sort_rows"] if sort_rows is None else sort_rows),
-                    int(cur["view_lanes"] if view_lanes is None else view_lanes))
+                    int(cur["view_lanes"] if view_lanes is None else view_lanes),
+                    int(cur["accum_px"] if accum_px is None else accum_px))
         self._ok(_lib.gs2_set_tuning(self.h, C.byref(t)), "gs2_set_tuning")
 
     def autotune(self, scene: DeviceScene, cams, targets, knn, t, reps=2, stream=None):
@@ -423,8 +430,7 @@ class Context:
         ms = C.c_float(0.0)
         self._ok(_lib.gs2_autotune(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
                                    int(reps), C.byref(best), C.byref(ms), _stream(stream)), "gs2_autotune")
-        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, view_lanes=best.view_lanes,
-                    ms=float(ms.value))
+        return dict(_tuning_dict(best), ms=float(ms.value))
 
     def profile(self, enable: bool):
         self._ok(_lib.gs2_profile(self.h, 1 if enable else 0), "gs2_profile")
@@ -525,8 +531,8 @@ class Batch:
         if st != 0:
             raise GS2Error(f"gs2_set_config: {STATUS.get(st, st)}")
 
-    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int, view_lanes: int = 1):
-        t = Tuning_(int(sort_blocks), int(sort_rows), int(view_lanes))
+    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int, view_lanes: int = 1, accum_px: int = 2):
+        t = Tuning_(int(sort_blocks), int(sort_rows), int(view_lanes), int(accum_px))
         st = _lib.gs2_set_tuning(self.ctx_handle(i), C.byref(t))
         if st != 0:
             raise GS2Error(f"gs2_set_tuning: {STATUS.get(st, st)}")
@@ -543,8 +549,7 @@ class Batch:
                                int(reps), C.byref(best), C.byref(ms), _stream(stream))
         if st != 0:
             raise GS2Error(f"gs2_autotune: {STATUS.get(st, st)}")
-        return dict(sort_blocks=best.sort_blocks, sort_rows=best.sort_rows, view_lanes=best.view_lanes,
-                    ms=float(ms.value))
+        return dict(_tuning_dict(best), ms=float(ms.value))
 
     def prepare(self, scenes, cams, targets, knn):
         """Marshals the per-scene host arrays once (cameras, target pointers,

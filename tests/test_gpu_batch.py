@@ -130,8 +130,10 @@ def test_autotune_keeps_scene_and_results():
     torch.cuda.synchronize()
     for name in NAMES:
         assert torch.equal(getattr(ds, name), getattr(before, name)), name
-    assert best["sort_blocks"] in (296, 592, 888) and best["sort_rows"] in (2, 4, 8) and best["ms"] > 0
-    assert ctx.tuning() == dict(sort_blocks=best["sort_blocks"], sort_rows=best["sort_rows"], view_lanes=1)
+    assert best["sort_blocks"] in (296, 592, 888) and best["sort_rows"] in (2, 4, 8, 16) and best["ms"] > 0
+    assert best["accum_px"] in (2, 4)
+    assert ctx.tuning() == dict(sort_blocks=best["sort_blocks"], sort_rows=best["sort_rows"], view_lanes=1,
+                                accum_px=best["accum_px"])
     ctx.sweep(ds, s["cams"], targets[2], knns[2], 1)
     ref = gs2.DeviceScene.from_host(s["train"])
     ctx2 = gs2.Context(s["n"], s["w"], s["h"], 3, 64 * s["n"])
@@ -167,6 +169,9 @@ def test_tuning_rejects_bad_values():
             ctx.set_tuning(b, r)
     with pytest.raises(gs2.GS2Error):
         ctx.set_tuning(view_lanes=2)
+    for px in (0, 1, 3, 8):
+        with pytest.raises(gs2.GS2Error):
+            ctx.set_tuning(accum_px=px)
 
 
 def test_concurrent_views_equal_serial_views():

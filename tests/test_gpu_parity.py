@@ -167,9 +167,11 @@ def _colour_full(blocks, n_views, S, n):
     return g, H
 
 
-def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, extra=None):
+def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, extra=None, tuning=None):
     sc, cams = _tiny(n=n, size=size, sh=sh)
     ctx, gcfg, ocfg = _setup(gs2, sc, cams, dict(lambda_ssim=lam, **(extra or {})))
+    if tuning:
+        ctx.set_tuning(**tuning)
     gt = synth.perturbed(sc, seed=2, sd=0.05)
     primary = cams[0]
     view = O.downsample_camera(cams[1], 2) if secondary else primary
@@ -247,6 +249,20 @@ def test_blocks_parity_ragged_tiles(gs2, group):
     some accumulation threads have their first pixel inside and their second
     (four rows below) outside, and some have both outside."""
     r = _blocks_case(gs2, group, sh=(1 if group == O.COLOR else 0), lam=0.2, n=700, size=90)
+    _check_blocks(r)
+
+
+@pytest.mark.parametrize("px", [2, 4])
+@pytest.mark.parametrize("case", [dict(lam=0.0), dict(lam=0.2), dict(lam=0.2, n=700, size=90),
+                                  dict(lam=0.2, sh=3, secondary=True, n=1500, size=96),
+                                  dict(lam=0.2, extra=dict(gauss_newton=1))],
+                         ids=["l2", "ssim", "ragged", "secondary-sh3", "gauss-newton"])
+def test_blocks_parity_position_pixels_per_thread(gs2, case, px):
+    """The position accumulation with two pixels per thread (a warp per 8x8
+    block) and with four (tuning accum_px = 4, the default: two warps per
+    tile, one warp reduction per 128 pixels) against the oracle."""
+    r = _blocks_case(gs2, O.POS, tuning=dict(accum_px=px), **case)
+    assert r["ctx"].tuning()["accum_px"] == px
     _check_blocks(r)
 
 
