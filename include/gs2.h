@@ -490,7 +490,8 @@ gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene *scene, con
 
 /* Introspection for tests: copies the current tile ranges (device uint32
  * [ntiles][2]) and sorted Gaussian ids (device uint32, up to capacity) and
- * returns the pair count (host) after synchronising the stream. */
+ * returns the number of listed pairs (host; the tile lists' total length)
+ * after synchronising the stream. */
 gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32_t *ids_out, int64_t capacity,
                            int64_t *n_pairs_out, gs2_stream stream);
 /* Depth keys (FP32 bit patterns) written by the last gs2_project into proj. */

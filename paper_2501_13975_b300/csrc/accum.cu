@@ -954,13 +954,13 @@ __global__ void __launch_bounds__(128, 6) k_epi_pos(DevScene sc, DevCam cam, con
 // warp per depth rank r (Gaussian order[r]), lane i summing payload entry i
 // (and i + 32), so every partial row is read by one coalesced access; emitted
 // pairs past the pair capacity and box tiles the support ellipse misses
-// (sorted key >= ntiles) hold no entry and are skipped.
+// (dropped by the tile sort: ids_emit = 0xFFFFFFFF) hold no entry and are skipped.
 template <int P, typename ACC>
 __global__ void __launch_bounds__(128) k_det_reduce(const uint32_t *__restrict__ order, const uint32_t *__restrict__ offs,
                                                     const uint32_t *__restrict__ tsort, int n,
                                                     const uint32_t *__restrict__ count,
                                                     const uint32_t *__restrict__ inv,
-                                                    const uint32_t *__restrict__ skeys, uint32_t ntiles,
+                                                    const uint32_t *__restrict__ ids_emit,
                                                     const float *__restrict__ part, ACC *__restrict__ zbuf) {
     constexpr int NE = (P + 31) / 32;   // entries per lane
     const int lane = threadIdx.x & 31;
@@ -978,8 +978,8 @@ __global__ void __launch_bounds__(128) k_det_reduce(const uint32_t *__restrict__
         comp[e] = 0.f;
     }
     for (uint32_t j = j0; j < j1; ++j) {
+        if (ids_emit[j] == 0xFFFFFFFFu) continue;   // dropped pair
         const uint32_t sp = inv[j];
-        if (skeys[sp] >= ntiles) continue;
         const float *row = part + (size_t)sp * P;
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
@@ -1013,7 +1013,6 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
     unsigned long long *act = pc->prof_on ? pc->d_stats + 5 * group + 3 : nullptr;
     const bool det = cfg.deterministic != 0 && ctx->det_part && ctx->det_order;
-    const uint32_t ntiles = (uint32_t)(ctx->tiles_x * ctx->tiles_y);
 #define ACC_LAUNCH(G)                                                                                             \
     do {                                                                                                          \
         if (det) {                                                                                                \
@@ -1022,8 +1021,8 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
                 cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part, ctx->tile_order);       \
             if (n > 0)                                                                                            \
                 k_det_reduce<Payload<G>::P, ACC><<<(n + 3) / 4, 128, 0, st>>>(                                    \
-                    ctx->det_order, pv.offs, pv.tsort, n, ctx->d_count, ctx->det_inv, ctx->keys[ctx->sorted],     \
-                    ntiles, ctx->det_part, zb);                                                                   \
+                    ctx->det_order, pv.offs, pv.tsort, n, ctx->d_count, ctx->det_inv, ctx->det_ids,               \
+                    ctx->det_part, zb);                                                                           \
         } else {                                                                                                  \
             k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h,  \
                                                                view.w, view.h, ctx->tiles_x, cfg.alpha_min,       \

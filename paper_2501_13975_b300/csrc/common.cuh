@@ -38,6 +38,20 @@
 #define GS2_ST_TIMEOUT 4u
 
 static inline int sh_count(int deg) { return (deg + 1) * (deg + 1); }
+
+// Sort state of one binning (uint32 words, zeroed at the start of every
+// binning): the tiles-touched scan's chunk ticket and its look-back states
+// (GS2_SCAN_CHUNKS 64-bit words).
+#define GS2_SS_TICKET 0
+#define GS2_SS_CHUNKS 2               // 8-byte aligned
+#define GS2_SCAN_CHUNKS 256
+#define GS2_SS_WORDS (GS2_SS_CHUNKS + 2 * GS2_SCAN_CHUNKS)
+// bits of the tile-sort keys 0..ntiles (ntiles marks a dropped pair)
+static constexpr int gs2_tile_bits(int64_t ntiles) {
+    int bits = 1;
+    while ((1ll << bits) <= ntiles) ++bits;
+    return bits;
+}
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // --------------------------------------------------------------------------
@@ -150,9 +164,10 @@ struct gs2_ctx {
     // sorting
     uint32_t *keys[2];           // pair keys: tile id
     uint32_t *vals[2];           // pair values: Gaussian id
-    uint32_t *ghist;             // [256][nb_sort]
-    uint32_t *bsum;              // scan block sums
-    uint32_t *d_count;           // [0] clamped pair count, [1] raw count, [2] Gaussian count (depth sort)
+    uint32_t *ghist;             // [256][nb_sort] block histograms of the depth sort
+    uint32_t *sort_state;        // GS2_SS_WORDS: the tiles-touched scan's ticket and chunk states
+    uint32_t *d_count;           // [0] clamped pair count, [1] raw count, [2] Gaussian count (depth sort),
+                                 // [3] listed pairs (the live keys)
     uint2 *ranges;               // [max tiles]
     int sorted;                  // which of keys/vals holds the sorted pairs
     const uint32_t *list_ids;    // Gaussian ids of the sorted tile lists (vals[sorted], or det_list)

@@ -119,7 +119,7 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 
 // a view lane's own scratch (the rest is shared with its owner)
 static void free_lane(gs2_ctx *l) {
-    void *ptrs[] = {l->keys[0], l->keys[1], l->vals[0], l->vals[1], l->ghist, l->bsum, l->d_count, l->ranges,
+    void *ptrs[] = {l->keys[0], l->keys[1], l->vals[0], l->vals[1], l->ghist, l->sort_state, l->d_count, l->ranges,
                     l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image, l->tile_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -135,7 +135,7 @@ static void free_ctx(gs2_ctx *c) {
     }
     for (int i = 0; i <= c->n_lanes && i <= GS2_MAX_LANES; ++i)
         if (c->lane_ev[i]) cudaEventDestroy(c->lane_ev[i]);
-    void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->bsum, c->d_count, c->ranges,
+    void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->sort_state, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->d_resolves, c->flags, c->g_prim, c->lg_phi,
                     c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list, c->tile_order};
@@ -243,7 +243,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
         A((void **)&c->vals[i], sizeof(uint32_t) * (size_t)max_pairs);
     }
     A((void **)&c->ghist, sizeof(uint32_t) * (256 * (size_t)GS2_SORT_BLOCKS_MAX + 256));  // + digit totals
-    A((void **)&c->bsum, sizeof(unsigned long long) * 1024);
+    A((void **)&c->sort_state, sizeof(uint32_t) * GS2_SS_WORDS);
     A((void **)&c->d_count, sizeof(uint32_t) * 4);
     A((void **)&c->ranges, sizeof(uint2) * (size_t)tiles);
     A((void **)&c->tile_order, sizeof(uint32_t) * (size_t)tiles);
@@ -298,7 +298,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
             A((void **)&l->vals[j], sizeof(uint32_t) * (size_t)max_pairs);
         }
         A((void **)&l->ghist, sizeof(uint32_t) * (256 * (size_t)GS2_SORT_BLOCKS_MAX + 256));
-        A((void **)&l->bsum, sizeof(unsigned long long) * 1024);
+        A((void **)&l->sort_state, sizeof(uint32_t) * GS2_SS_WORDS);
         A((void **)&l->d_count, sizeof(uint32_t) * 4);
         A((void **)&l->ranges, sizeof(uint2) * (size_t)tiles);
         A((void **)&l->tile_order, sizeof(uint32_t) * (size_t)tiles);
@@ -975,13 +975,13 @@ extern "C" gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32
                                       int64_t *n_pairs_out, gs2_stream stream) {
     if (!ctx || !ranges_out || !ids_out || !n_pairs_out) return GS2_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t cnt[2];
+    uint32_t cnt[4];
     RET_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     RET_CUDA(ctx, cudaStreamSynchronize(st));
-    *n_pairs_out = cnt[0];
+    *n_pairs_out = cnt[3];   // the listed pairs
     const size_t ntiles = (size_t)ctx->tiles_x * ctx->tiles_y;
     RET_CUDA(ctx, cudaMemcpyAsync(ranges_out, ctx->ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToDevice, st));
-    const size_t m = std::min<size_t>(cnt[0], (size_t)std::max<int64_t>(capacity, 0));
+    const size_t m = std::min<size_t>(cnt[3], (size_t)std::max<int64_t>(capacity, 0));
     if (m) RET_CUDA(ctx, cudaMemcpyAsync(ids_out, ctx->list_ids, sizeof(uint32_t) * m,
                                          cudaMemcpyDeviceToDevice, st));
     return GS2_OK;

@@ -25,20 +25,21 @@
 #define NA_KEYS_BYTES (4ull * GS2_NOALLOC_MAX_PAIRS)
 #define NA_VALS_BYTES (4ull * GS2_NOALLOC_MAX_PAIRS)
 #define NA_GHIST_BYTES (4ull * (256 * NA_SORT_BLOCKS + 256))
-#define NA_BSUM_BYTES (8ull * 1024)
+#define NA_SS_BYTES (8ull * 1024)   // the tiles-touched scan's state (GS2_SS_WORDS words)
 #define NA_RANGES_BYTES (8ull * GS2_NOALLOC_MAX_TILES)
 #define NA_OFF_KEYS0 0ull
 #define NA_OFF_KEYS1 (NA_OFF_KEYS0 + NA_KEYS_BYTES)
 #define NA_OFF_VALS0 (NA_OFF_KEYS1 + NA_KEYS_BYTES)
 #define NA_OFF_VALS1 (NA_OFF_VALS0 + NA_VALS_BYTES)
 #define NA_OFF_GHIST (NA_OFF_VALS1 + NA_VALS_BYTES)
-#define NA_OFF_BSUM (NA_OFF_GHIST + NA_GHIST_BYTES)
-#define NA_OFF_RANGES (NA_OFF_BSUM + NA_BSUM_BYTES)
+#define NA_OFF_SS (NA_OFF_GHIST + NA_GHIST_BYTES)
+#define NA_OFF_RANGES (NA_OFF_SS + NA_SS_BYTES)
 #define NA_OFF_COUNT (NA_OFF_RANGES + NA_RANGES_BYTES)
 #define NA_OFF_STATUS (NA_OFF_COUNT + 256ull)
 #define NA_TOTAL (NA_OFF_STATUS + 256ull)
 
 static_assert(NA_TOTAL == GS2_NOALLOC_SCRATCH_BYTES, "scratch size in gs2.h must match the carve-up");
+static_assert(4ull * GS2_SS_WORDS <= NA_SS_BYTES, "scan state fits its slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GS2_NOALLOC_SCRATCH_BYTES];
 
@@ -97,7 +98,7 @@ extern "C" gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene 
     v.vals[0] = (uint32_t *)(base + NA_OFF_VALS0);
     v.vals[1] = (uint32_t *)(base + NA_OFF_VALS1);
     v.ghist = (uint32_t *)(base + NA_OFF_GHIST);
-    v.bsum = (uint32_t *)(base + NA_OFF_BSUM);
+    v.sort_state = (uint32_t *)(base + NA_OFF_SS);
     v.ranges = (uint2 *)(base + NA_OFF_RANGES);
     v.d_count = (uint32_t *)(base + NA_OFF_COUNT);
     v.d_status = (uint32_t *)(base + NA_OFF_STATUS);

@@ -4,80 +4,175 @@
 //  1. depth   stable LSD radix sort of the Gaussians by FP32 depth bits (4
 //             passes over n; Gaussians that touch no tile get the largest key
 //             and sort last) -> rank order (key, index);
-//  2. scan    exclusive prefix sum of tiles-touched in rank order (3 kernels,
-//             fixed grid); total pair count M on the device, clamped to the
-//             context capacity (overflow sets a status bit);
-//  3. emit    pairs (tile id, Gaussian id) in rank order, one CTA per 256 ranks;
-//  4. tiles   stable LSD radix sort of the pairs by tile id (ceil(tile bits/8)
-//             passes of equal width, 2 of 7 and 6 bits at 1600x1040) --
+//  2. scan    exclusive prefix sum of tiles-touched in rank order, one kernel
+//             (decoupled look-back over chunks of ranks); total pair count M
+//             on the device, clamped to the context capacity (overflow sets a
+//             status bit);
+//  3. emit    pairs (tile id, Gaussian id) in rank order, one CTA per 256
+//             ranks; a tile of a Gaussian's rectangle that its support
+//             ellipse misses gets the key ntiles (a dropped pair);
+//  4. tiles   stable LSD radix sort of the live pairs by tile id
+//             (ceil(tile bits / 8) passes of equal width, 2 of 7 and 6 bits at
+//             1600x1040); the first pass drops the dead pairs (neither counted
+//             nor written), so the second sorts the listed pairs only --
 //             stability keeps rank order per tile;
 //  5. ranges  [start, end) of every tile in the sorted list.
 // Result: total order (tile, depth key, Gaussian index), bit-exact.  Each
 // radix pass = block histograms over a fixed grid of NB CTAs (each owning a
 // contiguous chunk), a per-digit scan, and a stable scatter; element counts
-// live on the device, so no host synchronisation sizes anything.
+// live on the device, so no host synchronisation sizes anything.  The scan's
+// wait on an earlier chunk's look-back word is bounded: past the limit it sets
+// GS2_ST_TIMEOUT and goes on (the result is then wrong but every access stays
+// in bounds); with chunks claimed in order the wait cannot block, since a
+// claimed chunk publishes its sum before it waits.
+// (Measured and not kept: the same one-kernel look-back pass for every radix
+// pass, fed with digit counts gathered by the emission -- 2x slower per pass,
+// each 1024-key tile exposing its load and a look-back chain.)
 #include "common.cuh"
 
-#define SCAN_BLOCKS 1024
 #define SORT_THREADS 256
 
+// ---------------------------------------------------------------- look-back words
+// 64-bit words written and read whole (single-copy atomic): a flag (the
+// aggregate of one unit, or the inclusive prefix up to it) and a value.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+#define LB_SPIN_LIMIT (1u << 22)   // polls of one look-back word before giving up (seconds)
+
 // ---------------------------------------------------------------- scan
-__global__ void k_scan_reduce(const uint32_t *__restrict__ x, int n, unsigned long long *bsum) {
-    __shared__ unsigned long long s[256];
-    const int chunk = (n + SCAN_BLOCKS - 1) / SCAN_BLOCKS;
-    const int beg = blockIdx.x * chunk, end = min(beg + chunk, n);
-    unsigned long long acc = 0;
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) acc += x[i];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
+// Exclusive prefix sum of tiles-touched in rank order, in one pass: chunk c
+// (claimed in order by ticket) of `chunk` consecutive ranks gathers touched
+// in rank order into tsort, publishes its sum, adds the sums of the earlier
+// chunks (look-back until an inclusive prefix), publishes its own inclusive
+// prefix, and writes its offsets (clamped to cap).  The last chunk writes the
+// pair count.  States: GS2_SCAN_CHUNKS 64-bit words (bits 63..62: 1 sum, 2
+// inclusive prefix), zero at the start, as is the chunk ticket.
+#define TS_THREADS 256
+#define TS_ITEMS 16
+#define TS_ROUND (TS_THREADS * TS_ITEMS)
+#define TS_PAD(j) ((j) + ((j) >> 5))
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v, unsigned long long *swarp,
+                                                                unsigned long long &total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
     }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = s[0];
+    if (lane == 31) swarp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long z = lane < (TS_THREADS >> 5) ? swarp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < (TS_THREADS >> 5)) swarp[lane] = z;
+    }
+    __syncthreads();
+    total = swarp[(TS_THREADS >> 5) - 1];
+    const unsigned long long before = (w > 0) ? swarp[w - 1] : 0ull;
+    __syncthreads();
+    return before + x - v;
 }
 
-__global__ void k_scan_blocks(unsigned long long *bsum, uint32_t *count, uint32_t cap, uint32_t *status) {
-    __shared__ unsigned long long s[SCAN_BLOCKS];
+__global__ void __launch_bounds__(TS_THREADS) k_touch_scan(ProjView pv, const uint32_t *__restrict__ order, int n,
+                                                           int chunk, uint32_t cap, uint32_t *count,
+                                                           uint32_t *status, uint32_t *ss) {
+    __shared__ uint32_t s_v[TS_PAD(TS_ROUND)];
+    __shared__ unsigned long long swarp[TS_THREADS / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_c;
     const int t = threadIdx.x;
-    s[t] = bsum[t];
+    unsigned long long *state = reinterpret_cast<unsigned long long *>(ss + GS2_SS_CHUNKS);
+    if (t == 0) s_c = atomicAdd(&ss[GS2_SS_TICKET], 1u);
     __syncthreads();
-    for (int off = 1; off < SCAN_BLOCKS; off <<= 1) {
-        unsigned long long v = (t >= off) ? s[t - off] : 0ull;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
+    const int c = (int)s_c;
+    const int beg = c * chunk, end = min(n, beg + chunk);
+    // the chunk's sum, gathering tsort on the way (coalesced writes)
+    unsigned long long acc = 0;
+    for (int r = beg + t; r < end; r += TS_THREADS) {
+        const uint32_t v = pv.touched[order[r]];
+        pv.tsort[r] = v;
+        acc += v;
     }
-    const unsigned long long incl = s[t];
-    bsum[t] = incl - bsum[t];  // exclusive
-    if (t == SCAN_BLOCKS - 1) {
-        const unsigned long long total = incl;
+    unsigned long long agg;
+    block_excl_scan64(acc, swarp, agg);
+    if (t == 0) {
+        unsigned long long excl = 0;
+        if (c == 0) {
+            st_relaxed_u64(&state[0], (2ull << 62) | agg);
+        } else {
+            st_relaxed_u64(&state[c], (1ull << 62) | agg);
+            int j = c - 1;
+            uint32_t spins = 0;
+            for (;;) {
+                const unsigned long long w = ld_relaxed_u64(&state[j]);
+                const unsigned long long flag = w >> 62;
+                if (flag == 0) {
+                    if (++spins > LB_SPIN_LIMIT) {
+                        atomicOr(status, GS2_ST_TIMEOUT);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(64);
+                    continue;
+                }
+                excl += w & ((1ull << 62) - 1);
+                if (flag == 2) break;
+                --j;
+                spins = 0;
+            }
+            st_relaxed_u64(&state[c], (2ull << 62) | (excl + agg));
+        }
+        s_base = excl;
+    }
+    __syncthreads();
+    // offsets: rounds of TS_ROUND ranks, read back coalesced, transposed so
+    // that each thread scans TS_ITEMS consecutive ranks
+    unsigned long long base = s_base;
+    for (int r0 = beg; r0 < end; r0 += TS_ROUND) {
+#pragma unroll
+        for (int i = 0; i < TS_ITEMS; ++i) {
+            const int j = i * TS_THREADS + t;
+            s_v[TS_PAD(j)] = (r0 + j < end) ? pv.tsort[r0 + j] : 0u;
+        }
+        __syncthreads();
+        uint32_t x[TS_ITEMS];
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int i = 0; i < TS_ITEMS; ++i) {
+            x[i] = s_v[TS_PAD(t * TS_ITEMS + i)];
+            sum += x[i];
+        }
+        unsigned long long tot;
+        unsigned long long run = base + block_excl_scan64(sum, swarp, tot);
+#pragma unroll
+        for (int i = 0; i < TS_ITEMS; ++i) {
+            s_v[TS_PAD(t * TS_ITEMS + i)] = (uint32_t)min(run, (unsigned long long)cap);
+            run += x[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < TS_ITEMS; ++i) {
+            const int j = i * TS_THREADS + t;
+            if (r0 + j < end) pv.offs[r0 + j] = s_v[TS_PAD(j)];
+        }
+        __syncthreads();
+        base += tot;
+    }
+    if (end == n && t == 0) {   // the last chunk: the pair count
+        const unsigned long long total = base;
         count[1] = (uint32_t)min(total, (unsigned long long)0xFFFFFFFFull);
         count[0] = (uint32_t)min(total, (unsigned long long)cap);
         if (total > cap) atomicOr(status, GS2_ST_CAPACITY);
-    }
-}
-
-__global__ void k_scan_down(const uint32_t *__restrict__ x, int n, const unsigned long long *bsum, uint32_t cap,
-                            uint32_t *offs) {
-    __shared__ unsigned long long s[256];
-    const int chunk = (n + SCAN_BLOCKS - 1) / SCAN_BLOCKS;
-    const int beg = blockIdx.x * chunk, end = min(beg + chunk, n);
-    unsigned long long base = bsum[blockIdx.x];
-    for (int b0 = beg; b0 < end; b0 += 256) {
-        const int i = b0 + threadIdx.x;
-        const unsigned long long v = (i < end) ? x[i] : 0ull;
-        s[threadIdx.x] = v;
-        __syncthreads();
-        for (int off = 1; off < 256; off <<= 1) {
-            unsigned long long a = (threadIdx.x >= off) ? s[threadIdx.x - off] : 0ull;
-            __syncthreads();
-            s[threadIdx.x] += a;
-            __syncthreads();
-        }
-        if (i < end) offs[i] = (uint32_t)min(base + s[threadIdx.x] - v, (unsigned long long)cap);
-        base += s[255];
-        __syncthreads();
     }
 }
 
@@ -96,13 +191,6 @@ __global__ void k_depth_keys(ProjView pv, int n, uint32_t *count_slot) {
     pv.dv[0][k] = (uint32_t)k;
 }
 
-// tiles-touched in rank order
-__global__ void k_gather_touched(ProjView pv, const uint32_t *__restrict__ order, int n) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    pv.tsort[r] = pv.touched[order[r]];
-}
-
 // ---------------------------------------------------------------- emit
 // One CTA per 256 consecutive ranks: their pairs (one per tile of each
 // Gaussian's rectangle) occupy one contiguous output range, which the CTA
@@ -115,8 +203,9 @@ __global__ void k_gather_touched(ProjView pv, const uint32_t *__restrict__ order
 // support_reaches of decide.cuh, so the lists are a function of the FP32
 // parameters and camera alone, bit for bit.
 // ids_emit (deterministic mode, else NULL): the pair's value is its emission
-// index j and its Gaussian id goes to ids_emit[j], so that after the tile sort
-// every pair's sorted position can be mapped back to its emission slot.
+// index j and its Gaussian id goes to ids_emit[j] (0xFFFFFFFF for a dropped
+// pair), so that after the tile sort every pair's sorted position can be
+// mapped back to its emission slot.
 __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__restrict__ order, int n, int tiles_x,
                                               uint32_t ntiles, uint32_t cap, uint32_t *keys, uint32_t *vals,
                                               unsigned long long *stats, uint32_t *__restrict__ ids_emit) {
@@ -136,7 +225,7 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
     }
     const uint32_t off = (r < n) ? pv.offs[r] : 0u;
     s_off[t] = (r < n) ? off : 0xFFFFFFFFu;
-    s_rect[t] = (r < n) ? pv.rect[id] : make_uint2(0u, 0u);
+    s_rect[t] = (cnt != 0u) ? pv.rect[id] : make_uint2(0u, 0u);   // only ranks with pairs are looked up
     s_id[t] = id;
     if (cnt != 0u) {
         const float4 A = pv.recA[id];
@@ -171,12 +260,12 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
             rem -= (int)wdt;
         }
         const uint32_t tx = tx0 + (uint32_t)rem, ty = ty0 + row;
-        keys[j] = support_reaches(s_sr[lo], (float)(tx * GS2_TILE), (float)(ty * GS2_TILE), (float)GS2_TILE)
-                      ? ty * (uint32_t)tiles_x + tx
-                      : ntiles;
+        const bool live =
+            support_reaches(s_sr[lo], (float)(tx * GS2_TILE), (float)(ty * GS2_TILE), (float)GS2_TILE);
+        keys[j] = live ? ty * (uint32_t)tiles_x + tx : ntiles;
         if (ids_emit) {
             vals[j] = j;
-            ids_emit[j] = s_id[lo];
+            ids_emit[j] = live ? s_id[lo] : 0xFFFFFFFFu;
         } else {
             vals[j] = s_id[lo];
         }
@@ -184,10 +273,12 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
 }
 
 // Deterministic mode, after the tile sort (values = emission indices):
-// list[s] = Gaussian id of sorted pair s, inv[j] = sorted position of emitted pair j.
+// list[s] = Gaussian id of sorted pair s, inv[j] = sorted position of emitted
+// pair j (dropped pairs have no sorted position: ids_emit[j] = 0xFFFFFFFF
+// marks them).  count[3]: the listed pairs.
 __global__ void k_det_gather(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ids_emit,
                              const uint32_t *count, uint32_t *__restrict__ list, uint32_t *__restrict__ inv) {
-    const uint32_t M = count[0];
+    const uint32_t M = count[3];
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < M; s += gridDim.x * blockDim.x) {
         const uint32_t j = sorted_vals[s];
         list[s] = ids_emit[j];
@@ -203,14 +294,19 @@ __device__ __forceinline__ void chunk_of(uint32_t M, int nb, int b, uint32_t &be
     end = (uint32_t)min(bb + chunk, (unsigned long long)M);
 }
 
+// keys >= dead_from (dropped pairs) are not counted
 __global__ void __launch_bounds__(SORT_THREADS) k_hist(const uint32_t *__restrict__ keys, const uint32_t *count,
-                                                       int shift, uint32_t mask, uint32_t *ghist, int nb) {
+                                                       int shift, uint32_t mask, uint32_t *ghist, int nb,
+                                                       uint32_t dead_from) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0u;
     __syncthreads();
     uint32_t beg, end;
     chunk_of(*count, nb, blockIdx.x, beg, end);
-    for (uint32_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    for (uint32_t i = beg + threadIdx.x; i < end; i += SORT_THREADS) {
+        const uint32_t k = keys[i];
+        if (k < dead_from) atomicAdd(&h[(k >> shift) & mask], 1u);
+    }
     __syncthreads();
     ghist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
@@ -255,13 +351,17 @@ __global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *ghist, int nb, ui
     if (t == 0) dtot[d] = tot;
 }
 
-// ROWS keys per thread per 256-thread round (a tuning parameter: 2, 4, 8 or 16)
+// ROWS keys per thread per 256-thread round (a tuning parameter: 2, 4, 8 or 16).
+// Keys >= dead_from (dropped pairs) are neither ranked nor written;
+// count_live (or NULL) receives the number of the others, the element count
+// of the following passes.
 template <int ROWS>
 __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ vin,
                                                           uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                           const uint32_t *count, int shift, uint32_t mask,
-                                                          const uint32_t *ghist, int nb, const uint32_t *dtot) {
+                                                          const uint32_t *ghist, int nb, const uint32_t *dtot,
+                                                          uint32_t dead_from, uint32_t *count_live) {
     constexpr int SORT_TILE = SORT_THREADS * ROWS;
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[SORT_THREADS / 32][256];
@@ -275,6 +375,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
         uint32_t tot;
         const uint32_t base = block_excl_scan(dtot[t], swarp, tot);
         s_off[t] = base + ghist[t * nb + blockIdx.x];
+        if (count_live && blockIdx.x == 0 && t == 0) *count_live = tot;
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
     // the next tile's keys and values are loaded while this one is ranked and written
@@ -302,7 +403,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             const uint32_t idx = base + (uint32_t)(w * (32 * ROWS) + r * 32 + lane);
-            const bool valid = idx < end;
+            const bool valid = idx < end && key[r] < dead_from;
             dig[r] = valid ? ((key[r] >> shift) & mask) : 256u;
             // lanes with the same digit value (256 marks a slot past the end)
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[r]);
@@ -352,9 +453,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(const uint32_t *__rest
 // returns the index of the buffer holding the result.  The passes split the
 // bits evenly (13 tile bits: 7 + 6, not 8 + 5): a digit of fewer values
 // leaves longer runs of equal digits in each radix tile, so the scatter's
-// stores cover fewer memory segments.
+// stores cover fewer memory segments.  Keys >= dead_from are dropped by the
+// first pass, which writes the number of the others to count_live (the count
+// of the later passes); count_live = NULL: count for every pass.
 static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int bits, uint32_t *ghist, int nb,
-                      int rows, cudaStream_t st, int *launches) {
+                      int rows, cudaStream_t st, int *launches, uint32_t dead_from = 0xFFFFFFFFu,
+                      uint32_t *count_live = nullptr) {
     uint32_t *dtot = ghist + 256 * nb;
     int cur = 0;
     const int passes = (bits + 7) / 8;
@@ -362,20 +466,19 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
     const uint32_t mask = (1u << width) - 1u;
     for (int p = 0; p < passes; ++p) {
         const int shift = width * p;
-        k_hist<<<nb, SORT_THREADS, 0, st>>>(k[cur], count, shift, mask, ghist, nb);
+        const uint32_t *cnt = (p > 0 && count_live) ? count_live : count;
+        const uint32_t dead = p == 0 ? dead_from : 0xFFFFFFFFu;
+        uint32_t *live = p == 0 ? count_live : nullptr;
+        k_hist<<<nb, SORT_THREADS, 0, st>>>(k[cur], cnt, shift, mask, ghist, nb, dead);
         k_digit_scan<<<256, 1024, 0, st>>>(ghist, nb, dtot);
-        if (rows == 2)
-            k_scatter<2><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
-                                                      ghist, nb, dtot);
-        else if (rows == 8)
-            k_scatter<8><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
-                                                      ghist, nb, dtot);
-        else if (rows == 16)
-            k_scatter<16><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
-                                                       ghist, nb, dtot);
-        else
-            k_scatter<4><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], count, shift, mask,
-                                                      ghist, nb, dtot);
+#define GS2_SCATTER(R)                                                                                            \
+    k_scatter<R><<<nb, SORT_THREADS, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], cnt, shift, mask, ghist, nb,  \
+                                              dtot, dead, live)
+        if (rows == 2) GS2_SCATTER(2);
+        else if (rows == 8) GS2_SCATTER(8);
+        else if (rows == 16) GS2_SCATTER(16);
+        else GS2_SCATTER(4);
+#undef GS2_SCATTER
         cur ^= 1;
     }
     *launches += 3 * passes;
@@ -383,13 +486,14 @@ static int radix_sort(uint32_t *k[2], uint32_t *v[2], const uint32_t *count, int
 }
 
 // [start, end) of every tile: each thread checks four consecutive sorted keys
-// (one 16-byte load when aligned) against their successors; keys >= ntiles
-// (tiles of a rectangle that the support ellipse misses) are not tiles and are skipped
+// (one 16-byte load when aligned) against their successors.  count[3]: the
+// listed pairs (the tile sort dropped the pairs whose tile the support
+// ellipse misses); count[0]: the emitted pairs (statistics).
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *count, uint2 *ranges, uint32_t ntiles,
                          unsigned long long *stats) {
-    const uint32_t M = count[0];
+    const uint32_t M = count[3];
     if (stats && blockIdx.x == 0 && threadIdx.x == 0) {   // atomic: concurrent views share the counters
-        atomicAdd(&stats[0], (unsigned long long)M);
+        atomicAdd(&stats[0], (unsigned long long)count[0]);
         atomicAdd(&stats[2], 1ull);
     }
     // listed pairs: the end of the last tile (pairs past it are not tiles)
@@ -469,8 +573,11 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
             k_tile_order<<<1, 1024, 0, st>>>(ctx->ranges, ntiles, ctx->tile_order);
             GS2_COUNT_LAUNCH(1);
         }
-        return cudaMemsetAsync(ctx->d_count, 0, sizeof(uint32_t) * 2, st);
+        return cudaMemsetAsync(ctx->d_count, 0, sizeof(uint32_t) * 4, st);
     }
+    // the scan's chunk ticket and look-back states start at zero
+    e = cudaMemsetAsync(ctx->sort_state, 0, sizeof(uint32_t) * GS2_SS_WORDS, st);
+    if (e != cudaSuccess) return e;
     // 1. depth order of the Gaussians (or the caller's copy of it for the same
     //    means and camera)
     const uint32_t *order = order_in;
@@ -486,19 +593,15 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
         }
     }
     // 2. tiles-touched in rank order, exclusive scan -> pair offsets and the pair count
-    k_gather_touched<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n);
-    unsigned long long *bsum = (unsigned long long *)ctx->bsum;
-    k_scan_reduce<<<SCAN_BLOCKS, 256, 0, st>>>(pv.tsort, n, bsum);
-    k_scan_blocks<<<1, SCAN_BLOCKS, 0, st>>>(bsum, ctx->d_count, cap, ctx->d_status);
-    k_scan_down<<<SCAN_BLOCKS, 256, 0, st>>>(pv.tsort, n, bsum, cap, pv.offs);
+    const int chunk = ((n + GS2_SCAN_CHUNKS - 1) / GS2_SCAN_CHUNKS + TS_ROUND - 1) / TS_ROUND * TS_ROUND;
+    k_touch_scan<<<(n + chunk - 1) / chunk, TS_THREADS, 0, st>>>(pv, order, n, chunk, cap, ctx->d_count,
+                                                                 ctx->d_status, ctx->sort_state);
     // 3. pairs in rank order
     k_emit<<<(n + 255) / 256, 256, 0, st>>>(pv, order, n, tiles_x, (uint32_t)ntiles, cap, ctx->keys[0],
                                             ctx->vals[0], stats, det ? ctx->det_ids : nullptr);
-    // 4. stable sort by tile id (keys 0..ntiles: one more value than there are tiles)
-    int tile_bits = 1;
-    while ((1 << tile_bits) <= ntiles) ++tile_bits;
-    ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, tile_bits, ctx->ghist, nb, ctx->sort_rows, st,
-                             &launches);
+    // 4. stable sort of the live pairs by tile id (keys 0..ntiles - 1; ntiles: dropped by the first pass)
+    ctx->sorted = radix_sort(ctx->keys, ctx->vals, ctx->d_count, gs2_tile_bits(ntiles), ctx->ghist, nb,
+                             ctx->sort_rows, st, &launches, (uint32_t)ntiles, ctx->d_count + 3);
     ctx->list_ids = ctx->vals[ctx->sorted];
     ctx->det_order = order;
     if (det) {
@@ -514,6 +617,6 @@ cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int t
         k_tile_order<<<1, 1024, 0, st>>>(ctx->ranges, ntiles, ctx->tile_order);
         ++launches;
     }
-    GS2_COUNT_LAUNCH(launches + 7);
+    GS2_COUNT_LAUNCH(launches + 3);
     return cudaGetLastError();
 }
