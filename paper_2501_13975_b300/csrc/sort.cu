@@ -49,9 +49,9 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
 // Exclusive prefix sum of tiles-touched in rank order, in one pass: chunk c
 // (claimed in order by ticket) of `chunk` consecutive ranks gathers touched
 // in rank order into tsort, publishes its sum, adds the sums of the earlier
-// chunks (look-back until an inclusive prefix), publishes its own inclusive
-// prefix, and writes its offsets (clamped to cap).  The last chunk writes the
-// pair count.  States: GS2_SCAN_CHUNKS 64-bit words (bits 63..62: 1 sum, 2
+// chunks (look-back until an inclusive prefix, one warp reading 32 chunks at
+// a time), publishes its own inclusive prefix, and writes its offsets
+// (clamped to cap).  The last chunk writes the pair count.  States: GS2_SCAN_CHUNKS 64-bit words (bits 63..62: 1 sum, 2
 // inclusive prefix), zero at the start, as is the chunk ticket.
 #define TS_THREADS 256
 #define TS_ITEMS 16
@@ -106,33 +106,42 @@ __global__ void __launch_bounds__(TS_THREADS) k_touch_scan(ProjView pv, const ui
     }
     unsigned long long agg;
     block_excl_scan64(acc, swarp, agg);
-    if (t == 0) {
+    // warp 0 looks back over the earlier chunks, 32 at a time (lane i reads
+    // chunk j0 - i; a chunk before 0 reads as an inclusive prefix of 0)
+    if (t < 32) {
         unsigned long long excl = 0;
         if (c == 0) {
-            st_relaxed_u64(&state[0], (2ull << 62) | agg);
+            if (t == 0) st_relaxed_u64(&state[0], (2ull << 62) | agg);
         } else {
-            st_relaxed_u64(&state[c], (1ull << 62) | agg);
-            int j = c - 1;
+            if (t == 0) st_relaxed_u64(&state[c], (1ull << 62) | agg);
+            int j0 = c - 1;
             uint32_t spins = 0;
             for (;;) {
-                const unsigned long long w = ld_relaxed_u64(&state[j]);
-                const unsigned long long flag = w >> 62;
-                if (flag == 0) {
+                const int j = j0 - t;
+                const unsigned long long v = j >= 0 ? ld_relaxed_u64(&state[j]) : (2ull << 62);
+                const uint32_t flag = (uint32_t)(v >> 62);
+                const uint32_t pre = __ballot_sync(0xFFFFFFFFu, flag == 2u);
+                const int lim = pre ? __ffs(pre) - 1 : 31;   // lanes 0..lim are needed
+                const uint32_t need = lim == 31 ? 0xFFFFFFFFu : ((2u << lim) - 1u);
+                if (__ballot_sync(0xFFFFFFFFu, flag == 0u) & need) {   // some not published yet
                     if (++spins > LB_SPIN_LIMIT) {
-                        atomicOr(status, GS2_ST_TIMEOUT);
+                        if (t == 0) atomicOr(status, GS2_ST_TIMEOUT);
                         break;
                     }
                     if (spins > 32) __nanosleep(64);
                     continue;
                 }
-                excl += w & ((1ull << 62) - 1);
-                if (flag == 2) break;
-                --j;
+                unsigned long long part = t <= lim ? (v & ((1ull << 62) - 1)) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+                excl += part;
+                if (pre) break;
+                j0 -= 32;
                 spins = 0;
             }
-            st_relaxed_u64(&state[c], (2ull << 62) | (excl + agg));
+            if (t == 0) st_relaxed_u64(&state[c], (2ull << 62) | (excl + agg));
         }
-        s_base = excl;
+        if (t == 0) s_base = excl;
     }
     __syncthreads();
     // offsets: rounds of TS_ROUND ranks, read back coalesced, transposed so
