@@ -430,11 +430,13 @@ def run_gpu(args, rank, world, local_rank):
     pixels = float(prof["pixels"].sum())
     depth_sorts = float(binn[0] + binn[1])   # the position and rotation passes sort by depth
     stage_bytes = {
-        # emit 8 B, two tile radix passes (4 B histogram read + 8 B read + 8 B written), ranges 4 B per
-        # sorted pair; four depth radix passes of 20 B per Gaussian; tiles-touched gather and offsets
-        # 12 B per Gaussian; the support ellipse's parameters read by the emission, 24 B per visible one
-        "binning": pairs * (8 + 2 * 20 + 4) + depth_sorts * w["n"] * 4 * 20 + float(binn.sum()) * w["n"] * 12
-                   + visible * 24,
+        # per emitted pair: emit 8 B, first tile radix pass 4 B histogram read + 8 B read; per listed
+        # pair (the first pass drops the others): its 8 B write, the second pass 20 B, ranges 4 B;
+        # four depth radix passes of 20 B per Gaussian; the tiles-touched scan 16 B per Gaussian
+        # (order and touched read, tsort and offsets written); the support ellipse's parameters
+        # read by the emission, 24 B per visible one
+        "binning": pairs * (8 + 12) + listed * (8 + 20 + 4) + depth_sorts * w["n"] * 4 * 20
+                   + float(binn.sum()) * w["n"] * 16 + visible * 24,
         # per pixel 12 B image + 8 B state written; per listed pair 4 B id + 48 B staged record
         "compositing": pixels * 20 + listed * 52,
         # per pixel c, target read (24 B), e, h written (24 B)
@@ -1094,7 +1096,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v10"
+KERNEL_REV = "accum-v11"
 
 
 def main():
