@@ -494,6 +494,14 @@ gs2_status gs2_render_noalloc(const gs2_config *cfg, const gs2_scene *scene, con
  * after synchronising the stream. */
 gs2_status gs2_debug_tiles(gs2_ctx *ctx, uint32_t *ranges_out, uint32_t *ids_out, int64_t capacity,
                            int64_t *n_pairs_out, gs2_stream stream);
+/* Test of the device-side bounded wait (fault-free failure detection): the
+ * look-back wait of the tiles-touched scan (one warp; Sec. 3 binning) is run
+ * from chunk `chunk` (1..255) over look-back states that no chunk publishes
+ * (the context's scan state, cleared on `stream` first).  After `limit` polls
+ * (1..2^20; the scan itself allows 2^20, about a second) it gives up and sets
+ * the status bit that gs2_check reports as GS2_ERR_TIMEOUT; the context stays
+ * usable.  Asynchronous on `stream`. */
+gs2_status gs2_debug_lookback_timeout(gs2_ctx *ctx, int32_t chunk, uint32_t limit, gs2_stream stream);
 /* Depth keys (FP32 bit patterns) written by the last gs2_project into proj. */
 gs2_status gs2_debug_keys(const void *proj, int64_t n, uint32_t *keys_out, gs2_stream stream);
 /* Unpacks proj into planar FP32 [GS2_DEBUG_PROJ_ROWS][n]: pix_x pix_y conic_xx

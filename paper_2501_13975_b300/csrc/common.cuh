@@ -242,6 +242,7 @@ cudaError_t launch_project(const DevScene &sc, const DevCam &cam, const gs2_conf
                            int tiles_y, cudaStream_t st, uint32_t *status);
 // order_in: a depth order of the same means and camera to reuse (skips the
 // depth sort); order_out: where to keep the computed one (both may be NULL)
+cudaError_t launch_debug_lookback(gs2_ctx *ctx, int c, uint32_t limit, cudaStream_t st);
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,
                             unsigned long long *stats, const uint32_t *order_in = nullptr,
                             uint32_t *order_out = nullptr);

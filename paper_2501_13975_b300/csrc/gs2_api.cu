@@ -962,6 +962,12 @@ extern "C" gs2_status gs2_debug_proj(const void *proj, int64_t n, float *out, gs
     return cudaGetLastError() == cudaSuccess ? GS2_OK : GS2_ERR_CUDA;
 }
 
+extern "C" gs2_status gs2_debug_lookback_timeout(gs2_ctx *ctx, int32_t chunk, uint32_t limit, gs2_stream stream) {
+    if (!ctx || chunk < 1 || chunk >= GS2_SCAN_CHUNKS || limit < 1 || limit > (1u << 20)) return GS2_ERR_ARG;
+    RET_CUDA(ctx, launch_debug_lookback(ctx, chunk, limit, (cudaStream_t)stream));
+    return GS2_OK;
+}
+
 extern "C" gs2_status gs2_debug_keys(const void *proj, int64_t n, uint32_t *keys_out, gs2_stream stream) {
     if (!proj || !keys_out || n < 0) return GS2_ERR_ARG;
     ProjView pv = proj_view(const_cast<void *>(proj), n);

@@ -43,7 +43,42 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-#define LB_SPIN_LIMIT (1u << 22)   // polls of one look-back word before giving up (seconds)
+#define LB_SPIN_LIMIT (1u << 20)   // polls of one look-back window before giving up (about a second)
+
+// Look-back of chunk c > 0 over the states of the earlier chunks, by one full
+// warp: lane i reads chunk j0 - i (a chunk before 0 reads as an inclusive
+// prefix of 0); the sums of the chunks after the nearest inclusive prefix and
+// that prefix give c's exclusive prefix.  A window with an unpublished chunk
+// is read again, at most `limit` times in a row (with a short sleep after the
+// first 32); past that the wait gives up and the function returns false with a
+// partial sum.  Returns the exclusive prefix in excl (every lane).
+__device__ __forceinline__ bool scan_lookback(const unsigned long long *state, int c, uint32_t limit,
+                                              unsigned long long &excl) {
+    const int lane = threadIdx.x & 31;
+    excl = 0;
+    int j0 = c - 1;
+    uint32_t spins = 0;
+    for (;;) {
+        const int j = j0 - lane;
+        const unsigned long long v = j >= 0 ? ld_relaxed_u64(&state[j]) : (2ull << 62);
+        const uint32_t flag = (uint32_t)(v >> 62);
+        const uint32_t pre = __ballot_sync(0xFFFFFFFFu, flag == 2u);
+        const int lim = pre ? __ffs(pre) - 1 : 31;   // lanes 0..lim are needed
+        const uint32_t need = lim == 31 ? 0xFFFFFFFFu : ((2u << lim) - 1u);
+        if (__ballot_sync(0xFFFFFFFFu, flag == 0u) & need) {   // some not published yet
+            if (++spins > limit) return false;
+            if (spins > 32) __nanosleep(64);
+            continue;
+        }
+        unsigned long long part = lane <= lim ? (v & ((1ull << 62) - 1)) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        excl += part;
+        if (pre) return true;
+        j0 -= 32;
+        spins = 0;
+    }
+}
 
 // ---------------------------------------------------------------- scan
 // Exclusive prefix sum of tiles-touched in rank order, in one pass: chunk c
@@ -106,39 +141,14 @@ __global__ void __launch_bounds__(TS_THREADS) k_touch_scan(ProjView pv, const ui
     }
     unsigned long long agg;
     block_excl_scan64(acc, swarp, agg);
-    // warp 0 looks back over the earlier chunks, 32 at a time (lane i reads
-    // chunk j0 - i; a chunk before 0 reads as an inclusive prefix of 0)
+    // warp 0 publishes the chunk's sum and looks back over the earlier chunks
     if (t < 32) {
         unsigned long long excl = 0;
         if (c == 0) {
             if (t == 0) st_relaxed_u64(&state[0], (2ull << 62) | agg);
         } else {
             if (t == 0) st_relaxed_u64(&state[c], (1ull << 62) | agg);
-            int j0 = c - 1;
-            uint32_t spins = 0;
-            for (;;) {
-                const int j = j0 - t;
-                const unsigned long long v = j >= 0 ? ld_relaxed_u64(&state[j]) : (2ull << 62);
-                const uint32_t flag = (uint32_t)(v >> 62);
-                const uint32_t pre = __ballot_sync(0xFFFFFFFFu, flag == 2u);
-                const int lim = pre ? __ffs(pre) - 1 : 31;   // lanes 0..lim are needed
-                const uint32_t need = lim == 31 ? 0xFFFFFFFFu : ((2u << lim) - 1u);
-                if (__ballot_sync(0xFFFFFFFFu, flag == 0u) & need) {   // some not published yet
-                    if (++spins > LB_SPIN_LIMIT) {
-                        if (t == 0) atomicOr(status, GS2_ST_TIMEOUT);
-                        break;
-                    }
-                    if (spins > 32) __nanosleep(64);
-                    continue;
-                }
-                unsigned long long part = t <= lim ? (v & ((1ull << 62) - 1)) : 0ull;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-                excl += part;
-                if (pre) break;
-                j0 -= 32;
-                spins = 0;
-            }
+            if (!scan_lookback(state, c, LB_SPIN_LIMIT, excl) && t == 0) atomicOr(status, GS2_ST_TIMEOUT);
             if (t == 0) st_relaxed_u64(&state[c], (2ull << 62) | (excl + agg));
         }
         if (t == 0) s_base = excl;
@@ -563,6 +573,24 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
     }
     __syncthreads();
     for (int i = t; i < ntiles; i += blockDim.x) order[atomicAdd(&cnt[bucket(i)], 1u)] = (uint32_t)i;
+}
+
+// Test of the bounded wait (no GPU fault): one warp looks back from chunk c
+// over states that nothing publishes (zeroed by the caller), gives up after
+// `limit` polls and sets GS2_ST_TIMEOUT, as the scan does when a wait runs out.
+__global__ void k_debug_lookback(const unsigned long long *state, int c, uint32_t limit, uint32_t *status) {
+    unsigned long long excl;
+    const bool ok = scan_lookback(state, c, limit, excl);
+    if (!ok && threadIdx.x == 0) atomicOr(status, GS2_ST_TIMEOUT);
+}
+
+cudaError_t launch_debug_lookback(gs2_ctx *ctx, int c, uint32_t limit, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(ctx->sort_state, 0, sizeof(uint32_t) * GS2_SS_WORDS, st);
+    if (e != cudaSuccess) return e;
+    k_debug_lookback<<<1, 32, 0, st>>>(reinterpret_cast<const unsigned long long *>(ctx->sort_state + GS2_SS_CHUNKS),
+                                       c, limit, ctx->d_status);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bin_sort(gs2_ctx *ctx, ProjView pv, int n, int tiles_x, int tiles_y, cudaStream_t st,

@@ -125,6 +125,7 @@ _sigs = {
                                      _vp, _vp]),
     "gs2_debug_tiles": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
     "gs2_debug_keys": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+    "gs2_debug_lookback_timeout": (C.c_int, [_vp, C.c_int32, C.c_uint32, _vp]),
     "gs2_debug_proj": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -458,6 +459,11 @@ class Context:
         self._ok(_lib.gs2_debug_tiles(self.h, _ptr(ranges), _ptr(ids), int(capacity), C.byref(m), _stream(stream)),
                  "gs2_debug_tiles")
         return ranges, ids[: min(m.value, capacity)], m.value
+
+    def debug_lookback_timeout(self, chunk, limit, stream=None):
+        """Runs the scan's bounded look-back wait on states nothing publishes (test of the timeout path)."""
+        self._ok(_lib.gs2_debug_lookback_timeout(self.h, int(chunk), int(limit), _stream(stream)),
+                 "gs2_debug_lookback_timeout")
 
     def fp64_resolves(self, reset=True):
         """Blocks (colour: channels) re-solved in FP64 per group since the last reset."""

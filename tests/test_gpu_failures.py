@@ -88,3 +88,28 @@ def test_pair_capacity_overflow_is_reported():
     with pytest.raises(gs2.GS2Error, match="CAPACITY"):
         ctx.check()
     assert bool(torch.isfinite(img).all())
+
+
+@pytest.mark.parametrize("chunk,limit", [(1, 64), (40, 4096)])
+def test_bounded_wait_gives_up_and_is_reported(chunk, limit):
+    """The scan's look-back wait, run over states that nothing publishes,
+    gives up after its poll limit: gs2_check reports GS2_ERR_TIMEOUT (and
+    clears it), and the context then sweeps and checks clean."""
+    import time
+    from paper_2501_13975_b300 import gs2
+    sc, cams, ctx, targets, knn = _setup(gs2)
+    t0 = time.perf_counter()
+    ctx.debug_lookback_timeout(chunk, limit)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(gs2.GS2Error, match="TIMEOUT"):
+        ctx.check()
+    ctx.check()   # read and cleared
+    ds = gs2.DeviceScene.from_host(sc)
+    ctx.sweep(ds, cams, targets, knn, 0)
+    torch.cuda.synchronize()
+    ctx.check()
+    _finite_except(ds, None)
+    for bad in ((0, 10), (256, 10), (3, 0), (3, (1 << 20) + 1)):
+        with pytest.raises(gs2.GS2Error):
+            ctx.debug_lookback_timeout(*bad)
