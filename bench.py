@@ -1096,7 +1096,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v11"
+KERNEL_REV = "accum-v12"
 
 
 def main():

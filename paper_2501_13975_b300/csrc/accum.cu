@@ -228,7 +228,6 @@ __device__ __forceinline__ void warp_reduce_scatter_store(const float (&pl)[P], 
 // back-to-front state of one pixel
 struct PixState {
     float T, cb0, cb1, cb2;
-    float e[3], h[3];
     uint32_t last;
     bool inside;
 };
@@ -238,16 +237,16 @@ struct PixState {
 // gn (Gauss-Newton): the e-weighted second derivatives of the pixel colour
 // (e d2c/dz2 through the falloff, e d2c/dalpha dc~) are left out.
 template <int GROUP, int P>
-__device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, const float4 &B, const float4 &C,
-                                              float G, float alpha, float dx, float dy, bool clamped, bool gn,
-                                              float (&pl)[P]) {
+// e, h: the pixel's loss derivatives dL/dc and d2L/dc2 (per channel)
+__device__ __forceinline__ void pixel_payload(PixState &ps, const float *e, const float *h, const float4 &A,
+                                              const float4 &B, const float4 &C, float G, float alpha, float dx,
+                                              float dy, bool clamped, bool gn, float (&pl)[P]) {
     // T_k = T_after / (1 - alpha) undoes one rounded product of the forward
     // pass; a 2-ulp division (reciprocal + multiply) is far inside the tolerances
     const float om = __fsub_rn(1.f, alpha);
     const float Tk = __fdividef(ps.T, om);
     const float w = alpha * Tk;
     const float a0 = Tk * (C.x - ps.cb0), a1 = Tk * (C.y - ps.cb1), a2 = Tk * (C.z - ps.cb2);
-    const float *e = ps.e, *h = ps.h;
     const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
     const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
     if (GROUP == GS2_OPACITY) {
@@ -327,7 +326,11 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float4 &A, con
 template <int GROUP, int NQ> struct AccumShape {
     static constexpr int NT = GS2_TILE_PIX / NQ;   // threads per tile
     static constexpr int NW = NT / 32;
-    static constexpr int MIN_CTAS = NQ == 2 ? Payload<GROUP>::MIN_CTAS : 6;
+    static constexpr int MIN_CTAS = NQ == 2 ? Payload<GROUP>::MIN_CTAS : 8;
+    // four pixels a thread: e and h of the pixels in shared memory (24 registers
+    // fewer) and half-size staging batches, so that 8 CTAs (16 warps) fit on an SM
+    static constexpr bool EH_SMEM = NQ == 4;
+    static constexpr int NB = EH_SMEM ? GS2_TILE_PIX / 2 : GS2_TILE_PIX;   // list entries staged per batch
     static_assert(NT % 32 == 0, "a tile holds whole warps");
 };
 
@@ -342,12 +345,15 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
                                                            const uint32_t *__restrict__ tile_order) {
     constexpr int P = Payload<GROUP>::P;
     constexpr int NT = AccumShape<GROUP, NQ>::NT, NW = AccumShape<GROUP, NQ>::NW;
-    constexpr int NB = GS2_TILE_PIX;                 // list entries staged per batch
+    constexpr bool EH_SMEM = AccumShape<GROUP, NQ>::EH_SMEM;
+    constexpr int NB = AccumShape<GROUP, NQ>::NB;     // list entries staged per batch
     constexpr int PER = NB / NT;                      // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
+    __shared__ float4 sEH4[EH_SMEM ? GS2_TILE_PIX : 1];   // (e0, e1, e2, h0) of pixel q of thread t at q NT + t
+    __shared__ float2 sEH2[EH_SMEM ? GS2_TILE_PIX : 1];   // (h1, h2)
     __shared__ float sDet[DET ? NW : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
     const int t = threadIdx.x, lane = t & 31;
     if constexpr (DET) {
@@ -360,6 +366,7 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     const int py = trow * GS2_TILE + (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
     const size_t PI = (size_t)W * H;
     PixState ps[NQ];
+    float pe[EH_SMEM ? 1 : NQ][3], ph[EH_SMEM ? 1 : NQ][3];   // e, h in registers (two pixels a thread)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const int y = py + 4 * q;
@@ -368,16 +375,25 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
         s.last = 0u;
         s.T = 1.f;
         s.cb0 = s.cb1 = s.cb2 = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s.e[c] = s.h[c] = 0.f;
+        float e[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
         if (s.inside) {
             const size_t pp = (size_t)y * W + px;
             s.last = rv.last[pp];
             s.T = rv.tfinal[pp];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                s.e[c] = E[c * PI + pp];
-                s.h[c] = Hh[c * PI + pp];
+                e[c] = E[c * PI + pp];
+                h[c] = Hh[c * PI + pp];
+            }
+        }
+        if constexpr (EH_SMEM) {
+            sEH4[q * NT + t] = make_float4(e[0], e[1], e[2], h[0]);
+            sEH2[q * NT + t] = make_float2(h[1], h[2]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pe[q][c] = e[c];
+                ph[q][c] = h[c];
             }
         }
     }
@@ -472,7 +488,18 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
             const float4 C = sC[buf][s];
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
-                if (act[q]) pixel_payload<GROUP, P>(ps[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], gn != 0, pl);
+                if (act[q]) {
+                    if constexpr (EH_SMEM) {
+                        const float4 a = sEH4[q * NT + t];
+                        const float2 b = sEH2[q * NT + t];
+                        const float e[3] = {a.x, a.y, a.z}, h[3] = {a.w, b.x, b.y};
+                        pixel_payload<GROUP, P>(ps[q], e, h, A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], gn != 0,
+                                                pl);
+                    } else {
+                        pixel_payload<GROUP, P>(ps[q], pe[q], ph[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q],
+                                                gn != 0, pl);
+                    }
+                }
             if constexpr (DET)
                 warp_reduce_scatter_store<P>(pl, lane, row);
             else
