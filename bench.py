@@ -810,7 +810,7 @@ def time_to_psnr(args):
     # ---- network: records of the plain method, then Adam
     t0 = time.perf_counter()
     tiny = learned.collect_records(range(100, 100 + args.ttp_runs), kind="tiny")
-    shell = learned.collect_records(range(1000, 1000 + args.ttp_shell), kind="shell", sweeps=4)
+    shell = learned.collect_records(range(1000, 1000 + args.ttp_shell), kind="shell", sweeps=args.ttp_shell_sweeps)
     torch.cuda.synchronize()
     t_collect = time.perf_counter() - t0
     parts = [r.split(0.1) for r in (tiny, shell)]
@@ -951,7 +951,7 @@ def time_to_psnr(args):
         "starts": starts,
         "first_sweep_ms": first,
         "network": {"objective": args.ttp_objective, "learned_trust": args.ttp_learned_trust,
-                    "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell,
+                    "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell, "shell_sweeps": args.ttp_shell_sweeps,
                     "records": tiny.n + shell.n,
                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
                     "heldout": held_stats},
@@ -1134,7 +1134,8 @@ def main():
     ap.add_argument("--ttp", action="store_true", help="time to PSNR on the object workload (learned + mixed "
                                                        "vs plain FP32), one JSON line")
     ap.add_argument("--ttp-runs", type=int, default=1000, help="tiny-scene record runs")
-    ap.add_argument("--ttp-shell", type=int, default=24, help="shell-scene record runs (4 sweeps each)")
+    ap.add_argument("--ttp-shell", type=int, default=24, help="shell-scene record runs")
+    ap.add_argument("--ttp-shell-sweeps", type=int, default=4, help="logged sweeps per shell-scene record run")
     ap.add_argument("--ttp-epochs", type=int, default=3)
     ap.add_argument("--ttp-max", type=int, default=60)
     ap.add_argument("--ttp-learned-trust", type=float, default=1.0,
