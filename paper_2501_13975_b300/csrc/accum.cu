@@ -312,6 +312,80 @@ __device__ __forceinline__ void pixel_payload(PixState &ps, const float *e, cons
     ps.T = Tk;
 }
 
+// Packed FP32 pairs: the sm_100-family f32x2 instructions (add, mul, fma on a
+// 64-bit register pair, each half rounded as its scalar _rn counterpart) do the
+// same operation for both pixels of a lane in one issue slot.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// back-to-front state of the two pixels of a lane (x: q = 0, y: q = 1)
+struct PairState {
+    float2 T, cb0, cb1, cb2;
+};
+
+// One list entry for the pixel pair of a lane, branch free: a pixel that does
+// not composite the Gaussian (outside the image, past its last contributor,
+// or outside the support) takes alpha = 0 and keeps its state, and the
+// payload weight ap (alpha where composited and not clamped, else 0) zeroes
+// the falloff terms of clamped and inactive pixels.  The payload is kept per
+// pixel (pl[i].x, pl[i].y) and summed before the warp reduction.
+// e, h: (q = 0, q = 1) pairs of the pixels' loss derivatives per channel.
+template <int GROUP, int P>
+__device__ __forceinline__ void pair_payload(PairState &ps, const float2 (&e)[3], const float2 (&h)[3],
+                                             const float4 &A, const float4 &B, const float4 &C, float2 G,
+                                             float2 al, float2 ap, bool l0, bool l1, float dx, float2 dy,
+                                             float2 (&pl)[P]) {
+    const float2 om = fma2(al, f2(-1.f), f2(1.f));   // 1 - alpha, rounded once
+    float2 Tk = mul2(ps.T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+    Tk.x = l0 ? Tk.x : ps.T.x;
+    Tk.y = l1 ? Tk.y : ps.T.y;
+    const float2 w = mul2(al, Tk);
+    if constexpr (GROUP == GS2_COLOR) {
+        const float2 ww = mul2(w, w);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pl[c] = fma2(w, e[c], pl[c]);
+            pl[3 + c] = fma2(ww, h[c], pl[3 + c]);
+        }
+    } else {
+        const float2 a0 = mul2(Tk, fma2(ps.cb0, f2(-1.f), f2(C.x)));
+        const float2 a1 = mul2(Tk, fma2(ps.cb1, f2(-1.f), f2(C.y)));
+        const float2 a2 = mul2(Tk, fma2(ps.cb2, f2(-1.f), f2(C.z)));
+        const float2 Ea = fma2(e[2], a2, fma2(e[1], a1, mul2(e[0], a0)));
+        const float2 Ah = fma2(mul2(h[2], a2), a2, fma2(mul2(h[1], a1), a1, mul2(mul2(h[0], a0), a0)));
+        if constexpr (GROUP == GS2_OPACITY) {
+            const float2 Gp = make_float2(ap.x != 0.f ? G.x : 0.f, ap.y != 0.f ? G.y : 0.f);
+            pl[0] = fma2(Ea, Gp, pl[0]);
+            pl[1] = fma2(mul2(Ah, Gp), Gp, pl[1]);
+        } else {   // rotation / scaling: moments over (x4 x3y x2y2 xy3 y4) and (xx xy yy x4 ... y4)
+            const float2 dxv = f2(dx);
+            const float2 ux = fma2(f2(A.z), dxv, mul2(f2(A.w), dy));
+            const float2 uy = fma2(f2(A.w), dxv, mul2(f2(B.x), dy));
+            const float2 xx = mul2(ux, ux), xy = mul2(ux, uy), yy = mul2(uy, uy);
+            const float2 m4[5] = {mul2(xx, xx), mul2(xx, xy), mul2(xx, yy), mul2(xy, yy), mul2(yy, yy)};
+            const float2 W1 = mul2(mul2(Ah, ap), ap), W2 = mul2(Ea, ap);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) pl[i] = fma2(W1, m4[i], pl[i]);
+            pl[5] = fma2(W2, xx, pl[5]);
+            pl[6] = fma2(W2, xy, pl[6]);
+            pl[7] = fma2(W2, yy, pl[7]);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) pl[8 + i] = fma2(W2, m4[i], pl[8 + i]);
+        }
+        ps.cb0 = fma2(al, f2(C.x), mul2(om, ps.cb0));
+        ps.cb1 = fma2(al, f2(C.y), mul2(om, ps.cb1));
+        ps.cb2 = fma2(al, f2(C.z), mul2(om, ps.cb2));
+    }
+    ps.T = Tk;
+}
+
 // DET (deterministic mode): no atomics.  Every list entry's payload is the
 // sum of the tile's four warp sums taken in warp order, written to
 // det_part[sorted position][P] (entries past the tile's last contributor
@@ -347,6 +421,7 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     constexpr int NT = AccumShape<GROUP, NQ>::NT, NW = AccumShape<GROUP, NQ>::NW;
     constexpr bool EH_SMEM = AccumShape<GROUP, NQ>::EH_SMEM;
     constexpr int NB = AccumShape<GROUP, NQ>::NB;     // list entries staged per batch
+    constexpr bool PAIR = NQ == 2 && GROUP != GS2_POS;   // f32x2 pixel pairs (pair_payload)
     constexpr int PER = NB / NT;                      // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][NB];
@@ -397,6 +472,19 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
             }
         }
     }
+    // two pixels a thread: their FP state and loss derivatives as (q = 0, q = 1) pairs
+    PairState pst;
+    float2 pe2[3], ph2[3];
+    if constexpr (PAIR) {
+        pst.T = make_float2(ps[0].T, ps[1].T);
+        pst.cb0 = pst.cb1 = pst.cb2 = f2(0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pe2[c] = make_float2(pe[0][c], pe[1][c]);
+            ph2[c] = make_float2(ph[0][c], ph[1][c]);
+        }
+    }
+    const float2 pyf = make_float2((float)py, (float)(py + 4));
     uint32_t last2 = ps[0].last;
 #pragma unroll
     for (int q = 1; q < NQ; ++q) last2 = max(last2, ps[q].last);
@@ -431,7 +519,7 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
                 sId[buf][j] = k;
                 cp_async16(&sA[buf][j], &pv.recA[k]);
                 cp_async16(&sB[buf][j], &pv.recB[k]);
-                cp_async16(&sC[buf][j], &pv.col[k]);
+                if constexpr (GROUP != GS2_COLOR) cp_async16(&sC[buf][j], &pv.col[k]);   // colour: no c~
             }
         }
         cp_async_commit();
@@ -455,6 +543,43 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
         // (atomics, or stored to `row` in deterministic mode)
         auto entry = [&](int jj, float *row) {
             const int s = jj - base;
+            if constexpr (PAIR) {   // the pixel pair in f32x2 arithmetic, branch free
+                const float4 A = sA[buf][s], B = sB[buf][s];
+                const float dx = __fsub_rn(fx, A.x);
+                const float2 dxv = f2(dx);
+                const float2 dy = add2(pyf, f2(-A.y));
+                // dec_quad of both pixels (the same correctly rounded operations, in the same order)
+                float2 qa = fma2(f2(A.z), dxv, mul2(f2(A.w), dy));
+                qa = fma2(f2(A.w), dy, qa);
+                const float2 qf = fma2(dxv, qa, mul2(mul2(f2(B.x), dy), dy));
+                const bool l0 = (uint32_t)jj < ps[0].last && qf.x <= B.z;   // composited (as k_raster)
+                const bool l1 = (uint32_t)jj < ps[1].last && qf.y <= B.z;
+                nact += (l0 ? 1u : 0u) + (l1 ? 1u : 0u);
+                if (!__any_sync(0xFFFFFFFFu, l0 || l1)) return;
+                const float2 xg = mul2(qf, f2(-0.72134752044448170368f));   // gs2_falloff, both pixels
+                float2 G;
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G.x) : "f"(xg.x));
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G.y) : "f"(xg.y));
+                const bool c0 = qf.x < B.w, c1 = qf.y < B.w;   // clamped at alpha_max
+                float2 al = mul2(f2(B.y), G);
+                al.x = l0 ? (c0 ? amax : al.x) : 0.f;
+                al.y = l1 ? (c1 ? amax : al.y) : 0.f;
+                const float2 ap = make_float2(c0 ? 0.f : al.x, c1 ? 0.f : al.y);
+                float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (GROUP != GS2_COLOR) C = sC[buf][s];
+                float2 pl2[P];
+#pragma unroll
+                for (int i = 0; i < P; ++i) pl2[i] = f2(0.f);
+                pair_payload<GROUP, P>(pst, pe2, ph2, A, B, C, G, al, ap, l0, l1, dx, dy, pl2);
+                float pl[P];
+#pragma unroll
+                for (int i = 0; i < P; ++i) pl[i] = pl2[i].x + pl2[i].y;
+                if constexpr (DET)
+                    warp_reduce_scatter_store<P>(pl, lane, row);
+                else
+                    warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
+                return;
+            }
             const float4 A = sA[buf][s], B = sB[buf][s];
             const float dx = __fsub_rn(fx, A.x);
             bool act[NQ], clamped[NQ];
