@@ -1096,7 +1096,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v12"
+KERNEL_REV = "accum-v13"
 
 
 def main():

@@ -225,93 +225,6 @@ __device__ __forceinline__ void warp_reduce_scatter_store(const float (&pl)[P], 
 // Deterministic mode: list entries per flush of the per-warp sums
 #define GS2_DET_CHUNK 32
 
-// back-to-front state of one pixel
-struct PixState {
-    float T, cb0, cb1, cb2;
-    uint32_t last;
-    bool inside;
-};
-
-// One active (pixel, Gaussian) pair: adds the group's payload into pl and
-// steps the pixel's state past the Gaussian.
-// gn (Gauss-Newton): the e-weighted second derivatives of the pixel colour
-// (e d2c/dz2 through the falloff, e d2c/dalpha dc~) are left out.
-template <int GROUP, int P>
-// e, h: the pixel's loss derivatives dL/dc and d2L/dc2 (per channel)
-__device__ __forceinline__ void pixel_payload(PixState &ps, const float *e, const float *h, const float4 &A,
-                                              const float4 &B, const float4 &C, float G, float alpha, float dx,
-                                              float dy, bool clamped, bool gn, float (&pl)[P]) {
-    // T_k = T_after / (1 - alpha) undoes one rounded product of the forward
-    // pass; a 2-ulp division (reciprocal + multiply) is far inside the tolerances
-    const float om = __fsub_rn(1.f, alpha);
-    const float Tk = __fdividef(ps.T, om);
-    const float w = alpha * Tk;
-    const float a0 = Tk * (C.x - ps.cb0), a1 = Tk * (C.y - ps.cb1), a2 = Tk * (C.z - ps.cb2);
-    const float Ea = e[0] * a0 + e[1] * a1 + e[2] * a2;
-    const float Ah = h[0] * a0 * a0 + h[1] * a1 * a1 + h[2] * a2 * a2;
-    if (GROUP == GS2_OPACITY) {
-        if (!clamped) {
-            pl[0] += Ea * G;
-            pl[1] += Ah * G * G;
-        }
-    } else if (GROUP == GS2_COLOR) {
-        pl[0] += w * e[0];
-        pl[1] += w * e[1];
-        pl[2] += w * e[2];
-        pl[3] += w * w * h[0];
-        pl[4] += w * w * h[1];
-        pl[5] += w * w * h[2];
-    } else if (GROUP == GS2_ROT || GROUP == GS2_SCALE) {
-        if (!clamped) {   // not clamped: alpha = sigma G, the factor of every falloff derivative
-            const float ux = A.z * dx + A.w * dy, uy = A.w * dx + B.x * dy;
-            const float xx = ux * ux, xy = ux * uy, yy = uy * uy;
-            const float m4[5] = {xx * xx, xx * xy, xx * yy, xy * yy, yy * yy};
-            const float W1 = Ah * alpha * alpha, W2 = Ea * alpha;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) pl[i] += W1 * m4[i];
-            pl[5] += W2 * xx;
-            pl[6] += W2 * xy;
-            pl[7] += W2 * yy;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) pl[8 + i] += W2 * m4[i];
-        }
-    } else {  // position
-        const float aa[3] = {a0, a1, a2};
-        if (!clamped) {
-            const float ux = A.z * dx + A.w * dy, uy = A.w * dx + B.x * dy;
-            const float xx = ux * ux, xy = ux * uy, yy = uy * uy;
-            const float mono[12] = {xx,      xy,      yy,      xx * ux, xx * uy, xy * uy,
-                                    yy * uy, xx * xx, xx * xy, xx * yy, xy * yy, yy * yy};
-            const float W1 = Ah * alpha * alpha, W2 = Ea * alpha;
-#pragma unroll
-            for (int i = 0; i < 12; ++i) pl[i] += W1 * mono[i];
-            pl[12] += W2;
-            pl[13] += W2 * ux;
-            pl[14] += W2 * uy;
-#pragma unroll
-            for (int i = 0; i < 12; ++i) pl[15 + i] += W2 * mono[i];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const float X = (h[ch] * aa[ch] * w + (gn ? 0.f : e[ch] * Tk)) * alpha;
-                pl[27 + 5 * ch + 0] += X * ux;
-                pl[27 + 5 * ch + 1] += X * uy;
-                pl[27 + 5 * ch + 2] += X * xx;
-                pl[27 + 5 * ch + 3] += X * xy;
-                pl[27 + 5 * ch + 4] += X * yy;
-            }
-        }
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            pl[42 + ch] += w * e[ch];
-            pl[45 + ch] += w * w * h[ch];
-        }
-    }
-    ps.cb0 = alpha * C.x + om * ps.cb0;
-    ps.cb1 = alpha * C.y + om * ps.cb1;
-    ps.cb2 = alpha * C.z + om * ps.cb2;
-    ps.T = Tk;
-}
-
 // Packed FP32 pairs: the sm_100-family f32x2 instructions (add, mul, fma on a
 // 64-bit register pair, each half rounded as its scalar _rn counterpart) do the
 // same operation for both pixels of a lane in one issue slot.
@@ -386,6 +299,124 @@ __device__ __forceinline__ void pair_payload(PairState &ps, const float2 (&e)[3]
     ps.T = Tk;
 }
 
+// The position payload of one list entry for the NPR pixel pairs of a lane
+// (NPR = 1: two pixels, 2: four), straight into the 48 moment slots: each
+// moment is the f32x2 sum over the pairs of weight x monomial, then the two
+// halves added.  Colour and cross terms first, so that e, h and the colour-
+// path weights die before the 27 geometric moments are formed.
+// gn (Gauss-Newton): the e-weighted second derivatives of the pixel colour
+// (e d2c/dz2 through the falloff, e d2c/dalpha dc~) are left out.
+template <int NPR>
+__device__ __forceinline__ void pos_pairs(PairState (&ps)[NPR], const float2 (&e)[NPR][3],
+                                          const float2 (&h)[NPR][3], const float4 &A, const float4 &B,
+                                          const float4 &C, const float2 (&al)[NPR], const float2 (&ap)[NPR],
+                                          const bool (&lv)[NPR][2], float dx, const float2 (&dy)[NPR], bool gn,
+                                          float (&pl)[GS2_ZPOS]) {
+    float2 W1[NPR], W2[NPR], X[NPR][3], UX[NPR], UY[NPR];
+    float2 sc[6];   // colour sums: w e_c, w^2 h_c
+    const float2 dxv = f2(dx);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) {
+        const float2 om = fma2(al[r], f2(-1.f), f2(1.f));   // 1 - alpha, rounded once
+        float2 Tk = mul2(ps[r].T, make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+        Tk.x = lv[r][0] ? Tk.x : ps[r].T.x;
+        Tk.y = lv[r][1] ? Tk.y : ps[r].T.y;
+        const float2 w = mul2(al[r], Tk), ww = mul2(w, w);
+        const float2 a0 = mul2(Tk, fma2(ps[r].cb0, f2(-1.f), f2(C.x)));
+        const float2 a1 = mul2(Tk, fma2(ps[r].cb1, f2(-1.f), f2(C.y)));
+        const float2 a2 = mul2(Tk, fma2(ps[r].cb2, f2(-1.f), f2(C.z)));
+        const float2 ac[3] = {a0, a1, a2};
+        const float2 Ea = fma2(e[r][2], a2, fma2(e[r][1], a1, mul2(e[r][0], a0)));
+        const float2 Ah = fma2(mul2(h[r][2], a2), a2, fma2(mul2(h[r][1], a1), a1, mul2(mul2(h[r][0], a0), a0)));
+        W1[r] = mul2(mul2(Ah, ap[r]), ap[r]);
+        W2[r] = mul2(Ea, ap[r]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 et = gn ? f2(0.f) : mul2(e[r][c], Tk);
+            X[r][c] = mul2(fma2(mul2(h[r][c], ac[c]), w, et), ap[r]);
+            sc[c] = r == 0 ? mul2(w, e[r][c]) : fma2(w, e[r][c], sc[c]);
+            sc[3 + c] = r == 0 ? mul2(ww, h[r][c]) : fma2(ww, h[r][c], sc[3 + c]);
+        }
+        UX[r] = fma2(f2(A.z), dxv, mul2(f2(A.w), dy[r]));
+        UY[r] = fma2(f2(A.w), dxv, mul2(f2(B.x), dy[r]));
+        ps[r].cb0 = fma2(al[r], f2(C.x), mul2(om, ps[r].cb0));
+        ps[r].cb1 = fma2(al[r], f2(C.y), mul2(om, ps[r].cb1));
+        ps[r].cb2 = fma2(al[r], f2(C.z), mul2(om, ps[r].cb2));
+        ps[r].T = Tk;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pl[42 + i] = sc[i].x + sc[i].y;
+    // sum over the pairs of wt[r] m[r], both halves added
+    auto msum = [](const float2 (&wt)[NPR], const float2 (&m)[NPR]) {
+        float2 s = mul2(wt[0], m[0]);
+#pragma unroll
+        for (int r = 1; r < NPR; ++r) s = fma2(wt[r], m[r], s);
+        return s.x + s.y;
+    };
+    float2 XX[NPR], XY[NPR], YY[NPR];
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) {
+        XX[r] = mul2(UX[r], UX[r]);
+        XY[r] = mul2(UX[r], UY[r]);
+        YY[r] = mul2(UY[r], UY[r]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {   // cross terms: X_c over (x, y, xx, xy, yy)
+        float2 Xc[NPR];
+#pragma unroll
+        for (int r = 0; r < NPR; ++r) Xc[r] = X[r][c];
+        pl[27 + 5 * c + 0] = msum(Xc, UX);
+        pl[27 + 5 * c + 1] = msum(Xc, UY);
+        pl[27 + 5 * c + 2] = msum(Xc, XX);
+        pl[27 + 5 * c + 3] = msum(Xc, XY);
+        pl[27 + 5 * c + 4] = msum(Xc, YY);
+    }
+    {
+        float2 s = W2[0];
+#pragma unroll
+        for (int r = 1; r < NPR; ++r) s = add2(W2[r], s);
+        pl[12] = s.x + s.y;
+    }
+    pl[13] = msum(W2, UX);
+    pl[14] = msum(W2, UY);
+    // monomials in the W1-list order: xx xy yy xxx xxy xyy yyy x4 x3y x2y2 xy3 y4
+    auto both = [&](int i, const float2 (&m)[NPR]) {
+        pl[i] = msum(W1, m);
+        pl[15 + i] = msum(W2, m);
+    };
+    both(MXX, XX);
+    both(MXY, XY);
+    both(MYY, YY);
+    float2 m[NPR];
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XX[r], UX[r]);
+    both(MXXX, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XX[r], UY[r]);
+    both(MXXY, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XY[r], UY[r]);
+    both(MXYY, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(YY[r], UY[r]);
+    both(MYYY, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XX[r], XX[r]);
+    both(MX4, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XX[r], XY[r]);
+    both(MX3Y, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XX[r], YY[r]);
+    both(MX2Y2, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(XY[r], YY[r]);
+    both(MXY3, m);
+#pragma unroll
+    for (int r = 0; r < NPR; ++r) m[r] = mul2(YY[r], YY[r]);
+    both(MY4, m);
+}
+
 // DET (deterministic mode): no atomics.  Every list entry's payload is the
 // sum of the tile's four warp sums taken in warp order, written to
 // det_part[sorted position][P] (entries past the tile's last contributor
@@ -421,14 +452,16 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     constexpr int NT = AccumShape<GROUP, NQ>::NT, NW = AccumShape<GROUP, NQ>::NW;
     constexpr bool EH_SMEM = AccumShape<GROUP, NQ>::EH_SMEM;
     constexpr int NB = AccumShape<GROUP, NQ>::NB;     // list entries staged per batch
-    constexpr bool PAIR = NQ == 2 && GROUP != GS2_POS;   // f32x2 pixel pairs (pair_payload)
+    constexpr int NPR = NQ / 2;                       // pixel pairs a thread (f32x2 arithmetic)
+    static_assert(NQ == 2 || (NQ == 4 && GROUP == GS2_POS), "four pixels a thread: position only");
     constexpr int PER = NB / NT;                      // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
-    __shared__ float4 sEH4[EH_SMEM ? GS2_TILE_PIX : 1];   // (e0, e1, e2, h0) of pixel q of thread t at q NT + t
-    __shared__ float2 sEH2[EH_SMEM ? GS2_TILE_PIX : 1];   // (h1, h2)
+    // four pixels a thread: e, h of pixel pair r of thread t as f32x2 pairs,
+    // [r][0] = (e0, e1), [r][1] = (e2, h0), [r][2] = (h1, h2) (each .x: q = 2r, .y: q = 2r + 1)
+    __shared__ float4 sEP[EH_SMEM ? NPR : 1][3][EH_SMEM ? NT : 1];
     __shared__ float sDet[DET ? NW : 1][DET ? GS2_DET_CHUNK : 1][DET ? P : 1];   // per-warp sums of a chunk
     const int t = threadIdx.x, lane = t & 31;
     if constexpr (DET) {
@@ -440,54 +473,50 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     const int px = tcol * GS2_TILE + (wb % GS2_WPR) * 8 + (t & 7);
     const int py = trow * GS2_TILE + (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
     const size_t PI = (size_t)W * H;
-    PixState ps[NQ];
-    float pe[EH_SMEM ? 1 : NQ][3], ph[EH_SMEM ? 1 : NQ][3];   // e, h in registers (two pixels a thread)
+    uint32_t last[NQ];
+    PairState pst[NPR];
+    float2 pe2[EH_SMEM ? 1 : NPR][3], ph2[EH_SMEM ? 1 : NPR][3];   // e, h in registers (two pixels a thread)
+    float2 pyf[NPR];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int y = py + 4 * q;
-        PixState &s = ps[q];
-        s.inside = px < W && y < H;
-        s.last = 0u;
-        s.T = 1.f;
-        s.cb0 = s.cb1 = s.cb2 = 0.f;
-        float e[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
-        if (s.inside) {
-            const size_t pp = (size_t)y * W + px;
-            s.last = rv.last[pp];
-            s.T = rv.tfinal[pp];
+    for (int r = 0; r < NPR; ++r) {
+        float e[2][3], h[2][3], T[2];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                e[c] = E[c * PI + pp];
-                h[c] = Hh[c * PI + pp];
+        for (int j = 0; j < 2; ++j) {
+            const int y = py + 4 * (2 * r + j);
+            const bool inside = px < W && y < H;
+            last[2 * r + j] = 0u;   // outside the image: no list entry is composited
+            T[j] = 1.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) e[j][c] = h[j][c] = 0.f;
+            if (inside) {
+                const size_t pp = (size_t)y * W + px;
+                last[2 * r + j] = rv.last[pp];
+                T[j] = rv.tfinal[pp];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    e[j][c] = E[c * PI + pp];
+                    h[j][c] = Hh[c * PI + pp];
+                }
             }
         }
+        pst[r].T = make_float2(T[0], T[1]);
+        pst[r].cb0 = pst[r].cb1 = pst[r].cb2 = f2(0.f);
+        pyf[r] = make_float2((float)(py + 8 * r), (float)(py + 8 * r + 4));
         if constexpr (EH_SMEM) {
-            sEH4[q * NT + t] = make_float4(e[0], e[1], e[2], h[0]);
-            sEH2[q * NT + t] = make_float2(h[1], h[2]);
+            sEP[r][0][t] = make_float4(e[0][0], e[1][0], e[0][1], e[1][1]);
+            sEP[r][1][t] = make_float4(e[0][2], e[1][2], h[0][0], h[1][0]);
+            sEP[r][2][t] = make_float4(h[0][1], h[1][1], h[0][2], h[1][2]);
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                pe[q][c] = e[c];
-                ph[q][c] = h[c];
+                pe2[r][c] = make_float2(e[0][c], e[1][c]);
+                ph2[r][c] = make_float2(h[0][c], h[1][c]);
             }
         }
     }
-    // two pixels a thread: their FP state and loss derivatives as (q = 0, q = 1) pairs
-    PairState pst;
-    float2 pe2[3], ph2[3];
-    if constexpr (PAIR) {
-        pst.T = make_float2(ps[0].T, ps[1].T);
-        pst.cb0 = pst.cb1 = pst.cb2 = f2(0.f);
+    uint32_t last2 = last[0];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            pe2[c] = make_float2(pe[0][c], pe[1][c]);
-            ph2[c] = make_float2(ph[0][c], ph[1][c]);
-        }
-    }
-    const float2 pyf = make_float2((float)py, (float)(py + 4));
-    uint32_t last2 = ps[0].last;
-#pragma unroll
-    for (int q = 1; q < NQ; ++q) last2 = max(last2, ps[q].last);
+    for (int q = 1; q < NQ; ++q) last2 = max(last2, last[q]);
     if (t == 0) sMax = 0u;
     __syncthreads();
     atomicMax(&sMax, last2);
@@ -543,88 +572,70 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
         // (atomics, or stored to `row` in deterministic mode)
         auto entry = [&](int jj, float *row) {
             const int s = jj - base;
-            if constexpr (PAIR) {   // the pixel pair in f32x2 arithmetic, branch free
-                const float4 A = sA[buf][s], B = sB[buf][s];
-                const float dx = __fsub_rn(fx, A.x);
-                const float2 dxv = f2(dx);
-                const float2 dy = add2(pyf, f2(-A.y));
+            const float4 A = sA[buf][s], B = sB[buf][s];
+            const float dx = __fsub_rn(fx, A.x);
+            const float2 dxv = f2(dx);
+            float2 dy[NPR], qf[NPR];
+            bool lv[NPR][2];
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < NPR; ++r) {
+                dy[r] = add2(pyf[r], f2(-A.y));
                 // dec_quad of both pixels (the same correctly rounded operations, in the same order)
-                float2 qa = fma2(f2(A.z), dxv, mul2(f2(A.w), dy));
-                qa = fma2(f2(A.w), dy, qa);
-                const float2 qf = fma2(dxv, qa, mul2(mul2(f2(B.x), dy), dy));
-                const bool l0 = (uint32_t)jj < ps[0].last && qf.x <= B.z;   // composited (as k_raster)
-                const bool l1 = (uint32_t)jj < ps[1].last && qf.y <= B.z;
-                nact += (l0 ? 1u : 0u) + (l1 ? 1u : 0u);
-                if (!__any_sync(0xFFFFFFFFu, l0 || l1)) return;
-                const float2 xg = mul2(qf, f2(-0.72134752044448170368f));   // gs2_falloff, both pixels
-                float2 G;
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G.x) : "f"(xg.x));
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G.y) : "f"(xg.y));
-                const bool c0 = qf.x < B.w, c1 = qf.y < B.w;   // clamped at alpha_max
-                float2 al = mul2(f2(B.y), G);
-                al.x = l0 ? (c0 ? amax : al.x) : 0.f;
-                al.y = l1 ? (c1 ? amax : al.y) : 0.f;
-                const float2 ap = make_float2(c0 ? 0.f : al.x, c1 ? 0.f : al.y);
-                float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-                if constexpr (GROUP != GS2_COLOR) C = sC[buf][s];
+                float2 qa = fma2(f2(A.z), dxv, mul2(f2(A.w), dy[r]));
+                qa = fma2(f2(A.w), dy[r], qa);
+                qf[r] = fma2(dxv, qa, mul2(mul2(f2(B.x), dy[r]), dy[r]));
+                lv[r][0] = (uint32_t)jj < last[2 * r] && qf[r].x <= B.z;   // composited (as k_raster)
+                lv[r][1] = (uint32_t)jj < last[2 * r + 1] && qf[r].y <= B.z;
+                any = any || lv[r][0] || lv[r][1];
+                nact += (lv[r][0] ? 1u : 0u) + (lv[r][1] ? 1u : 0u);
+            }
+            if (!__any_sync(0xFFFFFFFFu, any)) return;
+            float2 G[NPR], al[NPR], ap[NPR];
+#pragma unroll
+            for (int r = 0; r < NPR; ++r) {
+                const float2 xg = mul2(qf[r], f2(-0.72134752044448170368f));   // gs2_falloff, both pixels
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G[r].x) : "f"(xg.x));
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G[r].y) : "f"(xg.y));
+                const bool c0 = qf[r].x < B.w, c1 = qf[r].y < B.w;   // clamped at alpha_max
+                al[r] = mul2(f2(B.y), G[r]);
+                al[r].x = lv[r][0] ? (c0 ? amax : al[r].x) : 0.f;
+                al[r].y = lv[r][1] ? (c1 ? amax : al[r].y) : 0.f;
+                ap[r] = make_float2(c0 ? 0.f : al[r].x, c1 ? 0.f : al[r].y);
+            }
+            float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (GROUP != GS2_COLOR) C = sC[buf][s];
+            float pl[P];
+            if constexpr (GROUP == GS2_POS) {
+                float2 pe[NPR][3], ph[NPR][3];
+#pragma unroll
+                for (int r = 0; r < NPR; ++r) {
+                    if constexpr (EH_SMEM) {
+                        const float4 k0 = sEP[r][0][t], k1 = sEP[r][1][t], k2 = sEP[r][2][t];
+                        pe[r][0] = make_float2(k0.x, k0.y);
+                        pe[r][1] = make_float2(k0.z, k0.w);
+                        pe[r][2] = make_float2(k1.x, k1.y);
+                        ph[r][0] = make_float2(k1.z, k1.w);
+                        ph[r][1] = make_float2(k2.x, k2.y);
+                        ph[r][2] = make_float2(k2.z, k2.w);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            pe[r][c] = pe2[r][c];
+                            ph[r][c] = ph2[r][c];
+                        }
+                    }
+                }
+                pos_pairs<NPR>(pst, pe, ph, A, B, C, al, ap, lv, dx, dy, gn != 0, pl);
+            } else {
                 float2 pl2[P];
 #pragma unroll
                 for (int i = 0; i < P; ++i) pl2[i] = f2(0.f);
-                pair_payload<GROUP, P>(pst, pe2, ph2, A, B, C, G, al, ap, l0, l1, dx, dy, pl2);
-                float pl[P];
+                pair_payload<GROUP, P>(pst[0], pe2[0], ph2[0], A, B, C, G[0], al[0], ap[0], lv[0][0], lv[0][1], dx,
+                                       dy[0], pl2);
 #pragma unroll
                 for (int i = 0; i < P; ++i) pl[i] = pl2[i].x + pl2[i].y;
-                if constexpr (DET)
-                    warp_reduce_scatter_store<P>(pl, lane, row);
-                else
-                    warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
-                return;
             }
-            const float4 A = sA[buf][s], B = sB[buf][s];
-            const float dx = __fsub_rn(fx, A.x);
-            bool act[NQ], clamped[NQ];
-            float G[NQ], alpha[NQ], dy[NQ];
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                act[q] = ps[q].inside && (uint32_t)jj < ps[q].last;
-                G[q] = 0.f;
-                alpha[q] = 0.f;
-                dy[q] = 0.f;
-                clamped[q] = false;
-                if (act[q]) {
-                    dy[q] = __fsub_rn((float)(py + 4 * q), A.y);
-                    const float qf = dec_quad(A.z, A.w, B.x, dx, dy[q]);
-                    if (qf <= B.z) {   // composited (the same decision as k_raster)
-                        G[q] = gs2_falloff(qf);
-                        clamped[q] = qf < B.w;
-                        alpha[q] = clamped[q] ? amax : __fmul_rn(B.y, G[q]);
-                    } else {
-                        act[q] = false;
-                    }
-                }
-                any = any || act[q];
-                nact += act[q] ? 1u : 0u;
-            }
-            if (!__any_sync(0xFFFFFFFFu, any)) return;
-            float pl[P];
-#pragma unroll
-            for (int i = 0; i < P; ++i) pl[i] = 0.f;
-            const float4 C = sC[buf][s];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-                if (act[q]) {
-                    if constexpr (EH_SMEM) {
-                        const float4 a = sEH4[q * NT + t];
-                        const float2 b = sEH2[q * NT + t];
-                        const float e[3] = {a.x, a.y, a.z}, h[3] = {a.w, b.x, b.y};
-                        pixel_payload<GROUP, P>(ps[q], e, h, A, B, C, G[q], alpha[q], dx, dy[q], clamped[q], gn != 0,
-                                                pl);
-                    } else {
-                        pixel_payload<GROUP, P>(ps[q], pe[q], ph[q], A, B, C, G[q], alpha[q], dx, dy[q], clamped[q],
-                                                gn != 0, pl);
-                    }
-                }
             if constexpr (DET)
                 warp_reduce_scatter_store<P>(pl, lane, row);
             else
