@@ -16,6 +16,11 @@
 // maps the other): 65 KB, so three CTAs fit on an SM.  HBM traffic per
 // pixel: read c, c^t (24 B), write e, h (24 B); the final pass re-reads its
 // pixel's c, c^t from L2.
+// The correlations run on f32x2 pairs (packed FP32 mul/fma, each half rounded
+// as its scalar counterpart): the inputs are kept as (c, c^t) pairs, the
+// moment sums as (x, y) and (xx, yy) pair planes beside the xy plane, and the
+// eight coefficient maps as four pair planes (A, B), (C, K0), (Kc, Kt),
+// (Kct, Kcc) correlated with (w, w), (w, w^2), (w^2, w^2), (w^2, w^2).
 #include <mutex>
 
 #include "common.cuh"
@@ -59,13 +64,21 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
     extern __shared__ float sm[];
     // region 1: moment sums, then (once they are consumed) the correlated maps;
     // region 2: the inputs, then (once the moments are formed) the coefficient maps
-    float *sH = sm, *sHC = sm;
-    float *sX = sm + SM_H1, *sY = sm + SM_H1 + SM_IN, *sK = sm + SM_H1;
+    float2 *sXY = reinterpret_cast<float2 *>(sm + SM_H1);           // (c, c^t) [IN_H][IN_W]
+    float2 *sH01 = reinterpret_cast<float2 *>(sm);                  // (w * x, w * y) [IN_H][MO_W]
+    float2 *sH23 = sH01 + IN_H * MO_W;                              // (w * xx, w * yy)
+    float *sH4 = reinterpret_cast<float *>(sH23 + IN_H * MO_W);     // w * xy
+    float2 *sK2 = reinterpret_cast<float2 *>(sm + SM_H1);           // 4 coefficient pair planes [MO_H][MO_W]
+    float2 *sHC2 = reinterpret_cast<float2 *>(sm);                  // 4 correlated pair planes [MO_H][LT_W]
     __shared__ double sred[8];
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * LT_W, y0 = blockIdx.y * LT_H;
     const size_t P = (size_t)W * H;
     double l2acc = 0.0, lsacc = 0.0;
+    // window weights of the coefficient pair planes: (w, w), (w, w^2), (w^2, w^2), (w^2, w^2)
+    auto cw = [&](int qq, int d) {
+        return make_float2(qq < 2 ? K.g[d] : K.g2[d], qq == 0 ? K.g[d] : K.g2[d]);
+    };
     for (int c = 0; c < 3; ++c) {
         const float *X = img + c * P, *Y = tgt + c * P;
         for (int i = t; i < SM_IN; i += 256) {
@@ -79,8 +92,7 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
                 xv = isfinite(xv) ? xv : 0.f;
                 yv = isfinite(yv) ? yv : 0.f;
             }
-            sX[i] = xv;
-            sY[i] = yv;
+            sXY[i] = make_float2(xv, yv);
         }
         __syncthreads();
         // horizontal window sums of x, y, xx, yy, xy: a thread slides one
@@ -88,31 +100,26 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
         constexpr int HR = 6, HSEG = MO_W / HR;   // 42 = 7 x 6
         for (int i = t; i < IN_H * HSEG; i += 256) {
             const int r = i / HSEG, j0 = (i % HSEG) * HR;
-            const float *xr = sX + r * IN_W + j0, *yr = sY + r * IN_W + j0;
-            float xv[HR + LWIN - 1], yv[HR + LWIN - 1];
+            const float2 *xr = sXY + r * IN_W + j0;
+            float2 xy[HR + LWIN - 1];
 #pragma unroll
-            for (int d = 0; d < HR + LWIN - 1; ++d) {
-                xv[d] = xr[d];
-                yv[d] = yr[d];
-            }
+            for (int d = 0; d < HR + LWIN - 1; ++d) xy[d] = xr[d];
 #pragma unroll
             for (int o = 0; o < HR; ++o) {
-                float a = 0.f, b = 0.f, cxx = 0.f, cyy = 0.f, cxy = 0.f;
+                float2 ab = make_float2(0.f, 0.f), sq = ab;
+                float cxy = 0.f;
 #pragma unroll
                 for (int d = 0; d < LWIN; ++d) {
-                    const float x = xv[o + d], y = yv[o + d], w = K.g[d];
-                    a = fmaf(w, x, a);
-                    b = fmaf(w, y, b);
-                    cxx = fmaf(w * x, x, cxx);
-                    cyy = fmaf(w * y, y, cyy);
-                    cxy = fmaf(w * x, y, cxy);
+                    const float2 w = make_float2(K.g[d], K.g[d]), v = xy[o + d];
+                    const float2 wv = __fmul2_rn(w, v);
+                    ab = __ffma2_rn(w, v, ab);
+                    sq = __ffma2_rn(wv, v, sq);
+                    cxy = fmaf(wv.x, v.y, cxy);
                 }
                 const int q = r * MO_W + j0 + o;
-                sH[0 * IN_H * MO_W + q] = a;
-                sH[1 * IN_H * MO_W + q] = b;
-                sH[2 * IN_H * MO_W + q] = cxx;
-                sH[3 * IN_H * MO_W + q] = cyy;
-                sH[4 * IN_H * MO_W + q] = cxy;
+                sH01[q] = ab;
+                sH23[q] = sq;
+                sH4[q] = cxy;
             }
         }
         __syncthreads();
@@ -122,23 +129,27 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
         for (int i = t; i < MO_W * VSEG; i += 256) {
             const int j = i % MO_W, r0 = (i / MO_W) * VR;
             const int nr = min(VR, MO_H - r0);
-            float m[VR][5];
+            float2 mab[VR], msq[VR];
+            float mxy[VR];
 #pragma unroll
-            for (int o = 0; o < VR; ++o)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) m[o][q] = 0.f;
+            for (int o = 0; o < VR; ++o) {
+                mab[o] = msq[o] = make_float2(0.f, 0.f);
+                mxy[o] = 0.f;
+            }
 #pragma unroll
             for (int d = 0; d < VR + LWIN - 1; ++d) {
                 if (r0 + d >= IN_H) break;
-                float hv[5];
-#pragma unroll
-                for (int q = 0; q < 5; ++q) hv[q] = sH[q * IN_H * MO_W + (r0 + d) * MO_W + j];
+                const int q = (r0 + d) * MO_W + j;
+                const float2 hab = sH01[q], hsq = sH23[q];
+                const float hxy = sH4[q];
 #pragma unroll
                 for (int o = 0; o < VR; ++o) {
                     const int tap = d - o;
                     if (tap >= 0 && tap < LWIN) {
-#pragma unroll
-                        for (int q = 0; q < 5; ++q) m[o][q] = fmaf(K.g[tap], hv[q], m[o][q]);
+                        const float2 w = make_float2(K.g[tap], K.g[tap]);
+                        mab[o] = __ffma2_rn(w, hab, mab[o]);
+                        msq[o] = __ffma2_rn(w, hsq, msq[o]);
+                        mxy[o] = fmaf(K.g[tap], hxy, mxy[o]);
                     }
                 }
             }
@@ -149,8 +160,8 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
                 const int gx = x0 - LRAD + j, gy = y0 - LRAD + r;
                 float co[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                    const float mu = m[o][0], mt = m[o][1];
-                    const float var = m[o][2] - mu * mu, vart = m[o][3] - mt * mt, cov = m[o][4] - mu * mt;
+                    const float mu = mab[o].x, mt = mab[o].y;
+                    const float var = msq[o].x - mu * mu, vart = msq[o].y - mt * mt, cov = mxy[o] - mu * mt;
                     const float f0 = 2.f * mu * mt + K.c1, f1 = 2.f * cov + K.c2;
                     const float f2 = mu * mu + mt * mt + K.c1, f3 = var + vart + K.c2;
                     const float D = f2 * f3, N = f0 * f1;
@@ -168,29 +179,30 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
                     if (j >= LRAD && j < LRAD + LT_W && r >= LRAD && r < LRAD + LT_H) lsacc += 1.0 - (double)(N * iD);
                 }
 #pragma unroll
-                for (int q = 0; q < 8; ++q) sK[q * MO_H * MO_W + r * MO_W + j] = co[q];
+                for (int qq = 0; qq < 4; ++qq)
+                    sK2[qq * MO_H * MO_W + r * MO_W + j] = make_float2(co[2 * qq], co[2 * qq + 1]);
             }
         }
         __syncthreads();
-        // horizontal correlation of the coefficient maps (w for A, B, C; w^2
-        // for the rest), CR consecutive outputs of a row per thread
+        // horizontal correlation of the coefficient pair planes, CR
+        // consecutive outputs of a row per thread
         constexpr int CR = 8, CSEG = LT_W / CR;   // 32 = 4 x 8
-        for (int i = t; i < 8 * MO_H * CSEG; i += 256) {
-            const int q = i / (MO_H * CSEG), rem = i % (MO_H * CSEG);
+        for (int i = t; i < 4 * MO_H * CSEG; i += 256) {
+            const int qq = i / (MO_H * CSEG), rem = i % (MO_H * CSEG);
             const int r = rem / CSEG, j0 = (rem % CSEG) * CR;
-            const float *src = sK + q * MO_H * MO_W + r * MO_W + j0;
-            float v[CR + LWIN - 1];
+            const float2 *src = sK2 + qq * MO_H * MO_W + r * MO_W + j0;
+            float2 v[CR + LWIN - 1];
 #pragma unroll
             for (int d = 0; d < CR + LWIN - 1; ++d) v[d] = src[d];
-            float wt[LWIN];
+            float2 wt[LWIN];
 #pragma unroll
-            for (int d = 0; d < LWIN; ++d) wt[d] = (q < 3) ? K.g[d] : K.g2[d];
+            for (int d = 0; d < LWIN; ++d) wt[d] = cw(qq, d);
 #pragma unroll
             for (int o = 0; o < CR; ++o) {
-                float acc = 0.f;
+                float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int d = 0; d < LWIN; ++d) acc = fmaf(wt[d], v[o + d], acc);
-                sHC[q * MO_H * LT_W + r * LT_W + j0 + o] = acc;
+                for (int d = 0; d < LWIN; ++d) acc = __ffma2_rn(wt[d], v[o + d], acc);
+                sHC2[qq * MO_H * LT_W + r * LT_W + j0 + o] = acc;
             }
         }
         __syncthreads();
@@ -199,20 +211,20 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
         constexpr int OR = 2, OSEG = LT_H / OR;   // 16 = 8 x 2
         for (int i = t; i < LT_W * OSEG; i += 256) {
             const int j = i % LT_W, r0 = (i / LT_W) * OR;
-            float v[OR][8];
+            float2 v2[OR][4];
 #pragma unroll
             for (int o = 0; o < OR; ++o)
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[o][q] = 0.f;
+                for (int qq = 0; qq < 4; ++qq) v2[o][qq] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int d = 0; d < OR + LWIN - 1; ++d) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float hv = sHC[q * MO_H * LT_W + (r0 + d) * LT_W + j];
+                for (int qq = 0; qq < 4; ++qq) {
+                    const float2 hv = sHC2[qq * MO_H * LT_W + (r0 + d) * LT_W + j];
 #pragma unroll
                     for (int o = 0; o < OR; ++o) {
                         const int tap = d - o;
-                        if (tap >= 0 && tap < LWIN) v[o][q] = fmaf(q < 3 ? K.g[tap] : K.g2[tap], hv, v[o][q]);
+                        if (tap >= 0 && tap < LWIN) v2[o][qq] = __ffma2_rn(cw(qq, tap), hv, v2[o][qq]);
                     }
                 }
             }
@@ -225,7 +237,8 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
             float x = __ldg(img + p), y = __ldg(tgt + p);   // sanitised as in the staging pass
             x = isfinite(x) ? x : 0.f;
             y = isfinite(y) ? y : 0.f;
-            const float *vo = v[o];
+            const float vo[8] = {v2[o][0].x, v2[o][0].y, v2[o][1].x, v2[o][1].y,
+                                 v2[o][2].x, v2[o][2].y, v2[o][3].x, v2[o][3].y};
             const float dS = vo[0] + y * vo[1] + x * vo[2];
             const float d2S = vo[3] + x * vo[4] + y * vo[5] + x * y * vo[6] + x * x * vo[7] + vo[2];
             eo[p] = K.scale * (x - y) - K.lam * K.scale * dS;
