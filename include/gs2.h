@@ -366,12 +366,14 @@ gs2_status gs2_mlp_adam(float *master, uint16_t *w_bf16, const float *partial, c
  *   view_lanes:  1 (default): a sweep runs the views of each group
  *                concurrently on streams of the context (one per secondary);
  *                0: one after another on the caller's stream
- *   accum_px:    pixels per thread of the position-group accumulation: 4
- *                (default with 16x16 tiles; a warp per 8x16 column of the
- *                tile, one warp reduction of the payload per 128 pixels, two
- *                warps per tile) or 2 (a warp per 8x8 block, one reduction
- *                per 64 pixels; the only choice with 8x8 tiles and in
- *                deterministic mode).  Same sums, added in another order.
+ *   accum_px:    pixels per thread of the position- and colour-group
+ *                accumulations: 4 (default with 16x16 tiles; a warp per 8x16
+ *                column of the tile, one warp reduction of the payload per
+ *                128 pixels, two warps per tile) or 2 (a warp per 8x8 block,
+ *                one reduction per 64 pixels; the only choice with 8x8 tiles
+ *                and in deterministic mode).  The rotation, scaling and
+ *                opacity groups always take 2.  Same sums, added in another
+ *                order.
  * gs2_autotune times `reps` sweeps with primary t for every candidate
  * (sort_blocks 296, 592, 888 x sort_rows 2, 4, 8, 16 at the current accum_px,
  * then the other accum_px at the best of those; view_lanes kept) on a scratch
