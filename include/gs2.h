@@ -323,14 +323,40 @@ gs2_status gs2_step_records(gs2_ctx *ctx, gs2_group group, const void *blocks, i
  * after the step was applied; fills row 9 of the pending records. */
 gs2_status gs2_step_labels(gs2_ctx *ctx, gs2_group group, const void *blocks_after, int32_t n_views,
                            const gs2_scene *scene, const void *step, float *records, gs2_stream stream);
-/* gs2_sweep of the plain method (an installed step model is not used) that
+/* gs2_sweep of the plain method (installed networks are not used) that
  * also logs every group's records, labelled by the loss over all ncam views
  * at full resolution (every view is accumulated before and after the step;
  * all cameras must fit the context).  records: device float
- * [5][GS2_REC_ROWS][n] out.  The scene ends as after gs2_sweep. */
+ * [5][GS2_REC_ROWS][n] out.  records_damping (may be NULL): device float
+ * [5][GS2_REC_ROWS][n] out, the damping network's records (see
+ * gs2_set_damping_model); the first call that passes it allocates the
+ * labels' scratch (so it is not for stream capture).  The scene ends as
+ * after gs2_sweep. */
 gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                             const float *const *targets, const int32_t *knn, int32_t t, float *records,
-                            double *losses_out, int32_t *n_failed, gs2_stream stream);
+                            float *records_damping, double *losses_out, int32_t *n_failed, gs2_stream stream);
+
+/* Learned damping (an extension; the paper is silent on damping, Sec. 4.2).
+ * A second network of the same shape, layout and features maps a Gaussian's
+ * plain damped step to a multiplier rho = 10^(3 (alpha - 1)) in (1e-3, 1e3)
+ * of the damping mu0 (alpha = 2 sigmoid(y)); for the position, scaling and
+ * colour groups, whose damping turns the step and not only shortens it,
+ * gs2_solve_step and gs2_sweep then solve again with mu0 rho (the rotation
+ * and opacity blocks are 1 x 1: there damping and step scale coincide).  The
+ * plain solve's rho stays 1 where the features are unusable or alpha is not
+ * finite.  An installed step-scale network then scales the re-solved step.
+ * Its records (gs2_sweep_logged) carry the step records' features and phi0
+ * and, in row 9, the label 1 + log10(rho*) / 3, rho* the multiplier among
+ * 10^-3, ..., 10^3 whose step (the same damped solve, trust radii and bounds)
+ * has the smallest quadratic model of the loss over every training view,
+ * Q(d) = g_all . d + 1/2 d^T H_all d (the group's blocks accumulated over
+ * every view at full resolution before the step; smallest rho on ties); -1
+ * where the step record is unusable, no candidate has Q < 0, or the group's
+ * damping is not learned.  It is trained with gs2_mlp_grad (labels) and
+ * gs2_mlp_adam like the step-scale network.
+ * Install (device, GS2_MLP_NPARAM BF16 words, read at every solve; the caller
+ * keeps it alive) or remove (NULL). */
+gs2_status gs2_set_damping_model(gs2_ctx *ctx, const uint16_t *w_bf16);
 
 /* Network training and evaluation on record buffers made of chunks
  * [GS2_REC_ROWS][chunk_n] (row j of record i at

@@ -35,6 +35,11 @@ Definitions (g, H: a Gaussian's group block; d: its plain damped step):
           s_c = 1 / sum |phi0| over the usable records of the record's chunk
   Adam    m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
           p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+  damping a second network of the same shape gives rho = 10^(3 (alpha - 1)),
+          the multiplier of damping_mu0 in a second solve (position, scaling,
+          colour); its label is 1 + log10(rho*) / 3, rho* in 10^-3 .. 10^3
+          minimising Q(d) = g_all . d + 1/2 d^T H_all d over the candidate
+          steps, g_all, H_all the blocks over every training view
 """
 from __future__ import annotations
 
@@ -324,6 +329,74 @@ def learned_step(group, g, H, d, scene, cfg, p, g_primary=None):
     return np.where(ok, out.reshape(d.shape), d)
 
 
+# ---------------------------------------------------------------- learned damping
+DAMP_GROUPS = (O.POS, O.SCALE, O.COLOR)   # damping turns these steps, not only shortens them
+RHO_GRID = tuple(10.0 ** j for j in range(-3, 4))
+
+
+def quad_model(group, g, H, d, S):
+    """Q(d) = g . d + 1/2 d^T H d per Gaussian (oracle block layouts)."""
+    gv, Hm, dv = _as_vectors(group, g, H, d, S)
+    return np.einsum("ni,ni->n", gv, dv) + 0.5 * np.einsum("ni,nij,nj->n", dv, Hm, dv)
+
+
+def damping_records(group, g, H, rec, scene, primary, g_all, H_all, cfg, return_q=False):
+    """The damping network's records: the step records' features and phi0
+    (rows 0-8 of rec) and the label 1 + log10(rho*) / 3, rho* the multiplier of
+    damping_mu0 among 10^-3 .. 10^3 (ascending; the first of equal values)
+    whose step -- O.solve of the local blocks g, H with mu0 rho -- has the
+    smallest Q over the all-view blocks g_all, H_all; -1 where the step record
+    is unusable, no candidate has Q < 0, or the group is not in DAMP_GROUPS.
+    return_q: also the candidates' Q [len(RHO_GRID)][n] (None if no label)."""
+    cfg = O.default_config(**(cfg or {}))
+    sc = O.scene_handle(scene)
+    n, S = sc.n, O.sh_count(sc.sh_degree)
+    out = np.zeros((REC_ROWS, n))
+    out[:NF + 1] = rec[:NF + 1]
+    out[NF + 1] = -1.0
+    if group not in DAMP_GROUPS or cfg["gd_lr"][group] > 0:
+        return (out, None) if return_q else out
+    best_q = np.full(n, np.inf)
+    best_rho = np.ones(n)
+    qs = []
+    for rho in RHO_GRID:
+        cj = dict(cfg, damping_mu0=cfg["damping_mu0"] * rho)
+        d = O.solve(group, sc, primary, g, H, cj)["step"]
+        q = quad_model(group, g_all, H_all, d, S)
+        q = np.where(np.isfinite(q), q, np.inf)
+        qs.append(q)
+        better = q < best_q
+        best_q = np.where(better, q, best_q)
+        best_rho = np.where(better, rho, best_rho)
+    ok = (rec[NF + 1] >= 0) & (best_q < 0)
+    out[NF + 1] = np.where(ok, np.clip(1.0 + np.log10(best_rho) / 3.0, 0.0, 2.0), -1.0)
+    return (out, np.stack(qs)) if return_q else out
+
+
+def damped_step(group, g, H, d, scene, primary, cfg, p_damp, g_primary=None):
+    """The learned-damping step: rho = 10^(3 (alpha - 1)) from the network
+    p_damp on the plain step d's record (1 where the record is unusable or
+    the group is not in DAMP_GROUPS), then O.solve with damping_mu0 rho per
+    Gaussian (one solve per Gaussian's own multiplier)."""
+    cfg = O.default_config(**(cfg or {}))
+    sc = O.scene_handle(scene)
+    n = sc.n
+    d = np.asarray(d, np.float64)
+    if group not in DAMP_GROUPS:
+        return d.copy(), np.ones(n)
+    rec = step_records(group, g, H, d, sc, cfg, g_primary)
+    ok = rec[NF + 1] >= 0
+    a, _ = mlp_forward(p_damp, np.where(ok[:, None], rec[:NF].T, 0.0))
+    rho = np.where(ok & np.isfinite(a), 10.0 ** (3.0 * (a - 1.0)), 1.0)
+    out = np.zeros_like(d)
+    for r in np.unique(rho):
+        cj = dict(cfg, damping_mu0=cfg["damping_mu0"] * r)
+        st = O.solve(group, sc, primary, g, H, cj)["step"]
+        sel = rho == r
+        out[..., sel] = st[..., sel]
+    return out, rho
+
+
 # ---------------------------------------------------------------- logged sweep
 def _views(cams, targets, knn_table, t, cfg):
     K, f = cfg["knn_k"], cfg["downsample"]
@@ -348,26 +421,34 @@ def _blocks(group, scene, views, primary, cfg):
     return ob
 
 
-def sweep_logged(scene, cams, targets, knn_table, t, cfg):
+def sweep_logged(scene, cams, targets, knn_table, t, cfg, damping=False):
     """The oracle's sweep (same order as O.sweep) logging every group's
     records; labels from the loss over every training view at full
-    resolution.  Returns (scene handle, records [5][REC_ROWS][n])."""
+    resolution.  Returns (scene handle, records [5][REC_ROWS][n]) and, with
+    damping, the damping records [5][REC_ROWS][n] third (damping == "q": a
+    list of damping_records(..., return_q=True) pairs instead)."""
     cfg = O.default_config(**(cfg or {}))
     cur = O.scene_handle(scene)
     views = _views(cams, targets, knn_table, t, cfg)
     every = [(c, np.asarray(targets[v], np.float64)) for v, c in enumerate(cams)]
     primary = cams[t]
     S = O.sh_count(cur.sh_degree)
-    recs = []
+    recs, drecs = [], []
     for group in O.GROUPS:
         ob = _blocks(group, cur, views, primary, cfg)
         gp = _blocks(group, cur, views[:1], primary, cfg)["g"]
         st = O.solve(group, cur, primary, ob["g"], ob["H"], cfg)
         d = st["step"]
         rec = step_records(group, ob["g"], ob["H"], d, cur, cfg, gp)
-        phi0 = phi(group, _blocks(group, cur, every, primary, cfg)["g"], d)
+        ball = _blocks(group, cur, every, primary, cfg)
+        phi0 = phi(group, ball["g"], d)
+        if damping:
+            drecs.append(damping_records(group, ob["g"], ob["H"], rec, cur, primary, ball["g"], ball["H"], cfg,
+                                         return_q=damping == "q"))
         nxt = O.apply(group, cur, primary, d, cfg)
         g_after = _blocks(group, nxt, every, primary, cfg)["g"]
         recs.append(step_labels(group, g_after, d, rec, S, phi0=phi0))
         cur = nxt
+    if damping:
+        return cur, np.stack(recs), (drecs if damping == "q" else np.stack(drecs))
     return cur, np.stack(recs)

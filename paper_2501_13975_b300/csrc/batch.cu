@@ -262,6 +262,7 @@ static uint64_t sweep_key(const gs2_ctx *c, const gs2_scene *scene, const gs2_ca
     fnv(h, &n_failed, sizeof(n_failed));
     fnv(h, &c->cfg, sizeof(c->cfg));
     fnv(h, &c->mlp_w, sizeof(c->mlp_w));
+    fnv(h, &c->damp_w, sizeof(c->damp_w));
     fnv(h, &c->nb_sort, sizeof(c->nb_sort));
     fnv(h, &c->sort_rows, sizeof(c->sort_rows));
     fnv(h, &c->view_lanes, sizeof(c->view_lanes));

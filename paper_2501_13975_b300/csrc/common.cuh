@@ -195,6 +195,14 @@ struct gs2_ctx {
     uint32_t *d_status;
     uint8_t *flags;              // [max_n] per-Gaussian flags (FP64 re-solve of the colour block)
     const void *mlp_w;           // installed step-scale network (BF16, caller-owned) or NULL
+    const void *damp_w;          // installed damping network (BF16, caller-owned) or NULL
+    float *d_rho;                // [max_n] per-Gaussian damping multipliers of the learned damping
+    // logged damping labels (allocated by the first gs2_sweep_logged that asks for them)
+    void *lg_bloc;               // the group's local blocks (the views it was solved from)
+    void *lg_ball;               // the group's blocks summed (colour: one slot per view) over every training view
+    void *lg_step2;              // a candidate step
+    float *lg_bq, *lg_brho;      // [max_n] best quadratic-model value so far and its multiplier
+    size_t lg_ball_bytes, lg_bloc_bytes;
     float *g_prim;               // [3][max_n] gradient rows right after the view-slot-0 accumulation
     float *lg_phi;               // [max_n] phi1 accumulator of the logged sweep
     uint32_t *order_cache;       // [1 + knn_k][max_n] depth orders of a sweep's views (reused while means are fixed)
@@ -253,9 +261,10 @@ cudaError_t launch_loss(const float *image, const float *target, int w, int h, c
 cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st);
+// rho: per-Gaussian multiplier of the damping mu0 (the learned damping), or NULL
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st,
-                         unsigned long long *resolves);
+                         unsigned long long *resolves, const float *rho = nullptr);
 cudaError_t launch_apply(int group, const void *step, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, cudaStream_t st);
 cudaError_t launch_downsample(const float *in, int w, int h, int f, float *out, cudaStream_t st);
@@ -270,7 +279,7 @@ bool cfg_ok(const gs2_config *c, std::string &err);
 // one sweep on ctx (gs2_sweep / gs2_sweep_logged; records may be NULL)
 gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                      const float *const *targets, const int32_t *knn, int32_t t, float *records, double *losses_out,
-                     int32_t *n_failed, cudaStream_t stream);
+                     int32_t *n_failed, cudaStream_t stream, float *records_damp = nullptr);
 cudaError_t launch_step_records(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
                                 const float *gp, const gs2_config &cfg, float *rec, cudaStream_t st);
 cudaError_t launch_step_labels(int group, const void *blocks_after, int n_views, const DevScene &sc,
@@ -279,6 +288,19 @@ cudaError_t launch_phi_add(int group, const void *blocks_one_view, const DevScen
                            cudaStream_t st);
 cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, const DevScene &sc, void *step,
                                  const float *gp, const gs2_config &cfg, const void *w, cudaStream_t st);
+// learned damping: the groups whose damping changes the step's direction
+__host__ __device__ constexpr bool damping_learned(int group) {
+    return group == GS2_POS || group == GS2_SCALE || group == GS2_COLOR;
+}
+cudaError_t launch_learned_damping(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
+                                   const float *gp, const gs2_config &cfg, const void *w, float *rho,
+                                   cudaStream_t st);
+cudaError_t launch_damp_eval(int group, const void *blocks_all, int n_all, const DevScene &sc, const void *step,
+                             const gs2_config &cfg, float rho_j, float *best_q, float *best_rho, int first,
+                             cudaStream_t st);
+cudaError_t launch_damp_labels(int group, const float *rec, const float *best_q, const float *best_rho, int n,
+                               float *rec_damp, cudaStream_t st);
+cudaError_t launch_add_floats(float *dst, const float *src, size_t count, cudaStream_t st);
 cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t st);
 
 // --------------------------------------------------------------------------

@@ -138,6 +138,7 @@ static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->sort_state, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->d_resolves, c->flags, c->g_prim, c->lg_phi,
+                    c->d_rho, c->lg_bloc, c->lg_ball, c->lg_step2, c->lg_bq, c->lg_brho,
                     c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list, c->tile_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -266,6 +267,7 @@ extern "C" gs2_status gs2_create(gs2_ctx **out, const gs2_config *cfg, int64_t m
     A((void **)&c->flags, (size_t)max_n);
     A((void **)&c->g_prim, sizeof(float) * 3 * (size_t)max_n);
     A((void **)&c->lg_phi, sizeof(float) * (size_t)max_n);
+    A((void **)&c->d_rho, sizeof(float) * (size_t)max_n);
     A((void **)&c->order_cache, sizeof(uint32_t) * (size_t)(1 + K) * max_n);
     if (ok) ok = cudaMemset(c->zbuf, 0, sizeof(double) * GS2_ZPOS * (size_t)max_n) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(uint32_t) * 4) == cudaSuccess;
@@ -499,6 +501,27 @@ extern "C" gs2_status gs2_accum_newton_blocks(gs2_ctx *ctx, gs2_group group, con
                     (cudaStream_t)stream);
 }
 
+// The plain damped solve, then the installed networks: the damping network
+// (position, scaling, colour) solves again with its per-Gaussian multiplier of
+// mu0, the step-scale network scales the result.  With a damping network the
+// plain solve counts neither failures nor FP64 re-solves (the second one does).
+gs2_status solve_learned(gs2_ctx *ctx, int group, const void *blocks, int n_views, const gs2_scene *scene,
+                         const gs2_camera *primary, void *step, int32_t *n_failed, cudaStream_t st) {
+    const DevScene dsc = make_devscene(scene);
+    const DevCam pc = make_devcam(primary);
+    const bool damp = ctx->damp_w && damping_learned(group) && ctx->cfg.gd_lr[group] <= 0.f;
+    RET_CUDA(ctx, launch_solve(group, blocks, n_views, dsc, pc, ctx->cfg, step, damp ? nullptr : n_failed, ctx->flags,
+                               st, damp ? nullptr : ctx->d_resolves));
+    if (damp) {
+        RET_CUDA(ctx, launch_learned_damping(group, blocks, n_views, dsc, step, ctx->g_prim, ctx->cfg, ctx->damp_w,
+                                             ctx->d_rho, st));
+        RET_CUDA(ctx, launch_solve(group, blocks, n_views, dsc, pc, ctx->cfg, step, n_failed, ctx->flags, st,
+                                   ctx->d_resolves, ctx->d_rho));
+    }
+    RET_CUDA(ctx, launch_learned_scale(group, blocks, n_views, dsc, step, ctx->g_prim, ctx->cfg, ctx->mlp_w, st));
+    return GS2_OK;
+}
+
 extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *blocks, int32_t n_views,
                                      const gs2_scene *scene, const gs2_camera *primary, void *step, int32_t *n_failed,
                                      gs2_stream stream) {
@@ -508,10 +531,13 @@ extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *
     TRY(check_cam(ctx, primary));
     REQUIRE(ctx, blocks && step, GS2_ERR_ARG, "null buffer");
     REQUIRE(ctx, n_views >= 1, GS2_ERR_ARG, "n_views must be >= 1");
-    RET_CUDA(ctx, launch_solve(group, blocks, n_views, make_devscene(scene), make_devcam(primary), ctx->cfg, step,
-                               n_failed, ctx->flags, (cudaStream_t)stream, ctx->d_resolves));
-    RET_CUDA(ctx, launch_learned_scale(group, blocks, n_views, make_devscene(scene), step, ctx->g_prim, ctx->cfg,
-                                       ctx->mlp_w, (cudaStream_t)stream));
+    TRY(solve_learned(ctx, group, blocks, n_views, scene, primary, step, n_failed, (cudaStream_t)stream));
+    return GS2_OK;
+}
+
+extern "C" gs2_status gs2_set_damping_model(gs2_ctx *ctx, const uint16_t *w_bf16) {
+    if (!ctx) return GS2_ERR_ARG;
+    ctx->damp_w = w_bf16;
     return GS2_OK;
 }
 
@@ -621,7 +647,7 @@ extern "C" gs2_status gs2_camera_knn(const float *centres, int32_t ncam, const f
 // are logged (the step model is then not applied)
 gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                              const float *const *targets, const int32_t *knn, int32_t t, float *records,
-                             double *losses_out, int32_t *n_failed, cudaStream_t stream) {
+                             double *losses_out, int32_t *n_failed, cudaStream_t stream, float *records_damp) {
     TRY(check_scene(ctx, scene));
     REQUIRE(ctx, cams && targets && ncam >= 1 && t >= 0 && t < ncam, GS2_ERR_ARG, "bad cameras or primary index");
     const int K = ctx->cfg.knn_k, f = ctx->cfg.downsample;
@@ -682,8 +708,8 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         // direction through the unmoved centre)
         REQUIRE(ctx, !records, GS2_ERR_UNSUPPORTED, "the logged sweep runs the groups in series");
         REQUIRE(ctx, ctx->jb_mem != nullptr, GS2_ERR_ARG, "group_jacobi is set but its buffers are missing");
-        REQUIRE(ctx, ctx->mlp_w == nullptr, GS2_ERR_UNSUPPORTED,
-                "the step-scale network is trained on the in-series sweep; remove it for group_jacobi");
+        REQUIRE(ctx, ctx->mlp_w == nullptr && ctx->damp_w == nullptr, GS2_ERR_UNSUPPORTED,
+                "the learned networks are trained on the in-series sweep; remove them for group_jacobi");
         const DevScene dsc = make_devscene(scene);
         for (int g = 0; g < 5; ++g)
             RET_CUDA(ctx, cudaMemsetAsync(ctx->jb_blocks[g], 0, blocks_bytes_impl(g, scene->n, scene->sh_degree, nv),
@@ -807,21 +833,31 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
         // a non-position pass stored or reused the views' depth orders; the
         // position step about to be applied invalidates them
         order_valid = group != GS2_POS;
-        RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, make_devscene(scene), make_devcam(primary), ctx->cfg,
-                                   ctx->sw_step, n_failed, ctx->flags, st, ctx->d_resolves));
         float *rec = records ? records + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;
         const DevScene dsc = make_devscene(scene);
         if (!rec) {
-            RET_CUDA(ctx, launch_learned_scale(group, ctx->sw_blocks, nv, dsc, ctx->sw_step, ctx->g_prim, ctx->cfg,
-                                               ctx->mlp_w, st));
+            TRY(solve_learned(ctx, group, ctx->sw_blocks, nv, scene, primary, ctx->sw_step, n_failed, st));
             RET_CUDA(ctx, launch_apply(group, ctx->sw_step, dsc, make_devcam(primary), ctx->cfg, st));
             continue;
         }
+        RET_CUDA(ctx, launch_solve(group, ctx->sw_blocks, nv, dsc, make_devcam(primary), ctx->cfg, ctx->sw_step,
+                                   n_failed, ctx->flags, st, ctx->d_resolves));
         // logged: records of the plain step, then the label loss (every view,
         // full resolution) along the step before and after it is applied
         RET_CUDA(ctx, launch_step_records(group, ctx->sw_blocks, nv, dsc, ctx->sw_step, ctx->g_prim, ctx->cfg, rec,
                                           st));
+        float *recd = records_damp ? records_damp + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;
+        const bool dlab = recd && damping_learned(group) && ctx->cfg.gd_lr[group] <= 0.f;
         const size_t b1 = blocks_bytes_impl(group, scene->n, scene->sh_degree, 1);
+        if (dlab) {   // the local blocks, kept for the candidate solves; the all-view sum starts at 0
+            RET_CUDA(ctx, cudaMemcpyAsync(ctx->lg_bloc, ctx->sw_blocks,
+                                          blocks_bytes_impl(group, scene->n, scene->sh_degree, nv),
+                                          cudaMemcpyDeviceToDevice, st));
+            RET_CUDA(ctx, cudaMemsetAsync(ctx->lg_ball, 0,
+                                          blocks_bytes_impl(group, scene->n, scene->sh_degree,
+                                                            group == GS2_COLOR ? ncam : 1),
+                                          st));
+        }
         for (int pass = 0; pass < 2; ++pass) {
             float *phi = pass == 0 ? rec + (size_t)GS2_MLP_NFEAT * scene->n : ctx->lg_phi;
             RET_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(float) * scene->n, st));
@@ -832,6 +868,30 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
                 TRY(do_accum(ctx, group, scene, &cams[v], primary, ctx->sw_proj, ctx->sw_rstate, ctx->sw_image,
                              targets[v], 0, ctx->sw_blocks, nullptr, st, false));
                 RET_CUDA(ctx, launch_phi_add(group, ctx->sw_blocks, dsc, ctx->sw_step, phi, st));
+                if (pass == 0 && dlab) {   // sum of the views' blocks (colour: view v in slot v)
+                    if (group == GS2_COLOR)
+                        RET_CUDA(ctx, cudaMemcpyAsync((char *)ctx->lg_ball + (size_t)v * b1, ctx->sw_blocks, b1,
+                                                      cudaMemcpyDeviceToDevice, st));
+                    else
+                        RET_CUDA(ctx, launch_add_floats((float *)ctx->lg_ball, (const float *)ctx->sw_blocks,
+                                                        b1 / sizeof(float), st));
+                }
+            }
+            if (pass == 0 && recd) {   // damping labels: candidate steps of the same solve, scored on the all-view model
+                if (dlab) {
+                    gs2_config cj = ctx->cfg;
+                    for (int j = 0; j < 7; ++j) {
+                        const float rj = exp10f((float)(j - 3));
+                        cj.damping_mu0 = ctx->cfg.damping_mu0 * rj;
+                        RET_CUDA(ctx, launch_solve(group, ctx->lg_bloc, nv, dsc, make_devcam(primary), cj,
+                                                   ctx->lg_step2, nullptr, ctx->flags, st, nullptr));
+                        RET_CUDA(ctx, launch_damp_eval(group, ctx->lg_ball, group == GS2_COLOR ? ncam : 1, dsc,
+                                                       ctx->lg_step2, ctx->cfg, rj, ctx->lg_bq, ctx->lg_brho, j == 0,
+                                                       st));
+                    }
+                }
+                RET_CUDA(ctx, launch_damp_labels(group, rec, dlab ? ctx->lg_bq : nullptr, ctx->lg_brho, scene->n,
+                                                 recd, st));
             }
             if (pass == 0)
                 RET_CUDA(ctx, launch_apply(group, ctx->sw_step, dsc, make_devcam(primary), ctx->cfg, st));
@@ -851,10 +911,38 @@ extern "C" gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera
 
 extern "C" gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int32_t ncam,
                                        const float *const *targets, const int32_t *knn, int32_t t, float *records,
-                                       double *losses_out, int32_t *n_failed, gs2_stream stream) {
+                                       float *records_damping, double *losses_out, int32_t *n_failed,
+                                       gs2_stream stream) {
     if (!ctx) return GS2_ERR_ARG;
     REQUIRE(ctx, records != nullptr, GS2_ERR_ARG, "records is null");
-    return sweep_run(ctx, scene, cams, ncam, targets, knn, t, records, losses_out, n_failed, (cudaStream_t)stream);
+    if (records_damping) {   // scratch of the damping labels, sized for this scene and camera count
+        TRY(check_scene(ctx, scene));
+        REQUIRE(ctx, ncam >= 1, GS2_ERR_ARG, "bad camera count");
+        const int n = scene->n, sh = scene->sh_degree, nv = 1 + ctx->cfg.knn_k;
+        size_t ball = 0, bloc = 0;
+        for (int g = 0; g < 5; ++g) {
+            ball = std::max(ball, blocks_bytes_impl(g, n, sh, g == GS2_COLOR ? ncam : 1));
+            bloc = std::max(bloc, blocks_bytes_impl(g, n, sh, nv));
+        }
+        if (ball > ctx->lg_ball_bytes || bloc > ctx->lg_bloc_bytes || !ctx->lg_bq) {
+            RET_CUDA(ctx, cudaDeviceSynchronize());
+            void *ptrs[] = {ctx->lg_ball, ctx->lg_bloc, ctx->lg_step2, ctx->lg_bq, ctx->lg_brho};
+            for (void *p : ptrs)
+                if (p) cudaFree(p);
+            ctx->lg_ball = ctx->lg_bloc = ctx->lg_step2 = nullptr;
+            ctx->lg_bq = ctx->lg_brho = nullptr;
+            ctx->lg_ball_bytes = ctx->lg_bloc_bytes = 0;
+            RET_CUDA(ctx, cudaMalloc(&ctx->lg_ball, ball));
+            RET_CUDA(ctx, cudaMalloc(&ctx->lg_bloc, bloc));
+            RET_CUDA(ctx, cudaMalloc(&ctx->lg_step2, ctx->sw_step_bytes));
+            RET_CUDA(ctx, cudaMalloc((void **)&ctx->lg_bq, sizeof(float) * (size_t)ctx->max_n));
+            RET_CUDA(ctx, cudaMalloc((void **)&ctx->lg_brho, sizeof(float) * (size_t)ctx->max_n));
+            ctx->lg_ball_bytes = ball;
+            ctx->lg_bloc_bytes = bloc;
+        }
+    }
+    return sweep_run(ctx, scene, cams, ncam, targets, knn, t, records, losses_out, n_failed, (cudaStream_t)stream,
+                     records_damping);
 }
 
 extern "C" uint64_t gs2_launch_count(void) { return g_gs2_launches.load(); }

@@ -35,6 +35,7 @@
 //   W1 [64][8], b1 [64], W2 [64][64], b2 [64], W3 [64], b3
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -361,6 +362,112 @@ cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, con
     if (sc.n == 0 || !w) return cudaSuccess;
     k_learned_scale<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks, n_views, sc, (float *)step,
                                                        gp, cfg, (const __nv_bfloat16 *)w);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- learned damping
+// A second network of the same shape and the same features predicts, for the
+// position, scaling and colour groups (whose damping turns the step, not only
+// lengthens it), a multiplier rho of the damping mu0 of the Gaussian's solve:
+// rho = 10^(3 (alpha - 1)) in (1e-3, 1e3), alpha = 2 sigmoid(y).  The solve is
+// then repeated with mu0 rho.  Its records share the step records' features
+// and phi0; the label (row 9) is alpha_rho* = 1 + log10(rho*) / 3 with rho*
+// the multiplier, among 10^-3 .. 10^3, whose damped step (same solve, trust
+// radii and bounds) minimises the quadratic model of the loss over every
+// training view, Q(d) = g_all . d + 1/2 d^T H_all d; -1 where the step record
+// is unusable, no candidate lowers Q, or the group's damping is not learned.
+__device__ __forceinline__ float rho_of(float a) { return exp10f(3.f * (a - 1.f)); }
+
+__global__ void __launch_bounds__(128) k_learned_damping(int group, const float *__restrict__ B, int n_views,
+                                                         DevScene sc, const float *__restrict__ step,
+                                                         const float *__restrict__ gp, gs2_config cfg,
+                                                         const __nv_bfloat16 *__restrict__ w, float *__restrict__ rho) {
+    __shared__ __align__(16) float sw[NPARAM + 3];
+    load_weights(sw, w);
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= sc.n) return;
+    const float smax = smax_of(sc, k);
+    const StepStats st = step_stats(group, B, n_views, sc, k, step, gp, cfg, smax);
+    float f[NF];
+    float r = 1.f;
+    if (step_features(group, st, sc.opacity[k], smax, f)) {
+        const float a = scale_of(mlp_eval(sw, f));
+        if (isfinite(a)) r = rho_of(a);
+    }
+    rho[k] = r;
+}
+
+// Q of a candidate step (the damping multiplier rho_j) from the all-view
+// blocks; the smallest Q so far and its multiplier are kept (first: set)
+__global__ void __launch_bounds__(128) k_damp_eval(int group, const float *__restrict__ Ball, int n_all, DevScene sc,
+                                                   const float *__restrict__ step, gs2_config cfg, float rho_j,
+                                                   float *__restrict__ best_q, float *__restrict__ best_rho,
+                                                   int first) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= sc.n) return;
+    // g_p is not used by Q: the all-view blocks stand in for it
+    const StepStats st = step_stats(group, Ball, n_all, sc, k, step, Ball, cfg, smax_of(sc, k));
+    float q = st.gd + 0.5f * st.q;
+    if (!isfinite(q)) q = INFINITY;
+    if (first || q < best_q[k]) {
+        best_q[k] = q;
+        best_rho[k] = rho_j;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_damp_labels(int group, const float *__restrict__ rec,
+                                                     const float *__restrict__ best_q,
+                                                     const float *__restrict__ best_rho, int n,
+                                                     float *__restrict__ rec_d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+#pragma unroll
+    for (int i = 0; i <= NF; ++i) rec_d[(size_t)i * n + k] = rec[(size_t)i * n + k];   // features, phi0
+    float lab = -1.f;
+    if (damping_learned(group) && best_q && rec[(size_t)(NF + 1) * n + k] >= 0.f && best_q[k] < 0.f)
+        lab = fminf(fmaxf(1.f + log10f(best_rho[k]) * (1.f / 3.f), 0.f), 2.f);
+    rec_d[(size_t)(NF + 1) * n + k] = lab;
+    rec_d[(size_t)(NF + 2) * n + k] = 0.f;
+}
+
+__global__ void k_add_floats(float *__restrict__ dst, const float *__restrict__ src, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] += src[i];
+}
+
+cudaError_t launch_learned_damping(int group, const void *blocks, int n_views, const DevScene &sc, const void *step,
+                                   const float *gp, const gs2_config &cfg, const void *w, float *rho,
+                                   cudaStream_t st) {
+    if (sc.n == 0 || !w) return cudaSuccess;
+    k_learned_damping<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks, n_views, sc,
+                                                         (const float *)step, gp, cfg, (const __nv_bfloat16 *)w, rho);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damp_eval(int group, const void *blocks_all, int n_all, const DevScene &sc, const void *step,
+                             const gs2_config &cfg, float rho_j, float *best_q, float *best_rho, int first,
+                             cudaStream_t st) {
+    if (sc.n == 0) return cudaSuccess;
+    k_damp_eval<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks_all, n_all, sc,
+                                                   (const float *)step, cfg, rho_j, best_q, best_rho, first);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damp_labels(int group, const float *rec, const float *best_q, const float *best_rho, int n,
+                               float *rec_damp, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_damp_labels<<<(n + 127) / 128, 128, 0, st>>>(group, rec, best_q, best_rho, n, rec_damp);
+    GS2_COUNT_LAUNCH(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_floats(float *dst, const float *src, size_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    k_add_floats<<<(unsigned)std::min<size_t>((count + 255) / 256, 148 * 8), 256, 0, st>>>(dst, src, count);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

@@ -154,10 +154,12 @@ __device__ __forceinline__ void pos_reduce(const DevCam &pr, const float p[3], c
 // 1e6 (or whose FP32 ladder failed) is solved again with its basis,
 // reduction, factorisation and step all in FP64.
 __global__ void k_solve_pos(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries, float trust,
-                            float *step, int32_t *nfail, int prec, unsigned long long *resolves) {
+                            float *step, int32_t *nfail, int prec, unsigned long long *resolves,
+                            const float *__restrict__ rho) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
+    if (rho) mu0 *= rho[k];   // learned per-Gaussian damping multiplier
     const float p[3] = {sc.mean[k], sc.mean[n + k], sc.mean[2 * n + k]};
     const float g[3] = {B[k], B[n + k], B[2 * n + k]};
     const float h00 = B[3 * n + k], h01 = B[4 * n + k], h02 = B[5 * n + k], h11 = B[6 * n + k], h12 = B[7 * n + k],
@@ -296,10 +298,11 @@ __device__ __forceinline__ bool scale_reduce(const DevCam &pr, const float p[3],
 // reduction, factorisation and step in FP64.
 __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ B, float mu0, int tries,
                               float near_z, float trust, float *step, int32_t *nfail, int prec,
-                              unsigned long long *resolves) {
+                              unsigned long long *resolves, const float *__restrict__ rho) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
+    if (rho) mu0 *= rho[k];   // learned per-Gaussian damping multiplier
     const float g[3] = {B[k], B[n + k], B[2 * n + k]};
     float Hs[6];
     bool zero = g[0] == 0.f && g[1] == 0.f && g[2] == 0.f;
@@ -340,11 +343,13 @@ __global__ void k_solve_scale(DevScene sc, DevCam pr, const float *__restrict__ 
 }
 
 __global__ void k_solve_color(DevScene sc, const float *__restrict__ B, int n_views, float mu0, int tries,
-                              float trust, float *step, int32_t *nfail, int prec, unsigned long long *resolves) {
+                              float trust, float *step, int32_t *nfail, int prec, unsigned long long *resolves,
+                              const float *__restrict__ rho) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n, S = sc.S;
     if (idx >= 3 * n) return;
     const int ch = idx / n, k = idx % n;
+    if (rho) mu0 *= rho[k];   // learned per-Gaussian damping multiplier
     float H[GS2_MAX_SH * GS2_MAX_SH], g[GS2_MAX_SH], x[GS2_MAX_SH];
     for (int i = 0; i < S * S; ++i) H[i] = 0.f;
     for (int i = 0; i < S; ++i) g[i] = 0.f;
@@ -570,10 +575,12 @@ __device__ __forceinline__ void load_color_slots(const float *__restrict__ B, in
 template <int S>
 __global__ void __launch_bounds__(128) k_solve_color_qr(DevScene sc, const float *__restrict__ B, int n_views,
                                                         float mu0, int tries, float trust, float *step,
-                                                        int32_t *nfail, int prec, uint8_t *flags) {
+                                                        int32_t *nfail, int prec, uint8_t *flags,
+                                                        const float *__restrict__ rho) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
+    if (rho) mu0 *= rho[k];   // learned per-Gaussian damping multiplier
     float a[QR_VMAX][3], s[QR_VMAX][3], b[QR_VMAX][S];
     load_color_slots<S>(B, n, k, n_views, a, s, b);
     float out[3][S], kappa[3];
@@ -598,12 +605,13 @@ template <int S>
 __global__ void __launch_bounds__(64) k_solve_color_qr64(DevScene sc, const float *__restrict__ B, int n_views,
                                                          float mu0, int tries, float trust, float *step,
                                                          int32_t *nfail, const uint8_t *__restrict__ flags,
-                                                         unsigned long long *resolves) {
+                                                         unsigned long long *resolves, const float *__restrict__ rho) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sc.n;
     if (k >= n) return;
     const unsigned redo = flags[k];
     if (!redo) return;
+    if (rho) mu0 *= rho[k];   // learned per-Gaussian damping multiplier
     float a[QR_VMAX][3], s[QR_VMAX][3], b[QR_VMAX][S];
     load_color_slots<S>(B, n, k, n_views, a, s, b);
     float out[3][S], kappa[3];
@@ -674,7 +682,7 @@ __global__ void k_solve_gradient(int group, DevScene sc, const float *__restrict
 
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st,
-                         unsigned long long *resolves) {
+                         unsigned long long *resolves, const float *rho) {
     unsigned long long *rs = resolves ? resolves + group : nullptr;
     const int n = sc.n;
     if (n == 0) return cudaSuccess;
@@ -689,7 +697,7 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
     switch (group) {
     case GS2_POS:
         k_solve_pos<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_pos, s,
-                                       n_failed, cfg.precision, rs);
+                                       n_failed, cfg.precision, rs, rho);
         break;
     case GS2_ROT:
         k_solve_scalar<<<g, 256, 0, st>>>(n, B, cfg.damping_mu0, cfg.damping_tries, cfg.trust_rot, s, n_failed,
@@ -697,7 +705,7 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
         break;
     case GS2_SCALE:
         k_solve_scale<<<g, 256, 0, st>>>(sc, primary, B, cfg.damping_mu0, cfg.damping_tries, cfg.near_z,
-                                         cfg.scale_trust, s, n_failed, cfg.precision, rs);
+                                         cfg.scale_trust, s, n_failed, cfg.precision, rs, rho);
         break;
     case GS2_OPACITY:
         k_solve_opacity<<<g, 256, 0, st>>>(sc, B, cfg.damping_mu0, cfg.damping_tries, cfg.barrier_alpha,
@@ -710,11 +718,11 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
 #define QR(SS)                                                                                                    \
     do {                                                                                                          \
         k_solve_color_qr<SS><<<gq, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,              \
-                                                 cfg.trust_color, s, n_failed, prec, flags);                      \
+                                                 cfg.trust_color, s, n_failed, prec, flags, rho);                 \
         if (prec)                                                                                                 \
             k_solve_color_qr64<SS><<<(n + 63) / 64, 64, 0, st>>>(sc, B, n_views, cfg.damping_mu0,                 \
                                                                  cfg.damping_tries, cfg.trust_color, s, n_failed, \
-                                                                 flags, rs);                                      \
+                                                                 flags, rs, rho);                                 \
     } while (0)
             switch (sc.S) {
             case 1: QR(1); break;
@@ -725,7 +733,7 @@ cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevSc
 #undef QR
         } else {
             k_solve_color<<<(3 * n + 127) / 128, 128, 0, st>>>(sc, B, n_views, cfg.damping_mu0, cfg.damping_tries,
-                                                              cfg.trust_color, s, n_failed, cfg.precision, rs);
+                                                              cfg.trust_color, s, n_failed, cfg.precision, rs, rho);
         }
     }
     GS2_COUNT_LAUNCH(1);

@@ -95,8 +95,9 @@ _sigs = {
     "gs2_sweep": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
                             C.c_int32, _vp, _vp, _vp]),
     "gs2_sweep_logged": (C.c_int, [_vp, C.POINTER(Scene_), C.POINTER(Camera_), C.c_int32, C.POINTER(_vp), _vp,
-                                   C.c_int32, _vp, _vp, _vp, _vp]),
+                                   C.c_int32, _vp, _vp, _vp, _vp, _vp]),
     "gs2_set_step_model": (C.c_int, [_vp, _vp]),
+    "gs2_set_damping_model": (C.c_int, [_vp, _vp]),
     "gs2_step_records": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), _vp, _vp, _vp]),
     "gs2_step_labels": (C.c_int, [_vp, C.c_int, _vp, C.c_int32, C.POINTER(Scene_), _vp, _vp, _vp]),
     "gs2_mlp_forward": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp]),
@@ -374,8 +375,9 @@ class Context:
                                 _ptr(losses), _ptr(n_failed), _stream(stream)), "gs2_sweep")
 
     def sweep_logged(self, scene: DeviceScene, cams, targets, knn, t, records=None, losses=None, n_failed=None,
-                     stream=None):
-        """Plain sweep that logs the records of every group: float [5][REC_ROWS][n]."""
+                     stream=None, records_damping=None):
+        """Plain sweep that logs the records of every group: float [5][REC_ROWS][n]
+        (and, with records_damping, the damping network's records of the same shape)."""
         if records is None:
             records = torch.empty((5, REC_ROWS, scene.n), dtype=torch.float32, device="cuda")
         arr = (Camera_ * len(cams))(*[camera_struct(c) for c in cams])
@@ -383,9 +385,16 @@ class Context:
         kt = np.ascontiguousarray(knn, np.int32)
         s = scene.struct()
         self._ok(_lib.gs2_sweep_logged(self.h, C.byref(s), arr, len(cams), tp, kt.ctypes.data_as(_vp), int(t),
-                                       _ptr(records), _ptr(losses), _ptr(n_failed), _stream(stream)),
+                                       _ptr(records), _ptr(records_damping), _ptr(losses), _ptr(n_failed),
+                                       _stream(stream)),
                  "gs2_sweep_logged")
         return records
+
+    def set_damping_model(self, w_bf16):
+        """Install (a device int16/uint16 tensor of MLP_NPARAM BF16 words, kept
+        alive by this context) or remove (None) the damping network."""
+        self._damping_model = w_bf16
+        self._ok(_lib.gs2_set_damping_model(self.h, _ptr(w_bf16)), "gs2_set_damping_model")
 
     def set_step_model(self, w_bf16):
         """Install (a device int16/uint16 tensor of MLP_NPARAM BF16 words, kept

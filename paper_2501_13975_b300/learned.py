@@ -9,6 +9,9 @@ the calls.  See include/gs2.h for the record format and the features.
     model = StepModel(seed=20)
     model.fit(recs, epochs=3)
     ctx.set_step_model(model.w)                    # every later solve uses it
+
+The damping network is a StepModel trained on the damping records (labels
+objective) and installed with ctx.set_damping_model.
 """
 from __future__ import annotations
 
@@ -48,7 +51,7 @@ class RecordSet:
 
 
 def collect_records(seeds, kind: str = "tiny", sweeps: int = 1, n: int | None = None, size: int | None = None,
-                    ncam: int | None = None, sd: float = 0.02, ctx=None, stream=None) -> RecordSet:
+                    ncam: int | None = None, sd: float = 0.02, ctx=None, stream=None, damping: bool = False):
     """Records of the plain method, `sweeps` logged sweeps per seed.
 
     kind "tiny": n (1000) Gaussians in [-1,1]^3, SH degree 0, 4 ring cameras
@@ -59,7 +62,9 @@ def collect_records(seeds, kind: str = "tiny", sweeps: int = 1, n: int | None = 
       training starts from a copy with means moved by N(0, sd^2), every second
       seed in the initialised state (grey colour, opacity 0.1, jittered
       scales).
-    Primaries: a seeded permutation of the cameras per seed."""
+    Primaries: a seeded permutation of the cameras per seed.
+    damping: also the damping network's records; returns (steps, damping)
+    RecordSets."""
     seeds = list(seeds)
     if kind == "tiny":
         n, size, ncam, sh = n or 1000, size or 128, 4, 0
@@ -72,6 +77,7 @@ def collect_records(seeds, kind: str = "tiny", sweeps: int = 1, n: int | None = 
     if own:
         ctx = gs2.Context(n, size, size, sh, 64 * n)
     out = torch.empty((len(seeds), sweeps, 5, gs2.REC_ROWS, n), dtype=torch.float32, device="cuda")
+    outd = torch.empty_like(out) if damping else None
     centres = np.stack([c.center() for c in cams]).astype(np.float32)
     proj = ctx.proj_buffer(n)
     for i, s in enumerate(seeds):
@@ -95,10 +101,13 @@ def collect_records(seeds, kind: str = "tiny", sweeps: int = 1, n: int | None = 
         knn = gs2.camera_knn(centres, sphere, 3)
         order = np.random.Generator(np.random.PCG64(s)).permutation(ncam)
         for j in range(sweeps):
-            ctx.sweep_logged(ds, cams, targets, knn, int(order[j % ncam]), records=out[i, j], stream=stream)
+            ctx.sweep_logged(ds, cams, targets, knn, int(order[j % ncam]), records=out[i, j], stream=stream,
+                             records_damping=None if outd is None else outd[i, j])
     if own:
         torch.cuda.synchronize()
         ctx.check()
+    if damping:
+        return RecordSet(out.reshape(-1), n), RecordSet(outd.reshape(-1), n)
     return RecordSet(out.reshape(-1), n)
 
 

@@ -1,0 +1,160 @@
+"""Learned damping on the GPU against the FP64 oracle (oracle/learned.py):
+the second solve with a per-Gaussian multiplier of the damping inside
+gs2_solve_step, and the damping records of the logged sweep (features and
+phi0 shared with the step records; labels from the candidate steps' quadratic
+model over every training view)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import learned as Lr  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2501_13975_b300 import synth  # noqa: E402
+from tests.gpu_common import ambiguous_gaussians, oracle_cfg  # noqa: E402
+
+
+def _setup(gs2, group, seed=60, n=1500):
+    """GPU and oracle blocks of one group over 4 views (primary plus 3
+    downsampled secondaries) of a tiny scene, the plain GPU step and the
+    Gaussians to compare (no ambiguous compositing decision, a contributing
+    pixel, a successful oracle solve)."""
+    sh = 3 if group == O.COLOR else 0
+    sc = synth.tiny_scene(n=n, seed=seed, sh_degree=sh)
+    if sh:
+        sc.sh[:, 1:, :] = np.random.default_rng(seed + 1).normal(0, 0.1, sc.sh[:, 1:, :].shape).astype(np.float32)
+    cams = synth.ring_cameras(4, 128)
+    gt = synth.perturbed(sc, seed=seed + 2, sd=0.05)
+    ctx = gs2.Context(sc.n, 128, 128, 3)
+    ocfg = oracle_cfg(ctx.config)
+    primary = cams[0]
+    ds = gs2.DeviceScene.from_host(sc)
+    blocks = ctx.blocks_buffer(group, sc.n, sh, 4)
+    ob, gp, amb = None, None, None
+    for slot in range(4):
+        cam = primary if slot == 0 else O.downsample_camera(cams[slot], 2)
+        cam = synth.Camera(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy,
+                           np.asarray(cam.viewmat, np.float32))
+        tgt = O.render(gt, cam, ocfg)["image"].astype(np.float32)
+        proj = ctx.project(ds, cam)
+        img, rs = ctx.raster_fwd(ds, cam, proj)
+        ctx.accum(group, ds, cam, primary, proj, rs, img, torch.tensor(tgt, device="cuda"), slot, blocks)
+        r = O.render(sc, cam, ocfg)
+        L = O.loss(r["image"], tgt, ocfg)
+        ob = O.accum(group, sc, cam, primary, L["e"], L["h"], ocfg, out=ob)
+        if slot == 0:
+            gp = np.array(ob["g"], copy=True)
+        a, _ = ambiguous_gaussians(O, sc, cam, ocfg, r["margin"], thresh=2e-5, dilate=10)
+        amb = a if amb is None else (amb | a)
+    plain = ctx.solve(group, blocks, 4, ds, primary)
+    os_ = O.solve(group, sc, primary, ob["g"], ob["H"], ocfg)
+    st_ok = (os_["status"] == 0).all(0) if group == O.COLOR else (os_["status"] == 0)
+    keep = ~amb & (ob["npix"] > 0) & st_ok
+    return dict(ctx=ctx, ds=ds, blocks=blocks, primary=primary, sc=sc, ocfg=ocfg, ob=ob, gp=gp, os=os_,
+                keep=keep, plain=plain, n=sc.n)
+
+
+def _rel(got, ref, n, keep):
+    g2, r2 = got.reshape(-1, n), ref.reshape(-1, n)
+    nr = np.maximum(np.linalg.norm(r2, axis=0), 1e-12)
+    return (np.linalg.norm(g2 - r2, axis=0) / nr)[keep]
+
+
+@pytest.mark.parametrize("group", [0, 2, 4])
+def test_constant_damping_network_equals_solve_with_scaled_mu0(group):
+    """A network with zero weights and output bias b gives one alpha = 2
+    sigmoid(b), rho = 10^(3 (alpha - 1)) = 10^1.5 for every usable record:
+    gs2_solve_step's second solve equals the oracle's solve with damping_mu0
+    rho, and the steps are shorter than the plain ones (more damping)."""
+    from paper_2501_13975_b300 import gs2
+    c = _setup(gs2, group)
+    n, ctx = c["n"], c["ctx"]
+    bits = np.zeros(Lr.NPARAM, np.uint16)
+    u = int(np.float32(np.log(3.0)).view(np.uint32))   # b3 = ln 3 in BF16 (1.1015625): alpha = 1.5012
+    bits[Lr.OFF_B3] = np.uint16(((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF)
+    pw = Lr.bf16_to_f64(bits)
+    w = torch.tensor(bits.astype(np.int16), device="cuda")
+    ctx.set_damping_model(w)
+    got = ctx.solve(group, c["blocks"], 4, c["ds"], c["primary"]).cpu().numpy()
+    ctx.set_damping_model(None)
+    torch.cuda.synchronize()
+    ctx.check()
+    ref, rho = Lr.damped_step(group, c["ob"]["g"], c["ob"]["H"], c["os"]["step"], c["sc"], c["primary"], c["ocfg"],
+                              pw, c["gp"])
+    keep = c["keep"] & (rho != 1.0)
+    assert keep.sum() >= 100, keep.sum()
+    a = 2.0 / (1.0 + np.exp(-pw[Lr.OFF_B3]))
+    assert np.allclose(rho[rho != 1.0], 10.0 ** (3.0 * (a - 1.0)))
+    err = _rel(got[: ref.size], ref, n, keep)
+    assert np.quantile(err, 0.99) <= 5e-3, np.quantile(err, 0.99)
+    plain = c["plain"].cpu().numpy()[: ref.size].reshape(-1, n)
+    shorter = np.linalg.norm(got[: ref.size].reshape(-1, n), axis=0) <= np.linalg.norm(plain, axis=0) * (1 + 1e-6)
+    assert shorter[keep].mean() >= 0.9   # blocks the damping ladder raised can differ
+
+
+@pytest.mark.parametrize("group", [0, 2])
+def test_damping_network_per_gaussian_matches_oracle(group):
+    """A random network: rho differs per Gaussian; the second solve matches
+    the oracle's per-Gaussian solves with damping_mu0 rho_k."""
+    from paper_2501_13975_b300 import gs2
+    c = _setup(gs2, group, seed=61, n=600)
+    n, ctx = c["n"], c["ctx"]
+    _, bits = synth.mlp_init(62, out_scale=2.0)
+    pw = Lr.bf16_to_f64(bits)
+    ctx.set_damping_model(torch.tensor(bits.astype(np.int16), device="cuda"))
+    got = ctx.solve(group, c["blocks"], 4, c["ds"], c["primary"]).cpu().numpy()
+    ctx.set_damping_model(None)
+    torch.cuda.synchronize()
+    ctx.check()
+    ref, rho = Lr.damped_step(group, c["ob"]["g"], c["ob"]["H"], c["os"]["step"], c["sc"], c["primary"], c["ocfg"],
+                              pw, c["gp"])
+    keep = c["keep"] & (rho != 1.0)
+    assert keep.sum() >= 50 and np.std(np.log10(rho[keep])) > 0.05
+    err = _rel(got[: ref.size], ref, n, keep)
+    assert np.quantile(err, 0.98) <= 1e-2, np.quantile(err, 0.98)
+
+
+def test_logged_damping_records_match_oracle():
+    """gs2_sweep_logged's damping records: rows 0-8 are the step records'
+    own; the labels match the oracle's logged sweep wherever the oracle's best
+    candidate beats the runner-up by 1% of its |Q| (elsewhere two multipliers
+    are equally good and either is a valid label); every GPU label is one of
+    the grid's values or -1; rotation and opacity carry no label."""
+    from paper_2501_13975_b300 import gs2
+    sc = synth.tiny_scene(n=300, seed=63)
+    gt = synth.perturbed(sc, seed=64, sd=0.05)
+    cams = synth.ring_cameras(4, 64)
+    ctx = gs2.Context(sc.n, 64, 64, 0)
+    ocfg = oracle_cfg(ctx.config)
+    tg_np = np.stack([O.render(gt, c, ocfg)["image"] for c in cams]).astype(np.float32)
+    targets = [torch.tensor(x, device="cuda") for x in tg_np]
+    centres = np.stack([c.center() for c in cams])
+    knn, _ = O.knn(centres, O.bounding_sphere(sc), 3)
+    t = 1
+    a = gs2.DeviceScene.from_host(sc)
+    recd = torch.empty((5, Lr.REC_ROWS, sc.n), dtype=torch.float32, device="cuda")
+    rec = ctx.sweep_logged(a, cams, targets, knn, t, records_damping=recd)
+    torch.cuda.synchronize()
+    ctx.check()
+    grec, gd = rec.cpu().numpy(), recd.cpu().numpy()
+    _, _, od = Lr.sweep_logged(sc, cams, tg_np.astype(np.float64), knn, t, ocfg, damping="q")
+    grid = 1.0 + np.log10(np.asarray(Lr.RHO_GRID)) / 3.0
+    for group in range(5):
+        assert np.array_equal(gd[group][:Lr.NF + 1], grec[group][:Lr.NF + 1]), group
+        lab = gd[group][Lr.NF + 1]
+        valid = (lab == -1.0) | np.any(np.abs(lab[:, None] - grid[None, :]) < 1e-6, axis=1)
+        assert valid.all(), group
+        orec, q = od[group]
+        if group in (O.ROT, O.OPACITY):
+            assert np.all(lab == -1.0) and np.all(orec[Lr.NF + 1] == -1.0)
+            continue
+        both = (lab >= 0) & (orec[Lr.NF + 1] >= 0)
+        assert both.sum() >= 20, (group, both.sum())
+        qs = np.sort(q, axis=0)
+        margin = (qs[1] - qs[0]) / np.maximum(np.abs(qs[0]), 1e-30)
+        clear = both & (margin > 1e-2)
+        assert clear.sum() >= 10, (group, clear.sum())
+        agree = np.abs(lab[clear] - orec[Lr.NF + 1][clear]) < 1e-6
+        assert agree.mean() >= 0.95, (group, agree.mean())

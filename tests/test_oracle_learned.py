@@ -410,3 +410,90 @@ def test_chunk_scale():
     rec[1, Lr.NF + 1] = -1.0                       # no usable record
     s = Lr.chunk_scale(rec)
     assert s[0] == pytest.approx(0.25) and s[1] == 0.0
+
+
+# ---------------------------------------------------------------- learned damping
+def _iso_blocks(rng, n, h):
+    """Position blocks with H = h I (so the reduced 2x2 block is h I for any
+    basis of the plane) and random gradients."""
+    g = rng.normal(size=(3, n))
+    Hu = np.zeros((6, n))
+    Hu[0] = Hu[3] = Hu[5] = h
+    return g, Hu
+
+
+@pytest.mark.parametrize("mu0, c, want", [(1.0, 2.0, 1.0), (0.01, 2.0, 1.0 + 2.0 / 3.0),
+                                          (1.0, 1.0, 0.0), (0.1, 11.0, 1.0 + 2.0 / 3.0)])
+def test_damping_label_closed_form(mu0, c, want):
+    """H = h I, g_all = g, H_all = c h I: the damped step (h + mu h) d = -g
+    in the plane has Q = |g_v|^2 / h (c t^2 / 2 - t), t = 1 / (1 + mu),
+    minimal at t = 1 / c, i.e. mu = c - 1.  With mu = mu0 rho on the grid
+    10^-3 .. 10^3: rho* = (c - 1) / mu0 (label 1 + log10(rho*) / 3), and
+    for c = 1 (the exact Newton step is best) the smallest rho (label 0)."""
+    rng = np.random.default_rng(21)
+    n, h = 8, 2.5
+    sc = _scene_for(n)
+    g, Hu = _iso_blocks(rng, n, h)
+    cfg = O.default_config(damping_mu0=mu0, trust_pos=1e9)
+    cams = synth.ring_cameras(4, 32)
+    d = O.solve(O.POS, sc, cams[0], g, Hu, cfg)["step"]
+    rec = Lr.step_records(O.POS, g, Hu, d, sc, cfg)
+    out = Lr.damping_records(O.POS, g, Hu, rec, sc, cams[0], g, c * Hu, cfg)
+    assert np.array_equal(out[:Lr.NF + 1], rec[:Lr.NF + 1])
+    assert np.allclose(out[Lr.NF + 1], want, atol=1e-12), out[Lr.NF + 1]
+    # Q of the candidates, from the plane's closed form (not the oracle's Q)
+    sh = O.scene_handle(sc)
+    for k in range(n):
+        r = np.asarray(sh.mean, np.float64).reshape(3, n)[:, k] - cams[0].center()
+        r /= np.linalg.norm(r)
+        gv2 = np.sum(g[:, k] ** 2) - np.dot(g[:, k], r) ** 2       # |g_v|^2: g without its ray component
+        for rho in Lr.RHO_GRID:
+            t = 1.0 / (1.0 + mu0 * rho)
+            dk = O.solve(O.POS, sc, cams[0], g, Hu, dict(cfg, damping_mu0=mu0 * rho))["step"][:, k]
+            q = np.dot(g[:, k], dk) + 0.5 * c * h * np.dot(dk, dk)
+            assert q == pytest.approx(gv2 / h * (0.5 * c * t * t - t), rel=1e-9, abs=1e-14)
+
+
+def test_damping_records_unusable_and_other_groups():
+    """Rotation and opacity get no damping label (1 x 1 blocks: damping and
+    step scale coincide); an unusable step record stays unusable; a model
+    that no candidate lowers (Q >= 0) gives no label."""
+    rng = np.random.default_rng(22)
+    n = 6
+    sc = _scene_for(n)
+    cams = synth.ring_cameras(4, 32)
+    cfg = O.default_config(trust_pos=1e9)
+    g, Hu = _iso_blocks(rng, n, 1.0)
+    d = O.solve(O.POS, sc, cams[0], g, Hu, cfg)["step"]
+    rec = Lr.step_records(O.POS, g, Hu, d, sc, cfg)
+    rec[Lr.NF + 1, 0] = -1.0
+    out = Lr.damping_records(O.POS, g, Hu, rec, sc, cams[0], g, Hu, cfg)
+    assert out[Lr.NF + 1, 0] == -1.0 and np.all(out[Lr.NF + 1, 1:] == 0.0)
+    up = Lr.damping_records(O.POS, g, Hu, rec, sc, cams[0], -g, Hu, cfg)   # every candidate ascends Q
+    assert np.all(up[Lr.NF + 1] == -1.0)
+    go = rng.normal(size=(1, n))
+    ho = np.abs(rng.normal(size=(1, n))) + 0.1
+    for grp in (O.ROT, O.OPACITY):
+        do = O.solve(grp, sc, cams[0], go, ho, cfg)["step"]
+        r1 = Lr.step_records(grp, go, ho, do, sc, cfg)
+        assert np.all(Lr.damping_records(grp, go, ho, r1, sc, cams[0], go, ho, cfg)[Lr.NF + 1] == -1.0)
+
+
+def test_damped_step_constant_network():
+    """A network with zero weights and output bias b gives alpha = 2 sigmoid(b)
+    for every usable record, so rho is one value and the damped step equals
+    O.solve with damping_mu0 rho; unusable records keep rho = 1."""
+    rng = np.random.default_rng(23)
+    n = 10
+    sc = _scene_for(n)
+    cams = synth.ring_cameras(4, 32)
+    cfg = O.default_config(trust_pos=1e9)
+    g, Hu, d, _ = _pos_blocks(rng, n, mu=0.3)
+    d = O.solve(O.POS, sc, cams[0], g, Hu, cfg)["step"]
+    p = np.zeros(Lr.NPARAM)
+    p[Lr.OFF_B3] = np.log(1.5 / 0.5)              # alpha = 1.5: rho = 10^1.5
+    out, rho = Lr.damped_step(O.POS, g, Hu, d, sc, cams[0], cfg, p)
+    assert np.allclose(rho, 10.0 ** 1.5, rtol=1e-12)
+    want = O.solve(O.POS, sc, cams[0], g, Hu, dict(cfg, damping_mu0=10.0 ** 1.5))["step"]
+    assert np.allclose(out, want, rtol=1e-12, atol=0)
+    assert np.linalg.norm(out) < np.linalg.norm(d)   # more damping, shorter steps
