@@ -787,10 +787,11 @@ def gd_baseline(args):
 
 def time_to_psnr(args):
     """Time to PSNR on the object workload.  The plain FP32 path runs 30
-    sweeps (primaries in a seeded permutation, seed 5); the learned step scale
-    with the mixed-precision policy then runs from the same start until its
-    PSNR over all training views reaches the plain path's PSNR after 30
-    sweeps (at most --ttp-max sweeps).  Two starts: the workload's own (means
+    sweeps (primaries in a seeded permutation, seed 5); the learned paths
+    (step-scale network, damping network, both, each with the mixed-precision
+    policy; --ttp-paths) then run from the same start until their PSNR over
+    all training views reaches the plain path's PSNR after 30 sweeps (at most
+    --ttp-max sweeps).  Two starts: the workload's own (means
     perturbed, everything else exact) and the initialised state a training
     run starts from (grey colour, opacity 0.1, jittered scales).  Times are the
     sweeps' device time (CUDA events); PSNR is taken between sweeps, outside
@@ -809,28 +810,40 @@ def time_to_psnr(args):
 
     # ---- network: records of the plain method, then Adam
     t0 = time.perf_counter()
-    tiny = learned.collect_records(range(100, 100 + args.ttp_runs), kind="tiny")
-    shell = learned.collect_records(range(1000, 1000 + args.ttp_shell), kind="shell", sweeps=args.ttp_shell_sweeps)
+    tiny, tiny_d = learned.collect_records(range(100, 100 + args.ttp_runs), kind="tiny", damping=True)
+    shell, shell_d = learned.collect_records(range(1000, 1000 + args.ttp_shell), kind="shell",
+                                             sweeps=args.ttp_shell_sweeps, damping=True)
     torch.cuda.synchronize()
     t_collect = time.perf_counter() - t0
     parts = [r.split(0.1) for r in (tiny, shell)]
     train_sets = [p[0] for p in parts]
     held = [p[1] for p in parts]
+    dparts = [r.split(0.1) for r in (tiny_d, shell_d)]
     model = learned.StepModel(seed=20)
+    damp = learned.StepModel(seed=22)
     t0 = time.perf_counter()
     model.fit(train_sets, epochs=args.ttp_epochs, batch=16384, objective=args.ttp_objective)
+    damp.fit([p[0] for p in dparts], epochs=args.ttp_epochs, batch=16384, objective="labels", seed=23)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     held_stats = {}
-    for name, hs in zip(("tiny", "shell"), held):
+    for name, hs, hd in zip(("tiny", "shell"), held, [p[1] for p in dparts]):
         pl, cnt = learned.plain_loss(hs)
         nl, _ = model.loss(hs)
         pll, _ = learned.plain_loss(hs, objective="line")
         nll, _ = model.loss(hs, objective="line")
+        dpl, dcnt = learned.plain_loss(hd)        # rho = 1 (alpha = 1) against the damping labels
+        dnl, _ = damp.loss(hd)
+        dl = hd.labels().cpu().numpy()
+        dl = dl[dl >= 0]
         held_stats[name] = {"records": cnt, "label_loss_plain": round(pl, 5), "label_loss_network": round(nl, 5),
-                            "line_loss_plain": float(f"{pll:.5g}"), "line_loss_network": float(f"{nll:.5g}")}
+                            "line_loss_plain": float(f"{pll:.5g}"), "line_loss_network": float(f"{nll:.5g}"),
+                            "damping_records": dcnt, "damping_label_loss_plain": round(dpl, 5),
+                            "damping_label_loss_network": round(dnl, 5),
+                            "damping_label_histogram": {f"rho=1e{int(round(3 * (v - 1)))}": int(np.sum(
+                                np.abs(dl - v) < 1e-4)) for v in np.linspace(0.0, 2.0, 7)}}
 
-    def run(start_host, precision, use_model, max_sweeps, target_psnr=None, learned_trust=None):
+    def run(start_host, precision, use_model, max_sweeps, target_psnr=None, learned_trust=None, use_damp=False):
         lt = args.ttp_learned_trust if learned_trust is None else learned_trust
         ctx = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=precision, learned_trust=lt))
         gt = gs2.DeviceScene.from_host(gt_host)
@@ -847,6 +860,8 @@ def time_to_psnr(args):
         knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
         if use_model:
             ctx.set_step_model(model.w)
+        if use_damp:
+            ctx.set_damping_model(damp.w)
         evl = torch.zeros((ncam, 2), dtype=torch.float64, device="cuda")
 
         def psnr():
@@ -879,7 +894,7 @@ def time_to_psnr(args):
         ctx.check()
         return dict(psnr=curve, ms=ms_curve, reached=reached, sweeps=len(curve) - 1)
 
-    def first_sweep_ms(precision, use_model, reps=5):
+    def first_sweep_ms(precision, use_model, reps=5, use_damp=False):
         """Median device time of the first sweep from the workload's start,
         each repetition from a fresh copy of it: the cost of the network's
         inference and of the precision policy on one scene state (the runs
@@ -900,6 +915,8 @@ def time_to_psnr(args):
         knn = gs2.camera_knn(centres, sphere, ctx.config["knn_k"])
         if use_model:
             ctx.set_step_model(model.w)
+        if use_damp:
+            ctx.set_damping_model(damp.w)
         times = []
         for _ in range(reps + 1):
             scene = gs2.DeviceScene.from_host(spec_host)
@@ -926,31 +943,39 @@ def time_to_psnr(args):
         plain = run(host, 0, False, 30)
         target = plain["psnr"][30]
         runs = {"plain_fp32": plain}
-        for name, prec, use, lt in (("learned_mixed", 1, True, None), ("learned_fp32", 0, True, None),
-                                    ("learned_mixed_radii_x2", 1, True, 2.0), ("plain_mixed", 1, False, None)):
-            runs[name] = run(host, prec, use, max(args.ttp_max, 30), target, lt)
-        lm = runs["learned_mixed"]
+        # path: (precision, step-scale network, learned_trust, damping network)
+        paths = {"learned_mixed": (1, True, None, False), "learned_fp32": (0, True, None, False),
+                 "learned_mixed_radii_x2": (1, True, 2.0, False), "damping_mixed": (1, False, None, True),
+                 "damping_scale_mixed": (1, True, None, True), "plain_mixed": (1, False, None, False)}
+        for name in args.ttp_paths.split(","):
+            prec, use, lt, ud = paths[name]
+            runs[name] = run(host, prec, use, max(args.ttp_max, 30), target, lt, ud)
+        head_path = "damping_mixed" if "damping_mixed" in runs else "learned_mixed"
+        lm = runs[head_path]
         t_plain = plain["ms"][30] * 1e-3
         t_lm = lm["ms"][lm["reached"]] * 1e-3 if lm["reached"] is not None else None
         starts[sname] = {
             "initial_psnr_db": round(plain["psnr"][0], 4), "target_psnr_db": round(target, 4),
             "plain_fp32_seconds_30": round(t_plain, 5),
             "plain_diverges": bool(target < plain["psnr"][0]),
-            "learned_mixed_seconds": None if t_lm is None else round(t_lm, 5),
+            "headline_path": head_path,
+            "learned_seconds": None if t_lm is None else round(t_lm, 5),
             "speedup_vs_plain": None if not t_lm else round(t_plain / t_lm, 3),
             "runs": {k: summary(r) for k, r in runs.items()},
             "psnr_curves": {k: [round(x, 3) for x in r["psnr"]] for k, r in runs.items()},
         }
     head = starts["workload"]
-    first = {name: first_sweep_ms(prec, use) for name, prec, use in
-             (("plain_fp32", 0, False), ("learned_fp32", 0, True), ("plain_mixed", 1, False),
-              ("learned_mixed", 1, True))}
+    first = {name: first_sweep_ms(prec, use, use_damp=ud) for name, prec, use, ud in
+             (("plain_fp32", 0, False, False), ("learned_fp32", 0, True, False), ("plain_mixed", 1, False, False),
+              ("learned_mixed", 1, True, False), ("damping_mixed", 1, False, True),
+              ("damping_scale_mixed", 1, True, True))}
     result = {
         "metric": "time to PSNR vs plain FP32 path (object workload)",
-        "value": head["learned_mixed_seconds"], "unit": "s", "higher_is_better": False,
+        "value": head["learned_seconds"], "unit": "s", "higher_is_better": False,
         "starts": starts,
         "first_sweep_ms": first,
         "network": {"objective": args.ttp_objective, "learned_trust": args.ttp_learned_trust,
+                    "damping_objective": "labels (candidate rho minimising the all-view quadratic model)",
                     "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell, "shell_sweeps": args.ttp_shell_sweeps,
                     "records": tiny.n + shell.n,
                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
@@ -1140,6 +1165,9 @@ def main():
     ap.add_argument("--ttp-max", type=int, default=60)
     ap.add_argument("--ttp-learned-trust", type=float, default=1.0,
                     help="learned_trust of the learned paths (the learned step may reach this many trust radii)")
+    ap.add_argument("--ttp-paths", default="learned_mixed,damping_mixed,damping_scale_mixed,plain_mixed",
+                    help="paths run against the plain FP32 path: learned_mixed, learned_fp32, learned_mixed_radii_x2, "
+                         "damping_mixed, damping_scale_mixed, plain_mixed")
     ap.add_argument("--ttp-objective", default="line", choices=["line", "labels"],
                     help="training loss of the step-scale network")
     args = ap.parse_args()
