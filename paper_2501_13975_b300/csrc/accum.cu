@@ -306,12 +306,16 @@ __device__ __forceinline__ void pair_payload(PairState &ps, const float2 (&e)[3]
 // path weights die before the 27 geometric moments are formed.
 // gn (Gauss-Newton): the e-weighted second derivatives of the pixel colour
 // (e d2c/dz2 through the falloff, e d2c/dalpha dc~) are left out.
-template <int NPR>
+// hi(pl) is called once slots 32..47 (two of the cross-term channels and the
+// colour sums) are formed, lo(pl) once slots 0..31 are: the warp reduction of
+// the first part runs before the second part's moments exist, so fewer of the
+// 48 slots are live at once.
+template <int NPR, typename Hi, typename Lo>
 __device__ __forceinline__ void pos_pairs(PairState (&ps)[NPR], const float2 (&e)[NPR][3],
                                           const float2 (&h)[NPR][3], const float4 &A, const float4 &B,
                                           const float4 &C, const float2 (&al)[NPR], const float2 (&ap)[NPR],
                                           const bool (&lv)[NPR][2], float dx, const float2 (&dy)[NPR], bool gn,
-                                          float (&pl)[GS2_ZPOS]) {
+                                          float (&pl)[GS2_ZPOS], Hi &&hi, Lo &&lo) {
     float2 W1[NPR], W2[NPR], X[NPR][3], UX[NPR], UY[NPR];
     float2 sc[6];   // colour sums: w e_c, w^2 h_c
     const float2 dxv = f2(dx);
@@ -360,8 +364,7 @@ __device__ __forceinline__ void pos_pairs(PairState (&ps)[NPR], const float2 (&e
         XY[r] = mul2(UX[r], UY[r]);
         YY[r] = mul2(UY[r], UY[r]);
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {   // cross terms: X_c over (x, y, xx, xy, yy)
+    auto cross = [&](int c) {   // cross terms: X_c over (x, y, xx, xy, yy)
         float2 Xc[NPR];
 #pragma unroll
         for (int r = 0; r < NPR; ++r) Xc[r] = X[r][c];
@@ -370,7 +373,11 @@ __device__ __forceinline__ void pos_pairs(PairState (&ps)[NPR], const float2 (&e
         pl[27 + 5 * c + 2] = msum(Xc, XX);
         pl[27 + 5 * c + 3] = msum(Xc, XY);
         pl[27 + 5 * c + 4] = msum(Xc, YY);
-    }
+    };
+    cross(1);
+    cross(2);
+    hi(pl);   // slots 32..47
+    cross(0);
     {
         float2 s = W2[0];
 #pragma unroll
@@ -415,6 +422,7 @@ __device__ __forceinline__ void pos_pairs(PairState (&ps)[NPR], const float2 (&e
 #pragma unroll
     for (int r = 0; r < NPR; ++r) m[r] = mul2(YY[r], YY[r]);
     both(MY4, m);
+    lo(pl);   // slots 0..31
 }
 
 // DET (deterministic mode): no atomics.  Every list entry's payload is the
@@ -626,7 +634,22 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
                         }
                     }
                 }
-                pos_pairs<NPR>(pst, pe, ph, A, B, C, al, ap, lv, dx, dy, gn != 0, pl);
+                const uint32_t k = sId[buf][s];
+                pos_pairs<NPR>(
+                    pst, pe, ph, A, B, C, al, ap, lv, dx, dy, gn != 0, pl,
+                    [&](const float (&v)[P]) {
+                        if constexpr (DET)
+                            reduce_scatter_part<P - 32, 32, P, float, 16, true>(v, lane, nullptr, 0, 0u, row);
+                        else
+                            reduce_scatter_part<P - 32, 32, P, ACC>(v, lane, zbuf, n, k);
+                    },
+                    [&](const float (&v)[P]) {
+                        if constexpr (DET)
+                            reduce_scatter_part<32, 0, P, float, 16, true>(v, lane, nullptr, 0, 0u, row);
+                        else
+                            reduce_scatter_part<32, 0, P, ACC>(v, lane, zbuf, n, k);
+                    });
+                return;
             } else {
                 float2 pl2[P];
 #pragma unroll
