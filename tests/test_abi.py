@@ -94,3 +94,13 @@ def test_render_noalloc_refuses_a_bad_config_before_any_device_call():
         cfg = gs2._config_struct({field: value})
         st = lib.gs2_render_noalloc(C.byref(cfg), C.byref(scene), C.byref(cam), fake, fake, fake, None, None)
         assert st == 1, (field, value, st)   # GS2_ERR_ARG
+
+
+def test_model_setters_refuse_a_null_context():
+    """gs2_set_step_model and gs2_set_damping_model answer GS2_ERR_ARG for a
+    NULL context (host check, no device call)."""
+    import ctypes as C
+    from paper_2501_13975_b300 import gs2
+    for name in ("gs2_set_step_model", "gs2_set_damping_model"):
+        f = getattr(gs2._lib, name)
+        assert f(None, None) == 1, name
