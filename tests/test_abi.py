@@ -99,7 +99,6 @@ def test_render_noalloc_refuses_a_bad_config_before_any_device_call():
 def test_model_setters_refuse_a_null_context():
     """gs2_set_step_model and gs2_set_damping_model answer GS2_ERR_ARG for a
     NULL context (host check, no device call)."""
-    import ctypes as C
     from paper_2501_13975_b300 import gs2
     for name in ("gs2_set_step_model", "gs2_set_damping_model"):
         f = getattr(gs2._lib, name)
