@@ -1121,7 +1121,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v13"
+KERNEL_REV = "accum-v14"
 
 
 def main():
