@@ -196,6 +196,9 @@ struct gs2_ctx {
     uint8_t *flags;              // [max_n] per-Gaussian flags (FP64 re-solve of the colour block)
     const void *mlp_w;           // installed step-scale network (BF16, caller-owned) or NULL
     const void *damp_w;          // installed damping network (BF16, caller-owned) or NULL
+    void *lane_blocks;           // a view lane's own blocks of one view (allocated when a network is
+                                 // installed): its epilogue adds there, not into the shared blocks,
+                                 // so that the primary view's gradient is copied free of the others'
     float *d_rho;                // [max_n] per-Gaussian damping multipliers of the learned damping
     // logged damping labels (allocated by the first gs2_sweep_logged that asks for them)
     void *lg_bloc;               // the group's local blocks (the views it was solved from)

@@ -120,7 +120,8 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 // a view lane's own scratch (the rest is shared with its owner)
 static void free_lane(gs2_ctx *l) {
     void *ptrs[] = {l->keys[0], l->keys[1], l->vals[0], l->vals[1], l->ghist, l->sort_state, l->d_count, l->ranges,
-                    l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image, l->tile_order};
+                    l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image, l->tile_order,
+                    l->lane_blocks};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -535,14 +536,28 @@ extern "C" gs2_status gs2_solve_step(gs2_ctx *ctx, gs2_group group, const void *
     return GS2_OK;
 }
 
+// With a network installed, a sweep's view lanes add their epilogues into
+// blocks of their own (the primary's gradient, a network feature, is then
+// copied before any secondary contributes); allocated here, from the host.
+static gs2_status ensure_lane_blocks(gs2_ctx *ctx) {
+    const size_t bytes = blocks_bytes_impl(GS2_POS, ctx->max_n, ctx->max_sh, 1);   // the largest non-colour block
+    for (int i = 0; i < ctx->n_lanes; ++i) {
+        gs2_ctx *l = ctx->lanes[i];
+        if (l && !l->lane_blocks) RET_CUDA(ctx, cudaMalloc(&l->lane_blocks, bytes));
+    }
+    return GS2_OK;
+}
+
 extern "C" gs2_status gs2_set_damping_model(gs2_ctx *ctx, const uint16_t *w_bf16) {
     if (!ctx) return GS2_ERR_ARG;
+    if (w_bf16) TRY(ensure_lane_blocks(ctx));
     ctx->damp_w = w_bf16;
     return GS2_OK;
 }
 
 extern "C" gs2_status gs2_set_step_model(gs2_ctx *ctx, const uint16_t *w_bf16) {
     if (!ctx) return GS2_ERR_ARG;
+    if (w_bf16) TRY(ensure_lane_blocks(ctx));
     ctx->mlp_w = w_bf16;
     return GS2_OK;
 }
@@ -802,10 +817,20 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[0], st));
             for (int i = 1; i < nv; ++i) RET_CUDA(ctx, cudaStreamWaitEvent(ctx->lane_st[i - 1], ctx->lane_ev[0], 0));
         }
+        // with a network installed the lanes add into their own blocks (not the
+        // colour group, whose views have slots of their own), summed after the join
+        const bool own = lanes && (ctx->mlp_w || ctx->damp_w) && group != GS2_COLOR;
+        const size_t b1 = blocks_bytes_impl(group, scene->n, scene->sh_degree, 1);
         for (int i = 0; i < nv; ++i) {
             if (vid[i] < 0) continue;
             gs2_ctx *vc = (lanes && i > 0) ? ctx->lanes[i - 1] : ctx;
             cudaStream_t vs = (lanes && i > 0) ? ctx->lane_st[i - 1] : st;
+            void *dst = ctx->sw_blocks;
+            if (own && i > 0) {
+                REQUIRE(ctx, vc->lane_blocks != nullptr, GS2_ERR_ARG, "a view lane has no blocks of its own");
+                dst = vc->lane_blocks;
+                RET_CUDA(ctx, cudaMemsetAsync(dst, 0, b1, vs));
+            }
             // only the position group moves the means: a pass that is not the
             // position pass and finds no valid order sorts each view by depth and
             // keeps the order; the following passes reuse it (the same means and
@@ -818,7 +843,7 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
                                (!order_valid && group != GS2_POS) ? cache : nullptr);
             if (rc == GS2_OK)
                 rc = do_accum(vc, group, scene, &vcam[i], primary, vc->sw_proj, vc->sw_rstate, vc->sw_image, vtgt[i],
-                              i, ctx->sw_blocks, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, vs);
+                              i, dst, (i == 0 && losses_out) ? losses_out + 2 * group : nullptr, vs);
             if (rc != GS2_OK) {
                 if (vc != ctx) ctx->err = vc->err;
                 return rc;
@@ -829,6 +854,12 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
                 RET_CUDA(ctx, cudaEventRecord(ctx->lane_ev[i], ctx->lane_st[i - 1]));
                 RET_CUDA(ctx, cudaStreamWaitEvent(st, ctx->lane_ev[i], 0));
             }
+            if (own)
+                for (int i = 1; i < nv; ++i)
+                    if (vid[i] >= 0)
+                        RET_CUDA(ctx, launch_add_floats((float *)ctx->sw_blocks,
+                                                        (const float *)ctx->lanes[i - 1]->lane_blocks,
+                                                        b1 / sizeof(float), st));
         }
         // a non-position pass stored or reused the views' depth orders; the
         // position step about to be applied invalidates them
@@ -848,7 +879,6 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
                                           st));
         float *recd = records_damp ? records_damp + (size_t)group * GS2_REC_ROWS * scene->n : nullptr;
         const bool dlab = recd && damping_learned(group) && ctx->cfg.gd_lr[group] <= 0.f;
-        const size_t b1 = blocks_bytes_impl(group, scene->n, scene->sh_degree, 1);
         if (dlab) {   // the local blocks, kept for the candidate solves; the all-view sum starts at 0
             RET_CUDA(ctx, cudaMemcpyAsync(ctx->lg_bloc, ctx->sw_blocks,
                                           blocks_bytes_impl(group, scene->n, scene->sh_degree, nv),
