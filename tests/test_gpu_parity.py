@@ -266,6 +266,19 @@ def test_blocks_parity_position_pixels_per_thread(gs2, case, px):
     _check_blocks(r)
 
 
+@pytest.mark.parametrize("px", [2, 4])
+@pytest.mark.parametrize("case", [dict(lam=0.2, sh=1, n=700, size=90),
+                                  dict(lam=0.2, sh=3, secondary=True, n=1500, size=96)],
+                         ids=["ragged", "secondary-sh3"])
+def test_blocks_parity_colour_pixels_per_thread(gs2, case, px):
+    """The colour accumulation, which also follows accum_px: one pixel pair
+    per lane (a warp per 8x8 block) and two pairs (a warp per 8x16 column,
+    e and h staged in shared memory) against the oracle."""
+    r = _blocks_case(gs2, O.COLOR, tuning=dict(accum_px=px), **case)
+    assert r["ctx"].tuning()["accum_px"] == px
+    _check_blocks(r)
+
+
 @pytest.mark.parametrize("group", [0, 1, 2, 4])
 def test_blocks_parity_secondary_sh3(gs2, group):
     """Downsampled secondary view, primary-view axes, SH degree 3 colour path."""
