@@ -311,7 +311,12 @@ gs2_status gs2_sweep(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
 
 /* Install (device, GS2_MLP_NPARAM BF16 words, read at every solve; the caller
  * keeps it alive) or remove (NULL) the step-scale network: gs2_solve_step and
- * gs2_sweep then scale each step after the plain solve. */
+ * gs2_sweep then scale each step after the plain solve.  With a network
+ * installed (this one or the damping network) a sweep's view lanes add their
+ * epilogues into blocks of their own, summed after the join, so that the
+ * primary view's gradient (feature f4) is taken before any secondary adds to
+ * the blocks; the first install allocates those blocks (one view's blocks
+ * per lane), so it does not belong in a stream capture. */
 gs2_status gs2_set_step_model(gs2_ctx *ctx, const uint16_t *w_bf16);
 
 /* Records of the plain step: features and phi0 of step (from blocks, as
@@ -355,7 +360,8 @@ gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *ca
  * damping is not learned.  It is trained with gs2_mlp_grad (labels) and
  * gs2_mlp_adam like the step-scale network.
  * Install (device, GS2_MLP_NPARAM BF16 words, read at every solve; the caller
- * keeps it alive) or remove (NULL). */
+ * keeps it alive) or remove (NULL); installing allocates as
+ * gs2_set_step_model does. */
 gs2_status gs2_set_damping_model(gs2_ctx *ctx, const uint16_t *w_bf16);
 
 /* Network training and evaluation on record buffers made of chunks
