@@ -823,7 +823,8 @@ def time_to_psnr(args):
     damp = learned.StepModel(seed=22)
     t0 = time.perf_counter()
     model.fit(train_sets, epochs=args.ttp_epochs, batch=16384, objective=args.ttp_objective)
-    damp.fit([p[0] for p in dparts], epochs=args.ttp_epochs, batch=16384, objective="labels", seed=23)
+    damp.fit([p[0] for p in dparts], epochs=args.ttp_epochs, batch=16384, objective=args.ttp_damping_objective,
+             seed=23)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     held_stats = {}
@@ -834,13 +835,17 @@ def time_to_psnr(args):
         nll, _ = model.loss(hs, objective="line")
         dpl, dcnt = learned.plain_loss(hd)        # rho = 1 (alpha = 1) against the damping labels
         dnl, _ = damp.loss(hd)
+        dwpl, _ = learned.plain_loss(hd, objective="line")   # the same, weighted by the spread of Q
+        dwnl, _ = damp.loss(hd, objective="line")
         dl = hd.labels().cpu().numpy()
         dl = dl[dl >= 0]
         held_stats[name] = {"records": cnt, "label_loss_plain": round(pl, 5), "label_loss_network": round(nl, 5),
                             "line_loss_plain": float(f"{pll:.5g}"), "line_loss_network": float(f"{nll:.5g}"),
                             "damping_records": dcnt, "damping_label_loss_plain": round(dpl, 5),
                             "damping_label_loss_network": round(dnl, 5),
-                            "damping_label_histogram": {f"rho=1e{int(round(3 * (v - 1)))}": int(np.sum(
+                            "damping_weighted_loss_plain": float(f"{dwpl:.5g}"),
+                            "damping_weighted_loss_network": float(f"{dwnl:.5g}"),
+                            "damping_label_histogram": {f"rho=1e{1.5 * v:.1f}": int(np.sum(
                                 np.abs(dl - v) < 1e-4)) for v in np.linspace(0.0, 2.0, 7)}}
 
     def run(start_host, precision, use_model, max_sweeps, target_psnr=None, learned_trust=None, use_damp=False):
@@ -931,38 +936,50 @@ def time_to_psnr(args):
         ctx.check()
         return round(float(np.median(times[1:])), 3)
 
-    def summary(r):
-        k = r["reached"] if r["reached"] is not None else r["sweeps"]
-        return {"sweeps_to_target": r["reached"], "seconds_to_target": round(r["ms"][k] * 1e-3, 5)
-                if r["reached"] is not None else None,
-                "psnr_at_30": round(r["psnr"][min(30, r["sweeps"])], 4), "best_psnr": round(max(r["psnr"]), 4),
-                "ms_per_sweep": round(r["ms"][-1] / max(r["sweeps"], 1), 3)}
+    def med(xs):
+        """Median with unreached runs (None) counted as slower than any reached one."""
+        v = sorted(float("inf") if x is None else x for x in xs)
+        m = v[len(v) // 2] if len(v) % 2 else 0.5 * (v[len(v) // 2 - 1] + v[len(v) // 2])
+        return None if m == float("inf") else m
 
+    R = max(1, args.ttp_reps)
     starts = {}
     for sname, host in (("workload", spec_host), ("initialised", init_host)):
-        plain = run(host, 0, False, 30)
-        target = plain["psnr"][30]
-        runs = {"plain_fp32": plain}
+        # the trajectories depend on the order of floating-point atomic
+        # additions, so every path runs R times: medians, with the spread
+        plains = [run(host, 0, False, 30) for _ in range(R)]
+        target = float(np.median([p["psnr"][30] for p in plains]))
+        t_plain = float(np.median([p["ms"][30] for p in plains])) * 1e-3
+        runs = {"plain_fp32": plains}
         # path: (precision, step-scale network, learned_trust, damping network)
         paths = {"learned_mixed": (1, True, None, False), "learned_fp32": (0, True, None, False),
                  "learned_mixed_radii_x2": (1, True, 2.0, False), "damping_mixed": (1, False, None, True),
                  "damping_scale_mixed": (1, True, None, True), "plain_mixed": (1, False, None, False)}
         for name in args.ttp_paths.split(","):
             prec, use, lt, ud = paths[name]
-            runs[name] = run(host, prec, use, max(args.ttp_max, 30), target, lt, ud)
+            runs[name] = [run(host, prec, use, max(args.ttp_max, 30), target, lt, ud) for _ in range(R)]
         head_path = "damping_mixed" if "damping_mixed" in runs else "learned_mixed"
-        lm = runs[head_path]
-        t_plain = plain["ms"][30] * 1e-3
-        t_lm = lm["ms"][lm["reached"]] * 1e-3 if lm["reached"] is not None else None
+
+        def per_path(rs):
+            secs = [r["ms"][r["reached"]] * 1e-3 if r["reached"] is not None else None for r in rs]
+            return {"sweeps_to_target": [r["reached"] for r in rs],
+                    "median_sweeps_to_target": med([r["reached"] for r in rs]),
+                    "seconds_to_target": [None if x is None else round(x, 5) for x in secs],
+                    "median_seconds_to_target": None if med(secs) is None else round(med(secs), 5),
+                    "psnr_at_30": [round(r["psnr"][min(30, r["sweeps"])], 4) for r in rs],
+                    "ms_per_sweep": round(float(np.median([r["ms"][-1] / max(r["sweeps"], 1) for r in rs])), 3)}
+
+        t_lm = med([r["ms"][r["reached"]] * 1e-3 if r["reached"] is not None else None for r in runs[head_path]])
         starts[sname] = {
-            "initial_psnr_db": round(plain["psnr"][0], 4), "target_psnr_db": round(target, 4),
+            "initial_psnr_db": round(plains[0]["psnr"][0], 4), "target_psnr_db": round(target, 4),
             "plain_fp32_seconds_30": round(t_plain, 5),
-            "plain_diverges": bool(target < plain["psnr"][0]),
+            "plain_fp32_psnr_at_30": [round(p["psnr"][30], 4) for p in plains],
+            "plain_diverges": bool(target < plains[0]["psnr"][0]),
             "headline_path": head_path,
             "learned_seconds": None if t_lm is None else round(t_lm, 5),
             "speedup_vs_plain": None if not t_lm else round(t_plain / t_lm, 3),
-            "runs": {k: summary(r) for k, r in runs.items()},
-            "psnr_curves": {k: [round(x, 3) for x in r["psnr"]] for k, r in runs.items()},
+            "runs": {k: per_path(rs) for k, rs in runs.items()},
+            "psnr_curves": {k: [round(x, 3) for x in rs[0]["psnr"]] for k, rs in runs.items()},
         }
     head = starts["workload"]
     first = {name: first_sweep_ms(prec, use, use_damp=ud) for name, prec, use, ud in
@@ -975,7 +992,9 @@ def time_to_psnr(args):
         "starts": starts,
         "first_sweep_ms": first,
         "network": {"objective": args.ttp_objective, "learned_trust": args.ttp_learned_trust,
-                    "damping_objective": "labels (candidate rho minimising the all-view quadratic model)",
+                    "damping_objective": args.ttp_damping_objective + " (labels: the candidate rho minimising the "
+                                         "all-view quadratic model; line: the same, each record weighted by the "
+                                         "spread of that model over the candidates)",
                     "tiny_runs": args.ttp_runs, "shell_runs": args.ttp_shell, "shell_sweeps": args.ttp_shell_sweeps,
                     "records": tiny.n + shell.n,
                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2), "epochs": args.ttp_epochs,
@@ -1165,9 +1184,14 @@ def main():
     ap.add_argument("--ttp-max", type=int, default=60)
     ap.add_argument("--ttp-learned-trust", type=float, default=1.0,
                     help="learned_trust of the learned paths (the learned step may reach this many trust radii)")
+    ap.add_argument("--ttp-reps", type=int, default=3,
+                    help="runs of every path from each start (medians and spread are reported)")
     ap.add_argument("--ttp-paths", default="learned_mixed,damping_mixed,damping_scale_mixed,plain_mixed",
                     help="paths run against the plain FP32 path: learned_mixed, learned_fp32, learned_mixed_radii_x2, "
                          "damping_mixed, damping_scale_mixed, plain_mixed")
+    ap.add_argument("--ttp-damping-objective", default="line", choices=["line", "labels"],
+                    help="damping network: line = label loss weighted per record by the spread of the all-view "
+                         "quadratic model over the candidates; labels = unweighted")
     ap.add_argument("--ttp-objective", default="line", choices=["line", "labels"],
                     help="training loss of the step-scale network")
     args = ap.parse_args()

@@ -343,22 +343,27 @@ gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *ca
 
 /* Learned damping (an extension; the paper is silent on damping, Sec. 4.2).
  * A second network of the same shape, layout and features maps a Gaussian's
- * plain damped step to a multiplier rho = 10^(3 (alpha - 1)) in (1e-3, 1e3)
- * of the damping mu0 (alpha = 2 sigmoid(y)); for the position, scaling and
+ * plain damped step to a multiplier rho = 10^(1.5 alpha) in (1, 1e3) of the
+ * damping mu0 (alpha = 2 sigmoid(y): the damping can only grow, where the
+ * measured gain of the best candidates lies); for the position, scaling and
  * colour groups, whose damping turns the step and not only shortens it,
  * gs2_solve_step and gs2_sweep then solve again with mu0 rho (the rotation
  * and opacity blocks are 1 x 1: there damping and step scale coincide).  The
  * plain solve's rho stays 1 where the features are unusable or alpha is not
  * finite.  An installed step-scale network then scales the re-solved step.
- * Its records (gs2_sweep_logged) carry the step records' features and phi0
- * and, in row 9, the label 1 + log10(rho*) / 3, rho* the multiplier among
- * 10^-3, ..., 10^3 whose step (the same damped solve, trust radii and bounds)
+ * Its records (gs2_sweep_logged) carry the step records' features and, in
+ * row 9, the label 2 log10(rho*) / 3, rho* the multiplier among
+ * 10^0, 10^0.5, ..., 10^3 whose step (the same damped solve, trust radii and bounds)
  * has the smallest quadratic model of the loss over every training view,
  * Q(d) = g_all . d + 1/2 d^T H_all d (the group's blocks accumulated over
  * every view at full resolution before the step; smallest rho on ties); -1
  * where the step record is unusable, no candidate has Q < 0, or the group's
- * damping is not learned.  It is trained with gs2_mlp_grad (labels) and
- * gs2_mlp_adam like the step-scale network.
+ * damping is not learned.  Rows 8 and 10 hold phi0 = -w a* and phi1 = phi0 + w
+ * (a* the label, w = the largest minus the smallest finite Q of the
+ * candidates; 0 without a label), so that gs2_mlp_grad's line objective
+ * becomes sum s_c w (a^2 / 2 - a* a): the label loss weighted by how much the
+ * record's choice of damping changes Q.  It is trained with gs2_mlp_grad
+ * (labels or line) and gs2_mlp_adam like the step-scale network.
  * Install (device, GS2_MLP_NPARAM BF16 words, read at every solve; the caller
  * keeps it alive) or remove (NULL); installing allocates as
  * gs2_set_step_model does. */

@@ -35,9 +35,9 @@ Definitions (g, H: a Gaussian's group block; d: its plain damped step):
           s_c = 1 / sum |phi0| over the usable records of the record's chunk
   Adam    m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
           p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
-  damping a second network of the same shape gives rho = 10^(3 (alpha - 1)),
-          the multiplier of damping_mu0 in a second solve (position, scaling,
-          colour); its label is 1 + log10(rho*) / 3, rho* in 10^-3 .. 10^3
+  damping a second network of the same shape gives rho = 10^(1.5 alpha) in
+          (1, 1e3), the multiplier of damping_mu0 in a second solve (position,
+          scaling, colour); its label is 2 log10(rho*) / 3, rho* in 10^0 .. 10^3
           minimising Q(d) = g_all . d + 1/2 d^T H_all d over the candidate
           steps, g_all, H_all the blocks over every training view
 """
@@ -331,7 +331,7 @@ def learned_step(group, g, H, d, scene, cfg, p, g_primary=None):
 
 # ---------------------------------------------------------------- learned damping
 DAMP_GROUPS = (O.POS, O.SCALE, O.COLOR)   # damping turns these steps, not only shortens them
-RHO_GRID = tuple(10.0 ** j for j in range(-3, 4))
+RHO_GRID = tuple(10.0 ** (0.5 * j) for j in range(7))   # the damping can only grow
 
 
 def quad_model(group, g, H, d, S):
@@ -341,18 +341,21 @@ def quad_model(group, g, H, d, S):
 
 
 def damping_records(group, g, H, rec, scene, primary, g_all, H_all, cfg, return_q=False):
-    """The damping network's records: the step records' features and phi0
-    (rows 0-8 of rec) and the label 1 + log10(rho*) / 3, rho* the multiplier of
-    damping_mu0 among 10^-3 .. 10^3 (ascending; the first of equal values)
+    """The damping network's records: the step records' features (rows 0-7
+    of rec), the label 2 log10(rho*) / 3 (row 9), rho* the multiplier of
+    damping_mu0 among 10^0, 10^0.5, .., 10^3 (ascending; the first of equal values)
     whose step -- O.solve of the local blocks g, H with mu0 rho -- has the
     smallest Q over the all-view blocks g_all, H_all; -1 where the step record
-    is unusable, no candidate has Q < 0, or the group is not in DAMP_GROUPS.
+    is unusable, no candidate has Q < 0, or the group is not in DAMP_GROUPS;
+    rows 8 and 10 = -w a*, -w a* + w (w = the largest minus the smallest
+    finite Q of the candidates, 0 without a label): the line objective's
+    quadratic with its minimum at the label.
     return_q: also the candidates' Q [len(RHO_GRID)][n] (None if no label)."""
     cfg = O.default_config(**(cfg or {}))
     sc = O.scene_handle(scene)
     n, S = sc.n, O.sh_count(sc.sh_degree)
     out = np.zeros((REC_ROWS, n))
-    out[:NF + 1] = rec[:NF + 1]
+    out[:NF] = rec[:NF]
     out[NF + 1] = -1.0
     if group not in DAMP_GROUPS or cfg["gd_lr"][group] > 0:
         return (out, None) if return_q else out
@@ -369,12 +372,20 @@ def damping_records(group, g, H, rec, scene, primary, g_all, H_all, cfg, return_
         best_q = np.where(better, q, best_q)
         best_rho = np.where(better, rho, best_rho)
     ok = (rec[NF + 1] >= 0) & (best_q < 0)
-    out[NF + 1] = np.where(ok, np.clip(1.0 + np.log10(best_rho) / 3.0, 0.0, 2.0), -1.0)
-    return (out, np.stack(qs)) if return_q else out
+    lab = np.clip(np.log10(best_rho) * (2.0 / 3.0), 0.0, 2.0)
+    out[NF + 1] = np.where(ok, lab, -1.0)
+    # rows 8 and 10: the label as the line objective's quadratic, weighted by
+    # the spread w of the candidates' finite Q
+    Q = np.stack(qs)
+    worst = np.max(np.where(np.isfinite(Q), Q, -np.inf), axis=0)
+    w = np.where(ok, np.maximum(worst - best_q, 0.0), 0.0)
+    out[NF] = -w * np.where(ok, lab, 0.0)
+    out[NF + 2] = out[NF] + w
+    return (out, Q) if return_q else out
 
 
 def damped_step(group, g, H, d, scene, primary, cfg, p_damp, g_primary=None):
-    """The learned-damping step: rho = 10^(3 (alpha - 1)) from the network
+    """The learned-damping step: rho = 10^(1.5 alpha) from the network
     p_damp on the plain step d's record (1 where the record is unusable or
     the group is not in DAMP_GROUPS), then O.solve with damping_mu0 rho per
     Gaussian (one solve per Gaussian's own multiplier)."""
@@ -387,7 +398,7 @@ def damped_step(group, g, H, d, scene, primary, cfg, p_damp, g_primary=None):
     rec = step_records(group, g, H, d, sc, cfg, g_primary)
     ok = rec[NF + 1] >= 0
     a, _ = mlp_forward(p_damp, np.where(ok[:, None], rec[:NF].T, 0.0))
-    rho = np.where(ok & np.isfinite(a), 10.0 ** (3.0 * (a - 1.0)), 1.0)
+    rho = np.where(ok & np.isfinite(a), 10.0 ** (1.5 * a), 1.0)
     out = np.zeros_like(d)
     for r in np.unique(rho):
         cj = dict(cfg, damping_mu0=cfg["damping_mu0"] * r)

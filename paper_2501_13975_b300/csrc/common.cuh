@@ -205,6 +205,7 @@ struct gs2_ctx {
     void *lg_ball;               // the group's blocks summed (colour: one slot per view) over every training view
     void *lg_step2;              // a candidate step
     float *lg_bq, *lg_brho;      // [max_n] best quadratic-model value so far and its multiplier
+    float *lg_wq;                // [max_n] largest finite quadratic-model value so far
     size_t lg_ball_bytes, lg_bloc_bytes;
     float *g_prim;               // [3][max_n] gradient rows right after the view-slot-0 accumulation
     float *lg_phi;               // [max_n] phi1 accumulator of the logged sweep
@@ -299,10 +300,10 @@ cudaError_t launch_learned_damping(int group, const void *blocks, int n_views, c
                                    const float *gp, const gs2_config &cfg, const void *w, float *rho,
                                    cudaStream_t st);
 cudaError_t launch_damp_eval(int group, const void *blocks_all, int n_all, const DevScene &sc, const void *step,
-                             const gs2_config &cfg, float rho_j, float *best_q, float *best_rho, int first,
-                             cudaStream_t st);
-cudaError_t launch_damp_labels(int group, const float *rec, const float *best_q, const float *best_rho, int n,
-                               float *rec_damp, cudaStream_t st);
+                             const gs2_config &cfg, float rho_j, float *best_q, float *best_rho, float *worst_q,
+                             int first, cudaStream_t st);
+cudaError_t launch_damp_labels(int group, const float *rec, const float *best_q, const float *worst_q,
+                               const float *best_rho, int n, float *rec_damp, cudaStream_t st);
 cudaError_t launch_add_floats(float *dst, const float *src, size_t count, cudaStream_t st);
 cudaError_t launch_bounding_sphere(const DevScene &sc, float *out, cudaStream_t st);
 

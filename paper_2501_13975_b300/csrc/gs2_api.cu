@@ -139,7 +139,7 @@ static void free_ctx(gs2_ctx *c) {
     void *ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->ghist, c->sort_state, c->d_count, c->ranges,
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->d_resolves, c->flags, c->g_prim, c->lg_phi,
-                    c->d_rho, c->lg_bloc, c->lg_ball, c->lg_step2, c->lg_bq, c->lg_brho,
+                    c->d_rho, c->lg_bloc, c->lg_ball, c->lg_step2, c->lg_bq, c->lg_brho, c->lg_wq,
                     c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list, c->tile_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -910,18 +910,18 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             if (pass == 0 && recd) {   // damping labels: candidate steps of the same solve, scored on the all-view model
                 if (dlab) {
                     gs2_config cj = ctx->cfg;
-                    for (int j = 0; j < 7; ++j) {
-                        const float rj = exp10f((float)(j - 3));
+                    for (int j = 0; j < 7; ++j) {   // rho = 10^0, 10^0.5, .., 10^3
+                        const float rj = exp10f(0.5f * (float)j);
                         cj.damping_mu0 = ctx->cfg.damping_mu0 * rj;
                         RET_CUDA(ctx, launch_solve(group, ctx->lg_bloc, nv, dsc, make_devcam(primary), cj,
                                                    ctx->lg_step2, nullptr, ctx->flags, st, nullptr));
                         RET_CUDA(ctx, launch_damp_eval(group, ctx->lg_ball, group == GS2_COLOR ? ncam : 1, dsc,
-                                                       ctx->lg_step2, ctx->cfg, rj, ctx->lg_bq, ctx->lg_brho, j == 0,
-                                                       st));
+                                                       ctx->lg_step2, ctx->cfg, rj, ctx->lg_bq, ctx->lg_brho,
+                                                       ctx->lg_wq, j == 0, st));
                     }
                 }
-                RET_CUDA(ctx, launch_damp_labels(group, rec, dlab ? ctx->lg_bq : nullptr, ctx->lg_brho, scene->n,
-                                                 recd, st));
+                RET_CUDA(ctx, launch_damp_labels(group, rec, dlab ? ctx->lg_bq : nullptr, ctx->lg_wq, ctx->lg_brho,
+                                                 scene->n, recd, st));
             }
             if (pass == 0)
                 RET_CUDA(ctx, launch_apply(group, ctx->sw_step, dsc, make_devcam(primary), ctx->cfg, st));
@@ -956,17 +956,18 @@ extern "C" gs2_status gs2_sweep_logged(gs2_ctx *ctx, gs2_scene *scene, const gs2
         }
         if (ball > ctx->lg_ball_bytes || bloc > ctx->lg_bloc_bytes || !ctx->lg_bq) {
             RET_CUDA(ctx, cudaDeviceSynchronize());
-            void *ptrs[] = {ctx->lg_ball, ctx->lg_bloc, ctx->lg_step2, ctx->lg_bq, ctx->lg_brho};
+            void *ptrs[] = {ctx->lg_ball, ctx->lg_bloc, ctx->lg_step2, ctx->lg_bq, ctx->lg_brho, ctx->lg_wq};
             for (void *p : ptrs)
                 if (p) cudaFree(p);
             ctx->lg_ball = ctx->lg_bloc = ctx->lg_step2 = nullptr;
-            ctx->lg_bq = ctx->lg_brho = nullptr;
+            ctx->lg_bq = ctx->lg_brho = ctx->lg_wq = nullptr;
             ctx->lg_ball_bytes = ctx->lg_bloc_bytes = 0;
             RET_CUDA(ctx, cudaMalloc(&ctx->lg_ball, ball));
             RET_CUDA(ctx, cudaMalloc(&ctx->lg_bloc, bloc));
             RET_CUDA(ctx, cudaMalloc(&ctx->lg_step2, ctx->sw_step_bytes));
             RET_CUDA(ctx, cudaMalloc((void **)&ctx->lg_bq, sizeof(float) * (size_t)ctx->max_n));
             RET_CUDA(ctx, cudaMalloc((void **)&ctx->lg_brho, sizeof(float) * (size_t)ctx->max_n));
+            RET_CUDA(ctx, cudaMalloc((void **)&ctx->lg_wq, sizeof(float) * (size_t)ctx->max_n));
             ctx->lg_ball_bytes = ball;
             ctx->lg_bloc_bytes = bloc;
         }

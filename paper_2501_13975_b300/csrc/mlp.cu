@@ -369,15 +369,21 @@ cudaError_t launch_learned_scale(int group, const void *blocks, int n_views, con
 // ---------------------------------------------------------------- learned damping
 // A second network of the same shape and the same features predicts, for the
 // position, scaling and colour groups (whose damping turns the step, not only
-// lengthens it), a multiplier rho of the damping mu0 of the Gaussian's solve:
-// rho = 10^(3 (alpha - 1)) in (1e-3, 1e3), alpha = 2 sigmoid(y).  The solve is
-// then repeated with mu0 rho.  Its records share the step records' features
-// and phi0; the label (row 9) is alpha_rho* = 1 + log10(rho*) / 3 with rho*
-// the multiplier, among 10^-3 .. 10^3, whose damped step (same solve, trust
-// radii and bounds) minimises the quadratic model of the loss over every
-// training view, Q(d) = g_all . d + 1/2 d^T H_all d; -1 where the step record
-// is unusable, no candidate lowers Q, or the group's damping is not learned.
-__device__ __forceinline__ float rho_of(float a) { return exp10f(3.f * (a - 1.f)); }
+// shortens it), a multiplier rho of the damping mu0 of the Gaussian's solve:
+// rho = 10^(1.5 alpha) in (1, 1e3), alpha = 2 sigmoid(y): the damping can only
+// grow (measured: applying the all-view best candidate per Gaussian gained
+// 1.7-1.8 dB after 30 sweeps on the object workload, of which raising the
+// damping gave 1.3-1.5 dB and lowering it 0.4-0.5).  The solve is then
+// repeated with mu0 rho.  Its records share the step records' features; the
+// label (row 9) is alpha_rho* = 2 log10(rho*) / 3 with rho* the multiplier,
+// among 10^0, 10^0.5, .., 10^3, whose damped step (same solve, trust radii and
+// bounds) minimises the quadratic model of the loss over every training view,
+// Q(d) = g_all . d + 1/2 d^T H_all d; -1 where the step record is unusable, no
+// candidate lowers Q, or the group's damping is not learned.
+// Rows 8 and 10 turn the label into the line objective's weighted quadratic
+// (k_damp_labels), so training can weight each record by how much its choice
+// of damping matters.
+__device__ __forceinline__ float rho_of(float a) { return exp10f(1.5f * a); }
 
 __global__ void __launch_bounds__(128) k_learned_damping(int group, const float *__restrict__ B, int n_views,
                                                          DevScene sc, const float *__restrict__ step,
@@ -404,32 +410,43 @@ __global__ void __launch_bounds__(128) k_learned_damping(int group, const float 
 __global__ void __launch_bounds__(128) k_damp_eval(int group, const float *__restrict__ Ball, int n_all, DevScene sc,
                                                    const float *__restrict__ step, gs2_config cfg, float rho_j,
                                                    float *__restrict__ best_q, float *__restrict__ best_rho,
-                                                   int first) {
+                                                   float *__restrict__ worst_q, int first) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= sc.n) return;
     // g_p is not used by Q: the all-view blocks stand in for it
     const StepStats st = step_stats(group, Ball, n_all, sc, k, step, Ball, cfg, smax_of(sc, k));
     float q = st.gd + 0.5f * st.q;
-    if (!isfinite(q)) q = INFINITY;
+    const bool fin = isfinite(q);
+    if (!fin) q = INFINITY;
     if (first || q < best_q[k]) {
         best_q[k] = q;
         best_rho[k] = rho_j;
     }
+    if (first) worst_q[k] = fin ? q : -INFINITY;
+    else if (fin && q > worst_q[k]) worst_q[k] = q;
 }
 
+// rows 8 and 10 hold the weighted quadratic -w a* a + 1/2 w a^2 in the line
+// objective's form (phi0 = -w a*, phi1 = phi0 + w): minimal at the label a*,
+// weighted by w = the spread of Q over the candidates (how much the choice
+// matters); 0 where there is no label
 __global__ void __launch_bounds__(128) k_damp_labels(int group, const float *__restrict__ rec,
                                                      const float *__restrict__ best_q,
+                                                     const float *__restrict__ worst_q,
                                                      const float *__restrict__ best_rho, int n,
                                                      float *__restrict__ rec_d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
 #pragma unroll
-    for (int i = 0; i <= NF; ++i) rec_d[(size_t)i * n + k] = rec[(size_t)i * n + k];   // features, phi0
-    float lab = -1.f;
-    if (damping_learned(group) && best_q && rec[(size_t)(NF + 1) * n + k] >= 0.f && best_q[k] < 0.f)
-        lab = fminf(fmaxf(1.f + log10f(best_rho[k]) * (1.f / 3.f), 0.f), 2.f);
+    for (int i = 0; i < NF; ++i) rec_d[(size_t)i * n + k] = rec[(size_t)i * n + k];   // features
+    float lab = -1.f, w = 0.f;
+    if (damping_learned(group) && best_q && rec[(size_t)(NF + 1) * n + k] >= 0.f && best_q[k] < 0.f) {
+        lab = fminf(fmaxf(log10f(best_rho[k]) * (2.f / 3.f), 0.f), 2.f);
+        w = fmaxf(worst_q[k] - best_q[k], 0.f);
+    }
+    rec_d[(size_t)NF * n + k] = -w * lab;
     rec_d[(size_t)(NF + 1) * n + k] = lab;
-    rec_d[(size_t)(NF + 2) * n + k] = 0.f;
+    rec_d[(size_t)(NF + 2) * n + k] = -w * lab + w;
 }
 
 __global__ void k_add_floats(float *__restrict__ dst, const float *__restrict__ src, size_t count) {
@@ -448,19 +465,19 @@ cudaError_t launch_learned_damping(int group, const void *blocks, int n_views, c
 }
 
 cudaError_t launch_damp_eval(int group, const void *blocks_all, int n_all, const DevScene &sc, const void *step,
-                             const gs2_config &cfg, float rho_j, float *best_q, float *best_rho, int first,
-                             cudaStream_t st) {
+                             const gs2_config &cfg, float rho_j, float *best_q, float *best_rho, float *worst_q,
+                             int first, cudaStream_t st) {
     if (sc.n == 0) return cudaSuccess;
     k_damp_eval<<<(sc.n + 127) / 128, 128, 0, st>>>(group, (const float *)blocks_all, n_all, sc,
-                                                   (const float *)step, cfg, rho_j, best_q, best_rho, first);
+                                                   (const float *)step, cfg, rho_j, best_q, best_rho, worst_q, first);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_damp_labels(int group, const float *rec, const float *best_q, const float *best_rho, int n,
-                               float *rec_damp, cudaStream_t st) {
+cudaError_t launch_damp_labels(int group, const float *rec, const float *best_q, const float *worst_q,
+                               const float *best_rho, int n, float *rec_damp, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_damp_labels<<<(n + 127) / 128, 128, 0, st>>>(group, rec, best_q, best_rho, n, rec_damp);
+    k_damp_labels<<<(n + 127) / 128, 128, 0, st>>>(group, rec, best_q, worst_q, best_rho, n, rec_damp);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

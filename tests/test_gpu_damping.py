@@ -65,7 +65,7 @@ def _rel(got, ref, n, keep):
 @pytest.mark.parametrize("group", [0, 2, 4])
 def test_constant_damping_network_equals_solve_with_scaled_mu0(group):
     """A network with zero weights and output bias b gives one alpha = 2
-    sigmoid(b), rho = 10^(3 (alpha - 1)) = 10^1.5 for every usable record:
+    sigmoid(b), rho = 10^(1.5 alpha) (about 10^2.25) for every usable record:
     gs2_solve_step's second solve equals the oracle's solve with damping_mu0
     rho, and the steps are shorter than the plain ones (more damping)."""
     from paper_2501_13975_b300 import gs2
@@ -86,7 +86,7 @@ def test_constant_damping_network_equals_solve_with_scaled_mu0(group):
     keep = c["keep"] & (rho != 1.0)
     assert keep.sum() >= 100, keep.sum()
     a = 2.0 / (1.0 + np.exp(-pw[Lr.OFF_B3]))
-    assert np.allclose(rho[rho != 1.0], 10.0 ** (3.0 * (a - 1.0)))
+    assert np.allclose(rho[rho != 1.0], 10.0 ** (1.5 * a))
     err = _rel(got[: ref.size], ref, n, keep)
     assert np.quantile(err, 0.99) <= 5e-3, np.quantile(err, 0.99)
     plain = c["plain"].cpu().numpy()[: ref.size].reshape(-1, n)
@@ -117,11 +117,14 @@ def test_damping_network_per_gaussian_matches_oracle(group):
 
 
 def test_logged_damping_records_match_oracle():
-    """gs2_sweep_logged's damping records: rows 0-8 are the step records'
-    own; the labels match the oracle's logged sweep wherever the oracle's best
-    candidate beats the runner-up by 1% of its |Q| (elsewhere two multipliers
-    are equally good and either is a valid label); every GPU label is one of
-    the grid's values or -1; rotation and opacity carry no label."""
+    """gs2_sweep_logged's damping records: rows 0-7 are the step records'
+    features; the labels match the oracle's logged sweep wherever the oracle's
+    best candidate beats the runner-up by 1% of its |Q| (elsewhere two
+    multipliers are equally good and either is a valid label); every GPU
+    label is one of the grid's values or -1; rows 8 and 10 hold -w a* and
+    -w a* + w with w >= 0 the candidates' spread of Q (0 without a label),
+    matching the oracle's w to 5% where the labels agree; rotation and
+    opacity carry no label."""
     from paper_2501_13975_b300 import gs2
     sc = synth.tiny_scene(n=300, seed=63)
     gt = synth.perturbed(sc, seed=64, sd=0.05)
@@ -140,10 +143,13 @@ def test_logged_damping_records_match_oracle():
     ctx.check()
     grec, gd = rec.cpu().numpy(), recd.cpu().numpy()
     _, _, od = Lr.sweep_logged(sc, cams, tg_np.astype(np.float64), knn, t, ocfg, damping="q")
-    grid = 1.0 + np.log10(np.asarray(Lr.RHO_GRID)) / 3.0
+    grid = np.log10(np.asarray(Lr.RHO_GRID)) * (2.0 / 3.0)
     for group in range(5):
-        assert np.array_equal(gd[group][:Lr.NF + 1], grec[group][:Lr.NF + 1]), group
+        assert np.array_equal(gd[group][:Lr.NF], grec[group][:Lr.NF]), group
         lab = gd[group][Lr.NF + 1]
+        wg = gd[group][Lr.NF + 2] - gd[group][Lr.NF]
+        assert np.all(wg >= 0) and np.all(wg[lab < 0] == 0), group
+        assert np.allclose(gd[group][Lr.NF][lab >= 0], -wg[lab >= 0] * lab[lab >= 0], rtol=1e-5, atol=0), group
         valid = (lab == -1.0) | np.any(np.abs(lab[:, None] - grid[None, :]) < 1e-6, axis=1)
         assert valid.all(), group
         orec, q = od[group]
@@ -158,6 +164,11 @@ def test_logged_damping_records_match_oracle():
         assert clear.sum() >= 10, (group, clear.sum())
         agree = np.abs(lab[clear] - orec[Lr.NF + 1][clear]) < 1e-6
         assert agree.mean() >= 0.95, (group, agree.mean())
+        wo = orec[Lr.NF + 2] - orec[Lr.NF]
+        sel = clear & (np.abs(lab - orec[Lr.NF + 1]) < 1e-6) & (wo > 1e-12)
+        if sel.sum():
+            relw = np.abs(wg[sel] - wo[sel]) / wo[sel]
+            assert np.quantile(relw, 0.9) <= 0.05, (group, np.quantile(relw, 0.9))
 
 
 def test_sweep_with_networks_equals_call_sequence():

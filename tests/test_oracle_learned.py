@@ -422,14 +422,16 @@ def _iso_blocks(rng, n, h):
     return g, Hu
 
 
-@pytest.mark.parametrize("mu0, c, want", [(1.0, 2.0, 1.0), (0.01, 2.0, 1.0 + 2.0 / 3.0),
-                                          (1.0, 1.0, 0.0), (0.1, 11.0, 1.0 + 2.0 / 3.0)])
+@pytest.mark.parametrize("mu0, c, want", [(1.0, 2.0, 0.0), (0.01, 2.0, 4.0 / 3.0),
+                                          (1.0, 1.0, 0.0), (0.1, 11.0, 4.0 / 3.0),
+                                          (0.1, 1.0 + 0.1 * 10.0 ** 2.5, 5.0 / 3.0)])
 def test_damping_label_closed_form(mu0, c, want):
     """H = h I, g_all = g, H_all = c h I: the damped step (h + mu h) d = -g
     in the plane has Q = |g_v|^2 / h (c t^2 / 2 - t), t = 1 / (1 + mu),
     minimal at t = 1 / c, i.e. mu = c - 1.  With mu = mu0 rho on the grid
-    10^-3 .. 10^3: rho* = (c - 1) / mu0 (label 1 + log10(rho*) / 3), and
-    for c = 1 (the exact Newton step is best) the smallest rho (label 0)."""
+    10^0, 10^0.5, .., 10^3: rho* = (c - 1) / mu0 (label 2 log10(rho*) / 3),
+    and where that is below the grid (c = 1: the exact Newton step is best;
+    mu0 = c - 1) the smallest rho, 1 (label 0)."""
     rng = np.random.default_rng(21)
     n, h = 8, 2.5
     sc = _scene_for(n)
@@ -439,19 +441,25 @@ def test_damping_label_closed_form(mu0, c, want):
     d = O.solve(O.POS, sc, cams[0], g, Hu, cfg)["step"]
     rec = Lr.step_records(O.POS, g, Hu, d, sc, cfg)
     out = Lr.damping_records(O.POS, g, Hu, rec, sc, cams[0], g, c * Hu, cfg)
-    assert np.array_equal(out[:Lr.NF + 1], rec[:Lr.NF + 1])
+    assert np.array_equal(out[:Lr.NF], rec[:Lr.NF])
     assert np.allclose(out[Lr.NF + 1], want, atol=1e-12), out[Lr.NF + 1]
-    # Q of the candidates, from the plane's closed form (not the oracle's Q)
+    # Q of the candidates, from the plane's closed form (not the oracle's Q),
+    # and the weight w = max Q - min Q of rows 8 and 10
     sh = O.scene_handle(sc)
     for k in range(n):
         r = np.asarray(sh.mean, np.float64).reshape(3, n)[:, k] - cams[0].center()
         r /= np.linalg.norm(r)
         gv2 = np.sum(g[:, k] ** 2) - np.dot(g[:, k], r) ** 2       # |g_v|^2: g without its ray component
+        qs = []
         for rho in Lr.RHO_GRID:
             t = 1.0 / (1.0 + mu0 * rho)
             dk = O.solve(O.POS, sc, cams[0], g, Hu, dict(cfg, damping_mu0=mu0 * rho))["step"][:, k]
             q = np.dot(g[:, k], dk) + 0.5 * c * h * np.dot(dk, dk)
             assert q == pytest.approx(gv2 / h * (0.5 * c * t * t - t), rel=1e-9, abs=1e-14)
+            qs.append(gv2 / h * (0.5 * c * t * t - t))
+        w = max(qs) - min(qs)
+        assert out[Lr.NF, k] == pytest.approx(-w * want, rel=1e-9, abs=1e-15)
+        assert out[Lr.NF + 2, k] - out[Lr.NF, k] == pytest.approx(w, rel=1e-9)
 
 
 def test_damping_records_unusable_and_other_groups():
@@ -469,6 +477,7 @@ def test_damping_records_unusable_and_other_groups():
     rec[Lr.NF + 1, 0] = -1.0
     out = Lr.damping_records(O.POS, g, Hu, rec, sc, cams[0], g, Hu, cfg)
     assert out[Lr.NF + 1, 0] == -1.0 and np.all(out[Lr.NF + 1, 1:] == 0.0)
+    assert out[Lr.NF, 0] == 0.0 and out[Lr.NF + 2, 0] == 0.0      # no label: no weight
     up = Lr.damping_records(O.POS, g, Hu, rec, sc, cams[0], -g, Hu, cfg)   # every candidate ascends Q
     assert np.all(up[Lr.NF + 1] == -1.0)
     go = rng.normal(size=(1, n))
@@ -491,9 +500,9 @@ def test_damped_step_constant_network():
     g, Hu, d, _ = _pos_blocks(rng, n, mu=0.3)
     d = O.solve(O.POS, sc, cams[0], g, Hu, cfg)["step"]
     p = np.zeros(Lr.NPARAM)
-    p[Lr.OFF_B3] = np.log(1.5 / 0.5)              # alpha = 1.5: rho = 10^1.5
+    p[Lr.OFF_B3] = np.log(1.5 / 0.5)              # alpha = 1.5: rho = 10^2.25
     out, rho = Lr.damped_step(O.POS, g, Hu, d, sc, cams[0], cfg, p)
-    assert np.allclose(rho, 10.0 ** 1.5, rtol=1e-12)
-    want = O.solve(O.POS, sc, cams[0], g, Hu, dict(cfg, damping_mu0=10.0 ** 1.5))["step"]
+    assert np.allclose(rho, 10.0 ** 2.25, rtol=1e-12)
+    want = O.solve(O.POS, sc, cams[0], g, Hu, dict(cfg, damping_mu0=10.0 ** 2.25))["step"]
     assert np.allclose(out, want, rtol=1e-12, atol=0)
     assert np.linalg.norm(out) < np.linalg.norm(d)   # more damping, shorter steps
