@@ -192,6 +192,9 @@ def run_gpu(args, rank, world, local_rank):
     if args.accum_px:
         ctx.set_tuning(accum_px=args.accum_px)
         tuning = dict(tuning, accum_px=args.accum_px)
+    if args.accum_split >= 0:
+        ctx.set_tuning(accum_split=args.accum_split)
+        tuning = dict(tuning, accum_split=args.accum_split)
 
     # the timed sweeps: through a one-scene gs2_batch captured as a CUDA graph
     # per sweep (re-captured and updated in place: no priming, any primary
@@ -200,7 +203,8 @@ def run_gpu(args, rank, world, local_rank):
     if args.graph:
         batch = gs2.Batch([dict(max_gaussians=w["n"], max_width=W, max_height=H, max_sh_degree=w["sh"],
                                 max_pairs=w["max_pairs"])], dict(precision=args.precision))
-        batch.set_tuning(0, tuning["sort_blocks"], tuning["sort_rows"], tuning["view_lanes"], tuning["accum_px"])
+        batch.set_tuning(0, tuning["sort_blocks"], tuning["sort_rows"], tuning["view_lanes"], tuning["accum_px"],
+                         tuning["accum_split"])
         prep = batch.prepare([scene], [cams], [targets], [knn])
 
     def sweep(i, tg=None):
@@ -366,7 +370,7 @@ def run_gpu(args, rank, world, local_rank):
     jacobi = None
     if not args.no_variants:
         cj = gs2.Context(w["n"], W, H, w["sh"], w["max_pairs"], dict(precision=args.precision, group_jacobi=1))
-        cj.set_tuning(**{k: tuning[k] for k in ("sort_blocks", "sort_rows", "view_lanes", "accum_px")})
+        cj.set_tuning(**{k: tuning[k] for k in ("sort_blocks", "sort_rows", "view_lanes", "accum_px", "accum_split")})
         sj = scene.clone()
         for i in range(2):
             cj.sweep(sj, cams, targets, knn, i % ncam)
@@ -528,6 +532,11 @@ def run_batched(args):
     if not args.no_autotune:
         for i, w in enumerate(work):
             tuning.append(batch.autotune(i, scenes[i], w["cams"], targets[i], knns[i], 0, reps=2))
+    if args.accum_split >= 0:
+        for i, w in enumerate(work):
+            cur = tuning[i] if tuning else batch.tuning(i)
+            batch.set_tuning(i, cur["sort_blocks"], cur["sort_rows"], cur["view_lanes"], cur["accum_px"],
+                             args.accum_split)
     t_tune = time.perf_counter() - t0
     prep = batch.prepare(scenes, [w["cams"] for w in work], targets, knns)
     views = [w["views"] for w in work]
@@ -1162,6 +1171,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tuning")
     ap.add_argument("--accum-px", type=int, default=0, choices=[0, 2, 4],
                     help="pixels per thread of the position accumulation (overrides the tuning; 0: keep)")
+    ap.add_argument("--accum-split", type=int, default=-1,
+                    help="list entries per work item of the split accumulation (overrides the tuning; 0: off, "
+                         "-1: keep)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: time sweeps as a CUDA graph re-captured per sweep (one-scene gs2_batch); 0: eager")
     ap.add_argument("--variants", action="store_true",

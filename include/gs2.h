@@ -411,18 +411,38 @@ gs2_status gs2_mlp_adam(float *master, uint16_t *w_bf16, const float *partial, c
  *                and in deterministic mode).  The rotation, scaling and
  *                opacity groups always take 2.  Same sums, added in another
  *                order.
+ *   accum_split: 0 (default): the accumulation runs one CTA per tile over the
+ *                tile's whole back-to-front walk.  A multiple of the tile's
+ *                pixel count (256 with 16x16 tiles, at most 2^20): every
+ *                walk is cut into work items of that many list entries,
+ *                which a persistent grid takes longest tiles first, so that a
+ *                few long walks no longer bound the launch (dense scenes at
+ *                low resolution).  gs2_raster_fwd then also writes, at every
+ *                multiple of accum_split entries of a tile's list, each
+ *                pixel's T there and the colour its entries from there on add
+ *                (checkpoints in ctx); an item starts a pixel whose last
+ *                contributor lies behind the item's end from there.  Same
+ *                sums, added in another order, with T and the colour behind
+ *                rounded differently.  Not used in deterministic mode.
+ *                gs2_set_tuning allocates the checkpoints (16 * 256 bytes per
+ *                accum_split pairs of max_pairs, plus the item list) for ctx
+ *                and its view lanes: it synchronises the device and must not
+ *                run under stream capture; GS2_ERR_OOM if they do not fit.
  * gs2_autotune times `reps` sweeps with primary t for every candidate
- * (sort_blocks 296, 592, 888 x sort_rows 2, 4, 8, 16 at the current accum_px,
- * then the other accum_px at the best of those; view_lanes kept) on a scratch
- * copy of the scene (the caller's scene is not changed), keeps the fastest in
- * ctx and returns it and its ms per sweep (host outputs, may be NULL).  It
- * allocates the copy, synchronises the stream and must not run under stream
+ * (sort_blocks 296, 592, 888 x sort_rows 2, 4, 8, 16 at the current accum_px
+ * and accum_split, then the other accum_px at the best of those, then
+ * accum_split 0, 1 and 4 times the tile's pixel count at the best of those;
+ * view_lanes kept) on a scratch copy of the scene (the caller's scene
+ * is not changed), keeps the fastest in ctx and returns it and its ms per
+ * sweep (host outputs, may be NULL).  It allocates the copy and the split
+ * checkpoints, synchronises the stream and must not run under stream
  * capture. */
 typedef struct {
     int32_t sort_blocks;
     int32_t sort_rows;
     int32_t view_lanes;
     int32_t accum_px;
+    int32_t accum_split;
 } gs2_tuning;
 gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out);
 gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *tuning);

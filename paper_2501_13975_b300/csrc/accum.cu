@@ -447,7 +447,13 @@ template <int GROUP, int NQ> struct AccumShape {
     static_assert(NT % 32 == 0, "a tile holds whole warps");
 };
 
-template <int GROUP, typename ACC, bool DET = false, int NQ = 2>
+// SPLIT: a persistent grid takes work items (tile, [c0, c1), checkpoint slot)
+// from `items` through the fetch counter ctrl[1] (ctrl[0] items), so that one
+// long tile walk is shared by several CTAs.  A pixel whose last contributor
+// lies behind c1 starts from the compositing's checkpoint at c1: T(c1), and
+// the colour behind, (colour its entries from c1 on add) / T(c1); the others
+// from the final state, as the whole walk does.
+template <int GROUP, typename ACC, bool DET = false, int NQ = 2, bool SPLIT = false>
 __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, NQ>::MIN_CTAS) k_accum(const uint2 *__restrict__ ranges,
                                                            const uint32_t *__restrict__ ids, ProjView pv,
                                                            RasterView rv, const float *__restrict__ E,
@@ -455,18 +461,22 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
                                                            float amin, float amax, int gn, ACC *__restrict__ zbuf,
                                                            int n, unsigned long long *__restrict__ active_stat,
                                                            float *__restrict__ det_part,
-                                                           const uint32_t *__restrict__ tile_order) {
+                                                           const uint32_t *__restrict__ tile_order,
+                                                           const uint4 *__restrict__ items,
+                                                           uint32_t *__restrict__ ctrl) {
     constexpr int P = Payload<GROUP>::P;
     constexpr int NT = AccumShape<GROUP, NQ>::NT, NW = AccumShape<GROUP, NQ>::NW;
     constexpr bool EH_SMEM = AccumShape<GROUP, NQ>::EH_SMEM;
     constexpr int NB = AccumShape<GROUP, NQ>::NB;     // list entries staged per batch
     constexpr int NPR = NQ / 2;                       // pixel pairs a thread (f32x2 arithmetic)
     static_assert(NQ == 2 || (NQ == 4 && GS2_TILE == 16), "four pixels a thread need 16x16 tiles");
+    static_assert(!(DET && SPLIT), "the deterministic mode walks whole tiles");
     constexpr int PER = NB / NT;                      // entries each thread stages
     // two staging buffers: batch b + 1 is copied in while batch b is walked
     __shared__ uint32_t sId[2][NB];
     __shared__ float4 sA[2][NB], sB[2][NB], sC[2][NB];
     __shared__ uint32_t sMax;
+    __shared__ uint4 sItem;
     // four pixels a thread: e, h of pixel pair r of thread t as f32x2 pairs,
     // [r][0] = (e0, e1), [r][1] = (e2, h0), [r][2] = (h1, h2) (each .x: q = 2r, .y: q = 2r + 1)
     __shared__ float4 sEP[EH_SMEM ? NPR : 1][3][EH_SMEM ? NT : 1];
@@ -475,19 +485,38 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     if constexpr (DET) {
         for (int q = t; q < NW * GS2_DET_CHUNK * P; q += NT) (&sDet[0][0][0])[q] = 0.f;
     }
-    const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
-    const int tcol = tile % tiles_x, trow = tile / tiles_x;
     const int wb = t >> 5;   // warp block: (wb % GS2_WPR) 8 columns, (wb / GS2_WPR) 4 NQ rows
-    const int px = tcol * GS2_TILE + (wb % GS2_WPR) * 8 + (t & 7);
-    const int py = trow * GS2_TILE + (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
     const size_t PI = (size_t)W * H;
+    uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
+    for (;;) {
+    int tile, c0 = 0, c1 = 0x7FFFFFFF;   // list entries [c0, c1) of the tile's walk
+    uint32_t slot = 0xFFFFFFFFu;        // checkpoint at c1
+    if constexpr (SPLIT) {
+        if (t == 0) {
+            const uint32_t i = atomicAdd(&ctrl[1], 1u);
+            sItem = i < ctrl[0] ? items[i] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        const uint4 w = sItem;
+        if (w.x == 0xFFFFFFFFu) break;   // CTA-uniform
+        tile = (int)w.x;
+        c0 = (int)w.y;
+        c1 = (int)w.z;
+        slot = w.w;
+    } else {
+        tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
+    }
+    const int tcol = tile % tiles_x, trow = tile / tiles_x;
+    const int lx = (wb % GS2_WPR) * 8 + (t & 7), ly0 = (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
+    const int px = tcol * GS2_TILE + lx;
+    const int py = trow * GS2_TILE + ly0;
     uint32_t last[NQ];
     PairState pst[NPR];
     float2 pe2[EH_SMEM ? 1 : NPR][3], ph2[EH_SMEM ? 1 : NPR][3];   // e, h in registers (two pixels a thread)
     float2 pyf[NPR];
 #pragma unroll
     for (int r = 0; r < NPR; ++r) {
-        float e[2][3], h[2][3], T[2];
+        float e[2][3], h[2][3], T[2], cb[2][3];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int y = py + 4 * (2 * r + j);
@@ -495,11 +524,24 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
             last[2 * r + j] = 0u;   // outside the image: no list entry is composited
             T[j] = 1.f;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) e[j][c] = h[j][c] = 0.f;
+            for (int c = 0; c < 3; ++c) e[j][c] = h[j][c] = cb[j][c] = 0.f;
             if (inside) {
                 const size_t pp = (size_t)y * W + px;
                 last[2 * r + j] = rv.last[pp];
                 T[j] = rv.tfinal[pp];
+                if constexpr (SPLIT) {
+                    if (last[2 * r + j] > (uint32_t)c1) {   // composites past c1: start at the checkpoint
+                        const int lp = (ly0 + 4 * (2 * r + j)) * GS2_TILE + lx;
+                        const float4 ck = rv.ck[(size_t)slot * GS2_TILE_PIX + lp];
+                        T[j] = ck.x;
+                        // T >= t_min > 0 where the compositing went on; with t_min = 0 an
+                        // underflowed T leaves every weight in front zero, as the whole walk does
+                        const float iT = ck.x > 0.f ? 1.f / ck.x : 0.f;
+                        cb[j][0] = ck.y * iT;
+                        cb[j][1] = ck.z * iT;
+                        cb[j][2] = ck.w * iT;
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     e[j][c] = E[c * PI + pp];
@@ -508,7 +550,9 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
             }
         }
         pst[r].T = make_float2(T[0], T[1]);
-        pst[r].cb0 = pst[r].cb1 = pst[r].cb2 = f2(0.f);
+        pst[r].cb0 = make_float2(cb[0][0], cb[1][0]);
+        pst[r].cb1 = make_float2(cb[0][1], cb[1][1]);
+        pst[r].cb2 = make_float2(cb[0][2], cb[1][2]);
         pyf[r] = make_float2((float)(py + 8 * r), (float)(py + 8 * r + 4));
         if constexpr (EH_SMEM) {
             sEP[r][0][t] = make_float4(e[0][0], e[1][0], e[0][1], e[1][1]);
@@ -530,20 +574,20 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     atomicMax(&sMax, last2);
     __syncthreads();
     const int maxlast = (int)sMax;
+    const int hi = min(c1, maxlast);   // end of this walk
     // this warp's own end of list: its lanes have nothing to do beyond it
     const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last2);
     const uint2 r = ranges[tile];
     const float fx = (float)px;
-    uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
-    // batches back to front: batch b covers [max(0, maxlast - NB (b + 1)), maxlast - NB b)
-    const int nbat = (maxlast + NB - 1) / NB;
-    auto list_index = [&](int b, int i) { return maxlast - NB * (b + 1) + t + i * NT; };
+    // batches back to front: batch b covers [max(c0, hi - NB (b + 1)), hi - NB b)
+    const int nbat = hi > c0 ? (hi - c0 + NB - 1) / NB : 0;
+    auto list_index = [&](int b, int i) { return hi - NB * (b + 1) + t + i * NT; };
     uint32_t knext[PER];
     auto fetch = [&](int b) {
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int li = list_index(b, i);
-            knext[i] = li >= 0 ? ids[r.x + li] : 0u;
+            knext[i] = li >= c0 ? ids[r.x + li] : 0u;
         }
     };
     auto issue = [&](int b) {
@@ -551,7 +595,7 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int j = t + i * NT;
-            if (list_index(b, i) >= 0) {
+            if (list_index(b, i) >= c0) {
                 const uint32_t k = knext[i];
                 sId[buf][j] = k;
                 cp_async16(&sA[buf][j], &pv.recA[k]);
@@ -574,7 +618,7 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
             if (b + 2 < nbat) fetch(b + 2);
         }
         const int buf = b & 1;
-        const int bend = maxlast - NB * b, bbeg = max(0, bend - NB);
+        const int bend = hi - NB * b, bbeg = max(c0, bend - NB);
         const int base = bend - NB;   // list index of slot 0 of this batch (may be negative)
         // one list entry (back to front): its payload, then the warp sum
         // (atomics, or stored to `row` in deterministic mode)
@@ -702,6 +746,9 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     if constexpr (DET) {   // entries past the last contributor of every pixel contribute nothing
         const int nl = (int)(r.y - r.x);
         for (int q = t + maxlast * P; q < nl * P; q += NT) det_part[(size_t)r.x * P + q] = 0.f;
+    }
+    if constexpr (!SPLIT) break;
+    __syncthreads();   // this item's shared memory is free before the next item is fetched
     }
     if (active_stat) {
         unsigned long long c = nact;
@@ -1201,6 +1248,131 @@ __global__ void __launch_bounds__(128) k_det_reduce(const uint32_t *__restrict__
     }
 }
 
+// Work items of the split accumulation: every tile's walk [0, maxlast) cut at
+// multiples of ca, in the tiles' launch order (longest lists first), the back
+// item of a tile first; an item ending below the walk's end names the
+// checkpoint slot at its end.  One CTA: per-thread runs of tiles, a block scan
+// of their item counts, then the items written in order.  Also resets the
+// fetch counter of the persistent accumulation grid.
+__global__ void __launch_bounds__(1024) k_accum_items(const uint32_t *__restrict__ order,
+                                                      const uint32_t *__restrict__ maxlast,
+                                                      const uint2 *__restrict__ ranges, int ntiles, int ca,
+                                                      uint4 *__restrict__ items, uint32_t *__restrict__ ctrl) {
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (ntiles + 1023) / 1024;
+    const int i0 = min(ntiles, t * per), i1 = min(ntiles, i0 + per);
+    const uint32_t uca = (uint32_t)ca;
+    uint32_t cnt = 0u;
+    for (int i = i0; i < i1; ++i) cnt += (maxlast[order ? (int)order[i] : i] + uca - 1u) / uca;
+    uint32_t inc = cnt;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = wsum[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        wsum[lane] = x - v;
+        if (lane == 31) {
+            ctrl[0] = x;
+            ctrl[1] = 0u;
+        }
+    }
+    __syncthreads();
+    uint32_t pos = wsum[w] + inc - cnt;
+    for (int i = i0; i < i1; ++i) {
+        const int tile = order ? (int)order[i] : i;
+        const uint32_t np = (maxlast[tile] + uca - 1u) / uca, base = ranges[tile].x / uca;
+        for (uint32_t s = np; s-- > 0u;)
+            items[pos++] = make_uint4((uint32_t)tile, s * uca, (s + 1u) * uca, s + 1u == np ? 0xFFFFFFFFu : base + s + 1u);
+    }
+}
+
+static int device_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    return sms;
+}
+
+struct AccumArgs {
+    const uint2 *ranges;
+    const uint32_t *ids;
+    ProjView pv;
+    RasterView rv;
+    const float *E, *Hh;
+    int W, H, tiles_x;
+    float amin, amax;
+    int gn, n;
+    unsigned long long *act;
+    const uint32_t *tile_order;
+    const uint4 *items;
+    uint32_t *ctrl;
+    dim3 grid;
+};
+
+// resident CTAs per SM of a split accumulation kernel (first asked for by
+// prepare_split_kernels, from the host, outside any stream capture)
+template <int G, typename ACC, int NQ>
+static int split_occupancy() {
+    static int occ = 0;
+    if (!occ) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_accum<G, ACC, false, NQ, true>,
+                                                      AccumShape<G, NQ>::NT, 0);
+        if (occ < 1) occ = 1;
+    }
+    return occ;
+}
+
+void prepare_split_kernels() {
+    device_sms();
+#define GS2_SPLIT_PREP(ACC)                                                                                      \
+    split_occupancy<GS2_POS, ACC, 2>();                                                                          \
+    split_occupancy<GS2_ROT, ACC, 2>();                                                                          \
+    split_occupancy<GS2_SCALE, ACC, 2>();                                                                        \
+    split_occupancy<GS2_OPACITY, ACC, 2>();                                                                      \
+    split_occupancy<GS2_COLOR, ACC, 2>();
+    GS2_SPLIT_PREP(float)
+    GS2_SPLIT_PREP(double)
+#undef GS2_SPLIT_PREP
+#if GS2_TILE == 16
+    split_occupancy<GS2_POS, float, 4>();
+    split_occupancy<GS2_COLOR, float, 4>();
+    split_occupancy<GS2_POS, double, 4>();
+    split_occupancy<GS2_COLOR, double, 4>();
+#endif
+}
+
+// one accumulation launch (atomics, not the deterministic mode): a CTA per tile, or
+// (split) a persistent grid of as many CTAs as are resident at once
+template <int G, typename ACC, int NQ>
+static void accum_launch(const AccumArgs &a, ACC *zb, bool split, cudaStream_t st) {
+    constexpr int NT = AccumShape<G, NQ>::NT;
+    if (split) {
+        const int occ = split_occupancy<G, ACC, NQ>();
+        k_accum<G, ACC, false, NQ, true><<<(unsigned)(device_sms() * occ), NT, 0, st>>>(
+            a.ranges, a.ids, a.pv, a.rv, a.E, a.Hh, a.W, a.H, a.tiles_x, a.amin, a.amax, a.gn, zb, a.n, a.act,
+            (float *)nullptr, nullptr, a.items, a.ctrl);
+    } else {
+        k_accum<G, ACC, false, NQ, false><<<a.grid, NT, 0, st>>>(a.ranges, a.ids, a.pv, a.rv, a.E, a.Hh, a.W, a.H,
+                                                                 a.tiles_x, a.amin, a.amax, a.gn, zb, a.n, a.act,
+                                                                 (float *)nullptr, a.tile_order, nullptr, nullptr);
+    }
+}
+
 template <typename ACC>
 static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                            ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks, dim3 grid,
@@ -1210,46 +1382,45 @@ static void launch_accum_t(gs2_ctx *ctx, int group, const DevScene &sc, const De
     gs2_ctx *pc = ctx->owner ? ctx->owner : ctx;   // profile pool and statistics
     unsigned long long *act = pc->prof_on ? pc->d_stats + 5 * group + 3 : nullptr;
     const bool det = cfg.deterministic != 0 && ctx->det_part && ctx->det_order;
+    // split walks: the last compositing on this context kept its checkpoints
+    const bool split = !det && ctx->rs_split > 0 && ctx->ck && ctx->acc_items;
+    if (split) {
+        rv.ck = ctx->ck;
+        rv.ck_every = ctx->rs_split;
+        k_accum_items<<<1, 1024, 0, st>>>(ctx->tile_order, ctx->tile_maxlast, ctx->ranges, (int)grid.x,
+                                          ctx->rs_split, ctx->acc_items, ctx->acc_ctrl);
+        GS2_COUNT_LAUNCH(1);
+    }
+    const AccumArgs a = {ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x,
+                         cfg.alpha_min, cfg.alpha_max, cfg.gauss_newton, n, act, ctx->tile_order, ctx->acc_items,
+                         ctx->acc_ctrl, grid};
 #define ACC_LAUNCH(G)                                                                                             \
     do {                                                                                                          \
         if (det) {                                                                                                \
             k_accum<G, float, true><<<grid, GS2_PAIR_THREADS, 0, st>>>(                                           \
                 ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,    \
-                cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part, ctx->tile_order);       \
+                cfg.alpha_max, cfg.gauss_newton, (float *)nullptr, n, act, ctx->det_part, ctx->tile_order,        \
+                nullptr, nullptr);                                                                                \
             if (n > 0)                                                                                            \
                 k_det_reduce<Payload<G>::P, ACC><<<(n + 3) / 4, 128, 0, st>>>(                                    \
                     ctx->det_order, pv.offs, pv.tsort, n, ctx->d_count, ctx->det_inv, ctx->det_ids,               \
                     ctx->det_part, zb);                                                                           \
         } else {                                                                                                  \
-            k_accum<G, ACC><<<grid, GS2_PAIR_THREADS, 0, st>>>(ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h,  \
-                                                               view.w, view.h, ctx->tiles_x, cfg.alpha_min,       \
-                                                               cfg.alpha_max, cfg.gauss_newton, zb, n, act,       \
-                                                               (float *)nullptr, ctx->tile_order);                \
+            accum_launch<G, ACC, 2>(a, zb, split, st);                                                            \
         }                                                                                                         \
     } while (0)
-    switch (group) {
-    case GS2_POS:
 #if GS2_TILE == 16
-        if (!det && ctx->accum_px == 4) {   // four pixels per thread: two warps per tile
-            k_accum<GS2_POS, ACC, false, 4><<<grid, AccumShape<GS2_POS, 4>::NT, 0, st>>>(
-                ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,
-                cfg.alpha_max, cfg.gauss_newton, zb, n, act, (float *)nullptr, ctx->tile_order);
-            break;
-        }
-#endif
-        ACC_LAUNCH(GS2_POS);
-        break;
-#if GS2_TILE == 16
+    // four pixels per thread (position, colour): two warps per tile
 #define ACC_LAUNCH4(G)                                                                                           \
     if (!det && ctx->accum_px == 4) {                                                                            \
-        k_accum<G, ACC, false, 4><<<grid, AccumShape<G, 4>::NT, 0, st>>>(                                        \
-            ctx->ranges, ids, pv, rv, ctx->pix_e, ctx->pix_h, view.w, view.h, ctx->tiles_x, cfg.alpha_min,       \
-            cfg.alpha_max, cfg.gauss_newton, zb, n, act, (float *)nullptr, ctx->tile_order);                     \
+        accum_launch<G, ACC, 4>(a, zb, split, st);                                                               \
         break;                                                                                                   \
     }
 #else
 #define ACC_LAUNCH4(G)
 #endif
+    switch (group) {
+    case GS2_POS: ACC_LAUNCH4(GS2_POS) ACC_LAUNCH(GS2_POS); break;
     // measured per sweep (two / four pixels a thread): rotation and scaling
     // 1.30 / 1.34 ms, opacity 0.85 / 0.89, colour 0.75 / 0.71
     case GS2_ROT: ACC_LAUNCH(GS2_ROT); break;

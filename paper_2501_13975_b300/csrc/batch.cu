@@ -50,6 +50,7 @@ extern "C" gs2_status gs2_get_tuning(const gs2_ctx *ctx, gs2_tuning *out) {
     out->sort_rows = ctx->sort_rows;
     out->view_lanes = ctx->view_lanes;
     out->accum_px = ctx->accum_px;
+    out->accum_split = ctx->accum_split;
     return GS2_OK;
 }
 
@@ -59,10 +60,14 @@ extern "C" gs2_status gs2_set_tuning(gs2_ctx *ctx, const gs2_tuning *t) {
     if (t->sort_rows != 2 && t->sort_rows != 4 && t->sort_rows != 8 && t->sort_rows != 16) return GS2_ERR_ARG;
     if (t->view_lanes != 0 && t->view_lanes != 1) return GS2_ERR_ARG;
     if (t->accum_px != 2 && !(t->accum_px == 4 && GS2_TILE == 16)) return GS2_ERR_ARG;
+    if (t->accum_split < 0 || t->accum_split > GS2_SPLIT_MAX || t->accum_split % GS2_TILE_PIX != 0)
+        return GS2_ERR_ARG;
+    if (!ensure_split(ctx, t->accum_split)) return GS2_ERR_OOM;
     ctx->nb_sort = t->sort_blocks;
     ctx->sort_rows = t->sort_rows;
     ctx->view_lanes = t->view_lanes;
     ctx->accum_px = t->accum_px;
+    ctx->accum_split = t->accum_split;
     return GS2_OK;
 }
 
@@ -92,7 +97,7 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gs2_status rc = GS2_OK;
-    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows, ctx->view_lanes, ctx->accum_px};
+    const gs2_tuning keep = {ctx->nb_sort, ctx->sort_rows, ctx->view_lanes, ctx->accum_px, ctx->accum_split};
     gs2_tuning best = keep;
     float best_ms = 1e30f;
     const int blocks[3] = {148 * 2, 148 * 4, 148 * 6};
@@ -102,6 +107,7 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
         ctx->nb_sort = c.sort_blocks;
         ctx->sort_rows = c.sort_rows;
         ctx->accum_px = c.accum_px;
+        ctx->accum_split = c.accum_split;
         if (!reset()) { rc = GS2_ERR_CUDA; return; }
         rc = sweep_run(ctx, &cp, cams, ncam, targets, knn, t, nullptr, nullptr, nullptr, st);
         if (rc != GS2_OK) return;
@@ -123,10 +129,17 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
     // accumulation's pixels per thread at the best sort setting
     for (int bi = 0; bi < 3 && rc == GS2_OK; ++bi)
         for (int ri = 0; ri < 4 && rc == GS2_OK; ++ri)
-            trial({blocks[bi], rows[ri], ctx->view_lanes, keep.accum_px});
+            trial({blocks[bi], rows[ri], ctx->view_lanes, keep.accum_px, keep.accum_split});
     const int pxs[2] = {2, 4};
     for (int pi = 0; pi < (GS2_TILE == 16 ? 2 : 1) && rc == GS2_OK; ++pi)
-        if (pxs[pi] != keep.accum_px) trial({best.sort_blocks, best.sort_rows, best.view_lanes, pxs[pi]});
+        if (pxs[pi] != keep.accum_px)
+            trial({best.sort_blocks, best.sort_rows, best.view_lanes, pxs[pi], keep.accum_split});
+    // then the split walks (off, and chunks of 1 and 4 compositing batches)
+    const int splits[3] = {0, GS2_TILE_PIX, 4 * GS2_TILE_PIX};
+    if (rc == GS2_OK && !ensure_split(ctx, GS2_TILE_PIX)) rc = GS2_ERR_OOM;
+    for (int si = 0; si < 3 && rc == GS2_OK; ++si)
+        if (splits[si] != keep.accum_split)
+            trial({best.sort_blocks, best.sort_rows, best.view_lanes, best.accum_px, splits[si]});
     cudaStreamSynchronize(st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -135,11 +148,13 @@ extern "C" gs2_status gs2_autotune(gs2_ctx *ctx, const gs2_scene *scene, const g
         ctx->nb_sort = keep.sort_blocks;
         ctx->sort_rows = keep.sort_rows;
         ctx->accum_px = keep.accum_px;
+        ctx->accum_split = keep.accum_split;
         return rc;
     }
     ctx->nb_sort = best.sort_blocks;
     ctx->sort_rows = best.sort_rows;
     ctx->accum_px = best.accum_px;
+    ctx->accum_split = best.accum_split;
     if (best_out) *best_out = best;
     if (best_ms_out) *best_ms_out = best_ms;
     return GS2_OK;
@@ -267,6 +282,7 @@ static uint64_t sweep_key(const gs2_ctx *c, const gs2_scene *scene, const gs2_ca
     fnv(h, &c->sort_rows, sizeof(c->sort_rows));
     fnv(h, &c->view_lanes, sizeof(c->view_lanes));
     fnv(h, &c->accum_px, sizeof(c->accum_px));
+    fnv(h, &c->accum_split, sizeof(c->accum_split));
     return h;
 }
 

@@ -21,6 +21,7 @@
 #error "GS2_TILE must be 8 or 16"
 #endif
 #define GS2_SORT_BLOCKS_MAX 1024     // the per-digit scan runs one 1024-thread CTA per digit
+#define GS2_SPLIT_MAX (1 << 20)      // largest work item of the split accumulation (list entries)
 // profiling pool (event pairs) and the stage tags beside the accumulation groups
 #define GS2_PROF_POOL 2048
 #define GS2_PROF_BIN 5
@@ -100,6 +101,13 @@ static inline ProjView proj_view(void *base, int64_t n) {
 struct RasterView {
     float *tfinal;   // [H*W] final transmittance
     uint32_t *last;  // [H*W] number of tile-list entries consumed (last contributor + 1)
+    // split accumulation (all NULL / 0 when off): the compositing also keeps,
+    // at every ck_every list entries of a tile's walk, each pixel's T there
+    // and the colour (r, g, b) its entries from there on add, and the tile's
+    // walk length (largest `last` of its pixels)
+    float4 *ck;                 // [slots][GS2_TILE_PIX]: slot r.x / ck_every + j for list position j ck_every
+    uint32_t *tile_maxlast;     // [tiles]
+    int ck_every;
 };
 
 static inline size_t raster_state_bytes_impl(int w, int h) {
@@ -110,6 +118,9 @@ static inline RasterView raster_view(void *base, int w, int h) {
     RasterView r;
     r.tfinal = (float *)base;
     r.last = (uint32_t *)((char *)base + align256(4 * (size_t)w * h));
+    r.ck = nullptr;
+    r.tile_maxlast = nullptr;
+    r.ck_every = 0;
     return r;
 }
 
@@ -161,6 +172,18 @@ struct gs2_ctx {
     int sort_rows;               // keys per thread per scatter round (tuning: 2, 4, 8 or 16)
     int view_lanes;              // run a sweep's views concurrently (tuning: 0, 1)
     int accum_px;                // pixels per thread of the position accumulation (tuning: 2 or 4)
+    int accum_split;             // list entries per work item of the split accumulation (tuning; 0: off)
+    // split accumulation: a tile's back-to-front walk cut into items of
+    // accum_split entries, each started from the compositing's checkpoint at
+    // its back end, fetched by a persistent grid longest tiles first
+    float4 *ck;                  // [ck_slots][GS2_TILE_PIX] per-pixel checkpoints (T, C) of the compositing
+    size_t ck_slots;
+    int ck_ca;                   // accum_split the checkpoints are sized for (smallest allowed)
+    uint32_t *tile_maxlast;      // [max tiles] walk length of every tile
+    uint4 *acc_items;            // [acc_items_cap] (tile, first entry, end entry, checkpoint slot or ~0)
+    size_t acc_items_cap;
+    uint32_t *acc_ctrl;          // [0] items, [1] fetch counter
+    int rs_split;                // accum_split of the last compositing on this context (0: no checkpoints)
     // sorting
     uint32_t *keys[2];           // pair keys: tile id
     uint32_t *vals[2];           // pair values: Gaussian id
@@ -265,6 +288,12 @@ cudaError_t launch_loss(const float *image, const float *target, int w, int h, c
 cudaError_t launch_accum(gs2_ctx *ctx, int group, const DevScene &sc, const DevCam &view, const DevCam &primary,
                          ProjView pv, RasterView rv, const gs2_config &cfg, int view_slot, void *blocks,
                          cudaStream_t st);
+// allocates the split accumulation's checkpoints and work items of a context
+// (and its view lanes) for chunks of ca list entries (host side, never under
+// stream capture); false on allocation failure
+bool ensure_split(gs2_ctx *ctx, int ca);
+// occupancy of the split accumulation kernels, asked once from the host
+void prepare_split_kernels();
 // rho: per-Gaussian multiplier of the damping mu0 (the learned damping), or NULL
 cudaError_t launch_solve(int group, const void *blocks, int n_views, const DevScene &sc, const DevCam &primary,
                          const gs2_config &cfg, void *step, int32_t *n_failed, uint8_t *flags, cudaStream_t st,

@@ -121,7 +121,7 @@ extern "C" size_t gs2_step_bytes(gs2_group g, int64_t n, int32_t sh) { return st
 static void free_lane(gs2_ctx *l) {
     void *ptrs[] = {l->keys[0], l->keys[1], l->vals[0], l->vals[1], l->ghist, l->sort_state, l->d_count, l->ranges,
                     l->zbuf, l->pix_e, l->pix_h, l->sw_proj, l->sw_rstate, l->sw_image, l->tile_order,
-                    l->lane_blocks};
+                    l->lane_blocks, l->ck, l->tile_maxlast, l->acc_items, l->acc_ctrl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -140,12 +140,59 @@ static void free_ctx(gs2_ctx *c) {
                     c->zbuf, c->pix_e, c->pix_h, c->sw_proj, c->sw_rstate, c->sw_image, c->sw_tgt, c->sw_blocks,
                     c->sw_step, c->d_status, c->d_stats, c->d_resolves, c->flags, c->g_prim, c->lg_phi,
                     c->d_rho, c->lg_bloc, c->lg_ball, c->lg_step2, c->lg_bq, c->lg_brho, c->lg_wq,
-                    c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list, c->tile_order};
+                    c->order_cache, c->jb_mem, c->det_part, c->det_ids, c->det_inv, c->det_list, c->tile_order,
+                    c->ck, c->tile_maxlast, c->acc_items, c->acc_ctrl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->prof_on >= 0 && c->prof_ev[0])
         for (int i = 0; i < 2 * GS2_PROF_POOL; ++i)
             if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
+}
+
+// split accumulation buffers of one context, sized for chunks of ca entries
+// (any larger chunk fits: fewer checkpoint slots and items)
+static bool split_buffers(gs2_ctx *c, int ca) {
+    if (c->ck && c->ck_ca <= ca) return true;
+    if (cudaDeviceSynchronize() != cudaSuccess) return false;   // the old buffers may be in use
+    void *old[] = {c->ck, c->tile_maxlast, c->acc_items, c->acc_ctrl};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    c->ck = nullptr;
+    c->tile_maxlast = nullptr;
+    c->acc_items = nullptr;
+    c->acc_ctrl = nullptr;
+    c->ck_ca = 0;
+    c->rs_split = 0;
+    const size_t tiles = (size_t)((c->max_w + GS2_TILE - 1) / GS2_TILE) * ((c->max_h + GS2_TILE - 1) / GS2_TILE);
+    const size_t pairs = (size_t)std::max<int64_t>(c->max_pairs, 1);
+    c->ck_slots = (pairs - 1) / (size_t)ca + 1;
+    c->acc_items_cap = tiles + pairs / (size_t)ca + 1;
+    bool ok = cudaMalloc((void **)&c->ck, sizeof(float4) * GS2_TILE_PIX * c->ck_slots) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&c->tile_maxlast, sizeof(uint32_t) * tiles) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&c->acc_items, sizeof(uint4) * c->acc_items_cap) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&c->acc_ctrl, sizeof(uint32_t) * 2) == cudaSuccess;
+    ok = ok && cudaMemset(c->acc_ctrl, 0, sizeof(uint32_t) * 2) == cudaSuccess;
+    if (!ok) {
+        void *got[] = {c->ck, c->tile_maxlast, c->acc_items, c->acc_ctrl};
+        for (void *p : got)
+            if (p) cudaFree(p);
+        c->ck = nullptr;
+        c->tile_maxlast = nullptr;
+        c->acc_items = nullptr;
+        c->acc_ctrl = nullptr;
+        return false;
+    }
+    c->ck_ca = ca;
+    return true;
+}
+
+bool ensure_split(gs2_ctx *ctx, int ca) {
+    if (ca <= 0) return true;
+    prepare_split_kernels();
+    if (!split_buffers(ctx, ca)) return false;
+    for (int i = 0; i < ctx->n_lanes; ++i)
+        if (ctx->lanes[i] && !split_buffers(ctx->lanes[i], ca)) return false;
+    return true;
 }
 
 // Jacobi over groups: every group's blocks and step at once (allocated when
@@ -436,8 +483,17 @@ static gs2_status do_raster(gs2_ctx *ctx, int n, const gs2_camera *cam, const vo
     prof_end(ctx, pe, st);
     if (pc->prof_on) pc->h_pixels[pc->stat_slot] += (unsigned long long)cam->width * cam->height;
     pe = prof_begin(ctx, GS2_PROF_RASTER, st);
-    RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image,
-                                raster_view(rstate, cam->width, cam->height), st));
+    RasterView rv = raster_view(rstate, cam->width, cam->height);
+    // split accumulation: checkpoints and walk lengths for the accumulations
+    // that follow (not in deterministic mode, which walks whole tiles)
+    ctx->rs_split = 0;
+    if (ctx->accum_split > 0 && ctx->ck && ctx->accum_split >= ctx->ck_ca && !ctx->cfg.deterministic) {
+        rv.ck = ctx->ck;
+        rv.tile_maxlast = ctx->tile_maxlast;
+        rv.ck_every = ctx->accum_split;
+        ctx->rs_split = ctx->accum_split;
+    }
+    RET_CUDA(ctx, launch_raster(ctx, pv, make_devcam(cam), ctx->cfg, image, rv, st));
     prof_end(ctx, pe, st);
     return GS2_OK;
 }
@@ -714,6 +770,7 @@ gs2_status sweep_run(gs2_ctx *ctx, gs2_scene *scene, const gs2_camera *cams, int
             l->nb_sort = ctx->nb_sort;
             l->sort_rows = ctx->sort_rows;
             l->accum_px = ctx->accum_px;
+            l->accum_split = ctx->accum_split;
         }
     }
     if (ctx->cfg.group_jacobi) {

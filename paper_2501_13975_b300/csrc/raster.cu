@@ -9,8 +9,16 @@
 //   Gaussian's thresholds l, lmax (decide.cuh), reproducibly.
 // Writes the planar image, the final transmittance and the list position
 // after the last contributor (consumed by the accumulation pass).
+// CK (the split accumulation's checkpoints, rv.ck): at every multiple c_j of
+// rv.ck_every list entries the tile's walk reaches, each pixel's T(c_j) and
+// the colour its entries from c_j on add (sum of alpha T c~, kept per segment
+// between checkpoints and summed from the back once the walk ends: no
+// difference of two nearly equal colours, which would lose the digits of a
+// deep T), and the tile's walk length (the largest list position after a
+// last contributor).
 #include "common.cuh"
 
+template <bool CK>
 __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ ids, ProjView pv, int W, int H,
                                                          int tiles_x, float amin, float amax, float tmin,
@@ -18,6 +26,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
                                                          const uint32_t *__restrict__ tile_order) {
     // two staging buffers: batch b + 1 is copied in (cp.async) while batch b is walked
     __shared__ float4 sA[2][GS2_TILE_PIX], sB[2][GS2_TILE_PIX], sC[2][GS2_TILE_PIX];
+    __shared__ uint32_t sMax;
     const int t = threadIdx.x;
     const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
     const int tcol = tile % tiles_x, trow = tile / tiles_x;
@@ -28,8 +37,15 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
     const int n = (int)(r.y - r.x);
     const float fx = (float)px, fy = (float)py;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;   // CK: colour of the current segment
     uint32_t lastc = 0u;
     const int nbat = (n + GS2_TILE_PIX - 1) / GS2_TILE_PIX;
+    // checkpoint j (list position j ck_every, j >= 1) of this tile goes to slot
+    // r.x / ck_every + j: distinct for all tiles, below (list length) / ck_every
+    const int ck_b = CK ? rv.ck_every / GS2_TILE_PIX : 1;   // batches between checkpoints
+    const size_t ck_base = CK ? (size_t)(r.x / (uint32_t)rv.ck_every) : 0;
+    const int lp = gs2_tile_py(t) * GS2_TILE + gs2_tile_px(t);   // row-major pixel of the tile
+    int nck = 0;   // checkpoints written (CTA-uniform)
     auto issue = [&](int b, uint32_t k) {
         const int buf = b & 1;
         if (b * GS2_TILE_PIX + t < n) {
@@ -48,6 +64,16 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
     for (int b = 0; b < nbat; ++b) {
         cp_async_wait_all();
         if (__syncthreads_count(done) == GS2_TILE_PIX) break;   // also: batch b visible, b - 1's buffer free
+        if constexpr (CK) {
+            // T after the entries in front of this batch, and the colour of the
+            // segment that ends here (only read back for pixels whose last
+            // contributor lies behind this point, which are not done)
+            if (b > 0 && b % ck_b == 0) {
+                ++nck;
+                rv.ck[(ck_base + (size_t)nck) * GS2_TILE_PIX + lp] = make_float4(T, s0, s1, s2);
+                s0 = s1 = s2 = 0.f;
+            }
+        }
         if (b + 1 < nbat) {
             issue(b + 1, knext);
             const int j2 = (b + 2) * GS2_TILE_PIX + t;
@@ -71,6 +97,11 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
             c0 = fmaf(wgt, C.x, c0);
             c1 = fmaf(wgt, C.y, c1);
             c2 = fmaf(wgt, C.z, c2);
+            if constexpr (CK) {
+                s0 = fmaf(wgt, C.x, s0);
+                s1 = fmaf(wgt, C.y, s1);
+                s2 = fmaf(wgt, C.z, s2);
+            }
             T = tt;
             lastc = (uint32_t)(b0 + i + 1);
         }
@@ -83,13 +114,39 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
         rv.tfinal[p] = T;
         rv.last[p] = lastc;
     }
+    if constexpr (CK) {
+        // checkpoint j: (T(c_j), colour of [c_j, end)), summed from the back
+        // over this thread's own checkpoints (it wrote them: no barrier)
+        float b0 = s0, b1 = s1, b2 = s2;
+        for (int j = nck; j >= 1; --j) {
+            float4 *ck = &rv.ck[(ck_base + (size_t)j) * GS2_TILE_PIX + lp];
+            const float4 v = *ck;   // (T(c_j), colour of [c_{j-1}, c_j))
+            *ck = make_float4(v.x, b0, b1, b2);
+            b0 += v.y;
+            b1 += v.z;
+            b2 += v.w;
+        }
+        // the tile's walk length
+        const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, lastc);
+        if (t == 0) sMax = 0u;
+        __syncthreads();
+        if ((t & 31) == 0) atomicMax(&sMax, wm);
+        __syncthreads();
+        if (t == 0) rv.tile_maxlast[tile] = sMax;
+    }
 }
 
 cudaError_t launch_raster(gs2_ctx *ctx, ProjView pv, const DevCam &cam, const gs2_config &cfg, float *image,
                           RasterView rv, cudaStream_t st) {
     const unsigned grid = (unsigned)(ctx->tiles_x * ctx->tiles_y);
-    k_raster<<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->list_ids, pv, cam.w, cam.h, ctx->tiles_x,
-                                            cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv, ctx->tile_order);
+    if (rv.ck && rv.tile_maxlast && rv.ck_every >= GS2_TILE_PIX)
+        k_raster<true><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->list_ids, pv, cam.w, cam.h, ctx->tiles_x,
+                                                      cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv,
+                                                      ctx->tile_order);
+    else
+        k_raster<false><<<grid, GS2_TILE_PIX, 0, st>>>(ctx->ranges, ctx->list_ids, pv, cam.w, cam.h, ctx->tiles_x,
+                                                       cfg.alpha_min, cfg.alpha_max, cfg.t_min, image, rv,
+                                                       ctx->tile_order);
     GS2_COUNT_LAUNCH(1);
     return cudaGetLastError();
 }

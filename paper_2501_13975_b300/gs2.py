@@ -56,11 +56,12 @@ class Config_(C.Structure):
 
 class Tuning_(C.Structure):
     _fields_ = [("sort_blocks", C.c_int32), ("sort_rows", C.c_int32), ("view_lanes", C.c_int32),
-                ("accum_px", C.c_int32)]
+                ("accum_px", C.c_int32), ("accum_split", C.c_int32)]
 
 
 def _tuning_dict(t) -> dict:
-    return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows, view_lanes=t.view_lanes, accum_px=t.accum_px)
+    return dict(sort_blocks=t.sort_blocks, sort_rows=t.sort_rows, view_lanes=t.view_lanes, accum_px=t.accum_px,
+                accum_split=t.accum_split)
 
 
 class BatchScene_(C.Structure):
@@ -422,12 +423,13 @@ class Context:
         return _tuning_dict(t)
 
     def set_tuning(self, sort_blocks: int | None = None, sort_rows: int | None = None, view_lanes: int | None = None,
-                   accum_px: int | None = None):
+                   accum_px: int | None = None, accum_split: int | None = None):
         cur = self.tuning()
         t = Tuning_(int(cur["sort_blocks"] if sort_blocks is None else sort_blocks),
                     int(cur["sort_rows"] if sort_rows is None else sort_rows),
                     int(cur["view_lanes"] if view_lanes is None else view_lanes),
-                    int(cur["accum_px"] if accum_px is None else accum_px))
+                    int(cur["accum_px"] if accum_px is None else accum_px),
+                    int(cur["accum_split"] if accum_split is None else accum_split))
         self._ok(_lib.gs2_set_tuning(self.h, C.byref(t)), "gs2_set_tuning")
 
     def autotune(self, scene: DeviceScene, cams, targets, knn, t, reps=2, stream=None):
@@ -546,8 +548,17 @@ class Batch:
         if st != 0:
             raise GS2Error(f"gs2_set_config: {STATUS.get(st, st)}")
 
-    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int, view_lanes: int = 1, accum_px: int = 2):
-        t = Tuning_(int(sort_blocks), int(sort_rows), int(view_lanes), int(accum_px))
+    def tuning(self, i: int) -> dict:
+        """gs2_get_tuning of scene i's context."""
+        t = Tuning_()
+        st = _lib.gs2_get_tuning(self.ctx_handle(i), C.byref(t))
+        if st != 0:
+            raise GS2Error(f"gs2_get_tuning: {STATUS.get(st, st)}")
+        return _tuning_dict(t)
+
+    def set_tuning(self, i: int, sort_blocks: int, sort_rows: int, view_lanes: int = 1, accum_px: int = 2,
+                   accum_split: int = 0):
+        t = Tuning_(int(sort_blocks), int(sort_rows), int(view_lanes), int(accum_px), int(accum_split))
         st = _lib.gs2_set_tuning(self.ctx_handle(i), C.byref(t))
         if st != 0:
             raise GS2Error(f"gs2_set_tuning: {STATUS.get(st, st)}")

@@ -131,9 +131,9 @@ def test_autotune_keeps_scene_and_results():
     for name in NAMES:
         assert torch.equal(getattr(ds, name), getattr(before, name)), name
     assert best["sort_blocks"] in (296, 592, 888) and best["sort_rows"] in (2, 4, 8, 16) and best["ms"] > 0
-    assert best["accum_px"] in (2, 4)
+    assert best["accum_px"] in (2, 4) and best["accum_split"] in (0, 256, 1024)
     assert ctx.tuning() == dict(sort_blocks=best["sort_blocks"], sort_rows=best["sort_rows"], view_lanes=1,
-                                accum_px=best["accum_px"])
+                                accum_px=best["accum_px"], accum_split=best["accum_split"])
     ctx.sweep(ds, s["cams"], targets[2], knns[2], 1)
     ref = gs2.DeviceScene.from_host(s["train"])
     ctx2 = gs2.Context(s["n"], s["w"], s["h"], 3, 64 * s["n"])

@@ -167,8 +167,11 @@ def _colour_full(blocks, n_views, S, n):
     return g, H
 
 
-def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, extra=None, tuning=None):
+def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, extra=None, tuning=None,
+                 opacity_scale=1.0):
     sc, cams = _tiny(n=n, size=size, sh=sh)
+    if opacity_scale != 1.0:   # fainter Gaussians: long walks through the tile lists
+        sc.opacity = (sc.opacity * opacity_scale).astype(np.float32)
     ctx, gcfg, ocfg = _setup(gs2, sc, cams, dict(lambda_ssim=lam, **(extra or {})))
     if tuning:
         ctx.set_tuning(**tuning)
@@ -195,7 +198,7 @@ def _blocks_case(gs2, group, sh=0, lam=0.2, secondary=False, n=1000, size=128, e
         g = b[: D * sc.n].reshape(D, sc.n)
         H = b[D * sc.n: (D + D * (D + 1) // 2) * sc.n].reshape(D * (D + 1) // 2, sc.n)
     return dict(sc=sc, g=g, H=H, ob=ob, amb=amb, ctx=ctx, ocfg=ocfg, ds=ds, cams=cams, vcam=vcam,
-                primary=primary, blocks=blocks, target=target)
+                primary=primary, blocks=blocks, target=target, rs=rs)
 
 
 def _check_blocks(r, gtol=1e-4, htol=1e-3):
