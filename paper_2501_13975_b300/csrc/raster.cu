@@ -14,8 +14,9 @@
 // the colour its entries from c_j on add (sum of alpha T c~, kept per segment
 // between checkpoints and summed from the back once the walk ends: no
 // difference of two nearly equal colours, which would lose the digits of a
-// deep T), and the tile's walk length (the largest list position after a
-// last contributor).
+// deep T; the pixel's colour is then the sum of its segments, added back to
+// front), and the tile's walk length (the largest list position after a last
+// contributor).
 #include "common.cuh"
 
 template <bool CK>
@@ -36,8 +37,7 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
     const uint2 r = ranges[tile];
     const int n = (int)(r.y - r.x);
     const float fx = (float)px, fy = (float)py;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;   // CK: colour of the current segment
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;   // CK: colour of the current segment
     uint32_t lastc = 0u;
     const int nbat = (n + GS2_TILE_PIX - 1) / GS2_TILE_PIX;
     // checkpoint j (list position j ck_every, j >= 1) of this tile goes to slot
@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
             // contributor lies behind this point, which are not done)
             if (b > 0 && b % ck_b == 0) {
                 ++nck;
-                rv.ck[(ck_base + (size_t)nck) * GS2_TILE_PIX + lp] = make_float4(T, s0, s1, s2);
-                s0 = s1 = s2 = 0.f;
+                rv.ck[(ck_base + (size_t)nck) * GS2_TILE_PIX + lp] = make_float4(T, c0, c1, c2);
+                c0 = c1 = c2 = 0.f;
             }
         }
         if (b + 1 < nbat) {
@@ -97,14 +97,48 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
             c0 = fmaf(wgt, C.x, c0);
             c1 = fmaf(wgt, C.y, c1);
             c2 = fmaf(wgt, C.z, c2);
-            if constexpr (CK) {
-                s0 = fmaf(wgt, C.x, s0);
-                s1 = fmaf(wgt, C.y, s1);
-                s2 = fmaf(wgt, C.z, s2);
-            }
             T = tt;
             lastc = (uint32_t)(b0 + i + 1);
         }
+    }
+    if constexpr (CK) {
+        // checkpoint j: (T(c_j), colour of [c_j, end)), summed from the back
+        // over this thread's own checkpoints (it wrote them: no barrier).  The
+        // accumulation reads checkpoint j of this pixel only if its last
+        // contributor lies behind c_j (j <= jmax); the segments from c_{jmax+1}
+        // on add no colour, so the sum starts at slot jmax + 1.
+        const int jmax = lastc ? min(nck, (int)((lastc - 1u) / (uint32_t)rv.ck_every)) : 0;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (jmax == nck) {   // the last segment holds the last contributor
+            b0 = c0;
+            b1 = c1;
+            b2 = c2;
+        }
+        float4 *base = rv.ck + ck_base * GS2_TILE_PIX + lp;
+        // four slots loaded at once: (T(c_j), colour of [c_{j-1}, c_j))
+        for (int j = min(nck, jmax + 1); j >= 1; j -= 4) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = j - u >= 1 ? base[(size_t)(j - u) * GS2_TILE_PIX] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j - u >= 1 && j - u <= jmax) base[(size_t)(j - u) * GS2_TILE_PIX] = make_float4(v[u].x, b0, b1, b2);
+                b0 += v[u].y;
+                b1 += v[u].z;
+                b2 += v[u].w;
+            }
+        }
+        c0 = b0;   // the pixel's colour
+        c1 = b1;
+        c2 = b2;
+        // the tile's walk length
+        const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, lastc);
+        if (t == 0) sMax = 0u;
+        __syncthreads();
+        if ((t & 31) == 0) atomicMax(&sMax, wm);
+        __syncthreads();
+        if (t == 0) rv.tile_maxlast[tile] = sMax;
     }
     if (inside) {
         const size_t P = (size_t)W * H, p = (size_t)py * W + px;
@@ -113,26 +147,6 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
         image[2 * P + p] = c2;
         rv.tfinal[p] = T;
         rv.last[p] = lastc;
-    }
-    if constexpr (CK) {
-        // checkpoint j: (T(c_j), colour of [c_j, end)), summed from the back
-        // over this thread's own checkpoints (it wrote them: no barrier)
-        float b0 = s0, b1 = s1, b2 = s2;
-        for (int j = nck; j >= 1; --j) {
-            float4 *ck = &rv.ck[(ck_base + (size_t)j) * GS2_TILE_PIX + lp];
-            const float4 v = *ck;   // (T(c_j), colour of [c_{j-1}, c_j))
-            *ck = make_float4(v.x, b0, b1, b2);
-            b0 += v.y;
-            b1 += v.z;
-            b2 += v.w;
-        }
-        // the tile's walk length
-        const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, lastc);
-        if (t == 0) sMax = 0u;
-        __syncthreads();
-        if ((t & 31) == 0) atomicMax(&sMax, wm);
-        __syncthreads();
-        if (t == 0) rv.tile_maxlast[tile] = sMax;
     }
 }
 
