@@ -81,16 +81,14 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
         }
         const int buf = b & 1, b0 = b * GS2_TILE_PIX;
         const int m = min(GS2_TILE_PIX, n - b0);
-        for (int i = 0; i < m && !done; ++i) {
-            const float4 A = sA[buf][i];
+        // one list entry that lies in the pixel's support (q <= l): composite or stop
+        auto composite = [&](int i, float q) {
             const float4 B = sB[buf][i];
-            const float q = dec_quad(A.z, A.w, B.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
-            if (!(q <= B.z)) continue;   // sigma G < alpha_min
             const float alpha = q < B.w ? amax : __fmul_rn(B.y, gs2_falloff(q));
             const float tt = __fmul_rn(T, __fsub_rn(1.f, alpha));
             if (tt < tmin) {
                 done = true;
-                break;
+                return;
             }
             const float4 C = sC[buf][i];
             const float wgt = alpha * T;
@@ -99,6 +97,30 @@ __global__ void __launch_bounds__(GS2_TILE_PIX) k_raster(const uint2 *__restrict
             c2 = fmaf(wgt, C.z, c2);
             T = tt;
             lastc = (uint32_t)(b0 + i + 1);
+        };
+        // four entries at a time: their quadratic forms do not depend on one
+        // another, so their loads and arithmetic overlap; the composites
+        // then follow in list order (the same operations as one at a time)
+        int i = 0;
+        for (; i + 4 <= m && !done; i += 4) {
+            float q[4];
+            uint32_t hit = 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 A = sA[buf][i + u];
+                const float2 Bxz = make_float2(sB[buf][i + u].x, sB[buf][i + u].z);
+                q[u] = dec_quad(A.z, A.w, Bxz.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
+                hit |= (q[u] <= Bxz.y) ? 1u << u : 0u;   // sigma G >= alpha_min
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (!done && (hit >> u & 1u)) composite(i + u, q[u]);
+        }
+        for (; i < m && !done; ++i) {
+            const float4 A = sA[buf][i];
+            const float2 Bxz = make_float2(sB[buf][i].x, sB[buf][i].z);
+            const float q = dec_quad(A.z, A.w, Bxz.x, __fsub_rn(fx, A.x), __fsub_rn(fy, A.y));
+            if (q <= Bxz.y) composite(i, q);
         }
     }
     if constexpr (CK) {
