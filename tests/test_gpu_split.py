@@ -146,6 +146,32 @@ def test_split_sweep_equals_whole_walk_sweep(gs2, lanes):
     _close(out[1], out[0], gs2.DeviceScene.from_host(train))
 
 
+@pytest.mark.parametrize("variant", ["jacobi", "gauss-newton", "networks"])
+def test_split_sweep_variants_equal_whole_walks(gs2, variant):
+    """The split walks under the other sweep forms: the single-render sweep
+    (every group accumulated from one compositing per view), Gauss-Newton
+    blocks, and the learned damping and step-scale networks (the view lanes
+    then accumulate into their own blocks) equal the same sweep with whole
+    walks, from the same snapshot, up to the rounding of atomic order."""
+    train, cams, targets, knn = _dense_sweep_setup(gs2)
+    cfg = dict(group_jacobi=1) if variant == "jacobi" else dict(gauss_newton=1) if variant == "gauss-newton" else {}
+    out = []
+    for split in (0, 256):
+        ctx = gs2.Context(train.n, 64, 64, 1, 0, cfg)
+        ctx.set_tuning(accum_split=split)
+        if variant == "networks":
+            _, dbits = synth.mlp_init(67, out_scale=2.0)
+            _, sbits = synth.mlp_init(68, out_scale=1.0)
+            ctx.set_damping_model(torch.tensor(dbits.astype(np.int16), device="cuda"))
+            ctx.set_step_model(torch.tensor(sbits.astype(np.int16), device="cuda"))
+        s = gs2.DeviceScene.from_host(train)
+        ctx.sweep(s, cams, targets, knn, 1)
+        torch.cuda.synchronize()
+        ctx.check()
+        out.append(s)
+    _close(out[1], out[0], gs2.DeviceScene.from_host(train))
+
+
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_split_batched_graph_equals_eager(gs2, use_graph):
     """A one-scene batch with split walks (eager fork/join, or captured as a
