@@ -283,6 +283,17 @@ static uint64_t sweep_key(const gs2_ctx *c, const gs2_scene *scene, const gs2_ca
     fnv(h, &c->view_lanes, sizeof(c->view_lanes));
     fnv(h, &c->accum_px, sizeof(c->accum_px));
     fnv(h, &c->accum_split, sizeof(c->accum_split));
+    // buffers that a tuning change can reallocate (the split walks'
+    // checkpoints and items, of the context and its view lanes): a graph
+    // captured with the old ones must not match
+    for (int i = -1; i < c->n_lanes; ++i) {
+        const gs2_ctx *l = i < 0 ? c : c->lanes[i];
+        if (!l) continue;
+        fnv(h, &l->ck, sizeof(l->ck));
+        fnv(h, &l->tile_maxlast, sizeof(l->tile_maxlast));
+        fnv(h, &l->acc_items, sizeof(l->acc_items));
+        fnv(h, &l->acc_ctrl, sizeof(l->acc_ctrl));
+    }
     return h;
 }
 

@@ -200,6 +200,33 @@ def test_split_batched_graph_equals_eager(gs2, use_graph):
     assert bool((losses[:, 0] > 0).all())
 
 
+def test_kept_graphs_follow_split_buffer_changes(gs2):
+    """Kept graphs (use_graph = 2) across tuning changes that reallocate the
+    split walks' checkpoints (1024 -> 256 -> 1024 entries per item): every
+    batched sweep equals gs2_sweep with the same settings from the same
+    snapshot (a graph captured with the freed buffers is not replayed: the
+    graph key holds the buffers' addresses)."""
+    train, cams, targets, knn = _dense_sweep_setup(gs2)
+    size = dict(max_gaussians=train.n, max_width=64, max_height=64, max_sh_degree=1, max_pairs=0)
+    batch = gs2.Batch([size])
+    tun = batch.tuning(0)
+    s = gs2.DeviceScene.from_host(train)
+    prep = batch.prepare([s], [cams], [targets], [knn])
+    for split in (1024, 256, 1024):
+        batch.set_tuning(0, tun["sort_blocks"], tun["sort_rows"], tun["view_lanes"], tun["accum_px"], split)
+        ref_ctx = gs2.Context(train.n, 64, 64, 1, 0)
+        ref_ctx.set_tuning(accum_split=split)
+        for t in (0, 3):
+            snap = s.clone()
+            ref = s.clone()
+            batch.sweep(prep, [t], use_graph=2)
+            ref_ctx.sweep(ref, cams, targets, knn, t)
+            torch.cuda.synchronize()
+            batch.check()
+            ref_ctx.check()
+            _close(s, ref, snap)
+
+
 def test_split_tuning_validation(gs2):
     ctx = gs2.Context(100, 32, 32, 0)
     assert ctx.tuning()["accum_split"] == 0
