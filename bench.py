@@ -504,6 +504,8 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     work = synth.batched_workload(seed=8)
+    if args.batched_only:   # a subset of the 16 scenes (profiling captures)
+        work = [work[int(i)] for i in args.batched_only.split(",")]
     sizes = [dict(max_gaussians=w["n"], max_width=w["width"], max_height=w["height"], max_sh_degree=3,
                   max_pairs=96 * w["n"]) for w in work]
     batch = gs2.Batch(sizes)
@@ -585,12 +587,13 @@ def run_batched(args):
     launches = gs2.launch_count() - l0
     head = max((res["graph"], res["graph_kept"]), key=lambda r: r["scenes_per_s"])
     return {
-        "metric": "scenes/s (batched sweeps, 16 independent scenes)", "value": head["scenes_per_s"],
+        "metric": f"scenes/s (batched sweeps, {len(work)} independent scenes)", "value": head["scenes_per_s"],
         "unit": "scenes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_batched_sweep"]["mean"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched: 16 scenes, N log-uniform [20k, 500k], 16-128 views, 512x512..1024x768, "
                                "SH3, shells and spread scenes alternating (seed 8)",
+                   "subset": args.batched_only or None,
                    "gaussians_total": int(sum(w["n"] for w in work)),
                    "scenes": [{k: w[k] for k in ("kind", "n", "views", "width", "height")} for w in work],
                    "sweep_restart": "every mode starts from the training start"},
@@ -1174,6 +1177,8 @@ def main():
     ap.add_argument("--accum-split", type=int, default=-1,
                     help="list entries per work item of the split accumulation (overrides the tuning; 0: off, "
                          "-1: keep)")
+    ap.add_argument("--batched-only", default="",
+                    help="comma-separated indices of the batched workload's scenes to run (profiling captures)")
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: time sweeps as a CUDA graph re-captured per sweep (one-scene gs2_batch); 0: eager")
     ap.add_argument("--variants", action="store_true",
