@@ -103,3 +103,44 @@ def test_model_setters_refuse_a_null_context():
     for name in ("gs2_set_step_model", "gs2_set_damping_model"):
         f = getattr(gs2._lib, name)
         assert f(None, None) == 1, name
+
+
+def _header_structs():
+    """Field (name, byte size) lists of the anonymous typedef structs in gs2.h, by typedef name."""
+    src = open(os.path.join(ROOT, "include", "gs2.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    size = {"int32_t": 4, "uint32_t": 4, "float": 4, "int64_t": 8, "double": 8}
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(gs2_[a-z_]+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            m = re.match(r"(\w+)\s*(\*?)\s*(.*)", decl)
+            ctype, ptr, names = m.group(1), m.group(2), m.group(3)
+            for nm in names.split(","):
+                nm = nm.strip()
+                star = ptr or nm.startswith("*")
+                nm = nm.lstrip("*").strip()
+                arr = re.match(r"(\w+)\[(\d+)\]", nm)
+                count = int(arr.group(2)) if arr else 1
+                nm = arr.group(1) if arr else nm
+                fields.append((nm, (8 if star else size[ctype]) * count))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_header():
+    """The binding's ctypes structures have the header's fields, in order and
+    with the same sizes (a field added on one side only would shift the rest)."""
+    import ctypes as C
+
+    from paper_2501_13975_b300 import gs2
+    hs = _header_structs()
+    pairs = {"gs2_tuning": gs2.Tuning_, "gs2_config": gs2.Config_, "gs2_camera": gs2.Camera_,
+             "gs2_scene": gs2.Scene_, "gs2_batch_scene": gs2.BatchScene_}
+    for cname, pyt in pairs.items():
+        assert cname in hs, cname
+        py = [(n, C.sizeof(t)) for n, t in pyt._fields_]
+        assert py == hs[cname], (cname, py, hs[cname])
