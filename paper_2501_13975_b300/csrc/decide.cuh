@@ -182,12 +182,23 @@ __device__ __forceinline__ SupportRows support_rows(float px, float py, float ca
     return s;
 }
 
-// Does the support reach a pixel of the tile with pixel rows [y0, y0 + t) and
-// columns [x0, x0 + t)?
-__device__ __forceinline__ bool support_reaches(const SupportRows &s, float x0, float y0, float tile) {
+// The support over the pixel rows [y0, y0 + t) of a tile row: ok when some
+// integer pixel row lies in its y-extent, and then the integer pixel columns
+// [ceil(xl), floor(xr)] it may reach in that band (one computation serves
+// every tile of the row).
+struct SupportRow {
+    bool ok;
+    float cl, cr;
+};
+
+__device__ __forceinline__ SupportRow support_row(const SupportRows &s, float y0, float tile) {
+    SupportRow o;
     const float ylo = fmaxf(y0, ceilf(D_SUB(s.py, s.ry)));
     const float yhi = fminf(D_SUB(D_ADD(y0, tile), 1.f), floorf(D_ADD(s.py, s.ry)));
-    if (!(ylo <= yhi)) return false;
+    o.ok = ylo <= yhi;
+    o.cl = 1.f;
+    o.cr = 0.f;
+    if (!o.ok) return o;
     const float ya = D_SUB(ylo, s.py), yb = D_SUB(yhi, s.py);
     const float yr = fminf(fmaxf(s.ystar, ya), yb), yl = fminf(fmaxf(-s.ystar, ya), yb);
     const float r2 = D_MUL(s.ry, s.ry);
@@ -195,8 +206,20 @@ __device__ __forceinline__ bool support_reaches(const SupportRows &s, float x0, 
     const float hl = D_SQRT(fmaxf(D_MUL(s.k2, D_SUB(r2, D_MUL(yl, yl))), 0.f));
     const float xr = D_ADD(D_ADD(D_FMA(s.k1, yr, s.px), hr), s.marg);   // rightmost reach in the band
     const float xl = D_SUB(D_SUB(D_FMA(s.k1, yl, s.px), hl), s.marg);   // leftmost
-    // some integer pixel column of the tile lies in [xl, xr]
-    const float c0 = fmaxf(ceilf(xl), x0);
-    const float c1 = fminf(floorf(xr), D_SUB(D_ADD(x0, tile), 1.f));
-    return c0 <= c1;
+    o.cl = ceilf(xl);
+    o.cr = floorf(xr);
+    return o;
+}
+
+// some integer pixel column of the tile [x0, x0 + t) lies in the row's range
+__device__ __forceinline__ bool support_row_reaches(const SupportRow &o, float x0, float tile) {
+    const float c0 = fmaxf(o.cl, x0);
+    const float c1 = fminf(o.cr, D_SUB(D_ADD(x0, tile), 1.f));
+    return o.ok && c0 <= c1;
+}
+
+// Does the support reach a pixel of the tile with pixel rows [y0, y0 + t) and
+// columns [x0, x0 + t)?
+__device__ __forceinline__ bool support_reaches(const SupportRows &s, float x0, float y0, float tile) {
+    return support_row_reaches(support_row(s, y0, tile), x0, tile);
 }

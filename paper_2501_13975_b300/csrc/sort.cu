@@ -230,63 +230,78 @@ __global__ void __launch_bounds__(256) k_emit(ProjView pv, const uint32_t *__res
                                               unsigned long long *stats, uint32_t *__restrict__ ids_emit) {
     __shared__ uint32_t s_off[256];
     __shared__ uint2 s_rect[256];
-    __shared__ float s_inv[256];      // 1 / rectangle width
     __shared__ SupportRows s_sr[256];
     __shared__ uint32_t s_id[256];
-    __shared__ uint32_t s_beg, s_end;
-    const int t = threadIdx.x;
+    __shared__ uint32_t s_row[256];    // exclusive prefix of the rectangles' tile rows over the CTA's ranks
+    __shared__ uint32_t s_wsum[8];
+    __shared__ uint32_t s_end, s_rows;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int r = blockIdx.x * 256 + t;
     const uint32_t id = (r < n) ? order[r] : 0u;
     const uint32_t cnt = (r < n) ? pv.tsort[r] : 0u;
     if (stats) {  // visible-Gaussian count, one atomic per warp
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, cnt != 0u);
-        if ((t & 31) == 0 && b) atomicAdd(&stats[1], (unsigned long long)__popc(b));
+        if (lane == 0 && b) atomicAdd(&stats[1], (unsigned long long)__popc(b));
     }
     const uint32_t off = (r < n) ? pv.offs[r] : 0u;
-    s_off[t] = (r < n) ? off : 0xFFFFFFFFu;
-    s_rect[t] = (cnt != 0u) ? pv.rect[id] : make_uint2(0u, 0u);   // only ranks with pairs are looked up
+    s_off[t] = off;
+    const uint2 rc = (cnt != 0u) ? pv.rect[id] : make_uint2(0u, 0u);   // only ranks with pairs are looked up
+    s_rect[t] = rc;
     s_id[t] = id;
     if (cnt != 0u) {
         const float4 A = pv.recA[id];
         s_sr[t] = support_rows(A.x, A.y, A.z, A.w, pv.k2[id], pv.col[id].w);
-        const uint2 rc = s_rect[t];
-        s_inv[t] = 1.f / (float)((rc.y & 0xFFFFu) - (rc.x & 0xFFFFu));
     }
+    // tile rows of this rank's rectangle (its pairs are row-major in it)
+    const uint32_t h = cnt != 0u ? (rc.y >> 16) - (rc.x >> 16) : 0u;
+    uint32_t inc = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) s_wsum[w] = inc;
     const int last = min(n - 1, blockIdx.x * 256 + 255) - blockIdx.x * 256;
     if (t == last) s_end = min(off + cnt, cap);   // offsets are already clamped to cap
-    if (t == 0) s_beg = off;
     __syncthreads();
-    const uint32_t beg = s_beg, end = s_end;
-    for (uint32_t j = beg + t; j < end; j += 256) {
-        int lo = 0, hi = last;   // largest i with s_off[i] <= j
+    uint32_t wbase = 0u, tot = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t v = s_wsum[q];
+        wbase += q < w ? v : 0u;
+        tot += v;
+    }
+    s_row[t] = wbase + inc - h;
+    if (t == 0) s_rows = tot;
+    __syncthreads();
+    const uint32_t end = s_end, nrows = s_rows;
+    // one (rank, tile row) per thread and step: the support's column range in
+    // that band once, then the row's tiles in order
+    for (uint32_t u = t; u < nrows; u += 256) {
+        int lo = 0, hi = last;   // largest i with s_row[i] <= u (a rank with rows)
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= j) lo = mid;
+            if (s_row[mid] <= u) lo = mid;
             else hi = mid - 1;
         }
-        const uint2 rc = s_rect[lo];
-        const uint32_t tx0 = rc.x & 0xFFFFu, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFFu;
-        const uint32_t wdt = tx1 - tx0, rel = j - s_off[lo];
-        // rel / wdt: the float product is within 0.25 of the quotient (rel < 2^20
-        // tiles), so one step either way makes it exact
-        uint32_t row = (uint32_t)((float)rel * s_inv[lo]);
-        int rem = (int)rel - (int)(row * wdt);
-        if (rem < 0) {
-            --row;
-            rem += (int)wdt;
-        } else if (rem >= (int)wdt) {
-            ++row;
-            rem -= (int)wdt;
-        }
-        const uint32_t tx = tx0 + (uint32_t)rem, ty = ty0 + row;
-        const bool live =
-            support_reaches(s_sr[lo], (float)(tx * GS2_TILE), (float)(ty * GS2_TILE), (float)GS2_TILE);
-        keys[j] = live ? ty * (uint32_t)tiles_x + tx : ntiles;
-        if (ids_emit) {
-            vals[j] = j;
-            ids_emit[j] = live ? s_id[lo] : 0xFFFFFFFFu;
-        } else {
-            vals[j] = s_id[lo];
+        const uint2 rr = s_rect[lo];
+        const uint32_t tx0 = rr.x & 0xFFFFu, ty0 = rr.x >> 16, tx1 = rr.y & 0xFFFFu;
+        const uint32_t wdt = tx1 - tx0, row = u - s_row[lo];
+        const uint32_t base = s_off[lo] + row * wdt;
+        if (base >= end) continue;
+        const uint32_t ty = ty0 + row, gid = s_id[lo];
+        const SupportRow band = support_row(s_sr[lo], (float)(ty * GS2_TILE), (float)GS2_TILE);
+        const uint32_t m = min(wdt, end - base);
+        for (uint32_t c = 0; c < m; ++c) {
+            const uint32_t j = base + c, tx = tx0 + c;
+            const bool live = support_row_reaches(band, (float)(tx * GS2_TILE), (float)GS2_TILE);
+            keys[j] = live ? ty * (uint32_t)tiles_x + tx : ntiles;
+            if (ids_emit) {
+                vals[j] = j;
+                ids_emit[j] = live ? gid : 0xFFFFFFFFu;
+            } else {
+                vals[j] = gid;
+            }
         }
     }
 }
