@@ -489,266 +489,266 @@ __global__ void __launch_bounds__(AccumShape<GROUP, NQ>::NT, AccumShape<GROUP, N
     const size_t PI = (size_t)W * H;
     uint32_t nact = 0u;   // (pixel, Gaussian) evaluations this thread did (profile statistic)
     for (;;) {
-    int tile, c0 = 0, c1 = 0x7FFFFFFF;   // list entries [c0, c1) of the tile's walk
-    uint32_t slot = 0xFFFFFFFFu;        // checkpoint at c1
-    if constexpr (SPLIT) {
-        if (t == 0) {
-            const uint32_t i = atomicAdd(&ctrl[1], 1u);
-            sItem = i < ctrl[0] ? items[i] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-        }
-        __syncthreads();
-        const uint4 w = sItem;
-        if (w.x == 0xFFFFFFFFu) break;   // CTA-uniform
-        tile = (int)w.x;
-        c0 = (int)w.y;
-        c1 = (int)w.z;
-        slot = w.w;
-    } else {
-        tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
-    }
-    const int tcol = tile % tiles_x, trow = tile / tiles_x;
-    const int lx = (wb % GS2_WPR) * 8 + (t & 7), ly0 = (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
-    const int px = tcol * GS2_TILE + lx;
-    const int py = trow * GS2_TILE + ly0;
-    uint32_t last[NQ];
-    PairState pst[NPR];
-    float2 pe2[EH_SMEM ? 1 : NPR][3], ph2[EH_SMEM ? 1 : NPR][3];   // e, h in registers (two pixels a thread)
-    float2 pyf[NPR];
-#pragma unroll
-    for (int r = 0; r < NPR; ++r) {
-        float e[2][3], h[2][3], T[2], cb[2][3];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int y = py + 4 * (2 * r + j);
-            const bool inside = px < W && y < H;
-            last[2 * r + j] = 0u;   // outside the image: no list entry is composited
-            T[j] = 1.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) e[j][c] = h[j][c] = cb[j][c] = 0.f;
-            if (inside) {
-                const size_t pp = (size_t)y * W + px;
-                last[2 * r + j] = rv.last[pp];
-                T[j] = rv.tfinal[pp];
-                if constexpr (SPLIT) {
-                    if (last[2 * r + j] > (uint32_t)c1) {   // composites past c1: start at the checkpoint
-                        const int lp = (ly0 + 4 * (2 * r + j)) * GS2_TILE + lx;
-                        const float4 ck = rv.ck[(size_t)slot * GS2_TILE_PIX + lp];
-                        T[j] = ck.x;
-                        // T >= t_min > 0 where the compositing went on; with t_min = 0 an
-                        // underflowed T leaves every weight in front zero, as the whole walk does
-                        const float iT = ck.x > 0.f ? 1.f / ck.x : 0.f;
-                        cb[j][0] = ck.y * iT;
-                        cb[j][1] = ck.z * iT;
-                        cb[j][2] = ck.w * iT;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    e[j][c] = E[c * PI + pp];
-                    h[j][c] = Hh[c * PI + pp];
-                }
+        int tile, c0 = 0, c1 = 0x7FFFFFFF;   // list entries [c0, c1) of the tile's walk
+        uint32_t slot = 0xFFFFFFFFu;        // checkpoint at c1
+        if constexpr (SPLIT) {
+            if (t == 0) {
+                const uint32_t i = atomicAdd(&ctrl[1], 1u);
+                sItem = i < ctrl[0] ? items[i] : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
             }
-        }
-        pst[r].T = make_float2(T[0], T[1]);
-        pst[r].cb0 = make_float2(cb[0][0], cb[1][0]);
-        pst[r].cb1 = make_float2(cb[0][1], cb[1][1]);
-        pst[r].cb2 = make_float2(cb[0][2], cb[1][2]);
-        pyf[r] = make_float2((float)(py + 8 * r), (float)(py + 8 * r + 4));
-        if constexpr (EH_SMEM) {
-            sEP[r][0][t] = make_float4(e[0][0], e[1][0], e[0][1], e[1][1]);
-            sEP[r][1][t] = make_float4(e[0][2], e[1][2], h[0][0], h[1][0]);
-            sEP[r][2][t] = make_float4(h[0][1], h[1][1], h[0][2], h[1][2]);
+            __syncthreads();
+            const uint4 w = sItem;
+            if (w.x == 0xFFFFFFFFu) break;   // CTA-uniform
+            tile = (int)w.x;
+            c0 = (int)w.y;
+            c1 = (int)w.z;
+            slot = w.w;
         } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                pe2[r][c] = make_float2(e[0][c], e[1][c]);
-                ph2[r][c] = make_float2(h[0][c], h[1][c]);
-            }
+            tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;   // longest lists first
         }
-    }
-    uint32_t last2 = last[0];
+        const int tcol = tile % tiles_x, trow = tile / tiles_x;
+        const int lx = (wb % GS2_WPR) * 8 + (t & 7), ly0 = (wb / GS2_WPR) * (4 * NQ) + ((t >> 3) & 3);
+        const int px = tcol * GS2_TILE + lx;
+        const int py = trow * GS2_TILE + ly0;
+        uint32_t last[NQ];
+        PairState pst[NPR];
+        float2 pe2[EH_SMEM ? 1 : NPR][3], ph2[EH_SMEM ? 1 : NPR][3];   // e, h in registers (two pixels a thread)
+        float2 pyf[NPR];
 #pragma unroll
-    for (int q = 1; q < NQ; ++q) last2 = max(last2, last[q]);
-    if (t == 0) sMax = 0u;
-    __syncthreads();
-    atomicMax(&sMax, last2);
-    __syncthreads();
-    const int maxlast = (int)sMax;
-    const int hi = min(c1, maxlast);   // end of this walk
-    // this warp's own end of list: its lanes have nothing to do beyond it
-    const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last2);
-    const uint2 r = ranges[tile];
-    const float fx = (float)px;
-    // batches back to front: batch b covers [max(c0, hi - NB (b + 1)), hi - NB b)
-    const int nbat = hi > c0 ? (hi - c0 + NB - 1) / NB : 0;
-    auto list_index = [&](int b, int i) { return hi - NB * (b + 1) + t + i * NT; };
-    uint32_t knext[PER];
-    auto fetch = [&](int b) {
+        for (int r = 0; r < NPR; ++r) {
+            float e[2][3], h[2][3], T[2], cb[2][3];
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int li = list_index(b, i);
-            knext[i] = li >= c0 ? ids[r.x + li] : 0u;
-        }
-    };
-    auto issue = [&](int b) {
-        const int buf = b & 1;
+            for (int j = 0; j < 2; ++j) {
+                const int y = py + 4 * (2 * r + j);
+                const bool inside = px < W && y < H;
+                last[2 * r + j] = 0u;   // outside the image: no list entry is composited
+                T[j] = 1.f;
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int j = t + i * NT;
-            if (list_index(b, i) >= c0) {
-                const uint32_t k = knext[i];
-                sId[buf][j] = k;
-                cp_async16(&sA[buf][j], &pv.recA[k]);
-                cp_async16(&sB[buf][j], &pv.recB[k]);
-                if constexpr (GROUP != GS2_COLOR) cp_async16(&sC[buf][j], &pv.col[k]);   // colour: no c~
-            }
-        }
-        cp_async_commit();
-    };
-    if (nbat > 0) {
-        fetch(0);
-        issue(0);
-        if (nbat > 1) fetch(1);
-    }
-    for (int b = 0; b < nbat; ++b) {
-        cp_async_wait_all();
-        __syncthreads();   // batch b visible to all; everyone is done with batch b - 1's buffer
-        if (b + 1 < nbat) {
-            issue(b + 1);
-            if (b + 2 < nbat) fetch(b + 2);
-        }
-        const int buf = b & 1;
-        const int bend = hi - NB * b, bbeg = max(c0, bend - NB);
-        const int base = bend - NB;   // list index of slot 0 of this batch (may be negative)
-        // one list entry (back to front): its payload, then the warp sum
-        // (atomics, or stored to `row` in deterministic mode)
-        auto entry = [&](int jj, float *row) {
-            const int s = jj - base;
-            const float4 A = sA[buf][s], B = sB[buf][s];
-            const float dx = __fsub_rn(fx, A.x);
-            const float2 dxv = f2(dx);
-            float2 dy[NPR], qf[NPR];
-            bool lv[NPR][2];
-            bool any = false;
-#pragma unroll
-            for (int r = 0; r < NPR; ++r) {
-                dy[r] = add2(pyf[r], f2(-A.y));
-                // dec_quad of both pixels (the same correctly rounded operations, in the same order)
-                float2 qa = fma2(f2(A.z), dxv, mul2(f2(A.w), dy[r]));
-                qa = fma2(f2(A.w), dy[r], qa);
-                qf[r] = fma2(dxv, qa, mul2(mul2(f2(B.x), dy[r]), dy[r]));
-                lv[r][0] = (uint32_t)jj < last[2 * r] && qf[r].x <= B.z;   // composited (as k_raster)
-                lv[r][1] = (uint32_t)jj < last[2 * r + 1] && qf[r].y <= B.z;
-                any = any || lv[r][0] || lv[r][1];
-                nact += (lv[r][0] ? 1u : 0u) + (lv[r][1] ? 1u : 0u);
-            }
-            if (!__any_sync(0xFFFFFFFFu, any)) return;
-            float2 G[NPR], al[NPR], ap[NPR];
-#pragma unroll
-            for (int r = 0; r < NPR; ++r) {
-                const float2 xg = mul2(qf[r], f2(-0.72134752044448170368f));   // gs2_falloff, both pixels
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G[r].x) : "f"(xg.x));
-                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G[r].y) : "f"(xg.y));
-                const bool c0 = qf[r].x < B.w, c1 = qf[r].y < B.w;   // clamped at alpha_max
-                al[r] = mul2(f2(B.y), G[r]);
-                al[r].x = lv[r][0] ? (c0 ? amax : al[r].x) : 0.f;
-                al[r].y = lv[r][1] ? (c1 ? amax : al[r].y) : 0.f;
-                ap[r] = make_float2(c0 ? 0.f : al[r].x, c1 ? 0.f : al[r].y);
-            }
-            float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (GROUP != GS2_COLOR) C = sC[buf][s];
-            float pl[P];
-            if constexpr (GROUP == GS2_POS) {
-                float2 pe[NPR][3], ph[NPR][3];
-#pragma unroll
-                for (int r = 0; r < NPR; ++r) {
-                    if constexpr (EH_SMEM) {
-                        const float4 k0 = sEP[r][0][t], k1 = sEP[r][1][t], k2 = sEP[r][2][t];
-                        pe[r][0] = make_float2(k0.x, k0.y);
-                        pe[r][1] = make_float2(k0.z, k0.w);
-                        pe[r][2] = make_float2(k1.x, k1.y);
-                        ph[r][0] = make_float2(k1.z, k1.w);
-                        ph[r][1] = make_float2(k2.x, k2.y);
-                        ph[r][2] = make_float2(k2.z, k2.w);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            pe[r][c] = pe2[r][c];
-                            ph[r][c] = ph2[r][c];
+                for (int c = 0; c < 3; ++c) e[j][c] = h[j][c] = cb[j][c] = 0.f;
+                if (inside) {
+                    const size_t pp = (size_t)y * W + px;
+                    last[2 * r + j] = rv.last[pp];
+                    T[j] = rv.tfinal[pp];
+                    if constexpr (SPLIT) {
+                        if (last[2 * r + j] > (uint32_t)c1) {   // composites past c1: start at the checkpoint
+                            const int lp = (ly0 + 4 * (2 * r + j)) * GS2_TILE + lx;
+                            const float4 ck = rv.ck[(size_t)slot * GS2_TILE_PIX + lp];
+                            T[j] = ck.x;
+                            // T >= t_min > 0 where the compositing went on; with t_min = 0 an
+                            // underflowed T leaves every weight in front zero, as the whole walk does
+                            const float iT = ck.x > 0.f ? 1.f / ck.x : 0.f;
+                            cb[j][0] = ck.y * iT;
+                            cb[j][1] = ck.z * iT;
+                            cb[j][2] = ck.w * iT;
                         }
                     }
-                }
-                const uint32_t k = sId[buf][s];
-                pos_pairs<NPR>(
-                    pst, pe, ph, A, B, C, al, ap, lv, dx, dy, gn != 0, pl,
-                    [&](const float (&v)[P]) {
-                        if constexpr (DET)
-                            reduce_scatter_part<P - 32, 32, P, float, 16, true>(v, lane, nullptr, 0, 0u, row);
-                        else
-                            reduce_scatter_part<P - 32, 32, P, ACC>(v, lane, zbuf, n, k);
-                    },
-                    [&](const float (&v)[P]) {
-                        if constexpr (DET)
-                            reduce_scatter_part<32, 0, P, float, 16, true>(v, lane, nullptr, 0, 0u, row);
-                        else
-                            reduce_scatter_part<32, 0, P, ACC>(v, lane, zbuf, n, k);
-                    });
-                return;
-            } else {
-                float2 pl2[P];
 #pragma unroll
-                for (int i = 0; i < P; ++i) pl2[i] = f2(0.f);
+                    for (int c = 0; c < 3; ++c) {
+                        e[j][c] = E[c * PI + pp];
+                        h[j][c] = Hh[c * PI + pp];
+                    }
+                }
+            }
+            pst[r].T = make_float2(T[0], T[1]);
+            pst[r].cb0 = make_float2(cb[0][0], cb[1][0]);
+            pst[r].cb1 = make_float2(cb[0][1], cb[1][1]);
+            pst[r].cb2 = make_float2(cb[0][2], cb[1][2]);
+            pyf[r] = make_float2((float)(py + 8 * r), (float)(py + 8 * r + 4));
+            if constexpr (EH_SMEM) {
+                sEP[r][0][t] = make_float4(e[0][0], e[1][0], e[0][1], e[1][1]);
+                sEP[r][1][t] = make_float4(e[0][2], e[1][2], h[0][0], h[1][0]);
+                sEP[r][2][t] = make_float4(h[0][1], h[1][1], h[0][2], h[1][2]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    pe2[r][c] = make_float2(e[0][c], e[1][c]);
+                    ph2[r][c] = make_float2(h[0][c], h[1][c]);
+                }
+            }
+        }
+        uint32_t last2 = last[0];
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) last2 = max(last2, last[q]);
+        if (t == 0) sMax = 0u;
+        __syncthreads();
+        atomicMax(&sMax, last2);
+        __syncthreads();
+        const int maxlast = (int)sMax;
+        const int hi = min(c1, maxlast);   // end of this walk
+        // this warp's own end of list: its lanes have nothing to do beyond it
+        const int wlast = (int)__reduce_max_sync(0xFFFFFFFFu, last2);
+        const uint2 r = ranges[tile];
+        const float fx = (float)px;
+        // batches back to front: batch b covers [max(c0, hi - NB (b + 1)), hi - NB b)
+        const int nbat = hi > c0 ? (hi - c0 + NB - 1) / NB : 0;
+        auto list_index = [&](int b, int i) { return hi - NB * (b + 1) + t + i * NT; };
+        uint32_t knext[PER];
+        auto fetch = [&](int b) {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int li = list_index(b, i);
+                knext[i] = li >= c0 ? ids[r.x + li] : 0u;
+            }
+        };
+        auto issue = [&](int b) {
+            const int buf = b & 1;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int j = t + i * NT;
+                if (list_index(b, i) >= c0) {
+                    const uint32_t k = knext[i];
+                    sId[buf][j] = k;
+                    cp_async16(&sA[buf][j], &pv.recA[k]);
+                    cp_async16(&sB[buf][j], &pv.recB[k]);
+                    if constexpr (GROUP != GS2_COLOR) cp_async16(&sC[buf][j], &pv.col[k]);   // colour: no c~
+                }
+            }
+            cp_async_commit();
+        };
+        if (nbat > 0) {
+            fetch(0);
+            issue(0);
+            if (nbat > 1) fetch(1);
+        }
+        for (int b = 0; b < nbat; ++b) {
+            cp_async_wait_all();
+            __syncthreads();   // batch b visible to all; everyone is done with batch b - 1's buffer
+            if (b + 1 < nbat) {
+                issue(b + 1);
+                if (b + 2 < nbat) fetch(b + 2);
+            }
+            const int buf = b & 1;
+            const int bend = hi - NB * b, bbeg = max(c0, bend - NB);
+            const int base = bend - NB;   // list index of slot 0 of this batch (may be negative)
+            // one list entry (back to front): its payload, then the warp sum
+            // (atomics, or stored to `row` in deterministic mode)
+            auto entry = [&](int jj, float *row) {
+                const int s = jj - base;
+                const float4 A = sA[buf][s], B = sB[buf][s];
+                const float dx = __fsub_rn(fx, A.x);
+                const float2 dxv = f2(dx);
+                float2 dy[NPR], qf[NPR];
+                bool lv[NPR][2];
+                bool any = false;
 #pragma unroll
                 for (int r = 0; r < NPR; ++r) {
-                    if constexpr (EH_SMEM) {
-                        const float4 k0 = sEP[r][0][t], k1 = sEP[r][1][t], k2 = sEP[r][2][t];
-                        const float2 pe[3] = {make_float2(k0.x, k0.y), make_float2(k0.z, k0.w), make_float2(k1.x, k1.y)};
-                        const float2 ph[3] = {make_float2(k1.z, k1.w), make_float2(k2.x, k2.y), make_float2(k2.z, k2.w)};
-                        pair_payload<GROUP, P>(pst[r], pe, ph, A, B, C, G[r], al[r], ap[r], lv[r][0], lv[r][1], dx,
-                                               dy[r], pl2);
-                    } else {
-                        pair_payload<GROUP, P>(pst[r], pe2[r], ph2[r], A, B, C, G[r], al[r], ap[r], lv[r][0],
-                                               lv[r][1], dx, dy[r], pl2);
-                    }
+                    dy[r] = add2(pyf[r], f2(-A.y));
+                    // dec_quad of both pixels (the same correctly rounded operations, in the same order)
+                    float2 qa = fma2(f2(A.z), dxv, mul2(f2(A.w), dy[r]));
+                    qa = fma2(f2(A.w), dy[r], qa);
+                    qf[r] = fma2(dxv, qa, mul2(mul2(f2(B.x), dy[r]), dy[r]));
+                    lv[r][0] = (uint32_t)jj < last[2 * r] && qf[r].x <= B.z;   // composited (as k_raster)
+                    lv[r][1] = (uint32_t)jj < last[2 * r + 1] && qf[r].y <= B.z;
+                    any = any || lv[r][0] || lv[r][1];
+                    nact += (lv[r][0] ? 1u : 0u) + (lv[r][1] ? 1u : 0u);
                 }
+                if (!__any_sync(0xFFFFFFFFu, any)) return;
+                float2 G[NPR], al[NPR], ap[NPR];
 #pragma unroll
-                for (int i = 0; i < P; ++i) pl[i] = pl2[i].x + pl2[i].y;
-            }
-            if constexpr (DET)
-                warp_reduce_scatter_store<P>(pl, lane, row);
-            else
-                warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
-        };
-        if constexpr (DET) {
-            const int w = t >> 5;
-            for (int c1 = bend; c1 > bbeg; c1 -= GS2_DET_CHUNK) {   // CTA-uniform chunks
-                const int c0 = max(bbeg, c1 - GS2_DET_CHUNK);
-                for (int jj = min(c1, wlast) - 1; jj >= c0; --jj) entry(jj, &sDet[w][jj - c0][0]);
-                __syncthreads();
-                const int cnt = (c1 - c0) * P;
-                for (int q = t; q < cnt; q += NT) {
-                    const int e = q / P, i = q - e * P;
-                    float v = sDet[0][e][i];
-                    sDet[0][e][i] = 0.f;
-#pragma unroll
-                    for (int ww = 1; ww < NW; ++ww) {   // warp order
-                        v = __fadd_rn(v, sDet[ww][e][i]);
-                        sDet[ww][e][i] = 0.f;
-                    }
-                    det_part[(size_t)(r.x + (uint32_t)(c0 + e)) * P + i] = v;
+                for (int r = 0; r < NPR; ++r) {
+                    const float2 xg = mul2(qf[r], f2(-0.72134752044448170368f));   // gs2_falloff, both pixels
+                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G[r].x) : "f"(xg.x));
+                    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G[r].y) : "f"(xg.y));
+                    const bool c0 = qf[r].x < B.w, c1 = qf[r].y < B.w;   // clamped at alpha_max
+                    al[r] = mul2(f2(B.y), G[r]);
+                    al[r].x = lv[r][0] ? (c0 ? amax : al[r].x) : 0.f;
+                    al[r].y = lv[r][1] ? (c1 ? amax : al[r].y) : 0.f;
+                    ap[r] = make_float2(c0 ? 0.f : al[r].x, c1 ? 0.f : al[r].y);
                 }
-                __syncthreads();
+                float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (GROUP != GS2_COLOR) C = sC[buf][s];
+                float pl[P];
+                if constexpr (GROUP == GS2_POS) {
+                    float2 pe[NPR][3], ph[NPR][3];
+#pragma unroll
+                    for (int r = 0; r < NPR; ++r) {
+                        if constexpr (EH_SMEM) {
+                            const float4 k0 = sEP[r][0][t], k1 = sEP[r][1][t], k2 = sEP[r][2][t];
+                            pe[r][0] = make_float2(k0.x, k0.y);
+                            pe[r][1] = make_float2(k0.z, k0.w);
+                            pe[r][2] = make_float2(k1.x, k1.y);
+                            ph[r][0] = make_float2(k1.z, k1.w);
+                            ph[r][1] = make_float2(k2.x, k2.y);
+                            ph[r][2] = make_float2(k2.z, k2.w);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                pe[r][c] = pe2[r][c];
+                                ph[r][c] = ph2[r][c];
+                            }
+                        }
+                    }
+                    const uint32_t k = sId[buf][s];
+                    pos_pairs<NPR>(
+                        pst, pe, ph, A, B, C, al, ap, lv, dx, dy, gn != 0, pl,
+                        [&](const float (&v)[P]) {
+                            if constexpr (DET)
+                                reduce_scatter_part<P - 32, 32, P, float, 16, true>(v, lane, nullptr, 0, 0u, row);
+                            else
+                                reduce_scatter_part<P - 32, 32, P, ACC>(v, lane, zbuf, n, k);
+                        },
+                        [&](const float (&v)[P]) {
+                            if constexpr (DET)
+                                reduce_scatter_part<32, 0, P, float, 16, true>(v, lane, nullptr, 0, 0u, row);
+                            else
+                                reduce_scatter_part<32, 0, P, ACC>(v, lane, zbuf, n, k);
+                        });
+                    return;
+                } else {
+                    float2 pl2[P];
+#pragma unroll
+                    for (int i = 0; i < P; ++i) pl2[i] = f2(0.f);
+#pragma unroll
+                    for (int r = 0; r < NPR; ++r) {
+                        if constexpr (EH_SMEM) {
+                            const float4 k0 = sEP[r][0][t], k1 = sEP[r][1][t], k2 = sEP[r][2][t];
+                            const float2 pe[3] = {make_float2(k0.x, k0.y), make_float2(k0.z, k0.w), make_float2(k1.x, k1.y)};
+                            const float2 ph[3] = {make_float2(k1.z, k1.w), make_float2(k2.x, k2.y), make_float2(k2.z, k2.w)};
+                            pair_payload<GROUP, P>(pst[r], pe, ph, A, B, C, G[r], al[r], ap[r], lv[r][0], lv[r][1], dx,
+                                                   dy[r], pl2);
+                        } else {
+                            pair_payload<GROUP, P>(pst[r], pe2[r], ph2[r], A, B, C, G[r], al[r], ap[r], lv[r][0],
+                                                   lv[r][1], dx, dy[r], pl2);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < P; ++i) pl[i] = pl2[i].x + pl2[i].y;
+                }
+                if constexpr (DET)
+                    warp_reduce_scatter_store<P>(pl, lane, row);
+                else
+                    warp_reduce_scatter_add<P, ACC>(pl, lane, zbuf, n, sId[buf][s]);
+            };
+            if constexpr (DET) {
+                const int w = t >> 5;
+                for (int c1 = bend; c1 > bbeg; c1 -= GS2_DET_CHUNK) {   // CTA-uniform chunks
+                    const int c0 = max(bbeg, c1 - GS2_DET_CHUNK);
+                    for (int jj = min(c1, wlast) - 1; jj >= c0; --jj) entry(jj, &sDet[w][jj - c0][0]);
+                    __syncthreads();
+                    const int cnt = (c1 - c0) * P;
+                    for (int q = t; q < cnt; q += NT) {
+                        const int e = q / P, i = q - e * P;
+                        float v = sDet[0][e][i];
+                        sDet[0][e][i] = 0.f;
+#pragma unroll
+                        for (int ww = 1; ww < NW; ++ww) {   // warp order
+                            v = __fadd_rn(v, sDet[ww][e][i]);
+                            sDet[ww][e][i] = 0.f;
+                        }
+                        det_part[(size_t)(r.x + (uint32_t)(c0 + e)) * P + i] = v;
+                    }
+                    __syncthreads();
+                }
+            } else {
+                for (int jj = min(bend, wlast) - 1; jj >= bbeg; --jj) entry(jj, nullptr);
             }
-        } else {
-            for (int jj = min(bend, wlast) - 1; jj >= bbeg; --jj) entry(jj, nullptr);
         }
-    }
-    if constexpr (DET) {   // entries past the last contributor of every pixel contribute nothing
-        const int nl = (int)(r.y - r.x);
-        for (int q = t + maxlast * P; q < nl * P; q += NT) det_part[(size_t)r.x * P + q] = 0.f;
-    }
-    if constexpr (!SPLIT) break;
-    __syncthreads();   // this item's shared memory is free before the next item is fetched
+        if constexpr (DET) {   // entries past the last contributor of every pixel contribute nothing
+            const int nl = (int)(r.y - r.x);
+            for (int q = t + maxlast * P; q < nl * P; q += NT) det_part[(size_t)r.x * P + q] = 0.f;
+        }
+        if constexpr (!SPLIT) break;
+        __syncthreads();   // this item's shared memory is free before the next item is fetched
     }
     if (active_stat) {
         unsigned long long c = nact;
