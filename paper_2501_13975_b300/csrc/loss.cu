@@ -81,18 +81,32 @@ __global__ void __launch_bounds__(256, 3) k_ssim(const float *__restrict__ img, 
     };
     for (int c = 0; c < 3; ++c) {
         const float *X = img + c * P, *Y = tgt + c * P;
-        for (int i = t; i < SM_IN; i += 256) {
-            const int r = i / IN_W, q = i % IN_W;
-            const int gx = x0 - 2 * LRAD + q, gy = y0 - 2 * LRAD + r;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            float xv = in ? X[(size_t)gy * W + gx] : 0.f, yv = in ? Y[(size_t)gy * W + gx] : 0.f;
-            // a non-finite pixel counts as 0 and raises the status bit
-            if (!(isfinite(xv) && isfinite(yv))) {
-                if (status) atomicOr(status, GS2_ST_NONFINITE);
-                xv = isfinite(xv) ? xv : 0.f;
-                yv = isfinite(yv) ? yv : 0.f;
+        {
+            // every load of this thread first, then the stores (the loads overlap)
+            constexpr int PER = (SM_IN + 255) / 256;
+            float xv[PER], yv[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int i = t + 256 * u;
+                const int r = i / IN_W, q = i % IN_W;
+                const int gx = x0 - 2 * LRAD + q, gy = y0 - 2 * LRAD + r;
+                const bool in = i < SM_IN && gx >= 0 && gx < W && gy >= 0 && gy < H;
+                xv[u] = in ? X[(size_t)gy * W + gx] : 0.f;
+                yv[u] = in ? Y[(size_t)gy * W + gx] : 0.f;
             }
-            sXY[i] = make_float2(xv, yv);
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int i = t + 256 * u;
+                if (i >= SM_IN) break;
+                float xx = xv[u], yy = yv[u];
+                // a non-finite pixel counts as 0 and raises the status bit
+                if (!(isfinite(xx) && isfinite(yy))) {
+                    if (status) atomicOr(status, GS2_ST_NONFINITE);
+                    xx = isfinite(xx) ? xx : 0.f;
+                    yy = isfinite(yy) ? yy : 0.f;
+                }
+                sXY[i] = make_float2(xx, yy);
+            }
         }
         __syncthreads();
         // horizontal window sums of x, y, xx, yy, xy: a thread slides one
