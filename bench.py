@@ -1152,7 +1152,7 @@ def run_reference(args):
     return res
 
 
-KERNEL_REV = "accum-v14"
+KERNEL_REV = "accum-v15"
 
 
 def main():
